@@ -1,0 +1,3 @@
+"""FP64 CPU oracle (test infrastructure only; see sfs_oracle's header)."""
+from .sfs_oracle import *  # noqa: F401,F403
+from .sfs_oracle import Geometry, LateralFFTOperator  # noqa: F401
