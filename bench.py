@@ -1,0 +1,391 @@
+"""Benchmark: FISTA iterations/s of the sub-sampled Fourier SAFT reconstruction.
+
+One step = one complete reconstruction of one measurement vector: lambda by
+the mu rule (one A^H apply and a max reduction on the device) followed by
+`iters` FISTA iterations (two operator applies each), through the C ABI.
+The operator (generator table) and its Lipschitz constant are built once per
+geometry before the timed region, as the paper reuses sigma_max across
+reconstructions; their setup times are reported separately.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload vol32]
+  python bench.py --impl reference ...   # the FP64 CPU oracle, same workload
+
+Multi-GPU (torchrun): independent replicas, one scene per rank (weak
+scaling); no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+STRATEGY_NAMES = {"random": 0, "contiguous": 1, "equispaced": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="vol32", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--strategy", default="random", choices=sorted(STRATEGY_NAMES))
+    ap.add_argument("--iters", type=int, default=None)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload_desc(name, w, strategy, iters):
+    if w["Ny"] == 1:
+        shape = "2-D line scan %d positions, %dx%d voxels" % (w["Nx"], w["Nx"], w["Nz"])
+    else:
+        shape = "3-D %dx%d scan, %dx%dx%d voxels" % (w["Nx"], w["Ny"], w["Nx"], w["Ny"], w["Nz"])
+    return ("%s: %s, Nt=%d, M=%d %s bins per position, %d FISTA iterations, mu=%g, "
+            "%g dB SNR" % (name, shape, w["Nt"], w["M"], strategy, iters, w["mu"], w["snr_db"]))
+
+
+# ------------------------------------------------------------------ clocks ---
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle ---
+
+def oracle_setup(name, w, strategy, seed):
+    import oracle as O
+    params = synth.geometry_params(name)
+    go = O.Geometry(**params)
+    idx = O.select_indices(go, STRATEGY_NAMES[strategy], w["M"], True, seed)
+    t0 = time.perf_counter()
+    op = O.LateralFFTOperator(go, idx)
+    t_table = time.perf_counter() - t0
+    x_true = make_scene(w, seed)
+    y0 = op.apply_A(x_true)
+    sig = synth.noise_scale(float(np.vdot(y0, y0).real), y0.size, w["snr_db"])
+    y = y0 + sig * synth.unit_noise(y0.shape, seed=seed + 1)
+    return O, op, y, t_table
+
+
+def time_oracle_iterations(O, op, y, mu, seconds):
+    """FISTA iterations of the FP64 oracle for about `seconds`; returns
+    (iterations/s, iterations done, threads actually used)."""
+    lam = O.lambda_from_mu(op.apply_AH, y, mu)
+    L = 1.0e9  # step size does not change the work per iteration
+    # one iteration first to size the sample
+    c0, t0 = time.process_time(), time.perf_counter()
+    O.fista(op.apply_A, op.apply_AH, y, lam, L, 1)
+    one = time.perf_counter() - t0
+    n = max(1, int(seconds / max(one, 1e-6)))
+    c0, t0 = time.process_time(), time.perf_counter()
+    O.fista(op.apply_A, op.apply_AH, y, lam, L, n)
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    return n / wall, n, max(1, round(cpu / wall))
+
+
+def make_scene(w, seed):
+    shape = (w["Nz"], w["Ny"], w["Nx"])
+    if w.get("n_scatter") is None:
+        return synth.scene(shape, None, w["amp"], seed=seed, p_bernoulli=w["p_bernoulli"])
+    return synth.scene(shape, w["n_scatter"], w["amp"], seed=seed)
+
+
+# ------------------------------------------------------------------- main ---
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 CPU oracle, as it stands, on rank 0."""
+    if rank != 0:
+        return
+    w = synth.WORKLOADS[args.workload]
+    iters = args.iters or w["iters"]
+    O, op, y, _ = oracle_setup(args.workload, w, args.strategy, seed=1001)
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        time_oracle_iterations(O, op, y, w["mu"], per_step)
+    vals, n_tot, threads, t_tot = [], 0, 1, 0.0
+    for _ in range(args.steps):
+        v, n, threads = time_oracle_iterations(O, op, y, w["mu"], per_step)
+        vals.append(v)
+        n_tot += n
+        t_tot += n / v
+    value = n_tot / t_tot
+    line = {
+        "impl": "reference", "metric": "FISTA iterations/s", "value": value,
+        "unit": "it/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(args.workload, w, args.strategy, iters)},
+        "cpu_baseline": {"value": value, "unit": "it/s", "cores": threads, "kind": "oracle",
+                         "sample": "%d FISTA iterations of the FP64 lateral-FFT oracle over "
+                                   "%d steps" % (n_tot, args.steps)},
+        "e2e": {"value": value, "unit": "it/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("sfs_kernels.cu", "sfs_fft.cuh"):
+        with open(os.path.join(ROOT, "paper_2012_04534_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload, strategy):
+    """DRAM bytes per contraction launch from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "contract_traffic.json")
+    try:
+        with open(p) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    key = "%s/%s" % (workload, strategy)
+    ent = rec.get(key)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    from paper_2012_04534_gb300 import build as sfs_build
+    if rank == 0 or world == 1:
+        sfs_build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.barrier()
+        sfs_build.build()
+    from paper_2012_04534_gb300 import sfs
+
+    dev = local
+    torch.cuda.set_device(dev)
+    w = synth.WORKLOADS[args.workload]
+    iters = args.iters or w["iters"]
+    seed = 1001 + 17 * rank
+    params = dict(synth.geometry_params(args.workload), device=dev)
+
+    # ---- setup (outside the timed region) ----
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    geom = sfs.Geometry(**params)
+    op = sfs.Operator.select(geom, STRATEGY_NAMES[args.strategy], w["M"], True, seed)
+    torch.cuda.synchronize()
+    t_table = time.perf_counter() - t0
+    info = op.info
+    x_true = make_scene(w, seed)
+    xt = torch.from_numpy(x_true.astype(np.complex64)).cuda()
+    y0 = op.apply_A(xt)
+    torch.cuda.synchronize()
+    y0h = y0.cpu().numpy().astype(np.complex128)
+    sig = synth.noise_scale(float(np.vdot(y0h, y0h).real), y0h.size, w["snr_db"])
+    y_host = (y0h + sig * synth.unit_noise(y0h.shape, seed=seed + 1)).astype(np.complex64)
+    y = torch.from_numpy(y_host).cuda()
+    t0 = time.perf_counter()
+    L, _ = op.lipschitz(max_iter=500, rtol=1e-6, seed=seed, safety=1e-3)
+    t_lip = time.perf_counter() - t0
+    x = torch.empty(op.shape_x, dtype=torch.complex64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        op.fista(y, -w["mu"], L, iters, x=x)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- timed region: device time, inputs resident ----
+    clocks = ClockSampler(dev)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)  # let the sampler start before the timed work
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps * iters / (ms / 1e3)
+    launches_per_step = 4 * iters + 5 if iters > 0 else 4
+
+    # ---- end to end through the public API with pinned host buffers ----
+    y_pin = torch.from_numpy(y_host).pin_memory()
+    x_pin = torch.empty(op.shape_x, dtype=torch.complex64).pin_memory()
+    y_dev = torch.empty_like(y)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        y_dev.copy_(y_pin, non_blocking=True)
+        op.fista(y_dev, -w["mu"], L, iters, x=x)
+        x_pin.copy_(x, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e = world * args.steps * iters / (ms_e2e / 1e3)
+
+    # ---- roofline of the dominant kernels (events around each launch) ----
+    for _ in range(args.steps):
+        op.fista(y, -w["mu"], L, iters, x=x, time_kernels=True)
+    fwd_ms, adj_ms, n_launch = op.kernel_times()
+    Nk, U, Nz = info["Nkappa"], info["U"], info["Nz"]
+    alg_bytes = info["table_bytes"] + 8 * Nk * (Nz + U)  # table + spectra in/out
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(peaks_path) as fh:
+            peak = float(json.load(fh)["hbm_gbs"])
+        peak_src = "measured"
+    except (OSError, ValueError, KeyError):
+        peak, peak_src = 6800.0, "fallback"
+    avg_ms = 0.5 * (fwd_ms + adj_ms)
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+    traffic = measured_traffic(args.workload, args.strategy)
+
+    # ---- CPU baseline: the FP64 oracle, bounded sample, rank 0 only ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        O, oop, oy, t_otab = oracle_setup(args.workload, w, args.strategy, seed)
+        v, n, threads = time_oracle_iterations(O, oop, oy, w["mu"], args.cpu_seconds)
+        cpu = {"value": v, "unit": "it/s", "cores": threads, "kind": "oracle",
+               "sample": "%d FISTA iterations of the FP64 lateral-FFT oracle on the same "
+                         "workload (table build %.1f s excluded)" % (n, t_otab)}
+
+    if rank == 0:
+        line = {
+            "metric": "FISTA iterations/s", "value": value, "unit": "it/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64 (f32)", "data": "synthetic",
+            "config": {
+                "workload": workload_desc(args.workload, w, args.strategy, iters),
+                "parallelism": "replicas" if world > 1 else "single GPU",
+                "l2": "inputs larger than L2 (generator table %.0f MB > 129 MB)"
+                      % (info["table_bytes"] / 1e6),
+                "U": U, "Nkappa": Nk, "Nz": Nz, "P": [info["Px"], info["Py"]],
+                "setup_s": {"table_build": round(t_table, 4), "lipschitz": round(t_lip, 4)},
+                "L": L,
+            },
+            "e2e": {"value": e2e, "unit": "it/s",
+                    "h2d_bytes_per_step": int(y_host.nbytes),
+                    "d2h_bytes_per_step": int(x_pin.numel() * 8)},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_src,
+                         "traffic": None if traffic is None else traffic["bytes_per_launch"],
+                         "kernel": "depth contraction (forward and adjoint, averaged)",
+                         "alg_bytes_per_launch": alg_bytes,
+                         "fwd_ms": fwd_ms, "adj_ms": adj_ms, "launches_timed": 2 * n_launch},
+            "clocks": clk,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * sfs.h -- C ABI of libsfs, the GB300 (sm_103a) implementation of the
+ * sub-sampled Fourier SAFT operator A = S F H of Kirchhof et al., "Frequency
+ * Sub-Sampling of Ultrasound Non-Destructive Measurements: Acquisition,
+ * Reconstruction and Performance" (arXiv 2012.04534), its adjoint A^H, and
+ * FISTA with complex soft thresholding.
+ *
+ * Conventions shared by every entry point
+ *   - Complex values are interleaved single precision (re, im) pairs
+ *     ("c64", 8 bytes), the layout of a C99 float complex or a torch.complex64.
+ *   - Reflectivity x: c64 [Nz][Ny][Nx], x fastest (the vectorisation order
+ *     of Sec. II-A), V = Nx*Ny*Nz elements.
+ *   - Measurements y: c64 [S][M], S = Nx*Ny scan positions, s = iy*Nx + ix;
+ *     the M kept DFT bins of a position are in ascending bin order.
+ *   - Pointers named *_dev are device pointers on the operator's device, at
+ *     least 16-byte aligned, owned by the caller; the library never frees
+ *     them.  Pointers named *_host are ordinary host memory.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     that take a stream enqueue their work on it and return without
+ *     synchronising unless stated otherwise.
+ *   - Every call returns an sfs_status.  On failure sfs_last_error() gives a
+ *     message for the calling thread; outputs are then unspecified.  No C++
+ *     exception crosses this boundary.  Handles are not thread safe: calls on
+ *     one operator must not overlap in time from several host threads.
+ */
+#ifndef SFS_H_
+#define SFS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sfs_status {
+  SFS_OK = 0,
+  SFS_ERR_INVALID_ARG = -1,    /* null pointer, bad size, unsupported shape   */
+  SFS_ERR_BAND_TOO_NARROW = -2,/* M exceeds the widest candidate band (40 dB) */
+  SFS_ERR_CUDA = -3,           /* a CUDA runtime call failed                  */
+  SFS_ERR_OOM = -4,            /* device allocation failed                    */
+  SFS_ERR_TIMEOUT = -5,        /* a bounded device wait gave up               */
+  SFS_ERR_NOT_CONVERGED = -6,  /* iteration limit reached; result is last est */
+  SFS_ERR_NON_FINITE = -7      /* NaN or Inf met in an input or a reduction   */
+} sfs_status;
+
+/* Frequency selection strategies (Sec. III-A, Table I; see sfs_select_freqs) */
+typedef enum sfs_strategy {
+  SFS_SEL_RANDOM = 0,      /* uniform M-subset of the candidate band (Phi_rnd)  */
+  SFS_SEL_CONTIGUOUS = 1,  /* M adjacent bins centred on round(fc Nt / fs)      */
+  SFS_SEL_EQUISPACED = 2   /* k_lo + floor((2i+1)|C|/(2M)), i = 0..M-1          */
+} sfs_strategy;
+
+/*
+ * Acquisition geometry and pulse: the scan grid G_2D and voxel grid G_3D of
+ * Sec. II-A, the time of flight of Eq. (3), and the Gaussian pulse
+ * h(t) = exp(-alpha^2 t^2 + j 2 pi fc t) of Sec. VI.
+ */
+typedef struct sfs_geometry_desc {
+  int32_t Nx, Ny;      /* scan positions per lateral axis (Ny = 1: line scan) */
+  double dx, dy;       /* lateral pitch of scan and voxel grid [m]            */
+  int32_t Nz;          /* voxels along depth                                  */
+  double z0, dz;       /* depth of the first voxel and depth pitch [m]        */
+  double c;            /* speed of sound [m/s]                                */
+  double fs;           /* sampling rate of the A-scans [Hz]                   */
+  int32_t Nt;          /* samples per A-scan; bins k = 0..Nt/2 are candidates */
+  double t0;           /* receive-window start [s]; NaN selects
+                          floor((2 z0/c - 3/alpha) fs)/fs                      */
+  double fc;           /* pulse centre frequency [Hz]                         */
+  double frac_bw;      /* -6 dB full amplitude bandwidth as a fraction of fc;
+                          alpha = pi (frac_bw fc / 2) / sqrt(ln 2)            */
+  double theta;        /* directivity angle [rad]; 0 turns g off (g = 1),
+                          else g = exp(-r^2 / (z tan theta)^2)                */
+  int32_t device;      /* CUDA device ordinal that holds the operator         */
+} sfs_geometry_desc;
+
+typedef struct sfs_geometry sfs_geometry;  /* opaque, library owned */
+typedef struct sfs_operator sfs_operator;  /* opaque, library owned */
+
+/* Sizes and derived constants of an operator (filled by sfs_operator_info). */
+typedef struct sfs_operator_info_t {
+  int32_t S, M, V, Nz;  /* scan positions, bins per position, voxels, depth   */
+  int32_t U;            /* bins in the union of all positions' sets           */
+  int32_t Px, Py;       /* lateral FFT sizes (powers of two >= 2N-1)          */
+  int32_t Nkappa;       /* lateral wavenumbers Px*Py                          */
+  int32_t k_lo, k_hi;   /* candidate band (inclusive) used by the selection   */
+  double band_db;       /* band rung (dB below the peak bin) that was used    */
+  double alpha, t0;     /* pulse rate [1/s] and receive-window start [s]      */
+  int64_t table_bytes;  /* bytes of the lateral-FFT generator table          */
+  int32_t launches_per_iter; /* kernels one FISTA iteration launches          */
+} sfs_operator_info_t;
+
+/*
+ * Geometry.  Validates the descriptor (positive sizes, Nx, Ny <= 64 for a
+ * 3-D scan, Nx <= 2048 for a line scan, Nt >= 2, positive pitches, c, fs,
+ * fc, frac_bw) and stores a copy.  Frees with sfs_destroy_geometry.
+ * Errors: SFS_ERR_INVALID_ARG.
+ */
+int sfs_create_geometry(const sfs_geometry_desc* desc, sfs_geometry** out);
+int sfs_destroy_geometry(sfs_geometry* g);
+
+/*
+ * Host-only frequency selection (no device work): the index sets S_{nx,ny}
+ * of Sec. II-B / III-A.  The candidate band is C = {0 <= k <= Nt/2 :
+ * |H(f_k)| >= 10^(-b/20) max_k |H(f_k)|} for the first b of 6, 10, 20, 40 dB
+ * holding at least M bins.  RANDOM draws, for each position s (or once with
+ * s = 0 when per_position is 0), a partial Fisher-Yates M-subset of C from
+ * the SplitMix64 stream seeded with seed XOR (s * 0x9E3779B97F4A7C15), and
+ * sorts it.  CONTIGUOUS and EQUISPACED are shared by all positions.
+ * idx_out_host: int32 [S][M] (caller-owned).  band_out_host (may be NULL):
+ * int32[2] = {k_lo, k_hi}.  Errors: SFS_ERR_INVALID_ARG, SFS_ERR_BAND_TOO_NARROW.
+ */
+int sfs_select_indices(const sfs_geometry* g, int strategy, int M,
+                       int per_position, uint64_t seed, int32_t* idx_out_host,
+                       int32_t* band_out_host);
+
+/*
+ * Selection plus operator build: computes the index sets as
+ * sfs_select_indices does (bit-identical), then builds the operator as
+ * sfs_operator_from_indices does.  idx_out_host (int32 [S][M]) and
+ * mask_out_host (uint32 [S][ceil((Nt/2+1)/32)], bit k of position s set when
+ * bin k is kept) may be NULL.  Synchronises the device.
+ */
+int sfs_select_freqs(sfs_geometry* g, int strategy, int M, int per_position,
+                     uint64_t seed, int32_t* idx_out_host,
+                     uint32_t* mask_out_host, sfs_operator** op);
+
+/*
+ * Operator from given index sets (e.g. sets shared with another
+ * implementation).  idx_host: int32 [S][M], each row strictly ascending,
+ * bins in 0..Nt/2.  Builds on the device the lateral-FFT table of the
+ * generating elements of the block 2-level Toeplitz H (Theorem 2, Sec. IV-B)
+ * evaluated at the union U of the kept bins with the frequency-domain model
+ * of Eq. (4):  h_{k,z}[d] = fs H(f_k) g exp(-j 2 pi f_k (tau(d, z) - t0)).
+ * Memory: 8 * Px*Py * U * Nz bytes for the table plus O(V + U*Px*Py) work
+ * space.  Synchronises the device.
+ * Errors: SFS_ERR_INVALID_ARG, SFS_ERR_OOM, SFS_ERR_CUDA.
+ */
+int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
+                              sfs_operator** op);
+int sfs_destroy_operator(sfs_operator* op);
+int sfs_operator_info(const sfs_operator* op, sfs_operator_info_t* info);
+
+/*
+ * Forward projection phi_{Phi H}: y = A x (Sec. IV-A; computed by the fast
+ * transform of Sec. IV-B, Algorithm 2, restricted to the kept bins).
+ * x_dev: c64 [Nz][Ny][Nx] (read), y_dev: c64 [S][M] (written).
+ */
+int sfs_apply_A(sfs_operator* op, const void* x_dev, void* y_dev, void* stream);
+
+/*
+ * Backward projection beta_{Phi H}: x = A^H y (Sec. IV-A; the composition
+ * beta_H o beta_Phi of Sec. IV-B).  y_dev: c64 [S][M] (read),
+ * x_dev: c64 [Nz][Ny][Nx] (written).  With y the measurements this is the
+ * one-step "compressed SAFT" image of Remark 1.
+ */
+int sfs_apply_AH(sfs_operator* op, const void* y_dev, void* x_dev, void* stream);
+
+/*
+ * ||A^H y||_inf (used by the regularisation rule lambda = mu ||beta(y)||_inf
+ * of Sec. VII).  Synchronises `stream`; writes the value to *out_host.
+ */
+int sfs_max_abs_AH(sfs_operator* op, const void* y_dev, double* out_host,
+                   void* stream);
+
+/*
+ * Lipschitz constant L >= sigma_max^2 of the gradient of 1/2||Ax - y||^2
+ * (Sec. IV-C).  Power iteration on A^H A from a seeded start vector, norms
+ * and Rayleigh quotients accumulated in FP64, stopped when the estimate
+ * changes by less than rtol (checked every few iterations) or after
+ * max_iter iterations; *L_out = estimate * (1 + safety).  Synchronises
+ * `stream`.  Returns SFS_ERR_NOT_CONVERGED (with *L_out set) when max_iter
+ * is reached.
+ */
+int sfs_lipschitz(sfs_operator* op, int max_iter, double rtol, uint64_t seed,
+                  double safety, double* L_out, void* stream);
+
+/* Flags of sfs_fista */
+#define SFS_FISTA_WARM_START 1u   /* x_inout_dev holds x_0 on entry (else 0)  */
+#define SFS_FISTA_TIME_KERNELS 2u /* time the two contraction kernels          */
+
+/*
+ * FISTA (Algorithm 1, Sec. IV-A) for min 1/2||A x - y||^2 + lambda ||x||_1:
+ *   x_k = tau_{lambda/L}(gamma_k - A^H(A gamma_k - y)/L),
+ *   gamma_{k+1} = x_k + ((t_k - 1)/t_{k+1})(x_k - x_{k-1}),  t_1 = 1,
+ * with tau the complex soft threshold max(|z| - a, 0) z/|z|.
+ * y_dev: c64 [S][M] (read).  lambda >= 0 is used as given; lambda < 0 means
+ * lambda = -lambda * ||A^H y||_inf (the mu rule of Sec. VII, computed on the
+ * device).  L: Lipschitz constant (> 0), e.g. from sfs_lipschitz.
+ * x_inout_dev: c64 [Nz][Ny][Nx]; receives x_iters.  obj_hist_host (may be
+ * NULL): double [iters], entry k-1 = 1/2||A gamma_k - y||^2 + lambda||x_k||_1
+ * (a monitor evaluated with the residual at gamma_k); when given, the call
+ * synchronises `stream`.  Errors: SFS_ERR_INVALID_ARG, SFS_ERR_CUDA.
+ */
+int sfs_fista(sfs_operator* op, const void* y_dev, double lambda, double L,
+              int iters, void* x_inout_dev, uint32_t flags,
+              double* obj_hist_host, void* stream);
+
+/*
+ * Average device time per launch [ms] of the forward and adjoint depth
+ * contraction kernels during the last sfs_fista call made with
+ * SFS_FISTA_TIME_KERNELS (CUDA events around each launch).  Synchronises the
+ * operator's device.  n_out_host receives the number of launches averaged.
+ */
+int sfs_kernel_times(sfs_operator* op, double* fwd_ms, double* adj_ms,
+                     int32_t* n_out_host);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* sfs_last_error(void);
+
+/* Library version string. */
+const char* sfs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFS_H_ */

@@ -1,0 +1,756 @@
+// Host side of libsfs: the C ABI of include/sfs.h.
+//
+// Geometry and pulse constants are computed on the host in FP64 (Sec. II-A,
+// Eq. (3); pulse of Sec. VI).  The frequency selection (Sec. III-A) is
+// integer work on the host.  Everything on the operator's data path runs in
+// the device kernels of sfs_kernels.cu; this file only sizes buffers,
+// validates arguments, and enqueues launches on the caller's stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sfs_internal.h"
+
+namespace sfs {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();  // clear the sticky-free allocation error
+    return SFS_ERR_OOM;
+  }
+  return SFS_ERR_CUDA;
+}
+
+namespace {
+
+// Sets the operator's device for the scope of an API call and restores the
+// caller's current device afterwards.
+class DeviceScope {
+ public:
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+    ok_ = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceScope() {
+    if (prev_ >= 0) cudaSetDevice(prev_);
+  }
+  bool ok() const { return ok_; }
+
+ private:
+  int prev_ = -1;
+  bool ok_ = false;
+};
+
+int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+double pulse_alpha(double fc, double frac_bw) {
+  return M_PI * (0.5 * frac_bw * fc) / sqrt(log(2.0));
+}
+
+// |H(f)| of h(t) = exp(-alpha^2 t^2 + j 2 pi fc t): (sqrt(pi)/alpha) exp(-(pi (f - fc)/alpha)^2)
+double pulse_mag(double f, double fc, double alpha) {
+  const double a = M_PI * (f - fc) / alpha;
+  return sqrt(M_PI) / alpha * exp(-a * a);
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): Weyl increment plus the 64-bit mixer.
+struct SplitMix64 {
+  uint64_t s;
+  uint64_t next() {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+};
+
+constexpr double kBandLadderDb[4] = {6.0, 10.0, 20.0, 40.0};
+
+int candidate_band(const sfs_geometry* g, int M, int* k_lo, int* k_hi, double* db) {
+  const int nb = g->d.Nt / 2 + 1;
+  std::vector<double> mag(nb);
+  double peak = 0.0;
+  for (int k = 0; k < nb; ++k) {
+    mag[k] = pulse_mag((double)k * g->d.fs / g->d.Nt, g->d.fc, g->alpha);
+    peak = std::max(peak, mag[k]);
+  }
+  for (double b : kBandLadderDb) {
+    const double thr = peak * pow(10.0, -b / 20.0);
+    int lo = -1, hi = -1, n = 0;
+    for (int k = 0; k < nb; ++k)
+      if (mag[k] >= thr) {
+        if (lo < 0) lo = k;
+        hi = k;
+        ++n;
+      }
+    if (n >= M) {
+      *k_lo = lo;
+      *k_hi = hi;
+      *db = b;
+      return SFS_OK;
+    }
+  }
+  set_error("M = %d exceeds the 40 dB band of the pulse", M);
+  return SFS_ERR_BAND_TOO_NARROW;
+}
+
+int select_host(const sfs_geometry* g, int strategy, int M, int per_position, uint64_t seed,
+                int32_t* idx, int* k_lo_out, int* k_hi_out, double* db_out) {
+  if (M <= 0) {
+    set_error("M must be positive (got %d)", M);
+    return SFS_ERR_INVALID_ARG;
+  }
+  int k_lo, k_hi;
+  double db;
+  SFS_TRY(candidate_band(g, M, &k_lo, &k_hi, &db));
+  const int n = k_hi - k_lo + 1;
+  const int S = g->d.Nx * g->d.Ny;
+  switch (strategy) {
+    case SFS_SEL_RANDOM: {
+      std::vector<int> perm(n);
+      const int rows = per_position ? S : 1;
+      for (int s = 0; s < rows; ++s) {
+        for (int i = 0; i < n; ++i) perm[i] = i;
+        SplitMix64 rng{seed ^ ((uint64_t)s * 0x9E3779B97F4A7C15ull)};
+        for (int i = 0; i < M; ++i) {
+          const uint64_t hi32 = rng.next() >> 32;
+          const int j = i + (int)((hi32 * (uint64_t)(n - i)) >> 32);
+          std::swap(perm[i], perm[j]);
+        }
+        std::sort(perm.begin(), perm.begin() + M);
+        for (int m = 0; m < M; ++m) idx[(size_t)s * M + m] = k_lo + perm[m];
+      }
+      if (!per_position)
+        for (int s = 1; s < S; ++s) memcpy(idx + (size_t)s * M, idx, sizeof(int32_t) * M);
+      break;
+    }
+    case SFS_SEL_CONTIGUOUS: {
+      const int kstar = (int)floor(g->d.fc * g->d.Nt / g->d.fs + 0.5);
+      const int start = std::min(std::max(kstar - M / 2, k_lo), k_hi - M + 1);
+      for (int s = 0; s < S; ++s)
+        for (int m = 0; m < M; ++m) idx[(size_t)s * M + m] = start + m;
+      break;
+    }
+    case SFS_SEL_EQUISPACED: {
+      for (int s = 0; s < S; ++s)
+        for (int m = 0; m < M; ++m)
+          idx[(size_t)s * M + m] = k_lo + (int)(((2LL * m + 1) * n) / (2LL * M));
+      break;
+    }
+    default:
+      set_error("unknown selection strategy %d", strategy);
+      return SFS_ERR_INVALID_ARG;
+  }
+  if (k_lo_out) *k_lo_out = k_lo;
+  if (k_hi_out) *k_hi_out = k_hi;
+  if (db_out) *db_out = db;
+  return SFS_OK;
+}
+
+template <typename T>
+int dev_alloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  SFS_CUDA(cudaMalloc((void**)p, count * sizeof(T)));
+  return SFS_OK;
+}
+
+void free_operator(sfs_operator* op) {
+  if (!op) return;
+  cudaFree(op->table);
+  cudaFree(op->posmap);
+  cudaFree(op->ws.Xh);
+  cudaFree(op->ws.Yh);
+  cudaFree(op->ws.Rh);
+  cudaFree(op->ws.Gh);
+  cudaFree(op->ws.xk);
+  cudaFree(op->ws.gam);
+  cudaFree(op->ws.ybuf);
+  cudaFree(op->ws.vbuf);
+  cudaFree(op->ws.scal);
+  cudaFree(op->ws.red);
+  cudaFree(op->ws.obj);
+  for (cudaEvent_t e : op->ev) cudaEventDestroy(e);
+  delete op;
+}
+
+PlaneDims dims_of(const sfs_operator* op) {
+  PlaneDims d;
+  d.Nx = op->geo.d.Nx;
+  d.Ny = op->geo.d.Ny;
+  d.Nz = op->geo.d.Nz;
+  d.Px = op->geo.Px;
+  d.Py = op->geo.Py;
+  d.Nk = op->Nk;
+  d.S = op->S;
+  d.M = op->M;
+  d.U = op->U;
+  return d;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// y = A x on `st` (x, y device pointers)
+int enqueue_A(sfs_operator* op, const float2* x, float2* y, double* red_sumsq, cudaStream_t st) {
+  const PlaneDims d = dims_of(op);
+  SFS_TRY(launch_fwd_planes(d, x, op->ws.Xh, st));
+  SFS_TRY(launch_contract_fwd(d, op->table, op->ws.Xh, op->ws.Yh, st));
+  SFS_TRY(launch_inv_gather(d, op->ws.Yh, op->posmap, y, red_sumsq, st));
+  return SFS_OK;
+}
+
+// x = A^H y on `st`; x may be null when only the reductions are wanted
+int enqueue_AH(sfs_operator* op, const float2* y, float2* x, double* red_sumsq,
+               unsigned int* maxabs_bits, cudaStream_t st) {
+  const PlaneDims d = dims_of(op);
+  SFS_TRY(launch_scatter_fwd(d, y, op->posmap, op->ws.Rh, st));
+  SFS_TRY(launch_contract_adj(d, op->table, op->ws.Rh, op->ws.Gh, st));
+  SFS_TRY(launch_inv_store(d, op->ws.Gh, x, red_sumsq, maxabs_bits, st));
+  return SFS_OK;
+}
+
+int ensure_obj(sfs_operator* op, int iters) {
+  if (op->ws.obj_cap >= iters) return SFS_OK;
+  cudaFree(op->ws.obj);
+  op->ws.obj = nullptr;
+  op->ws.obj_cap = 0;
+  SFS_TRY(dev_alloc(&op->ws.obj, 2 * (size_t)iters));
+  op->ws.obj_cap = iters;
+  return SFS_OK;
+}
+
+int ensure_events(sfs_operator* op, int n) {
+  while ((int)op->ev.size() < n) {
+    cudaEvent_t e;
+    SFS_CUDA(cudaEventCreate(&e));
+    op->ev.push_back(e);
+  }
+  return SFS_OK;
+}
+
+}  // namespace
+}  // namespace sfs
+
+using namespace sfs;
+
+extern "C" {
+
+const char* sfs_last_error(void) { return g_last_error.c_str(); }
+
+const char* sfs_version(void) { return "libsfs 0.1 (sm_103a)"; }
+
+int sfs_create_geometry(const sfs_geometry_desc* desc, sfs_geometry** out) {
+  clear_error();
+  if (!desc || !out) {
+    set_error("null argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  const sfs_geometry_desc& d = *desc;
+  if (d.Nx < 1 || d.Ny < 1 || d.Nz < 1 || d.Nt < 2) {
+    set_error("sizes must be positive (Nx=%d Ny=%d Nz=%d Nt=%d)", d.Nx, d.Ny, d.Nz, d.Nt);
+    return SFS_ERR_INVALID_ARG;
+  }
+  if (!(d.dx > 0) || !(d.dy > 0) || !(d.dz > 0) || !(d.c > 0) || !(d.fs > 0) || !(d.fc > 0) ||
+      !(d.frac_bw > 0) || !(d.z0 > 0) || !(d.theta >= 0) || !(d.theta < M_PI / 2)) {
+    set_error("physical parameters out of range");
+    return SFS_ERR_INVALID_ARG;
+  }
+  int Px, Py;
+  if (d.Ny == 1) {
+    Py = 1;
+    Px = std::max(64, next_pow2(2 * d.Nx - 1));
+    if (Px > 1024) {
+      set_error("line scans support Nx <= 512 (got %d)", d.Nx);
+      return SFS_ERR_INVALID_ARG;
+    }
+  } else {
+    const int P = std::max(32, next_pow2(2 * std::max(d.Nx, d.Ny) - 1));
+    if (P > kMaxP2D) {
+      set_error("area scans support Nx, Ny <= 64 (got %d x %d)", d.Nx, d.Ny);
+      return SFS_ERR_INVALID_ARG;
+    }
+    Px = Py = P;
+  }
+  sfs_geometry* g = new (std::nothrow) sfs_geometry;
+  if (!g) {
+    set_error("host allocation failed");
+    return SFS_ERR_OOM;
+  }
+  g->d = d;
+  g->alpha = pulse_alpha(d.fc, d.frac_bw);
+  if (isnan(d.t0)) g->d.t0 = floor((2.0 * d.z0 / d.c - 3.0 / g->alpha) * d.fs) / d.fs;
+  g->Px = Px;
+  g->Py = Py;
+  *out = g;
+  return SFS_OK;
+}
+
+int sfs_destroy_geometry(sfs_geometry* g) {
+  delete g;
+  return SFS_OK;
+}
+
+int sfs_select_indices(const sfs_geometry* g, int strategy, int M, int per_position,
+                       uint64_t seed, int32_t* idx_out_host, int32_t* band_out_host) {
+  clear_error();
+  if (!g || !idx_out_host) {
+    set_error("null argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  int lo, hi;
+  SFS_TRY(select_host(g, strategy, M, per_position, seed, idx_out_host, &lo, &hi, nullptr));
+  if (band_out_host) {
+    band_out_host[0] = lo;
+    band_out_host[1] = hi;
+  }
+  return SFS_OK;
+}
+
+int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
+                              sfs_operator** out) {
+  clear_error();
+  if (!g || !idx_host || !out) {
+    set_error("null argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  const sfs_geometry_desc& d = g->d;
+  const int S = d.Nx * d.Ny;
+  const int kmax = d.Nt / 2;
+  if (M <= 0 || M > kmax + 1) {
+    set_error("M = %d out of range 1..%d", M, kmax + 1);
+    return SFS_ERR_INVALID_ARG;
+  }
+  for (int s = 0; s < S; ++s)
+    for (int m = 0; m < M; ++m) {
+      const int k = idx_host[(size_t)s * M + m];
+      if (k < 0 || k > kmax || (m > 0 && k <= idx_host[(size_t)s * M + m - 1])) {
+        set_error("index row %d is not strictly ascending inside 0..%d", s, kmax);
+        return SFS_ERR_INVALID_ARG;
+      }
+    }
+  sfs_operator* op = new (std::nothrow) sfs_operator;
+  if (!op) {
+    set_error("host allocation failed");
+    return SFS_ERR_OOM;
+  }
+  op->geo = *g;
+  op->M = M;
+  op->S = S;
+  op->V = S * d.Nz;
+  op->Nk = g->Px * g->Py;
+  op->idx.assign(idx_host, idx_host + (size_t)S * M);
+  std::vector<char> used(kmax + 1, 0);
+  for (int32_t k : op->idx) used[k] = 1;
+  std::vector<int> u_of(kmax + 1, -1);
+  for (int k = 0; k <= kmax; ++k)
+    if (used[k]) {
+      u_of[k] = (int)op->bins.size();
+      op->bins.push_back(k);
+    }
+  op->U = (int)op->bins.size();
+  // band the strategies would use (reported only)
+  if (candidate_band(g, M, &op->k_lo, &op->k_hi, &op->band_db) != SFS_OK) {
+    op->k_lo = op->bins.front();
+    op->k_hi = op->bins.back();
+    op->band_db = NAN;
+    clear_error();
+  }
+  if ((size_t)op->U * 32 * 16 > (size_t)200 * 1024 || (size_t)d.Nz * 32 * 16 > (size_t)200 * 1024) {
+    set_error("U = %d or Nz = %d too large for one shared-memory tile (max 400)", op->U, d.Nz);
+    delete op;
+    return SFS_ERR_INVALID_ARG;
+  }
+
+  // host FP64 geometry tables: (tau - t0) fs / Nt split into (hi, lo) floats,
+  // directivity, per-bin amplitude fs H(f_k) / (Px Py)
+  const size_t nt = (size_t)d.Nz * d.Ny * d.Nx;
+  std::vector<float2> tof(nt);
+  std::vector<float> gdir(nt);
+  for (int iz = 0; iz < d.Nz; ++iz) {
+    const double z = d.z0 + iz * d.dz;
+    for (int ay = 0; ay < d.Ny; ++ay)
+      for (int ax = 0; ax < d.Nx; ++ax) {
+        const double rx = ax * d.dx, ry = ay * d.dy;
+        const double tau = 2.0 / d.c * sqrt(rx * rx + ry * ry + z * z);
+        const double tn = (tau - d.t0) * d.fs / d.Nt;
+        const float hi = (float)tn;
+        const float lo = (float)(tn - (double)hi);
+        const size_t i = ((size_t)iz * d.Ny + ay) * d.Nx + ax;
+        tof[i] = make_float2(hi, lo);
+        double gv = 1.0;
+        if (d.theta > 0) {
+          const double w = z * tan(d.theta);
+          gv = exp(-(rx * rx + ry * ry) / (w * w));
+        }
+        gdir[i] = (float)gv;
+      }
+  }
+  std::vector<float> amp(op->U);
+  for (int u = 0; u < op->U; ++u)
+    amp[u] = (float)(d.fs * pulse_mag((double)op->bins[u] * d.fs / d.Nt, d.fc, g->alpha) /
+                     ((double)g->Px * g->Py));
+  std::vector<int32_t> posmap((size_t)op->U * S, -1);
+  for (int s = 0; s < S; ++s)
+    for (int m = 0; m < M; ++m) posmap[(size_t)u_of[op->idx[(size_t)s * M + m]] * S + s] = m;
+
+  DeviceScope scope(d.device);
+  if (!scope.ok()) {
+    set_error("cannot select CUDA device %d", d.device);
+    delete op;
+    return SFS_ERR_CUDA;
+  }
+  float2* d_tof = nullptr;
+  float* d_gdir = nullptr;
+  float* d_amp = nullptr;
+  int32_t* d_bins = nullptr;
+  auto fail = [&](int rc) {
+    cudaFree(d_tof);
+    cudaFree(d_gdir);
+    cudaFree(d_amp);
+    cudaFree(d_bins);
+    free_operator(op);
+    return rc;
+  };
+  int rc;
+  const size_t Nk = op->Nk;
+  const size_t table_elems = Nk * op->U * d.Nz;
+  if ((rc = dev_alloc(&op->table, table_elems)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->posmap, posmap.size())) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.Xh, Nk * d.Nz)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.Gh, Nk * d.Nz)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.Yh, Nk * op->U)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.Rh, Nk * op->U)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.xk, (size_t)op->V)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.gam, (size_t)op->V)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.ybuf, (size_t)S * M)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.vbuf, (size_t)S * M)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.scal, kNumFloatScalars)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.red, kNumRed)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&d_tof, nt)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&d_gdir, nt)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&d_amp, (size_t)op->U)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&d_bins, (size_t)op->U)) != SFS_OK) return fail(rc);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMemcpy(op->posmap, posmap.data(), posmap.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_tof, tof.data(), nt * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_gdir, gdir.data(), nt * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_amp, amp.data(), op->U * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_bins, op->bins.data(), op->U * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(op->ws.scal, 0, kNumFloatScalars * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(op->ws.red, 0, kNumRed * sizeof(double));
+  if (e != cudaSuccess) return fail(cuda_fail(e, "upload of operator tables", __FILE__, __LINE__));
+  const PlaneDims pd = dims_of(op);
+  if ((rc = launch_build_table(pd, d_tof, d_gdir, d_amp, d_bins, op->table, 0)) != SFS_OK)
+    return fail(rc);
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(cuda_fail(e, "generator table build", __FILE__, __LINE__));
+  cudaFree(d_tof);
+  cudaFree(d_gdir);
+  cudaFree(d_amp);
+  cudaFree(d_bins);
+  *out = op;
+  return SFS_OK;
+}
+
+int sfs_select_freqs(sfs_geometry* g, int strategy, int M, int per_position, uint64_t seed,
+                     int32_t* idx_out_host, uint32_t* mask_out_host, sfs_operator** op) {
+  clear_error();
+  if (!g || !op) {
+    set_error("null argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  const int S = g->d.Nx * g->d.Ny;
+  std::vector<int32_t> idx((size_t)S * std::max(M, 1));
+  SFS_TRY(select_host(g, strategy, M, per_position, seed, idx.data(), nullptr, nullptr, nullptr));
+  if (idx_out_host) memcpy(idx_out_host, idx.data(), idx.size() * sizeof(int32_t));
+  if (mask_out_host) {
+    const int words = (g->d.Nt / 2 + 1 + 31) / 32;
+    memset(mask_out_host, 0, sizeof(uint32_t) * (size_t)S * words);
+    for (int s = 0; s < S; ++s)
+      for (int m = 0; m < M; ++m) {
+        const int k = idx[(size_t)s * M + m];
+        mask_out_host[(size_t)s * words + k / 32] |= 1u << (k % 32);
+      }
+  }
+  return sfs_operator_from_indices(g, M, idx.data(), op);
+}
+
+int sfs_destroy_operator(sfs_operator* op) {
+  if (!op) return SFS_OK;
+  DeviceScope scope(op->geo.d.device);
+  free_operator(op);
+  return SFS_OK;
+}
+
+int sfs_operator_info(const sfs_operator* op, sfs_operator_info_t* info) {
+  clear_error();
+  if (!op || !info) {
+    set_error("null argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  info->S = op->S;
+  info->M = op->M;
+  info->V = op->V;
+  info->Nz = op->geo.d.Nz;
+  info->U = op->U;
+  info->Px = op->geo.Px;
+  info->Py = op->geo.Py;
+  info->Nkappa = op->Nk;
+  info->k_lo = op->k_lo;
+  info->k_hi = op->k_hi;
+  info->band_db = op->band_db;
+  info->alpha = op->geo.alpha;
+  info->t0 = op->geo.d.t0;
+  info->table_bytes = (int64_t)op->Nk * op->U * op->geo.d.Nz * 8;
+  info->launches_per_iter = 4;
+  return SFS_OK;
+}
+
+int sfs_apply_A(sfs_operator* op, const void* x_dev, void* y_dev, void* stream) {
+  clear_error();
+  if (!op || !x_dev || !y_dev || !aligned16(x_dev) || !aligned16(y_dev)) {
+    set_error("null or misaligned argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(op->geo.d.device);
+  return enqueue_A(op, (const float2*)x_dev, (float2*)y_dev, nullptr, (cudaStream_t)stream);
+}
+
+int sfs_apply_AH(sfs_operator* op, const void* y_dev, void* x_dev, void* stream) {
+  clear_error();
+  if (!op || !x_dev || !y_dev || !aligned16(x_dev) || !aligned16(y_dev)) {
+    set_error("null or misaligned argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(op->geo.d.device);
+  return enqueue_AH(op, (const float2*)y_dev, (float2*)x_dev, nullptr, nullptr,
+                    (cudaStream_t)stream);
+}
+
+int sfs_max_abs_AH(sfs_operator* op, const void* y_dev, double* out_host, void* stream) {
+  clear_error();
+  if (!op || !y_dev || !out_host || !aligned16(y_dev)) {
+    set_error("null or misaligned argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(op->geo.d.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned int* bits = (unsigned int*)(op->ws.scal + kLamMax);
+  SFS_CUDA(cudaMemsetAsync(bits, 0, sizeof(unsigned int), st));
+  SFS_TRY(enqueue_AH(op, (const float2*)y_dev, nullptr, nullptr, bits, st));
+  unsigned int hb = 0;
+  SFS_CUDA(cudaMemcpyAsync(&hb, bits, sizeof(hb), cudaMemcpyDeviceToHost, st));
+  SFS_CUDA(cudaStreamSynchronize(st));
+  float f;
+  memcpy(&f, &hb, sizeof(f));
+  if (!isfinite(f)) {
+    set_error("non-finite value in A^H y");
+    return SFS_ERR_NON_FINITE;
+  }
+  *out_host = f;
+  return SFS_OK;
+}
+
+int sfs_lipschitz(sfs_operator* op, int max_iter, double rtol, uint64_t seed, double safety,
+                  double* L_out, void* stream) {
+  clear_error();
+  if (!op || !L_out || max_iter < 1 || !(rtol >= 0) || !(safety >= 0)) {
+    set_error("invalid argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(op->geo.d.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int V = op->V;
+  float2* v = op->ws.gam;
+  float2* w = op->ws.xk;
+  double* red = op->ws.red;
+  // v0: seeded complex Gaussian, normalised
+  SFS_TRY(launch_randn(v, V, seed, st));
+  SFS_CUDA(cudaMemsetAsync(red + kRedB, 0, sizeof(double), st));
+  SFS_TRY(launch_sumsq(v, V, red + kRedB, st));
+  SFS_TRY(launch_scale_by_rnorm(v, V, red + kRedB, st));
+  // power iteration on A^H A:  est = ||A v||^2, v <- A^H A v / ||A^H A v||
+  const int check = 8;
+  std::vector<double> hist(check);
+  double* d_hist = nullptr;
+  SFS_TRY(dev_alloc(&d_hist, check));
+  double prev = -1.0, est = 0.0;
+  int rc = SFS_ERR_NOT_CONVERGED;
+  int it = 0;
+  while (it < max_iter) {
+    const int n = std::min(check, max_iter - it);
+    for (int j = 0; j < n; ++j) {
+      cudaMemsetAsync(red, 0, 2 * sizeof(double), st);
+      if ((rc = enqueue_A(op, v, op->ws.vbuf, red + kRedA, st)) != SFS_OK) break;
+      if ((rc = enqueue_AH(op, op->ws.vbuf, w, red + kRedB, nullptr, st)) != SFS_OK) break;
+      if ((rc = launch_scale_by_rnorm(w, V, red + kRedB, st)) != SFS_OK) break;
+      cudaMemcpyAsync(d_hist + j, red + kRedA, sizeof(double), cudaMemcpyDeviceToDevice, st);
+      std::swap(v, w);
+      rc = SFS_ERR_NOT_CONVERGED;
+    }
+    if (cudaGetLastError() != cudaSuccess && rc == SFS_ERR_NOT_CONVERGED) rc = SFS_ERR_CUDA;
+    if (rc != SFS_ERR_NOT_CONVERGED) break;
+    cudaError_t e = cudaMemcpyAsync(hist.data(), d_hist, n * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "power iteration", __FILE__, __LINE__);
+      break;
+    }
+    bool done = false;
+    for (int j = 0; j < n; ++j) {
+      est = hist[j];
+      if (!isfinite(est)) {
+        set_error("non-finite Rayleigh quotient in power iteration");
+        rc = SFS_ERR_NON_FINITE;
+        done = true;
+        break;
+      }
+      ++it;
+      if (prev > 0 && fabs(est - prev) <= rtol * est) {
+        rc = SFS_OK;
+        done = true;
+        break;
+      }
+      prev = est;
+    }
+    if (done) break;
+  }
+  cudaFree(d_hist);
+  if (rc == SFS_OK || rc == SFS_ERR_NOT_CONVERGED) {
+    *L_out = est * (1.0 + safety);
+    if (rc == SFS_ERR_NOT_CONVERGED)
+      set_error("power iteration did not reach rtol %g in %d iterations", rtol, max_iter);
+  }
+  return rc;
+}
+
+int sfs_fista(sfs_operator* op, const void* y_dev, double lambda, double L, int iters,
+              void* x_inout_dev, uint32_t flags, double* obj_hist_host, void* stream) {
+  clear_error();
+  if (!op || !y_dev || !x_inout_dev || iters < 0 || !(L > 0) || !isfinite(lambda) ||
+      !aligned16(y_dev) || !aligned16(x_inout_dev)) {
+    set_error("invalid argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(op->geo.d.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const PlaneDims d = dims_of(op);
+  const size_t vbytes = (size_t)op->V * sizeof(float2);
+  float2* y = op->ws.ybuf;
+  SFS_CUDA(cudaMemcpyAsync(y, y_dev, (size_t)op->S * op->M * sizeof(float2),
+                           cudaMemcpyDeviceToDevice, st));
+  if (flags & SFS_FISTA_WARM_START) {
+    SFS_CUDA(cudaMemcpyAsync(op->ws.xk, x_inout_dev, vbytes, cudaMemcpyDeviceToDevice, st));
+    SFS_CUDA(cudaMemcpyAsync(op->ws.gam, x_inout_dev, vbytes, cudaMemcpyDeviceToDevice, st));
+  } else {
+    SFS_CUDA(cudaMemsetAsync(op->ws.xk, 0, vbytes, st));
+    SFS_CUDA(cudaMemsetAsync(op->ws.gam, 0, vbytes, st));
+  }
+  // thresholds: lambda/L and 1/L, with the mu rule evaluated on the device
+  const int use_mu = lambda < 0;
+  if (use_mu) {
+    unsigned int* bits = (unsigned int*)(op->ws.scal + kLamMax);
+    SFS_CUDA(cudaMemsetAsync(bits, 0, sizeof(unsigned int), st));
+    SFS_TRY(enqueue_AH(op, y, nullptr, nullptr, bits, st));
+  }
+  SFS_TRY(launch_set_thresholds(op->ws.scal, op->ws.red, use_mu ? 0.0 : lambda, L, use_mu,
+                                use_mu ? -lambda : 0.0, st));
+  double* obj = nullptr;
+  if (obj_hist_host && iters > 0) {
+    SFS_TRY(ensure_obj(op, iters));
+    obj = op->ws.obj;
+    SFS_CUDA(cudaMemsetAsync(obj, 0, 2 * sizeof(double) * iters, st));
+  }
+  const bool timing = (flags & SFS_FISTA_TIME_KERNELS) != 0;
+  if (timing) {
+    SFS_TRY(ensure_events(op, 4 * iters));
+    op->ev_used = 0;
+  }
+  std::vector<float> beta(iters);
+  {
+    double t = 1.0;
+    for (int k = 0; k < iters; ++k) {
+      const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+      beta[k] = (float)((t - 1.0) / tn);
+      t = tn;
+    }
+  }
+  if (iters > 0) SFS_TRY(launch_fwd_planes(d, op->ws.gam, op->ws.Xh, st));
+  for (int k = 0; k < iters; ++k) {
+    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 0], st));
+    SFS_TRY(launch_contract_fwd(d, op->table, op->ws.Xh, op->ws.Yh, st));
+    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 1], st));
+    SFS_TRY(launch_inv_resid_fwd(d, op->ws.Yh, op->posmap, y, op->ws.Rh,
+                                 obj ? obj + 2 * k : nullptr, st));
+    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 2], st));
+    SFS_TRY(launch_contract_adj(d, op->table, op->ws.Rh, op->ws.Gh, st));
+    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 3], st));
+    SFS_TRY(launch_inv_fista_fwd(d, op->ws.Gh, op->ws.xk, op->ws.gam, op->ws.scal, beta[k],
+                                 k + 1 < iters, op->ws.Xh, obj ? obj + 2 * k + 1 : nullptr, st));
+  }
+  if (timing) op->ev_used = iters;
+  SFS_CUDA(cudaMemcpyAsync(x_inout_dev, op->ws.xk, vbytes, cudaMemcpyDeviceToDevice, st));
+  if (obj) {
+    std::vector<double> h(2 * (size_t)iters);
+    double lam = 0.0;
+    SFS_CUDA(cudaMemcpyAsync(h.data(), obj, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SFS_CUDA(cudaMemcpyAsync(&lam, op->ws.red + kNumRed - 1, sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+    SFS_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < iters; ++k) obj_hist_host[k] = 0.5 * h[2 * k] + lam * h[2 * k + 1];
+  }
+  return SFS_OK;
+}
+
+int sfs_kernel_times(sfs_operator* op, double* fwd_ms, double* adj_ms, int32_t* n_out_host) {
+  clear_error();
+  if (!op || !fwd_ms || !adj_ms) {
+    set_error("null argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(op->geo.d.device);
+  double f = 0.0, a = 0.0;
+  for (int k = 0; k < op->ev_used; ++k) {
+    float t1 = 0.f, t2 = 0.f;
+    SFS_CUDA(cudaEventSynchronize(op->ev[4 * k + 3]));
+    SFS_CUDA(cudaEventElapsedTime(&t1, op->ev[4 * k + 0], op->ev[4 * k + 1]));
+    SFS_CUDA(cudaEventElapsedTime(&t2, op->ev[4 * k + 2], op->ev[4 * k + 3]));
+    f += t1;
+    a += t2;
+  }
+  const int n = op->ev_used;
+  *fwd_ms = n ? f / n : 0.0;
+  *adj_ms = n ? a / n : 0.0;
+  if (n_out_host) *n_out_host = n;
+  return SFS_OK;
+}
+
+}  // extern "C"

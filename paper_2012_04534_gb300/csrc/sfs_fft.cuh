@@ -1,0 +1,213 @@
+// Shared-memory FFT engine for one lateral plane per CTA.
+//
+// The fast transform of the block 2-level Toeplitz operator (Sec. IV-B,
+// Algorithm 2) needs 2-D FFTs of zero-padded Px x Py planes.  Each plane
+// fits in one CTA's shared memory (Px = Py <= 128, or a line of <= 4096), so
+// a plane is transformed in place: radix-2/4/8 Stockham passes whose
+// butterflies are held in registers between two barriers.
+//
+// 2-D layout: a P x P plane with row stride P + 1 (odd, so that both the
+// column passes and the transpose are free of bank conflicts).  The forward
+// transform runs column FFTs along y, transposes, and runs column FFTs
+// along x; its result is stored transposed, element (kx, ky) at row kx,
+// column ky.  The inverse consumes that layout and returns the natural
+// [y][x] layout.  Every producer and consumer of lateral spectra in this
+// library uses these two routines, so the transposed wavenumber order is
+// internal and consistent: kappa = kx * P + ky.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace sfs {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  return make_float2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  return make_float2(a.x - b.x, a.y - b.y);
+}
+// multiply by -j (forward) or +j (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_j(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// In-register DFT of length R (2, 4 or 8); forward uses e^{-j...}.
+template <int R, bool INV>
+__device__ __forceinline__ void dft_small(float2* v) {
+  if constexpr (R == 2) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else if constexpr (R == 4) {
+    float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    float2 s13 = cadd(v[1], v[3]), d13 = mul_j<INV>(csub(v[1], v[3]));
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = cadd(d02, d13);
+    v[3] = csub(d02, d13);
+  } else {
+    static_assert(R == 8, "radix");
+    float2 e[4] = {v[0], v[2], v[4], v[6]};
+    float2 o[4] = {v[1], v[3], v[5], v[7]};
+    dft_small<4, INV>(e);
+    dft_small<4, INV>(o);
+    const float h = 0.70710678118654752440f;
+    // o[k] *= W8^k, W8 = e^{-j pi/4} (forward) or e^{+j pi/4} (inverse)
+    o[1] = INV ? make_float2(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
+               : make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+    o[2] = mul_j<INV>(o[2]);
+    o[3] = INV ? make_float2(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y))
+               : make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = cadd(e[k], o[k]);
+      v[k + 4] = csub(e[k], o[k]);
+    }
+  }
+}
+
+// Radix for the pass that starts after Ns points are combined.
+__host__ __device__ constexpr int pass_radix(int N, int Ns) {
+  return (N / Ns) % 8 == 0 ? 8 : ((N / Ns) % 4 == 0 ? 4 : 2);
+}
+
+// twiddle table: tw[m] = exp(-2 pi j m / N), m in [0, N)
+template <int N, int NT>
+__device__ __forceinline__ void make_twiddles(float2* tw) {
+  for (int m = threadIdx.x; m < N; m += NT) {
+    float s, c;
+    sincospif(-2.0f * (float)m / (float)N, &s, &c);
+    tw[m] = make_float2(c, s);
+  }
+}
+
+// One Stockham pass (radix R, Ns points combined so far) over `count`
+// sequences of length N; element n of sequence q lives at buf[q*sd + n*es].
+// QFAST: consecutive threads take consecutive sequences (column passes),
+// otherwise consecutive butterflies of one sequence (row passes).
+template <int N, int R, bool INV, int NT, int MAXB, bool QFAST>
+__device__ __forceinline__ void stockham_pass(float2* buf, int count, int es,
+                                              int sd, int Ns, const float2* tw) {
+  constexpr int NB = N / R;
+  float2 v[MAXB][R];
+  const int total = count * NB;
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = threadIdx.x + i * NT;
+    if (b < total) {
+      const int q = QFAST ? b % count : b / NB;
+      const int j = QFAST ? b / count : b % NB;
+      const float2* src = buf + q * sd;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i][r] = src[(j + r * NB) * es];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = threadIdx.x + i * NT;
+    if (b < total) {
+      const int q = QFAST ? b % count : b / NB;
+      const int j = QFAST ? b / count : b % NB;
+      const int k = j & (Ns - 1);
+      if (Ns > 1) {
+        const int step = k * (N / (Ns * R));
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[step * r];
+          if (INV) w.y = -w.y;
+          v[i][r] = cmul(v[i][r], w);
+        }
+      }
+      dft_small<R, INV>(v[i]);
+      const int base = (j - k) * R + k;
+      float2* dst = buf + q * sd;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[(base + r * Ns) * es] = v[i][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Full FFT of length N on `count` sequences (all passes).
+template <int N, bool INV, int NT, int MAXCOUNT, bool QFAST, int Ns = 1>
+__device__ __forceinline__ void fft_multi(float2* buf, int count, int es, int sd,
+                                          const float2* tw) {
+  if constexpr (Ns < N) {
+    constexpr int R = pass_radix(N, Ns);
+    constexpr int MAXB = (MAXCOUNT * (N / R) + NT - 1) / NT;
+    stockham_pass<N, R, INV, NT, MAXB, QFAST>(buf, count, es, sd, Ns, tw);
+    fft_multi<N, INV, NT, MAXCOUNT, QFAST, Ns * R>(buf, count, es, sd, tw);
+  }
+}
+
+// In-place transpose of a P x P plane (row stride LD) through registers.
+template <int P, int LD, int NT>
+__device__ __forceinline__ void transpose_plane(float2* buf) {
+  constexpr int PER = (P * P + NT - 1) / NT;
+  float2 v[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int e = threadIdx.x + i * NT;
+    if (e < P * P) v[i] = buf[(e / P) * LD + (e % P)];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int e = threadIdx.x + i * NT;
+    if (e < P * P) buf[(e % P) * LD + (e / P)] = v[i];
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Plane transforms.  TWO_D: P x P plane, row stride P + 1.  Otherwise a line
+// of P points (Py = 1).
+// ---------------------------------------------------------------------------
+template <int P, bool TWO_D>
+struct PlaneFFT {
+  static constexpr int LD = TWO_D ? P + 1 : P;
+  static constexpr int NT = TWO_D ? (P >= 128 ? 512 : 256) : (P >= 512 ? 256 : (P >= 128 ? 128 : 64));
+  static constexpr int ELEMS = TWO_D ? P * LD : P;   // float2 slots of the plane
+  static constexpr int SMEM = (ELEMS + P) * 8;       // plane + twiddles
+
+  // spatial element (iy, ix) of the plane
+  __device__ static __forceinline__ int sidx(int iy, int ix) { return TWO_D ? iy * LD + ix : ix; }
+  // wavenumber kappa (transposed order, kappa = kx*P + ky) of the plane
+  __device__ static __forceinline__ int kidx(int kappa) {
+    return TWO_D ? (kappa / P) * LD + (kappa % P) : kappa;
+  }
+  static constexpr int NK = TWO_D ? P * P : P;
+
+  // Forward 2-D FFT; only spatial columns ix < ncols may be nonzero.
+  __device__ static __forceinline__ void forward(float2* buf, const float2* tw, int ncols) {
+    if constexpr (TWO_D) {
+      fft_multi<P, false, NT, P, true>(buf, ncols, LD, 1, tw);   // along y
+      transpose_plane<P, LD, NT>(buf);
+      fft_multi<P, false, NT, P, true>(buf, P, LD, 1, tw);       // along x
+    } else {
+      fft_multi<P, false, NT, 1, false>(buf, 1, 1, P, tw);
+    }
+  }
+  // Inverse (unnormalised) 2-D FFT; only spatial columns ix < ncols of the
+  // result are computed.
+  __device__ static __forceinline__ void inverse(float2* buf, const float2* tw, int ncols) {
+    if constexpr (TWO_D) {
+      fft_multi<P, true, NT, P, true>(buf, P, LD, 1, tw);        // kx -> x
+      transpose_plane<P, LD, NT>(buf);
+      fft_multi<P, true, NT, P, true>(buf, ncols, LD, 1, tw);    // ky -> y
+    } else {
+      fft_multi<P, true, NT, 1, false>(buf, 1, 1, P, tw);
+    }
+  }
+};
+
+}  // namespace sfs

@@ -1,0 +1,144 @@
+// Internal declarations of libsfs: operator state and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sfs.h"
+
+namespace sfs {
+
+// Thread-local error message behind sfs_last_error().
+void set_error(const char* fmt, ...);
+void clear_error();
+
+// A CUDA runtime failure: records the message and returns SFS_ERR_CUDA (or
+// SFS_ERR_OOM for allocation failures).
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define SFS_CUDA(call)                                                   \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) return ::sfs::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define SFS_TRY(call)                 \
+  do {                                \
+    int rc_ = (call);                 \
+    if (rc_ != SFS_OK) return rc_;    \
+  } while (0)
+
+// Largest lateral FFT side held in one CTA's shared memory (a 128 x 129
+// padded c64 plane is 132 KB).
+constexpr int kMaxP2D = 128;
+constexpr int kMaxP1D = 4096;
+// Lateral wavenumbers per table tile: a warp lane owns two, loaded as float4.
+constexpr int kKappaTile = 64;
+
+// Device-side scalars of one operator (one cudaMalloc, see Workspace).
+enum ScalarSlot {
+  kThr = 0,     // float: soft threshold lambda / L
+  kInvL = 1,    // float: 1 / L
+  kLamMax = 2,  // float bits (uint): max |A^H y| (atomicMax on the bit pattern)
+  kNumFloatScalars = 4
+};
+
+// Reduction slots (double) of one operator.
+enum RedSlot {
+  kRedA = 0,   // scratch sums used by the power iteration
+  kRedB = 1,
+  kRedC = 2,
+  kNumRed = 4
+};
+
+struct Workspace {
+  float2* Xh = nullptr;     // [Nz][Nk]   lateral spectra of voxel planes
+  float2* Yh = nullptr;     // [U][Nk]    lateral spectra of bin planes (forward)
+  float2* Rh = nullptr;     // [U][Nk]    lateral spectra of residual planes
+  float2* Gh = nullptr;     // [Nz][Nk]   lateral spectra of the gradient planes
+  float2* xk = nullptr;     // [V] FISTA iterate x_k
+  float2* gam = nullptr;    // [V] FISTA extrapolated point gamma_k
+  float2* ybuf = nullptr;   // [S][M] measurements copy
+  float2* vbuf = nullptr;   // [S][M] scratch (power iteration)
+  float* scal = nullptr;    // kNumFloatScalars floats
+  double* red = nullptr;    // kNumRed doubles
+  double* obj = nullptr;    // [2 * obj_cap] objective monitor sums
+  int obj_cap = 0;
+};
+
+}  // namespace sfs
+
+struct sfs_geometry {
+  sfs_geometry_desc d;  // validated copy, t0 resolved
+  double alpha;
+  int Px, Py;           // lateral FFT sizes
+};
+
+struct sfs_operator {
+  sfs_geometry geo;
+  int M = 0, S = 0, V = 0, U = 0, Nk = 0;
+  int k_lo = 0, k_hi = 0;
+  double band_db = 0.0;
+  std::vector<int32_t> idx;    // [S][M]
+  std::vector<int32_t> bins;   // [U] union of kept bins, ascending
+  // device data
+  float2* table = nullptr;     // [Nk/64][U][Nz][64] c64, includes 1/(Px*Py)
+  int32_t* posmap = nullptr;   // [U][S]: m with idx[s][m] == bins[u], else -1
+  sfs::Workspace ws;
+  // kernel timing (SFS_FISTA_TIME_KERNELS)
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
+};
+
+namespace sfs {
+
+// ---- kernel launchers (sfs_kernels.cu) ----
+
+struct PlaneDims {
+  int Nx, Ny, Nz, Px, Py, Nk, S, M, U;
+};
+
+// Table of generators (Theorem 2 / Eq. (4)); tof: float2 [Nz][Ny][Nx]
+// (hi, lo) of (tau - t0) fs / Nt in turns per unit bin; gdir: float
+// [Nz][Ny][Nx] directivity; amp: float [U] = fs H(f_k) / (Px Py); bins: int [U].
+int launch_build_table(const PlaneDims& d, const float2* tof, const float* gdir,
+                       const float* amp, const int32_t* bins, float2* table,
+                       cudaStream_t st);
+
+// Plane kernels.  Each processes one lateral plane per CTA.
+int launch_fwd_planes(const PlaneDims& d, const float2* x, float2* Xh,
+                      cudaStream_t st);
+int launch_inv_gather(const PlaneDims& d, const float2* Yh, const int32_t* posmap,
+                      float2* y, double* red_sumsq, cudaStream_t st);
+int launch_inv_resid_fwd(const PlaneDims& d, const float2* Yh, const int32_t* posmap,
+                         const float2* yobs, float2* Rh, double* red_sumsq,
+                         cudaStream_t st);
+int launch_scatter_fwd(const PlaneDims& d, const float2* y, const int32_t* posmap,
+                       float2* Rh, cudaStream_t st);
+int launch_inv_store(const PlaneDims& d, const float2* Gh, float2* x,
+                     double* red_sumsq, unsigned int* maxabs_bits,
+                     cudaStream_t st);
+int launch_inv_fista_fwd(const PlaneDims& d, const float2* Gh, float2* xk,
+                         float2* gam, const float* scal, float beta, int do_fwd,
+                         float2* Xh, double* red_l1, cudaStream_t st);
+
+// Depth contractions over the generator table.
+int launch_contract_fwd(const PlaneDims& d, const float2* table, const float2* Xh,
+                        float2* Yh, cudaStream_t st);
+int launch_contract_adj(const PlaneDims& d, const float2* table, const float2* Rh,
+                        float2* Gh, cudaStream_t st);
+
+// Small helpers.
+int launch_set_thresholds(float* scal, double* red, double lambda, double L,
+                          int use_mu, double mu, cudaStream_t st);
+int launch_randn(float2* v, int n, uint64_t seed, cudaStream_t st);
+int launch_sumsq(const float2* v, int n, double* out, cudaStream_t st);
+int launch_scale_by_rnorm(float2* v, int n, const double* sumsq, cudaStream_t st);
+
+// Opt-in shared memory limit of the current device (bytes).
+int max_smem_optin();
+
+}  // namespace sfs

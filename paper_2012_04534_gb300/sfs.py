@@ -1,0 +1,332 @@
+"""Thin ctypes binding of libsfs (include/sfs.h).
+
+Argument marshalling only: every step of the operator, the solver and the
+reductions runs in the library's CUDA kernels.  PyTorch supplies device
+memory (complex64 tensors) and the current CUDA stream.  The module-level
+``sfs_*`` functions mirror the C entry points one to one; ``Geometry`` and
+``Operator`` wrap the handles for convenience.  Importing this module does
+not load the library; the first call does, and it raises if libsfs.so has
+not been built (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsfs.so")
+
+SFS_OK = 0
+SFS_ERR_INVALID_ARG = -1
+SFS_ERR_BAND_TOO_NARROW = -2
+SFS_ERR_CUDA = -3
+SFS_ERR_OOM = -4
+SFS_ERR_TIMEOUT = -5
+SFS_ERR_NOT_CONVERGED = -6
+SFS_ERR_NON_FINITE = -7
+
+SFS_SEL_RANDOM = 0
+SFS_SEL_CONTIGUOUS = 1
+SFS_SEL_EQUISPACED = 2
+
+SFS_FISTA_WARM_START = 1
+SFS_FISTA_TIME_KERNELS = 2
+
+STATUS_NAMES = {0: "SFS_OK", -1: "SFS_ERR_INVALID_ARG", -2: "SFS_ERR_BAND_TOO_NARROW",
+                -3: "SFS_ERR_CUDA", -4: "SFS_ERR_OOM", -5: "SFS_ERR_TIMEOUT",
+                -6: "SFS_ERR_NOT_CONVERGED", -7: "SFS_ERR_NON_FINITE"}
+
+# every symbol include/sfs.h declares
+EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
+           "sfs_select_freqs", "sfs_operator_from_indices", "sfs_destroy_operator",
+           "sfs_operator_info", "sfs_apply_A", "sfs_apply_AH", "sfs_max_abs_AH",
+           "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_last_error",
+           "sfs_version")
+
+
+class SfsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class GeometryDesc(ctypes.Structure):
+    _fields_ = [("Nx", ctypes.c_int32), ("Ny", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("Nz", ctypes.c_int32), ("z0", ctypes.c_double), ("dz", ctypes.c_double),
+                ("c", ctypes.c_double), ("fs", ctypes.c_double), ("Nt", ctypes.c_int32),
+                ("t0", ctypes.c_double), ("fc", ctypes.c_double),
+                ("frac_bw", ctypes.c_double), ("theta", ctypes.c_double),
+                ("device", ctypes.c_int32)]
+
+
+class OperatorInfo(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_int32), ("M", ctypes.c_int32), ("V", ctypes.c_int32),
+                ("Nz", ctypes.c_int32), ("U", ctypes.c_int32), ("Px", ctypes.c_int32),
+                ("Py", ctypes.c_int32), ("Nkappa", ctypes.c_int32),
+                ("k_lo", ctypes.c_int32), ("k_hi", ctypes.c_int32),
+                ("band_db", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("t0", ctypes.c_double), ("table_bytes", ctypes.c_int64),
+                ("launches_per_iter", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libsfs.so (built in-tree by paper_2012_04534_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libsfs.so is not built; run __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, u32, u64, dbl = (ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32,
+                              ctypes.c_uint64, ctypes.c_double)
+    P = ctypes.POINTER
+    sig = {
+        "sfs_create_geometry": [P(GeometryDesc), P(vp)],
+        "sfs_destroy_geometry": [vp],
+        "sfs_select_indices": [vp, i32, i32, i32, u64, P(ctypes.c_int32), P(ctypes.c_int32)],
+        "sfs_select_freqs": [vp, i32, i32, i32, u64, P(ctypes.c_int32), P(ctypes.c_uint32), P(vp)],
+        "sfs_operator_from_indices": [vp, i32, P(ctypes.c_int32), P(vp)],
+        "sfs_destroy_operator": [vp],
+        "sfs_operator_info": [vp, P(OperatorInfo)],
+        "sfs_apply_A": [vp, vp, vp, vp],
+        "sfs_apply_AH": [vp, vp, vp, vp],
+        "sfs_max_abs_AH": [vp, vp, P(dbl), vp],
+        "sfs_lipschitz": [vp, i32, dbl, u64, dbl, P(dbl), vp],
+        "sfs_fista": [vp, vp, dbl, dbl, i32, vp, u32, P(dbl), vp],
+        "sfs_kernel_times": [vp, P(dbl), P(dbl), P(ctypes.c_int32)],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.sfs_last_error.restype = ctypes.c_char_p
+    L.sfs_last_error.argtypes = []
+    L.sfs_version.restype = ctypes.c_char_p
+    L.sfs_version.argtypes = []
+    _lib = L
+    return L
+
+
+def _check(rc: int, allow=()):
+    if rc != SFS_OK and rc not in allow:
+        raise SfsError(rc, lib().sfs_last_error().decode())
+    return rc
+
+
+def _stream_ptr(stream, device):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, numel, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.complex64 or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError("%s must be a contiguous complex64 tensor of %d elements "
+                         "(got %s %s %d)" % (name, numel, t.dtype, tuple(t.shape), t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- C names ---
+
+def sfs_create_geometry(**params) -> ctypes.c_void_p:
+    d = GeometryDesc()
+    d.Nx = int(params["Nx"]); d.Ny = int(params["Ny"])
+    d.dx = float(params["dx"]); d.dy = float(params.get("dy", params["dx"]))
+    d.Nz = int(params["Nz"]); d.z0 = float(params["z0"]); d.dz = float(params["dz"])
+    d.c = float(params["c"]); d.fs = float(params["fs"]); d.Nt = int(params["Nt"])
+    d.t0 = float(params.get("t0", math.nan)); d.fc = float(params["fc"])
+    d.frac_bw = float(params["frac_bw"]); d.theta = float(params.get("theta", 0.0))
+    d.device = int(params.get("device", 0))
+    h = ctypes.c_void_p()
+    _check(lib().sfs_create_geometry(ctypes.byref(d), ctypes.byref(h)))
+    return h
+
+
+def sfs_select_indices(geom, strategy: int, M: int, per_position: bool, seed: int,
+                       S: int):
+    idx = np.zeros((S, M), dtype=np.int32)
+    band = np.zeros(2, dtype=np.int32)
+    _check(lib().sfs_select_indices(geom, strategy, M, int(per_position), seed,
+                                    idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                    band.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return idx, (int(band[0]), int(band[1]))
+
+
+def sfs_select_freqs(geom, strategy: int, M: int, per_position: bool, seed: int, S: int,
+                     Nt: int):
+    idx = np.zeros((S, M), dtype=np.int32)
+    words = (Nt // 2 + 1 + 31) // 32
+    mask = np.zeros((S, words), dtype=np.uint32)
+    h = ctypes.c_void_p()
+    _check(lib().sfs_select_freqs(geom, strategy, M, int(per_position), seed,
+                                  idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                  ctypes.byref(h)))
+    return h, idx, mask
+
+
+def sfs_operator_from_indices(geom, idx):
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(lib().sfs_operator_from_indices(
+        geom, idx.shape[1], idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(h)))
+    return h
+
+
+def sfs_operator_info(op) -> dict:
+    info = OperatorInfo()
+    _check(lib().sfs_operator_info(op, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def sfs_apply_A(op, x_dev_ptr, y_dev_ptr, stream_ptr):
+    _check(lib().sfs_apply_A(op, x_dev_ptr, y_dev_ptr, stream_ptr))
+
+
+def sfs_apply_AH(op, y_dev_ptr, x_dev_ptr, stream_ptr):
+    _check(lib().sfs_apply_AH(op, y_dev_ptr, x_dev_ptr, stream_ptr))
+
+
+def sfs_max_abs_AH(op, y_dev_ptr, stream_ptr) -> float:
+    out = ctypes.c_double()
+    _check(lib().sfs_max_abs_AH(op, y_dev_ptr, ctypes.byref(out), stream_ptr))
+    return out.value
+
+
+def sfs_lipschitz(op, max_iter, rtol, seed, safety, stream_ptr):
+    out = ctypes.c_double()
+    rc = _check(lib().sfs_lipschitz(op, max_iter, rtol, seed, safety, ctypes.byref(out),
+                                    stream_ptr), allow=(SFS_ERR_NOT_CONVERGED,))
+    return out.value, rc == SFS_OK
+
+
+def sfs_fista(op, y_dev_ptr, lam, L, iters, x_dev_ptr, flags, obj_hist, stream_ptr):
+    ptr = None
+    if obj_hist is not None:
+        ptr = obj_hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(lib().sfs_fista(op, y_dev_ptr, lam, L, iters, x_dev_ptr, flags, ptr, stream_ptr))
+
+
+def sfs_kernel_times(op):
+    f, a, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    _check(lib().sfs_kernel_times(op, ctypes.byref(f), ctypes.byref(a), ctypes.byref(n)))
+    return f.value, a.value, n.value
+
+
+def sfs_version() -> str:
+    return lib().sfs_version().decode()
+
+
+# --------------------------------------------------------------- wrappers ---
+
+class Geometry:
+    """Scan / voxel grid and pulse (sfs_geometry_desc)."""
+
+    def __init__(self, **params):
+        self.params = dict(params)
+        self.device = int(params.get("device", 0))
+        self.handle = sfs_create_geometry(**params)
+        self.Nx, self.Ny, self.Nz = int(params["Nx"]), int(params["Ny"]), int(params["Nz"])
+        self.Nt = int(params["Nt"])
+        self.S = self.Nx * self.Ny
+        self.V = self.S * self.Nz
+
+    def select_indices(self, strategy, M, per_position=True, seed=0):
+        return sfs_select_indices(self.handle, strategy, M, per_position, seed, self.S)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.sfs_destroy_geometry(h)
+            self.handle = None
+
+
+class Operator:
+    """A = S F H and its adjoint on one GPU (sfs_operator)."""
+
+    def __init__(self, geom: Geometry, handle):
+        self.geom = geom
+        self.handle = handle
+        self.info = sfs_operator_info(handle)
+        self.S, self.M, self.V = self.info["S"], self.info["M"], self.info["V"]
+        self.shape_x = (geom.Nz, geom.Ny, geom.Nx)
+        self.shape_y = (self.S, self.M)
+        self.device = geom.device
+
+    @classmethod
+    def select(cls, geom: Geometry, strategy=SFS_SEL_RANDOM, M=32, per_position=True, seed=0):
+        h, idx, mask = sfs_select_freqs(geom.handle, strategy, M, per_position, seed,
+                                        geom.S, geom.Nt)
+        op = cls(geom, h)
+        op.idx, op.mask = idx, mask
+        return op
+
+    @classmethod
+    def from_indices(cls, geom: Geometry, idx):
+        op = cls(geom, sfs_operator_from_indices(geom.handle, idx))
+        op.idx = np.ascontiguousarray(idx, dtype=np.int32)
+        return op
+
+    def _new(self, shape):
+        import torch
+        return torch.empty(shape, dtype=torch.complex64, device="cuda:%d" % self.device)
+
+    def apply_A(self, x, out=None, stream=None):
+        y = self._new(self.shape_y) if out is None else out
+        sfs_apply_A(self.handle, _dev_ptr(x, self.V, "x"), _dev_ptr(y, self.S * self.M, "y"),
+                    _stream_ptr(stream, x.device))
+        return y
+
+    def apply_AH(self, y, out=None, stream=None):
+        x = self._new(self.shape_x) if out is None else out
+        sfs_apply_AH(self.handle, _dev_ptr(y, self.S * self.M, "y"), _dev_ptr(x, self.V, "x"),
+                     _stream_ptr(stream, y.device))
+        return x
+
+    def max_abs_AH(self, y, stream=None) -> float:
+        return sfs_max_abs_AH(self.handle, _dev_ptr(y, self.S * self.M, "y"),
+                              _stream_ptr(stream, y.device))
+
+    def lipschitz(self, max_iter=500, rtol=1e-6, seed=0, safety=1e-3, stream=None):
+        import torch
+        return sfs_lipschitz(self.handle, max_iter, rtol, seed, safety,
+                             _stream_ptr(stream, torch.device("cuda", self.device)))
+
+    def fista(self, y, lam, L, iters, x=None, warm_start=False, obj_hist=False,
+              time_kernels=False, stream=None):
+        """lam >= 0: lambda; lam < 0: lambda = -lam * ||A^H y||_inf."""
+        if x is None:
+            x = self._new(self.shape_x)
+        flags = (SFS_FISTA_WARM_START if warm_start else 0) | \
+                (SFS_FISTA_TIME_KERNELS if time_kernels else 0)
+        hist = np.zeros(iters) if obj_hist else None
+        sfs_fista(self.handle, _dev_ptr(y, self.S * self.M, "y"), float(lam), float(L), iters,
+                  _dev_ptr(x, self.V, "x"), flags, hist, _stream_ptr(stream, y.device))
+        return (x, hist) if obj_hist else x
+
+    def kernel_times(self):
+        return sfs_kernel_times(self.handle)
+
+    def close(self):
+        if self.handle and _lib is not None:
+            _lib.sfs_destroy_operator(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()

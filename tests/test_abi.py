@@ -1,0 +1,99 @@
+"""CPU tests of the C-ABI library: it loads, exports every symbol the header
+declares, and its host-side logic (geometry validation, integer frequency
+selection) agrees with the oracle.  No device work is requested."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests._common import ensure_built, geom_params, oracle_geometry
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sfs():
+    ensure_built()
+    from paper_2012_04534_gb300 import sfs as mod
+    mod.lib()
+    return mod
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "sfs.h")).read()
+    return set(re.findall(r"^(?:int|const char\*)\s+(sfs_\w+)\s*\(", text, re.M))
+
+
+def test_library_exports_every_declared_symbol(sfs):
+    names = declared_symbols()
+    assert len(names) >= 15
+    assert names == set(sfs.EXPORTS)
+    L = sfs.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert "sm_103a" in sfs.sfs_version()
+
+
+def test_geometry_validation(sfs):
+    ok = geom_params(Nx=8, Ny=8, Nz=4, dz=1e-4, Nt=64)
+    g = sfs.Geometry(**ok)
+    assert g.handle
+    for bad in (dict(Nx=0), dict(Nz=-1), dict(Nt=1), dict(c=0.0), dict(fs=-1.0),
+                dict(Nx=65, Ny=65), dict(Nx=600, Ny=1), dict(theta=2.0), dict(dz=0.0)):
+        p = dict(ok)
+        p.update(bad)
+        with pytest.raises(sfs.SfsError) as ei:
+            sfs.Geometry(**p)
+        assert ei.value.status == sfs.SFS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name", ["line2d", "vol32", "vol64"])
+@pytest.mark.parametrize("strategy", [O.SEL_RANDOM, O.SEL_CONTIGUOUS, O.SEL_EQUISPACED])
+def test_host_selection_bit_exact_with_oracle(sfs, name, strategy):
+    w = synth.WORKLOADS[name]
+    params = synth.geometry_params(name)
+    g = sfs.Geometry(**params)
+    go = O.Geometry(**params)
+    for per in (True, False):
+        idx, band = g.select_indices(strategy, w["M"], per, seed=2024)
+        ref = O.select_indices(go, strategy, w["M"], per, seed=2024)
+        assert idx.dtype == np.int32
+        assert np.array_equal(idx, ref)
+        k_lo, k_hi, _ = O.candidate_band(go, w["M"])
+        assert band == (k_lo, k_hi)
+
+
+def test_host_selection_many_seeds_and_sizes(sfs):
+    for (Nx, Ny, Nt, M) in [(5, 3, 128, 7), (1, 1, 64, 1), (9, 1, 256, 20), (4, 4, 512, 40)]:
+        p = geom_params(Nx=Nx, Ny=Ny, Nz=3, dz=1e-4, Nt=Nt)
+        g = sfs.Geometry(**p)
+        go = oracle_geometry(p)
+        for seed in (0, 1, 2**63 + 5, 12345678901234):
+            idx, _ = g.select_indices(O.SEL_RANDOM, M, True, seed)
+            assert np.array_equal(idx, O.select_indices(go, O.SEL_RANDOM, M, True, seed))
+
+
+def test_band_too_narrow(sfs):
+    g = sfs.Geometry(**geom_params(Nx=4, Ny=4, Nz=2, dz=1e-4, Nt=64))
+    with pytest.raises(sfs.SfsError) as ei:
+        g.select_indices(O.SEL_RANDOM, 30, True, 0)
+    assert ei.value.status == sfs.SFS_ERR_BAND_TOO_NARROW
+    with pytest.raises(sfs.SfsError) as ei:
+        g.select_indices(O.SEL_RANDOM, 0, True, 0)
+    assert ei.value.status == sfs.SFS_ERR_INVALID_ARG
+    with pytest.raises(sfs.SfsError) as ei:
+        g.select_indices(7, 3, True, 0)
+    assert ei.value.status == sfs.SFS_ERR_INVALID_ARG
+
+
+def test_null_handles_rejected(sfs):
+    L = sfs.lib()
+    assert L.sfs_apply_A(None, None, None, None) == sfs.SFS_ERR_INVALID_ARG
+    assert "null" in L.sfs_last_error().decode()
+    assert L.sfs_fista(None, None, 0.0, 1.0, 1, None, 0, None, None) == sfs.SFS_ERR_INVALID_ARG
+    assert L.sfs_operator_from_indices(None, 1, None, None) == sfs.SFS_ERR_INVALID_ARG
+    assert L.sfs_destroy_operator(None) == sfs.SFS_OK
