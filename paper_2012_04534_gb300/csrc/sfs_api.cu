@@ -35,11 +35,8 @@ void clear_error() { g_last_error.clear(); }
 
 int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
   set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
-  if (e == cudaErrorMemoryAllocation) {
-    cudaGetLastError();  // clear the sticky-free allocation error
-    return SFS_ERR_OOM;
-  }
-  return SFS_ERR_CUDA;
+  cudaGetLastError();  // clear a non-sticky error so later calls do not report it
+  return e == cudaErrorMemoryAllocation ? SFS_ERR_OOM : SFS_ERR_CUDA;
 }
 
 namespace {
@@ -189,6 +186,8 @@ void free_operator(sfs_operator* op) {
   cudaFree(op->ws.Yh);
   cudaFree(op->ws.Rh);
   cudaFree(op->ws.Gh);
+  cudaFree(op->ws.segslot);
+  cudaFree(op->ws.err);
   cudaFree(op->ws.xk);
   cudaFree(op->ws.gam);
   cudaFree(op->ws.ybuf);
@@ -211,6 +210,8 @@ PlaneDims dims_of(const sfs_operator* op) {
   d.S = op->S;
   d.M = op->M;
   d.U = op->U;
+  d.nzb = op->nzb;
+  d.G = op->G;
   return d;
 }
 
@@ -220,7 +221,7 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 int enqueue_A(sfs_operator* op, const float2* x, float2* y, double* red_sumsq, cudaStream_t st) {
   const PlaneDims d = dims_of(op);
   SFS_TRY(launch_fwd_planes(d, x, op->ws.Xh, st));
-  SFS_TRY(launch_contract_fwd(d, op->table, op->ws.Xh, op->ws.Yh, st));
+  SFS_TRY(launch_contract_fwd(d, op->table, op->ws.Xh, op->ws.Yh, op->ws.err, st));
   SFS_TRY(launch_inv_gather(d, op->ws.Yh, op->posmap, y, red_sumsq, st));
   return SFS_OK;
 }
@@ -230,8 +231,8 @@ int enqueue_AH(sfs_operator* op, const float2* y, float2* x, double* red_sumsq,
                unsigned int* maxabs_bits, cudaStream_t st) {
   const PlaneDims d = dims_of(op);
   SFS_TRY(launch_scatter_fwd(d, y, op->posmap, op->ws.Rh, st));
-  SFS_TRY(launch_contract_adj(d, op->table, op->ws.Rh, op->ws.Gh, st));
-  SFS_TRY(launch_inv_store(d, op->ws.Gh, x, red_sumsq, maxabs_bits, st));
+  SFS_TRY(launch_contract_adj(d, op->table, op->ws.Rh, op->ws.Gh, op->ws.err, st));
+  SFS_TRY(launch_inv_store(d, op->ws.Gh, op->ws.segslot, x, red_sumsq, maxabs_bits, st));
   return SFS_OK;
 }
 
@@ -252,6 +253,40 @@ int ensure_events(sfs_operator* op, int n) {
     op->ev.push_back(e);
   }
   return SFS_OK;
+}
+
+// Reads (and clears) the device timeout flag; call only where the stream is
+// synchronised anyway.
+int check_err_flag(sfs_operator* op, cudaStream_t st) {
+  int h = 0;
+  SFS_CUDA(cudaMemcpyAsync(&h, op->ws.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SFS_CUDA(cudaStreamSynchronize(st));
+  if (h) {
+    SFS_CUDA(cudaMemsetAsync(op->ws.err, 0, sizeof(int), st));
+    set_error("a bounded wait in a contraction kernel timed out");
+    return SFS_ERR_TIMEOUT;
+  }
+  return SFS_OK;
+}
+
+// Slot table of the adjoint contraction: CTA b of G owns units
+// [N b / G, N (b+1) / G) of the N = nseg * U units (segment-major, bin
+// fastest) and leaves one partial per segment it touches in slot seg + b.
+// The CTAs touching a segment are consecutive, so its partials occupy the
+// consecutive slots seg + b_first .. seg + b_last.
+std::vector<int2> segment_slots(int nseg, int U, int G) {
+  const long long N = (long long)nseg * U;
+  std::vector<int2> out(nseg);
+  int b = 0;
+  auto last_of = [&](int bb) { return (N * (bb + 1)) / G; };  // one past CTA bb's range
+  for (int seg = 0; seg < nseg; ++seg) {
+    const long long r0 = (long long)seg * U, r1 = r0 + U - 1;
+    while (last_of(b) <= r0) ++b;
+    int be = b;
+    while (last_of(be) <= r1) ++be;
+    out[seg] = make_int2(seg + b, be - b + 1);
+  }
+  return out;
 }
 
 }  // namespace
@@ -383,11 +418,7 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
     op->band_db = NAN;
     clear_error();
   }
-  if ((size_t)op->U * 32 * 16 > (size_t)200 * 1024 || (size_t)d.Nz * 32 * 16 > (size_t)200 * 1024) {
-    set_error("U = %d or Nz = %d too large for one shared-memory tile (max 400)", op->U, d.Nz);
-    delete op;
-    return SFS_ERR_INVALID_ARG;
-  }
+  op->nzb = (d.Nz + kZBlockRows - 1) / kZBlockRows;
 
   // host FP64 geometry tables: (tau - t0) fs / Nt split into (hi, lo) floats,
   // directivity, per-bin amplitude fs H(f_k) / (Px Py)
@@ -440,13 +471,25 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
     return rc;
   };
   int rc;
+  int sms = 0;
+  {
+    cudaError_t e0 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d.device);
+    if (e0 != cudaSuccess) return fail(cuda_fail(e0, "SM count query", __FILE__, __LINE__));
+  }
+  const int nseg = (op->Nk / kKappaTile) * op->nzb;
+  op->G = std::max(1, std::min(sms, nseg * op->U));
+  op->nslots = nseg + op->G - 1;
+  const std::vector<int2> segslot = segment_slots(nseg, op->U, op->G);
   const size_t Nk = op->Nk;
   const size_t table_elems = Nk * op->U * d.Nz;
   if ((rc = dev_alloc(&op->table, table_elems)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->posmap, posmap.size())) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.Xh, Nk * d.Nz)) != SFS_OK) return fail(rc);
-  if ((rc = dev_alloc(&op->ws.Gh, Nk * d.Nz)) != SFS_OK) return fail(rc);
-  if ((rc = dev_alloc(&op->ws.Yh, Nk * op->U)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.Gh, (size_t)op->nslots * kZBlockRows * kKappaTile)) != SFS_OK)
+    return fail(rc);
+  if ((rc = dev_alloc(&op->ws.segslot, segslot.size())) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.err, 1)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.Yh, Nk * op->U * op->nzb)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.Rh, Nk * op->U)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.xk, (size_t)op->V)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.gam, (size_t)op->V)) != SFS_OK) return fail(rc);
@@ -466,6 +509,10 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
   if (e == cudaSuccess) e = cudaMemcpy(d_bins, op->bins.data(), op->U * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(op->ws.scal, 0, kNumFloatScalars * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(op->ws.red, 0, kNumRed * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(op->ws.err, 0, sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(op->ws.segslot, segslot.data(), segslot.size() * sizeof(int2),
+                   cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(cuda_fail(e, "upload of operator tables", __FILE__, __LINE__));
   const PlaneDims pd = dims_of(op);
   if ((rc = launch_build_table(pd, d_tof, d_gdir, d_amp, d_bins, op->table, 0)) != SFS_OK)
@@ -569,6 +616,7 @@ int sfs_max_abs_AH(sfs_operator* op, const void* y_dev, double* out_host, void* 
   unsigned int hb = 0;
   SFS_CUDA(cudaMemcpyAsync(&hb, bits, sizeof(hb), cudaMemcpyDeviceToHost, st));
   SFS_CUDA(cudaStreamSynchronize(st));
+  SFS_TRY(check_err_flag(op, st));
   float f;
   memcpy(&f, &hb, sizeof(f));
   if (!isfinite(f)) {
@@ -645,6 +693,10 @@ int sfs_lipschitz(sfs_operator* op, int max_iter, double rtol, uint64_t seed, do
   }
   cudaFree(d_hist);
   if (rc == SFS_OK || rc == SFS_ERR_NOT_CONVERGED) {
+    const int rc2 = check_err_flag(op, st);
+    if (rc2 != SFS_OK) return rc2;
+  }
+  if (rc == SFS_OK || rc == SFS_ERR_NOT_CONVERGED) {
     *L_out = est * (1.0 + safety);
     if (rc == SFS_ERR_NOT_CONVERGED)
       set_error("power iteration did not reach rtol %g in %d iterations", rtol, max_iter);
@@ -706,14 +758,15 @@ int sfs_fista(sfs_operator* op, const void* y_dev, double lambda, double L, int 
   if (iters > 0) SFS_TRY(launch_fwd_planes(d, op->ws.gam, op->ws.Xh, st));
   for (int k = 0; k < iters; ++k) {
     if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 0], st));
-    SFS_TRY(launch_contract_fwd(d, op->table, op->ws.Xh, op->ws.Yh, st));
+    SFS_TRY(launch_contract_fwd(d, op->table, op->ws.Xh, op->ws.Yh, op->ws.err, st));
     if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 1], st));
     SFS_TRY(launch_inv_resid_fwd(d, op->ws.Yh, op->posmap, y, op->ws.Rh,
                                  obj ? obj + 2 * k : nullptr, st));
     if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 2], st));
-    SFS_TRY(launch_contract_adj(d, op->table, op->ws.Rh, op->ws.Gh, st));
+    SFS_TRY(launch_contract_adj(d, op->table, op->ws.Rh, op->ws.Gh, op->ws.err, st));
     if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 3], st));
-    SFS_TRY(launch_inv_fista_fwd(d, op->ws.Gh, op->ws.xk, op->ws.gam, op->ws.scal, beta[k],
+    SFS_TRY(launch_inv_fista_fwd(d, op->ws.Gh, op->ws.segslot, op->ws.xk, op->ws.gam,
+                                 op->ws.scal, beta[k],
                                  k + 1 < iters, op->ws.Xh, obj ? obj + 2 * k + 1 : nullptr, st));
   }
   if (timing) op->ev_used = iters;
@@ -725,6 +778,7 @@ int sfs_fista(sfs_operator* op, const void* y_dev, double lambda, double L, int 
     SFS_CUDA(cudaMemcpyAsync(&lam, op->ws.red + kNumRed - 1, sizeof(double),
                              cudaMemcpyDeviceToHost, st));
     SFS_CUDA(cudaStreamSynchronize(st));
+    SFS_TRY(check_err_flag(op, st));
     for (int k = 0; k < iters; ++k) obj_hist_host[k] = 0.5 * h[2 * k] + lam * h[2 * k + 1];
   }
   return SFS_OK;

@@ -58,7 +58,9 @@ struct Workspace {
   float2* Xh = nullptr;     // [Nz][Nk]   lateral spectra of voxel planes
   float2* Yh = nullptr;     // [U][Nk]    lateral spectra of bin planes (forward)
   float2* Rh = nullptr;     // [U][Nk]    lateral spectra of residual planes
-  float2* Gh = nullptr;     // [Nz][Nk]   lateral spectra of the gradient planes
+  float2* Gh = nullptr;     // [nslots][128][64] adjoint contraction partials
+  int2* segslot = nullptr;  // [nseg] {first slot, slot count} per (tile, depth block)
+  int* err = nullptr;       // device flag: a bounded wait in a kernel timed out
   float2* xk = nullptr;     // [V] FISTA iterate x_k
   float2* gam = nullptr;    // [V] FISTA extrapolated point gamma_k
   float2* ybuf = nullptr;   // [S][M] measurements copy
@@ -80,6 +82,9 @@ struct sfs_geometry {
 struct sfs_operator {
   sfs_geometry geo;
   int M = 0, S = 0, V = 0, U = 0, Nk = 0;
+  int nzb = 1;                 // depth blocks of <= 128 in the contractions
+  int G = 1;                   // persistent CTAs of the contractions
+  int nslots = 0;              // adjoint partial-sum slots
   int k_lo = 0, k_hi = 0;
   double band_db = 0.0;
   std::vector<int32_t> idx;    // [S][M]
@@ -99,7 +104,14 @@ namespace sfs {
 
 struct PlaneDims {
   int Nx, Ny, Nz, Px, Py, Nk, S, M, U;
+  int nzb;  // depth blocks of <= 128 depths in the contractions
+  int G;    // persistent CTAs of the contractions (<= SM count)
 };
+
+// Depth block of the contractions and the partial-sum slots of the adjoint.
+constexpr int kZBlockRows = 128;
+// Units of contraction work: (wavenumber tile, depth block, bin).
+int contract_units(const PlaneDims& d);
 
 // Table of generators (Theorem 2 / Eq. (4)); tof: float2 [Nz][Ny][Nx]
 // (hi, lo) of (tau - t0) fs / Nt in turns per unit bin; gdir: float
@@ -118,18 +130,20 @@ int launch_inv_resid_fwd(const PlaneDims& d, const float2* Yh, const int32_t* po
                          cudaStream_t st);
 int launch_scatter_fwd(const PlaneDims& d, const float2* y, const int32_t* posmap,
                        float2* Rh, cudaStream_t st);
-int launch_inv_store(const PlaneDims& d, const float2* Gh, float2* x,
-                     double* red_sumsq, unsigned int* maxabs_bits,
+int launch_inv_store(const PlaneDims& d, const float2* Gh, const int2* segslot,
+                     float2* x, double* red_sumsq, unsigned int* maxabs_bits,
                      cudaStream_t st);
-int launch_inv_fista_fwd(const PlaneDims& d, const float2* Gh, float2* xk,
-                         float2* gam, const float* scal, float beta, int do_fwd,
-                         float2* Xh, double* red_l1, cudaStream_t st);
+int launch_inv_fista_fwd(const PlaneDims& d, const float2* Gh, const int2* segslot,
+                         float2* xk, float2* gam, const float* scal, float beta,
+                         int do_fwd, float2* Xh, double* red_l1, cudaStream_t st);
 
-// Depth contractions over the generator table.
+// Depth contractions over the generator table.  Yp: [nzb][U][Nk] depth-block
+// partials; Gs: [slots][128][64] adjoint partials (see segment_slots).  err:
+// device int set to 1 when a bounded wait times out.
 int launch_contract_fwd(const PlaneDims& d, const float2* table, const float2* Xh,
-                        float2* Yh, cudaStream_t st);
+                        float2* Yp, int* err, cudaStream_t st);
 int launch_contract_adj(const PlaneDims& d, const float2* table, const float2* Rh,
-                        float2* Gh, cudaStream_t st);
+                        float2* Gs, int* err, cudaStream_t st);
 
 // Small helpers.
 int launch_set_thresholds(float* scal, double* red, double lambda, double L,

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 #include <unordered_map>
 
@@ -121,10 +122,37 @@ __device__ __forceinline__ void zero_plane(float2* buf) {
   for (int e = threadIdx.x; e < F::ELEMS; e += F::NT) buf[e] = make_float2(0.f, 0.f);
 }
 
+// Spectrum of bin plane u from the forward contraction: the sum of its nzb
+// depth-block partials Yp[zb][u][kap] (plane stride U * Nk).
 template <int P, bool TWO_D>
-__device__ __forceinline__ void load_spectrum(float2* buf, const float2* __restrict__ src) {
+__device__ __forceinline__ void load_spectrum_fwd(float2* buf, const float2* __restrict__ Yp,
+                                                  int u, const PlaneDims& d) {
   using F = PlaneFFT<P, TWO_D>;
-  for (int kap = threadIdx.x; kap < F::NK; kap += F::NT) buf[F::kidx(kap)] = src[kap];
+  const float2* src = Yp + (size_t)u * d.Nk;
+  const size_t stride = (size_t)d.U * d.Nk;
+  for (int kap = threadIdx.x; kap < F::NK; kap += F::NT) {
+    float2 v = src[kap];
+    for (int zb = 1; zb < d.nzb; ++zb) v = cadd(v, src[zb * stride + kap]);
+    buf[F::kidx(kap)] = v;
+  }
+}
+
+// Spectrum of voxel plane z from the adjoint contraction: for each wavenumber
+// tile, the sum of the partial results its segment (tile, depth block) left
+// in consecutive slots of Gs[slot][128][64]; segslot[seg] = {first, count}.
+template <int P, bool TWO_D>
+__device__ __forceinline__ void load_spectrum_adj(float2* buf, const float2* __restrict__ Gs,
+                                                  const int2* __restrict__ segslot, int z,
+                                                  const PlaneDims& d) {
+  using F = PlaneFFT<P, TWO_D>;
+  const int zb = z / 128, zr = z % 128;
+  for (int kap = threadIdx.x; kap < F::NK; kap += F::NT) {
+    const int2 sc = segslot[(kap >> 6) * d.nzb + zb];
+    const float2* src = Gs + ((size_t)sc.x * 128 + zr) * 64 + (kap & 63);
+    float2 v = src[0];
+    for (int k = 1; k < sc.y; ++k) v = cadd(v, src[(size_t)k * 128 * 64]);
+    buf[F::kidx(kap)] = v;
+  }
 }
 
 template <int P, bool TWO_D>
@@ -176,7 +204,7 @@ inv_gather_kernel(PlaneDims d, const float2* __restrict__ Yh,
   float2* tw = smem + F::ELEMS;
   const int u = blockIdx.x;
   make_twiddles<P, F::NT>(tw);
-  load_spectrum<P, TWO_D>(buf, Yh + (size_t)u * d.Nk);
+  load_spectrum_fwd<P, TWO_D>(buf, Yh, u, d);
   __syncthreads();
   F::inverse(buf, tw, d.Nx);
   double acc = 0.0;
@@ -204,7 +232,7 @@ inv_resid_fwd_kernel(PlaneDims d, const float2* __restrict__ Yh,
   float2* tw = smem + F::ELEMS;
   const int u = blockIdx.x;
   make_twiddles<P, F::NT>(tw);
-  load_spectrum<P, TWO_D>(buf, Yh + (size_t)u * d.Nk);
+  load_spectrum_fwd<P, TWO_D>(buf, Yh, u, d);
   __syncthreads();
   F::inverse(buf, tw, d.Nx);
   double acc = 0.0;
@@ -252,15 +280,16 @@ scatter_fwd_kernel(PlaneDims d, const float2* __restrict__ y,
 // Gh[z] -> x plane z = crop(IFFT2(Gh_z)); optional sum |x|^2 and max |x|.
 template <int P, bool TWO_D>
 __global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT)
-inv_store_kernel(PlaneDims d, const float2* __restrict__ Gh, float2* __restrict__ x,
-                 double* __restrict__ red_sumsq, unsigned int* __restrict__ maxabs_bits) {
+inv_store_kernel(PlaneDims d, const float2* __restrict__ Gh, const int2* __restrict__ segslot,
+                 float2* __restrict__ x, double* __restrict__ red_sumsq,
+                 unsigned int* __restrict__ maxabs_bits) {
   using F = PlaneFFT<P, TWO_D>;
   extern __shared__ float2 smem[];
   float2* buf = smem;
   float2* tw = smem + F::ELEMS;
   const int z = blockIdx.x;
   make_twiddles<P, F::NT>(tw);
-  load_spectrum<P, TWO_D>(buf, Gh + (size_t)z * d.Nk);
+  load_spectrum_adj<P, TWO_D>(buf, Gh, segslot, z, d);
   __syncthreads();
   F::inverse(buf, tw, d.Nx);
   double acc = 0.0;
@@ -284,7 +313,8 @@ inv_store_kernel(PlaneDims d, const float2* __restrict__ Gh, float2* __restrict_
 // then, unless this is the last iteration, Xh[z] = FFT2(pad(gamma_{k+1})).
 template <int P, bool TWO_D>
 __global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT)
-inv_fista_fwd_kernel(PlaneDims d, const float2* __restrict__ Gh, float2* __restrict__ xk,
+inv_fista_fwd_kernel(PlaneDims d, const float2* __restrict__ Gh,
+                     const int2* __restrict__ segslot, float2* __restrict__ xk,
                      float2* __restrict__ gam, const float* __restrict__ scal, float beta,
                      int do_fwd, float2* __restrict__ Xh, double* __restrict__ red_l1) {
   using F = PlaneFFT<P, TWO_D>;
@@ -293,7 +323,7 @@ inv_fista_fwd_kernel(PlaneDims d, const float2* __restrict__ Gh, float2* __restr
   float2* tw = smem + F::ELEMS;
   const int z = blockIdx.x;
   make_twiddles<P, F::NT>(tw);
-  load_spectrum<P, TWO_D>(buf, Gh + (size_t)z * d.Nk);
+  load_spectrum_adj<P, TWO_D>(buf, Gh, segslot, z, d);
   __syncthreads();
   F::inverse(buf, tw, d.Nx);
   const float thr = scal[kThr];
@@ -325,15 +355,34 @@ inv_fista_fwd_kernel(PlaneDims d, const float2* __restrict__ Gh, float2* __restr
 
 // ---------------------------------------------------------------------------
 // Depth contractions (the blockwise products of Sec. IV-B restricted to the
-// kept bins).  T is tiled by 64 wavenumbers: T[kt][u][z][ki].  A warp lane
-// owns the wavenumber pair (2 lane, 2 lane + 1) of the tile, so every table
-// load is a coalesced 16-byte vector (512 bytes per warp) and no cross-lane
-// reduction is needed: the sums run over z (forward) or u (adjoint) inside
-// each lane.  The small spectra (Xh tile or Rh tile) are staged in shared
-// memory once per CTA; the table streams from HBM with evict-first loads.
+// kept bins).  T is tiled by 64 wavenumbers, T[kt][u][z][ki]; one table row
+// (kt, u, z) is 512 bytes.  Work is cut into units (kt, zb, u): bin u of
+// wavenumber tile kt over the depth block zb (<= 128 depths).  A persistent
+// CTA per SM takes a contiguous, equal share of the units.  Each of its 8
+// warps owns 16 depths of the block and streams its 16 rows of every unit
+// (8 KB) through its own 3-slot shared-memory ring, filled by
+// cp.async.bulk and tracked by one mbarrier per slot, so 128 KB per SM are
+// in flight without holding them in registers.  A lane owns the wavenumber
+// pair (2 lane, 2 lane + 1), so rows are read from shared memory as 16-byte
+// vectors without bank conflicts and no lane exchanges data with another.
+//   forward: Yp[zb][u][kap] = sum_{z in zb} T[kt][u][z][ki] Xh[z][kap]; the
+//            warp holds its 16 Xh values in registers and the 8 warps' partial
+//            sums are added in shared memory, four units at a time.
+//   adjoint: Gs[slot][z][ki] = sum_{u in the CTA's share} conj(T) Rh[u][kap];
+//            the warp holds its 16 accumulators in registers.  A segment
+//            (kt, zb) split between CTAs leaves one partial per CTA in
+//            consecutive slots; the consumer plane kernel adds them.
+// Waits on the mbarriers are bounded (2 s of global time); a timeout sets
+// *err, drains the copies already issued (again bounded) and ends the CTA.
 // ---------------------------------------------------------------------------
-constexpr int kContractThreads = 256;
-constexpr int kContractWarps = kContractThreads / 32;
+constexpr int kContractWarps = 8;
+constexpr int kContractThreads = kContractWarps * 32;
+constexpr int kRowsPerWarp = 16;
+constexpr int kZBlock = kContractWarps * kRowsPerWarp;  // 128 depths
+constexpr int kSlots = 3;
+constexpr int kSlotFloat4 = kRowsPerWarp * 32;          // 8 KB
+constexpr int kFwdBatch = 4;
+constexpr uint64_t kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ void cmac2(float4& acc, const float4 h, const float4 x) {
   // acc.(x,y) += (h.x + j h.y)(x.x + j x.y); acc.(z,w) likewise
@@ -350,88 +399,260 @@ __device__ __forceinline__ void cmacc2(float4& acc, const float4 h, const float4
   acc.w = fmaf(h.z, r.w, acc.w); acc.w = fmaf(-h.w, r.z, acc.w);
 }
 
-// Yh[u][kap] = sum_z T[kt][u][z][ki] Xh[z][kap]
-// grid (ceil(U / UC), Nk / 64); each warp owns whole rows u.
-template <int UNROLL>
-__global__ void __launch_bounds__(kContractThreads)
-contract_fwd_kernel(const float4* __restrict__ T, const float4* __restrict__ Xh,
-                    float4* __restrict__ Yh, int Nz, int U, int Nk, int UC) {
-  extern __shared__ float4 xs[];  // [Nz][32]
-  const int kt = blockIdx.y;
-  const size_t nk4 = (size_t)Nk / 2;
-  for (int i = threadIdx.x; i < Nz * 32; i += kContractThreads)
-    xs[i] = Xh[(size_t)(i >> 5) * nk4 + kt * 32 + (i & 31)];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int u0 = blockIdx.x * UC;
-  const int u1 = min(U, u0 + UC);
-  for (int u = u0 + warp; u < u1; u += kContractWarps) {
-    const float4* row = T + ((size_t)kt * U + u) * Nz * 32 + lane;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    int z = 0;
-    for (; z + UNROLL <= Nz; z += UNROLL) {
-      float4 h[UNROLL];
-#pragma unroll
-      for (int j = 0; j < UNROLL; ++j) h[j] = __ldcs(row + (size_t)(z + j) * 32);
-#pragma unroll
-      for (int j = 0; j < UNROLL; ++j) cmac2(acc, h[j], xs[(z + j) * 32 + lane]);
-    }
-    for (; z < Nz; ++z) cmac2(acc, __ldcs(row + (size_t)z * 32), xs[z * 32 + lane]);
-    Yh[(size_t)u * nk4 + kt * 32 + lane] = acc;
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for phase `parity` of the mbarrier; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 
-// Gh[z][kap] = sum_u conj(T[kt][u][z][ki]) Rh[u][kap]
-// grid (ceil(Nz / (8 ZW)), Nk / 64); warp w owns depths z0 + w ZW + j.
-template <int ZW>
-__global__ void __launch_bounds__(kContractThreads)
-contract_adj_kernel(const float4* __restrict__ T, const float4* __restrict__ Rh,
-                    float4* __restrict__ Gh, int Nz, int U, int Nk) {
-  extern __shared__ float4 rs[];  // [U][32]
-  const int kt = blockIdx.y;
-  const size_t nk4 = (size_t)Nk / 2;
-  for (int i = threadIdx.x; i < U * 32; i += kContractThreads)
-    rs[i] = Rh[(size_t)(i >> 5) * nk4 + kt * 32 + (i & 31)];
+struct WarpRows {
+  int z0;   // first depth of the warp's rows in the unit's block
+  int n;    // rows (0..16)
+};
+__device__ __forceinline__ WarpRows warp_rows(int zb, int w, int Nz) {
+  WarpRows r;
+  r.z0 = zb * kZBlock + w * kRowsPerWarp;
+  r.n = min(kRowsPerWarp, max(0, Nz - r.z0));
+  return r;
+}
+
+// Issue the bulk copy of this warp's rows of unit `unit` into slot `s`.  The
+// slot's mbarrier is always arrived on (with zero bytes when the warp has no
+// rows in this depth block) so that every slot completes one phase per use.
+__device__ __forceinline__ void issue_unit(const float4* __restrict__ T, int unit, int U, int Nz,
+                                           int nzb, int w, float4* slot, uint32_t bar) {
+  const int seg = unit / U, u = unit - seg * U;
+  const int kt = seg / nzb, zb = seg - kt * nzb;
+  const WarpRows wr = warp_rows(zb, w, Nz);
+  const uint32_t bytes = (uint32_t)wr.n * 512u;
+  fence_proxy_async();
+  mbar_expect_tx(bar, bytes);
+  if (bytes) {
+    const float4* src = T + ((size_t)(kt * U + u) * Nz + wr.z0) * 32;
+    bulk_g2s(smem_addr(slot), src, bytes, bar);
+  }
+}
+
+// Drain the copies this warp has in flight (uses [from, to) of its ring).
+__device__ __forceinline__ void drain_warp(int from, int to, uint32_t bar0) {
+  for (int i = from; i < to; ++i)
+    mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, kWaitNs / 4);
+}
+
+__global__ void __launch_bounds__(kContractThreads, 1)
+contract_fwd_stream(const float4* __restrict__ T, const float4* __restrict__ Xh,
+                    float4* __restrict__ Yp, int Nz, int U, int Nk, int nzb, int nunits,
+                    int* __restrict__ err) {
+  extern __shared__ __align__(128) float4 sm4[];
+  float4* ring = sm4;                                              // [8][3][512]
+  float4* red = sm4 + kContractWarps * kSlots * kSlotFloat4;       // [4][8][32]
+  uint64_t* bars = (uint64_t*)(red + kFwdBatch * kContractWarps * 32);  // [8][3]
+  __shared__ int abort_flag;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = gridDim.x, b = blockIdx.x;
+  const int first = (int)(((long long)nunits * b) / G);
+  const int last = (int)(((long long)nunits * (b + 1)) / G);
+  const int n = last - first;
+  float4* my = ring + w * kSlots * kSlotFloat4;
+  const uint32_t bar0 = smem_addr(bars + w * kSlots);
+  if (threadIdx.x == 0) abort_flag = 0;
+  if (lane == 0) {
+    for (int s = 0; s < kSlots; ++s) mbar_init(bar0 + 8u * s, 1);
+    fence_mbar_init();
+  }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int z0 = blockIdx.x * (kContractWarps * ZW) + warp * ZW;
-  if (z0 >= Nz) return;
-  const int nz = min(ZW, Nz - z0);
-  float4 acc[ZW];
+  const size_t nk4 = (size_t)Nk / 2;
+  int next_issue = 0;
+  if (lane == 0)
+    for (; next_issue < kSlots - 1 && next_issue < n; ++next_issue)
+      issue_unit(T, first + next_issue, U, Nz, nzb, w, my + (next_issue % kSlots) * kSlotFloat4,
+                 bar0 + 8u * (next_issue % kSlots));
+  next_issue = __shfl_sync(0xffffffffu, next_issue, 0);
+  float4 xr[kRowsPerWarp];
+  int cur_seg = -1;
+  bool ok = true;
+  int waited = 0;  // uses of the ring waited for so far
+  int i = 0;
+  for (int base = 0; base < n; base += kFwdBatch) {
+    const int nb = min(kFwdBatch, n - base);
+    for (int j = 0; j < nb; ++j, ++i) {
+      const int unit = first + i;
+      const int seg = unit / U;
+      const int kt = seg / nzb, zb = seg - kt * nzb;
+      const WarpRows wr = warp_rows(zb, w, Nz);
+      // keep kSlots - 1 copies ahead: refill the slot consumed last time
+      if (ok && next_issue < n && next_issue <= i + kSlots - 1) {
+        if (lane == 0)
+          issue_unit(T, first + next_issue, U, Nz, nzb, w, my + (next_issue % kSlots) * kSlotFloat4,
+                     bar0 + 8u * (next_issue % kSlots));
+        ++next_issue;
+      }
+      if (seg != cur_seg) {  // new (kt, zb): this warp's Xh rows into registers
+        cur_seg = seg;
 #pragma unroll
-  for (int j = 0; j < ZW; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-  const float4* base = T + ((size_t)kt * U * Nz + z0) * 32 + lane;
-  const size_t ustride = (size_t)Nz * 32;
-  if (nz == ZW) {
-    int u = 0;
-    for (; u + 2 <= U; u += 2) {
-      float4 h0[ZW], h1[ZW];
+        for (int r = 0; r < kRowsPerWarp; ++r)
+          xr[r] = r < wr.n ? Xh[(size_t)(wr.z0 + r) * nk4 + kt * 32 + lane]
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (ok) {
+        if (!mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, kWaitNs)) {
+          ok = false;
+          if (lane == 0) {
+            atomicExch(err, 1);
+            abort_flag = 1;
+          }
+        } else {
+          waited = i + 1;
+          const float4* slot = my + (i % kSlots) * kSlotFloat4;
 #pragma unroll
-      for (int j = 0; j < ZW; ++j) h0[j] = __ldcs(base + u * ustride + j * 32);
-#pragma unroll
-      for (int j = 0; j < ZW; ++j) h1[j] = __ldcs(base + (u + 1) * ustride + j * 32);
-      const float4 r0 = rs[u * 32 + lane], r1 = rs[(u + 1) * 32 + lane];
-#pragma unroll
-      for (int j = 0; j < ZW; ++j) cmacc2(acc[j], h0[j], r0);
-#pragma unroll
-      for (int j = 0; j < ZW; ++j) cmacc2(acc[j], h1[j], r1);
+          for (int r = 0; r < kRowsPerWarp; ++r)
+            if (r < wr.n) cmac2(acc, slot[r * 32 + lane], xr[r]);
+        }
+      }
+      __syncwarp();
+      red[(j * kContractWarps + w) * 32 + lane] = acc;
     }
-    for (; u < U; ++u) {
-      const float4 r = rs[u * 32 + lane];
+    __syncthreads();
+    if (abort_flag) ok = false;
+    if (w < nb && ok) {
+      float4 s = red[(w * kContractWarps) * 32 + lane];
 #pragma unroll
-      for (int j = 0; j < ZW; ++j) cmacc2(acc[j], __ldcs(base + u * ustride + j * 32), r);
+      for (int k = 1; k < kContractWarps; ++k) {
+        const float4 v = red[(w * kContractWarps + k) * 32 + lane];
+        s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+      }
+      const int unit = first + base + w;
+      const int seg = unit / U, u = unit - seg * U;
+      const int kt = seg / nzb, zb = seg - kt * nzb;
+      Yp[((size_t)zb * U + u) * nk4 + kt * 32 + lane] = s;
     }
-  } else {
-    for (int u = 0; u < U; ++u) {
-      const float4 r = rs[u * 32 + lane];
+    __syncthreads();
+    if (!ok) break;
+  }
+  if (!ok) drain_warp(waited, next_issue, bar0);
+}
+
+__global__ void __launch_bounds__(kContractThreads, 1)
+contract_adj_stream(const float4* __restrict__ T, const float4* __restrict__ Rh,
+                    float4* __restrict__ Gs, int Nz, int U, int Nk, int nzb, int nunits,
+                    int* __restrict__ err) {
+  extern __shared__ __align__(128) float4 sm4[];
+  float4* ring = sm4;
+  uint64_t* bars = (uint64_t*)(sm4 + kContractWarps * kSlots * kSlotFloat4);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = gridDim.x, b = blockIdx.x;
+  const int first = (int)(((long long)nunits * b) / G);
+  const int last = (int)(((long long)nunits * (b + 1)) / G);
+  const int n = last - first;
+  float4* my = ring + w * kSlots * kSlotFloat4;
+  const uint32_t bar0 = smem_addr(bars + w * kSlots);
+  if (lane == 0) {
+    for (int s = 0; s < kSlots; ++s) mbar_init(bar0 + 8u * s, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  const size_t nk4 = (size_t)Nk / 2;
+  int next_issue = 0;
+  if (lane == 0)
+    for (; next_issue < kSlots - 1 && next_issue < n; ++next_issue)
+      issue_unit(T, first + next_issue, U, Nz, nzb, w, my + (next_issue % kSlots) * kSlotFloat4,
+                 bar0 + 8u * (next_issue % kSlots));
+  next_issue = __shfl_sync(0xffffffffu, next_issue, 0);
+  // Rh rows prefetched two units ahead in registers
+  auto rh_of = [&](int i) -> float4 {
+    if (i >= n) return make_float4(0.f, 0.f, 0.f, 0.f);
+    const int unit = first + i;
+    const int seg = unit / U, u = unit - seg * U;
+    const int kt = seg / nzb;
+    return Rh[(size_t)u * nk4 + kt * 32 + lane];
+  };
+  float4 r0 = rh_of(0), r1 = rh_of(1);
+  float4 acc[kRowsPerWarp];
 #pragma unroll
-      for (int j = 0; j < ZW; ++j)
-        if (j < nz) cmacc2(acc[j], __ldcs(base + u * ustride + j * 32), r);
+  for (int r = 0; r < kRowsPerWarp; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+  int i = 0;
+  for (; i < n; ++i) {
+    const int unit = first + i;
+    const int seg = unit / U;
+    const int zb = seg % nzb;
+    const WarpRows wr = warp_rows(zb, w, Nz);
+    if (next_issue < n && next_issue <= i + kSlots - 1) {
+      if (lane == 0)
+        issue_unit(T, first + next_issue, U, Nz, nzb, w, my + (next_issue % kSlots) * kSlotFloat4,
+                   bar0 + 8u * (next_issue % kSlots));
+      ++next_issue;
+    }
+    const float4 r = r0;
+    r0 = r1;
+    r1 = rh_of(i + 2);
+    if (!mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, kWaitNs)) {
+      if (lane == 0) atomicExch(err, 1);
+      drain_warp(i, next_issue, bar0);
+      return;
+    }
+    if (wr.n > 0) {
+      const float4* slot = my + (i % kSlots) * kSlotFloat4;
+#pragma unroll
+      for (int rr = 0; rr < kRowsPerWarp; ++rr)
+        if (rr < wr.n) cmacc2(acc[rr], slot[rr * 32 + lane], r);
+    }
+    __syncwarp();
+    const bool seg_end = (i + 1 == n) || ((unit + 1) / U != seg);
+    if (seg_end) {
+      if (wr.n > 0) {
+        float4* dst = Gs + ((size_t)(seg + b) * kZBlock + w * kRowsPerWarp) * 32 + lane;
+#pragma unroll
+        for (int rr = 0; rr < kRowsPerWarp; ++rr)
+          if (rr < wr.n) dst[rr * 32] = acc[rr];
+      }
+#pragma unroll
+      for (int rr = 0; rr < kRowsPerWarp; ++rr) acc[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
-#pragma unroll
-  for (int j = 0; j < ZW; ++j)
-    if (j < nz) Gh[(size_t)(z0 + j) * nk4 + kt * 32 + lane] = acc[j];
 }
 
 // ---------------------------------------------------------------------------
@@ -485,24 +706,27 @@ __global__ void scale_rnorm_kernel(float2* v, int n, const double* sumsq) {
 // ---------------------------------------------------------------------------
 // Dispatch on the plane size
 // ---------------------------------------------------------------------------
-// Raise a kernel's dynamic shared memory limit to the device's opt-in maximum
-// once per (kernel, device); each launch then asks for what it needs.
+// Raise a kernel's dynamic shared memory limit to what the device allows next
+// to the kernel's static shared memory, once per (kernel, device); each
+// launch then asks for what it needs.
 int ensure_smem_attr_ptr(const void* kernel, int need) {
   int dev = 0;
   SFS_CUDA(cudaGetDevice(&dev));
-  const int optin = max_smem_optin();
-  if (need > optin) {
-    set_error("kernel needs %d bytes of shared memory, device allows %d", need, optin);
-    return SFS_ERR_INVALID_ARG;
-  }
-  if (need <= 48 * 1024) return SFS_OK;
   static std::mutex mu;
   static std::unordered_map<const void*, uint64_t> done;  // kernel -> device bits
   std::lock_guard<std::mutex> lock(mu);
   uint64_t& bits = done[kernel];
   if (dev < 64 && ((bits >> dev) & 1u)) return SFS_OK;
-  SFS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-  if (dev < 64) bits |= (uint64_t)1 << dev;
+  cudaFuncAttributes fa;
+  SFS_CUDA(cudaFuncGetAttributes(&fa, kernel));
+  const int limit = max_smem_optin() - (int)fa.sharedSizeBytes;
+  if (need > limit) {
+    set_error("kernel needs %d bytes of dynamic shared memory, device allows %d", need, limit);
+    return SFS_ERR_INVALID_ARG;
+  }
+  if (need > 48 * 1024)
+    SFS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+  if (dev < 64) bits |= (uint64_t)1 << dev;  // each kernel always asks the same size
   return SFS_OK;
 }
 
@@ -592,44 +816,53 @@ int launch_scatter_fwd(const PlaneDims& d, const float2* y, const int32_t* posma
   });
 }
 
-int launch_inv_store(const PlaneDims& d, const float2* Gh, float2* x, double* red_sumsq,
-                     unsigned int* maxabs_bits, cudaStream_t st) {
+int launch_inv_store(const PlaneDims& d, const float2* Gh, const int2* segslot, float2* x,
+                     double* red_sumsq, unsigned int* maxabs_bits, cudaStream_t st) {
   return dispatch_plane(d, [&]<int P, bool TD>() {
-    return launch_plane<P, TD>(inv_store_kernel<P, TD>, d.Nz, st, d, Gh, x, red_sumsq,
+    return launch_plane<P, TD>(inv_store_kernel<P, TD>, d.Nz, st, d, Gh, segslot, x, red_sumsq,
                                maxabs_bits);
   });
 }
 
-int launch_inv_fista_fwd(const PlaneDims& d, const float2* Gh, float2* xk, float2* gam,
-                         const float* scal, float beta, int do_fwd, float2* Xh,
+int launch_inv_fista_fwd(const PlaneDims& d, const float2* Gh, const int2* segslot, float2* xk,
+                         float2* gam, const float* scal, float beta, int do_fwd, float2* Xh,
                          double* red_l1, cudaStream_t st) {
   return dispatch_plane(d, [&]<int P, bool TD>() {
-    return launch_plane<P, TD>(inv_fista_fwd_kernel<P, TD>, d.Nz, st, d, Gh, xk, gam, scal,
-                               beta, do_fwd, Xh, red_l1);
+    return launch_plane<P, TD>(inv_fista_fwd_kernel<P, TD>, d.Nz, st, d, Gh, segslot, xk, gam,
+                               scal, beta, do_fwd, Xh, red_l1);
   });
 }
 
+int contract_units(const PlaneDims& d) { return (d.Nk / kKappaTile) * d.nzb * d.U; }
+
+size_t contract_fwd_smem() {
+  return (size_t)kContractWarps * kSlots * kSlotFloat4 * 16 +
+         (size_t)kFwdBatch * kContractWarps * 32 * 16 + kContractWarps * kSlots * 8;
+}
+size_t contract_adj_smem() {
+  return (size_t)kContractWarps * kSlots * kSlotFloat4 * 16 + kContractWarps * kSlots * 8;
+}
+
 int launch_contract_fwd(const PlaneDims& d, const float2* table, const float2* Xh,
-                        float2* Yh, cudaStream_t st) {
-  constexpr int UC = 2 * kContractWarps;
-  const size_t smem = (size_t)d.Nz * 32 * sizeof(float4);
-  SFS_TRY(ensure_smem_attr(contract_fwd_kernel<8>, (int)smem));
-  dim3 grid((d.U + UC - 1) / UC, d.Nk / kKappaTile);
-  contract_fwd_kernel<8><<<grid, kContractThreads, smem, st>>>(
-      (const float4*)table, (const float4*)Xh, (float4*)Yh, d.Nz, d.U, d.Nk, UC);
+                        float2* Yp, int* err, cudaStream_t st) {
+  const size_t smem = contract_fwd_smem();
+  SFS_TRY(ensure_smem_attr(contract_fwd_stream, (int)smem));
+  const int n = contract_units(d);
+  const int G = std::min(d.G, n);
+  contract_fwd_stream<<<G, kContractThreads, smem, st>>>(
+      (const float4*)table, (const float4*)Xh, (float4*)Yp, d.Nz, d.U, d.Nk, d.nzb, n, err);
   SFS_CUDA(cudaGetLastError());
   return SFS_OK;
 }
 
 int launch_contract_adj(const PlaneDims& d, const float2* table, const float2* Rh,
-                        float2* Gh, cudaStream_t st) {
-  constexpr int ZW = 2;
-  const size_t smem = (size_t)d.U * 32 * sizeof(float4);
-  SFS_TRY(ensure_smem_attr(contract_adj_kernel<ZW>, (int)smem));
-  const int zc = kContractWarps * ZW;
-  dim3 grid((d.Nz + zc - 1) / zc, d.Nk / kKappaTile);
-  contract_adj_kernel<ZW><<<grid, kContractThreads, smem, st>>>(
-      (const float4*)table, (const float4*)Rh, (float4*)Gh, d.Nz, d.U, d.Nk);
+                        float2* Gs, int* err, cudaStream_t st) {
+  const size_t smem = contract_adj_smem();
+  SFS_TRY(ensure_smem_attr(contract_adj_stream, (int)smem));
+  const int n = contract_units(d);
+  const int G = std::min(d.G, n);
+  contract_adj_stream<<<G, kContractThreads, smem, st>>>(
+      (const float4*)table, (const float4*)Rh, (float4*)Gs, d.Nz, d.U, d.Nk, d.nzb, n, err);
   SFS_CUDA(cudaGetLastError());
   return SFS_OK;
 }

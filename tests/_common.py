@@ -16,7 +16,10 @@ def geom_params(**kw):
 
 
 def oracle_geometry(params):
-    return O.Geometry(**{k: params[k] for k in synth.GEOM_KEYS if k in params})
+    kw = {k: params[k] for k in synth.GEOM_KEYS if k in params}
+    if "t0" in params:
+        kw["t0"] = params["t0"]
+    return O.Geometry(**kw)
 
 
 def rel_err(a, b):
