@@ -156,6 +156,28 @@ int sfs_apply_A(sfs_operator* op, const void* x_dev, void* y_dev, void* stream);
 int sfs_apply_AH(sfs_operator* op, const void* y_dev, void* x_dev, void* stream);
 
 /*
+ * Backward projection x = A^H y that allocates nothing at call time.  The
+ * paper has no counterpart: this is an interface variant of sfs_apply_AH
+ * (same arguments, same result) for callers that must not allocate device
+ * memory once they are running: acquisition or real-time loops that forbid
+ * allocation after start-up so that every call has the same latency, and
+ * host frameworks that own all device memory through their own pool.  Such
+ * callers create the operator at set-up time; this call then touches no
+ * allocator.  Its intermediate data live in one static device array of
+ * SFS_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  All calls share that array and it keeps the last
+ * call's contents, so calls whose device work overlaps in time (on other
+ * streams, or with other operators of the same device) race and give wrong
+ * results; order them on one stream.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  An operator whose scratch,
+ * 8 * (U * Nkappa + slots * 8192) bytes, exceeds the maximum is rejected with
+ * SFS_ERR_INVALID_ARG and a message naming both sizes.
+ */
+#define SFS_NOALLOC_SCRATCH_BYTES (32u << 20)
+int sfs_apply_AH_noalloc(sfs_operator* op, const void* y_dev, void* x_dev, void* stream);
+
+/*
  * ||A^H y||_inf (used by the regularisation rule lambda = mu ||beta(y)||_inf
  * of Sec. VII).  Synchronises `stream`; writes the value to *out_host.
  */

@@ -43,7 +43,8 @@ STATUS_NAMES = {0: "SFS_OK", -1: "SFS_ERR_INVALID_ARG", -2: "SFS_ERR_BAND_TOO_NA
 # every symbol include/sfs.h declares
 EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_select_freqs", "sfs_operator_from_indices", "sfs_destroy_operator",
-           "sfs_operator_info", "sfs_apply_A", "sfs_apply_AH", "sfs_max_abs_AH",
+           "sfs_operator_info", "sfs_apply_A", "sfs_apply_AH", "sfs_apply_AH_noalloc",
+           "sfs_max_abs_AH",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_last_error",
            "sfs_version")
 
@@ -102,6 +103,7 @@ def lib():
         "sfs_operator_info": [vp, P(OperatorInfo)],
         "sfs_apply_A": [vp, vp, vp, vp],
         "sfs_apply_AH": [vp, vp, vp, vp],
+        "sfs_apply_AH_noalloc": [vp, vp, vp, vp],
         "sfs_max_abs_AH": [vp, vp, P(dbl), vp],
         "sfs_lipschitz": [vp, i32, dbl, u64, dbl, P(dbl), vp],
         "sfs_fista": [vp, vp, dbl, dbl, i32, vp, u32, P(dbl), vp],
@@ -201,6 +203,12 @@ def sfs_apply_A(op, x_dev_ptr, y_dev_ptr, stream_ptr):
 
 def sfs_apply_AH(op, y_dev_ptr, x_dev_ptr, stream_ptr):
     _check(lib().sfs_apply_AH(op, y_dev_ptr, x_dev_ptr, stream_ptr))
+
+
+def sfs_apply_AH_noalloc(op, y_dev_ptr, x_dev_ptr, stream_ptr):
+    """A^H y with all intermediate data in the library's static device array
+    (no allocation during the call); see include/sfs.h."""
+    _check(lib().sfs_apply_AH_noalloc(op, y_dev_ptr, x_dev_ptr, stream_ptr))
 
 
 def sfs_max_abs_AH(op, y_dev_ptr, stream_ptr) -> float:
