@@ -85,8 +85,11 @@ typedef struct sfs_operator_info_t {
   int32_t k_lo, k_hi;   /* candidate band (inclusive) used by the selection   */
   double band_db;       /* band rung (dB below the peak bin) that was used    */
   double alpha, t0;     /* pulse rate [1/s] and receive-window start [s]      */
-  int64_t table_bytes;  /* bytes of the lateral-FFT generator table          */
+  int64_t table_bytes;  /* bytes of the lateral-FFT generator table (one entry
+                           per symmetry orbit of wavenumbers)                 */
   int32_t launches_per_iter; /* kernels one FISTA iteration launches          */
+  int32_t Nslot;        /* wavenumber slots (orbit-major, padded to 64)        */
+  int32_t GS;           /* slots per symmetry orbit (2, 4 or 8)               */
 } sfs_operator_info_t;
 
 /*
@@ -131,7 +134,10 @@ int sfs_select_freqs(sfs_geometry* g, int strategy, int M, int per_position,
  * generating elements of the block 2-level Toeplitz H (Theorem 2, Sec. IV-B)
  * evaluated at the union U of the kept bins with the frequency-domain model
  * of Eq. (4):  h_{k,z}[d] = fs H(f_k) g exp(-j 2 pi f_k (tau(d, z) - t0)).
- * Memory: 8 * Px*Py * U * Nz bytes for the table plus O(V + U*Px*Py) work
+ * The FFT2 of a generator is the same on every wavenumber of a symmetry
+ * orbit (sign flips, and kx <-> ky on square grids), so the table holds one
+ * entry per orbit: about 8 * Px*Py * U * Nz / 7.2 bytes for square area scans,
+ * / 3.7 for other area scans, / 2 for line scans, plus O(V + U*Px*Py) work
  * space.  Synchronises the device.
  * Errors: SFS_ERR_INVALID_ARG, SFS_ERR_OOM, SFS_ERR_CUDA.
  */
@@ -171,7 +177,7 @@ int sfs_apply_AH(sfs_operator* op, const void* y_dev, void* x_dev, void* stream)
  * results; order them on one stream.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture.  An operator whose scratch,
- * 8 * (U * Nkappa + slots * 8192) bytes, exceeds the maximum is rejected with
+ * 8 * (U * Nslot + slots * 8192) bytes, exceeds the maximum is rejected with
  * SFS_ERR_INVALID_ARG and a message naming both sizes.
  */
 #define SFS_NOALLOC_SCRATCH_BYTES (32u << 20)

@@ -187,6 +187,8 @@ void free_operator(sfs_operator* op) {
   cudaFree(op->ws.Rh);
   cudaFree(op->ws.Gh);
   cudaFree(op->ws.segslot);
+  cudaFree(op->slot_kappa);
+  cudaFree(op->orbit_rep);
   cudaFree(op->ws.err);
   cudaFree(op->ws.xk);
   cudaFree(op->ws.gam);
@@ -199,7 +201,9 @@ void free_operator(sfs_operator* op) {
   delete op;
 }
 
-PlaneDims dims_of(const sfs_operator* op) {
+}  // namespace
+
+PlaneDims operator_dims(const sfs_operator* op) {
   PlaneDims d;
   d.Nx = op->geo.d.Nx;
   d.Ny = op->geo.d.Ny;
@@ -212,8 +216,17 @@ PlaneDims dims_of(const sfs_operator* op) {
   d.U = op->U;
   d.nzb = op->nzb;
   d.G = op->G;
+  d.Ns = op->Ns;
+  d.GS = op->GS;
+  d.Up = op->Up;
+  d.slot_kappa = op->slot_kappa;
+  d.orbit_rep = op->orbit_rep;
   return d;
 }
+
+namespace {
+
+PlaneDims dims_of(const sfs_operator* op) { return operator_dims(op); }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -420,6 +433,45 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
   }
   op->nzb = (d.Nz + kZBlockRows - 1) / kZBlockRows;
 
+  // Symmetry orbits of the lateral wavenumbers.  The generators depend on
+  // dx^2 + dy^2 only, so their FFT2 is invariant under kx -> -kx, ky -> -ky
+  // and, on a square grid with equal pitches and sizes, kx <-> ky.  Spectra
+  // are kept orbit-major in GS slots per orbit (padding slots carry -1), and
+  // the table holds one entry per orbit.  Wavenumber kappa = kx * Py + ky
+  // (the FFT engine's order); for a line scan kappa = kx.
+  const bool two_d = g->Py > 1;
+  const bool swap = two_d && g->Px == g->Py && d.Nx == d.Ny && d.dx == d.dy;
+  op->GS = two_d ? (swap ? 8 : 4) : 2;
+  std::vector<int32_t> slot_kappa, orbit_rep;
+  {
+    const int Px = g->Px, Py = g->Py;
+    const int half = std::max(Px, Py) / 2 + 1;
+    std::vector<int> orbit_of((size_t)half * half, -1);
+    std::vector<std::vector<int>> members;
+    for (int kap = 0; kap < Px * Py; ++kap) {
+      const int kx = two_d ? kap / Py : kap;
+      const int ky = two_d ? kap % Py : 0;
+      int ax = std::min(kx, (Px - kx) % Px);
+      int ay = two_d ? std::min(ky, (Py - ky) % Py) : 0;
+      if (swap && ax > ay) std::swap(ax, ay);
+      int& o = orbit_of[(size_t)ax * half + ay];
+      if (o < 0) {
+        o = (int)members.size();
+        members.emplace_back();
+      }
+      members[o].push_back(kap);
+    }
+    op->No = (int)members.size();
+    op->Up = (op->U + op->GS / 2 - 1) / (op->GS / 2) * (op->GS / 2);
+    op->Ns = (op->No * op->GS + kKappaTile - 1) / kKappaTile * kKappaTile;
+    slot_kappa.assign(op->Ns, -1);
+    orbit_rep.assign(op->Ns / op->GS, -1);
+    for (int o = 0; o < op->No; ++o) {
+      orbit_rep[o] = members[o][0];
+      for (size_t m = 0; m < members[o].size(); ++m) slot_kappa[(size_t)o * op->GS + m] = members[o][m];
+    }
+  }
+
   // host FP64 geometry tables: (tau - t0) fs / Nt split into (hi, lo) floats,
   // directivity, per-bin amplitude fs H(f_k) / (Px Py)
   const size_t nt = (size_t)d.Nz * d.Ny * d.Nx;
@@ -476,21 +528,24 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
     cudaError_t e0 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d.device);
     if (e0 != cudaSuccess) return fail(cuda_fail(e0, "SM count query", __FILE__, __LINE__));
   }
-  const int nseg = (op->Nk / kKappaTile) * op->nzb;
-  op->G = std::max(1, std::min(sms, nseg * op->U));
+  const int nseg = (op->Ns / kKappaTile) * op->nzb;
+  const int ngroups = op->Up / (op->GS / 2);
+  op->G = std::max(1, std::min(sms, nseg * ngroups));
   op->nslots = nseg + op->G - 1;
-  const std::vector<int2> segslot = segment_slots(nseg, op->U, op->G);
-  const size_t Nk = op->Nk;
-  const size_t table_elems = Nk * op->U * d.Nz;
+  const std::vector<int2> segslot = segment_slots(nseg, ngroups, op->G);
+  const size_t Ns = op->Ns;
+  const size_t table_elems = Ns / op->GS * op->Up * d.Nz;
   if ((rc = dev_alloc(&op->table, table_elems)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->posmap, posmap.size())) != SFS_OK) return fail(rc);
-  if ((rc = dev_alloc(&op->ws.Xh, Nk * d.Nz)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.Xh, Ns * d.Nz)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->slot_kappa, slot_kappa.size())) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->orbit_rep, orbit_rep.size())) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.Gh, (size_t)op->nslots * kZBlockRows * kKappaTile)) != SFS_OK)
     return fail(rc);
   if ((rc = dev_alloc(&op->ws.segslot, segslot.size())) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.err, 1)) != SFS_OK) return fail(rc);
-  if ((rc = dev_alloc(&op->ws.Yh, Nk * op->U * op->nzb)) != SFS_OK) return fail(rc);
-  if ((rc = dev_alloc(&op->ws.Rh, Nk * op->U)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.Yh, Ns * op->Up * op->nzb)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.Rh, Ns * op->Up)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.xk, (size_t)op->V)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.gam, (size_t)op->V)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.ybuf, (size_t)S * M)) != SFS_OK) return fail(rc);
@@ -510,6 +565,13 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
   if (e == cudaSuccess) e = cudaMemset(op->ws.scal, 0, kNumFloatScalars * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(op->ws.red, 0, kNumRed * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(op->ws.err, 0, sizeof(int));
+  // padding bins U..Up-1: zero table rows and zero residual spectra, never written later
+  if (e == cudaSuccess) e = cudaMemset(op->table, 0, table_elems * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMemset(op->ws.Rh, 0, Ns * op->Up * sizeof(float2));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(op->slot_kappa, slot_kappa.data(), slot_kappa.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(op->orbit_rep, orbit_rep.data(), orbit_rep.size() * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(op->ws.segslot, segslot.data(), segslot.size() * sizeof(int2),
                    cudaMemcpyHostToDevice);
@@ -576,8 +638,10 @@ int sfs_operator_info(const sfs_operator* op, sfs_operator_info_t* info) {
   info->band_db = op->band_db;
   info->alpha = op->geo.alpha;
   info->t0 = op->geo.d.t0;
-  info->table_bytes = (int64_t)op->Nk * op->U * op->geo.d.Nz * 8;
+  info->table_bytes = (int64_t)(op->Ns / op->GS) * op->Up * op->geo.d.Nz * 8;
   info->launches_per_iter = 4;
+  info->Nslot = op->Ns;
+  info->GS = op->GS;
   return SFS_OK;
 }
 

@@ -55,9 +55,10 @@ enum RedSlot {
 };
 
 struct Workspace {
-  float2* Xh = nullptr;     // [Nz][Nk]   lateral spectra of voxel planes
-  float2* Yh = nullptr;     // [U][Nk]    lateral spectra of bin planes (forward)
-  float2* Rh = nullptr;     // [U][Nk]    lateral spectra of residual planes
+  float2* Xh = nullptr;     // [Nz][Ns]   lateral spectra of voxel planes (slot order)
+  float2* Yh = nullptr;     // [nzb][Up][Ns] depth-block partials of bin-plane spectra
+  float2* Rh = nullptr;     // [Up][Ns]   lateral spectra of residual planes (rows
+                            //            U..Up-1 stay zero)
   float2* Gh = nullptr;     // [nslots][128][64] adjoint contraction partials
   int2* segslot = nullptr;  // [nseg] {first slot, slot count} per (tile, depth block)
   int* err = nullptr;       // device flag: a bounded wait in a kernel timed out
@@ -82,6 +83,8 @@ struct sfs_geometry {
 struct sfs_operator {
   sfs_geometry geo;
   int M = 0, S = 0, V = 0, U = 0, Nk = 0;
+  int Ns = 0, GS = 0, No = 0;  // wavenumber slots, slots per orbit, orbits
+  int Up = 0;                  // bins padded to a multiple of GS / 2
   int nzb = 1;                 // depth blocks of <= 128 in the contractions
   int G = 1;                   // persistent CTAs of the contractions
   int nslots = 0;              // adjoint partial-sum slots
@@ -90,7 +93,10 @@ struct sfs_operator {
   std::vector<int32_t> idx;    // [S][M]
   std::vector<int32_t> bins;   // [U] union of kept bins, ascending
   // device data
-  float2* table = nullptr;     // [Nk/64][U][Nz][64] c64, includes 1/(Px*Py)
+  float2* table = nullptr;     // [Ns/64][Up][Nz][64/GS] c64, one entry per symmetry
+                               // orbit of wavenumbers, includes 1/(Px*Py)
+  int32_t* slot_kappa = nullptr;  // [Ns]
+  int32_t* orbit_rep = nullptr;   // [Ns/GS]
   int32_t* posmap = nullptr;   // [U][S]: m with idx[s][m] == bins[u], else -1
   sfs::Workspace ws;
   // kernel timing (SFS_FISTA_TIME_KERNELS)
@@ -106,12 +112,20 @@ struct PlaneDims {
   int Nx, Ny, Nz, Px, Py, Nk, S, M, U;
   int nzb;  // depth blocks of <= 128 depths in the contractions
   int G;    // persistent CTAs of the contractions (<= SM count)
+  int Ns;   // wavenumber slots (orbit-major, a multiple of 64)
+  int GS;   // slots per symmetry orbit: 2 (line), 4 (area), 8 (square area)
+  int Up;   // bins padded to a multiple of GS / 2 (zero table rows and spectra)
+  const int32_t* slot_kappa;  // [Ns] wavenumber of each slot, -1 for padding
+  const int32_t* orbit_rep;   // [Ns / GS] representative wavenumber, -1 for padding
 };
 
 // Depth block of the contractions and the partial-sum slots of the adjoint.
 constexpr int kZBlockRows = 128;
-// Units of contraction work: (wavenumber tile, depth block, bin).
+// Units of contraction work: (slot tile, depth block, bin).
 int contract_units(const PlaneDims& d);
+
+// Kernel-side dimensions and tables of an operator (sfs_api.cu).
+PlaneDims operator_dims(const sfs_operator* op);
 
 // Table of generators (Theorem 2 / Eq. (4)); tof: float2 [Nz][Ny][Nx]
 // (hi, lo) of (tau - t0) fs / Nt in turns per unit bin; gdir: float

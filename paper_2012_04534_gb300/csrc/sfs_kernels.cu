@@ -107,9 +107,14 @@ build_table_kernel(PlaneDims d, const float2* __restrict__ tof,
   }
   __syncthreads();
   F::forward(buf, tw, P);
-  for (int kap = threadIdx.x; kap < F::NK; kap += F::NT) {
-    const size_t o = (((size_t)(kap >> 6) * d.U + u) * d.Nz + z) * kKappaTile + (kap & 63);
-    table[o] = buf[F::kidx(kap)];
+  // FFT2 of the generator is constant on each symmetry orbit of wavenumbers
+  // (h depends on dx^2 + dy^2 only); store it once per orbit, at the orbit's
+  // representative.  Orbit o lives in slot tile o / E, entry o % E.
+  const int E = kKappaTile / d.GS;
+  for (int o = threadIdx.x; o < d.Ns / d.GS; o += F::NT) {
+    const int rep = d.orbit_rep[o];
+    const size_t off = (((size_t)(o / E) * d.Up + u) * d.Nz + z) * E + (o % E);
+    table[off] = rep >= 0 ? buf[F::kidx(rep)] : make_float2(0.f, 0.f);
   }
 }
 
@@ -122,33 +127,41 @@ __device__ __forceinline__ void zero_plane(float2* buf) {
   for (int e = threadIdx.x; e < F::ELEMS; e += F::NT) buf[e] = make_float2(0.f, 0.f);
 }
 
+// Lateral spectra travel between kernels in slot order: slot j holds
+// wavenumber slot_kappa[j] (orbit-major, GS slots per symmetry orbit, -1 for
+// padding slots, which carry zero).
+
 // Spectrum of bin plane u from the forward contraction: the sum of its nzb
-// depth-block partials Yp[zb][u][kap] (plane stride U * Nk).
+// depth-block partials Yp[zb][u][slot] (plane stride U * Ns).
 template <int P, bool TWO_D>
 __device__ __forceinline__ void load_spectrum_fwd(float2* buf, const float2* __restrict__ Yp,
                                                   int u, const PlaneDims& d) {
   using F = PlaneFFT<P, TWO_D>;
-  const float2* src = Yp + (size_t)u * d.Nk;
-  const size_t stride = (size_t)d.U * d.Nk;
-  for (int kap = threadIdx.x; kap < F::NK; kap += F::NT) {
-    float2 v = src[kap];
-    for (int zb = 1; zb < d.nzb; ++zb) v = cadd(v, src[zb * stride + kap]);
+  const float2* src = Yp + (size_t)u * d.Ns;
+  const size_t stride = (size_t)d.Up * d.Ns;
+  for (int j = threadIdx.x; j < d.Ns; j += F::NT) {
+    const int kap = d.slot_kappa[j];
+    if (kap < 0) continue;
+    float2 v = src[j];
+    for (int zb = 1; zb < d.nzb; ++zb) v = cadd(v, src[zb * stride + j]);
     buf[F::kidx(kap)] = v;
   }
 }
 
-// Spectrum of voxel plane z from the adjoint contraction: for each wavenumber
-// tile, the sum of the partial results its segment (tile, depth block) left
-// in consecutive slots of Gs[slot][128][64]; segslot[seg] = {first, count}.
+// Spectrum of voxel plane z from the adjoint contraction: for each slot tile,
+// the sum of the partial results its segment (tile, depth block) left in
+// consecutive slots of Gs[slot][128][64]; segslot[seg] = {first, count}.
 template <int P, bool TWO_D>
 __device__ __forceinline__ void load_spectrum_adj(float2* buf, const float2* __restrict__ Gs,
                                                   const int2* __restrict__ segslot, int z,
                                                   const PlaneDims& d) {
   using F = PlaneFFT<P, TWO_D>;
   const int zb = z / 128, zr = z % 128;
-  for (int kap = threadIdx.x; kap < F::NK; kap += F::NT) {
-    const int2 sc = segslot[(kap >> 6) * d.nzb + zb];
-    const float2* src = Gs + ((size_t)sc.x * 128 + zr) * 64 + (kap & 63);
+  for (int j = threadIdx.x; j < d.Ns; j += F::NT) {
+    const int kap = d.slot_kappa[j];
+    if (kap < 0) continue;
+    const int2 sc = segslot[(j >> 6) * d.nzb + zb];
+    const float2* src = Gs + ((size_t)sc.x * 128 + zr) * 64 + (j & 63);
     float2 v = src[0];
     for (int k = 1; k < sc.y; ++k) v = cadd(v, src[(size_t)k * 128 * 64]);
     buf[F::kidx(kap)] = v;
@@ -156,9 +169,13 @@ __device__ __forceinline__ void load_spectrum_adj(float2* buf, const float2* __r
 }
 
 template <int P, bool TWO_D>
-__device__ __forceinline__ void store_spectrum(const float2* buf, float2* __restrict__ dst) {
+__device__ __forceinline__ void store_spectrum(const float2* buf, float2* __restrict__ dst,
+                                               const PlaneDims& d) {
   using F = PlaneFFT<P, TWO_D>;
-  for (int kap = threadIdx.x; kap < F::NK; kap += F::NT) dst[kap] = buf[F::kidx(kap)];
+  for (int j = threadIdx.x; j < d.Ns; j += F::NT) {
+    const int kap = d.slot_kappa[j];
+    dst[j] = kap >= 0 ? buf[F::kidx(kap)] : make_float2(0.f, 0.f);
+  }
 }
 
 // Zero every slot of the plane outside the Ny x Nx crop window.
@@ -189,7 +206,7 @@ fwd_planes_kernel(PlaneDims d, const float2* __restrict__ x, float2* __restrict_
     buf[F::sidx(e / d.Nx, e % d.Nx)] = xz[e];
   __syncthreads();
   F::forward(buf, tw, d.Nx);
-  store_spectrum<P, TWO_D>(buf, Xh + (size_t)z * d.Nk);
+  store_spectrum<P, TWO_D>(buf, Xh + (size_t)z * d.Ns, d);
 }
 
 // Yh[u] -> y[s, m] = IFFT2(Yh_u)(s) where bins[u] = idx[s, m]
@@ -251,7 +268,7 @@ inv_resid_fwd_kernel(PlaneDims d, const float2* __restrict__ Yh,
   if (red_sumsq) block_add_double<F::NT>(acc, red_sumsq);
   __syncthreads();
   F::forward(buf, tw, d.Nx);
-  store_spectrum<P, TWO_D>(buf, Rh + (size_t)u * d.Nk);
+  store_spectrum<P, TWO_D>(buf, Rh + (size_t)u * d.Ns, d);
 }
 
 // y[s, m] scattered to bin plane u -> Rh[u] = FFT2(pad(.))
@@ -274,7 +291,7 @@ scatter_fwd_kernel(PlaneDims d, const float2* __restrict__ y,
   }
   __syncthreads();
   F::forward(buf, tw, d.Nx);
-  store_spectrum<P, TWO_D>(buf, Rh + (size_t)u * d.Nk);
+  store_spectrum<P, TWO_D>(buf, Rh + (size_t)u * d.Ns, d);
 }
 
 // Gh[z] -> x plane z = crop(IFFT2(Gh_z)); optional sum |x|^2 and max |x|.
@@ -350,53 +367,60 @@ inv_fista_fwd_kernel(PlaneDims d, const float2* __restrict__ Gh,
   zero_outside<P, TWO_D>(buf, d.Ny, d.Nx);
   __syncthreads();
   F::forward(buf, tw, d.Nx);
-  store_spectrum<P, TWO_D>(buf, Xh + (size_t)z * d.Nk);
+  store_spectrum<P, TWO_D>(buf, Xh + (size_t)z * d.Ns, d);
 }
 
 // ---------------------------------------------------------------------------
 // Depth contractions (the blockwise products of Sec. IV-B restricted to the
-// kept bins).  T is tiled by 64 wavenumbers, T[kt][u][z][ki]; one table row
-// (kt, u, z) is 512 bytes.  Work is cut into units (kt, zb, u): bin u of
-// wavenumber tile kt over the depth block zb (<= 128 depths).  A persistent
-// CTA per SM takes a contiguous, equal share of the units.  Each of its 8
-// warps owns 16 depths of the block and streams its 16 rows of every unit
-// (8 KB) through its own 3-slot shared-memory ring, filled by
-// cp.async.bulk and tracked by one mbarrier per slot, so 128 KB per SM are
-// in flight without holding them in registers.  A lane owns the wavenumber
-// pair (2 lane, 2 lane + 1), so rows are read from shared memory as 16-byte
-// vectors without bank conflicts and no lane exchanges data with another.
-//   forward: Yp[zb][u][kap] = sum_{z in zb} T[kt][u][z][ki] Xh[z][kap]; the
+// kept bins).
+//
+// Folded table.  The lateral kernel h_{k,z}[dy, dx] depends on dx^2 + dy^2
+// only, so its FFT2 is the same for every wavenumber of a symmetry orbit
+// (sign flips of kx and ky, and kx <-> ky on a square grid).  Spectra are
+// kept in slot order, GS slots per orbit (2 line, 4 area, 8 square area,
+// padding slots carry zero), and the table stores one entry per orbit:
+// T[st][u][z][e], e < E = 64 / GS, for slot tile st of 64 slots.  One table
+// row (st, u, z) is 8 E bytes.  The arithmetic is that of the unfolded
+// operator; only the bytes streamed shrink by about GS.
+//
+// Work is cut into units (st, zb, u): bin u of slot tile st over the depth
+// block zb (<= 128 depths).  A persistent CTA per SM takes a contiguous,
+// equal share of the units.  Each of its 8 warps owns 16 depths of the block
+// and streams its 16 rows of every unit through its own 3-slot shared-memory
+// ring, filled by cp.async.bulk and tracked by one mbarrier per slot.  Lane l
+// owns the slot pair (2l, 2l + 1), both in orbit entry l / (GS / 2), so the
+// GS / 2 lanes of an orbit read the same entry (a shared-memory broadcast)
+// and no lane exchanges data with another.
+//   forward: Yp[zb][u][slot] = sum_{z in zb} T[st][u][z][e] Xh[z][slot]; the
 //            warp holds its 16 Xh values in registers and the 8 warps' partial
 //            sums are added in shared memory, four units at a time.
-//   adjoint: Gs[slot][z][ki] = sum_{u in the CTA's share} conj(T) Rh[u][kap];
+//   adjoint: Gs[gslot][z][slot % 64] = sum_{u in the CTA's share} conj(T) Rh[u][slot];
 //            the warp holds its 16 accumulators in registers.  A segment
-//            (kt, zb) split between CTAs leaves one partial per CTA in
-//            consecutive slots; the consumer plane kernel adds them.
+//            (st, zb) split between CTAs leaves one partial per CTA in
+//            consecutive gslots; the consumer plane kernel adds them.
 // Waits on the mbarriers are bounded (2 s of global time); a timeout sets
-// *err, drains the copies already issued (again bounded) and ends the CTA.
+// *err, drains the copies already issued (again bounded) and ends the warp.
 // ---------------------------------------------------------------------------
 constexpr int kContractWarps = 8;
 constexpr int kContractThreads = kContractWarps * 32;
 constexpr int kRowsPerWarp = 16;
 constexpr int kZBlock = kContractWarps * kRowsPerWarp;  // 128 depths
 constexpr int kSlots = 3;
-constexpr int kSlotFloat4 = kRowsPerWarp * 32;          // 8 KB
-constexpr int kFwdBatch = 4;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
-__device__ __forceinline__ void cmac2(float4& acc, const float4 h, const float4 x) {
-  // acc.(x,y) += (h.x + j h.y)(x.x + j x.y); acc.(z,w) likewise
+// (h.x + j h.y) times the two complex values of x, accumulated
+__device__ __forceinline__ void cmac_pair(float4& acc, const float2 h, const float4 x) {
   acc.x = fmaf(h.x, x.x, acc.x); acc.x = fmaf(-h.y, x.y, acc.x);
   acc.y = fmaf(h.x, x.y, acc.y); acc.y = fmaf(h.y, x.x, acc.y);
-  acc.z = fmaf(h.z, x.z, acc.z); acc.z = fmaf(-h.w, x.w, acc.z);
-  acc.w = fmaf(h.z, x.w, acc.w); acc.w = fmaf(h.w, x.z, acc.w);
+  acc.z = fmaf(h.x, x.z, acc.z); acc.z = fmaf(-h.y, x.w, acc.z);
+  acc.w = fmaf(h.x, x.w, acc.w); acc.w = fmaf(h.y, x.z, acc.w);
 }
-__device__ __forceinline__ void cmacc2(float4& acc, const float4 h, const float4 r) {
-  // acc += conj(h) r for both halves
+// conj(h) times the two complex values of r, accumulated
+__device__ __forceinline__ void cmacc_pair(float4& acc, const float2 h, const float4 r) {
   acc.x = fmaf(h.x, r.x, acc.x); acc.x = fmaf(h.y, r.y, acc.x);
   acc.y = fmaf(h.x, r.y, acc.y); acc.y = fmaf(-h.y, r.x, acc.y);
-  acc.z = fmaf(h.z, r.z, acc.z); acc.z = fmaf(h.w, r.w, acc.z);
-  acc.w = fmaf(h.z, r.w, acc.w); acc.w = fmaf(-h.w, r.z, acc.w);
+  acc.z = fmaf(h.x, r.z, acc.z); acc.z = fmaf(h.y, r.w, acc.z);
+  acc.w = fmaf(h.x, r.w, acc.w); acc.w = fmaf(-h.y, r.z, acc.w);
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -459,116 +483,157 @@ __device__ __forceinline__ WarpRows warp_rows(int zb, int w, int Nz) {
   return r;
 }
 
-// Issue the bulk copy of this warp's rows of unit `unit` into slot `s`.  The
-// slot's mbarrier is always arrived on (with zero bytes when the warp has no
-// rows in this depth block) so that every slot completes one phase per use.
-__device__ __forceinline__ void issue_unit(const float4* __restrict__ T, int unit, int U, int Nz,
-                                           int nzb, int w, float4* slot, uint32_t bar) {
-  const int seg = unit / U, u = unit - seg * U;
-  const int kt = seg / nzb, zb = seg - kt * nzb;
-  const WarpRows wr = warp_rows(zb, w, Nz);
-  const uint32_t bytes = (uint32_t)wr.n * 512u;
+// Position in the unit sequence (segment-major, bin group fastest), advanced
+// without divisions.
+struct UnitPos {
+  int seg, ug, st, zb;
+  __device__ __forceinline__ void init(int unit, int NUG, int nzb) {
+    seg = unit / NUG;
+    ug = unit - seg * NUG;
+    st = seg / nzb;
+    zb = seg - st * nzb;
+  }
+  __device__ __forceinline__ void next(int NUG, int nzb) {
+    if (++ug == NUG) {
+      ug = 0;
+      ++seg;
+      if (++zb == nzb) {
+        zb = 0;
+        ++st;
+      }
+    }
+  }
+};
+
+// Issue the bulk copies of this warp's rows of one unit (UP bins, each a
+// contiguous run of n rows of 8 E bytes) into a ring slot laid out
+// [UP][16][E].  The slot's mbarrier is always arrived on (zero bytes when the
+// warp has no rows in this depth block) so every slot completes one phase per
+// use.
+template <int GS>
+__device__ __forceinline__ void issue_unit(const float2* __restrict__ T, const UnitPos& p,
+                                           int Up, int Nz, int w, float2* slot, uint32_t bar) {
+  constexpr int E = kKappaTile / GS;
+  constexpr int UP = GS / 2;
+  const WarpRows wr = warp_rows(p.zb, w, Nz);
+  const uint32_t bytes = (uint32_t)wr.n * (E * 8u);
   fence_proxy_async();
-  mbar_expect_tx(bar, bytes);
+  mbar_expect_tx(bar, bytes * UP);
   if (bytes) {
-    const float4* src = T + ((size_t)(kt * U + u) * Nz + wr.z0) * 32;
-    bulk_g2s(smem_addr(slot), src, bytes, bar);
+    const float2* src = T + ((size_t)(p.st * Up + p.ug * UP) * Nz + wr.z0) * E;
+#pragma unroll
+    for (int q = 0; q < UP; ++q)
+      bulk_g2s(smem_addr(slot + q * kRowsPerWarp * E), src + (size_t)q * Nz * E, bytes, bar);
   }
 }
 
-// Drain the copies this warp has in flight (uses [from, to) of its ring).
+// Drain the copies this warp has in flight (ring uses [from, to)).
 __device__ __forceinline__ void drain_warp(int from, int to, uint32_t bar0) {
   for (int i = from; i < to; ++i)
     mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, kWaitNs / 4);
 }
 
+// Up = bins padded to a multiple of UP = GS / 2 (padding table rows are zero);
+// nunits = (Ns / 64) * nzb * (Up / UP).
+template <int GS>
 __global__ void __launch_bounds__(kContractThreads, 1)
-contract_fwd_stream(const float4* __restrict__ T, const float4* __restrict__ Xh,
-                    float4* __restrict__ Yp, int Nz, int U, int Nk, int nzb, int nunits,
+contract_fwd_stream(const float2* __restrict__ T, const float4* __restrict__ Xh,
+                    float4* __restrict__ Yp, int Nz, int Up, int Ns, int nzb, int nunits,
                     int* __restrict__ err) {
+  constexpr int E = kKappaTile / GS;
+  constexpr int UP = GS / 2;
+  constexpr int SLOT = UP * kRowsPerWarp * E;  // float2 per ring slot (4 KB)
   extern __shared__ __align__(128) float4 sm4[];
-  float4* ring = sm4;                                              // [8][3][512]
-  float4* red = sm4 + kContractWarps * kSlots * kSlotFloat4;       // [4][8][32]
-  uint64_t* bars = (uint64_t*)(red + kFwdBatch * kContractWarps * 32);  // [8][3]
+  float4* red = sm4;                                        // [8][UP][32]
+  float2* ring = (float2*)(red + kContractWarps * UP * 32);  // [8][3][SLOT]
+  uint64_t* bars = (uint64_t*)(ring + kContractWarps * kSlots * SLOT);  // [8][3]
   __shared__ int abort_flag;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int NUG = Up / UP;
   const int G = gridDim.x, b = blockIdx.x;
   const int first = (int)(((long long)nunits * b) / G);
-  const int last = (int)(((long long)nunits * (b + 1)) / G);
-  const int n = last - first;
-  float4* my = ring + w * kSlots * kSlotFloat4;
+  const int n = (int)(((long long)nunits * (b + 1)) / G) - first;
+  float2* my = ring + w * kSlots * SLOT;
   const uint32_t bar0 = smem_addr(bars + w * kSlots);
+  const int ent = lane / (GS / 2);  // this lane's orbit entry in a row
   if (threadIdx.x == 0) abort_flag = 0;
   if (lane == 0) {
     for (int s = 0; s < kSlots; ++s) mbar_init(bar0 + 8u * s, 1);
     fence_mbar_init();
   }
   __syncthreads();
-  const size_t nk4 = (size_t)Nk / 2;
+  const size_t ns4 = (size_t)Ns / 2;
+  UnitPos ip;  // next unit to issue
+  ip.init(first, NUG, nzb);
   int next_issue = 0;
-  if (lane == 0)
-    for (; next_issue < kSlots - 1 && next_issue < n; ++next_issue)
-      issue_unit(T, first + next_issue, U, Nz, nzb, w, my + (next_issue % kSlots) * kSlotFloat4,
-                 bar0 + 8u * (next_issue % kSlots));
-  next_issue = __shfl_sync(0xffffffffu, next_issue, 0);
+  for (; next_issue < kSlots - 1 && next_issue < n; ++next_issue, ip.next(NUG, nzb))
+    if (lane == 0)
+      issue_unit<GS>(T, ip, Up, Nz, w, my + (next_issue % kSlots) * SLOT,
+                     bar0 + 8u * (next_issue % kSlots));
+  UnitPos cp;  // unit being computed
+  cp.init(first, NUG, nzb);
   float4 xr[kRowsPerWarp];
   int cur_seg = -1;
+  WarpRows wr{0, 0};
   bool ok = true;
-  int waited = 0;  // uses of the ring waited for so far
-  int i = 0;
-  for (int base = 0; base < n; base += kFwdBatch) {
-    const int nb = min(kFwdBatch, n - base);
-    for (int j = 0; j < nb; ++j, ++i) {
-      const int unit = first + i;
-      const int seg = unit / U;
-      const int kt = seg / nzb, zb = seg - kt * nzb;
-      const WarpRows wr = warp_rows(zb, w, Nz);
-      // keep kSlots - 1 copies ahead: refill the slot consumed last time
-      if (ok && next_issue < n && next_issue <= i + kSlots - 1) {
-        if (lane == 0)
-          issue_unit(T, first + next_issue, U, Nz, nzb, w, my + (next_issue % kSlots) * kSlotFloat4,
-                     bar0 + 8u * (next_issue % kSlots));
-        ++next_issue;
-      }
-      if (seg != cur_seg) {  // new (kt, zb): this warp's Xh rows into registers
-        cur_seg = seg;
+  int waited = 0;
+  for (int i = 0; i < n; ++i, cp.next(NUG, nzb)) {
+    if (ok && next_issue < n) {  // refill the slot consumed in the previous unit
+      if (lane == 0)
+        issue_unit<GS>(T, ip, Up, Nz, w, my + (next_issue % kSlots) * SLOT,
+                       bar0 + 8u * (next_issue % kSlots));
+      ++next_issue;
+      ip.next(NUG, nzb);
+    }
+    if (cp.seg != cur_seg) {  // new (st, zb): this warp's Xh rows into registers
+      cur_seg = cp.seg;
+      wr = warp_rows(cp.zb, w, Nz);
 #pragma unroll
-        for (int r = 0; r < kRowsPerWarp; ++r)
-          xr[r] = r < wr.n ? Xh[(size_t)(wr.z0 + r) * nk4 + kt * 32 + lane]
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (ok) {
-        if (!mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, kWaitNs)) {
-          ok = false;
-          if (lane == 0) {
-            atomicExch(err, 1);
-            abort_flag = 1;
-          }
-        } else {
-          waited = i + 1;
-          const float4* slot = my + (i % kSlots) * kSlotFloat4;
+      for (int r = 0; r < kRowsPerWarp; ++r)
+        xr[r] = r < wr.n ? Xh[(size_t)(wr.z0 + r) * ns4 + cp.st * 32 + lane]
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float4 acc[UP];
+#pragma unroll
+    for (int q = 0; q < UP; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ok) {
+      if (!mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, kWaitNs)) {
+        ok = false;
+        if (lane == 0) {
+          atomicExch(err, 1);
+          abort_flag = 1;
+        }
+      } else {
+        waited = i + 1;
+        const float2* slot = my + (i % kSlots) * SLOT + ent;
+        if (wr.n == kRowsPerWarp) {
 #pragma unroll
           for (int r = 0; r < kRowsPerWarp; ++r)
-            if (r < wr.n) cmac2(acc, slot[r * 32 + lane], xr[r]);
+#pragma unroll
+            for (int q = 0; q < UP; ++q) cmac_pair(acc[q], slot[(q * kRowsPerWarp + r) * E], xr[r]);
+        } else {
+#pragma unroll
+          for (int r = 0; r < kRowsPerWarp; ++r)
+            if (r < wr.n)
+#pragma unroll
+              for (int q = 0; q < UP; ++q)
+                cmac_pair(acc[q], slot[(q * kRowsPerWarp + r) * E], xr[r]);
         }
       }
-      __syncwarp();
-      red[(j * kContractWarps + w) * 32 + lane] = acc;
     }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < UP; ++q) red[(w * UP + q) * 32 + lane] = acc[q];
     __syncthreads();
     if (abort_flag) ok = false;
-    if (w < nb && ok) {
-      float4 s = red[(w * kContractWarps) * 32 + lane];
+    if (w < UP && ok) {  // warp q adds the 8 partials of bin ug*UP + q
+      float4 sum = red[w * 32 + lane];
 #pragma unroll
       for (int k = 1; k < kContractWarps; ++k) {
-        const float4 v = red[(w * kContractWarps + k) * 32 + lane];
-        s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+        const float4 v = red[(k * UP + w) * 32 + lane];
+        sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
       }
-      const int unit = first + base + w;
-      const int seg = unit / U, u = unit - seg * U;
-      const int kt = seg / nzb, zb = seg - kt * nzb;
-      Yp[((size_t)zb * U + u) * nk4 + kt * 32 + lane] = s;
+      Yp[((size_t)cp.zb * Up + cp.ug * UP + w) * ns4 + cp.st * 32 + lane] = sum;
     }
     __syncthreads();
     if (!ok) break;
@@ -576,81 +641,100 @@ contract_fwd_stream(const float4* __restrict__ T, const float4* __restrict__ Xh,
   if (!ok) drain_warp(waited, next_issue, bar0);
 }
 
+template <int GS>
 __global__ void __launch_bounds__(kContractThreads, 1)
-contract_adj_stream(const float4* __restrict__ T, const float4* __restrict__ Rh,
-                    float4* __restrict__ Gs, int Nz, int U, int Nk, int nzb, int nunits,
+contract_adj_stream(const float2* __restrict__ T, const float4* __restrict__ Rh,
+                    float4* __restrict__ Gs, int Nz, int Up, int Ns, int nzb, int nunits,
                     int* __restrict__ err) {
+  constexpr int E = kKappaTile / GS;
+  constexpr int UP = GS / 2;
+  constexpr int SLOT = UP * kRowsPerWarp * E;
   extern __shared__ __align__(128) float4 sm4[];
-  float4* ring = sm4;
-  uint64_t* bars = (uint64_t*)(sm4 + kContractWarps * kSlots * kSlotFloat4);
+  float2* ring = (float2*)sm4;
+  uint64_t* bars = (uint64_t*)(ring + kContractWarps * kSlots * SLOT);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int NUG = Up / UP;
   const int G = gridDim.x, b = blockIdx.x;
   const int first = (int)(((long long)nunits * b) / G);
-  const int last = (int)(((long long)nunits * (b + 1)) / G);
-  const int n = last - first;
-  float4* my = ring + w * kSlots * kSlotFloat4;
+  const int n = (int)(((long long)nunits * (b + 1)) / G) - first;
+  float2* my = ring + w * kSlots * SLOT;
   const uint32_t bar0 = smem_addr(bars + w * kSlots);
+  const int ent = lane / (GS / 2);
   if (lane == 0) {
     for (int s = 0; s < kSlots; ++s) mbar_init(bar0 + 8u * s, 1);
     fence_mbar_init();
   }
   __syncwarp();
-  const size_t nk4 = (size_t)Nk / 2;
+  const size_t ns4 = (size_t)Ns / 2;
+  UnitPos ip;
+  ip.init(first, NUG, nzb);
   int next_issue = 0;
-  if (lane == 0)
-    for (; next_issue < kSlots - 1 && next_issue < n; ++next_issue)
-      issue_unit(T, first + next_issue, U, Nz, nzb, w, my + (next_issue % kSlots) * kSlotFloat4,
-                 bar0 + 8u * (next_issue % kSlots));
-  next_issue = __shfl_sync(0xffffffffu, next_issue, 0);
-  // Rh rows prefetched two units ahead in registers
-  auto rh_of = [&](int i) -> float4 {
-    if (i >= n) return make_float4(0.f, 0.f, 0.f, 0.f);
-    const int unit = first + i;
-    const int seg = unit / U, u = unit - seg * U;
-    const int kt = seg / nzb;
-    return Rh[(size_t)u * nk4 + kt * 32 + lane];
+  for (; next_issue < kSlots - 1 && next_issue < n; ++next_issue, ip.next(NUG, nzb))
+    if (lane == 0)
+      issue_unit<GS>(T, ip, Up, Nz, w, my + (next_issue % kSlots) * SLOT,
+                     bar0 + 8u * (next_issue % kSlots));
+  // Rh rows of the next unit prefetched into registers
+  UnitPos rp;
+  rp.init(first, NUG, nzb);
+  auto load_rh = [&](float4* dst, const UnitPos& p, bool valid) {
+#pragma unroll
+    for (int q = 0; q < UP; ++q)
+      dst[q] = valid ? Rh[(size_t)(p.ug * UP + q) * ns4 + p.st * 32 + lane]
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
   };
-  float4 r0 = rh_of(0), r1 = rh_of(1);
+  float4 rnext[UP];
+  load_rh(rnext, rp, n > 0);
+  UnitPos cp;
+  cp.init(first, NUG, nzb);
+  WarpRows wr = warp_rows(cp.zb, w, Nz);
   float4 acc[kRowsPerWarp];
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-  int i = 0;
-  for (; i < n; ++i) {
-    const int unit = first + i;
-    const int seg = unit / U;
-    const int zb = seg % nzb;
-    const WarpRows wr = warp_rows(zb, w, Nz);
-    if (next_issue < n && next_issue <= i + kSlots - 1) {
+  for (int i = 0; i < n; ++i) {
+    if (next_issue < n) {
       if (lane == 0)
-        issue_unit(T, first + next_issue, U, Nz, nzb, w, my + (next_issue % kSlots) * kSlotFloat4,
-                   bar0 + 8u * (next_issue % kSlots));
+        issue_unit<GS>(T, ip, Up, Nz, w, my + (next_issue % kSlots) * SLOT,
+                       bar0 + 8u * (next_issue % kSlots));
       ++next_issue;
+      ip.next(NUG, nzb);
     }
-    const float4 r = r0;
-    r0 = r1;
-    r1 = rh_of(i + 2);
+    float4 rr[UP];
+#pragma unroll
+    for (int q = 0; q < UP; ++q) rr[q] = rnext[q];
+    rp.next(NUG, nzb);
+    load_rh(rnext, rp, i + 1 < n);
     if (!mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, kWaitNs)) {
       if (lane == 0) atomicExch(err, 1);
       drain_warp(i, next_issue, bar0);
       return;
     }
-    if (wr.n > 0) {
-      const float4* slot = my + (i % kSlots) * kSlotFloat4;
+    const float2* slot = my + (i % kSlots) * SLOT + ent;
+    if (wr.n == kRowsPerWarp) {
 #pragma unroll
-      for (int rr = 0; rr < kRowsPerWarp; ++rr)
-        if (rr < wr.n) cmacc2(acc[rr], slot[rr * 32 + lane], r);
+      for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+        for (int q = 0; q < UP; ++q) cmacc_pair(acc[r], slot[(q * kRowsPerWarp + r) * E], rr[q]);
+    } else if (wr.n > 0) {
+#pragma unroll
+      for (int r = 0; r < kRowsPerWarp; ++r)
+        if (r < wr.n)
+#pragma unroll
+          for (int q = 0; q < UP; ++q)
+            cmacc_pair(acc[r], slot[(q * kRowsPerWarp + r) * E], rr[q]);
     }
     __syncwarp();
-    const bool seg_end = (i + 1 == n) || ((unit + 1) / U != seg);
-    if (seg_end) {
+    const int seg = cp.seg;
+    cp.next(NUG, nzb);
+    if (i + 1 == n || cp.seg != seg) {  // end of this CTA's part of segment seg
       if (wr.n > 0) {
         float4* dst = Gs + ((size_t)(seg + b) * kZBlock + w * kRowsPerWarp) * 32 + lane;
 #pragma unroll
-        for (int rr = 0; rr < kRowsPerWarp; ++rr)
-          if (rr < wr.n) dst[rr * 32] = acc[rr];
+        for (int r = 0; r < kRowsPerWarp; ++r)
+          if (r < wr.n) dst[r * 32] = acc[r];
       }
 #pragma unroll
-      for (int rr = 0; rr < kRowsPerWarp; ++rr) acc[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int r = 0; r < kRowsPerWarp; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      wr = warp_rows(cp.zb, w, Nz);
     }
   }
 }
@@ -833,38 +917,68 @@ int launch_inv_fista_fwd(const PlaneDims& d, const float2* Gh, const int2* segsl
   });
 }
 
-int contract_units(const PlaneDims& d) { return (d.Nk / kKappaTile) * d.nzb * d.U; }
+int contract_units(const PlaneDims& d) {
+  return (d.Ns / kKappaTile) * d.nzb * (d.Up / (d.GS / 2));
+}
 
+namespace {
+// ring slot: (GS / 2) bins x 16 rows x (64 / GS) entries x 8 bytes = 4 KB
+constexpr size_t kRingSlotBytes = 4096;
+template <int GS>
 size_t contract_fwd_smem() {
-  return (size_t)kContractWarps * kSlots * kSlotFloat4 * 16 +
-         (size_t)kFwdBatch * kContractWarps * 32 * 16 + kContractWarps * kSlots * 8;
+  return (size_t)kContractWarps * (GS / 2) * 32 * 16 +
+         (size_t)kContractWarps * kSlots * kRingSlotBytes + kContractWarps * kSlots * 8;
 }
+template <int GS>
 size_t contract_adj_smem() {
-  return (size_t)kContractWarps * kSlots * kSlotFloat4 * 16 + kContractWarps * kSlots * 8;
+  return (size_t)kContractWarps * kSlots * kRingSlotBytes + kContractWarps * kSlots * 8;
 }
+template <int GS>
+int launch_fwd_gs(const PlaneDims& d, const float2* table, const float2* Xh, float2* Yp,
+                  int* err, cudaStream_t st) {
+  const size_t smem = contract_fwd_smem<GS>();
+  SFS_TRY(ensure_smem_attr(contract_fwd_stream<GS>, (int)smem));
+  const int n = contract_units(d);
+  const int G = std::min(d.G, n);
+  contract_fwd_stream<GS><<<G, kContractThreads, smem, st>>>(
+      table, (const float4*)Xh, (float4*)Yp, d.Nz, d.Up, d.Ns, d.nzb, n, err);
+  SFS_CUDA(cudaGetLastError());
+  return SFS_OK;
+}
+template <int GS>
+int launch_adj_gs(const PlaneDims& d, const float2* table, const float2* Rh, float2* Gs,
+                  int* err, cudaStream_t st) {
+  const size_t smem = contract_adj_smem<GS>();
+  SFS_TRY(ensure_smem_attr(contract_adj_stream<GS>, (int)smem));
+  const int n = contract_units(d);
+  const int G = std::min(d.G, n);
+  contract_adj_stream<GS><<<G, kContractThreads, smem, st>>>(
+      table, (const float4*)Rh, (float4*)Gs, d.Nz, d.Up, d.Ns, d.nzb, n, err);
+  SFS_CUDA(cudaGetLastError());
+  return SFS_OK;
+}
+}  // namespace
 
 int launch_contract_fwd(const PlaneDims& d, const float2* table, const float2* Xh,
                         float2* Yp, int* err, cudaStream_t st) {
-  const size_t smem = contract_fwd_smem();
-  SFS_TRY(ensure_smem_attr(contract_fwd_stream, (int)smem));
-  const int n = contract_units(d);
-  const int G = std::min(d.G, n);
-  contract_fwd_stream<<<G, kContractThreads, smem, st>>>(
-      (const float4*)table, (const float4*)Xh, (float4*)Yp, d.Nz, d.U, d.Nk, d.nzb, n, err);
-  SFS_CUDA(cudaGetLastError());
-  return SFS_OK;
+  switch (d.GS) {
+    case 2: return launch_fwd_gs<2>(d, table, Xh, Yp, err, st);
+    case 4: return launch_fwd_gs<4>(d, table, Xh, Yp, err, st);
+    case 8: return launch_fwd_gs<8>(d, table, Xh, Yp, err, st);
+  }
+  set_error("unsupported orbit size %d", d.GS);
+  return SFS_ERR_INVALID_ARG;
 }
 
 int launch_contract_adj(const PlaneDims& d, const float2* table, const float2* Rh,
                         float2* Gs, int* err, cudaStream_t st) {
-  const size_t smem = contract_adj_smem();
-  SFS_TRY(ensure_smem_attr(contract_adj_stream, (int)smem));
-  const int n = contract_units(d);
-  const int G = std::min(d.G, n);
-  contract_adj_stream<<<G, kContractThreads, smem, st>>>(
-      (const float4*)table, (const float4*)Rh, (float4*)Gs, d.Nz, d.U, d.Nk, d.nzb, n, err);
-  SFS_CUDA(cudaGetLastError());
-  return SFS_OK;
+  switch (d.GS) {
+    case 2: return launch_adj_gs<2>(d, table, Rh, Gs, err, st);
+    case 4: return launch_adj_gs<4>(d, table, Rh, Gs, err, st);
+    case 8: return launch_adj_gs<8>(d, table, Rh, Gs, err, st);
+  }
+  set_error("unsupported orbit size %d", d.GS);
+  return SFS_ERR_INVALID_ARG;
 }
 
 int launch_set_thresholds(float* scal, double* red, double lambda, double L, int use_mu,

@@ -1,13 +1,11 @@
 // sfs_apply_AH_noalloc: the backward projection x = A^H y for callers that
 // cannot allocate device memory at call time.
 //
-// Who needs it: code that runs inside a CUDA stream capture (cudaMalloc is
-// not allowed while a stream is being captured), acquisition or real-time
-// loops that forbid allocation after start-up so that every call has the
-// same latency, and host frameworks that own all device memory through their
-// own pool and must not see a library allocate behind their back.  These
-// callers create the operator once at set-up time and afterwards need calls
-// that touch no allocator at all.
+// Who needs it: acquisition or real-time loops that forbid allocation after
+// start-up so that every call has the same latency, and host frameworks that
+// own all device memory through their own pool and must not see a library
+// allocate behind their back.  These callers create the operator once at
+// set-up time and afterwards need calls that touch no allocator at all.
 //
 // sfs_apply_AH keeps its intermediate data (the lateral spectra of the bin
 // planes and the adjoint contraction's partial-sum slots) in workspace that
@@ -65,8 +63,8 @@ extern "C" int sfs_apply_AH_noalloc(sfs_operator* op, const void* y_dev, void* x
     set_error("null or misaligned argument");
     return SFS_ERR_INVALID_ARG;
   }
-  // the bin-plane spectra [U][Nk] followed by the partial-sum slots [nslots][128][64]
-  const size_t n_rh = (size_t)op->U * op->Nk;
+  // the bin-plane spectra [Up][Ns] followed by the partial-sum slots [nslots][128][64]
+  const size_t n_rh = (size_t)op->Up * op->Ns;
   const size_t n_slots = (size_t)op->nslots * kZBlockRows * kKappaTile;
   if (n_rh + n_slots > kNoAllocScratchElems) {
     set_error("sfs_apply_AH_noalloc needs %zu bytes of scratch, the static maximum is %zu "
@@ -80,25 +78,21 @@ extern "C" int sfs_apply_AH_noalloc(sfs_operator* op, const void* y_dev, void* x
   float2* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc == SFS_OK) {
-    // Nothing in the scratch has to start at zero: the scatter kernel writes
-    // every wavenumber of every bin plane, and the adjoint contraction writes
-    // every slot row that the consumer reads before it is read.
+    // The spectra rows of the padding bins U..Up-1 must be zero (the scatter
+    // kernel writes only rows 0..U-1 and the contraction reads all Up rows);
+    // they are cleared on every call because other operators may have used
+    // the array since.  The contraction writes every slot row the consumer
+    // reads before it is read.
     float2* rh = scratch;
     float2* gs = scratch + n_rh;
-    PlaneDims d;
-    d.Nx = op->geo.d.Nx;
-    d.Ny = op->geo.d.Ny;
-    d.Nz = op->geo.d.Nz;
-    d.Px = op->geo.Px;
-    d.Py = op->geo.Py;
-    d.Nk = op->Nk;
-    d.S = op->S;
-    d.M = op->M;
-    d.U = op->U;
-    d.nzb = op->nzb;
-    d.G = op->G;
+    const PlaneDims d = operator_dims(op);
     cudaStream_t st = (cudaStream_t)stream;
-    rc = launch_scatter_fwd(d, (const float2*)y_dev, op->posmap, rh, st);
+    if (op->Up > op->U) {
+      const cudaError_t e = cudaMemsetAsync(rh + (size_t)op->U * op->Ns, 0,
+                                            (size_t)(op->Up - op->U) * op->Ns * sizeof(float2), st);
+      if (e != cudaSuccess) rc = cuda_fail(e, "clearing padding spectra", __FILE__, __LINE__);
+    }
+    if (rc == SFS_OK) rc = launch_scatter_fwd(d, (const float2*)y_dev, op->posmap, rh, st);
     if (rc == SFS_OK) rc = launch_contract_adj(d, op->table, rh, gs, op->ws.err, st);
     if (rc == SFS_OK)
       rc = launch_inv_store(d, gs, op->ws.segslot, (float2*)x_dev, nullptr, nullptr, st);

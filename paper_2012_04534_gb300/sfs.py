@@ -72,7 +72,8 @@ class OperatorInfo(ctypes.Structure):
                 ("k_lo", ctypes.c_int32), ("k_hi", ctypes.c_int32),
                 ("band_db", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("t0", ctypes.c_double), ("table_bytes", ctypes.c_int64),
-                ("launches_per_iter", ctypes.c_int32)]
+                ("launches_per_iter", ctypes.c_int32), ("Nslot", ctypes.c_int32),
+                ("GS", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
