@@ -530,7 +530,7 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
   }
   const int nseg = (op->Ns / kKappaTile) * op->nzb;
   const int ngroups = op->Up / (op->GS / 2);
-  op->G = std::max(1, std::min(sms, nseg * ngroups));
+  op->G = std::max(1, std::min(sms * kContractCtasPerSm, nseg * ngroups));
   op->nslots = nseg + op->G - 1;
   const std::vector<int2> segslot = segment_slots(nseg, ngroups, op->G);
   const size_t Ns = op->Ns;

@@ -175,7 +175,7 @@ __device__ __forceinline__ void transpose_plane(float2* buf) {
 template <int P, bool TWO_D>
 struct PlaneFFT {
   static constexpr int LD = TWO_D ? P + 1 : P;
-  static constexpr int NT = TWO_D ? (P >= 128 ? 512 : 256) : (P >= 512 ? 256 : (P >= 128 ? 128 : 64));
+  static constexpr int NT = TWO_D ? (P >= 64 ? 512 : 256) : (P >= 512 ? 256 : (P >= 128 ? 128 : 64));
   static constexpr int ELEMS = TWO_D ? P * LD : P;   // float2 slots of the plane
   static constexpr int SMEM = (ELEMS + P) * 8;       // plane + twiddles
 

@@ -119,6 +119,9 @@ struct PlaneDims {
   const int32_t* orbit_rep;   // [Ns / GS] representative wavenumber, -1 for padding
 };
 
+// Resident contraction CTAs per SM (8 warps each); the persistent grid is
+// this times the SM count.
+constexpr int kContractCtasPerSm = 2;
 // Depth block of the contractions and the partial-sum slots of the adjoint.
 constexpr int kZBlockRows = 128;
 // Units of contraction work: (slot tile, depth block, bin).

@@ -131,20 +131,37 @@ __device__ __forceinline__ void zero_plane(float2* buf) {
 // wavenumber slot_kappa[j] (orbit-major, GS slots per symmetry orbit, -1 for
 // padding slots, which carry zero).
 
+// The slot loops below run kLoadBatch slots per thread per round and issue
+// all independent global loads of a round before using any of them, so that
+// several L2 round trips overlap instead of queueing one after another.
+constexpr int kLoadBatch = 4;
+
 // Spectrum of bin plane u from the forward contraction: the sum of its nzb
-// depth-block partials Yp[zb][u][slot] (plane stride U * Ns).
+// depth-block partials Yp[zb][u][slot] (plane stride Up * Ns).
 template <int P, bool TWO_D>
 __device__ __forceinline__ void load_spectrum_fwd(float2* buf, const float2* __restrict__ Yp,
                                                   int u, const PlaneDims& d) {
   using F = PlaneFFT<P, TWO_D>;
   const float2* src = Yp + (size_t)u * d.Ns;
   const size_t stride = (size_t)d.Up * d.Ns;
-  for (int j = threadIdx.x; j < d.Ns; j += F::NT) {
-    const int kap = d.slot_kappa[j];
-    if (kap < 0) continue;
-    float2 v = src[j];
-    for (int zb = 1; zb < d.nzb; ++zb) v = cadd(v, src[zb * stride + j]);
-    buf[F::kidx(kap)] = v;
+  for (int j0 = threadIdx.x; j0 < d.Ns; j0 += kLoadBatch * F::NT) {
+    int kap[kLoadBatch];
+    float2 v[kLoadBatch];
+#pragma unroll
+    for (int k = 0; k < kLoadBatch; ++k) {
+      const int j = j0 + k * F::NT;
+      kap[k] = j < d.Ns ? __ldg(d.slot_kappa + j) : -1;
+      v[k] = j < d.Ns ? src[j] : make_float2(0.f, 0.f);
+    }
+    for (int zb = 1; zb < d.nzb; ++zb)
+#pragma unroll
+      for (int k = 0; k < kLoadBatch; ++k) {
+        const int j = j0 + k * F::NT;
+        if (j < d.Ns) v[k] = cadd(v[k], src[zb * stride + j]);
+      }
+#pragma unroll
+    for (int k = 0; k < kLoadBatch; ++k)
+      if (kap[k] >= 0) buf[F::kidx(kap[k])] = v[k];
   }
 }
 
@@ -157,14 +174,34 @@ __device__ __forceinline__ void load_spectrum_adj(float2* buf, const float2* __r
                                                   const PlaneDims& d) {
   using F = PlaneFFT<P, TWO_D>;
   const int zb = z / 128, zr = z % 128;
-  for (int j = threadIdx.x; j < d.Ns; j += F::NT) {
-    const int kap = d.slot_kappa[j];
-    if (kap < 0) continue;
-    const int2 sc = segslot[(j >> 6) * d.nzb + zb];
-    const float2* src = Gs + ((size_t)sc.x * 128 + zr) * 64 + (j & 63);
-    float2 v = src[0];
-    for (int k = 1; k < sc.y; ++k) v = cadd(v, src[(size_t)k * 128 * 64]);
-    buf[F::kidx(kap)] = v;
+  for (int j0 = threadIdx.x; j0 < d.Ns; j0 += kLoadBatch * F::NT) {
+    int kap[kLoadBatch];
+    int2 sc[kLoadBatch];
+#pragma unroll
+    for (int k = 0; k < kLoadBatch; ++k) {
+      const int j = j0 + k * F::NT;
+      kap[k] = j < d.Ns ? __ldg(d.slot_kappa + j) : -1;
+      sc[k] = j < d.Ns ? __ldg(segslot + (j >> 6) * d.nzb + zb) : make_int2(0, 0);
+    }
+    float2 v[kLoadBatch];
+#pragma unroll
+    for (int k = 0; k < kLoadBatch; ++k) {
+      const int j = j0 + k * F::NT;
+      v[k] = sc[k].y > 0 ? Gs[((size_t)sc[k].x * 128 + zr) * 64 + (j & 63)] : make_float2(0.f, 0.f);
+    }
+    int more = 0;
+#pragma unroll
+    for (int k = 0; k < kLoadBatch; ++k) more = max(more, sc[k].y);
+    for (int c = 1; c < more; ++c)
+#pragma unroll
+      for (int k = 0; k < kLoadBatch; ++k) {
+        const int j = j0 + k * F::NT;
+        if (c < sc[k].y)
+          v[k] = cadd(v[k], Gs[((size_t)(sc[k].x + c) * 128 + zr) * 64 + (j & 63)]);
+      }
+#pragma unroll
+    for (int k = 0; k < kLoadBatch; ++k)
+      if (kap[k] >= 0) buf[F::kidx(kap[k])] = v[k];
   }
 }
 
@@ -172,9 +209,18 @@ template <int P, bool TWO_D>
 __device__ __forceinline__ void store_spectrum(const float2* buf, float2* __restrict__ dst,
                                                const PlaneDims& d) {
   using F = PlaneFFT<P, TWO_D>;
-  for (int j = threadIdx.x; j < d.Ns; j += F::NT) {
-    const int kap = d.slot_kappa[j];
-    dst[j] = kap >= 0 ? buf[F::kidx(kap)] : make_float2(0.f, 0.f);
+  for (int j0 = threadIdx.x; j0 < d.Ns; j0 += kLoadBatch * F::NT) {
+    int kap[kLoadBatch];
+#pragma unroll
+    for (int k = 0; k < kLoadBatch; ++k) {
+      const int j = j0 + k * F::NT;
+      kap[k] = j < d.Ns ? __ldg(d.slot_kappa + j) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kLoadBatch; ++k) {
+      const int j = j0 + k * F::NT;
+      if (j < d.Ns) dst[j] = kap[k] >= 0 ? buf[F::kidx(kap[k])] : make_float2(0.f, 0.f);
+    }
   }
 }
 
@@ -536,7 +582,7 @@ __device__ __forceinline__ void drain_warp(int from, int to, uint32_t bar0) {
 // Up = bins padded to a multiple of UP = GS / 2 (padding table rows are zero);
 // nunits = (Ns / 64) * nzb * (Up / UP).
 template <int GS>
-__global__ void __launch_bounds__(kContractThreads, 1)
+__global__ void __launch_bounds__(kContractThreads, kContractCtasPerSm)
 contract_fwd_stream(const float2* __restrict__ T, const float4* __restrict__ Xh,
                     float4* __restrict__ Yp, int Nz, int Up, int Ns, int nzb, int nunits,
                     int* __restrict__ err) {
@@ -642,7 +688,7 @@ contract_fwd_stream(const float2* __restrict__ T, const float4* __restrict__ Xh,
 }
 
 template <int GS>
-__global__ void __launch_bounds__(kContractThreads, 1)
+__global__ void __launch_bounds__(kContractThreads, kContractCtasPerSm)
 contract_adj_stream(const float2* __restrict__ T, const float4* __restrict__ Rh,
                     float4* __restrict__ Gs, int Nz, int Up, int Ns, int nzb, int nunits,
                     int* __restrict__ err) {
