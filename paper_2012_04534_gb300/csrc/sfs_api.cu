@@ -198,6 +198,8 @@ void free_operator(sfs_operator* op) {
   cudaFree(op->ws.red);
   cudaFree(op->ws.obj);
   for (cudaEvent_t e : op->ev) cudaEventDestroy(e);
+  for (auto& ge : op->graphs) cudaGraphExecDestroy(ge.exec);
+  if (op->capture_stream) cudaStreamDestroy(op->capture_stream);
   delete op;
 }
 
@@ -219,6 +221,10 @@ PlaneDims operator_dims(const sfs_operator* op) {
   d.Ns = op->Ns;
   d.GS = op->GS;
   d.Up = op->Up;
+  d.adj_seg = op->adj_seg;
+  d.azb = op->azb;
+  d.anzb = op->anzb;
+  d.Ga = op->Ga;
   d.slot_kappa = op->slot_kappa;
   d.orbit_rep = op->orbit_rep;
   return d;
@@ -251,6 +257,15 @@ int enqueue_AH(sfs_operator* op, const float2* y, float2* x, double* red_sumsq,
 
 int ensure_obj(sfs_operator* op, int iters) {
   if (op->ws.obj_cap >= iters) return SFS_OK;
+  // graphs that recorded the old monitor buffer become invalid
+  for (auto it = op->graphs.begin(); it != op->graphs.end();) {
+    if (it->with_obj) {
+      cudaGraphExecDestroy(it->exec);
+      it = op->graphs.erase(it);
+    } else {
+      ++it;
+    }
+  }
   cudaFree(op->ws.obj);
   op->ws.obj = nullptr;
   op->ws.obj_cap = 0;
@@ -265,6 +280,69 @@ int ensure_events(sfs_operator* op, int n) {
     SFS_CUDA(cudaEventCreate(&e));
     op->ev.push_back(e);
   }
+  return SFS_OK;
+}
+
+// The FISTA iteration loop (Algorithm 1): X^ of gamma_1, then per iteration
+// forward contraction, residual planes (with the adjoint scatter and FFT),
+// adjoint contraction, and the update planes that also transform
+// gamma_{k+1}.  beta_k = (t_k - 1)/t_{k+1} is fixed by k, so the loop can be
+// captured once and replayed.
+int enqueue_fista_iterations(sfs_operator* op, int iters, double* obj, bool timing,
+                             cudaStream_t st) {
+  const PlaneDims d = dims_of(op);
+  std::vector<float> beta(iters);
+  double t = 1.0;
+  for (int k = 0; k < iters; ++k) {
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    beta[k] = (float)((t - 1.0) / tn);
+    t = tn;
+  }
+  SFS_TRY(launch_fwd_planes(d, op->ws.gam, op->ws.Xh, st));
+  for (int k = 0; k < iters; ++k) {
+    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 0], st));
+    SFS_TRY(launch_contract_fwd(d, op->table, op->ws.Xh, op->ws.Yh, op->ws.err, st));
+    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 1], st));
+    SFS_TRY(launch_inv_resid_fwd(d, op->ws.Yh, op->posmap, op->ws.ybuf, op->ws.Rh,
+                                 obj ? obj + 2 * k : nullptr, st));
+    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 2], st));
+    SFS_TRY(launch_contract_adj(d, op->table, op->ws.Rh, op->ws.Gh, op->ws.err, st));
+    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 3], st));
+    SFS_TRY(launch_inv_fista_fwd(d, op->ws.Gh, op->ws.segslot, op->ws.xk, op->ws.gam,
+                                 op->ws.scal, beta[k], k + 1 < iters, op->ws.Xh,
+                                 obj ? obj + 2 * k + 1 : nullptr, st));
+  }
+  return SFS_OK;
+}
+
+// Executable graph of the iteration loop for (iters, monitor), captured on
+// the operator's own stream the first time it is needed.  All pointers it
+// bakes in are operator-owned, so it stays valid for the operator's life.
+int fista_graph(sfs_operator* op, int iters, bool with_obj, cudaGraphExec_t* out) {
+  for (auto& ge : op->graphs)
+    if (ge.iters == iters && ge.with_obj == with_obj) {
+      *out = ge.exec;
+      return SFS_OK;
+    }
+  if (!op->capture_stream)
+    SFS_CUDA(cudaStreamCreateWithFlags(&op->capture_stream, cudaStreamNonBlocking));
+  SFS_TRY(prepare_kernels(dims_of(op)));  // function attributes are set outside the capture
+  cudaStream_t cs = op->capture_stream;
+  SFS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_fista_iterations(op, iters, with_obj ? op->ws.obj : nullptr, false, cs);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  if (rc != SFS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t e2 = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaGraphInstantiate", __FILE__, __LINE__);
+  op->graphs.push_back({iters, with_obj, exec});
+  *out = exec;
   return SFS_OK;
 }
 
@@ -531,8 +609,29 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
   const int nseg = (op->Ns / kKappaTile) * op->nzb;
   const int ngroups = op->Up / (op->GS / 2);
   op->G = std::max(1, std::min(sms * kContractCtasPerSm, nseg * ngroups));
-  op->nslots = nseg + op->G - 1;
-  const std::vector<int2> segslot = segment_slots(nseg, ngroups, op->G);
+  // Adjoint: one CTA per (slot tile, 32-depth block) when those segments fit
+  // the resident grid and the tile's spectra fit beside the ring (dense
+  // result); otherwise CTAs share segments and leave partial sums.
+  const int anzb32 = (d.Nz + 31) / 32;
+  const int nseg32 = (op->Ns / kKappaTile) * anzb32;
+  std::vector<int2> segslot;
+  if (nseg32 <= sms * kContractCtasPerSm &&
+      adj_seg_smem_bytes(op->Up) * kContractCtasPerSm + 2048 <= (size_t)max_smem_optin() + 1024) {
+    op->adj_seg = 1;
+    op->azb = 32;
+    op->anzb = anzb32;
+    op->Ga = nseg32;
+    op->nslots = nseg32;
+    segslot.resize(nseg32);
+    for (int sgi = 0; sgi < nseg32; ++sgi) segslot[sgi] = make_int2(sgi, 1);
+  } else {
+    op->adj_seg = 0;
+    op->azb = kZBlockRows;
+    op->anzb = op->nzb;
+    op->Ga = 0;
+    op->nslots = nseg + op->G - 1;
+    segslot = segment_slots(nseg, ngroups, op->G);
+  }
   const size_t Ns = op->Ns;
   const size_t table_elems = Ns / op->GS * op->Up * d.Nz;
   if ((rc = dev_alloc(&op->table, table_elems)) != SFS_OK) return fail(rc);
@@ -540,7 +639,7 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
   if ((rc = dev_alloc(&op->ws.Xh, Ns * d.Nz)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->slot_kappa, slot_kappa.size())) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->orbit_rep, orbit_rep.size())) != SFS_OK) return fail(rc);
-  if ((rc = dev_alloc(&op->ws.Gh, (size_t)op->nslots * kZBlockRows * kKappaTile)) != SFS_OK)
+  if ((rc = dev_alloc(&op->ws.Gh, (size_t)op->nslots * op->azb * kKappaTile)) != SFS_OK)
     return fail(rc);
   if ((rc = dev_alloc(&op->ws.segslot, segslot.size())) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.err, 1)) != SFS_OK) return fail(rc);
@@ -778,7 +877,6 @@ int sfs_fista(sfs_operator* op, const void* y_dev, double lambda, double L, int 
   }
   DeviceScope scope(op->geo.d.device);
   cudaStream_t st = (cudaStream_t)stream;
-  const PlaneDims d = dims_of(op);
   const size_t vbytes = (size_t)op->V * sizeof(float2);
   float2* y = op->ws.ybuf;
   SFS_CUDA(cudaMemcpyAsync(y, y_dev, (size_t)op->S * op->M * sizeof(float2),
@@ -810,28 +908,15 @@ int sfs_fista(sfs_operator* op, const void* y_dev, double lambda, double L, int 
     SFS_TRY(ensure_events(op, 4 * iters));
     op->ev_used = 0;
   }
-  std::vector<float> beta(iters);
-  {
-    double t = 1.0;
-    for (int k = 0; k < iters; ++k) {
-      const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-      beta[k] = (float)((t - 1.0) / tn);
-      t = tn;
+  if (iters > 0) {
+    if (timing) {
+      // direct launches with events around the two contractions
+      SFS_TRY(enqueue_fista_iterations(op, iters, obj, true, st));
+    } else {
+      cudaGraphExec_t exec = nullptr;
+      SFS_TRY(fista_graph(op, iters, obj != nullptr, &exec));
+      SFS_CUDA(cudaGraphLaunch(exec, st));
     }
-  }
-  if (iters > 0) SFS_TRY(launch_fwd_planes(d, op->ws.gam, op->ws.Xh, st));
-  for (int k = 0; k < iters; ++k) {
-    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 0], st));
-    SFS_TRY(launch_contract_fwd(d, op->table, op->ws.Xh, op->ws.Yh, op->ws.err, st));
-    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 1], st));
-    SFS_TRY(launch_inv_resid_fwd(d, op->ws.Yh, op->posmap, y, op->ws.Rh,
-                                 obj ? obj + 2 * k : nullptr, st));
-    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 2], st));
-    SFS_TRY(launch_contract_adj(d, op->table, op->ws.Rh, op->ws.Gh, op->ws.err, st));
-    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 3], st));
-    SFS_TRY(launch_inv_fista_fwd(d, op->ws.Gh, op->ws.segslot, op->ws.xk, op->ws.gam,
-                                 op->ws.scal, beta[k],
-                                 k + 1 < iters, op->ws.Xh, obj ? obj + 2 * k + 1 : nullptr, st));
   }
   if (timing) op->ev_used = iters;
   SFS_CUDA(cudaMemcpyAsync(x_inout_dev, op->ws.xk, vbytes, cudaMemcpyDeviceToDevice, st));

@@ -88,6 +88,7 @@ struct sfs_operator {
   int nzb = 1;                 // depth blocks of <= 128 in the contractions
   int G = 1;                   // persistent CTAs of the contractions
   int nslots = 0;              // adjoint partial-sum slots
+  int adj_seg = 0, azb = 128, anzb = 1, Ga = 0;  // adjoint layout (see PlaneDims)
   int k_lo = 0, k_hi = 0;
   double band_db = 0.0;
   std::vector<int32_t> idx;    // [S][M]
@@ -102,6 +103,15 @@ struct sfs_operator {
   // kernel timing (SFS_FISTA_TIME_KERNELS)
   std::vector<cudaEvent_t> ev;
   int ev_used = 0;
+  // FISTA iteration loops captured as CUDA graphs, keyed by (iterations,
+  // objective monitor on/off); replayed on the caller's stream
+  struct GraphEntry {
+    int iters;
+    bool with_obj;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t capture_stream = nullptr;
 };
 
 namespace sfs {
@@ -115,6 +125,10 @@ struct PlaneDims {
   int Ns;   // wavenumber slots (orbit-major, a multiple of 64)
   int GS;   // slots per symmetry orbit: 2 (line), 4 (area), 8 (square area)
   int Up;   // bins padded to a multiple of GS / 2 (zero table rows and spectra)
+  int adj_seg;  // adjoint by segment-aligned CTAs (dense result) instead of partial sums
+  int azb;      // depth rows per adjoint segment (32 segment-aligned, 128 otherwise)
+  int anzb;     // adjoint depth blocks per slot tile
+  int Ga;       // CTAs of the segment-aligned adjoint (= its segment count)
   const int32_t* slot_kappa;  // [Ns] wavenumber of each slot, -1 for padding
   const int32_t* orbit_rep;   // [Ns / GS] representative wavenumber, -1 for padding
 };
@@ -168,6 +182,13 @@ int launch_set_thresholds(float* scal, double* red, double lambda, double L,
 int launch_randn(float2* v, int n, uint64_t seed, cudaStream_t st);
 int launch_sumsq(const float2* v, int n, double* out, cudaStream_t st);
 int launch_scale_by_rnorm(float2* v, int n, const double* sumsq, cudaStream_t st);
+
+// Sets the shared-memory attributes of every kernel an operator of shape d
+// launches (needed once per device before a stream capture).
+int prepare_kernels(const PlaneDims& d);
+
+// Shared memory of the segment-aligned adjoint for Up bins (bytes).
+size_t adj_seg_smem_bytes(int Up);
 
 // Opt-in shared memory limit of the current device (bytes).
 int max_smem_optin();

@@ -167,13 +167,14 @@ __device__ __forceinline__ void load_spectrum_fwd(float2* buf, const float2* __r
 
 // Spectrum of voxel plane z from the adjoint contraction: for each slot tile,
 // the sum of the partial results its segment (tile, depth block) left in
-// consecutive slots of Gs[slot][128][64]; segslot[seg] = {first, count}.
+// consecutive slots of Gs[slot][azb][64]; segslot[seg] = {first, count}.
 template <int P, bool TWO_D>
 __device__ __forceinline__ void load_spectrum_adj(float2* buf, const float2* __restrict__ Gs,
                                                   const int2* __restrict__ segslot, int z,
                                                   const PlaneDims& d) {
   using F = PlaneFFT<P, TWO_D>;
-  const int zb = z / 128, zr = z % 128;
+  const int zb = z / d.azb, zr = z % d.azb;
+  const size_t slot_stride = (size_t)d.azb * 64;
   for (int j0 = threadIdx.x; j0 < d.Ns; j0 += kLoadBatch * F::NT) {
     int kap[kLoadBatch];
     int2 sc[kLoadBatch];
@@ -181,13 +182,14 @@ __device__ __forceinline__ void load_spectrum_adj(float2* buf, const float2* __r
     for (int k = 0; k < kLoadBatch; ++k) {
       const int j = j0 + k * F::NT;
       kap[k] = j < d.Ns ? __ldg(d.slot_kappa + j) : -1;
-      sc[k] = j < d.Ns ? __ldg(segslot + (j >> 6) * d.nzb + zb) : make_int2(0, 0);
+      sc[k] = j < d.Ns ? __ldg(segslot + (j >> 6) * d.anzb + zb) : make_int2(0, 0);
     }
     float2 v[kLoadBatch];
 #pragma unroll
     for (int k = 0; k < kLoadBatch; ++k) {
       const int j = j0 + k * F::NT;
-      v[k] = sc[k].y > 0 ? Gs[((size_t)sc[k].x * 128 + zr) * 64 + (j & 63)] : make_float2(0.f, 0.f);
+      v[k] = sc[k].y > 0 ? Gs[(size_t)sc[k].x * slot_stride + (size_t)zr * 64 + (j & 63)]
+                         : make_float2(0.f, 0.f);
     }
     int more = 0;
 #pragma unroll
@@ -197,7 +199,7 @@ __device__ __forceinline__ void load_spectrum_adj(float2* buf, const float2* __r
       for (int k = 0; k < kLoadBatch; ++k) {
         const int j = j0 + k * F::NT;
         if (c < sc[k].y)
-          v[k] = cadd(v[k], Gs[((size_t)(sc[k].x + c) * 128 + zr) * 64 + (j & 63)]);
+          v[k] = cadd(v[k], Gs[(size_t)(sc[k].x + c) * slot_stride + (size_t)zr * 64 + (j & 63)]);
       }
 #pragma unroll
     for (int k = 0; k < kLoadBatch; ++k)
@@ -785,6 +787,101 @@ contract_adj_stream(const float2* __restrict__ T, const float4* __restrict__ Rh,
   }
 }
 
+// Segment-aligned adjoint: one CTA per segment (slot tile st, 32-depth block
+// zb), all bins, so each output value is summed by exactly one warp and the
+// result is dense (Gs[seg][32][64] = Ghat[z][slot] in tile order): no partial
+// sums.  Chosen when the number of such segments fits the resident grid.
+// Warp w owns depths zb*32 + 4w .. +3.  The slot tile's residual spectra
+// Rh[.][st] for all bins are staged once in shared memory; the table streams
+// through a 2-slot ring per warp, each slot holding 2 GS bins x 4 rows
+// (4 KB), filled by cp.async.bulk (one copy per bin, issued by one lane per
+// bin) and tracked by one mbarrier per slot.
+constexpr int kSegRows = 4;    // depths per warp
+constexpr int kSegSlots = 2;   // ring slots per warp
+template <int GS>
+__global__ void __launch_bounds__(kContractThreads, kContractCtasPerSm)
+contract_adj_seg(const float2* __restrict__ T, const float4* __restrict__ Rh,
+                 float4* __restrict__ Gs, int Nz, int Up, int Ns, int anzb,
+                 int* __restrict__ err) {
+  constexpr int E = kKappaTile / GS;
+  constexpr int UPA = 2 * GS;                   // bins per ring slot
+  constexpr int SLOT = UPA * kSegRows * E;      // float2 per slot (4 KB)
+  extern __shared__ __align__(128) float4 sm4[];
+  float4* rtile = sm4;                                          // [Up][32]
+  float2* ring = (float2*)(rtile + (size_t)Up * 32);            // [8][2][SLOT]
+  uint64_t* bars = (uint64_t*)(ring + kContractWarps * kSegSlots * SLOT);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int seg = blockIdx.x;
+  const int st = seg / anzb, zb = seg - st * anzb;
+  const size_t ns4 = (size_t)Ns / 2;
+  for (int i = threadIdx.x; i < Up * 32; i += kContractThreads)
+    rtile[i] = Rh[(size_t)(i >> 5) * ns4 + st * 32 + (i & 31)];
+  float2* my = ring + w * kSegSlots * SLOT;
+  const uint32_t bar0 = smem_addr(bars + w * kSegSlots);
+  if (lane == 0) {
+    for (int k = 0; k < kSegSlots; ++k) mbar_init(bar0 + 8u * k, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int z0 = zb * (kContractWarps * kSegRows) + w * kSegRows;
+  const int n = min(kSegRows, max(0, Nz - z0));
+  const int ent = lane / (GS / 2);
+  const int nch = (Up + UPA - 1) / UPA;
+  const uint32_t bin_bytes = (uint32_t)n * E * 8u;
+  auto issue = [&](int c) {
+    const int nb = min(UPA, Up - c * UPA);
+    float2* slot = my + (c % kSegSlots) * SLOT;
+    const uint32_t bar = bar0 + 8u * (c % kSegSlots);
+    if (lane == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(bar, bin_bytes * nb);
+    }
+    __syncwarp();
+    if (bin_bytes && lane < nb) {
+      const float2* src = T + ((size_t)(st * Up + c * UPA + lane) * Nz + z0) * E;
+      bulk_g2s(smem_addr(slot + lane * kSegRows * E), src, bin_bytes, bar);
+    }
+  };
+  for (int c = 0; c < kSegSlots - 1 && c < nch; ++c) issue(c);
+  float4 acc[kSegRows];
+#pragma unroll
+  for (int r = 0; r < kSegRows; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int c = 0; c < nch; ++c) {
+    if (c + kSegSlots - 1 < nch) issue(c + kSegSlots - 1);
+    if (!mbar_wait_bounded(bar0 + 8u * (c % kSegSlots), (c / kSegSlots) & 1, kWaitNs)) {
+      if (lane == 0) atomicExch(err, 1);
+      for (int k = c; k < min(nch, c + kSegSlots); ++k)  // drain what was issued
+        mbar_wait_bounded(bar0 + 8u * (k % kSegSlots), (k / kSegSlots) & 1, kWaitNs / 4);
+      return;
+    }
+    const float2* slot = my + (c % kSegSlots) * SLOT + ent;
+    const int nb = min(UPA, Up - c * UPA);
+    if (n == kSegRows) {
+#pragma unroll
+      for (int q = 0; q < UPA; ++q)
+        if (q < nb) {
+          const float4 rr = rtile[(c * UPA + q) * 32 + lane];
+#pragma unroll
+          for (int r = 0; r < kSegRows; ++r) cmacc_pair(acc[r], slot[(q * kSegRows + r) * E], rr);
+        }
+    } else {
+#pragma unroll
+      for (int q = 0; q < UPA; ++q)
+        if (q < nb) {
+          const float4 rr = rtile[(c * UPA + q) * 32 + lane];
+#pragma unroll
+          for (int r = 0; r < kSegRows; ++r)
+            if (r < n) cmacc_pair(acc[r], slot[(q * kSegRows + r) * E], rr);
+        }
+    }
+    __syncwarp();
+  }
+  float4* dst = Gs + ((size_t)seg * (kContractWarps * kSegRows) + w * kSegRows) * 32 + lane;
+#pragma unroll
+  for (int r = 0; r < kSegRows; ++r)
+    if (r < n) dst[r * 32] = acc[r];
+}
+
 // ---------------------------------------------------------------------------
 // Small kernels
 // ---------------------------------------------------------------------------
@@ -1016,12 +1113,71 @@ int launch_contract_fwd(const PlaneDims& d, const float2* table, const float2* X
   return SFS_ERR_INVALID_ARG;
 }
 
+template <int GS>
+size_t contract_adj_seg_smem(int Up) {
+  return (size_t)Up * 32 * 16 + (size_t)kContractWarps * kSegSlots * kRingSlotBytes +
+         kContractWarps * kSegSlots * 8;
+}
+template <int GS>
+int launch_adj_seg_gs(const PlaneDims& d, const float2* table, const float2* Rh, float2* Gs,
+                      int* err, cudaStream_t st) {
+  const size_t smem = contract_adj_seg_smem<GS>(d.Up);
+  SFS_TRY(ensure_smem_attr(contract_adj_seg<GS>, (int)smem));
+  contract_adj_seg<GS><<<d.Ga, kContractThreads, smem, st>>>(
+      table, (const float4*)Rh, (float4*)Gs, d.Nz, d.Up, d.Ns, d.anzb, err);
+  SFS_CUDA(cudaGetLastError());
+  return SFS_OK;
+}
+
+size_t adj_seg_smem_bytes(int Up) { return contract_adj_seg_smem<8>(Up); }
+
 int launch_contract_adj(const PlaneDims& d, const float2* table, const float2* Rh,
                         float2* Gs, int* err, cudaStream_t st) {
+  if (d.adj_seg) {
+    switch (d.GS) {
+      case 2: return launch_adj_seg_gs<2>(d, table, Rh, Gs, err, st);
+      case 4: return launch_adj_seg_gs<4>(d, table, Rh, Gs, err, st);
+      case 8: return launch_adj_seg_gs<8>(d, table, Rh, Gs, err, st);
+    }
+  }
   switch (d.GS) {
     case 2: return launch_adj_gs<2>(d, table, Rh, Gs, err, st);
     case 4: return launch_adj_gs<4>(d, table, Rh, Gs, err, st);
     case 8: return launch_adj_gs<8>(d, table, Rh, Gs, err, st);
+  }
+  set_error("unsupported orbit size %d", d.GS);
+  return SFS_ERR_INVALID_ARG;
+}
+
+int prepare_kernels(const PlaneDims& d) {
+  SFS_TRY(dispatch_plane(d, [&]<int P, bool TD>() -> int {
+    constexpr int sm = PlaneFFT<P, TD>::SMEM;
+    SFS_TRY(ensure_smem_attr(build_table_kernel<P, TD>, sm));
+    SFS_TRY(ensure_smem_attr(fwd_planes_kernel<P, TD>, sm));
+    SFS_TRY(ensure_smem_attr(inv_gather_kernel<P, TD>, sm));
+    SFS_TRY(ensure_smem_attr(inv_resid_fwd_kernel<P, TD>, sm));
+    SFS_TRY(ensure_smem_attr(scatter_fwd_kernel<P, TD>, sm));
+    SFS_TRY(ensure_smem_attr(inv_store_kernel<P, TD>, sm));
+    SFS_TRY(ensure_smem_attr(inv_fista_fwd_kernel<P, TD>, sm));
+    return SFS_OK;
+  }));
+  if (d.adj_seg) {
+    switch (d.GS) {
+      case 2: SFS_TRY(ensure_smem_attr(contract_adj_seg<2>, (int)contract_adj_seg_smem<2>(d.Up))); break;
+      case 4: SFS_TRY(ensure_smem_attr(contract_adj_seg<4>, (int)contract_adj_seg_smem<4>(d.Up))); break;
+      case 8: SFS_TRY(ensure_smem_attr(contract_adj_seg<8>, (int)contract_adj_seg_smem<8>(d.Up))); break;
+    }
+  }
+  switch (d.GS) {
+    case 2:
+      SFS_TRY(ensure_smem_attr(contract_fwd_stream<2>, (int)contract_fwd_smem<2>()));
+      return ensure_smem_attr(contract_adj_stream<2>, (int)contract_adj_smem<2>());
+    case 4:
+      SFS_TRY(ensure_smem_attr(contract_fwd_stream<4>, (int)contract_fwd_smem<4>()));
+      return ensure_smem_attr(contract_adj_stream<4>, (int)contract_adj_smem<4>());
+    case 8:
+      SFS_TRY(ensure_smem_attr(contract_fwd_stream<8>, (int)contract_fwd_smem<8>()));
+      return ensure_smem_attr(contract_adj_stream<8>, (int)contract_adj_smem<8>());
   }
   set_error("unsupported orbit size %d", d.GS);
   return SFS_ERR_INVALID_ARG;

@@ -63,9 +63,9 @@ extern "C" int sfs_apply_AH_noalloc(sfs_operator* op, const void* y_dev, void* x
     set_error("null or misaligned argument");
     return SFS_ERR_INVALID_ARG;
   }
-  // the bin-plane spectra [Up][Ns] followed by the partial-sum slots [nslots][128][64]
+  // the bin-plane spectra [Up][Ns] followed by the adjoint slots [nslots][azb][64]
   const size_t n_rh = (size_t)op->Up * op->Ns;
-  const size_t n_slots = (size_t)op->nslots * kZBlockRows * kKappaTile;
+  const size_t n_slots = (size_t)op->nslots * op->azb * kKappaTile;
   if (n_rh + n_slots > kNoAllocScratchElems) {
     set_error("sfs_apply_AH_noalloc needs %zu bytes of scratch, the static maximum is %zu "
               "bytes; use sfs_apply_AH for this operator",
