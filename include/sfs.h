@@ -232,6 +232,34 @@ int sfs_fista(sfs_operator* op, const void* y_dev, double lambda, double L,
 int sfs_kernel_times(sfs_operator* op, double* fwd_ms, double* adj_ms,
                      int32_t* n_out_host);
 
+/*
+ * Limit of every bounded wait inside the contraction kernels (default 2 s of
+ * device time).  A wait that runs out sets the operator's device error flag,
+ * waits (at most 0.5 s more) for the copies its warp already issued, and
+ * returns; the calls that synchronise then report SFS_ERR_TIMEOUT, and so
+ * does sfs_check_status.  Results of the affected call are unspecified; the
+ * operator and the CUDA context stay usable.  Used to test failure handling
+ * (a very small limit forces timeouts).  ns must be > 0.
+ */
+int sfs_set_wait_timeout_ns(sfs_operator* op, uint64_t ns);
+
+/*
+ * Failure injection for tests of the timeout handling: while enabled, the
+ * first wait of every warp in each contraction launch is made on a barrier
+ * that nothing arrives at, so it runs out after the wait limit and takes the
+ * timeout path (error flag, bounded drain of the copies in flight, early
+ * return) for real.  Results are unspecified while enabled.
+ */
+int sfs_inject_wait_timeout(sfs_operator* op, int enable);
+
+/*
+ * Synchronises `stream`, then reports (and clears) the operator's device
+ * error flag: SFS_OK, SFS_ERR_TIMEOUT if a bounded wait ran out, or
+ * SFS_ERR_NON_FINITE if a non-finite lambda was computed, in any call since
+ * the last check.
+ */
+int sfs_check_status(sfs_operator* op, void* stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* sfs_last_error(void);
 

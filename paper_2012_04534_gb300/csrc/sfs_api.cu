@@ -225,6 +225,8 @@ PlaneDims operator_dims(const sfs_operator* op) {
   d.azb = op->azb;
   d.anzb = op->anzb;
   d.Ga = op->Ga;
+  d.wait_ns = op->wait_ns;
+  d.inject = op->inject;
   d.slot_kappa = op->slot_kappa;
   d.orbit_rep = op->orbit_rep;
   return d;
@@ -354,6 +356,11 @@ int check_err_flag(sfs_operator* op, cudaStream_t st) {
   SFS_CUDA(cudaStreamSynchronize(st));
   if (h) {
     SFS_CUDA(cudaMemsetAsync(op->ws.err, 0, sizeof(int), st));
+    SFS_CUDA(cudaStreamSynchronize(st));
+    if (h == 2) {
+      set_error("non-finite value reached the lambda rule");
+      return SFS_ERR_NON_FINITE;
+    }
     set_error("a bounded wait in a contraction kernel timed out");
     return SFS_ERR_TIMEOUT;
   }
@@ -896,7 +903,7 @@ int sfs_fista(sfs_operator* op, const void* y_dev, double lambda, double L, int 
     SFS_TRY(enqueue_AH(op, y, nullptr, nullptr, bits, st));
   }
   SFS_TRY(launch_set_thresholds(op->ws.scal, op->ws.red, use_mu ? 0.0 : lambda, L, use_mu,
-                                use_mu ? -lambda : 0.0, st));
+                                use_mu ? -lambda : 0.0, op->ws.err, st));
   double* obj = nullptr;
   if (obj_hist_host && iters > 0) {
     SFS_TRY(ensure_obj(op, iters));
@@ -931,6 +938,43 @@ int sfs_fista(sfs_operator* op, const void* y_dev, double lambda, double L, int 
     for (int k = 0; k < iters; ++k) obj_hist_host[k] = 0.5 * h[2 * k] + lam * h[2 * k + 1];
   }
   return SFS_OK;
+}
+
+int sfs_set_wait_timeout_ns(sfs_operator* op, uint64_t ns) {
+  clear_error();
+  if (!op || ns == 0) {
+    set_error("invalid argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(op->geo.d.device);
+  op->wait_ns = ns;
+  // captured iteration loops carry the old limit as a kernel argument
+  for (auto& ge : op->graphs) cudaGraphExecDestroy(ge.exec);
+  op->graphs.clear();
+  return SFS_OK;
+}
+
+int sfs_inject_wait_timeout(sfs_operator* op, int enable) {
+  clear_error();
+  if (!op) {
+    set_error("null argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(op->geo.d.device);
+  op->inject = enable ? 1 : 0;
+  for (auto& ge : op->graphs) cudaGraphExecDestroy(ge.exec);
+  op->graphs.clear();
+  return SFS_OK;
+}
+
+int sfs_check_status(sfs_operator* op, void* stream) {
+  clear_error();
+  if (!op) {
+    set_error("null argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(op->geo.d.device);
+  return check_err_flag(op, (cudaStream_t)stream);
 }
 
 int sfs_kernel_times(sfs_operator* op, double* fwd_ms, double* adj_ms, int32_t* n_out_host) {

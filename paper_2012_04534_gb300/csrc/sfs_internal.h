@@ -89,6 +89,8 @@ struct sfs_operator {
   int G = 1;                   // persistent CTAs of the contractions
   int nslots = 0;              // adjoint partial-sum slots
   int adj_seg = 0, azb = 128, anzb = 1, Ga = 0;  // adjoint layout (see PlaneDims)
+  uint64_t wait_ns = 2000000000ull;              // bounded-wait limit (2 s)
+  int inject = 0;                                // see PlaneDims::inject
   int k_lo = 0, k_hi = 0;
   double band_db = 0.0;
   std::vector<int32_t> idx;    // [S][M]
@@ -129,6 +131,8 @@ struct PlaneDims {
   int azb;      // depth rows per adjoint segment (32 segment-aligned, 128 otherwise)
   int anzb;     // adjoint depth blocks per slot tile
   int Ga;       // CTAs of the segment-aligned adjoint (= its segment count)
+  uint64_t wait_ns;  // limit of each bounded mbarrier wait in the contractions
+  int inject;        // failure-handling tests: first wait of each warp never completes
   const int32_t* slot_kappa;  // [Ns] wavenumber of each slot, -1 for padding
   const int32_t* orbit_rep;   // [Ns / GS] representative wavenumber, -1 for padding
 };
@@ -178,7 +182,7 @@ int launch_contract_adj(const PlaneDims& d, const float2* table, const float2* R
 
 // Small helpers.
 int launch_set_thresholds(float* scal, double* red, double lambda, double L,
-                          int use_mu, double mu, cudaStream_t st);
+                          int use_mu, double mu, int* err, cudaStream_t st);
 int launch_randn(float2* v, int n, uint64_t seed, cudaStream_t st);
 int launch_sumsq(const float2* v, int n, double* out, cudaStream_t st);
 int launch_scale_by_rnorm(float2* v, int n, const double* sumsq, cudaStream_t st);

@@ -46,20 +46,27 @@ __device__ __forceinline__ void block_add_double(double v, double* out) {
   }
 }
 
+// max that keeps a NaN (fmaxf would drop it), so that a non-finite input shows
+// up in the reduced value
+__device__ __forceinline__ float nanmax(float a, float b) {
+  return (a != a) ? a : ((b != b) ? b : fmaxf(a, b));
+}
+
 template <int NT>
 __device__ __forceinline__ void block_max_bits(float v, unsigned int* out) {
   __shared__ float part[NT / 32];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+  for (int off = 16; off > 0; off >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, off));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) part[warp] = v;
   __syncthreads();
   if (warp == 0) {
     v = lane < NT / 32 ? part[lane] : 0.0f;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
-    // non-negative floats order like their bit patterns
-    if (lane == 0) atomicMax(out, __float_as_uint(v));
+    for (int off = 16; off > 0; off >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    // non-negative floats order like their bit patterns, and a NaN (positive
+    // quiet NaN bits) orders above every finite value
+    if (lane == 0) atomicMax(out, __float_as_uint(v != v ? __int_as_float(0x7fc00000) : v));
   }
 }
 
@@ -364,7 +371,7 @@ inv_store_kernel(PlaneDims d, const float2* __restrict__ Gh, const int2* __restr
     const float2 v = buf[F::sidx(e / d.Nx, e % d.Nx)];
     if (xz) xz[e] = v;
     acc += (double)v.x * v.x + (double)v.y * v.y;
-    mx = fmaxf(mx, hypotf(v.x, v.y));
+    mx = nanmax(mx, hypotf(v.x, v.y));
   }
   if (red_sumsq) block_add_double<F::NT>(acc, red_sumsq);
   if (maxabs_bits) {
@@ -446,15 +453,18 @@ inv_fista_fwd_kernel(PlaneDims d, const float2* __restrict__ Gh,
 //            the warp holds its 16 accumulators in registers.  A segment
 //            (st, zb) split between CTAs leaves one partial per CTA in
 //            consecutive gslots; the consumer plane kernel adds them.
-// Waits on the mbarriers are bounded (2 s of global time); a timeout sets
-// *err, drains the copies already issued (again bounded) and ends the warp.
+// Waits on the mbarriers are bounded (wait_ns of global time, 2 s unless the
+// operator sets another limit); a timeout sets *err, drains the copies
+// already issued (again bounded, by a fixed 0.5 s) and ends the warp.  With
+// `inject` set (failure-handling tests), each warp's first wait is made on a
+// per-warp barrier that nothing ever arrives at, so that path runs for real.
 // ---------------------------------------------------------------------------
 constexpr int kContractWarps = 8;
 constexpr int kContractThreads = kContractWarps * 32;
 constexpr int kRowsPerWarp = 16;
 constexpr int kZBlock = kContractWarps * kRowsPerWarp;  // 128 depths
 constexpr int kSlots = 3;
-constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr uint64_t kDrainNs = 500000000ull;  // bound of the post-timeout drain
 
 // (h.x + j h.y) times the two complex values of x, accumulated
 __device__ __forceinline__ void cmac_pair(float4& acc, const float2 h, const float4 x) {
@@ -578,7 +588,7 @@ __device__ __forceinline__ void issue_unit(const float2* __restrict__ T, const U
 // Drain the copies this warp has in flight (ring uses [from, to)).
 __device__ __forceinline__ void drain_warp(int from, int to, uint32_t bar0) {
   for (int i = from; i < to; ++i)
-    mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, kWaitNs / 4);
+    mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, kDrainNs);
 }
 
 // Up = bins padded to a multiple of UP = GS / 2 (padding table rows are zero);
@@ -587,14 +597,14 @@ template <int GS>
 __global__ void __launch_bounds__(kContractThreads, kContractCtasPerSm)
 contract_fwd_stream(const float2* __restrict__ T, const float4* __restrict__ Xh,
                     float4* __restrict__ Yp, int Nz, int Up, int Ns, int nzb, int nunits,
-                    int* __restrict__ err) {
+                    int* __restrict__ err, uint64_t wait_ns, int inject) {
   constexpr int E = kKappaTile / GS;
   constexpr int UP = GS / 2;
   constexpr int SLOT = UP * kRowsPerWarp * E;  // float2 per ring slot (4 KB)
   extern __shared__ __align__(128) float4 sm4[];
   float4* red = sm4;                                        // [8][UP][32]
   float2* ring = (float2*)(red + kContractWarps * UP * 32);  // [8][3][SLOT]
-  uint64_t* bars = (uint64_t*)(ring + kContractWarps * kSlots * SLOT);  // [8][3]
+  uint64_t* bars = (uint64_t*)(ring + kContractWarps * kSlots * SLOT);  // [8][4]
   __shared__ int abort_flag;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int NUG = Up / UP;
@@ -602,11 +612,12 @@ contract_fwd_stream(const float2* __restrict__ T, const float4* __restrict__ Xh,
   const int first = (int)(((long long)nunits * b) / G);
   const int n = (int)(((long long)nunits * (b + 1)) / G) - first;
   float2* my = ring + w * kSlots * SLOT;
-  const uint32_t bar0 = smem_addr(bars + w * kSlots);
+  const uint32_t bar0 = smem_addr(bars + w * (kSlots + 1));
+  const uint32_t never = bar0 + 8u * kSlots;  // nothing arrives here
   const int ent = lane / (GS / 2);  // this lane's orbit entry in a row
   if (threadIdx.x == 0) abort_flag = 0;
   if (lane == 0) {
-    for (int s = 0; s < kSlots; ++s) mbar_init(bar0 + 8u * s, 1);
+    for (int s = 0; s <= kSlots; ++s) mbar_init(bar0 + 8u * s, 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -645,7 +656,10 @@ contract_fwd_stream(const float2* __restrict__ T, const float4* __restrict__ Xh,
 #pragma unroll
     for (int q = 0; q < UP; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (ok) {
-      if (!mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, kWaitNs)) {
+      const bool got = (inject && i == 0)
+                           ? mbar_wait_bounded(never, 0, wait_ns)
+                           : mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, wait_ns);
+      if (!got) {
         ok = false;
         if (lane == 0) {
           atomicExch(err, 1);
@@ -693,23 +707,24 @@ template <int GS>
 __global__ void __launch_bounds__(kContractThreads, kContractCtasPerSm)
 contract_adj_stream(const float2* __restrict__ T, const float4* __restrict__ Rh,
                     float4* __restrict__ Gs, int Nz, int Up, int Ns, int nzb, int nunits,
-                    int* __restrict__ err) {
+                    int* __restrict__ err, uint64_t wait_ns, int inject) {
   constexpr int E = kKappaTile / GS;
   constexpr int UP = GS / 2;
   constexpr int SLOT = UP * kRowsPerWarp * E;
   extern __shared__ __align__(128) float4 sm4[];
   float2* ring = (float2*)sm4;
-  uint64_t* bars = (uint64_t*)(ring + kContractWarps * kSlots * SLOT);
+  uint64_t* bars = (uint64_t*)(ring + kContractWarps * kSlots * SLOT);  // [8][4]
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int NUG = Up / UP;
   const int G = gridDim.x, b = blockIdx.x;
   const int first = (int)(((long long)nunits * b) / G);
   const int n = (int)(((long long)nunits * (b + 1)) / G) - first;
   float2* my = ring + w * kSlots * SLOT;
-  const uint32_t bar0 = smem_addr(bars + w * kSlots);
+  const uint32_t bar0 = smem_addr(bars + w * (kSlots + 1));
+  const uint32_t never = bar0 + 8u * kSlots;  // nothing arrives here
   const int ent = lane / (GS / 2);
   if (lane == 0) {
-    for (int s = 0; s < kSlots; ++s) mbar_init(bar0 + 8u * s, 1);
+    for (int s = 0; s <= kSlots; ++s) mbar_init(bar0 + 8u * s, 1);
     fence_mbar_init();
   }
   __syncwarp();
@@ -751,7 +766,10 @@ contract_adj_stream(const float2* __restrict__ T, const float4* __restrict__ Rh,
     for (int q = 0; q < UP; ++q) rr[q] = rnext[q];
     rp.next(NUG, nzb);
     load_rh(rnext, rp, i + 1 < n);
-    if (!mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, kWaitNs)) {
+    const bool got = (inject && i == 0)
+                         ? mbar_wait_bounded(never, 0, wait_ns)
+                         : mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, wait_ns);
+    if (!got) {
       if (lane == 0) atomicExch(err, 1);
       drain_warp(i, next_issue, bar0);
       return;
@@ -802,7 +820,7 @@ template <int GS>
 __global__ void __launch_bounds__(kContractThreads, kContractCtasPerSm)
 contract_adj_seg(const float2* __restrict__ T, const float4* __restrict__ Rh,
                  float4* __restrict__ Gs, int Nz, int Up, int Ns, int anzb,
-                 int* __restrict__ err) {
+                 int* __restrict__ err, uint64_t wait_ns, int inject) {
   constexpr int E = kKappaTile / GS;
   constexpr int UPA = 2 * GS;                   // bins per ring slot
   constexpr int SLOT = UPA * kSegRows * E;      // float2 per slot (4 KB)
@@ -817,9 +835,10 @@ contract_adj_seg(const float2* __restrict__ T, const float4* __restrict__ Rh,
   for (int i = threadIdx.x; i < Up * 32; i += kContractThreads)
     rtile[i] = Rh[(size_t)(i >> 5) * ns4 + st * 32 + (i & 31)];
   float2* my = ring + w * kSegSlots * SLOT;
-  const uint32_t bar0 = smem_addr(bars + w * kSegSlots);
+  const uint32_t bar0 = smem_addr(bars + w * (kSegSlots + 1));
+  const uint32_t never = bar0 + 8u * kSegSlots;  // nothing arrives here
   if (lane == 0) {
-    for (int k = 0; k < kSegSlots; ++k) mbar_init(bar0 + 8u * k, 1);
+    for (int k = 0; k <= kSegSlots; ++k) mbar_init(bar0 + 8u * k, 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -848,10 +867,13 @@ contract_adj_seg(const float2* __restrict__ T, const float4* __restrict__ Rh,
   for (int r = 0; r < kSegRows; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int c = 0; c < nch; ++c) {
     if (c + kSegSlots - 1 < nch) issue(c + kSegSlots - 1);
-    if (!mbar_wait_bounded(bar0 + 8u * (c % kSegSlots), (c / kSegSlots) & 1, kWaitNs)) {
+    const bool got = (inject && c == 0)
+                         ? mbar_wait_bounded(never, 0, wait_ns)
+                         : mbar_wait_bounded(bar0 + 8u * (c % kSegSlots), (c / kSegSlots) & 1, wait_ns);
+    if (!got) {
       if (lane == 0) atomicExch(err, 1);
       for (int k = c; k < min(nch, c + kSegSlots); ++k)  // drain what was issued
-        mbar_wait_bounded(bar0 + 8u * (k % kSegSlots), (k / kSegSlots) & 1, kWaitNs / 4);
+        mbar_wait_bounded(bar0 + 8u * (k % kSegSlots), (k / kSegSlots) & 1, kDrainNs);
       return;
     }
     const float2* slot = my + (c % kSegSlots) * SLOT + ent;
@@ -886,9 +908,10 @@ contract_adj_seg(const float2* __restrict__ T, const float4* __restrict__ Rh,
 // Small kernels
 // ---------------------------------------------------------------------------
 __global__ void set_thresholds_kernel(float* scal, double* red, double lambda, double L,
-                                      int use_mu, double mu) {
+                                      int use_mu, double mu, int* err) {
   double lam = lambda;
   if (use_mu) lam = mu * (double)__uint_as_float(((unsigned int*)scal)[kLamMax]);
+  if (!isfinite(lam)) atomicExch(err, 2);  // non-finite data reached the lambda rule
   scal[kThr] = (float)(lam / L);
   scal[kInvL] = (float)(1.0 / L);
   red[kNumRed - 1] = lam;
@@ -1070,11 +1093,11 @@ constexpr size_t kRingSlotBytes = 4096;
 template <int GS>
 size_t contract_fwd_smem() {
   return (size_t)kContractWarps * (GS / 2) * 32 * 16 +
-         (size_t)kContractWarps * kSlots * kRingSlotBytes + kContractWarps * kSlots * 8;
+         (size_t)kContractWarps * kSlots * kRingSlotBytes + kContractWarps * (kSlots + 1) * 8;
 }
 template <int GS>
 size_t contract_adj_smem() {
-  return (size_t)kContractWarps * kSlots * kRingSlotBytes + kContractWarps * kSlots * 8;
+  return (size_t)kContractWarps * kSlots * kRingSlotBytes + kContractWarps * (kSlots + 1) * 8;
 }
 template <int GS>
 int launch_fwd_gs(const PlaneDims& d, const float2* table, const float2* Xh, float2* Yp,
@@ -1084,7 +1107,7 @@ int launch_fwd_gs(const PlaneDims& d, const float2* table, const float2* Xh, flo
   const int n = contract_units(d);
   const int G = std::min(d.G, n);
   contract_fwd_stream<GS><<<G, kContractThreads, smem, st>>>(
-      table, (const float4*)Xh, (float4*)Yp, d.Nz, d.Up, d.Ns, d.nzb, n, err);
+      table, (const float4*)Xh, (float4*)Yp, d.Nz, d.Up, d.Ns, d.nzb, n, err, d.wait_ns, d.inject);
   SFS_CUDA(cudaGetLastError());
   return SFS_OK;
 }
@@ -1096,7 +1119,7 @@ int launch_adj_gs(const PlaneDims& d, const float2* table, const float2* Rh, flo
   const int n = contract_units(d);
   const int G = std::min(d.G, n);
   contract_adj_stream<GS><<<G, kContractThreads, smem, st>>>(
-      table, (const float4*)Rh, (float4*)Gs, d.Nz, d.Up, d.Ns, d.nzb, n, err);
+      table, (const float4*)Rh, (float4*)Gs, d.Nz, d.Up, d.Ns, d.nzb, n, err, d.wait_ns, d.inject);
   SFS_CUDA(cudaGetLastError());
   return SFS_OK;
 }
@@ -1116,7 +1139,7 @@ int launch_contract_fwd(const PlaneDims& d, const float2* table, const float2* X
 template <int GS>
 size_t contract_adj_seg_smem(int Up) {
   return (size_t)Up * 32 * 16 + (size_t)kContractWarps * kSegSlots * kRingSlotBytes +
-         kContractWarps * kSegSlots * 8;
+         kContractWarps * (kSegSlots + 1) * 8;
 }
 template <int GS>
 int launch_adj_seg_gs(const PlaneDims& d, const float2* table, const float2* Rh, float2* Gs,
@@ -1124,7 +1147,7 @@ int launch_adj_seg_gs(const PlaneDims& d, const float2* table, const float2* Rh,
   const size_t smem = contract_adj_seg_smem<GS>(d.Up);
   SFS_TRY(ensure_smem_attr(contract_adj_seg<GS>, (int)smem));
   contract_adj_seg<GS><<<d.Ga, kContractThreads, smem, st>>>(
-      table, (const float4*)Rh, (float4*)Gs, d.Nz, d.Up, d.Ns, d.anzb, err);
+      table, (const float4*)Rh, (float4*)Gs, d.Nz, d.Up, d.Ns, d.anzb, err, d.wait_ns, d.inject);
   SFS_CUDA(cudaGetLastError());
   return SFS_OK;
 }
@@ -1184,8 +1207,8 @@ int prepare_kernels(const PlaneDims& d) {
 }
 
 int launch_set_thresholds(float* scal, double* red, double lambda, double L, int use_mu,
-                          double mu, cudaStream_t st) {
-  set_thresholds_kernel<<<1, 1, 0, st>>>(scal, red, lambda, L, use_mu, mu);
+                          double mu, int* err, cudaStream_t st) {
+  set_thresholds_kernel<<<1, 1, 0, st>>>(scal, red, lambda, L, use_mu, mu, err);
   SFS_CUDA(cudaGetLastError());
   return SFS_OK;
 }

@@ -45,8 +45,8 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_select_freqs", "sfs_operator_from_indices", "sfs_destroy_operator",
            "sfs_operator_info", "sfs_apply_A", "sfs_apply_AH", "sfs_apply_AH_noalloc",
            "sfs_max_abs_AH",
-           "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_last_error",
-           "sfs_version")
+           "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_set_wait_timeout_ns",
+           "sfs_inject_wait_timeout", "sfs_check_status", "sfs_last_error", "sfs_version")
 
 
 class SfsError(RuntimeError):
@@ -109,6 +109,9 @@ def lib():
         "sfs_lipschitz": [vp, i32, dbl, u64, dbl, P(dbl), vp],
         "sfs_fista": [vp, vp, dbl, dbl, i32, vp, u32, P(dbl), vp],
         "sfs_kernel_times": [vp, P(dbl), P(dbl), P(ctypes.c_int32)],
+        "sfs_set_wait_timeout_ns": [vp, u64],
+        "sfs_check_status": [vp, vp],
+        "sfs_inject_wait_timeout": [vp, i32],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -238,6 +241,20 @@ def sfs_kernel_times(op):
     return f.value, a.value, n.value
 
 
+def sfs_set_wait_timeout_ns(op, ns: int):
+    _check(lib().sfs_set_wait_timeout_ns(op, ns))
+
+
+def sfs_inject_wait_timeout(op, enable: bool):
+    _check(lib().sfs_inject_wait_timeout(op, int(enable)))
+
+
+def sfs_check_status(op, stream_ptr) -> int:
+    """SFS_OK, SFS_ERR_TIMEOUT or SFS_ERR_NON_FINITE (returned, not raised)."""
+    return _check(lib().sfs_check_status(op, stream_ptr),
+                  allow=(SFS_ERR_TIMEOUT, SFS_ERR_NON_FINITE))
+
+
 def sfs_version() -> str:
     return lib().sfs_version().decode()
 
@@ -331,6 +348,16 @@ class Operator:
 
     def kernel_times(self):
         return sfs_kernel_times(self.handle)
+
+    def set_wait_timeout_ns(self, ns: int):
+        sfs_set_wait_timeout_ns(self.handle, ns)
+
+    def inject_wait_timeout(self, enable: bool):
+        sfs_inject_wait_timeout(self.handle, enable)
+
+    def check_status(self, stream=None) -> int:
+        import torch
+        return sfs_check_status(self.handle, _stream_ptr(stream, torch.device("cuda", self.device)))
 
     def close(self):
         if self.handle and _lib is not None:
