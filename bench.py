@@ -341,6 +341,7 @@ def main():
         flush.fill_(i & 0xFF)
         op.fista(y, -w["mu"], L, iters, x=x, time_kernels=True)
     fwd_ms, adj_ms, n_launch = op.kernel_times()
+    stage_ms, _ = op.stage_times()
     Nk, U, Nz, Ns = info["Nkappa"], info["U"], info["Nz"], info["Nslot"]
     # algorithmic bytes per launch: the folded table plus the spectra read and
     # written; algorithmic flops: one complex multiply-add (8 flops) per
@@ -374,7 +375,9 @@ def main():
                  "kernel": "depth contraction (forward and adjoint, averaged)",
                  "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": alg_flops,
                  "hbm_frac": hbm_frac, "alu_frac": alu_frac,
-                 "fwd_ms": fwd_ms, "adj_ms": adj_ms, "launches_timed": 2 * n_launch})
+                 "fwd_ms": fwd_ms, "adj_ms": adj_ms, "launches_timed": 2 * n_launch,
+                 "iteration_stages_ms": {"contract_fwd": stage_ms[0], "resid_planes": stage_ms[1],
+                                         "contract_adj": stage_ms[2], "update_planes": stage_ms[3]}})
 
     # ---- CPU baseline: the FP64 oracle, bounded sample, rank 0 only ----
     cpu = None

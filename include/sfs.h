@@ -233,6 +233,15 @@ int sfs_kernel_times(sfs_operator* op, double* fwd_ms, double* adj_ms,
                      int32_t* n_out_host);
 
 /*
+ * Average device time per iteration [ms] of each of the four stages of the
+ * last sfs_fista call made with SFS_FISTA_TIME_KERNELS: ms4_host[0] forward
+ * contraction, [1] residual planes (inverse FFT, residual, forward FFT),
+ * [2] adjoint contraction, [3] update planes (inverse FFT, FISTA step,
+ * forward FFT).  Synchronises the operator's device.
+ */
+int sfs_stage_times(sfs_operator* op, double* ms4_host, int32_t* n_out_host);
+
+/*
  * Limit of every bounded wait inside the contraction kernels (default 2 s of
  * device time).  A wait that runs out sets the operator's device error flag,
  * waits (at most 0.5 s more) for the copies its warp already issued, and

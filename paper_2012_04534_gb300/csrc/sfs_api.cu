@@ -193,6 +193,7 @@ void free_operator(sfs_operator* op) {
   cudaFree(op->ws.xk);
   cudaFree(op->ws.gam);
   cudaFree(op->ws.ybuf);
+  cudaFree(op->ws.yplane);
   cudaFree(op->ws.vbuf);
   cudaFree(op->ws.scal);
   cudaFree(op->ws.red);
@@ -300,19 +301,21 @@ int enqueue_fista_iterations(sfs_operator* op, int iters, double* obj, bool timi
     beta[k] = (float)((t - 1.0) / tn);
     t = tn;
   }
+  SFS_TRY(launch_scatter_y_planes(d, op->ws.ybuf, op->posmap, op->ws.yplane, st));
   SFS_TRY(launch_fwd_planes(d, op->ws.gam, op->ws.Xh, st));
   for (int k = 0; k < iters; ++k) {
-    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 0], st));
+    if (timing) SFS_CUDA(cudaEventRecord(op->ev[5 * k + 0], st));
     SFS_TRY(launch_contract_fwd(d, op->table, op->ws.Xh, op->ws.Yh, op->ws.err, st));
-    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 1], st));
-    SFS_TRY(launch_inv_resid_fwd(d, op->ws.Yh, op->posmap, op->ws.ybuf, op->ws.Rh,
+    if (timing) SFS_CUDA(cudaEventRecord(op->ev[5 * k + 1], st));
+    SFS_TRY(launch_inv_resid_fwd(d, op->ws.Yh, op->posmap, op->ws.yplane, op->ws.Rh,
                                  obj ? obj + 2 * k : nullptr, st));
-    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 2], st));
+    if (timing) SFS_CUDA(cudaEventRecord(op->ev[5 * k + 2], st));
     SFS_TRY(launch_contract_adj(d, op->table, op->ws.Rh, op->ws.Gh, op->ws.err, st));
-    if (timing) SFS_CUDA(cudaEventRecord(op->ev[4 * k + 3], st));
+    if (timing) SFS_CUDA(cudaEventRecord(op->ev[5 * k + 3], st));
     SFS_TRY(launch_inv_fista_fwd(d, op->ws.Gh, op->ws.segslot, op->ws.xk, op->ws.gam,
                                  op->ws.scal, beta[k], k + 1 < iters, op->ws.Xh,
                                  obj ? obj + 2 * k + 1 : nullptr, st));
+    if (timing) SFS_CUDA(cudaEventRecord(op->ev[5 * k + 4], st));
   }
   return SFS_OK;
 }
@@ -655,6 +658,7 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
   if ((rc = dev_alloc(&op->ws.xk, (size_t)op->V)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.gam, (size_t)op->V)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.ybuf, (size_t)S * M)) != SFS_OK) return fail(rc);
+  if ((rc = dev_alloc(&op->ws.yplane, (size_t)op->U * S)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.vbuf, (size_t)S * M)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.scal, kNumFloatScalars)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.red, kNumRed)) != SFS_OK) return fail(rc);
@@ -912,7 +916,7 @@ int sfs_fista(sfs_operator* op, const void* y_dev, double lambda, double L, int 
   }
   const bool timing = (flags & SFS_FISTA_TIME_KERNELS) != 0;
   if (timing) {
-    SFS_TRY(ensure_events(op, 4 * iters));
+    SFS_TRY(ensure_events(op, 5 * iters));
     op->ev_used = 0;
   }
   if (iters > 0) {
@@ -977,26 +981,38 @@ int sfs_check_status(sfs_operator* op, void* stream) {
   return check_err_flag(op, (cudaStream_t)stream);
 }
 
+int sfs_stage_times(sfs_operator* op, double* ms4, int32_t* n_out_host) {
+  clear_error();
+  if (!op || !ms4) {
+    set_error("null argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(op->geo.d.device);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = 0; k < op->ev_used; ++k) {
+    SFS_CUDA(cudaEventSynchronize(op->ev[5 * k + 4]));
+    for (int j = 0; j < 4; ++j) {
+      float t = 0.f;
+      SFS_CUDA(cudaEventElapsedTime(&t, op->ev[5 * k + j], op->ev[5 * k + j + 1]));
+      acc[j] += t;
+    }
+  }
+  const int n = op->ev_used;
+  for (int j = 0; j < 4; ++j) ms4[j] = n ? acc[j] / n : 0.0;
+  if (n_out_host) *n_out_host = n;
+  return SFS_OK;
+}
+
 int sfs_kernel_times(sfs_operator* op, double* fwd_ms, double* adj_ms, int32_t* n_out_host) {
   clear_error();
   if (!op || !fwd_ms || !adj_ms) {
     set_error("null argument");
     return SFS_ERR_INVALID_ARG;
   }
-  DeviceScope scope(op->geo.d.device);
-  double f = 0.0, a = 0.0;
-  for (int k = 0; k < op->ev_used; ++k) {
-    float t1 = 0.f, t2 = 0.f;
-    SFS_CUDA(cudaEventSynchronize(op->ev[4 * k + 3]));
-    SFS_CUDA(cudaEventElapsedTime(&t1, op->ev[4 * k + 0], op->ev[4 * k + 1]));
-    SFS_CUDA(cudaEventElapsedTime(&t2, op->ev[4 * k + 2], op->ev[4 * k + 3]));
-    f += t1;
-    a += t2;
-  }
-  const int n = op->ev_used;
-  *fwd_ms = n ? f / n : 0.0;
-  *adj_ms = n ? a / n : 0.0;
-  if (n_out_host) *n_out_host = n;
+  double ms4[4];
+  SFS_TRY(sfs_stage_times(op, ms4, n_out_host));
+  *fwd_ms = ms4[0];
+  *adj_ms = ms4[2];
   return SFS_OK;
 }
 

@@ -169,12 +169,54 @@ __device__ __forceinline__ void transpose_plane(float2* buf) {
 }
 
 // ---------------------------------------------------------------------------
-// Plane transforms.  TWO_D: P x P plane, row stride P + 1.  Otherwise a line
-// of P points (Py = 1).
+// 64-point FFTs by groups of 8 lanes.  Lane bits 2..4 are the FFT lane l;
+// lane l holds x[l + 8 j], j = 0..7.  64 = 8 x 8: an 8-point DFT over j, the
+// twiddles W64^(l k1), an 8 x 8 transpose across the 8 lanes (three xor
+// shuffle stages), and an 8-point DFT over l leave X[l + 8 k2] in lane l,
+// slot k2.  No shared memory and no barrier inside the transform.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void transpose8_lanes(float2 v[8], int l) {
+#pragma unroll
+  for (int s = 4; s >= 1; s >>= 1) {
+    const bool hi = (l & s) != 0;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      if (m & s) continue;
+      // the lane with bit s clear sends v[m ^ s] and receives into it; its
+      // partner sends v[m] and receives into v[m]
+      const float2 send = hi ? v[m] : v[m ^ s];
+      float2 recv;
+      recv.x = __shfl_xor_sync(0xffffffffu, send.x, s << 2);
+      recv.y = __shfl_xor_sync(0xffffffffu, send.y, s << 2);
+      if (hi) v[m] = recv;
+      else v[m ^ s] = recv;
+    }
+  }
+}
+
+template <bool INV>
+__device__ __forceinline__ void fft64_lanes(float2 v[8], const float2* tw, int l) {
+  dft_small<8, INV>(v);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) {
+    float2 w = tw[l * k];
+    if (INV) w.y = -w.y;
+    v[k] = cmul(v[k], w);
+  }
+  transpose8_lanes(v, l);
+  dft_small<8, INV>(v);
+}
+
+// ---------------------------------------------------------------------------
+// Plane transforms.  TWO_D: P x P plane, row stride P + 1 (P + 4 for P = 64,
+// which the lane-group engine reads and writes without bank conflicts).
+// Otherwise a line of P points (Py = 1).
 // ---------------------------------------------------------------------------
 template <int P, bool TWO_D>
 struct PlaneFFT {
-  static constexpr int LD = TWO_D ? P + 1 : P;
+  // 64 x 64 planes use the lane-group engine (512 threads = 64 columns x 8)
+  static constexpr bool LANES64 = TWO_D && P == 64;
+  static constexpr int LD = TWO_D ? (LANES64 ? P + 4 : P + 1) : P;
   static constexpr int NT = TWO_D ? (P >= 64 ? 512 : 256) : (P >= 512 ? 256 : (P >= 128 ? 128 : 64));
   static constexpr int ELEMS = TWO_D ? P * LD : P;   // float2 slots of the plane
   static constexpr int SMEM = (ELEMS + P) * 8;       // plane + twiddles
@@ -189,7 +231,27 @@ struct PlaneFFT {
 
   // Forward 2-D FFT; only spatial columns ix < ncols may be nonzero.
   __device__ static __forceinline__ void forward(float2* buf, const float2* tw, int ncols) {
-    if constexpr (TWO_D) {
+    if constexpr (LANES64) {
+      const int lane = threadIdx.x & 31, l = lane >> 2;
+      const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
+      float2 v[8];
+      // along y for column x = c; written transposed: row x, column ky
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        v[j] = c < ncols ? buf[(l + 8 * j) * LD + c] : make_float2(0.f, 0.f);
+      __syncthreads();
+      fft64_lanes<false>(v, tw, l);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) buf[c * LD + l + 8 * k] = v[k];
+      __syncthreads();
+      // along x for column ky = c: result kx = l + 8 k at row kx (own column only)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
+      fft64_lanes<false>(v, tw, l);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) buf[(l + 8 * k) * LD + c] = v[k];
+      __syncthreads();
+    } else if constexpr (TWO_D) {
       fft_multi<P, false, NT, P, true>(buf, ncols, LD, 1, tw);   // along y
       transpose_plane<P, LD, NT>(buf);
       fft_multi<P, false, NT, P, true>(buf, P, LD, 1, tw);       // along x
@@ -200,7 +262,28 @@ struct PlaneFFT {
   // Inverse (unnormalised) 2-D FFT; only spatial columns ix < ncols of the
   // result are computed.
   __device__ static __forceinline__ void inverse(float2* buf, const float2* tw, int ncols) {
-    if constexpr (TWO_D) {
+    if constexpr (LANES64) {
+      const int lane = threadIdx.x & 31, l = lane >> 2;
+      const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
+      float2 v[8];
+      // along kx for column ky = c; written transposed: row ky, column x
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
+      __syncthreads();
+      fft64_lanes<true>(v, tw, l);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) buf[c * LD + l + 8 * k] = v[k];
+      __syncthreads();
+      // along ky for column x = c: result y = l + 8 k at row y (own column only)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
+      fft64_lanes<true>(v, tw, l);
+      if (c < ncols) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) buf[(l + 8 * k) * LD + c] = v[k];
+      }
+      __syncthreads();
+    } else if constexpr (TWO_D) {
       fft_multi<P, true, NT, P, true>(buf, P, LD, 1, tw);        // kx -> x
       transpose_plane<P, LD, NT>(buf);
       fft_multi<P, true, NT, P, true>(buf, ncols, LD, 1, tw);    // ky -> y

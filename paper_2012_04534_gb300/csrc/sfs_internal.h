@@ -65,6 +65,7 @@ struct Workspace {
   float2* xk = nullptr;     // [V] FISTA iterate x_k
   float2* gam = nullptr;    // [V] FISTA extrapolated point gamma_k
   float2* ybuf = nullptr;   // [S][M] measurements copy
+  float2* yplane = nullptr; // [U][S] measurements by bin plane (FISTA residual)
   float2* vbuf = nullptr;   // [S][M] scratch (power iteration)
   float* scal = nullptr;    // kNumFloatScalars floats
   double* red = nullptr;    // kNumRed doubles
@@ -161,8 +162,11 @@ int launch_fwd_planes(const PlaneDims& d, const float2* x, float2* Xh,
 int launch_inv_gather(const PlaneDims& d, const float2* Yh, const int32_t* posmap,
                       float2* y, double* red_sumsq, cudaStream_t st);
 int launch_inv_resid_fwd(const PlaneDims& d, const float2* Yh, const int32_t* posmap,
-                         const float2* yobs, float2* Rh, double* red_sumsq,
+                         const float2* yplane, float2* Rh, double* red_sumsq,
                          cudaStream_t st);
+// y[s][m] -> yplane[u][s], zero where bin plane u is not kept at position s
+int launch_scatter_y_planes(const PlaneDims& d, const float2* y, const int32_t* posmap,
+                            float2* yplane, cudaStream_t st);
 int launch_scatter_fwd(const PlaneDims& d, const float2* y, const int32_t* posmap,
                        float2* Rh, cudaStream_t st);
 int launch_inv_store(const PlaneDims& d, const float2* Gh, const int2* segslot,

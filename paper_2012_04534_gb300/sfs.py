@@ -45,7 +45,8 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_select_freqs", "sfs_operator_from_indices", "sfs_destroy_operator",
            "sfs_operator_info", "sfs_apply_A", "sfs_apply_AH", "sfs_apply_AH_noalloc",
            "sfs_max_abs_AH",
-           "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_set_wait_timeout_ns",
+           "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
+           "sfs_set_wait_timeout_ns",
            "sfs_inject_wait_timeout", "sfs_check_status", "sfs_last_error", "sfs_version")
 
 
@@ -110,6 +111,7 @@ def lib():
         "sfs_fista": [vp, vp, dbl, dbl, i32, vp, u32, P(dbl), vp],
         "sfs_kernel_times": [vp, P(dbl), P(dbl), P(ctypes.c_int32)],
         "sfs_set_wait_timeout_ns": [vp, u64],
+        "sfs_stage_times": [vp, P(dbl), P(ctypes.c_int32)],
         "sfs_check_status": [vp, vp],
         "sfs_inject_wait_timeout": [vp, i32],
     }
@@ -241,6 +243,13 @@ def sfs_kernel_times(op):
     return f.value, a.value, n.value
 
 
+def sfs_stage_times(op):
+    ms4 = (ctypes.c_double * 4)()
+    n = ctypes.c_int32()
+    _check(lib().sfs_stage_times(op, ms4, ctypes.byref(n)))
+    return list(ms4), n.value
+
+
 def sfs_set_wait_timeout_ns(op, ns: int):
     _check(lib().sfs_set_wait_timeout_ns(op, ns))
 
@@ -348,6 +357,11 @@ class Operator:
 
     def kernel_times(self):
         return sfs_kernel_times(self.handle)
+
+    def stage_times(self):
+        """[forward contraction, residual planes, adjoint contraction, update
+        planes] average ms per iteration of the last timed sfs_fista call."""
+        return sfs_stage_times(self.handle)
 
     def set_wait_timeout_ns(self, ns: int):
         sfs_set_wait_timeout_ns(self.handle, ns)
