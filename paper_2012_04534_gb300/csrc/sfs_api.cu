@@ -643,7 +643,8 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
     segslot = segment_slots(nseg, ngroups, op->G);
   }
   const size_t Ns = op->Ns;
-  const size_t table_elems = Ns / op->GS * op->Up * d.Nz;
+  // depth pairs interleaved: Nz rounded up to even (the odd padding is zero)
+  const size_t table_elems = Ns / op->GS * op->Up * (size_t)((d.Nz + 1) / 2 * 2);
   if ((rc = dev_alloc(&op->table, table_elems)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->posmap, posmap.size())) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.Xh, Ns * d.Nz)) != SFS_OK) return fail(rc);
@@ -748,7 +749,7 @@ int sfs_operator_info(const sfs_operator* op, sfs_operator_info_t* info) {
   info->band_db = op->band_db;
   info->alpha = op->geo.alpha;
   info->t0 = op->geo.d.t0;
-  info->table_bytes = (int64_t)(op->Ns / op->GS) * op->Up * op->geo.d.Nz * 8;
+  info->table_bytes = (int64_t)(op->Ns / op->GS) * op->Up * ((op->geo.d.Nz + 1) / 2 * 2) * 8;
   info->launches_per_iter = 4;
   info->Nslot = op->Ns;
   info->GS = op->GS;

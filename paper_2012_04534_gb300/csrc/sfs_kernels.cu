@@ -136,11 +136,17 @@ build_table_kernel(PlaneDims d, const float2* __restrict__ tof,
   // FFT2 of the generator is constant on each symmetry orbit of wavenumbers
   // (h depends on dx^2 + dy^2 only); store it once per orbit, at the orbit's
   // representative.  Orbit o lives in slot tile o / E, entry o % E.
+  // Depths 2p and 2p + 1 share one 16-byte word (re_2p, re_2p+1, im_2p,
+  // im_2p+1): T4[st][u][p][e] with e < E = 64 / GS.
   const int E = kKappaTile / d.GS;
+  const int Nzp = (d.Nz + 1) / 2;
+  float* tf = (float*)table;
   for (int o = threadIdx.x; o < d.Ns / d.GS; o += F::NT) {
     const int rep = d.orbit_rep[o];
-    const size_t off = (((size_t)(o / E) * d.Up + u) * d.Nz + z) * E + (o % E);
-    table[off] = rep >= 0 ? buf[F::kidx(rep)] : make_float2(0.f, 0.f);
+    const float2 v = rep >= 0 ? buf[F::kidx(rep)] : make_float2(0.f, 0.f);
+    const size_t w4 = (((size_t)(o / E) * d.Up + u) * Nzp + z / 2) * E + (o % E);
+    tf[4 * w4 + (z & 1)] = v.x;
+    tf[4 * w4 + 2 + (z & 1)] = v.y;
   }
 }
 
@@ -470,53 +476,40 @@ inv_fista_fwd_kernel(PlaneDims d, const float2* __restrict__ Gh,
 // only, so its FFT2 is the same for every wavenumber of a symmetry orbit
 // (sign flips of kx and ky, and kx <-> ky on a square grid).  Spectra are
 // kept in slot order, GS slots per orbit (2 line, 4 area, 8 square area,
-// padding slots carry zero), and the table stores one entry per orbit:
-// T[st][u][z][e], e < E = 64 / GS, for slot tile st of 64 slots.  One table
-// row (st, u, z) is 8 E bytes.  The arithmetic is that of the unfolded
-// operator; only the bytes streamed shrink by about GS.
+// padding slots carry zero), and the table stores one entry per orbit.
 //
-// Work is cut into units (st, zb, u): bin u of slot tile st over the depth
-// block zb (<= 128 depths).  A persistent CTA per SM takes a contiguous,
-// equal share of the units.  Each of its 8 warps owns 16 depths of the block
-// and streams its 16 rows of every unit through its own 3-slot shared-memory
-// ring, filled by cp.async.bulk and tracked by one mbarrier per slot.  Lane l
-// owns the slot pair (2l, 2l + 1), both in orbit entry l / (GS / 2), so the
-// GS / 2 lanes of an orbit read the same entry (a shared-memory broadcast)
-// and no lane exchanges data with another.
-//   forward: Yp[zb][u][slot] = sum_{z in zb} T[st][u][z][e] Xh[z][slot]; the
-//            warp holds its 16 Xh values in registers and the 8 warps' partial
-//            sums are added in shared memory, four units at a time.
-//   adjoint: Gs[gslot][z][slot % 64] = sum_{u in the CTA's share} conj(T) Rh[u][slot];
-//            the warp holds its 16 accumulators in registers.  A segment
-//            (st, zb) split between CTAs leaves one partial per CTA in
-//            consecutive gslots; the consumer plane kernel adds them.
+// Depth pairs.  Entries of depths 2p and 2p + 1 are interleaved as one
+// 16-byte word (re_2p, re_2p+1, im_2p, im_2p+1): T4[st][u][p][e], e < E =
+// 64 / GS, for slot tile st of 64 slots, bin u and depth pair p < Nzp =
+// ceil(Nz / 2) (a missing odd depth is zero).  One 16-byte shared-memory
+// load serves two depths.  In the adjoints its halves are packed pairs that
+// multiply duplicated residual spectra in the packed FP32 FMA (FFMA2, two
+// FMAs per instruction), with even- and odd-depth sums kept apart; the
+// forward uses scalar FMAs.  Lane l owns the slot pair (2l, 2l + 1), both in
+// orbit entry l / (GS / 2).
+//
 // Waits on the mbarriers are bounded (wait_ns of global time, 2 s unless the
 // operator sets another limit); a timeout sets *err, drains the copies
-// already issued (again bounded, by a fixed 0.5 s) and ends the warp.  With
-// `inject` set (failure-handling tests), each warp's first wait is made on a
-// per-warp barrier that nothing ever arrives at, so that path runs for real.
+// already issued (again bounded, by a fixed 0.5 s) and ends the warp or CTA.
+// With `inject` set (failure-handling tests), the first wait is made on a
+// barrier that nothing ever arrives at, so that path runs for real.
 // ---------------------------------------------------------------------------
 constexpr int kContractWarps = 8;
 constexpr int kContractThreads = kContractWarps * 32;
-constexpr int kRowsPerWarp = 16;
+constexpr int kRowsPerWarp = 16;                         // depths (8 pairs)
+constexpr int kPairsPerWarp = kRowsPerWarp / 2;
 constexpr int kZBlock = kContractWarps * kRowsPerWarp;  // 128 depths
+constexpr int kZPairs = kZBlock / 2;                     // 64 pairs
 constexpr int kSlots = 3;
 constexpr uint64_t kDrainNs = 500000000ull;  // bound of the post-timeout drain
 
-// (h.x + j h.y) times the two complex values of x, accumulated
-__device__ __forceinline__ void cmac_pair(float4& acc, const float2 h, const float4 x) {
-  acc.x = fmaf(h.x, x.x, acc.x); acc.x = fmaf(-h.y, x.y, acc.x);
-  acc.y = fmaf(h.x, x.y, acc.y); acc.y = fmaf(h.y, x.x, acc.y);
-  acc.z = fmaf(h.x, x.z, acc.z); acc.z = fmaf(-h.y, x.w, acc.z);
-  acc.w = fmaf(h.x, x.w, acc.w); acc.w = fmaf(h.y, x.z, acc.w);
-}
-// conj(h) times the two complex values of r, accumulated
-__device__ __forceinline__ void cmacc_pair(float4& acc, const float2 h, const float4 r) {
-  acc.x = fmaf(h.x, r.x, acc.x); acc.x = fmaf(h.y, r.y, acc.x);
-  acc.y = fmaf(h.x, r.y, acc.y); acc.y = fmaf(-h.y, r.x, acc.y);
-  acc.z = fmaf(h.x, r.z, acc.z); acc.z = fmaf(h.y, r.w, acc.z);
-  acc.w = fmaf(h.x, r.w, acc.w); acc.w = fmaf(-h.y, r.z, acc.w);
-}
+// Packed pairs of floats (one 64-bit register pair) and the packed FP32
+// arithmetic of sm_100 and later (one FFMA2 does two FMAs).
+typedef float2 f2x;
+__device__ __forceinline__ f2x pk(float lo, float hi) { return make_float2(lo, hi); }
+__device__ __forceinline__ float psum(f2x v) { return v.x + v.y; }
+__device__ __forceinline__ f2x ffma2(f2x a, f2x b, f2x c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2x fneg2(f2x a) { return make_float2(-a.x, -a.y); }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -567,17 +560,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   }
 }
 
-struct WarpRows {
-  int z0;   // first depth of the warp's rows in the unit's block
-  int n;    // rows (0..16)
-};
-__device__ __forceinline__ WarpRows warp_rows(int zb, int w, int Nz) {
-  WarpRows r;
-  r.z0 = zb * kZBlock + w * kRowsPerWarp;
-  r.n = min(kRowsPerWarp, max(0, Nz - r.z0));
-  return r;
-}
-
 // Position in the unit sequence (segment-major, bin group fastest), advanced
 // without divisions.
 struct UnitPos {
@@ -600,133 +582,177 @@ struct UnitPos {
   }
 };
 
-// Issue the bulk copies of this warp's rows of one unit (UP bins, each a
-// contiguous run of n rows of 8 E bytes) into a ring slot laid out
-// [UP][16][E].  The slot's mbarrier is always arrived on (zero bytes when the
-// warp has no rows in this depth block) so every slot completes one phase per
-// use.
-template <int GS>
-__device__ __forceinline__ void issue_unit(const float2* __restrict__ T, const UnitPos& p,
-                                           int Up, int Nz, int w, float2* slot, uint32_t bar) {
-  constexpr int E = kKappaTile / GS;
-  constexpr int UP = GS / 2;
-  const WarpRows wr = warp_rows(p.zb, w, Nz);
-  const uint32_t bytes = (uint32_t)wr.n * (E * 8u);
-  fence_proxy_async();
-  mbar_expect_tx(bar, bytes * UP);
-  if (bytes) {
-    const float2* src = T + ((size_t)(p.st * Up + p.ug * UP) * Nz + wr.z0) * E;
-#pragma unroll
-    for (int q = 0; q < UP; ++q)
-      bulk_g2s(smem_addr(slot + q * kRowsPerWarp * E), src + (size_t)q * Nz * E, bytes, bar);
-  }
+// A lane's spectra of its slot pair at two depths as packed pairs:
+// xr = (x_2p.re, x_2p+1.re), xi likewise, for slots a (2 lane) and b.
+struct PairX {
+  f2x ra, ia, rb, ib;
+};
+__device__ __forceinline__ PairX load_pair_x(const float4* __restrict__ Xh, size_t ns4, int st,
+                                             int lane, int z, int Nz) {
+  const float4 lo = z < Nz ? Xh[(size_t)z * ns4 + st * 32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 hi =
+      z + 1 < Nz ? Xh[(size_t)(z + 1) * ns4 + st * 32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  return PairX{pk(lo.x, hi.x), pk(lo.y, hi.y), pk(lo.z, hi.z), pk(lo.w, hi.w)};
 }
 
-// Drain the copies this warp has in flight (ring uses [from, to)).
-__device__ __forceinline__ void drain_warp(int from, int to, uint32_t bar0) {
-  for (int i = from; i < to; ++i)
-    mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, kDrainNs);
+// Accumulators of a lane's slot pair as packed pairs (adjoint): even depth
+// in .x, odd depth in .y.
+struct PairAcc {
+  f2x ra, ia, rb, ib;
+};
+
+// acc += h x for the two slots of a lane at one depth pair (forward), both
+// depths summed into one value: a = (re_a, im_a, re_b, im_b), h4 = (re_2p,
+// re_2p+1, im_2p, im_2p+1) one table word; real hr xr - hi xi, imag hr xi +
+// hi xr.  Scalar FMAs: with the spectra of 8 depth pairs held in registers
+// the packed form needs more registers than the 2-CTA budget leaves and
+// measured slower.
+__device__ __forceinline__ void fwd_mac(float4& a, const float4 h4, const PairX& x) {
+  a.x = fmaf(h4.x, x.ra.x, a.x); a.x = fmaf(-h4.z, x.ia.x, a.x);
+  a.x = fmaf(h4.y, x.ra.y, a.x); a.x = fmaf(-h4.w, x.ia.y, a.x);
+  a.y = fmaf(h4.x, x.ia.x, a.y); a.y = fmaf(h4.z, x.ra.x, a.y);
+  a.y = fmaf(h4.y, x.ia.y, a.y); a.y = fmaf(h4.w, x.ra.y, a.y);
+  a.z = fmaf(h4.x, x.rb.x, a.z); a.z = fmaf(-h4.z, x.ib.x, a.z);
+  a.z = fmaf(h4.y, x.rb.y, a.z); a.z = fmaf(-h4.w, x.ib.y, a.z);
+  a.w = fmaf(h4.x, x.ib.x, a.w); a.w = fmaf(h4.z, x.rb.x, a.w);
+  a.w = fmaf(h4.y, x.ib.y, a.w); a.w = fmaf(h4.w, x.rb.y, a.w);
+}
+__device__ __forceinline__ void zero_acc(float4& a) { a = make_float4(0.f, 0.f, 0.f, 0.f); }
+
+// Residual spectra of a lane's slot pair for one bin, duplicated into packed
+// pairs for the adjoint: rr = (r.re, r.re), ri = (r.im, r.im) for slots a, b.
+struct DupR {
+  f2x rra, ria, rrb, rib;
+};
+__device__ __forceinline__ DupR dup_r(const float4 r) {
+  return DupR{pk(r.x, r.x), pk(r.y, r.y), pk(r.z, r.z), pk(r.w, r.w)};
+}
+// acc += conj(h) r at one depth pair (adjoint): real hr rr + hi ri, imag hr ri - hi rr.
+__device__ __forceinline__ void adj_mac(PairAcc& a, const float4 h4, const DupR& r) {
+  const f2x hr = pk(h4.x, h4.y), hi = pk(h4.z, h4.w);
+  const f2x nhi = fneg2(hi);
+  a.ra = ffma2(hr, r.rra, a.ra);
+  a.ra = ffma2(hi, r.ria, a.ra);
+  a.ia = ffma2(hr, r.ria, a.ia);
+  a.ia = ffma2(nhi, r.rra, a.ia);
+  a.rb = ffma2(hr, r.rrb, a.rb);
+  a.rb = ffma2(hi, r.rib, a.rb);
+  a.ib = ffma2(hr, r.rib, a.ib);
+  a.ib = ffma2(nhi, r.rrb, a.ib);
+}
+__device__ __forceinline__ void zero_acc(PairAcc& a) {
+  a.ra = a.ia = a.rb = a.ib = make_float2(0.f, 0.f);
 }
 
-// Up = bins padded to a multiple of UP = GS / 2 (padding table rows are zero);
-// nunits = (Ns / 64) * nzb * (Up / UP).
+
+// Forward contraction.  Up = bins padded to a multiple of UP = GS / 2
+// (padding table rows are zero); nunits = (Ns / 64) * nzb * (Up / UP).
+// Work is cut into units (st, zb, bin group): UP bins of slot tile st over
+// the 128-depth block zb; a persistent CTA (two per SM) takes a contiguous,
+// equal share.  The 8 warps meet at a CTA barrier after every unit to add
+// their depth partials, so the ring is CTA-wide: stage s holds one unit (UP
+// bins x 64 depth pairs x E entries, 32 KB), refilled by one thread right
+// after the barrier that frees it, one bulk copy per bin (a bin's pairs of a
+// depth block are contiguous) and one mbarrier per stage.  Warp w consumes
+// pairs 8 w .. 8 w + 7 and keeps their spectra in registers.
+constexpr int kFwdStages = 3;
 template <int GS>
 __global__ void __launch_bounds__(kContractThreads, kContractCtasPerSm)
-contract_fwd_stream(const float2* __restrict__ T, const float4* __restrict__ Xh,
+contract_fwd_stream(const float4* __restrict__ T4, const float4* __restrict__ Xh,
                     float4* __restrict__ Yp, int Nz, int Up, int Ns, int nzb, int nunits,
                     int* __restrict__ err, uint64_t wait_ns, int inject) {
   constexpr int E = kKappaTile / GS;
   constexpr int UP = GS / 2;
-  constexpr int SLOT = UP * kRowsPerWarp * E;  // float2 per ring slot (4 KB)
+  constexpr int STAGE = UP * kZPairs * E;  // float4 per stage (32 KB)
   extern __shared__ __align__(128) float4 sm4[];
-  float4* red = sm4;                                        // [8][UP][32]
-  float2* ring = (float2*)(red + kContractWarps * UP * 32);  // [8][3][SLOT]
-  uint64_t* bars = (uint64_t*)(ring + kContractWarps * kSlots * SLOT);  // [8][4]
+  float4* red = sm4;                                      // [8][UP][32]
+  float4* ring = red + kContractWarps * UP * 32;          // [3][STAGE]
+  uint64_t* bars = (uint64_t*)(ring + kFwdStages * STAGE);  // [3] + never
   __shared__ int abort_flag;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int NUG = Up / UP;
+  const int Nzp = (Nz + 1) / 2;
   const int G = gridDim.x, b = blockIdx.x;
   const int first = (int)(((long long)nunits * b) / G);
   const int n = (int)(((long long)nunits * (b + 1)) / G) - first;
-  float2* my = ring + w * kSlots * SLOT;
-  const uint32_t bar0 = smem_addr(bars + w * (kSlots + 1));
-  const uint32_t never = bar0 + 8u * kSlots;  // nothing arrives here
+  const uint32_t bar0 = smem_addr(bars);
+  const uint32_t never = bar0 + 8u * kFwdStages;  // nothing arrives here
   const int ent = lane / (GS / 2);  // this lane's orbit entry in a row
-  if (threadIdx.x == 0) abort_flag = 0;
-  if (lane == 0) {
-    for (int s = 0; s <= kSlots; ++s) mbar_init(bar0 + 8u * s, 1);
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int k = 0; k <= kFwdStages; ++k) mbar_init(bar0 + 8u * k, 1);
     fence_mbar_init();
   }
   __syncthreads();
-  const size_t ns4 = (size_t)Ns / 2;
-  UnitPos ip;  // next unit to issue
+  UnitPos ip;
   ip.init(first, NUG, nzb);
-  int next_issue = 0;
-  for (; next_issue < kSlots - 1 && next_issue < n; ++next_issue, ip.next(NUG, nzb))
-    if (lane == 0)
-      issue_unit<GS>(T, ip, Up, Nz, w, my + (next_issue % kSlots) * SLOT,
-                     bar0 + 8u * (next_issue % kSlots));
+  auto issue = [&](int i) {
+    const int pairs = min(kZPairs, Nzp - ip.zb * kZPairs);
+    const uint32_t bytes = (uint32_t)pairs * (E * 16u);
+    const uint32_t bar = bar0 + 8u * (i % kFwdStages);
+    float4* stage = ring + (i % kFwdStages) * STAGE;
+    const float4* src = T4 + ((size_t)(ip.st * Up + ip.ug * UP) * Nzp + ip.zb * kZPairs) * E;
+    fence_proxy_async();
+    mbar_expect_tx(bar, bytes * UP);
+#pragma unroll
+    for (int q = 0; q < UP; ++q)
+      bulk_g2s(smem_addr(stage + q * kZPairs * E), src + (size_t)q * Nzp * E, bytes, bar);
+    ip.next(NUG, nzb);
+  };
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kFwdStages && i < n; ++i) issue(i);
   pdl_wait();  // Xh comes from the predecessor; the table copies above do not
   pdl_trigger();
+  const size_t ns4 = (size_t)Ns / 2;
   UnitPos cp;  // unit being computed
   cp.init(first, NUG, nzb);
-  float4 xr[kRowsPerWarp];
-  int cur_seg = -1;
-  WarpRows wr{0, 0};
+  PairX xr[kPairsPerWarp];
+  int cur_seg = -1, npw = 0;
   bool ok = true;
   int waited = 0;
   for (int i = 0; i < n; ++i, cp.next(NUG, nzb)) {
-    if (ok && next_issue < n) {  // refill the slot consumed in the previous unit
-      if (lane == 0)
-        issue_unit<GS>(T, ip, Up, Nz, w, my + (next_issue % kSlots) * SLOT,
-                       bar0 + 8u * (next_issue % kSlots));
-      ++next_issue;
-      ip.next(NUG, nzb);
-    }
-    if (cp.seg != cur_seg) {  // new (st, zb): this warp's Xh rows into registers
+    if (cp.seg != cur_seg) {  // new (st, zb): this warp's spectra into registers
       cur_seg = cp.seg;
-      wr = warp_rows(cp.zb, w, Nz);
+      const int p0 = cp.zb * kZPairs + w * kPairsPerWarp;
+      npw = min(kPairsPerWarp, max(0, Nzp - p0));
 #pragma unroll
-      for (int r = 0; r < kRowsPerWarp; ++r)
-        xr[r] = r < wr.n ? Xh[(size_t)(wr.z0 + r) * ns4 + cp.st * 32 + lane]
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int p = 0; p < kPairsPerWarp; ++p) xr[p] = load_pair_x(Xh, ns4, cp.st, lane, 2 * (p0 + p), Nz);
     }
     float4 acc[UP];
 #pragma unroll
-    for (int q = 0; q < UP; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (ok) {
-      const bool got = (inject && i == 0)
-                           ? mbar_wait_bounded(never, 0, wait_ns)
-                           : mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, wait_ns);
-      if (!got) {
-        ok = false;
-        if (lane == 0) {
-          atomicExch(err, 1);
-          abort_flag = 1;
-        }
+    for (int q = 0; q < UP; ++q) zero_acc(acc[q]);
+    const bool got = (inject && i == 0)
+                         ? mbar_wait_bounded(never, 0, wait_ns)
+                         : mbar_wait_bounded(bar0 + 8u * (i % kFwdStages), (i / kFwdStages) & 1,
+                                             wait_ns);
+    if (!got) {
+      ok = false;
+      if (lane == 0) {
+        atomicExch(err, 1);
+        abort_flag = 1;
+      }
+    } else {
+      waited = i + 1;
+      const float4* rows = ring + (i % kFwdStages) * STAGE + (size_t)w * kPairsPerWarp * E + ent;
+      if (npw == kPairsPerWarp) {
+#pragma unroll
+        for (int p = 0; p < kPairsPerWarp; ++p)
+#pragma unroll
+          for (int q = 0; q < UP; ++q) fwd_mac(acc[q], rows[(q * kZPairs + p) * E], xr[p]);
       } else {
-        waited = i + 1;
-        const float2* slot = my + (i % kSlots) * SLOT + ent;
-        if (wr.n == kRowsPerWarp) {
 #pragma unroll
-          for (int r = 0; r < kRowsPerWarp; ++r)
+        for (int p = 0; p < kPairsPerWarp; ++p)
+          if (p < npw)
 #pragma unroll
-            for (int q = 0; q < UP; ++q) cmac_pair(acc[q], slot[(q * kRowsPerWarp + r) * E], xr[r]);
-        } else {
-#pragma unroll
-          for (int r = 0; r < kRowsPerWarp; ++r)
-            if (r < wr.n)
-#pragma unroll
-              for (int q = 0; q < UP; ++q)
-                cmac_pair(acc[q], slot[(q * kRowsPerWarp + r) * E], xr[r]);
-        }
+            for (int q = 0; q < UP; ++q) fwd_mac(acc[q], rows[(q * kZPairs + p) * E], xr[p]);
       }
     }
-    __syncwarp();
 #pragma unroll
-    for (int q = 0; q < UP; ++q) red[(w * UP + q) * 32 + lane] = acc[q];
-    __syncthreads();
+    for (int q = 0; q < UP; ++q)
+      red[(w * UP + q) * 32 + lane] = acc[q];
+    __syncthreads();  // partials written; every warp is done with stage i
     if (abort_flag) ok = false;
+    if (ok && threadIdx.x == 0 && i + kFwdStages < n) issue(i + kFwdStages);
     if (w < UP && ok) {  // warp q adds the 8 partials of bin ug*UP + q
       float4 sum = red[w * 32 + lane];
 #pragma unroll
@@ -736,29 +762,69 @@ contract_fwd_stream(const float2* __restrict__ T, const float4* __restrict__ Xh,
       }
       Yp[((size_t)cp.zb * Up + cp.ug * UP + w) * ns4 + cp.st * 32 + lane] = sum;
     }
-    __syncthreads();
+    __syncthreads();  // red free for the next unit
     if (!ok) break;
   }
-  if (!ok) drain_warp(waited, next_issue, bar0);
+  if (!ok && threadIdx.x == 0) {  // drain the units issued but not waited for
+    const int issued = min(n, waited + kFwdStages);
+    for (int k = waited; k < issued; ++k)
+      mbar_wait_bounded(bar0 + 8u * (k % kFwdStages), (k / kFwdStages) & 1, kDrainNs);
+  }
+}
+
+// Adjoint contraction with partial sums (used when the segment-aligned
+// variant below does not fit): units (st, zb, bin group) as in the forward,
+// a contiguous share per CTA; warp w owns depth pairs 8 w .. 8 w + 7 of the
+// block and streams its part of every unit (UP bins x 8 pairs x E, 4 KB)
+// through its own 3-slot ring, filled by its lane 0 with one bulk copy per
+// bin and tracked by one mbarrier per slot (always arrived on, with zero
+// bytes when the warp has no pairs, so every slot completes one phase per
+// use).  It accumulates Gs[gslot][z][slot % 64] = sum over the CTA's bins of
+// conj(T) Rh[u][slot] in registers; a segment (st, zb) split between CTAs
+// leaves one partial per CTA in consecutive gslots, which the consumer adds.
+template <int GS>
+__device__ __forceinline__ void issue_adj_unit(const float4* __restrict__ T4, const UnitPos& p,
+                                               int Up, int Nzp, int w, float4* slot,
+                                               uint32_t bar) {
+  constexpr int E = kKappaTile / GS;
+  constexpr int UP = GS / 2;
+  const int p0 = p.zb * kZPairs + w * kPairsPerWarp;
+  const int np = min(kPairsPerWarp, max(0, Nzp - p0));
+  const uint32_t bytes = (uint32_t)np * (E * 16u);
+  fence_proxy_async();
+  mbar_expect_tx(bar, bytes * UP);
+  if (bytes) {
+    const float4* src = T4 + ((size_t)(p.st * Up + p.ug * UP) * Nzp + p0) * E;
+#pragma unroll
+    for (int q = 0; q < UP; ++q)
+      bulk_g2s(smem_addr(slot + q * kPairsPerWarp * E), src + (size_t)q * Nzp * E, bytes, bar);
+  }
+}
+
+// Drain the copies this warp has in flight (ring uses [from, to)).
+__device__ __forceinline__ void drain_warp(int from, int to, uint32_t bar0) {
+  for (int i = from; i < to; ++i)
+    mbar_wait_bounded(bar0 + 8u * (i % kSlots), (i / kSlots) & 1, kDrainNs);
 }
 
 template <int GS>
 __global__ void __launch_bounds__(kContractThreads, kContractCtasPerSm)
-contract_adj_stream(const float2* __restrict__ T, const float4* __restrict__ Rh,
+contract_adj_stream(const float4* __restrict__ T4, const float4* __restrict__ Rh,
                     float4* __restrict__ Gs, int Nz, int Up, int Ns, int nzb, int nunits,
                     int* __restrict__ err, uint64_t wait_ns, int inject) {
   constexpr int E = kKappaTile / GS;
   constexpr int UP = GS / 2;
-  constexpr int SLOT = UP * kRowsPerWarp * E;
+  constexpr int SLOT = UP * kPairsPerWarp * E;  // float4 per slot (4 KB)
   extern __shared__ __align__(128) float4 sm4[];
-  float2* ring = (float2*)sm4;
+  float4* ring = sm4;
   uint64_t* bars = (uint64_t*)(ring + kContractWarps * kSlots * SLOT);  // [8][4]
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int NUG = Up / UP;
+  const int Nzp = (Nz + 1) / 2;
   const int G = gridDim.x, b = blockIdx.x;
   const int first = (int)(((long long)nunits * b) / G);
   const int n = (int)(((long long)nunits * (b + 1)) / G) - first;
-  float2* my = ring + w * kSlots * SLOT;
+  float4* my = ring + w * kSlots * SLOT;
   const uint32_t bar0 = smem_addr(bars + w * (kSlots + 1));
   const uint32_t never = bar0 + 8u * kSlots;  // nothing arrives here
   const int ent = lane / (GS / 2);
@@ -773,32 +839,33 @@ contract_adj_stream(const float2* __restrict__ T, const float4* __restrict__ Rh,
   int next_issue = 0;
   for (; next_issue < kSlots - 1 && next_issue < n; ++next_issue, ip.next(NUG, nzb))
     if (lane == 0)
-      issue_unit<GS>(T, ip, Up, Nz, w, my + (next_issue % kSlots) * SLOT,
-                     bar0 + 8u * (next_issue % kSlots));
+      issue_adj_unit<GS>(T4, ip, Up, Nzp, w, my + (next_issue % kSlots) * SLOT,
+                         bar0 + 8u * (next_issue % kSlots));
   pdl_wait();  // Rh comes from the predecessor; the table copies above do not
   pdl_trigger();
   // Rh rows of the next unit prefetched into registers
   UnitPos rp;
   rp.init(first, NUG, nzb);
-  auto load_rh = [&](float4* dst, const UnitPos& p, bool valid) {
+  auto load_rh = [&](float4* dst, const UnitPos& q0, bool valid) {
 #pragma unroll
     for (int q = 0; q < UP; ++q)
-      dst[q] = valid ? Rh[(size_t)(p.ug * UP + q) * ns4 + p.st * 32 + lane]
+      dst[q] = valid ? Rh[(size_t)(q0.ug * UP + q) * ns4 + q0.st * 32 + lane]
                      : make_float4(0.f, 0.f, 0.f, 0.f);
   };
   float4 rnext[UP];
   load_rh(rnext, rp, n > 0);
   UnitPos cp;
   cp.init(first, NUG, nzb);
-  WarpRows wr = warp_rows(cp.zb, w, Nz);
-  float4 acc[kRowsPerWarp];
+  int p0 = cp.zb * kZPairs + w * kPairsPerWarp;
+  int npw = min(kPairsPerWarp, max(0, Nzp - p0));
+  PairAcc acc[kPairsPerWarp];
 #pragma unroll
-  for (int r = 0; r < kRowsPerWarp; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int p = 0; p < kPairsPerWarp; ++p) zero_acc(acc[p]);
   for (int i = 0; i < n; ++i) {
     if (next_issue < n) {
       if (lane == 0)
-        issue_unit<GS>(T, ip, Up, Nz, w, my + (next_issue % kSlots) * SLOT,
-                       bar0 + 8u * (next_issue % kSlots));
+        issue_adj_unit<GS>(T4, ip, Up, Nzp, w, my + (next_issue % kSlots) * SLOT,
+                           bar0 + 8u * (next_issue % kSlots));
       ++next_issue;
       ip.next(NUG, nzb);
     }
@@ -815,33 +882,38 @@ contract_adj_stream(const float2* __restrict__ T, const float4* __restrict__ Rh,
       drain_warp(i, next_issue, bar0);
       return;
     }
-    const float2* slot = my + (i % kSlots) * SLOT + ent;
-    if (wr.n == kRowsPerWarp) {
+    const float4* slot = my + (i % kSlots) * SLOT + ent;
 #pragma unroll
-      for (int r = 0; r < kRowsPerWarp; ++r)
+    for (int q = 0; q < UP; ++q) {
+      const DupR r = dup_r(rr[q]);
+      if (npw == kPairsPerWarp) {
 #pragma unroll
-        for (int q = 0; q < UP; ++q) cmacc_pair(acc[r], slot[(q * kRowsPerWarp + r) * E], rr[q]);
-    } else if (wr.n > 0) {
+        for (int p = 0; p < kPairsPerWarp; ++p) adj_mac(acc[p], slot[(q * kPairsPerWarp + p) * E], r);
+      } else {
 #pragma unroll
-      for (int r = 0; r < kRowsPerWarp; ++r)
-        if (r < wr.n)
-#pragma unroll
-          for (int q = 0; q < UP; ++q)
-            cmacc_pair(acc[r], slot[(q * kRowsPerWarp + r) * E], rr[q]);
+        for (int p = 0; p < kPairsPerWarp; ++p)
+          if (p < npw) adj_mac(acc[p], slot[(q * kPairsPerWarp + p) * E], r);
+      }
     }
     __syncwarp();
     const int seg = cp.seg;
     cp.next(NUG, nzb);
     if (i + 1 == n || cp.seg != seg) {  // end of this CTA's part of segment seg
-      if (wr.n > 0) {
+      if (npw > 0) {
         float4* dst = Gs + ((size_t)(seg + b) * kZBlock + w * kRowsPerWarp) * 32 + lane;
 #pragma unroll
-        for (int r = 0; r < kRowsPerWarp; ++r)
-          if (r < wr.n) dst[r * 32] = acc[r];
+        for (int p = 0; p < kPairsPerWarp; ++p) {
+          if (p < npw) {
+            const float2 ra = acc[p].ra, ia = acc[p].ia, rb = acc[p].rb, ib = acc[p].ib;
+            dst[(2 * p) * 32] = make_float4(ra.x, ia.x, rb.x, ib.x);
+            dst[(2 * p + 1) * 32] = make_float4(ra.y, ia.y, rb.y, ib.y);
+          }
+        }
       }
 #pragma unroll
-      for (int r = 0; r < kRowsPerWarp; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-      wr = warp_rows(cp.zb, w, Nz);
+      for (int p = 0; p < kPairsPerWarp; ++p) zero_acc(acc[p]);
+      p0 = cp.zb * kZPairs + w * kPairsPerWarp;
+      npw = min(kPairsPerWarp, max(0, Nzp - p0));
     }
   }
 }
@@ -850,30 +922,32 @@ contract_adj_stream(const float2* __restrict__ T, const float4* __restrict__ Rh,
 // zb), all bins, so each output value is summed by exactly one warp and the
 // result is dense (Gs[seg][32][64] = Ghat[z][slot] in tile order): no partial
 // sums.  Chosen when the number of such segments fits the resident grid.
-// Warp w owns depths zb*32 + 4w .. +3.  The slot tile's residual spectra
-// Rh[.][st] for all bins are staged once in shared memory; the table streams
-// through a 2-slot ring per warp, each slot holding 2 GS bins x 4 rows
-// (4 KB), filled by cp.async.bulk (one copy per bin, issued by one lane per
-// bin) and tracked by one mbarrier per slot.
-constexpr int kSegRows = 4;    // depths per warp
-constexpr int kSegSlots = 2;   // ring slots per warp
+// Warp w owns depths zb*32 + 4w .. +3 (two depth pairs).  The slot tile's
+// residual spectra Rh[.][st] for all bins are staged once in shared memory;
+// the table streams through a 2-slot ring per warp, each slot holding 2 GS
+// bins x 2 depth pairs (4 KB), filled by cp.async.bulk (one copy per bin,
+// issued by one lane per bin) and tracked by one mbarrier per slot.
+constexpr int kSegRows = 4;                // depths per warp
+constexpr int kSegPairs = kSegRows / 2;    // depth pairs per warp
+constexpr int kSegSlots = 2;               // ring slots per warp
 template <int GS>
 __global__ void __launch_bounds__(kContractThreads, kContractCtasPerSm)
-contract_adj_seg(const float2* __restrict__ T, const float4* __restrict__ Rh,
+contract_adj_seg(const float4* __restrict__ T4, const float4* __restrict__ Rh,
                  float4* __restrict__ Gs, int Nz, int Up, int Ns, int anzb,
                  int* __restrict__ err, uint64_t wait_ns, int inject) {
   constexpr int E = kKappaTile / GS;
   constexpr int UPA = 2 * GS;                   // bins per ring slot
-  constexpr int SLOT = UPA * kSegRows * E;      // float2 per slot (4 KB)
+  constexpr int SLOT = UPA * kSegPairs * E;     // float4 per slot (4 KB)
   extern __shared__ __align__(128) float4 sm4[];
   float4* rtile = sm4;                                          // [Up][32]
-  float2* ring = (float2*)(rtile + (size_t)Up * 32);            // [8][2][SLOT]
+  float4* ring = rtile + (size_t)Up * 32;                       // [8][2][SLOT]
   uint64_t* bars = (uint64_t*)(ring + kContractWarps * kSegSlots * SLOT);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int seg = blockIdx.x;
   const int st = seg / anzb, zb = seg - st * anzb;
+  const int Nzp = (Nz + 1) / 2;
   const size_t ns4 = (size_t)Ns / 2;
-  float2* my = ring + w * kSegSlots * SLOT;
+  float4* my = ring + w * kSegSlots * SLOT;
   const uint32_t bar0 = smem_addr(bars + w * (kSegSlots + 1));
   const uint32_t never = bar0 + 8u * kSegSlots;  // nothing arrives here
   if (lane == 0) {
@@ -881,14 +955,14 @@ contract_adj_seg(const float2* __restrict__ T, const float4* __restrict__ Rh,
     fence_mbar_init();
   }
   __syncthreads();
-  const int z0 = zb * (kContractWarps * kSegRows) + w * kSegRows;
-  const int n = min(kSegRows, max(0, Nz - z0));
+  const int p0 = zb * (kContractWarps * kSegPairs) + w * kSegPairs;  // first global pair
+  const int np = min(kSegPairs, max(0, Nzp - p0));
   const int ent = lane / (GS / 2);
   const int nch = (Up + UPA - 1) / UPA;
-  const uint32_t bin_bytes = (uint32_t)n * E * 8u;
+  const uint32_t bin_bytes = (uint32_t)np * E * 16u;
   auto issue = [&](int c) {
     const int nb = min(UPA, Up - c * UPA);
-    float2* slot = my + (c % kSegSlots) * SLOT;
+    float4* slot = my + (c % kSegSlots) * SLOT;
     const uint32_t bar = bar0 + 8u * (c % kSegSlots);
     if (lane == 0) {
       fence_proxy_async();
@@ -896,8 +970,8 @@ contract_adj_seg(const float2* __restrict__ T, const float4* __restrict__ Rh,
     }
     __syncwarp();
     if (bin_bytes && lane < nb) {
-      const float2* src = T + ((size_t)(st * Up + c * UPA + lane) * Nz + z0) * E;
-      bulk_g2s(smem_addr(slot + lane * kSegRows * E), src, bin_bytes, bar);
+      const float4* src = T4 + ((size_t)(st * Up + c * UPA + lane) * Nzp + p0) * E;
+      bulk_g2s(smem_addr(slot + lane * kSegPairs * E), src, bin_bytes, bar);
     }
   };
   for (int c = 0; c < kSegSlots - 1 && c < nch; ++c) issue(c);
@@ -906,9 +980,9 @@ contract_adj_seg(const float2* __restrict__ T, const float4* __restrict__ Rh,
   for (int i = threadIdx.x; i < Up * 32; i += kContractThreads)
     rtile[i] = Rh[(size_t)(i >> 5) * ns4 + st * 32 + (i & 31)];
   __syncthreads();
-  float4 acc[kSegRows];
+  PairAcc acc[kSegPairs];
 #pragma unroll
-  for (int r = 0; r < kSegRows; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int p = 0; p < kSegPairs; ++p) zero_acc(acc[p]);
   for (int c = 0; c < nch; ++c) {
     if (c + kSegSlots - 1 < nch) issue(c + kSegSlots - 1);
     const bool got = (inject && c == 0)
@@ -920,32 +994,32 @@ contract_adj_seg(const float2* __restrict__ T, const float4* __restrict__ Rh,
         mbar_wait_bounded(bar0 + 8u * (k % kSegSlots), (k / kSegSlots) & 1, kDrainNs);
       return;
     }
-    const float2* slot = my + (c % kSegSlots) * SLOT + ent;
+    const float4* slot = my + (c % kSegSlots) * SLOT + ent;
     const int nb = min(UPA, Up - c * UPA);
-    if (n == kSegRows) {
 #pragma unroll
-      for (int q = 0; q < UPA; ++q)
-        if (q < nb) {
-          const float4 rr = rtile[(c * UPA + q) * 32 + lane];
+    for (int q = 0; q < UPA; ++q)
+      if (q < nb) {
+        const DupR r = dup_r(rtile[(c * UPA + q) * 32 + lane]);
+        if (np == kSegPairs) {
 #pragma unroll
-          for (int r = 0; r < kSegRows; ++r) cmacc_pair(acc[r], slot[(q * kSegRows + r) * E], rr);
+          for (int p = 0; p < kSegPairs; ++p) adj_mac(acc[p], slot[(q * kSegPairs + p) * E], r);
+        } else {
+#pragma unroll
+          for (int p = 0; p < kSegPairs; ++p)
+            if (p < np) adj_mac(acc[p], slot[(q * kSegPairs + p) * E], r);
         }
-    } else {
-#pragma unroll
-      for (int q = 0; q < UPA; ++q)
-        if (q < nb) {
-          const float4 rr = rtile[(c * UPA + q) * 32 + lane];
-#pragma unroll
-          for (int r = 0; r < kSegRows; ++r)
-            if (r < n) cmacc_pair(acc[r], slot[(q * kSegRows + r) * E], rr);
-        }
-    }
+      }
     __syncwarp();
   }
+  // rows 4 w .. 4 w + 3 of the segment: depths 2 (p0 + p) and 2 (p0 + p) + 1
   float4* dst = Gs + ((size_t)seg * (kContractWarps * kSegRows) + w * kSegRows) * 32 + lane;
 #pragma unroll
-  for (int r = 0; r < kSegRows; ++r)
-    if (r < n) dst[r * 32] = acc[r];
+  for (int p = 0; p < kSegPairs; ++p) {
+    const int z = 2 * (p0 + p);
+    const float2 ra = acc[p].ra, ia = acc[p].ia, rb = acc[p].rb, ib = acc[p].ib;
+    if (z < Nz) dst[(2 * p) * 32] = make_float4(ra.x, ia.x, rb.x, ib.x);
+    if (z + 1 < Nz) dst[(2 * p + 1) * 32] = make_float4(ra.y, ia.y, rb.y, ib.y);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1174,13 +1248,15 @@ int contract_units(const PlaneDims& d) {
   return (d.Ns / kKappaTile) * d.nzb * (d.Up / (d.GS / 2));
 }
 
+
 namespace {
-// ring slot: (GS / 2) bins x 16 rows x (64 / GS) entries x 8 bytes = 4 KB
+// ring slot of the adjoints: (GS / 2) bins x 8 depth pairs (stream) or 2 GS
+// bins x 2 depth pairs (segment-aligned), x (64 / GS) entries x 16 bytes = 4 KB
 constexpr size_t kRingSlotBytes = 4096;
 template <int GS>
 size_t contract_fwd_smem() {
   return (size_t)kContractWarps * (GS / 2) * 32 * 16 +
-         (size_t)kContractWarps * kSlots * kRingSlotBytes + kContractWarps * (kSlots + 1) * 8;
+         (size_t)kFwdStages * (GS / 2) * kZPairs * (kKappaTile / GS) * 16 + (kFwdStages + 1) * 8;
 }
 template <int GS>
 size_t contract_adj_smem() {
@@ -1193,9 +1269,9 @@ int launch_fwd_gs(const PlaneDims& d, const float2* table, const float2* Xh, flo
   SFS_TRY(ensure_smem_attr(contract_fwd_stream<GS>, (int)smem));
   const int n = contract_units(d);
   const int G = std::min(d.G, n);
-  return launch_pdl(contract_fwd_stream<GS>, dim3(G), dim3(kContractThreads), smem, st, table,
-                    (const float4*)Xh, (float4*)Yp, d.Nz, d.Up, d.Ns, d.nzb, n, err, d.wait_ns,
-                    d.inject);
+  return launch_pdl(contract_fwd_stream<GS>, dim3(G), dim3(kContractThreads), smem, st,
+                    (const float4*)table, (const float4*)Xh, (float4*)Yp, d.Nz, d.Up, d.Ns, d.nzb, n,
+                    err, d.wait_ns, d.inject);
 }
 template <int GS>
 int launch_adj_gs(const PlaneDims& d, const float2* table, const float2* Rh, float2* Gs,
@@ -1204,8 +1280,8 @@ int launch_adj_gs(const PlaneDims& d, const float2* table, const float2* Rh, flo
   SFS_TRY(ensure_smem_attr(contract_adj_stream<GS>, (int)smem));
   const int n = contract_units(d);
   const int G = std::min(d.G, n);
-  return launch_pdl(contract_adj_stream<GS>, dim3(G), dim3(kContractThreads), smem, st, table,
-                    (const float4*)Rh, (float4*)Gs, d.Nz, d.Up, d.Ns, d.nzb, n, err, d.wait_ns,
+  return launch_pdl(contract_adj_stream<GS>, dim3(G), dim3(kContractThreads), smem, st,
+                    (const float4*)table, (const float4*)Rh, (float4*)Gs, d.Nz, d.Up, d.Ns, d.nzb, n, err, d.wait_ns,
                     d.inject);
 }
 }  // namespace
@@ -1231,8 +1307,8 @@ int launch_adj_seg_gs(const PlaneDims& d, const float2* table, const float2* Rh,
                       int* err, cudaStream_t st) {
   const size_t smem = contract_adj_seg_smem<GS>(d.Up);
   SFS_TRY(ensure_smem_attr(contract_adj_seg<GS>, (int)smem));
-  return launch_pdl(contract_adj_seg<GS>, dim3(d.Ga), dim3(kContractThreads), smem, st, table,
-                    (const float4*)Rh, (float4*)Gs, d.Nz, d.Up, d.Ns, d.anzb, err, d.wait_ns,
+  return launch_pdl(contract_adj_seg<GS>, dim3(d.Ga), dim3(kContractThreads), smem, st,
+                    (const float4*)table, (const float4*)Rh, (float4*)Gs, d.Nz, d.Up, d.Ns, d.anzb, err, d.wait_ns,
                     d.inject);
 }
 
