@@ -222,6 +222,8 @@ PlaneDims operator_dims(const sfs_operator* op) {
   d.Ns = op->Ns;
   d.GS = op->GS;
   d.Up = op->Up;
+  d.tc = op->tc;
+  d.nzc = op->nzc;
   d.adj_seg = op->adj_seg;
   d.azb = op->azb;
   d.anzb = op->anzb;
@@ -236,6 +238,15 @@ PlaneDims operator_dims(const sfs_operator* op) {
 namespace {
 
 PlaneDims dims_of(const sfs_operator* op) { return operator_dims(op); }
+
+// Generator table size in c64 entries.  CUDA-core layout: depth pairs of
+// Nz rounded up to even, Up rows per slot tile of 64; tensor-core layout:
+// 16-depth blocks, U rows per orbit.
+size_t table_c64(const sfs_operator* op) {
+  const size_t No = (size_t)(op->Ns / op->GS);
+  if (op->tc) return No * op->nzc * 16 * op->U;
+  return No * op->Up * (size_t)((op->geo.d.Nz + 1) / 2 * 2);
+}
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -616,17 +627,27 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
     cudaError_t e0 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d.device);
     if (e0 != cudaSuccess) return fail(cuda_fail(e0, "SM count query", __FILE__, __LINE__));
   }
+  // Contractions on the tensor cores unless SFS_CONTRACT=cuda selects the
+  // CUDA-core kernels (read per operator).
+  {
+    const char* cv = getenv("SFS_CONTRACT");
+    op->tc = !(cv && strcmp(cv, "cuda") == 0);
+  }
+  op->nzc = (d.Nz + 15) / 16;
+  if (op->tc) op->nzb = 1;
   const int nseg = (op->Ns / kKappaTile) * op->nzb;
   const int ngroups = op->Up / (op->GS / 2);
-  op->G = std::max(1, std::min(sms * kContractCtasPerSm, nseg * ngroups));
+  op->G = op->tc ? sms * kContractCtasPerSm
+                 : std::max(1, std::min(sms * kContractCtasPerSm, nseg * ngroups));
   // Adjoint: one CTA per (slot tile, 32-depth block) when those segments fit
   // the resident grid and the tile's spectra fit beside the ring (dense
   // result); otherwise CTAs share segments and leave partial sums.
   const int anzb32 = (d.Nz + 31) / 32;
   const int nseg32 = (op->Ns / kKappaTile) * anzb32;
   std::vector<int2> segslot;
-  if (nseg32 <= sms * kContractCtasPerSm &&
-      adj_seg_smem_bytes(op->Up) * kContractCtasPerSm + 2048 <= (size_t)max_smem_optin() + 1024) {
+  if (op->tc || (nseg32 <= sms * kContractCtasPerSm &&
+                 adj_seg_smem_bytes(op->Up) * kContractCtasPerSm + 2048 <=
+                     (size_t)max_smem_optin() + 1024)) {
     op->adj_seg = 1;
     op->azb = 32;
     op->anzb = anzb32;
@@ -643,8 +664,7 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
     segslot = segment_slots(nseg, ngroups, op->G);
   }
   const size_t Ns = op->Ns;
-  // depth pairs interleaved: Nz rounded up to even (the odd padding is zero)
-  const size_t table_elems = Ns / op->GS * op->Up * (size_t)((d.Nz + 1) / 2 * 2);
+  const size_t table_elems = table_c64(op);
   if ((rc = dev_alloc(&op->table, table_elems)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->posmap, posmap.size())) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.Xh, Ns * d.Nz)) != SFS_OK) return fail(rc);
@@ -749,7 +769,7 @@ int sfs_operator_info(const sfs_operator* op, sfs_operator_info_t* info) {
   info->band_db = op->band_db;
   info->alpha = op->geo.alpha;
   info->t0 = op->geo.d.t0;
-  info->table_bytes = (int64_t)(op->Ns / op->GS) * op->Up * ((op->geo.d.Nz + 1) / 2 * 2) * 8;
+  info->table_bytes = (int64_t)table_c64(op) * 8;
   info->launches_per_iter = 4;
   info->Nslot = op->Ns;
   info->GS = op->GS;

@@ -86,6 +86,8 @@ struct sfs_operator {
   int M = 0, S = 0, V = 0, U = 0, Nk = 0;
   int Ns = 0, GS = 0, No = 0;  // wavenumber slots, slots per orbit, orbits
   int Up = 0;                  // bins padded to a multiple of GS / 2
+  int tc = 0;                  // contractions on the tensor cores (sfs_tc.cu)
+  int nzc = 0;                 // depth blocks of 16 in the tensor-core table
   int nzb = 1;                 // depth blocks of <= 128 in the contractions
   int G = 1;                   // persistent CTAs of the contractions
   int nslots = 0;              // adjoint partial-sum slots
@@ -97,8 +99,10 @@ struct sfs_operator {
   std::vector<int32_t> idx;    // [S][M]
   std::vector<int32_t> bins;   // [U] union of kept bins, ascending
   // device data
-  float2* table = nullptr;     // [Ns/64][Up][Nz][64/GS] c64, one entry per symmetry
-                               // orbit of wavenumbers, includes 1/(Px*Py)
+  float2* table = nullptr;     // one entry per symmetry orbit of wavenumbers per
+                               // (bin, depth), includes 1/(Px*Py); depth pairs
+                               // interleaved, layout per contraction path
+                               // (sfs_kernels.cu / sfs_tc.cu)
   int32_t* slot_kappa = nullptr;  // [Ns]
   int32_t* orbit_rep = nullptr;   // [Ns/GS]
   int32_t* posmap = nullptr;   // [U][S]: m with idx[s][m] == bins[u], else -1
@@ -128,6 +132,9 @@ struct PlaneDims {
   int Ns;   // wavenumber slots (orbit-major, a multiple of 64)
   int GS;   // slots per symmetry orbit: 2 (line), 4 (area), 8 (square area)
   int Up;   // bins padded to a multiple of GS / 2 (zero table rows and spectra)
+  int tc;   // contractions on the tensor cores: table in the layout of sfs_tc.cu,
+            // nzb = 1 and the dense segment-aligned adjoint result
+  int nzc;  // depth blocks of 16 of the tensor-core table
   int adj_seg;  // adjoint by segment-aligned CTAs (dense result) instead of partial sums
   int azb;      // depth rows per adjoint segment (32 segment-aligned, 128 otherwise)
   int anzb;     // adjoint depth blocks per slot tile
@@ -183,6 +190,13 @@ int launch_contract_fwd(const PlaneDims& d, const float2* table, const float2* X
                         float2* Yp, int* err, cudaStream_t st);
 int launch_contract_adj(const PlaneDims& d, const float2* table, const float2* Rh,
                         float2* Gs, int* err, cudaStream_t st);
+
+// The same two contractions on the tensor cores (sfs_tc.cu); used when d.tc.
+int launch_contract_fwd_tc(const PlaneDims& d, const float2* table, const float2* Xh,
+                           float2* Yp, int* err, cudaStream_t st);
+int launch_contract_adj_tc(const PlaneDims& d, const float2* table, const float2* Rh,
+                           float2* Gs, int* err, cudaStream_t st);
+int prepare_tc_kernels();
 
 // Small helpers.
 int launch_set_thresholds(float* scal, double* red, double lambda, double L,

@@ -23,28 +23,13 @@
 #include <utility>
 #include <unordered_map>
 
+#include "sfs_async.cuh"
 #include "sfs_fft.cuh"
 #include "sfs_internal.h"
+#include "sfs_launch.h"
 
 namespace sfs {
 namespace {
-
-// ---------------------------------------------------------------------------
-// Programmatic dependent launch.  The kernels of the FISTA loop are launched
-// so that the next one may start while the current one drains.  Each kernel
-// does only work independent of its predecessor (shared-memory set-up,
-// twiddles, first bulk copies of the constant table) before pdl_wait(), which
-// returns once the predecessor grid has completed and its writes are
-// visible; it then allows its own successor to launch.  Since a kernel lets
-// its successor start only after its own wait, at most two grids overlap,
-// and the successor's early work never touches data of the kernels before.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void pdl_wait() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-__device__ __forceinline__ void pdl_trigger() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
 
 // ---------------------------------------------------------------------------
 // Block reductions
@@ -138,13 +123,16 @@ build_table_kernel(PlaneDims d, const float2* __restrict__ tof,
   // representative.  Orbit o lives in slot tile o / E, entry o % E.
   // Depths 2p and 2p + 1 share one 16-byte word (re_2p, re_2p+1, im_2p,
   // im_2p+1): T4[st][u][p][e] with e < E = 64 / GS.
+  // The tensor-core contractions use words ((o nzc + z/16) U + u) 8 + ((z%16)/2
+  // xor u%8), one orbit's rows per 16-depth block (sfs_tc.cu).
   const int E = kKappaTile / d.GS;
   const int Nzp = (d.Nz + 1) / 2;
   float* tf = (float*)table;
   for (int o = threadIdx.x; o < d.Ns / d.GS; o += F::NT) {
     const int rep = d.orbit_rep[o];
     const float2 v = rep >= 0 ? buf[F::kidx(rep)] : make_float2(0.f, 0.f);
-    const size_t w4 = (((size_t)(o / E) * d.Up + u) * Nzp + z / 2) * E + (o % E);
+    const size_t w4 = d.tc ? (((size_t)o * d.nzc + (z >> 4)) * d.U + u) * 8 + (((z & 15) >> 1) ^ (u & 7))
+                           : (((size_t)(o / E) * d.Up + u) * Nzp + z / 2) * E + (o % E);
     tf[4 * w4 + (z & 1)] = v.x;
     tf[4 * w4 + 2 + (z & 1)] = v.y;
   }
@@ -501,64 +489,13 @@ constexpr int kPairsPerWarp = kRowsPerWarp / 2;
 constexpr int kZBlock = kContractWarps * kRowsPerWarp;  // 128 depths
 constexpr int kZPairs = kZBlock / 2;                     // 64 pairs
 constexpr int kSlots = 3;
-constexpr uint64_t kDrainNs = 500000000ull;  // bound of the post-timeout drain
 
 // Packed pairs of floats (one 64-bit register pair) and the packed FP32
 // arithmetic of sm_100 and later (one FFMA2 does two FMAs).
 typedef float2 f2x;
 __device__ __forceinline__ f2x pk(float lo, float hi) { return make_float2(lo, hi); }
-__device__ __forceinline__ float psum(f2x v) { return v.x + v.y; }
 __device__ __forceinline__ f2x ffma2(f2x a, f2x b, f2x c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ f2x fneg2(f2x a) { return make_float2(-a.x, -a.y); }
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
-                                         uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Bounded wait for phase `parity` of the mbarrier; false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (true) {
-    for (int i = 0; i < 64; ++i)
-      if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > limit_ns) return false;
-  }
-}
 
 // Position in the unit sequence (segment-major, bin group fastest), advanced
 // without divisions.
@@ -1087,67 +1024,6 @@ __global__ void scale_rnorm_kernel(float2* v, int n, const double* sumsq) {
 // ---------------------------------------------------------------------------
 // Dispatch on the plane size
 // ---------------------------------------------------------------------------
-// Raise a kernel's dynamic shared memory limit to what the device allows next
-// to the kernel's static shared memory, once per (kernel, device); each
-// launch then asks for what it needs.
-int ensure_smem_attr_ptr(const void* kernel, int need) {
-  int dev = 0;
-  SFS_CUDA(cudaGetDevice(&dev));
-  static std::mutex mu;
-  static std::unordered_map<const void*, uint64_t> done;  // kernel -> device bits
-  std::lock_guard<std::mutex> lock(mu);
-  uint64_t& bits = done[kernel];
-  if (dev < 64 && ((bits >> dev) & 1u)) return SFS_OK;
-  cudaFuncAttributes fa;
-  SFS_CUDA(cudaFuncGetAttributes(&fa, kernel));
-  const int limit = max_smem_optin() - (int)fa.sharedSizeBytes;
-  if (need > limit) {
-    set_error("kernel needs %d bytes of dynamic shared memory, device allows %d", need, limit);
-    return SFS_ERR_INVALID_ARG;
-  }
-  if (need > 48 * 1024)
-    SFS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-  if (dev < 64) bits |= (uint64_t)1 << dev;  // each kernel always asks the same size
-  return SFS_OK;
-}
-
-template <typename K>
-int ensure_smem_attr(K kernel, int need) {
-  return ensure_smem_attr_ptr((const void*)kernel, need);
-}
-
-// Programmatic dependent launch is off unless SFS_PDL=1 is set in the
-// environment (read once per process).  Measured on GB300 with the graph-
-// replayed FISTA loop it was 4-5 % slower than plain stream order (vol32
-// 19,955 vs 20,887 iterations/s; vol64 1,593 vs 1,662), so the kernels keep
-// their pdl_wait / pdl_trigger points (no-ops without the launch attribute)
-// but are launched in plain stream order by default.
-bool pdl_enabled() {
-  static const bool on = [] {
-    const char* v = getenv("SFS_PDL");
-    return v && v[0] == '1';
-  }();
-  return on;
-}
-
-// Launch with programmatic stream serialisation (see pdl_wait).
-template <typename... KArgs, typename... Args>
-int launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-               Args&&... args) {
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  SFS_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
-  return SFS_OK;
-}
-
 template <int P, bool TWO_D, typename K, typename... Args>
 int launch_plane(K kernel, int nplanes, cudaStream_t st, Args... args) {
   using F = PlaneFFT<P, TWO_D>;
@@ -1179,6 +1055,35 @@ int dispatch_plane(const PlaneDims& d, Fn&& fn) {
 }
 
 }  // namespace
+
+int ensure_smem_attr_ptr(const void* kernel, int need) {
+  int dev = 0;
+  SFS_CUDA(cudaGetDevice(&dev));
+  static std::mutex mu;
+  static std::unordered_map<const void*, uint64_t> done;  // kernel -> device bits
+  std::lock_guard<std::mutex> lock(mu);
+  uint64_t& bits = done[kernel];
+  if (dev < 64 && ((bits >> dev) & 1u)) return SFS_OK;
+  cudaFuncAttributes fa;
+  SFS_CUDA(cudaFuncGetAttributes(&fa, kernel));
+  const int limit = max_smem_optin() - (int)fa.sharedSizeBytes;
+  if (need > limit) {
+    set_error("kernel needs %d bytes of dynamic shared memory, device allows %d", need, limit);
+    return SFS_ERR_INVALID_ARG;
+  }
+  if (need > 48 * 1024)
+    SFS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+  if (dev < 64) bits |= (uint64_t)1 << dev;  // each kernel always asks the same size
+  return SFS_OK;
+}
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = getenv("SFS_PDL");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
 
 int max_smem_optin() {
   int dev = 0, v = 48 * 1024;
@@ -1288,6 +1193,7 @@ int launch_adj_gs(const PlaneDims& d, const float2* table, const float2* Rh, flo
 
 int launch_contract_fwd(const PlaneDims& d, const float2* table, const float2* Xh,
                         float2* Yp, int* err, cudaStream_t st) {
+  if (d.tc) return launch_contract_fwd_tc(d, table, Xh, Yp, err, st);
   switch (d.GS) {
     case 2: return launch_fwd_gs<2>(d, table, Xh, Yp, err, st);
     case 4: return launch_fwd_gs<4>(d, table, Xh, Yp, err, st);
@@ -1316,6 +1222,7 @@ size_t adj_seg_smem_bytes(int Up) { return contract_adj_seg_smem<8>(Up); }
 
 int launch_contract_adj(const PlaneDims& d, const float2* table, const float2* Rh,
                         float2* Gs, int* err, cudaStream_t st) {
+  if (d.tc) return launch_contract_adj_tc(d, table, Rh, Gs, err, st);
   if (d.adj_seg) {
     switch (d.GS) {
       case 2: return launch_adj_seg_gs<2>(d, table, Rh, Gs, err, st);
@@ -1344,6 +1251,7 @@ int prepare_kernels(const PlaneDims& d) {
     SFS_TRY(ensure_smem_attr(inv_fista_fwd_kernel<P, TD>, sm));
     return SFS_OK;
   }));
+  if (d.tc) return prepare_tc_kernels();
   if (d.adj_seg) {
     switch (d.GS) {
       case 2: SFS_TRY(ensure_smem_attr(contract_adj_seg<2>, (int)contract_adj_seg_smem<2>(d.Up))); break;

@@ -129,11 +129,15 @@ def test_adjoint_identity_on_gpu(sfs):
     rng = np.random.default_rng(1)
     x = crandn(rng, *op.shape_x)
     y = crandn(rng, *op.shape_y)
-    Ax = to_host(op.apply_A(to_dev(x)))
-    AHy = to_host(op.apply_AH(to_dev(y)))
-    lhs = np.vdot(y.astype(np.complex64), Ax)
-    rhs = np.vdot(AHy, x.astype(np.complex64))
-    assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
+    Ax = to_host(op.apply_A(to_dev(x))).astype(np.complex128)
+    AHy = to_host(op.apply_AH(to_dev(y))).astype(np.complex128)
+    lhs = np.vdot(y, Ax)
+    rhs = np.vdot(AHy, x)
+    # If each operator is within TOL_OP of the exact one (relative, in norm),
+    # Cauchy-Schwarz bounds the mismatch by TOL_OP (|y| |Ax| + |A^H y| |x|); a
+    # wrong conjugate, sign or index breaks the identity by O(1) of that scale.
+    scale = (np.linalg.norm(y) * np.linalg.norm(Ax) + np.linalg.norm(AHy) * np.linalg.norm(x))
+    assert abs(lhs - rhs) <= TOL_OP * scale
 
 
 def test_vol32_full_size_against_structured_and_dense_rows(sfs):
