@@ -627,11 +627,12 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
     cudaError_t e0 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d.device);
     if (e0 != cudaSuccess) return fail(cuda_fail(e0, "SM count query", __FILE__, __LINE__));
   }
-  // Contractions on the tensor cores unless SFS_CONTRACT=cuda selects the
-  // CUDA-core kernels (read per operator).
+  // CUDA-core contractions unless SFS_CONTRACT=tc selects the tensor-core
+  // (kind::tf32, three-pass) kernels (read per operator).  On the 3-D
+  // workloads the CUDA-core kernels are the faster of the two.
   {
     const char* cv = getenv("SFS_CONTRACT");
-    op->tc = !(cv && strcmp(cv, "cuda") == 0);
+    op->tc = cv && strcmp(cv, "tc") == 0;
   }
   op->nzc = (d.Nz + 15) / 16;
   if (op->tc) op->nzb = 1;

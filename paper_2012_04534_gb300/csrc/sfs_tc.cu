@@ -16,16 +16,17 @@
 // a_lo b_lo and the cut of lo leave at most about 2^-19 relative error per
 // product (about 2^-21 on average), against 2^-24 per FP32 rounding.
 //
-// Per CTA (192 threads, two CTAs per SM, 256 TMEM columns each):
-//   warp 4           streams table chunks into shared memory (cp.async.bulk,
-//                    one mbarrier per stage, 4 stages of 16 KB);
-//   warps 0-3        (one per 32-lane quarter of TMEM) read their rows of a
-//                    chunk, split them and store A_hi / A_lo in TMEM
-//                    (tcgen05.st); they also split the chunk's spectra into
-//                    the B operand in shared memory (K-major, no swizzle) and
-//                    read a unit's accumulator (tcgen05.ld) once they have
-//                    loaded the first chunk of the next unit;
-//   warp 5           issues tcgen05.mma (kind::tf32, M = 128, N = 16, K = 8)
+// Per CTA (320 threads, two CTAs per SM, 256 TMEM columns each):
+//   warp 8           streams table chunks into shared memory (cp.async.bulk,
+//                    one mbarrier per stage, 6 stages of 16 KB);
+//   warps 0-7        two warpgroups, one per K-step (8 of the 16) of a chunk;
+//                    warp w serves the 32-lane quarter w % 4 of TMEM.  They
+//                    read their rows of a chunk, split them and store A_hi /
+//                    A_lo in TMEM (tcgen05.st), split the chunk's spectra
+//                    into the B operand in shared memory (K-major, no
+//                    swizzle), and warpgroup 0 reads a unit's accumulator
+//                    (tcgen05.ld) once the next unit's first chunk is queued;
+//   warp 9           issues tcgen05.mma (kind::tf32, M = 128, N = 16, K = 8)
 //                    and commits to mbarriers that free the chunk buffers and
 //                    signal the accumulators (two, alternating by unit).
 // The copy and MMA warps run their loops with all 32 lanes and issue from
@@ -90,14 +91,11 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
 __device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// 32 lanes (the warp's quarter) x 16 consecutive 32-bit columns
-__device__ __forceinline__ void tc_st16(uint32_t taddr, const uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15, %16};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
-      "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-      : "memory");
+// 32 lanes (the warp's quarter) x 8 (st) or 16 (ld) consecutive 32-bit columns
+__device__ __forceinline__ void tc_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
 }
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
@@ -164,8 +162,10 @@ __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity, uint64_t 
 // ---------------------------------------------------------------------------
 // Shared-memory plan of one CTA
 // ---------------------------------------------------------------------------
-constexpr int kTcThreads = 192;            // warps 0-3 loaders, 4 copies, 5 MMA
-constexpr int kTcStages = 4;               // table stages
+constexpr int kTcLoaderWarps = 8;         // two warpgroups, one per K-step of a chunk
+constexpr int kTcCopyWarp = kTcLoaderWarps, kTcMmaWarp = kTcLoaderWarps + 1;
+constexpr int kTcThreads = (kTcLoaderWarps + 2) * 32;
+constexpr int kTcStages = 6;               // table stages
 constexpr int kTcBufs = 3;                 // chunk buffers (A in TMEM, B in smem)
 constexpr int kTcStageBytes = 16384;       // 128 rows x 128 B (fwd) or 8 x 16 rows x 128 B (adj)
 constexpr int kTcBBytes = 1536;            // B hi (or lo): 3 groups x 8 rows x 16 K x 4 B
@@ -207,10 +207,10 @@ contract_tc(const float4* __restrict__ T4, const float2* __restrict__ Sp,
     *abort_flag = 0;
     for (int k = 0; k < kTcStages; ++k) {
       mbar_init(bar(kSF + k), 1);
-      mbar_init(bar(kSE + k), 4);
+      mbar_init(bar(kSE + k), kTcLoaderWarps);
     }
     for (int k = 0; k < kTcBufs; ++k) {
-      mbar_init(bar(kBF + k), 4);
+      mbar_init(bar(kBF + k), kTcLoaderWarps);
       mbar_init(bar(kBE + k), 1);
     }
     for (int k = 0; k < 2; ++k) {
@@ -230,7 +230,7 @@ contract_tc(const float4* __restrict__ T4, const float2* __restrict__ Sp,
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  if (warp == 4) {
+  if (warp == kTcCopyWarp) {
     // ---- copy producer: table chunks into the stages (whole warp) ----
     int issued = 0;
     bool ok = true;
@@ -283,7 +283,7 @@ contract_tc(const float4* __restrict__ T4, const float2* __restrict__ Sp,
     // copies in flight: the latest use of each stage
     for (int i = max(0, issued - kTcStages); i < issued; ++i)
       mbar_wait_bounded(bar(kSF + i % kTcStages), (i / kTcStages) & 1, kDrainNs);
-  } else if (warp == 5) {
+  } else if (warp == kTcMmaWarp) {
     // ---- MMA issuer (whole warp, one elected lane issues) ----
     constexpr uint32_t idesc = idesc_tf32(128, 16);
     // B rows: forward [-Xi; Xr; Xi], adjoint [Rr; Ri; -Rr] (8 rows each);
@@ -337,13 +337,16 @@ contract_tc(const float4* __restrict__ T4, const float2* __restrict__ Sp,
     __syncwarp();
     mbar_wait_bounded(bar(kDR), 0, kDrainNs);
   } else {
-    // ---- loaders: warps 0-3, thread t owns TMEM lane t ----
-    const int t = threadIdx.x;
-    const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
-    const int nn = t & 7, kk = t >> 3;  // this thread's B element: slot nn, K index kk
+    // ---- loaders: warps 0-7; thread t of a warpgroup owns TMEM lane t ----
+    const int g = warp >> 2;  // warpgroup: K-step g (entries 8 g .. 8 g + 7) of each chunk
+    const int t = threadIdx.x & 127;
+    const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    // this thread's B element (threads 0-63 of each warpgroup): slot nn, K index kk
+    const bool has_b = t < 64;
+    const int nn = t & 7, kk = (t >> 3) + 8 * g;
     const int boff = (kk >> 2) * 32 + nn * 4 + (kk & 3);
     // Accumulator of local unit k (buffer k & 1) to the output; false if the
-    // wait for its MMAs failed.
+    // wait for its MMAs failed.  Warpgroup 0 only.
     auto epilogue = [&](int k, int o, int mt) -> bool {
       const bool dgot = tc_wait(bar(kDF + (k & 1)), (k >> 1) & 1, wait_ns, abort_flag);
       if (!__all_sync(0xffffffffu, dgot)) return false;
@@ -379,16 +382,24 @@ contract_tc(const float4* __restrict__ T4, const float2* __restrict__ Sp,
     int o = first / nmt, mt = first - (first / nmt) * nmt;
     int po = o, pmt = mt;  // the previous unit
     int s = 0, bf = 0, sph = 0, bph = 0;  // stage, buffer and their use counts' parity
+    // Spectra value of this thread's B element in chunk cc of orbit oo (the
+    // same for every M tile).  It is loaded one item ahead, so that its L2
+    // latency overlaps the previous chunk's work.
+    auto load_sv = [&](int oo, int cc) -> float2 {
+      float2 v = make_float2(0.f, 0.f);
+      if (has_b && nn < d.GS) {
+        const int r = 16 * cc + kk;  // depth (forward) or bin (adjoint)
+        if (r < (FWD ? d.Nz : d.U)) v = Sp[(size_t)r * d.Ns + oo * d.GS + nn];
+      }
+      return v;
+    };
     pdl_wait();
+    float2 sv_next = items > 0 ? load_sv(o, c) : make_float2(0.f, 0.f);
     for (int i = 0; i < items; ++i) {
-      // spectra value of this thread's B element
-      float2 sv = make_float2(0.f, 0.f);
-      if (FWD) {
-        const int z = 16 * c + kk;
-        if (nn < d.GS && z < d.Nz) sv = Sp[(size_t)z * d.Ns + o * d.GS + nn];
-      } else {
-        const int u = 16 * c + kk;
-        if (nn < d.GS && u < d.U) sv = Sp[(size_t)u * d.Ns + o * d.GS + nn];
+      const float2 sv = sv_next;
+      if (i + 1 < items) {
+        const bool wrap = c + 1 == nch;
+        sv_next = load_sv(wrap && mt + 1 == nmt ? o + 1 : o, wrap ? 0 : c + 1);
       }
       const bool got = (d.inject && i == 0) ? tc_wait(bar(kNV), 0, wait_ns, abort_flag)
                                             : tc_wait(bar(kSF + s), sph, wait_ns, abort_flag);
@@ -396,13 +407,14 @@ contract_tc(const float4* __restrict__ T4, const float2* __restrict__ Sp,
         ok = false;
         break;
       }
-      float ar[16], ai[16];
+      float ar[8], ai[8];  // K entries 8 g .. 8 g + 7 of this thread's row
       const float4* st4 = stages + s * (kTcStageBytes / 16);
       if (FWD) {
         const bool valid = t < d.U - 128 * mt;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float4 w = valid ? st4[t * 8 + (j ^ (t & 7))] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < 4; ++j) {
+          const int jj = 4 * g + j;
+          const float4 w = valid ? st4[t * 8 + (jj ^ (t & 7))] : make_float4(0.f, 0.f, 0.f, 0.f);
           ar[2 * j] = w.x;
           ar[2 * j + 1] = w.y;
           ai[2 * j] = w.z;
@@ -414,8 +426,9 @@ contract_tc(const float4* __restrict__ T4, const float2* __restrict__ Sp,
         const int zcl = t >> 4, j = (t & 15) >> 1;
         const bool odd = t & 1;
 #pragma unroll
-        for (int ul = 0; ul < 16; ++ul) {
-          const float4 w = (zv && ul < nu) ? st4[(zcl * 16 + ul) * 8 + (j ^ (ul & 7))]
+        for (int ul = 0; ul < 8; ++ul) {
+          const int ur = 8 * g + ul;
+          const float4 w = (zv && ur < nu) ? st4[(zcl * 16 + ur) * 8 + (j ^ (ur & 7))]
                                            : make_float4(0.f, 0.f, 0.f, 0.f);
           ar[ul] = odd ? w.y : w.x;
           ai[ul] = odd ? w.w : w.z;
@@ -430,7 +443,7 @@ contract_tc(const float4* __restrict__ T4, const float2* __restrict__ Sp,
           break;
         }
       }
-      {  // B operand element, three row groups, hi and lo
+      if (has_b) {  // B operand element, three row groups, hi and lo
         uint32_t* bh = (uint32_t*)(bbuf + (2 * bf) * (kTcBBytes / 4));
         uint32_t* bl = bh + kTcBBytes / 4;
         const float v0 = FWD ? -sv.y : sv.x, v1 = FWD ? sv.x : sv.y, v2 = FWD ? sv.y : -sv.x;
@@ -446,24 +459,24 @@ contract_tc(const float4* __restrict__ T4, const float2* __restrict__ Sp,
         bl[256 + boff] = l2;
         fence_proxy_async();
       }
-      {  // A operand rows into TMEM
-        uint32_t h[16], l[16];
-        const uint32_t ca = tl + kTcColA + 64u * bf;
+      {  // this K-step's A columns into TMEM: Ar_hi, Ar_lo, Ai_hi, Ai_lo at +0, 16, 32, 48
+        uint32_t h[8], l[8];
+        const uint32_t ca = tl + kTcColA + 64u * bf + 8u * g;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) tf32_split(ar[q], h[q], l[q]);
-        tc_st16(ca, h);
-        tc_st16(ca + 16, l);
+        for (int q = 0; q < 8; ++q) tf32_split(ar[q], h[q], l[q]);
+        tc_st8(ca, h);
+        tc_st8(ca + 16, l);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) tf32_split(ai[q], h[q], l[q]);
-        tc_st16(ca + 32, h);
-        tc_st16(ca + 48, l);
+        for (int q = 0; q < 8; ++q) tf32_split(ai[q], h[q], l[q]);
+        tc_st8(ca + 32, h);
+        tc_st8(ca + 48, l);
         tc_wait_st();
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(kBF + bf));
       // the previous unit's accumulator, now that this unit's first chunk is queued
-      if (c == 0 && k >= 1 && !epilogue(k - 1, po, pmt)) {
+      if (g == 0 && c == 0 && k >= 1 && !epilogue(k - 1, po, pmt)) {
         ok = false;
         break;
       }
@@ -486,7 +499,7 @@ contract_tc(const float4* __restrict__ T4, const float2* __restrict__ Sp,
         }
       }
     }
-    if (ok && items > 0 && !epilogue(k - 1, po, pmt)) ok = false;
+    if (g == 0 && ok && items > 0 && !epilogue(k - 1, po, pmt)) ok = false;
     if (!ok && lane == 0) {
       *abort_flag = 1;
       atomicExch(err, 1);
