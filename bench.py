@@ -43,11 +43,22 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="vol32", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--strategy", default="random", choices=sorted(STRATEGY_NAMES))
+    ap.add_argument("--precision", default="fp32",
+                    choices=["fp32", "tf32x3", "bf16", "bf16x2"],
+                    help="arithmetic of the depth contractions (sfs_precision)")
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
+
+
+# arithmetic of each contraction mode (the lateral FFTs and the FISTA update
+# are c64 in every mode)
+DTYPE_OF = {"fp32": "c64 (f32)",
+            "tf32x3": "c64 (f32 state; contractions tf32 hi/lo x3 on tensor cores, f32 accumulate)",
+            "bf16": "c64 (f32 state; contractions bf16 table x bf16 hi/lo spectra, f32 accumulate)",
+            "bf16x2": "c64 (f32 state; contractions bf16 hi/lo table x bf16 hi/lo spectra, f32 accumulate)"}
 
 
 def workload_desc(name, w, strategy, iters):
@@ -251,7 +262,8 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     geom = sfs.Geometry(**params)
-    op = sfs.Operator.select(geom, STRATEGY_NAMES[args.strategy], w["M"], True, seed)
+    op = sfs.Operator.select(geom, STRATEGY_NAMES[args.strategy], w["M"], True, seed,
+                             precision=sfs.PRECISION_NAMES[args.precision])
     torch.cuda.synchronize()
     t_table = time.perf_counter() - t0
     info = op.info
@@ -364,7 +376,7 @@ def main():
     achieved_tf = alg_flops / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else 0.0
     traffic = measured_traffic(args.workload, args.strategy)
     hbm_frac, alu_frac = achieved / peak, achieved_tf / alu_peak
-    if hbm_frac >= alu_frac:
+    if hbm_frac >= alu_frac or args.precision != "fp32":
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": hbm_frac, "peak_source": peak_src}
     else:
@@ -393,9 +405,10 @@ def main():
             "metric": "FISTA iterations/s", "value": value, "unit": "it/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c64 (f32)", "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPE_OF[args.precision], "data": "synthetic",
             "config": {
                 "workload": workload_desc(args.workload, w, args.strategy, iters),
+                "precision": args.precision,
                 "parallelism": "replicas" if world > 1 else "single GPU",
                 "l2": "L2 flushed before every timed step (256 MB buffer write outside the "
                       "per-step events); generator table %.0f MB" % (info["table_bytes"] / 1e6),

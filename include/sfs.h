@@ -73,6 +73,29 @@ typedef struct sfs_geometry_desc {
   int32_t device;      /* CUDA device ordinal that holds the operator         */
 } sfs_geometry_desc;
 
+/*
+ * Arithmetic of the depth contractions (the per-wavenumber products of
+ * Theorem 2 / Algorithm 2 that dominate A and A^H).  The paper fixes no
+ * precision; every mode accumulates in FP32, and the lateral FFTs, the
+ * FISTA update and all reductions are the same in every mode.  u below is
+ * the unit roundoff of the stored table.
+ *   SFS_PREC_FP32    CUDA-core FP32 FMAs on the FP32 table (the default).
+ *   SFS_PREC_TF32X3  tensor cores (tcgen05 kind::tf32): table and spectra
+ *                    each split into TF32 hi + lo parts, three products;
+ *                    FP32-level accuracy, FP32 table.
+ *   SFS_PREC_BF16    tensor cores (kind::f16): table rounded to BF16
+ *                    (u = 2^-8, half the bytes of FP32), spectra split into
+ *                    BF16 hi + lo; relative error of A x about u.
+ *   SFS_PREC_BF16X2  tensor cores (kind::f16): table stored as BF16 hi + lo
+ *                    (u about 2^-16, the bytes of FP32), spectra hi + lo.
+ */
+typedef enum sfs_precision {
+  SFS_PREC_FP32 = 0,
+  SFS_PREC_TF32X3 = 1,
+  SFS_PREC_BF16 = 2,
+  SFS_PREC_BF16X2 = 3
+} sfs_precision;
+
 typedef struct sfs_geometry sfs_geometry;  /* opaque, library owned */
 typedef struct sfs_operator sfs_operator;  /* opaque, library owned */
 
@@ -90,6 +113,7 @@ typedef struct sfs_operator_info_t {
   int32_t launches_per_iter; /* kernels one FISTA iteration launches          */
   int32_t Nslot;        /* wavenumber slots (orbit-major, padded to 64)        */
   int32_t GS;           /* slots per symmetry orbit (2, 4 or 8)               */
+  int32_t precision;    /* sfs_precision of the depth contractions            */
 } sfs_operator_info_t;
 
 /*
@@ -143,6 +167,20 @@ int sfs_select_freqs(sfs_geometry* g, int strategy, int M, int per_position,
  */
 int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
                               sfs_operator** op);
+
+/*
+ * As sfs_operator_from_indices, with the arithmetic of the depth
+ * contractions chosen by `precision` (an sfs_precision).  The table is
+ * built in FP32 (as above) and stored in the mode's format: BF16 halves its
+ * bytes.  sfs_operator_from_indices uses SFS_PREC_FP32 (or SFS_PREC_TF32X3
+ * when the environment sets SFS_CONTRACT=tc).  Several operators of one
+ * geometry and index set, in different precisions, may coexist (e.g. a fast
+ * BF16 operator for the first FISTA iterations and an FP32 one to finish).
+ * Errors: as sfs_operator_from_indices; SFS_ERR_INVALID_ARG for an unknown
+ * precision.
+ */
+int sfs_operator_from_indices_prec(sfs_geometry* g, int M, const int32_t* idx_host,
+                                   int precision, sfs_operator** op);
 int sfs_destroy_operator(sfs_operator* op);
 int sfs_operator_info(const sfs_operator* op, sfs_operator_info_t* info);
 

@@ -201,6 +201,7 @@ void free_operator(sfs_operator* op) {
   for (cudaEvent_t e : op->ev) cudaEventDestroy(e);
   for (auto& ge : op->graphs) cudaGraphExecDestroy(ge.exec);
   if (op->capture_stream) cudaStreamDestroy(op->capture_stream);
+  free_tc_maps(op->tmaps);
   delete op;
 }
 
@@ -224,6 +225,10 @@ PlaneDims operator_dims(const sfs_operator* op) {
   d.Up = op->Up;
   d.tc = op->tc;
   d.nzc = op->nzc;
+  d.prec = op->prec;
+  d.nkb = op->nkb;
+  d.nparts = op->nparts;
+  d.tmaps = op->tmaps;
   d.adj_seg = op->adj_seg;
   d.azb = op->azb;
   d.anzb = op->anzb;
@@ -240,10 +245,12 @@ namespace {
 PlaneDims dims_of(const sfs_operator* op) { return operator_dims(op); }
 
 // Generator table size in c64 entries.  CUDA-core layout: depth pairs of
-// Nz rounded up to even, Up rows per slot tile of 64; tensor-core layout:
-// 16-depth blocks, U rows per orbit.
+// Nz rounded up to even, Up rows per slot tile of 64; tf32 tensor-core
+// layout: 16-depth blocks, U rows per orbit; 16-bit layout: per part, orbit
+// and 32-depth block, U rows of 64 16-bit values (128 B).
 size_t table_c64(const sfs_operator* op) {
   const size_t No = (size_t)(op->Ns / op->GS);
+  if (op->tc == 2) return (size_t)op->nparts * No * op->nkb * op->U * 16;  // 128 B per row
   if (op->tc) return No * op->nzc * 16 * op->U;
   return No * op->Up * (size_t)((op->geo.d.Nz + 1) / 2 * 2);
 }
@@ -480,9 +487,8 @@ int sfs_select_indices(const sfs_geometry* g, int strategy, int M, int per_posit
   return SFS_OK;
 }
 
-int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
-                              sfs_operator** out) {
-  clear_error();
+static int build_operator(sfs_geometry* g, int M, const int32_t* idx_host, int prec,
+                          sfs_operator** out) {
   if (!g || !idx_host || !out) {
     set_error("null argument");
     return SFS_ERR_INVALID_ARG;
@@ -509,6 +515,9 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
     return SFS_ERR_OOM;
   }
   op->geo = *g;
+  op->prec = prec;
+  op->tc = prec == SFS_PREC_FP32 ? 0 : (prec == SFS_PREC_TF32X3 ? 1 : 2);
+  op->nparts = prec == SFS_PREC_BF16X2 ? 2 : 1;
   op->M = M;
   op->S = S;
   op->V = S * d.Nz;
@@ -627,14 +636,8 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
     cudaError_t e0 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d.device);
     if (e0 != cudaSuccess) return fail(cuda_fail(e0, "SM count query", __FILE__, __LINE__));
   }
-  // CUDA-core contractions unless SFS_CONTRACT=tc selects the tensor-core
-  // (kind::tf32, three-pass) kernels (read per operator).  On the 3-D
-  // workloads the CUDA-core kernels are the faster of the two.
-  {
-    const char* cv = getenv("SFS_CONTRACT");
-    op->tc = cv && strcmp(cv, "tc") == 0;
-  }
   op->nzc = (d.Nz + 15) / 16;
+  op->nkb = (d.Nz + 31) / 32;
   if (op->tc) op->nzb = 1;
   const int nseg = (op->Ns / kKappaTile) * op->nzb;
   const int ngroups = op->Up / (op->GS / 2);
@@ -717,8 +720,33 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
   cudaFree(d_gdir);
   cudaFree(d_amp);
   cudaFree(d_bins);
+  d_tof = nullptr;
+  d_gdir = nullptr;
+  d_amp = nullptr;
+  d_bins = nullptr;
+  if (op->tc == 2 && (rc = tc16_setup(op)) != SFS_OK) return fail(rc);
   *out = op;
   return SFS_OK;
+}
+
+int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
+                              sfs_operator** out) {
+  clear_error();
+  // SFS_CONTRACT=tc selects the tf32 tensor-core contractions (read per
+  // operator); on the 3-D workloads the CUDA-core kernels are the faster.
+  const char* cv = getenv("SFS_CONTRACT");
+  const int prec = (cv && strcmp(cv, "tc") == 0) ? SFS_PREC_TF32X3 : SFS_PREC_FP32;
+  return build_operator(g, M, idx_host, prec, out);
+}
+
+int sfs_operator_from_indices_prec(sfs_geometry* g, int M, const int32_t* idx_host,
+                                   int precision, sfs_operator** out) {
+  clear_error();
+  if (precision < SFS_PREC_FP32 || precision > SFS_PREC_BF16X2) {
+    set_error("unknown precision %d", precision);
+    return SFS_ERR_INVALID_ARG;
+  }
+  return build_operator(g, M, idx_host, precision, out);
 }
 
 int sfs_select_freqs(sfs_geometry* g, int strategy, int M, int per_position, uint64_t seed,
@@ -774,6 +802,7 @@ int sfs_operator_info(const sfs_operator* op, sfs_operator_info_t* info) {
   info->launches_per_iter = 4;
   info->Nslot = op->Ns;
   info->GS = op->GS;
+  info->precision = op->prec;
   return SFS_OK;
 }
 

@@ -81,13 +81,26 @@ struct sfs_geometry {
   int Px, Py;           // lateral FFT sizes
 };
 
+namespace sfs {
+// Tensor maps of the 16-bit tensor-core contractions (sfs_tc16.cu); opaque
+// elsewhere.
+struct TcMaps;
+void free_tc_maps(TcMaps* m);
+}  // namespace sfs
+
 struct sfs_operator {
   sfs_geometry geo;
   int M = 0, S = 0, V = 0, U = 0, Nk = 0;
   int Ns = 0, GS = 0, No = 0;  // wavenumber slots, slots per orbit, orbits
   int Up = 0;                  // bins padded to a multiple of GS / 2
-  int tc = 0;                  // contractions on the tensor cores (sfs_tc.cu)
-  int nzc = 0;                 // depth blocks of 16 in the tensor-core table
+  int prec = 0;                // sfs_precision of the depth contractions
+  int tc = 0;                  // contraction kernels: 0 CUDA cores (sfs_kernels.cu),
+                               // 1 tensor cores kind::tf32 (sfs_tc.cu), 2 tensor
+                               // cores kind::f16 from a 16-bit table (sfs_tc16.cu)
+  int nzc = 0;                 // depth blocks of 16 in the tf32 tensor-core table
+  int nkb = 0;                 // depth blocks of 32 in the 16-bit table
+  int nparts = 1;              // 16-bit table parts: 1 (value) or 2 (hi, lo)
+  sfs::TcMaps* tmaps = nullptr;  // tensor maps of the 16-bit contractions
   int nzb = 1;                 // depth blocks of <= 128 in the contractions
   int G = 1;                   // persistent CTAs of the contractions
   int nslots = 0;              // adjoint partial-sum slots
@@ -132,9 +145,13 @@ struct PlaneDims {
   int Ns;   // wavenumber slots (orbit-major, a multiple of 64)
   int GS;   // slots per symmetry orbit: 2 (line), 4 (area), 8 (square area)
   int Up;   // bins padded to a multiple of GS / 2 (zero table rows and spectra)
-  int tc;   // contractions on the tensor cores: table in the layout of sfs_tc.cu,
-            // nzb = 1 and the dense segment-aligned adjoint result
-  int nzc;  // depth blocks of 16 of the tensor-core table
+  int tc;   // contraction kernels (see sfs_operator::tc); tc > 0: nzb = 1 and the
+            // dense segment-aligned adjoint result
+  int nzc;  // depth blocks of 16 of the tf32 tensor-core table
+  int prec;    // sfs_precision
+  int nkb;     // depth blocks of 32 of the 16-bit table
+  int nparts;  // parts of the 16-bit table (1 or 2)
+  TcMaps* tmaps;  // host pointer: tensor maps of the 16-bit contractions
   int adj_seg;  // adjoint by segment-aligned CTAs (dense result) instead of partial sums
   int azb;      // depth rows per adjoint segment (32 segment-aligned, 128 otherwise)
   int anzb;     // adjoint depth blocks per slot tile
@@ -197,6 +214,16 @@ int launch_contract_fwd_tc(const PlaneDims& d, const float2* table, const float2
 int launch_contract_adj_tc(const PlaneDims& d, const float2* table, const float2* Rh,
                            float2* Gs, int* err, cudaStream_t st);
 int prepare_tc_kernels();
+
+// The same two contractions on the tensor cores from the 16-bit table
+// (sfs_tc16.cu); used when d.tc == 2.  tc16_setup encodes the tensor maps of
+// an operator's table and workspace (once, after the table is allocated).
+int tc16_setup(sfs_operator* op);
+int launch_contract_fwd_h(const PlaneDims& d, const float2* Xh, float2* Yp, int* err,
+                          cudaStream_t st);
+int launch_contract_adj_h(const PlaneDims& d, const float2* Rh, float2* Gs, int* err,
+                          cudaStream_t st);
+int prepare_tc16_kernels(const PlaneDims& d);
 
 // Small helpers.
 int launch_set_thresholds(float* scal, double* red, double lambda, double L,

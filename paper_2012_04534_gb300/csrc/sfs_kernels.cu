@@ -14,6 +14,7 @@
 // unnormalised forward and inverse FFTs make A and A^H exact adjoints.
 // The two contractions stream T and dominate the run time; everything else
 // works on single planes held in shared memory.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -125,6 +126,27 @@ build_table_kernel(PlaneDims d, const float2* __restrict__ tof,
   // im_2p+1): T4[st][u][p][e] with e < E = 64 / GS.
   // The tensor-core contractions use words ((o nzc + z/16) U + u) 8 + ((z%16)/2
   // xor u%8), one orbit's rows per 16-depth block (sfs_tc.cu).
+  // The 16-bit tensor-core contractions (sfs_tc16.cu) use rows of 64 values
+  // T16[part][o][z/32][u][2 (z%32) + {0: re, 1: im}]: part 0 holds the BF16
+  // rounding of the FP32 value v, part 1 (two-part tables) the BF16 rounding
+  // of v - part 0.
+  if (d.tc == 2) {
+    const int No = d.Ns / d.GS;
+    __nv_bfloat162* t16 = (__nv_bfloat162*)table;
+    for (int o = threadIdx.x; o < No; o += F::NT) {
+      const int rep = d.orbit_rep[o];
+      const float2 v = rep >= 0 ? buf[F::kidx(rep)] : make_float2(0.f, 0.f);
+      const __nv_bfloat162 hi = __floats2bfloat162_rn(v.x, v.y);
+      const size_t row = ((size_t)o * d.nkb + (z >> 5)) * d.U + u;
+      t16[row * 32 + (z & 31)] = hi;
+      if (d.nparts == 2) {
+        const float2 r = make_float2(v.x - __low2float(hi), v.y - __high2float(hi));
+        const size_t row1 = (((size_t)No + o) * d.nkb + (z >> 5)) * d.U + u;
+        t16[row1 * 32 + (z & 31)] = __floats2bfloat162_rn(r.x, r.y);
+      }
+    }
+    return;
+  }
   const int E = kKappaTile / d.GS;
   const int Nzp = (d.Nz + 1) / 2;
   float* tf = (float*)table;
@@ -1193,6 +1215,7 @@ int launch_adj_gs(const PlaneDims& d, const float2* table, const float2* Rh, flo
 
 int launch_contract_fwd(const PlaneDims& d, const float2* table, const float2* Xh,
                         float2* Yp, int* err, cudaStream_t st) {
+  if (d.tc == 2) return launch_contract_fwd_h(d, Xh, Yp, err, st);
   if (d.tc) return launch_contract_fwd_tc(d, table, Xh, Yp, err, st);
   switch (d.GS) {
     case 2: return launch_fwd_gs<2>(d, table, Xh, Yp, err, st);
@@ -1222,6 +1245,7 @@ size_t adj_seg_smem_bytes(int Up) { return contract_adj_seg_smem<8>(Up); }
 
 int launch_contract_adj(const PlaneDims& d, const float2* table, const float2* Rh,
                         float2* Gs, int* err, cudaStream_t st) {
+  if (d.tc == 2) return launch_contract_adj_h(d, Rh, Gs, err, st);
   if (d.tc) return launch_contract_adj_tc(d, table, Rh, Gs, err, st);
   if (d.adj_seg) {
     switch (d.GS) {
@@ -1251,6 +1275,7 @@ int prepare_kernels(const PlaneDims& d) {
     SFS_TRY(ensure_smem_attr(inv_fista_fwd_kernel<P, TD>, sm));
     return SFS_OK;
   }));
+  if (d.tc == 2) return prepare_tc16_kernels(d);
   if (d.tc) return prepare_tc_kernels();
   if (d.adj_seg) {
     switch (d.GS) {

@@ -1,0 +1,552 @@
+// Depth contractions on the tensor cores from a 16-bit table (tcgen05
+// kind::f16, BF16 operands, FP32 accumulation in tensor memory).
+//
+// The generator table holds one entry per symmetry orbit of wavenumbers
+// (the lateral kernel depends on dx^2 + dy^2 only, Eq. (3)), so both
+// contractions of Sec. IV-B are small dense products per orbit o, with n
+// over the orbit's slots (Theorem 2, Algorithm 2):
+//   forward  Y[u][n] = sum_z T[u][z] X[z][n]           M = bins,   K = depths
+//   adjoint  G[z][n] = sum_u conj(T[u][z]) R[u][n]     M = depths, K = bins
+// The table is stored as rows of 64 16-bit values, one row per (part, orbit,
+// 32-depth block kb, bin u): element 2 zz + q is Re (q = 0) or Im (q = 1) of
+// T[u][32 kb + zz].  Part 0 is the BF16 rounding of the FP32 table, part 1
+// (two-part tables) the BF16 rounding of the remainder.  Such a row is one
+// 128-byte line of the 128-byte-swizzled canonical layouts, so bulk tensor
+// copies (TMA) bring table tiles from global memory straight into the
+// layout the MMA reads: the table never passes through registers.
+//
+// Forward (K-major A = table tile, rows u, K index k = 2 zz + q):
+//   [Yr | Yi][u] = sum_k A[u][k] B[k],  B[2zz] = [Xr | Xi],  B[2zz+1] = [-Xi | Xr]
+// Adjoint (MN-major A: the same tile read with M index m = 2 zz + q, K = u;
+// two depth blocks side by side give M = 128):
+//   D[2zz + q][n] = sum_u T_q[u][z] [Rr | Ri][u][n],
+//   Gr = D[2zz][re] + D[2zz+1][im],  Gi = D[2zz][im] - D[2zz+1][re],
+// combined in the epilogue between neighbouring TMEM lanes.
+// The spectra operand B (8 slots x re/im = 16 columns) is split into BF16
+// hi and lo = the BF16 rounding of (value - hi); both are stacked along N
+// (N = 32) and summed in the epilogue, so the spectra keep about 16
+// significant bits and the table's rounding dominates the error.
+//
+// Per CTA (192 threads, two CTAs per SM, 64 TMEM columns):
+//   warp 4     issues the TMA copies of a chunk (table tile(s) and the
+//              chunk's spectra tile) into a stage, one mbarrier per stage;
+//   warps 0-3  build the chunk's B operand (hi and lo) in the stage from the
+//              spectra tile, and read a unit's accumulator (tcgen05.ld) once
+//              the next unit's first chunk is built;
+//   warp 5     issues the 4 x parts MMAs of a chunk (M = 128, N = 32,
+//              K = 16) and commits to the barriers that free the stage and
+//              signal the accumulator (two, alternating by unit).
+// Work: units (orbit, bin tile of 128) forward, (orbit, pair of depth
+// blocks) adjoint; a contiguous share of units per persistent CTA; a unit
+// runs over K in chunks (a 32-depth block forward, 64 bins adjoint).
+//
+// Every mbarrier wait is bounded (wait_ns).  A timeout sets the device error
+// flag and a shared abort flag that ends the other roles' waits; the copy
+// warp then waits (bounded) for its copies in flight, the MMA warp for its
+// MMAs, and warp 0 frees the tensor memory before the CTA exits.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched at run time)
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "sfs_async.cuh"
+#include "sfs_internal.h"
+#include "sfs_launch.h"
+#include "sfs_tcgen05.cuh"
+
+namespace sfs {
+
+struct TcMaps {
+  CUtensorMap tab_f;  // table, box 64 x 128 rows: forward A tiles
+  CUtensorMap tab_a;  // table, box 64 x 64 rows: adjoint A tiles (one depth block)
+  CUtensorMap xh;     // X^ c64 [Nz][Ns] as floats, box 16 x 32
+  CUtensorMap rh;     // R^ c64 [Up][Ns] as floats, box 16 x 64
+  const void* xh_ptr = nullptr;
+  const void* rh_ptr = nullptr;
+};
+
+void free_tc_maps(TcMaps* m) { delete m; }
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Tensor maps (host)
+// ---------------------------------------------------------------------------
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int encoder(EncodeTiledFn* out) {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  static cudaError_t qerr = cudaSuccess;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    qerr = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (qerr == cudaSuccess && q == cudaDriverEntryPointSuccess) fn = (EncodeTiledFn)p;
+  });
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available (%s)", cudaGetErrorString(qerr));
+    return SFS_ERR_CUDA;
+  }
+  *out = fn;
+  return SFS_OK;
+}
+
+// 16-bit table [parts * No][nkb][U][64], 128-byte swizzle, box 64 x rows;
+// rows past U and blocks past nkb read as zero.
+int encode_table(CUtensorMap* m, const void* table, int U, int nkb, int planes, int rows) {
+  EncodeTiledFn enc;
+  SFS_TRY(encoder(&enc));
+  const cuuint64_t dims[4] = {64, (cuuint64_t)U, (cuuint64_t)nkb, (cuuint64_t)planes};
+  const cuuint64_t strides[3] = {128, (cuuint64_t)U * 128, (cuuint64_t)nkb * U * 128};
+  const cuuint32_t box[4] = {64, (cuuint32_t)rows, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(table), dims, strides,
+                         box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("tensor map of the 16-bit table rejected (CUresult %d)", (int)r);
+    return SFS_ERR_CUDA;
+  }
+  return SFS_OK;
+}
+
+// Lateral spectra c64 [rows][Ns] seen as floats [rows][2 Ns]; box of 8 slots
+// (16 floats) x box_rows, no swizzle; rows past `rows` read as zero.
+int encode_spec(CUtensorMap* m, const void* base, int rows, int Ns, int box_rows) {
+  EncodeTiledFn enc;
+  SFS_TRY(encoder(&enc));
+  const cuuint64_t dims[2] = {(cuuint64_t)2 * Ns, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Ns * 8};
+  const cuuint32_t box[2] = {16, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box,
+                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("tensor map of the lateral spectra rejected (CUresult %d)", (int)r);
+    return SFS_ERR_CUDA;
+  }
+  return SFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            int c3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor, 128-byte swizzle (layout type 2),
+// descriptor version 1.  K-major: sbo = stride between 8-row groups (lbo
+// unused); MN-major: lbo = stride between 64-element column blocks, sbo =
+// stride between 8-row K groups.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
+         ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor of kind::f16: D f32, A and B bf16, B K-major,
+// A K-major (forward) or MN-major (adjoint).
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// D[tmem] (+)= A[smem] * B[smem]^T
+__device__ __forceinline__ void mma_bf16_ss(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Two values as a BF16 pair (low half first): their BF16 roundings (lo =
+// false) or the BF16 roundings of what those leave (lo = true).
+__device__ __forceinline__ uint32_t bf16_pair_part(float v0, float v1, bool lo) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+  if (lo) h = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory plan of one CTA
+// ---------------------------------------------------------------------------
+constexpr int kHThreads = 192;  // warps 0-3 build B and read out, 4 copies, 5 MMA
+constexpr int kHCopyWarp = 4, kHMmaWarp = 5;
+constexpr int kHATile = 16384;  // A tile of one part: 128 rows x 128 B (or 2 x 64 rows)
+constexpr int kHBTile = 4096;   // B: 32 rows (16 hi, 16 lo) x 64 K x 2 B, swizzled
+constexpr int kHSTile = 4096;   // spectra tile: 32 depths x 64 B (fwd), 64 bins x 64 B (adj)
+constexpr uint32_t kHCols = 64; // two accumulators of 32 columns
+
+template <int NP>
+struct HPlan {
+  static constexpr int kStages = NP == 1 ? 4 : 2;
+  static constexpr int kStage = NP * kHATile + kHBTile + kHSTile;
+  static constexpr int kOffB = NP * kHATile;  // within a stage
+  static constexpr int kOffS = kOffB + kHBTile;
+  // barriers: stage full / empty / B built, accumulator full / empty, MMA
+  // drain, one that nothing arrives at (failure-handling tests)
+  static constexpr int kSF = 0, kSE = kStages, kBF = 2 * kStages, kDF = 3 * kStages,
+                       kDE = kDF + 2, kDR = kDE + 2, kNV = kDR + 1, kNumBars = kNV + 1;
+  static constexpr int kOffBar = kStages * kStage;
+  static constexpr int kOffSlot = kOffBar + kNumBars * 8;
+  static constexpr int kSmem = kOffSlot + 16 + 1024;  // + alignment of the base to 1 KB
+};
+
+template <bool FWD, int NP>
+__global__ void __launch_bounds__(kHThreads, 2)
+contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUtensorMap spec,
+           float2* __restrict__ out, PlaneDims d, int nmt, int nch, int nunits, int* __restrict__ err) {
+  using Pl = HPlan<NP>;
+  constexpr int S = Pl::kStages;
+  extern __shared__ unsigned char hsm_raw[];
+  // 128-byte-swizzled tiles need 1 KB alignment of the shared-memory address
+  unsigned char* hsm = hsm_raw + ((1024u - (smem_addr(hsm_raw) & 1023u)) & 1023u);
+  const uint32_t sbase = smem_addr(hsm);
+  uint32_t* tslot = (uint32_t*)(hsm + Pl::kOffSlot);
+  volatile int* abort_flag = (volatile int*)(hsm + Pl::kOffSlot + 4);
+  const uint32_t bar0 = sbase + Pl::kOffBar;
+  auto bar = [&](int k) { return bar0 + 8u * (uint32_t)k; };
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = gridDim.x, b = blockIdx.x;
+  const int first = (int)(((long long)nunits * b) / G);
+  const int items = ((int)(((long long)nunits * (b + 1)) / G) - first) * nch;
+  const uint64_t wait_ns = d.wait_ns;
+  const int No = d.Ns / d.GS;
+
+  if (threadIdx.x == 0) {
+    *abort_flag = 0;
+    for (int k = 0; k < S; ++k) {
+      mbar_init(bar(Pl::kSF + k), 1);
+      mbar_init(bar(Pl::kSE + k), 1);
+      mbar_init(bar(Pl::kBF + k), 4);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(bar(Pl::kDF + k), 1);
+      mbar_init(bar(Pl::kDE + k), 4);
+    }
+    mbar_init(bar(Pl::kDR), 1);
+    mbar_init(bar(Pl::kNV), 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc_alloc(smem_addr(tslot), kHCols);
+    tc_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == kHCopyWarp) {
+    // ---- copy producer: a chunk's table tile(s) and spectra tile ----
+    int issued = 0;
+    bool ok = true;
+    int c = 0;
+    int o = first / nmt, mt = first - (first / nmt) * nmt;
+    pdl_wait();  // the spectra come from the previous kernel
+    for (int i = 0; i < items; ++i) {
+      const int s = i % S;
+      if (i >= S) {
+        const bool got = tc_wait(bar(Pl::kSE + s), ((i / S) + 1) & 1, wait_ns, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+      }
+      if (elect_one()) {
+        const uint32_t dst = sbase + (uint32_t)(s * Pl::kStage), fb = bar(Pl::kSF + s);
+        mbar_expect_tx(fb, NP * kHATile + (FWD ? 2048 : 4096));
+        if (FWD) {  // bins 128 mt .., depth block c
+#pragma unroll
+          for (int p = 0; p < NP; ++p) tma_load_4d(dst + p * kHATile, &tab, 0, 128 * mt, c, p * No + o, fb);
+          tma_load_2d(dst + Pl::kOffS, &spec, 2 * o * d.GS, 32 * c, fb);
+        } else {  // bins 64 c .., depth blocks 2 mt and 2 mt + 1
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            tma_load_4d(dst + p * kHATile, &tab, 0, 64 * c, 2 * mt, p * No + o, fb);
+            tma_load_4d(dst + p * kHATile + 8192, &tab, 0, 64 * c, 2 * mt + 1, p * No + o, fb);
+          }
+          tma_load_2d(dst + Pl::kOffS, &spec, 2 * o * d.GS, 64 * c, fb);
+        }
+      }
+      __syncwarp();
+      ++issued;
+      if (++c == nch) {
+        c = 0;
+        if (++mt == nmt) {
+          mt = 0;
+          ++o;
+        }
+      }
+    }
+    if (!ok && lane == 0) {
+      *abort_flag = 1;
+      atomicExch(err, 1);
+    }
+    // copies in flight: the latest use of each stage
+    for (int i = max(0, issued - S); i < issued; ++i)
+      mbar_wait_bounded(bar(Pl::kSF + i % S), (i / S) & 1, kDrainNs);
+  } else if (warp == kHMmaWarp) {
+    // ---- MMA issuer (whole warp, one elected lane issues) ----
+    constexpr uint32_t idesc = idesc_bf16(128, 32, !FWD);
+    bool ok = true;
+    int k = 0, c = 0;
+    for (int i = 0; i < items; ++i) {
+      const int s = i % S;
+      bool got = true;
+      // accumulator k & 1 is free once unit k - 2 has been read out
+      if (c == 0 && k >= 2) got = tc_wait(bar(Pl::kDE + (k & 1)), ((k - 2) >> 1) & 1, wait_ns, abort_flag);
+      if (got) got = tc_wait(bar(Pl::kBF + s), (i / S) & 1, wait_ns, abort_flag);
+      if (!__all_sync(0xffffffffu, got)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t D = tmem + 32u * (uint32_t)(k & 1);
+      const uint32_t a0 = sbase + (uint32_t)(s * Pl::kStage), b0 = a0 + Pl::kOffB;
+      if (elect_one()) {
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            const uint64_t ad = FWD ? desc_sw128(a0 + p * kHATile + 32 * ks, 16, 1024)
+                                    : desc_sw128(a0 + p * kHATile + 2048 * ks, 8192, 1024);
+            const uint64_t bd = desc_sw128(b0 + 32 * ks, 16, 1024);
+            mma_bf16_ss(D, ad, bd, idesc, (c > 0 || ks > 0 || p > 0) ? 1u : 0u);
+          }
+        tc_commit(bar(Pl::kSE + s));
+        if (c == nch - 1) tc_commit(bar(Pl::kDF + (k & 1)));
+      }
+      __syncwarp();
+      if (++c == nch) {
+        c = 0;
+        ++k;
+      }
+    }
+    if (!ok && lane == 0) {
+      *abort_flag = 1;
+      atomicExch(err, 1);
+    }
+    if (elect_one()) tc_commit(bar(Pl::kDR));  // all MMAs of this CTA
+    __syncwarp();
+    mbar_wait_bounded(bar(Pl::kDR), 0, kDrainNs);
+  } else {
+    // ---- B builders and epilogue: warps 0-3, thread t owns TMEM lane t ----
+    const int t = threadIdx.x;
+    const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
+    // this thread's B row n (0-15 hi, 16-31 lo; column n & 15: slot n & 7,
+    // re for n & 15 < 8, im otherwise) and K range 16 cq .. 16 cq + 15
+    const int n = t >> 2, cq = t & 3;
+    const bool lo = n >= 16;
+    const int nc = n & 15, sl = nc & 7;
+    const bool slot_ok = sl < d.GS;
+    // accumulator of local unit k to the output; false if the wait for its
+    // MMAs failed
+    auto epilogue = [&](int k, int o, int mt) -> bool {
+      const bool dgot = tc_wait(bar(Pl::kDF + (k & 1)), (k >> 1) & 1, wait_ns, abort_flag);
+      if (!__all_sync(0xffffffffu, dgot)) return false;
+      tc_fence_after();
+      uint32_t v[32];
+      uint32_t(&v0)[16] = *reinterpret_cast<uint32_t(*)[16]>(v);
+      uint32_t(&v1)[16] = *reinterpret_cast<uint32_t(*)[16]>(v + 16);
+      tc_ld16(tl + 32u * (uint32_t)(k & 1), v0);
+      tc_ld16(tl + 32u * (uint32_t)(k & 1) + 16, v1);
+      tc_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(Pl::kDE + (k & 1)));
+      float e[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) e[q] = __uint_as_float(v[q]) + __uint_as_float(v[16 + q]);
+      if (FWD) {
+        const int u = 128 * mt + t;
+        if (u < d.U) {
+          float2* dst = out + (size_t)u * d.Ns + o * d.GS;
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (q < d.GS) dst[q] = make_float2(e[q], e[8 + q]);
+        }
+      } else {
+        // lane pair (2 zz, 2 zz + 1) holds the Re and Im table rows of depth zz
+        float f[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) f[q] = __shfl_xor_sync(0xffffffffu, e[q], 1);
+        const int z = 32 * (2 * mt + (t >> 6)) + ((t & 63) >> 1);
+        if ((t & 1) == 0 && z < d.Nz) {
+          const int s0 = o * d.GS;  // the orbit's slots lie in one tile of 64
+          float2* dst = out + (((size_t)(s0 >> 6) * d.anzb + (z >> 5)) * 32 + (z & 31)) * 64 + (s0 & 63);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (q < d.GS) dst[q] = make_float2(e[q] + f[8 + q], e[8 + q] - f[q]);
+        }
+      }
+      return true;
+    };
+    bool ok = true;
+    int k = 0, c = 0;  // local unit, chunk
+    int o = first / nmt, mt = first - (first / nmt) * nmt;
+    int po = o, pmt = mt;  // the previous unit
+    for (int i = 0; i < items; ++i) {
+      const int s = i % S;
+      const bool got = (d.inject && i == 0) ? tc_wait(bar(Pl::kNV), 0, wait_ns, abort_flag)
+                                            : tc_wait(bar(Pl::kSF + s), (i / S) & 1, wait_ns, abort_flag);
+      if (!__all_sync(0xffffffffu, got)) {
+        ok = false;
+        break;
+      }
+      unsigned char* st = hsm + s * Pl::kStage;
+      const float* sp = (const float*)(st + Pl::kOffS);
+      uint32_t w[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        float v0, v1;
+        if (FWD) {  // K index 2 zz + q, zz = 8 cq + j
+          const float2 x = *(const float2*)(sp + (8 * cq + j) * 16 + 2 * sl);
+          v0 = nc < 8 ? x.x : x.y;
+          v1 = nc < 8 ? -x.y : x.x;
+        } else {  // K index = bin 16 cq + 2 j (+1)
+          const int ub = 16 * cq + 2 * j, comp = nc < 8 ? 0 : 1;
+          v0 = sp[ub * 16 + 2 * sl + comp];
+          v1 = sp[(ub + 1) * 16 + 2 * sl + comp];
+        }
+        if (!slot_ok) v0 = v1 = 0.f;
+        w[j] = bf16_pair_part(v0, v1, lo);
+      }
+      unsigned char* brow = st + Pl::kOffB + n * 128;
+      *(uint4*)(brow + (((2 * cq) ^ (n & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+      *(uint4*)(brow + (((2 * cq + 1) ^ (n & 7)) << 4)) = make_uint4(w[4], w[5], w[6], w[7]);
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(Pl::kBF + s));
+      // the previous unit's accumulator, now that this unit's first chunk is built
+      if (c == 0 && k >= 1 && !epilogue(k - 1, po, pmt)) {
+        ok = false;
+        break;
+      }
+      if (++c == nch) {
+        c = 0;
+        ++k;
+        po = o;
+        pmt = mt;
+        if (++mt == nmt) {
+          mt = 0;
+          ++o;
+        }
+      }
+    }
+    if (ok && items > 0 && !epilogue(k - 1, po, pmt)) ok = false;
+    if (!ok && lane == 0) {
+      *abort_flag = 1;
+      atomicExch(err, 1);
+    }
+  }
+  pdl_trigger();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tc_dealloc(tmem, kHCols);
+  }
+}
+
+template <bool FWD, int NP>
+int launch_h(const PlaneDims& d, const CUtensorMap& tab, const CUtensorMap& spec, float2* out, int* err,
+             cudaStream_t st) {
+  SFS_TRY(ensure_smem_attr(contract_h<FWD, NP>, HPlan<NP>::kSmem));
+  const int No = d.Ns / d.GS;
+  const int nmt = FWD ? (d.U + 127) / 128 : (d.nkb + 1) / 2;
+  const int nch = FWD ? d.nkb : (d.U + 63) / 64;
+  const int nunits = No * nmt;
+  const int G = std::min(d.G, nunits);
+  if (G <= 0) return SFS_OK;
+  return launch_pdl(contract_h<FWD, NP>, dim3(G), dim3(kHThreads), (size_t)HPlan<NP>::kSmem, st, tab, spec,
+                    out, d, nmt, nch, nunits, err);
+}
+
+int check_maps(const PlaneDims& d) {
+  if (!d.tmaps || (d.nparts != 1 && d.nparts != 2)) {
+    set_error("16-bit contraction without tensor maps");
+    return SFS_ERR_INVALID_ARG;
+  }
+  return SFS_OK;
+}
+
+}  // namespace
+
+int tc16_setup(sfs_operator* op) {
+  TcMaps* m = new (std::nothrow) TcMaps;
+  if (!m) {
+    set_error("host allocation failed");
+    return SFS_ERR_OOM;
+  }
+  const int planes = op->nparts * (op->Ns / op->GS);
+  int rc = encode_table(&m->tab_f, op->table, op->U, op->nkb, planes, 128);
+  if (rc == SFS_OK) rc = encode_table(&m->tab_a, op->table, op->U, op->nkb, planes, 64);
+  if (rc == SFS_OK) rc = encode_spec(&m->xh, op->ws.Xh, op->geo.d.Nz, op->Ns, 32);
+  if (rc == SFS_OK) rc = encode_spec(&m->rh, op->ws.Rh, op->Up, op->Ns, 64);
+  if (rc != SFS_OK) {
+    delete m;
+    return rc;
+  }
+  m->xh_ptr = op->ws.Xh;
+  m->rh_ptr = op->ws.Rh;
+  free_tc_maps(op->tmaps);
+  op->tmaps = m;
+  return SFS_OK;
+}
+
+int launch_contract_fwd_h(const PlaneDims& d, const float2* Xh, float2* Yp, int* err, cudaStream_t st) {
+  SFS_TRY(check_maps(d));
+  CUtensorMap local;
+  const CUtensorMap* spec = &d.tmaps->xh;
+  if (Xh != d.tmaps->xh_ptr) {  // spectra elsewhere than the operator's workspace
+    SFS_TRY(encode_spec(&local, Xh, d.Nz, d.Ns, 32));
+    spec = &local;
+  }
+  return d.nparts == 2 ? launch_h<true, 2>(d, d.tmaps->tab_f, *spec, Yp, err, st)
+                       : launch_h<true, 1>(d, d.tmaps->tab_f, *spec, Yp, err, st);
+}
+
+int launch_contract_adj_h(const PlaneDims& d, const float2* Rh, float2* Gs, int* err, cudaStream_t st) {
+  SFS_TRY(check_maps(d));
+  CUtensorMap local;
+  const CUtensorMap* spec = &d.tmaps->rh;
+  if (Rh != d.tmaps->rh_ptr) {  // e.g. the static scratch of sfs_apply_AH_noalloc
+    SFS_TRY(encode_spec(&local, Rh, d.Up, d.Ns, 64));
+    spec = &local;
+  }
+  return d.nparts == 2 ? launch_h<false, 2>(d, d.tmaps->tab_a, *spec, Gs, err, st)
+                       : launch_h<false, 1>(d, d.tmaps->tab_a, *spec, Gs, err, st);
+}
+
+int prepare_tc16_kernels(const PlaneDims& d) {
+  if (d.nparts == 2) {
+    SFS_TRY(ensure_smem_attr(contract_h<true, 2>, HPlan<2>::kSmem));
+    return ensure_smem_attr(contract_h<false, 2>, HPlan<2>::kSmem);
+  }
+  SFS_TRY(ensure_smem_attr(contract_h<true, 1>, HPlan<1>::kSmem));
+  return ensure_smem_attr(contract_h<false, 1>, HPlan<1>::kSmem);
+}
+
+}  // namespace sfs

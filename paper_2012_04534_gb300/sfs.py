@@ -33,6 +33,13 @@ SFS_SEL_RANDOM = 0
 SFS_SEL_CONTIGUOUS = 1
 SFS_SEL_EQUISPACED = 2
 
+SFS_PREC_FP32 = 0
+SFS_PREC_TF32X3 = 1
+SFS_PREC_BF16 = 2
+SFS_PREC_BF16X2 = 3
+PRECISION_NAMES = {"fp32": SFS_PREC_FP32, "tf32x3": SFS_PREC_TF32X3, "bf16": SFS_PREC_BF16,
+                   "bf16x2": SFS_PREC_BF16X2}
+
 SFS_FISTA_WARM_START = 1
 SFS_FISTA_TIME_KERNELS = 2
 
@@ -42,7 +49,8 @@ STATUS_NAMES = {0: "SFS_OK", -1: "SFS_ERR_INVALID_ARG", -2: "SFS_ERR_BAND_TOO_NA
 
 # every symbol include/sfs.h declares
 EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
-           "sfs_select_freqs", "sfs_operator_from_indices", "sfs_destroy_operator",
+           "sfs_select_freqs", "sfs_operator_from_indices", "sfs_operator_from_indices_prec",
+           "sfs_destroy_operator",
            "sfs_operator_info", "sfs_apply_A", "sfs_apply_AH", "sfs_apply_AH_noalloc",
            "sfs_max_abs_AH",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
@@ -74,7 +82,7 @@ class OperatorInfo(ctypes.Structure):
                 ("band_db", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("t0", ctypes.c_double), ("table_bytes", ctypes.c_int64),
                 ("launches_per_iter", ctypes.c_int32), ("Nslot", ctypes.c_int32),
-                ("GS", ctypes.c_int32)]
+                ("GS", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -101,6 +109,7 @@ def lib():
         "sfs_select_indices": [vp, i32, i32, i32, u64, P(ctypes.c_int32), P(ctypes.c_int32)],
         "sfs_select_freqs": [vp, i32, i32, i32, u64, P(ctypes.c_int32), P(ctypes.c_uint32), P(vp)],
         "sfs_operator_from_indices": [vp, i32, P(ctypes.c_int32), P(vp)],
+        "sfs_operator_from_indices_prec": [vp, i32, P(ctypes.c_int32), i32, P(vp)],
         "sfs_destroy_operator": [vp],
         "sfs_operator_info": [vp, P(OperatorInfo)],
         "sfs_apply_A": [vp, vp, vp, vp],
@@ -194,6 +203,15 @@ def sfs_operator_from_indices(geom, idx):
     h = ctypes.c_void_p()
     _check(lib().sfs_operator_from_indices(
         geom, idx.shape[1], idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(h)))
+    return h
+
+
+def sfs_operator_from_indices_prec(geom, idx, precision: int):
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(lib().sfs_operator_from_indices_prec(
+        geom, idx.shape[1], idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(precision),
+        ctypes.byref(h)))
     return h
 
 
@@ -305,7 +323,13 @@ class Operator:
         self.device = geom.device
 
     @classmethod
-    def select(cls, geom: Geometry, strategy=SFS_SEL_RANDOM, M=32, per_position=True, seed=0):
+    def select(cls, geom: Geometry, strategy=SFS_SEL_RANDOM, M=32, per_position=True, seed=0,
+               precision=None):
+        """Selection plus operator; `precision` (an SFS_PREC_* value) goes
+        through sfs_select_indices + sfs_operator_from_indices_prec."""
+        if precision is not None:
+            idx, _ = sfs_select_indices(geom.handle, strategy, M, per_position, seed, geom.S)
+            return cls.from_indices(geom, idx, precision)
         h, idx, mask = sfs_select_freqs(geom.handle, strategy, M, per_position, seed,
                                         geom.S, geom.Nt)
         op = cls(geom, h)
@@ -313,8 +337,12 @@ class Operator:
         return op
 
     @classmethod
-    def from_indices(cls, geom: Geometry, idx):
-        op = cls(geom, sfs_operator_from_indices(geom.handle, idx))
+    def from_indices(cls, geom: Geometry, idx, precision=None):
+        if precision is None:
+            h = sfs_operator_from_indices(geom.handle, idx)
+        else:
+            h = sfs_operator_from_indices_prec(geom.handle, idx, precision)
+        op = cls(geom, h)
         op.idx = np.ascontiguousarray(idx, dtype=np.int32)
         return op
 
