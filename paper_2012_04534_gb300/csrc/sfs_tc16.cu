@@ -28,14 +28,18 @@
 // significant bits and the table's rounding dominates the error.
 //
 // Per CTA (192 threads, two CTAs per SM, 64 TMEM columns):
-//   warp 4     issues the TMA copies of a chunk (table tile(s) and the
-//              chunk's spectra tile) into a stage, one mbarrier per stage;
-//   warps 0-3  build the chunk's B operand (hi and lo) in the stage from the
-//              spectra tile, and read a unit's accumulator (tcgen05.ld) once
-//              the next unit's first chunk is built;
+//   warp 4     issues the TMA copies of a chunk's table tile(s) into a stage
+//              of the table ring (one mbarrier per stage);
+//   warp 6     issues the TMA copy of a chunk's spectra tile into a slot of
+//              the operand ring (one mbarrier per slot), as far ahead as the
+//              slots allow;
+//   warps 0-3  build a chunk's B operand (hi and lo) in its slot from the
+//              spectra tile, and read a unit's accumulator (tcgen05.ld)
+//              while building the next unit's third chunk;
 //   warp 5     issues the 4 x parts MMAs of a chunk (M = 128, N = 32,
 //              K = 16) and commits to the barriers that free the stage and
-//              signal the accumulator (two, alternating by unit).
+//              the slot and signal the accumulator (two, alternating by
+//              unit).
 // Work: units (orbit, bin tile of 128) forward, (orbit, pair of depth
 // blocks) adjoint; a contiguous share of units per persistent CTA; a unit
 // runs over K in chunks (a 32-depth block forward, 64 bins adjoint).
@@ -191,8 +195,9 @@ __device__ __forceinline__ uint32_t bf16_pair_part(float v0, float v1, bool lo) 
 // ---------------------------------------------------------------------------
 // Shared-memory plan of one CTA
 // ---------------------------------------------------------------------------
-constexpr int kHThreads = 192;  // warps 0-3 build B and read out, 4 copies, 5 MMA
-constexpr int kHCopyWarp = 4, kHMmaWarp = 5;
+constexpr int kHThreads = 224;  // warps 0-3 build B and read out, 4 table copies, 5 MMA,
+                                // 6 spectra copies
+constexpr int kHCopyWarp = 4, kHMmaWarp = 5, kHSpecWarp = 6;
 constexpr int kHATile = 16384;  // A tile of one part: 128 rows x 128 B (or 2 x 64 rows)
 constexpr int kHBTile = 4096;   // B: 32 rows (16 hi, 16 lo) x 64 K x 2 B, swizzled
 constexpr int kHSTile = 4096;   // spectra tile: 32 depths x 64 B (fwd), 64 bins x 64 B (adj)
@@ -200,17 +205,25 @@ constexpr uint32_t kHCols = 64; // two accumulators of 32 columns
 
 template <int NP>
 struct HPlan {
-  static constexpr int kStages = NP == 1 ? 4 : 2;
-  static constexpr int kStage = NP * kHATile + kHBTile + kHSTile;
-  static constexpr int kOffB = NP * kHATile;  // within a stage
-  static constexpr int kOffS = kOffB + kHBTile;
-  // barriers: stage full / empty / B built, accumulator full / empty, MMA
-  // drain, one that nothing arrives at (failure-handling tests)
-  static constexpr int kSF = 0, kSE = kStages, kBF = 2 * kStages, kDF = 3 * kStages,
-                       kDE = kDF + 2, kDR = kDE + 2, kNV = kDR + 1, kNumBars = kNV + 1;
-  static constexpr int kOffBar = kStages * kStage;
+  // table ring: kST stages of NP A tiles; operand ring: kSB slots of a B
+  // tile and the spectra tile it is built from.  Each ring has its own
+  // producer warp, so a chunk's B is usually built before its table tile
+  // lands and a table stage is busy only for the copy and the MMAs.
+  static constexpr int kST = NP == 1 ? 5 : 2;
+  static constexpr int kSB = 3;
+  static constexpr int kLead = 2;  // the builders read out a unit at chunk kLead of the next
+  static constexpr int kTStage = NP * kHATile;
+  static constexpr int kBSlot = kHBTile + kHSTile;  // B at +0, spectra at +kHBTile
+  static constexpr int kOffRing = kST * kTStage;
+  // barriers: table full / empty, spectra full, slot empty, B built,
+  // accumulator full / empty, MMA drain, one that nothing arrives at
+  // (failure-handling tests)
+  static constexpr int kTF = 0, kTE = kST, kPF = 2 * kST, kPE = kPF + kSB, kBF = kPE + kSB,
+                       kDF = kBF + kSB, kDE = kDF + 2, kDR = kDE + 2, kNV = kDR + 1, kNumBars = kNV + 1;
+  static constexpr int kOffBar = kOffRing + kSB * kBSlot;
   static constexpr int kOffSlot = kOffBar + kNumBars * 8;
   static constexpr int kSmem = kOffSlot + 16 + 1024;  // + alignment of the base to 1 KB
+  static_assert(kLead < kSB, "operand ring lead");
 };
 
 template <bool FWD, int NP>
@@ -218,7 +231,7 @@ __global__ void __launch_bounds__(kHThreads, 2)
 contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUtensorMap spec,
            float2* __restrict__ out, PlaneDims d, int nmt, int nch, int nunits, int* __restrict__ err) {
   using Pl = HPlan<NP>;
-  constexpr int S = Pl::kStages;
+  constexpr int ST = Pl::kST, SB = Pl::kSB, LEAD = Pl::kLead;
   extern __shared__ unsigned char hsm_raw[];
   // 128-byte-swizzled tiles need 1 KB alignment of the shared-memory address
   unsigned char* hsm = hsm_raw + ((1024u - (smem_addr(hsm_raw) & 1023u)) & 1023u);
@@ -233,12 +246,23 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
   const int items = ((int)(((long long)nunits * (b + 1)) / G) - first) * nch;
   const uint64_t wait_ns = d.wait_ns;
   const int No = d.Ns / d.GS;
+  // item j of this CTA: unit first + j / nch = (orbit o, tile mt), chunk c
+  auto item = [&](int j, int& o, int& mt, int& c) {
+    const int unit = first + j / nch;
+    c = j - (j / nch) * nch;
+    o = unit / nmt;
+    mt = unit - o * nmt;
+  };
 
   if (threadIdx.x == 0) {
     *abort_flag = 0;
-    for (int k = 0; k < S; ++k) {
-      mbar_init(bar(Pl::kSF + k), 1);
-      mbar_init(bar(Pl::kSE + k), 1);
+    for (int k = 0; k < ST; ++k) {
+      mbar_init(bar(Pl::kTF + k), 1);
+      mbar_init(bar(Pl::kTE + k), 1);
+    }
+    for (int k = 0; k < SB; ++k) {
+      mbar_init(bar(Pl::kPF + k), 1);
+      mbar_init(bar(Pl::kPE + k), 1);
       mbar_init(bar(Pl::kBF + k), 4);
     }
     for (int k = 0; k < 2; ++k) {
@@ -258,73 +282,96 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  if (warp == kHCopyWarp) {
-    // ---- copy producer: a chunk's table tile(s) and spectra tile ----
+  if (warp == kHSpecWarp) {
+    // ---- spectra producer: the spectra tile of item j into operand slot j % SB ----
     int issued = 0;
     bool ok = true;
-    int c = 0;
-    int o = first / nmt, mt = first - (first / nmt) * nmt;
     pdl_wait();  // the spectra come from the previous kernel
-    for (int i = 0; i < items; ++i) {
-      const int s = i % S;
-      if (i >= S) {
-        const bool got = tc_wait(bar(Pl::kSE + s), ((i / S) + 1) & 1, wait_ns, abort_flag);
+    for (int j = 0; j < items; ++j) {
+      const int sl = j % SB;
+      if (j >= SB) {
+        const bool got = tc_wait(bar(Pl::kPE + sl), ((j / SB) + 1) & 1, wait_ns, abort_flag);
         if (!__all_sync(0xffffffffu, got)) {
           ok = false;
           break;
         }
       }
+      int o, mt, c;
+      item(j, o, mt, c);
       if (elect_one()) {
-        const uint32_t dst = sbase + (uint32_t)(s * Pl::kStage), fb = bar(Pl::kSF + s);
-        mbar_expect_tx(fb, NP * kHATile + (FWD ? 2048 : 4096));
+        const uint32_t fb = bar(Pl::kPF + sl);
+        mbar_expect_tx(fb, FWD ? 2048 : 4096);
+        tma_load_2d(sbase + Pl::kOffRing + sl * Pl::kBSlot + kHBTile, &spec, 2 * o * d.GS,
+                    (FWD ? 32 : 64) * c, fb);
+      }
+      __syncwarp();
+      ++issued;
+    }
+    if (!ok && lane == 0) {
+      *abort_flag = 1;
+      atomicExch(err, 1);
+    }
+    for (int j = max(0, issued - SB); j < issued; ++j)
+      mbar_wait_bounded(bar(Pl::kPF + j % SB), (j / SB) & 1, kDrainNs);
+  } else if (warp == kHCopyWarp) {
+    // ---- table producer: the table tile(s) of item i into stage i % ST ----
+    int issued = 0;
+    bool ok = true;
+    for (int i = 0; i < items; ++i) {
+      const int s = i % ST;
+      if (i >= ST) {
+        const bool got = tc_wait(bar(Pl::kTE + s), ((i / ST) + 1) & 1, wait_ns, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+      }
+      int o, mt, c;
+      item(i, o, mt, c);
+      if (elect_one()) {
+        const uint32_t dst = sbase + (uint32_t)(s * Pl::kTStage), fb = bar(Pl::kTF + s);
+        mbar_expect_tx(fb, NP * kHATile);
         if (FWD) {  // bins 128 mt .., depth block c
 #pragma unroll
           for (int p = 0; p < NP; ++p) tma_load_4d(dst + p * kHATile, &tab, 0, 128 * mt, c, p * No + o, fb);
-          tma_load_2d(dst + Pl::kOffS, &spec, 2 * o * d.GS, 32 * c, fb);
         } else {  // bins 64 c .., depth blocks 2 mt and 2 mt + 1
 #pragma unroll
           for (int p = 0; p < NP; ++p) {
             tma_load_4d(dst + p * kHATile, &tab, 0, 64 * c, 2 * mt, p * No + o, fb);
             tma_load_4d(dst + p * kHATile + 8192, &tab, 0, 64 * c, 2 * mt + 1, p * No + o, fb);
           }
-          tma_load_2d(dst + Pl::kOffS, &spec, 2 * o * d.GS, 64 * c, fb);
         }
       }
       __syncwarp();
       ++issued;
-      if (++c == nch) {
-        c = 0;
-        if (++mt == nmt) {
-          mt = 0;
-          ++o;
-        }
-      }
     }
     if (!ok && lane == 0) {
       *abort_flag = 1;
       atomicExch(err, 1);
     }
     // copies in flight: the latest use of each stage
-    for (int i = max(0, issued - S); i < issued; ++i)
-      mbar_wait_bounded(bar(Pl::kSF + i % S), (i / S) & 1, kDrainNs);
+    for (int i = max(0, issued - ST); i < issued; ++i)
+      mbar_wait_bounded(bar(Pl::kTF + i % ST), (i / ST) & 1, kDrainNs);
   } else if (warp == kHMmaWarp) {
     // ---- MMA issuer (whole warp, one elected lane issues) ----
     constexpr uint32_t idesc = idesc_bf16(128, 32, !FWD);
     bool ok = true;
     int k = 0, c = 0;
     for (int i = 0; i < items; ++i) {
-      const int s = i % S;
+      const int s = i % ST, sl = i % SB;
       bool got = true;
       // accumulator k & 1 is free once unit k - 2 has been read out
       if (c == 0 && k >= 2) got = tc_wait(bar(Pl::kDE + (k & 1)), ((k - 2) >> 1) & 1, wait_ns, abort_flag);
-      if (got) got = tc_wait(bar(Pl::kBF + s), (i / S) & 1, wait_ns, abort_flag);
+      if (got) got = tc_wait(bar(Pl::kBF + sl), (i / SB) & 1, wait_ns, abort_flag);
+      if (got) got = tc_wait(bar(Pl::kTF + s), (i / ST) & 1, wait_ns, abort_flag);
       if (!__all_sync(0xffffffffu, got)) {
         ok = false;
         break;
       }
       tc_fence_after();
       const uint32_t D = tmem + 32u * (uint32_t)(k & 1);
-      const uint32_t a0 = sbase + (uint32_t)(s * Pl::kStage), b0 = a0 + Pl::kOffB;
+      const uint32_t a0 = sbase + (uint32_t)(s * Pl::kTStage);
+      const uint32_t b0 = sbase + (uint32_t)(Pl::kOffRing + sl * Pl::kBSlot);
       if (elect_one()) {
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks)
@@ -335,7 +382,8 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
             const uint64_t bd = desc_sw128(b0 + 32 * ks, 16, 1024);
             mma_bf16_ss(D, ad, bd, idesc, (c > 0 || ks > 0 || p > 0) ? 1u : 0u);
           }
-        tc_commit(bar(Pl::kSE + s));
+        tc_commit(bar(Pl::kTE + s));
+        tc_commit(bar(Pl::kPE + sl));
         if (c == nch - 1) tc_commit(bar(Pl::kDF + (k & 1)));
       }
       __syncwarp();
@@ -359,11 +407,13 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
     // re for n & 15 < 8, im otherwise) and K range 16 cq .. 16 cq + 15
     const int n = t >> 2, cq = t & 3;
     const bool lo = n >= 16;
-    const int nc = n & 15, sl = nc & 7;
-    const bool slot_ok = sl < d.GS;
+    const int nc = n & 15, sl8 = nc & 7;
+    const bool slot_ok = sl8 < d.GS;
     // accumulator of local unit k to the output; false if the wait for its
     // MMAs failed
-    auto epilogue = [&](int k, int o, int mt) -> bool {
+    auto epilogue = [&](int k) -> bool {
+      int o, mt, c;
+      item(k * nch, o, mt, c);
       const bool dgot = tc_wait(bar(Pl::kDF + (k & 1)), (k >> 1) & 1, wait_ns, abort_flag);
       if (!__all_sync(0xffffffffu, dgot)) return false;
       tc_fence_after();
@@ -403,59 +453,53 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
       }
       return true;
     };
+    // a unit's accumulator is read out while the builders are at chunk ce of
+    // the next unit, by when the MMAs of the unit have usually completed
+    const int ce = min(LEAD, nch - 1);
     bool ok = true;
     int k = 0, c = 0;  // local unit, chunk
-    int o = first / nmt, mt = first - (first / nmt) * nmt;
-    int po = o, pmt = mt;  // the previous unit
     for (int i = 0; i < items; ++i) {
-      const int s = i % S;
+      const int sl = i % SB;
       const bool got = (d.inject && i == 0) ? tc_wait(bar(Pl::kNV), 0, wait_ns, abort_flag)
-                                            : tc_wait(bar(Pl::kSF + s), (i / S) & 1, wait_ns, abort_flag);
+                                            : tc_wait(bar(Pl::kPF + sl), (i / SB) & 1, wait_ns, abort_flag);
       if (!__all_sync(0xffffffffu, got)) {
         ok = false;
         break;
       }
-      unsigned char* st = hsm + s * Pl::kStage;
-      const float* sp = (const float*)(st + Pl::kOffS);
+      unsigned char* slot = hsm + Pl::kOffRing + sl * Pl::kBSlot;
+      const float* sp = (const float*)(slot + kHBTile);
       uint32_t w[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         float v0, v1;
         if (FWD) {  // K index 2 zz + q, zz = 8 cq + j
-          const float2 x = *(const float2*)(sp + (8 * cq + j) * 16 + 2 * sl);
+          const float2 x = *(const float2*)(sp + (8 * cq + j) * 16 + 2 * sl8);
           v0 = nc < 8 ? x.x : x.y;
           v1 = nc < 8 ? -x.y : x.x;
         } else {  // K index = bin 16 cq + 2 j (+1)
           const int ub = 16 * cq + 2 * j, comp = nc < 8 ? 0 : 1;
-          v0 = sp[ub * 16 + 2 * sl + comp];
-          v1 = sp[(ub + 1) * 16 + 2 * sl + comp];
+          v0 = sp[ub * 16 + 2 * sl8 + comp];
+          v1 = sp[(ub + 1) * 16 + 2 * sl8 + comp];
         }
         if (!slot_ok) v0 = v1 = 0.f;
         w[j] = bf16_pair_part(v0, v1, lo);
       }
-      unsigned char* brow = st + Pl::kOffB + n * 128;
+      unsigned char* brow = slot + n * 128;
       *(uint4*)(brow + (((2 * cq) ^ (n & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
       *(uint4*)(brow + (((2 * cq + 1) ^ (n & 7)) << 4)) = make_uint4(w[4], w[5], w[6], w[7]);
       fence_proxy_async();
       __syncwarp();
-      if (lane == 0) mbar_arrive(bar(Pl::kBF + s));
-      // the previous unit's accumulator, now that this unit's first chunk is built
-      if (c == 0 && k >= 1 && !epilogue(k - 1, po, pmt)) {
+      if (lane == 0) mbar_arrive(bar(Pl::kBF + sl));
+      if (c == ce && k >= 1 && !epilogue(k - 1)) {
         ok = false;
         break;
       }
       if (++c == nch) {
         c = 0;
         ++k;
-        po = o;
-        pmt = mt;
-        if (++mt == nmt) {
-          mt = 0;
-          ++o;
-        }
       }
     }
-    if (ok && items > 0 && !epilogue(k - 1, po, pmt)) ok = false;
+    if (ok && items > 0 && !epilogue(k - 1)) ok = false;
     if (!ok && lane == 0) {
       *abort_flag = 1;
       atomicExch(err, 1);

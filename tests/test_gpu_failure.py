@@ -30,11 +30,15 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex64)).cuda()
 
 
-def test_forced_wait_timeout_is_reported_and_recoverable(sfs):
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "bf16", "bf16x2"])
+def test_forced_wait_timeout_is_reported_and_recoverable(sfs, precision):
+    """Every contraction kernel family: CUDA cores, tf32 tensor cores, and the
+    TMA-fed 16-bit tensor-core kernels (one and two table parts)."""
     import torch
     params = geom_params(Nx=32, Ny=32, Nz=128, dz=0.15e-3, Nt=512)
     g = sfs.Geometry(**params)
-    op = sfs.Operator.select(g, O.SEL_RANDOM, 64, True, 3)
+    op = sfs.Operator.select(g, O.SEL_RANDOM, 64, True, 3,
+                             precision=sfs.PRECISION_NAMES[precision])
     rng = np.random.default_rng(0)
     x = to_dev(crandn(rng, *op.shape_x))
     y = to_dev(crandn(rng, *op.shape_y))
