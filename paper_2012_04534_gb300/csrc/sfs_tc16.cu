@@ -31,11 +31,11 @@
 //   warp 4     issues the TMA copies of a chunk's table tile(s) into a stage
 //              of the table ring (one mbarrier per stage);
 //   warp 6     issues the TMA copy of a chunk's spectra tile into a slot of
-//              the operand ring (one mbarrier per slot), as far ahead as the
-//              slots allow;
-//   warps 0-3  build a chunk's B operand (hi and lo) in its slot from the
-//              spectra tile, and read a unit's accumulator (tcgen05.ld)
-//              while building the next unit's third chunk;
+//              the spectra ring (8 slots, one mbarrier per slot), as far
+//              ahead as the slots allow;
+//   warps 0-3  build a chunk's B operand (hi and lo) from its spectra tile
+//              into a slot of the B ring, and read a unit's accumulator
+//              (tcgen05.ld) while building the next unit's third chunk;
 //   warp 5     issues the 4 x parts MMAs of a chunk (M = 128, N = 32,
 //              K = 16) and commits to the barriers that free the stage and
 //              the slot and signal the accumulator (two, alternating by
@@ -205,25 +205,28 @@ constexpr uint32_t kHCols = 64; // two accumulators of 32 columns
 
 template <int NP>
 struct HPlan {
-  // table ring: kST stages of NP A tiles; operand ring: kSB slots of a B
-  // tile and the spectra tile it is built from.  Each ring has its own
-  // producer warp, so a chunk's B is usually built before its table tile
-  // lands and a table stage is busy only for the copy and the MMAs.
-  static constexpr int kST = NP == 1 ? 5 : 2;
-  static constexpr int kSB = 3;
+  // Three rings, each with its own producer: the table ring (kST stages of
+  // NP A tiles, filled by TMA), the spectra ring (kSS slots of spectra
+  // tiles, filled by TMA, emptied by the builders once read) and the B ring
+  // (kSBB slots of B operands, built by the builders, emptied by the MMAs).
+  // The spectra ring is deep so that the spectra copies, which queue behind
+  // the table stream, land well before the builders need them.
+  static constexpr int kST = NP == 1 ? 4 : 2;
+  static constexpr int kSS = 8;
+  static constexpr int kSBB = 3;
   static constexpr int kLead = 2;  // the builders read out a unit at chunk kLead of the next
   static constexpr int kTStage = NP * kHATile;
-  static constexpr int kBSlot = kHBTile + kHSTile;  // B at +0, spectra at +kHBTile
-  static constexpr int kOffRing = kST * kTStage;
-  // barriers: table full / empty, spectra full, slot empty, B built,
+  static constexpr int kOffB = kST * kTStage;          // B ring (1 KB aligned)
+  static constexpr int kOffS = kOffB + kSBB * kHBTile;  // spectra ring
+  // barriers: table full / empty, spectra full / empty, B built / empty,
   // accumulator full / empty, MMA drain, one that nothing arrives at
   // (failure-handling tests)
-  static constexpr int kTF = 0, kTE = kST, kPF = 2 * kST, kPE = kPF + kSB, kBF = kPE + kSB,
-                       kDF = kBF + kSB, kDE = kDF + 2, kDR = kDE + 2, kNV = kDR + 1, kNumBars = kNV + 1;
-  static constexpr int kOffBar = kOffRing + kSB * kBSlot;
+  static constexpr int kTF = 0, kTE = kST, kXF = 2 * kST, kXE = kXF + kSS, kBF = kXE + kSS,
+                       kBE = kBF + kSBB, kDF = kBE + kSBB, kDE = kDF + 2, kDR = kDE + 2, kNV = kDR + 1,
+                       kNumBars = kNV + 1;
+  static constexpr int kOffBar = kOffS + kSS * kHSTile;
   static constexpr int kOffSlot = kOffBar + kNumBars * 8;
   static constexpr int kSmem = kOffSlot + 16 + 1024;  // + alignment of the base to 1 KB
-  static_assert(kLead < kSB, "operand ring lead");
 };
 
 template <bool FWD, int NP>
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(kHThreads, 2)
 contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUtensorMap spec,
            float2* __restrict__ out, PlaneDims d, int nmt, int nch, int nunits, int* __restrict__ err) {
   using Pl = HPlan<NP>;
-  constexpr int ST = Pl::kST, SB = Pl::kSB, LEAD = Pl::kLead;
+  constexpr int ST = Pl::kST, SS = Pl::kSS, SBB = Pl::kSBB, LEAD = Pl::kLead;
   extern __shared__ unsigned char hsm_raw[];
   // 128-byte-swizzled tiles need 1 KB alignment of the shared-memory address
   unsigned char* hsm = hsm_raw + ((1024u - (smem_addr(hsm_raw) & 1023u)) & 1023u);
@@ -260,10 +263,13 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
       mbar_init(bar(Pl::kTF + k), 1);
       mbar_init(bar(Pl::kTE + k), 1);
     }
-    for (int k = 0; k < SB; ++k) {
-      mbar_init(bar(Pl::kPF + k), 1);
-      mbar_init(bar(Pl::kPE + k), 1);
+    for (int k = 0; k < SS; ++k) {
+      mbar_init(bar(Pl::kXF + k), 1);
+      mbar_init(bar(Pl::kXE + k), 4);
+    }
+    for (int k = 0; k < SBB; ++k) {
       mbar_init(bar(Pl::kBF + k), 4);
+      mbar_init(bar(Pl::kBE + k), 1);
     }
     for (int k = 0; k < 2; ++k) {
       mbar_init(bar(Pl::kDF + k), 1);
@@ -283,14 +289,14 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
   const uint32_t tmem = *tslot;
 
   if (warp == kHSpecWarp) {
-    // ---- spectra producer: the spectra tile of item j into operand slot j % SB ----
+    // ---- spectra producer: the spectra tile of item j into slot j % SS ----
     int issued = 0;
     bool ok = true;
     pdl_wait();  // the spectra come from the previous kernel
     for (int j = 0; j < items; ++j) {
-      const int sl = j % SB;
-      if (j >= SB) {
-        const bool got = tc_wait(bar(Pl::kPE + sl), ((j / SB) + 1) & 1, wait_ns, abort_flag);
+      const int sl = j % SS;
+      if (j >= SS) {
+        const bool got = tc_wait(bar(Pl::kXE + sl), ((j / SS) + 1) & 1, wait_ns, abort_flag);
         if (!__all_sync(0xffffffffu, got)) {
           ok = false;
           break;
@@ -299,10 +305,9 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
       int o, mt, c;
       item(j, o, mt, c);
       if (elect_one()) {
-        const uint32_t fb = bar(Pl::kPF + sl);
+        const uint32_t fb = bar(Pl::kXF + sl);
         mbar_expect_tx(fb, FWD ? 2048 : 4096);
-        tma_load_2d(sbase + Pl::kOffRing + sl * Pl::kBSlot + kHBTile, &spec, 2 * o * d.GS,
-                    (FWD ? 32 : 64) * c, fb);
+        tma_load_2d(sbase + Pl::kOffS + sl * kHSTile, &spec, 2 * o * d.GS, (FWD ? 32 : 64) * c, fb);
       }
       __syncwarp();
       ++issued;
@@ -311,8 +316,8 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
       *abort_flag = 1;
       atomicExch(err, 1);
     }
-    for (int j = max(0, issued - SB); j < issued; ++j)
-      mbar_wait_bounded(bar(Pl::kPF + j % SB), (j / SB) & 1, kDrainNs);
+    for (int j = max(0, issued - SS); j < issued; ++j)
+      mbar_wait_bounded(bar(Pl::kXF + j % SS), (j / SS) & 1, kDrainNs);
   } else if (warp == kHCopyWarp) {
     // ---- table producer: the table tile(s) of item i into stage i % ST ----
     int issued = 0;
@@ -358,11 +363,11 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
     bool ok = true;
     int k = 0, c = 0;
     for (int i = 0; i < items; ++i) {
-      const int s = i % ST, sl = i % SB;
+      const int s = i % ST, sl = i % SBB;
       bool got = true;
       // accumulator k & 1 is free once unit k - 2 has been read out
       if (c == 0 && k >= 2) got = tc_wait(bar(Pl::kDE + (k & 1)), ((k - 2) >> 1) & 1, wait_ns, abort_flag);
-      if (got) got = tc_wait(bar(Pl::kBF + sl), (i / SB) & 1, wait_ns, abort_flag);
+      if (got) got = tc_wait(bar(Pl::kBF + sl), (i / SBB) & 1, wait_ns, abort_flag);
       if (got) got = tc_wait(bar(Pl::kTF + s), (i / ST) & 1, wait_ns, abort_flag);
       if (!__all_sync(0xffffffffu, got)) {
         ok = false;
@@ -371,7 +376,7 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
       tc_fence_after();
       const uint32_t D = tmem + 32u * (uint32_t)(k & 1);
       const uint32_t a0 = sbase + (uint32_t)(s * Pl::kTStage);
-      const uint32_t b0 = sbase + (uint32_t)(Pl::kOffRing + sl * Pl::kBSlot);
+      const uint32_t b0 = sbase + (uint32_t)(Pl::kOffB + sl * kHBTile);
       if (elect_one()) {
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks)
@@ -383,7 +388,7 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
             mma_bf16_ss(D, ad, bd, idesc, (c > 0 || ks > 0 || p > 0) ? 1u : 0u);
           }
         tc_commit(bar(Pl::kTE + s));
-        tc_commit(bar(Pl::kPE + sl));
+        tc_commit(bar(Pl::kBE + sl));
         if (c == nch - 1) tc_commit(bar(Pl::kDF + (k & 1)));
       }
       __syncwarp();
@@ -459,15 +464,16 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
     bool ok = true;
     int k = 0, c = 0;  // local unit, chunk
     for (int i = 0; i < items; ++i) {
-      const int sl = i % SB;
-      const bool got = (d.inject && i == 0) ? tc_wait(bar(Pl::kNV), 0, wait_ns, abort_flag)
-                                            : tc_wait(bar(Pl::kPF + sl), (i / SB) & 1, wait_ns, abort_flag);
+      const int xs = i % SS, sl = i % SBB;
+      bool got = (d.inject && i == 0) ? tc_wait(bar(Pl::kNV), 0, wait_ns, abort_flag)
+                                      : tc_wait(bar(Pl::kXF + xs), (i / SS) & 1, wait_ns, abort_flag);
+      // the B slot is free once the MMAs of item i - SBB are done
+      if (got && i >= SBB) got = tc_wait(bar(Pl::kBE + sl), ((i / SBB) + 1) & 1, wait_ns, abort_flag);
       if (!__all_sync(0xffffffffu, got)) {
         ok = false;
         break;
       }
-      unsigned char* slot = hsm + Pl::kOffRing + sl * Pl::kBSlot;
-      const float* sp = (const float*)(slot + kHBTile);
+      const float* sp = (const float*)(hsm + Pl::kOffS + xs * kHSTile);
       uint32_t w[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
@@ -484,7 +490,9 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
         if (!slot_ok) v0 = v1 = 0.f;
         w[j] = bf16_pair_part(v0, v1, lo);
       }
-      unsigned char* brow = slot + n * 128;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(Pl::kXE + xs));  // spectra slot read
+      unsigned char* brow = hsm + Pl::kOffB + sl * kHBTile + n * 128;
       *(uint4*)(brow + (((2 * cq) ^ (n & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
       *(uint4*)(brow + (((2 * cq + 1) ^ (n & 7)) << 4)) = make_uint4(w[4], w[5], w[6], w[7]);
       fence_proxy_async();
