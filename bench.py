@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision-study", action="store_true",
+                    help="skip the BF16 / BF16X2 vs FP32 time-to-same-NMSE study")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -59,6 +61,69 @@ DTYPE_OF = {"fp32": "c64 (f32)",
             "tf32x3": "c64 (f32 state; contractions tf32 hi/lo x3 on tensor cores, f32 accumulate)",
             "bf16": "c64 (f32 state; contractions bf16 table x bf16 hi/lo spectra, f32 accumulate)",
             "bf16x2": "c64 (f32 state; contractions bf16 hi/lo table x bf16 hi/lo spectra, f32 accumulate)"}
+
+
+def precision_study(sfs, torch, geom, op, args, w, iters, y, L, x_true, flush, stream):
+    """FISTA with the FP32 contractions against the BF16 and BF16X2 ones on the
+    same scene, measurements, lambda rule and L: per mode the device time of
+    one solve (L2 flushed first), the NMSE against the true scene, and the
+    iterations and time a reduced-precision solve needs to reach the FP32
+    solve's NMSE (first of K, 1.1 K, 1.25 K, 1.5 K, 2 K iterations within
+    0.01 dB).  Errors are stated against the FP32 result of the same call
+    (which itself matches the FP64 oracle to about 1e-6 in the tests)."""
+    xt = torch.from_numpy(x_true.astype(np.complex64)).cuda()
+    ops = {}
+    for mode in ("fp32", "bf16", "bf16x2"):
+        ops[mode] = op if args.precision == mode else sfs.Operator.from_indices(
+            geom, op.idx, precision=sfs.PRECISION_NAMES[mode])
+
+    def solve(o, k):
+        x = torch.empty(o.shape_x, dtype=torch.complex64, device="cuda")
+        o.fista(y, -w["mu"], L, k, x=x)  # warm (graph capture for k)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(3):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            o.fista(y, -w["mu"], L, k, x=x)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b)
+            best = t if best is None else min(best, t)
+        return best, x.cpu().numpy().astype(np.complex128)
+
+    def nmse_db(x):
+        return float(10 * np.log10(np.linalg.norm(x - x_true) ** 2 / np.linalg.norm(x_true) ** 2))
+
+    ax32 = ops["fp32"].apply_A(xt).cpu().numpy().astype(np.complex128)
+    t32, x32 = solve(ops["fp32"], iters)
+    target = nmse_db(x32)
+    out = {"reference": "fp32", "iters": iters, "target_nmse_db": target,
+           "timing": "device time of one solve (lambda rule + iterations), best of 3, L2 flushed first",
+           "modes": {"fp32": {"ms_per_solve": t32, "nmse_db": target,
+                              "table_bytes": ops["fp32"].info["table_bytes"]}}}
+    for mode in ("bf16", "bf16x2"):
+        o = ops[mode]
+        axm = o.apply_A(xt).cpu().numpy().astype(np.complex128)
+        tk, xk = solve(o, iters)
+        rec = {"ms_per_solve": tk, "nmse_db": nmse_db(xk), "table_bytes": o.info["table_bytes"],
+               "rel_err_Ax_vs_fp32": float(np.linalg.norm(axm - ax32) / np.linalg.norm(ax32)),
+               "rel_err_x_vs_fp32": float(np.linalg.norm(xk - x32) / np.linalg.norm(x32))}
+        reach = None
+        for f in (1.0, 1.1, 1.25, 1.5, 2.0):
+            k = int(math.ceil(f * iters))
+            t, xk2 = (tk, xk) if k == iters else solve(o, k)
+            if nmse_db(xk2) <= target + 0.01:
+                reach = (k, t)
+                break
+        if reach is not None:
+            rec.update({"iters_to_target": reach[0], "ms_to_target": reach[1],
+                        "speedup_vs_fp32": t32 / reach[1]})
+        else:
+            rec.update({"iters_to_target": None, "ms_to_target": None, "speedup_vs_fp32": None})
+        out["modes"][mode] = rec
+    return out
 
 
 def workload_desc(name, w, strategy, iters):
@@ -211,14 +276,18 @@ def run_reference(args, rank, world):
 
 
 def kernel_source_hash():
+    """Hash of every kernel source file: a traffic record taken on other
+    sources is stale."""
     h = hashlib.sha256()
-    for f in ("sfs_kernels.cu", "sfs_fft.cuh"):
-        with open(os.path.join(ROOT, "paper_2012_04534_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_2012_04534_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def measured_traffic(workload, strategy):
+def measured_traffic(workload, strategy, precision):
     """DRAM bytes per contraction launch from the committed ncu summary, if it
     was taken on the current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", "contract_traffic.json")
@@ -227,7 +296,7 @@ def measured_traffic(workload, strategy):
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    key = "%s/%s" % (workload, strategy)
+    key = "%s/%s/%s" % (workload, strategy, precision)
     ent = rec.get(key)
     if not ent or ent.get("source_hash") != kernel_source_hash():
         return None
@@ -374,7 +443,7 @@ def main():
     avg_ms = 0.5 * (fwd_ms + adj_ms)
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
     achieved_tf = alg_flops / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else 0.0
-    traffic = measured_traffic(args.workload, args.strategy)
+    traffic = measured_traffic(args.workload, args.strategy, args.precision)
     hbm_frac, alu_frac = achieved / peak, achieved_tf / alu_peak
     if hbm_frac >= alu_frac or args.precision != "fp32":
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -390,6 +459,12 @@ def main():
                  "fwd_ms": fwd_ms, "adj_ms": adj_ms, "launches_timed": 2 * n_launch,
                  "iteration_stages_ms": {"contract_fwd": stage_ms[0], "resid_planes": stage_ms[1],
                                          "contract_adj": stage_ms[2], "update_planes": stage_ms[3]}})
+
+    # ---- precision study: reduced-precision contractions vs FP32, time to
+    # the FP32 solve's NMSE (rank 0 at N = 1 only) ----
+    study = None
+    if rank == 0 and world == 1 and not args.no_precision_study:
+        study = precision_study(sfs, torch, geom, op, args, w, iters, y, L, x_true, flush, stream)
 
     # ---- CPU baseline: the FP64 oracle, bounded sample, rank 0 only ----
     cpu = None
@@ -426,6 +501,8 @@ def main():
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if study is not None:
+            line["precision_study"] = study
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
