@@ -222,6 +222,34 @@ int sfs_apply_AH(sfs_operator* op, const void* y_dev, void* x_dev, void* stream)
 int sfs_apply_AH_noalloc(sfs_operator* op, const void* y_dev, void* x_dev, void* stream);
 
 /*
+ * Batched projections and FISTA: `batch` independent scenes measured with
+ * the same geometry and the same kept bins (one operator) processed by one
+ * sequence of launches.  This is the serving pattern of a fixed acquisition
+ * system, whose frequency sub-sampling is set once (Sec. III) and then
+ * applied to every scan.  Scene b occupies x_dev + b V and y_dev + b S M
+ * (c64, layouts as for the single-scene calls).  The lateral-FFT plane
+ * kernels run the planes of all scenes in one grid; the depth contractions
+ * of the 16-bit precisions read each table tile once for a group of up to
+ * four scenes (a GEMM with N = 32 columns per scene); the other precisions
+ * run one contraction per scene.  The library keeps a batched workspace in
+ * the operator, allocated on the first call for a batch size and grown on
+ * demand (these calls may therefore allocate, and synchronise the device
+ * when they do).  1 <= batch <= SFS_MAX_BATCH.
+ * sfs_fista_batched: Algorithm 1 on every scene with the same L and
+ * iteration count; lambda >= 0 is used for every scene, lambda < 0 means
+ * lambda_b = -lambda ||A^H y_b||_inf per scene (the mu rule of Sec. VII);
+ * x_out_dev receives x_iters of every scene (no warm start, no monitor).
+ * Errors: SFS_ERR_INVALID_ARG, SFS_ERR_OOM, SFS_ERR_CUDA.
+ */
+#define SFS_MAX_BATCH 256
+int sfs_apply_A_batched(sfs_operator* op, int batch, const void* x_dev, void* y_dev,
+                        void* stream);
+int sfs_apply_AH_batched(sfs_operator* op, int batch, const void* y_dev, void* x_dev,
+                         void* stream);
+int sfs_fista_batched(sfs_operator* op, int batch, const void* y_dev, double lambda,
+                      double L, int iters, void* x_out_dev, void* stream);
+
+/*
  * ||A^H y||_inf (used by the regularisation rule lambda = mu ||beta(y)||_inf
  * of Sec. VII).  Synchronises `stream`; writes the value to *out_host.
  */

@@ -178,6 +178,23 @@ int dev_alloc(T** p, size_t count) {
   return SFS_OK;
 }
 
+// Batched workspace and the loops captured on it.
+void free_batch(sfs_operator* op) {
+  sfs::BatchWorkspace& w = op->bws;
+  for (auto& ge : op->bgraphs) cudaGraphExecDestroy(ge.exec);
+  op->bgraphs.clear();
+  cudaFree(w.Xh);
+  cudaFree(w.Yh);
+  cudaFree(w.Rh);
+  cudaFree(w.Gh);
+  cudaFree(w.xk);
+  cudaFree(w.gam);
+  cudaFree(w.yplane);
+  cudaFree(w.ybuf);
+  cudaFree(w.scal);
+  w = sfs::BatchWorkspace();
+}
+
 void free_operator(sfs_operator* op) {
   if (!op) return;
   cudaFree(op->table);
@@ -202,6 +219,7 @@ void free_operator(sfs_operator* op) {
   for (auto& ge : op->graphs) cudaGraphExecDestroy(ge.exec);
   if (op->capture_stream) cudaStreamDestroy(op->capture_stream);
   free_tc_maps(op->tmaps);
+  free_batch(op);
   delete op;
 }
 
@@ -237,6 +255,16 @@ PlaneDims operator_dims(const sfs_operator* op) {
   d.inject = op->inject;
   d.slot_kappa = op->slot_kappa;
   d.orbit_rep = op->orbit_rep;
+  d.batch = 1;
+  d.bs_x = op->V;
+  d.bs_xh = (long long)op->geo.d.Nz * op->Ns;
+  d.bs_yh = (long long)op->nzb * op->Up * op->Ns;
+  d.bs_rh = (long long)op->Up * op->Ns;
+  d.bs_gh = (long long)op->nslots * op->azb * kKappaTile;
+  d.bs_y = (long long)op->S * op->M;
+  d.bs_yplane = (long long)op->U * op->S;
+  d.bs_scal = kNumFloatScalars;
+  d.bs_red = 0;
   return d;
 }
 
@@ -309,9 +337,15 @@ int ensure_events(sfs_operator* op, int n) {
 // adjoint contraction, and the update planes that also transform
 // gamma_{k+1}.  beta_k = (t_k - 1)/t_{k+1} is fixed by k, so the loop can be
 // captured once and replayed.
-int enqueue_fista_iterations(sfs_operator* op, int iters, double* obj, bool timing,
-                             cudaStream_t st) {
-  const PlaneDims d = dims_of(op);
+// Buffers of one FISTA loop: the operator's workspace (one scene) or the
+// batched workspace (d.batch scenes).
+struct FistaBufs {
+  float2 *ybuf, *yplane, *Xh, *Yh, *Rh, *Gh, *xk, *gam;
+  float* scal;
+};
+
+int enqueue_fista_loop(sfs_operator* op, const PlaneDims& d, const FistaBufs& b, int iters,
+                       double* obj, bool timing, cudaStream_t st) {
   std::vector<float> beta(iters);
   double t = 1.0;
   for (int k = 0; k < iters; ++k) {
@@ -319,22 +353,97 @@ int enqueue_fista_iterations(sfs_operator* op, int iters, double* obj, bool timi
     beta[k] = (float)((t - 1.0) / tn);
     t = tn;
   }
-  SFS_TRY(launch_scatter_y_planes(d, op->ws.ybuf, op->posmap, op->ws.yplane, st));
-  SFS_TRY(launch_fwd_planes(d, op->ws.gam, op->ws.Xh, st));
+  SFS_TRY(launch_scatter_y_planes(d, b.ybuf, op->posmap, b.yplane, st));
+  SFS_TRY(launch_fwd_planes(d, b.gam, b.Xh, st));
   for (int k = 0; k < iters; ++k) {
     if (timing) SFS_CUDA(cudaEventRecord(op->ev[5 * k + 0], st));
-    SFS_TRY(launch_contract_fwd(d, op->table, op->ws.Xh, op->ws.Yh, op->ws.err, st));
+    SFS_TRY(launch_contract_fwd(d, op->table, b.Xh, b.Yh, op->ws.err, st));
     if (timing) SFS_CUDA(cudaEventRecord(op->ev[5 * k + 1], st));
-    SFS_TRY(launch_inv_resid_fwd(d, op->ws.Yh, op->posmap, op->ws.yplane, op->ws.Rh,
-                                 obj ? obj + 2 * k : nullptr, st));
+    SFS_TRY(launch_inv_resid_fwd(d, b.Yh, op->posmap, b.yplane, b.Rh, obj ? obj + 2 * k : nullptr, st));
     if (timing) SFS_CUDA(cudaEventRecord(op->ev[5 * k + 2], st));
-    SFS_TRY(launch_contract_adj(d, op->table, op->ws.Rh, op->ws.Gh, op->ws.err, st));
+    SFS_TRY(launch_contract_adj(d, op->table, b.Rh, b.Gh, op->ws.err, st));
     if (timing) SFS_CUDA(cudaEventRecord(op->ev[5 * k + 3], st));
-    SFS_TRY(launch_inv_fista_fwd(d, op->ws.Gh, op->ws.segslot, op->ws.xk, op->ws.gam,
-                                 op->ws.scal, beta[k], k + 1 < iters, op->ws.Xh,
-                                 obj ? obj + 2 * k + 1 : nullptr, st));
+    SFS_TRY(launch_inv_fista_fwd(d, b.Gh, op->ws.segslot, b.xk, b.gam, b.scal, beta[k], k + 1 < iters,
+                                 b.Xh, obj ? obj + 2 * k + 1 : nullptr, st));
     if (timing) SFS_CUDA(cudaEventRecord(op->ev[5 * k + 4], st));
   }
+  return SFS_OK;
+}
+
+int enqueue_fista_iterations(sfs_operator* op, int iters, double* obj, bool timing,
+                             cudaStream_t st) {
+  const FistaBufs b = {op->ws.ybuf, op->ws.yplane, op->ws.Xh, op->ws.Yh, op->ws.Rh,
+                       op->ws.Gh,   op->ws.xk,     op->ws.gam, op->ws.scal};
+  return enqueue_fista_loop(op, dims_of(op), b, iters, obj, timing, st);
+}
+
+// Dimensions of a batched call on `batch` scenes.
+PlaneDims batch_dims(const sfs_operator* op, int batch) {
+  PlaneDims d = dims_of(op);
+  d.batch = batch;
+  return d;
+}
+
+// Batched workspace for at least `batch` scenes (grown on demand; loops
+// captured on the old buffers are dropped).
+int ensure_batch(sfs_operator* op, int batch) {
+  if (op->bws.cap >= batch) return SFS_OK;
+  free_batch(op);
+  const PlaneDims d = dims_of(op);
+  sfs::BatchWorkspace& w = op->bws;
+  const size_t B = (size_t)batch;
+  int rc = SFS_OK;
+  if (rc == SFS_OK) rc = dev_alloc(&w.Xh, B * d.bs_xh);
+  if (rc == SFS_OK) rc = dev_alloc(&w.Yh, B * d.bs_yh);
+  if (rc == SFS_OK) rc = dev_alloc(&w.Rh, B * d.bs_rh);
+  if (rc == SFS_OK) rc = dev_alloc(&w.Gh, B * d.bs_gh);
+  if (rc == SFS_OK) rc = dev_alloc(&w.xk, B * d.bs_x);
+  if (rc == SFS_OK) rc = dev_alloc(&w.gam, B * d.bs_x);
+  if (rc == SFS_OK) rc = dev_alloc(&w.yplane, B * d.bs_yplane);
+  if (rc == SFS_OK) rc = dev_alloc(&w.ybuf, B * d.bs_y);
+  if (rc == SFS_OK) rc = dev_alloc(&w.scal, B * kNumFloatScalars);
+  if (rc == SFS_OK) {
+    // spectra rows of the padding bins U..Up-1 are read by the contractions
+    // and never written
+    const cudaError_t e = cudaMemset(w.Rh, 0, B * d.bs_rh * sizeof(float2));
+    if (e != cudaSuccess) rc = cuda_fail(e, "clearing batched spectra", __FILE__, __LINE__);
+  }
+  if (rc != SFS_OK) {
+    free_batch(op);
+    return rc;
+  }
+  w.cap = batch;
+  return SFS_OK;
+}
+
+int fista_graph_batched(sfs_operator* op, int iters, int batch, cudaGraphExec_t* out) {
+  for (auto& ge : op->bgraphs)
+    if (ge.iters == iters && ge.batch == batch) {
+      *out = ge.exec;
+      return SFS_OK;
+    }
+  if (!op->capture_stream)
+    SFS_CUDA(cudaStreamCreateWithFlags(&op->capture_stream, cudaStreamNonBlocking));
+  const PlaneDims d = batch_dims(op, batch);
+  SFS_TRY(prepare_kernels(d));
+  const sfs::BatchWorkspace& w = op->bws;
+  const FistaBufs b = {w.ybuf, w.yplane, w.Xh, w.Yh, w.Rh, w.Gh, w.xk, w.gam, w.scal};
+  cudaStream_t cs = op->capture_stream;
+  SFS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_fista_loop(op, d, b, iters, nullptr, false, cs);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  if (rc != SFS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t e2 = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaGraphInstantiate", __FILE__, __LINE__);
+  op->bgraphs.push_back({iters, batch, exec});
+  *out = exec;
   return SFS_OK;
 }
 
@@ -1006,6 +1115,8 @@ int sfs_set_wait_timeout_ns(sfs_operator* op, uint64_t ns) {
   // captured iteration loops carry the old limit as a kernel argument
   for (auto& ge : op->graphs) cudaGraphExecDestroy(ge.exec);
   op->graphs.clear();
+  for (auto& ge : op->bgraphs) cudaGraphExecDestroy(ge.exec);
+  op->bgraphs.clear();
   return SFS_OK;
 }
 
@@ -1019,6 +1130,8 @@ int sfs_inject_wait_timeout(sfs_operator* op, int enable) {
   op->inject = enable ? 1 : 0;
   for (auto& ge : op->graphs) cudaGraphExecDestroy(ge.exec);
   op->graphs.clear();
+  for (auto& ge : op->bgraphs) cudaGraphExecDestroy(ge.exec);
+  op->bgraphs.clear();
   return SFS_OK;
 }
 
@@ -1051,6 +1164,74 @@ int sfs_stage_times(sfs_operator* op, double* ms4, int32_t* n_out_host) {
   const int n = op->ev_used;
   for (int j = 0; j < 4; ++j) ms4[j] = n ? acc[j] / n : 0.0;
   if (n_out_host) *n_out_host = n;
+  return SFS_OK;
+}
+
+int sfs_apply_A_batched(sfs_operator* op, int batch, const void* x_dev, void* y_dev, void* stream) {
+  clear_error();
+  if (!op || batch < 1 || batch > SFS_MAX_BATCH || !x_dev || !y_dev || !aligned16(x_dev) ||
+      !aligned16(y_dev)) {
+    set_error("invalid argument (batch must be 1..%d, pointers 16-byte aligned)", SFS_MAX_BATCH);
+    return SFS_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(op->geo.d.device);
+  SFS_TRY(ensure_batch(op, batch));
+  const PlaneDims d = batch_dims(op, batch);
+  cudaStream_t st = (cudaStream_t)stream;
+  SFS_TRY(launch_fwd_planes(d, (const float2*)x_dev, op->bws.Xh, st));
+  SFS_TRY(launch_contract_fwd(d, op->table, op->bws.Xh, op->bws.Yh, op->ws.err, st));
+  return launch_inv_gather(d, op->bws.Yh, op->posmap, (float2*)y_dev, nullptr, st);
+}
+
+int sfs_apply_AH_batched(sfs_operator* op, int batch, const void* y_dev, void* x_dev, void* stream) {
+  clear_error();
+  if (!op || batch < 1 || batch > SFS_MAX_BATCH || !x_dev || !y_dev || !aligned16(x_dev) ||
+      !aligned16(y_dev)) {
+    set_error("invalid argument (batch must be 1..%d, pointers 16-byte aligned)", SFS_MAX_BATCH);
+    return SFS_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(op->geo.d.device);
+  SFS_TRY(ensure_batch(op, batch));
+  const PlaneDims d = batch_dims(op, batch);
+  cudaStream_t st = (cudaStream_t)stream;
+  SFS_TRY(launch_scatter_fwd(d, (const float2*)y_dev, op->posmap, op->bws.Rh, st));
+  SFS_TRY(launch_contract_adj(d, op->table, op->bws.Rh, op->bws.Gh, op->ws.err, st));
+  return launch_inv_store(d, op->bws.Gh, op->ws.segslot, (float2*)x_dev, nullptr, nullptr, st);
+}
+
+int sfs_fista_batched(sfs_operator* op, int batch, const void* y_dev, double lambda, double L,
+                      int iters, void* x_out_dev, void* stream) {
+  clear_error();
+  if (!op || batch < 1 || batch > SFS_MAX_BATCH || !y_dev || !x_out_dev || iters < 0 || !(L > 0) ||
+      !isfinite(lambda) || !aligned16(y_dev) || !aligned16(x_out_dev)) {
+    set_error("invalid argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(op->geo.d.device);
+  SFS_TRY(ensure_batch(op, batch));
+  const PlaneDims d = batch_dims(op, batch);
+  const sfs::BatchWorkspace& w = op->bws;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t B = (size_t)batch;
+  SFS_CUDA(cudaMemcpyAsync(w.ybuf, y_dev, B * d.bs_y * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+  SFS_CUDA(cudaMemsetAsync(w.xk, 0, B * d.bs_x * sizeof(float2), st));
+  SFS_CUDA(cudaMemsetAsync(w.gam, 0, B * d.bs_x * sizeof(float2), st));
+  const int use_mu = lambda < 0;
+  SFS_CUDA(cudaMemsetAsync(w.scal, 0, B * kNumFloatScalars * sizeof(float), st));
+  if (use_mu) {  // max |A^H y_b| of every scene, on the device
+    SFS_TRY(launch_scatter_fwd(d, w.ybuf, op->posmap, w.Rh, st));
+    SFS_TRY(launch_contract_adj(d, op->table, w.Rh, w.Gh, op->ws.err, st));
+    SFS_TRY(launch_inv_store(d, w.Gh, op->ws.segslot, nullptr, nullptr,
+                             (unsigned int*)(w.scal + kLamMax), st));
+  }
+  SFS_TRY(launch_set_thresholds_batched(w.scal, batch, use_mu ? 0.0 : lambda, L, use_mu,
+                                        use_mu ? -lambda : 0.0, op->ws.err, st));
+  if (iters > 0) {
+    cudaGraphExec_t exec = nullptr;
+    SFS_TRY(fista_graph_batched(op, iters, batch, &exec));
+    SFS_CUDA(cudaGraphLaunch(exec, st));
+  }
+  SFS_CUDA(cudaMemcpyAsync(x_out_dev, w.xk, B * d.bs_x * sizeof(float2), cudaMemcpyDeviceToDevice, st));
   return SFS_OK;
 }
 

@@ -220,6 +220,10 @@ struct PlaneFFT {
   static constexpr int NT = TWO_D ? (P >= 64 ? 512 : 256) : (P >= 512 ? 256 : (P >= 128 ? 128 : 64));
   static constexpr int ELEMS = TWO_D ? P * LD : P;   // float2 slots of the plane
   static constexpr int SMEM = (ELEMS + P) * 8;       // plane + twiddles
+  // resident CTAs per SM the plane kernels are compiled for: two 64 x 64
+  // planes per SM (at most 64 registers a thread) so that batched calls,
+  // which launch many planes per scene, keep two planes in flight per SM
+  static constexpr int MINB = LANES64 ? 2 : 1;
 
   // spatial element (iy, ix) of the plane
   __device__ static __forceinline__ int sidx(int iy, int ix) { return TWO_D ? iy * LD + ix : ix; }

@@ -54,6 +54,21 @@ enum RedSlot {
   kNumRed = 4
 };
 
+// Buffers of batched calls (scenes sharing one operator), `cap` scenes each,
+// allocated on first use and grown on demand.
+struct BatchWorkspace {
+  int cap = 0;
+  float2* Xh = nullptr;      // [cap][Nz][Ns]
+  float2* Yh = nullptr;      // [cap][nzb][Up][Ns]
+  float2* Rh = nullptr;      // [cap][Up][Ns] (rows U..Up-1 zero)
+  float2* Gh = nullptr;      // [cap][nslots][azb][64]
+  float2* xk = nullptr;      // [cap][V]
+  float2* gam = nullptr;     // [cap][V]
+  float2* yplane = nullptr;  // [cap][U][S]
+  float2* ybuf = nullptr;    // [cap][S][M] measurements copy
+  float* scal = nullptr;     // [cap][kNumFloatScalars]
+};
+
 struct Workspace {
   float2* Xh = nullptr;     // [Nz][Ns]   lateral spectra of voxel planes (slot order)
   float2* Yh = nullptr;     // [nzb][Up][Ns] depth-block partials of bin-plane spectra
@@ -132,6 +147,14 @@ struct sfs_operator {
   };
   std::vector<GraphEntry> graphs;
   cudaStream_t capture_stream = nullptr;
+  // batched FISTA: workspace and captured loops keyed by (iterations, scenes)
+  sfs::BatchWorkspace bws;
+  struct BatchGraphEntry {
+    int iters;
+    int batch;
+    cudaGraphExec_t exec;
+  };
+  std::vector<BatchGraphEntry> bgraphs;
 };
 
 namespace sfs {
@@ -158,6 +181,19 @@ struct PlaneDims {
   int Ga;       // CTAs of the segment-aligned adjoint (= its segment count)
   uint64_t wait_ns;  // limit of each bounded mbarrier wait in the contractions
   int inject;        // failure-handling tests: first wait of each warp never completes
+  // Scenes sharing this operator processed by one launch (gridDim.y of the
+  // plane kernels, blockIdx.y = scene), and the per-scene strides (elements)
+  // of the batched buffers; batch = 1 for single-scene calls.
+  int batch;
+  long long bs_x;       // x, x_k, gamma: V
+  long long bs_xh;      // X^: Nz * Ns
+  long long bs_yh;      // forward contraction output: nzb * Up * Ns
+  long long bs_rh;      // R^: Up * Ns
+  long long bs_gh;      // adjoint contraction output: nslots * azb * 64
+  long long bs_y;       // measurements: S * M
+  long long bs_yplane;  // measurements by bin plane: U * S
+  int bs_scal;          // device scalars (floats) per scene
+  int bs_red;           // reduction slots (doubles) per scene
   const int32_t* slot_kappa;  // [Ns] wavenumber of each slot, -1 for padding
   const int32_t* orbit_rep;   // [Ns / GS] representative wavenumber, -1 for padding
 };
@@ -228,6 +264,9 @@ int prepare_tc16_kernels(const PlaneDims& d);
 // Small helpers.
 int launch_set_thresholds(float* scal, double* red, double lambda, double L,
                           int use_mu, double mu, int* err, cudaStream_t st);
+// The same for `batch` scenes: scal + b * kNumFloatScalars (red unused).
+int launch_set_thresholds_batched(float* scal, int batch, double lambda, double L, int use_mu,
+                                  double mu, int* err, cudaStream_t st);
 int launch_randn(float2* v, int n, uint64_t seed, cudaStream_t st);
 int launch_sumsq(const float2* v, int n, double* out, cudaStream_t st);
 int launch_scale_by_rnorm(float2* v, int n, const double* sumsq, cudaStream_t st);

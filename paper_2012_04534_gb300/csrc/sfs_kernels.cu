@@ -85,7 +85,7 @@ __device__ __forceinline__ void block_max_bits(float v, unsigned int* out) {
 // added, so the reduced phase keeps ~1e-7 turn accuracy where a plain
 // float product of ~100 turns would lose ~1e-5.
 template <int P, bool TWO_D>
-__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT)
+__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT, PlaneFFT<P, TWO_D>::MINB)
 build_table_kernel(PlaneDims d, const float2* __restrict__ tof,
                    const float* __restrict__ gdir, const float* __restrict__ amp,
                    const int32_t* __restrict__ bins, float2* __restrict__ table) {
@@ -177,6 +177,10 @@ __device__ __forceinline__ void zero_plane(float2* buf) {
 // all independent global loads of a round before using any of them, so that
 // several L2 round trips overlap instead of queueing one after another.
 constexpr int kLoadBatch = 12;
+// 64 x 64 planes (4544 slots on a 32 x 32 scan) run two CTAs per SM at <= 64
+// registers a thread: 9 slots per thread still cover 4608 slots in one round
+template <int P, bool TWO_D>
+__host__ __device__ constexpr int load_batch() { return PlaneFFT<P, TWO_D>::LANES64 ? 9 : kLoadBatch; }
 
 // Spectrum of bin plane u from the forward contraction: the sum of its nzb
 // depth-block partials Yp[zb][u][slot] (plane stride Up * Ns).
@@ -184,25 +188,26 @@ template <int P, bool TWO_D>
 __device__ __forceinline__ void load_spectrum_fwd(float2* buf, const float2* __restrict__ Yp,
                                                   int u, const PlaneDims& d) {
   using F = PlaneFFT<P, TWO_D>;
+  constexpr int LB = load_batch<P, TWO_D>();
   const float2* src = Yp + (size_t)u * d.Ns;
   const size_t stride = (size_t)d.Up * d.Ns;
-  for (int j0 = threadIdx.x; j0 < d.Ns; j0 += kLoadBatch * F::NT) {
-    int kap[kLoadBatch];
-    float2 v[kLoadBatch];
+  for (int j0 = threadIdx.x; j0 < d.Ns; j0 += LB * F::NT) {
+    int kap[LB];
+    float2 v[LB];
 #pragma unroll
-    for (int k = 0; k < kLoadBatch; ++k) {
+    for (int k = 0; k < LB; ++k) {
       const int j = j0 + k * F::NT;
       kap[k] = j < d.Ns ? __ldg(d.slot_kappa + j) : -1;
       v[k] = j < d.Ns ? src[j] : make_float2(0.f, 0.f);
     }
     for (int zb = 1; zb < d.nzb; ++zb)
 #pragma unroll
-      for (int k = 0; k < kLoadBatch; ++k) {
+      for (int k = 0; k < LB; ++k) {
         const int j = j0 + k * F::NT;
         if (j < d.Ns) v[k] = cadd(v[k], src[zb * stride + j]);
       }
 #pragma unroll
-    for (int k = 0; k < kLoadBatch; ++k)
+    for (int k = 0; k < LB; ++k)
       if (kap[k] >= 0) buf[F::kidx(kap[k])] = v[k];
   }
 }
@@ -215,38 +220,39 @@ __device__ __forceinline__ void load_spectrum_adj(float2* buf, const float2* __r
                                                   const int2* __restrict__ segslot, int z,
                                                   const PlaneDims& d) {
   using F = PlaneFFT<P, TWO_D>;
+  constexpr int LB = load_batch<P, TWO_D>();
   const int zb = z / d.azb, zr = z % d.azb;
   const size_t slot_stride = (size_t)d.azb * 64;
-  for (int j0 = threadIdx.x; j0 < d.Ns; j0 += kLoadBatch * F::NT) {
-    int kap[kLoadBatch];
-    int2 sc[kLoadBatch];
+  for (int j0 = threadIdx.x; j0 < d.Ns; j0 += LB * F::NT) {
+    int kap[LB];
+    int2 sc[LB];
 #pragma unroll
-    for (int k = 0; k < kLoadBatch; ++k) {
+    for (int k = 0; k < LB; ++k) {
       const int j = j0 + k * F::NT;
       kap[k] = j < d.Ns ? __ldg(d.slot_kappa + j) : -1;
       // the segment-aligned adjoint leaves one dense result per segment
       const int seg = (j >> 6) * d.anzb + zb;
       sc[k] = j >= d.Ns ? make_int2(0, 0) : (d.adj_seg ? make_int2(seg, 1) : __ldg(segslot + seg));
     }
-    float2 v[kLoadBatch];
+    float2 v[LB];
 #pragma unroll
-    for (int k = 0; k < kLoadBatch; ++k) {
+    for (int k = 0; k < LB; ++k) {
       const int j = j0 + k * F::NT;
       v[k] = sc[k].y > 0 ? Gs[(size_t)sc[k].x * slot_stride + (size_t)zr * 64 + (j & 63)]
                          : make_float2(0.f, 0.f);
     }
     int more = 0;
 #pragma unroll
-    for (int k = 0; k < kLoadBatch; ++k) more = max(more, sc[k].y);
+    for (int k = 0; k < LB; ++k) more = max(more, sc[k].y);
     for (int c = 1; c < more; ++c)
 #pragma unroll
-      for (int k = 0; k < kLoadBatch; ++k) {
+      for (int k = 0; k < LB; ++k) {
         const int j = j0 + k * F::NT;
         if (c < sc[k].y)
           v[k] = cadd(v[k], Gs[(size_t)(sc[k].x + c) * slot_stride + (size_t)zr * 64 + (j & 63)]);
       }
 #pragma unroll
-    for (int k = 0; k < kLoadBatch; ++k)
+    for (int k = 0; k < LB; ++k)
       if (kap[k] >= 0) buf[F::kidx(kap[k])] = v[k];
   }
 }
@@ -255,15 +261,16 @@ template <int P, bool TWO_D>
 __device__ __forceinline__ void store_spectrum(const float2* buf, float2* __restrict__ dst,
                                                const PlaneDims& d) {
   using F = PlaneFFT<P, TWO_D>;
-  for (int j0 = threadIdx.x; j0 < d.Ns; j0 += kLoadBatch * F::NT) {
-    int kap[kLoadBatch];
+  constexpr int LB = load_batch<P, TWO_D>();
+  for (int j0 = threadIdx.x; j0 < d.Ns; j0 += LB * F::NT) {
+    int kap[LB];
 #pragma unroll
-    for (int k = 0; k < kLoadBatch; ++k) {
+    for (int k = 0; k < LB; ++k) {
       const int j = j0 + k * F::NT;
       kap[k] = j < d.Ns ? __ldg(d.slot_kappa + j) : -1;
     }
 #pragma unroll
-    for (int k = 0; k < kLoadBatch; ++k) {
+    for (int k = 0; k < LB; ++k) {
       const int j = j0 + k * F::NT;
       if (j < d.Ns) dst[j] = kap[k] >= 0 ? buf[F::kidx(kap[k])] : make_float2(0.f, 0.f);
     }
@@ -283,9 +290,14 @@ __device__ __forceinline__ void zero_outside(float2* buf, int Ny, int Nx) {
 
 // x plane z -> Xh[z] = FFT2(pad(x_z))
 template <int P, bool TWO_D>
-__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT)
+__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT, PlaneFFT<P, TWO_D>::MINB)
 fwd_planes_kernel(PlaneDims d, const float2* __restrict__ x, float2* __restrict__ Xh) {
   using F = PlaneFFT<P, TWO_D>;
+  {  // scene blockIdx.y of a batched launch
+    const long long b = blockIdx.y;
+    x += b * d.bs_x;
+    Xh += b * d.bs_xh;
+  }
   extern __shared__ float2 smem[];
   float2* buf = smem;
   float2* tw = smem + F::ELEMS;
@@ -305,11 +317,17 @@ fwd_planes_kernel(PlaneDims d, const float2* __restrict__ x, float2* __restrict_
 
 // Yh[u] -> y[s, m] = IFFT2(Yh_u)(s) where bins[u] = idx[s, m]
 template <int P, bool TWO_D>
-__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT)
+__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT, PlaneFFT<P, TWO_D>::MINB)
 inv_gather_kernel(PlaneDims d, const float2* __restrict__ Yh,
                   const int32_t* __restrict__ posmap, float2* __restrict__ y,
                   double* __restrict__ red_sumsq) {
   using F = PlaneFFT<P, TWO_D>;
+  {  // scene blockIdx.y of a batched launch
+    const long long b = blockIdx.y;
+    Yh += b * d.bs_yh;
+    y += b * d.bs_y;
+    if (red_sumsq) red_sumsq += b * d.bs_red;
+  }
   extern __shared__ float2 smem[];
   float2* buf = smem;
   float2* tw = smem + F::ELEMS;
@@ -337,11 +355,18 @@ inv_gather_kernel(PlaneDims d, const float2* __restrict__ Yh,
 // yplane[u][s] holds the measurements laid out by bin plane (scatter_y_planes),
 // so they load alongside the selection mask instead of after it.
 template <int P, bool TWO_D>
-__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT)
+__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT, PlaneFFT<P, TWO_D>::MINB)
 inv_resid_fwd_kernel(PlaneDims d, const float2* __restrict__ Yh,
                      const int32_t* __restrict__ posmap, const float2* __restrict__ yplane,
                      float2* __restrict__ Rh, double* __restrict__ red_sumsq) {
   using F = PlaneFFT<P, TWO_D>;
+  {  // scene blockIdx.y of a batched launch
+    const long long b = blockIdx.y;
+    Yh += b * d.bs_yh;
+    yplane += b * d.bs_yplane;
+    Rh += b * d.bs_rh;
+    if (red_sumsq) red_sumsq += b * d.bs_red;
+  }
   extern __shared__ float2 smem[];
   float2* buf = smem;
   float2* tw = smem + F::ELEMS;
@@ -375,10 +400,15 @@ inv_resid_fwd_kernel(PlaneDims d, const float2* __restrict__ Yh,
 
 // y[s, m] scattered to bin plane u -> Rh[u] = FFT2(pad(.))
 template <int P, bool TWO_D>
-__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT)
+__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT, PlaneFFT<P, TWO_D>::MINB)
 scatter_fwd_kernel(PlaneDims d, const float2* __restrict__ y,
                    const int32_t* __restrict__ posmap, float2* __restrict__ Rh) {
   using F = PlaneFFT<P, TWO_D>;
+  {  // scene blockIdx.y of a batched launch
+    const long long b = blockIdx.y;
+    y += b * d.bs_y;
+    Rh += b * d.bs_rh;
+  }
   extern __shared__ float2 smem[];
   float2* buf = smem;
   float2* tw = smem + F::ELEMS;
@@ -400,11 +430,18 @@ scatter_fwd_kernel(PlaneDims d, const float2* __restrict__ y,
 
 // Gh[z] -> x plane z = crop(IFFT2(Gh_z)); optional sum |x|^2 and max |x|.
 template <int P, bool TWO_D>
-__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT)
+__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT, PlaneFFT<P, TWO_D>::MINB)
 inv_store_kernel(PlaneDims d, const float2* __restrict__ Gh, const int2* __restrict__ segslot,
                  float2* __restrict__ x, double* __restrict__ red_sumsq,
                  unsigned int* __restrict__ maxabs_bits) {
   using F = PlaneFFT<P, TWO_D>;
+  {  // scene blockIdx.y of a batched launch
+    const long long b = blockIdx.y;
+    Gh += b * d.bs_gh;
+    if (x) x += b * d.bs_x;
+    if (red_sumsq) red_sumsq += b * d.bs_red;
+    if (maxabs_bits) maxabs_bits += b * d.bs_scal;
+  }
   extern __shared__ float2 smem[];
   float2* buf = smem;
   float2* tw = smem + F::ELEMS;
@@ -435,12 +472,21 @@ inv_store_kernel(PlaneDims d, const float2* __restrict__ Gh, const int2* __restr
 //   x_k = tau_{lambda/L}(gamma_k - grad/L), gamma_{k+1} = x_k + beta_k (x_k - x_{k-1})
 // then, unless this is the last iteration, Xh[z] = FFT2(pad(gamma_{k+1})).
 template <int P, bool TWO_D>
-__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT)
+__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT, PlaneFFT<P, TWO_D>::MINB)
 inv_fista_fwd_kernel(PlaneDims d, const float2* __restrict__ Gh,
                      const int2* __restrict__ segslot, float2* __restrict__ xk,
                      float2* __restrict__ gam, const float* __restrict__ scal, float beta,
                      int do_fwd, float2* __restrict__ Xh, double* __restrict__ red_l1) {
   using F = PlaneFFT<P, TWO_D>;
+  {  // scene blockIdx.y of a batched launch
+    const long long b = blockIdx.y;
+    Gh += b * d.bs_gh;
+    xk += b * d.bs_x;
+    gam += b * d.bs_x;
+    scal += b * d.bs_scal;
+    Xh += b * d.bs_xh;
+    if (red_l1) red_l1 += b * d.bs_red;
+  }
   extern __shared__ float2 smem[];
   float2* buf = smem;
   float2* tw = smem + F::ELEMS;
@@ -994,10 +1040,24 @@ __global__ void set_thresholds_kernel(float* scal, double* red, double lambda, d
   red[kNumRed - 1] = lam;
 }
 
+// Thresholds of scene blockIdx.x of a batched FISTA call (scal per scene).
+__global__ void set_thresholds_batched_kernel(float* scal, double lambda, double L, int use_mu,
+                                              double mu, int* err) {
+  float* sc = scal + (size_t)blockIdx.x * kNumFloatScalars;
+  double lam = lambda;
+  if (use_mu) lam = mu * (double)__uint_as_float(((unsigned int*)sc)[kLamMax]);
+  if (!isfinite(lam)) atomicExch(err, 2);
+  sc[kThr] = (float)(lam / L);
+  sc[kInvL] = (float)(1.0 / L);
+}
+
 // y[s][m] -> yplane[u][s] (zero where plane u is not kept at position s)
 __global__ void scatter_y_planes_kernel(const float2* __restrict__ y,
                                         const int32_t* __restrict__ posmap,
                                         float2* __restrict__ yplane, int S, int M, int U) {
+  // scene blockIdx.y of a batched launch
+  y += (size_t)blockIdx.y * S * M;
+  yplane += (size_t)blockIdx.y * U * S;
   const size_t n = (size_t)U * S;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -1046,12 +1106,13 @@ __global__ void scale_rnorm_kernel(float2* v, int n, const double* sumsq) {
 // ---------------------------------------------------------------------------
 // Dispatch on the plane size
 // ---------------------------------------------------------------------------
+// nplanes planes of each of `batch` scenes (gridDim.y; blockIdx.y = scene)
 template <int P, bool TWO_D, typename K, typename... Args>
-int launch_plane(K kernel, int nplanes, cudaStream_t st, Args... args) {
+int launch_plane(K kernel, int nplanes, int d_batch, cudaStream_t st, Args... args) {
   using F = PlaneFFT<P, TWO_D>;
   if (nplanes <= 0) return SFS_OK;
   SFS_TRY(ensure_smem_attr(kernel, F::SMEM));
-  return launch_pdl(kernel, dim3(nplanes), dim3(F::NT), F::SMEM, st, args...);
+  return launch_pdl(kernel, dim3(nplanes, std::max(1, d_batch)), dim3(F::NT), F::SMEM, st, args...);
 }
 
 // Calls fn.template operator()<P, TWO_D>() for the plane shape of d.
@@ -1119,21 +1180,21 @@ int launch_build_table(const PlaneDims& d, const float2* tof, const float* gdir,
                        const float* amp, const int32_t* bins, float2* table,
                        cudaStream_t st) {
   return dispatch_plane(d, [&]<int P, bool TD>() {
-    return launch_plane<P, TD>(build_table_kernel<P, TD>, d.U * d.Nz, st, d, tof, gdir,
+    return launch_plane<P, TD>(build_table_kernel<P, TD>, d.U * d.Nz, 1, st, d, tof, gdir,
                                amp, bins, table);
   });
 }
 
 int launch_fwd_planes(const PlaneDims& d, const float2* x, float2* Xh, cudaStream_t st) {
   return dispatch_plane(d, [&]<int P, bool TD>() {
-    return launch_plane<P, TD>(fwd_planes_kernel<P, TD>, d.Nz, st, d, x, Xh);
+    return launch_plane<P, TD>(fwd_planes_kernel<P, TD>, d.Nz, d.batch, st, d, x, Xh);
   });
 }
 
 int launch_inv_gather(const PlaneDims& d, const float2* Yh, const int32_t* posmap,
                       float2* y, double* red_sumsq, cudaStream_t st) {
   return dispatch_plane(d, [&]<int P, bool TD>() {
-    return launch_plane<P, TD>(inv_gather_kernel<P, TD>, d.U, st, d, Yh, posmap, y,
+    return launch_plane<P, TD>(inv_gather_kernel<P, TD>, d.U, d.batch, st, d, Yh, posmap, y,
                                red_sumsq);
   });
 }
@@ -1142,7 +1203,7 @@ int launch_inv_resid_fwd(const PlaneDims& d, const float2* Yh, const int32_t* po
                          const float2* yplane, float2* Rh, double* red_sumsq,
                          cudaStream_t st) {
   return dispatch_plane(d, [&]<int P, bool TD>() {
-    return launch_plane<P, TD>(inv_resid_fwd_kernel<P, TD>, d.U, st, d, Yh, posmap, yplane,
+    return launch_plane<P, TD>(inv_resid_fwd_kernel<P, TD>, d.U, d.batch, st, d, Yh, posmap, yplane,
                                Rh, red_sumsq);
   });
 }
@@ -1150,14 +1211,14 @@ int launch_inv_resid_fwd(const PlaneDims& d, const float2* Yh, const int32_t* po
 int launch_scatter_fwd(const PlaneDims& d, const float2* y, const int32_t* posmap,
                        float2* Rh, cudaStream_t st) {
   return dispatch_plane(d, [&]<int P, bool TD>() {
-    return launch_plane<P, TD>(scatter_fwd_kernel<P, TD>, d.U, st, d, y, posmap, Rh);
+    return launch_plane<P, TD>(scatter_fwd_kernel<P, TD>, d.U, d.batch, st, d, y, posmap, Rh);
   });
 }
 
 int launch_inv_store(const PlaneDims& d, const float2* Gh, const int2* segslot, float2* x,
                      double* red_sumsq, unsigned int* maxabs_bits, cudaStream_t st) {
   return dispatch_plane(d, [&]<int P, bool TD>() {
-    return launch_plane<P, TD>(inv_store_kernel<P, TD>, d.Nz, st, d, Gh, segslot, x, red_sumsq,
+    return launch_plane<P, TD>(inv_store_kernel<P, TD>, d.Nz, d.batch, st, d, Gh, segslot, x, red_sumsq,
                                maxabs_bits);
   });
 }
@@ -1166,7 +1227,7 @@ int launch_inv_fista_fwd(const PlaneDims& d, const float2* Gh, const int2* segsl
                          float2* gam, const float* scal, float beta, int do_fwd, float2* Xh,
                          double* red_l1, cudaStream_t st) {
   return dispatch_plane(d, [&]<int P, bool TD>() {
-    return launch_plane<P, TD>(inv_fista_fwd_kernel<P, TD>, d.Nz, st, d, Gh, segslot, xk, gam,
+    return launch_plane<P, TD>(inv_fista_fwd_kernel<P, TD>, d.Nz, d.batch, st, d, Gh, segslot, xk, gam,
                                scal, beta, do_fwd, Xh, red_l1);
   });
 }
@@ -1216,6 +1277,13 @@ int launch_adj_gs(const PlaneDims& d, const float2* table, const float2* Rh, flo
 int launch_contract_fwd(const PlaneDims& d, const float2* table, const float2* Xh,
                         float2* Yp, int* err, cudaStream_t st) {
   if (d.tc == 2) return launch_contract_fwd_h(d, Xh, Yp, err, st);
+  if (d.batch > 1) {  // one launch per scene
+    PlaneDims d1 = d;
+    d1.batch = 1;
+    for (int b = 0; b < d.batch; ++b)
+      SFS_TRY(launch_contract_fwd(d1, table, Xh + b * d.bs_xh, Yp + b * d.bs_yh, err, st));
+    return SFS_OK;
+  }
   if (d.tc) return launch_contract_fwd_tc(d, table, Xh, Yp, err, st);
   switch (d.GS) {
     case 2: return launch_fwd_gs<2>(d, table, Xh, Yp, err, st);
@@ -1246,6 +1314,13 @@ size_t adj_seg_smem_bytes(int Up) { return contract_adj_seg_smem<8>(Up); }
 int launch_contract_adj(const PlaneDims& d, const float2* table, const float2* Rh,
                         float2* Gs, int* err, cudaStream_t st) {
   if (d.tc == 2) return launch_contract_adj_h(d, Rh, Gs, err, st);
+  if (d.batch > 1) {  // one launch per scene
+    PlaneDims d1 = d;
+    d1.batch = 1;
+    for (int b = 0; b < d.batch; ++b)
+      SFS_TRY(launch_contract_adj(d1, table, Rh + b * d.bs_rh, Gs + b * d.bs_gh, err, st));
+    return SFS_OK;
+  }
   if (d.tc) return launch_contract_adj_tc(d, table, Rh, Gs, err, st);
   if (d.adj_seg) {
     switch (d.GS) {
@@ -1306,12 +1381,20 @@ int launch_set_thresholds(float* scal, double* red, double lambda, double L, int
   return SFS_OK;
 }
 
+int launch_set_thresholds_batched(float* scal, int batch, double lambda, double L, int use_mu,
+                                  double mu, int* err, cudaStream_t st) {
+  set_thresholds_batched_kernel<<<batch, 1, 0, st>>>(scal, lambda, L, use_mu, mu, err);
+  SFS_CUDA(cudaGetLastError());
+  return SFS_OK;
+}
+
 int launch_scatter_y_planes(const PlaneDims& d, const float2* y, const int32_t* posmap,
                             float2* yplane, cudaStream_t st) {
   const size_t n = (size_t)d.U * d.S;
   size_t blocks = (n + 255) / 256;
   if (blocks > 2432) blocks = 2432;
-  scatter_y_planes_kernel<<<(unsigned)blocks, 256, 0, st>>>(y, posmap, yplane, d.S, d.M, d.U);
+  scatter_y_planes_kernel<<<dim3((unsigned)blocks, std::max(1, d.batch)), 256, 0, st>>>(y, posmap, yplane,
+                                                                                     d.S, d.M, d.U);
   SFS_CUDA(cudaGetLastError());
   return SFS_OK;
 }

@@ -121,16 +121,19 @@ int encode_table(CUtensorMap* m, const void* table, int U, int nkb, int planes, 
   return SFS_OK;
 }
 
-// Lateral spectra c64 [rows][Ns] seen as floats [rows][2 Ns]; box of 8 slots
-// (16 floats) x box_rows, no swizzle; rows past `rows` read as zero.
-int encode_spec(CUtensorMap* m, const void* base, int rows, int Ns, int box_rows) {
+// Lateral spectra of `scenes` consecutive scenes, c64 [scenes][rows][Ns]
+// seen as floats [scenes][rows][2 Ns]; box of 8 slots (16 floats) x
+// box_rows x box_scenes, no swizzle; rows past `rows` and scenes past
+// `scenes` read as zero.
+int encode_spec(CUtensorMap* m, const void* base, int rows, int Ns, int box_rows, int scenes = 1,
+                int box_scenes = 1) {
   EncodeTiledFn enc;
   SFS_TRY(encoder(&enc));
-  const cuuint64_t dims[2] = {(cuuint64_t)2 * Ns, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)Ns * 8};
-  const cuuint32_t box[2] = {16, (cuuint32_t)box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box,
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * Ns, (cuuint64_t)rows, (cuuint64_t)scenes};
+  const cuuint64_t strides[2] = {(cuuint64_t)Ns * 8, (cuuint64_t)rows * Ns * 8};
+  const cuuint32_t box[3] = {16, (cuuint32_t)box_rows, (cuuint32_t)box_scenes};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box,
                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -149,6 +152,14 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
       "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
       "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
       : "memory");
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
@@ -199,11 +210,13 @@ constexpr int kHThreads = 224;  // warps 0-3 build B and read out, 4 table copie
                                 // 6 spectra copies
 constexpr int kHCopyWarp = 4, kHMmaWarp = 5, kHSpecWarp = 6;
 constexpr int kHATile = 16384;  // A tile of one part: 128 rows x 128 B (or 2 x 64 rows)
-constexpr int kHBTile = 4096;   // B: 32 rows (16 hi, 16 lo) x 64 K x 2 B, swizzled
-constexpr int kHSTile = 4096;   // spectra tile: 32 depths x 64 B (fwd), 64 bins x 64 B (adj)
-constexpr uint32_t kHCols = 64; // two accumulators of 32 columns
+constexpr int kHBTile = 4096;   // B of one scene: 32 rows (16 hi, 16 lo) x 64 K x 2 B, swizzled
+constexpr int kHSTile = 4096;   // spectra tile of one scene: 32 depths x 64 B (fwd), 64 bins x 64 B (adj)
 
-template <int NP>
+// NB = scenes sharing a table tile (batched calls): B has 32 NB columns, the
+// accumulators 2 x 32 NB TMEM columns.  NB = 1 runs two CTAs per SM, NB > 1
+// one CTA per SM with deeper rings.
+template <int NP, int NB>
 struct HPlan {
   // Three rings, each with its own producer: the table ring (kST stages of
   // NP A tiles, filled by TMA), the spectra ring (kSS slots of spectra
@@ -211,29 +224,38 @@ struct HPlan {
   // (kSBB slots of B operands, built by the builders, emptied by the MMAs).
   // The spectra ring is deep so that the spectra copies, which queue behind
   // the table stream, land well before the builders need them.
-  static constexpr int kST = NP == 1 ? 4 : 2;
-  static constexpr int kSS = 8;
+  static constexpr int kCtasPerSm = NB == 1 ? 2 : 1;
+  static constexpr int kST = NB == 1 ? (NP == 1 ? 4 : 2) : (NP == 1 ? 6 : 3);
+  static constexpr int kSS = NB == 1 ? 8 : 4;
   static constexpr int kSBB = 3;
   static constexpr int kLead = 2;  // the builders read out a unit at chunk kLead of the next
   static constexpr int kTStage = NP * kHATile;
+  static constexpr int kBSlot = NB * kHBTile;
+  static constexpr int kSSlot = NB * kHSTile;
+  static constexpr uint32_t kCols = 64 * NB;           // two accumulators of 32 NB columns
   static constexpr int kOffB = kST * kTStage;          // B ring (1 KB aligned)
-  static constexpr int kOffS = kOffB + kSBB * kHBTile;  // spectra ring
+  static constexpr int kOffS = kOffB + kSBB * kBSlot;   // spectra ring
   // barriers: table full / empty, spectra full / empty, B built / empty,
   // accumulator full / empty, MMA drain, one that nothing arrives at
   // (failure-handling tests)
   static constexpr int kTF = 0, kTE = kST, kXF = 2 * kST, kXE = kXF + kSS, kBF = kXE + kSS,
                        kBE = kBF + kSBB, kDF = kBE + kSBB, kDE = kDF + 2, kDR = kDE + 2, kNV = kDR + 1,
                        kNumBars = kNV + 1;
-  static constexpr int kOffBar = kOffS + kSS * kHSTile;
+  static constexpr int kOffBar = kOffS + kSS * kSSlot;
   static constexpr int kOffSlot = kOffBar + kNumBars * 8;
   static constexpr int kSmem = kOffSlot + 16 + 1024;  // + alignment of the base to 1 KB
+  static_assert(kSmem <= (NB == 1 ? 115 * 1024 : 227 * 1024), "shared memory plan");
 };
 
-template <bool FWD, int NP>
-__global__ void __launch_bounds__(kHThreads, 2)
+// out: output of the group's first scene; scene j of the group writes
+// out + j * out_stride if j < nscene.
+template <bool FWD, int NP, int NB>
+__global__ void __launch_bounds__(kHThreads, HPlan<NP, NB>::kCtasPerSm)
 contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUtensorMap spec,
-           float2* __restrict__ out, PlaneDims d, int nmt, int nch, int nunits, int* __restrict__ err) {
-  using Pl = HPlan<NP>;
+           float2* __restrict__ out, long long out_stride, int nscene, PlaneDims d, int nmt, int nch,
+           int nunits, int* __restrict__ err) {
+  using Pl = HPlan<NP, NB>;
+  constexpr uint32_t kHCols = Pl::kCols;
   constexpr int ST = Pl::kST, SS = Pl::kSS, SBB = Pl::kSBB, LEAD = Pl::kLead;
   extern __shared__ unsigned char hsm_raw[];
   // 128-byte-swizzled tiles need 1 KB alignment of the shared-memory address
@@ -306,8 +328,8 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
       item(j, o, mt, c);
       if (elect_one()) {
         const uint32_t fb = bar(Pl::kXF + sl);
-        mbar_expect_tx(fb, FWD ? 2048 : 4096);
-        tma_load_2d(sbase + Pl::kOffS + sl * kHSTile, &spec, 2 * o * d.GS, (FWD ? 32 : 64) * c, fb);
+        mbar_expect_tx(fb, NB * (FWD ? 2048 : 4096));
+        tma_load_3d(sbase + Pl::kOffS + sl * Pl::kSSlot, &spec, 2 * o * d.GS, (FWD ? 32 : 64) * c, 0, fb);
       }
       __syncwarp();
       ++issued;
@@ -359,7 +381,7 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
       mbar_wait_bounded(bar(Pl::kTF + i % ST), (i / ST) & 1, kDrainNs);
   } else if (warp == kHMmaWarp) {
     // ---- MMA issuer (whole warp, one elected lane issues) ----
-    constexpr uint32_t idesc = idesc_bf16(128, 32, !FWD);
+    constexpr uint32_t idesc = idesc_bf16(128, 32 * NB, !FWD);
     bool ok = true;
     int k = 0, c = 0;
     for (int i = 0; i < items; ++i) {
@@ -374,9 +396,9 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
         break;
       }
       tc_fence_after();
-      const uint32_t D = tmem + 32u * (uint32_t)(k & 1);
+      const uint32_t D = tmem + 32u * NB * (uint32_t)(k & 1);
       const uint32_t a0 = sbase + (uint32_t)(s * Pl::kTStage);
-      const uint32_t b0 = sbase + (uint32_t)(Pl::kOffB + sl * kHBTile);
+      const uint32_t b0 = sbase + (uint32_t)(Pl::kOffB + sl * Pl::kBSlot);
       if (elect_one()) {
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks)
@@ -422,22 +444,28 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
       const bool dgot = tc_wait(bar(Pl::kDF + (k & 1)), (k >> 1) & 1, wait_ns, abort_flag);
       if (!__all_sync(0xffffffffu, dgot)) return false;
       tc_fence_after();
+#pragma unroll 1
+      for (int j = 0; j < NB; ++j) {
       uint32_t v[32];
       uint32_t(&v0)[16] = *reinterpret_cast<uint32_t(*)[16]>(v);
       uint32_t(&v1)[16] = *reinterpret_cast<uint32_t(*)[16]>(v + 16);
-      tc_ld16(tl + 32u * (uint32_t)(k & 1), v0);
-      tc_ld16(tl + 32u * (uint32_t)(k & 1) + 16, v1);
+      const uint32_t col = 32u * NB * (uint32_t)(k & 1) + 32u * j;
+      tc_ld16(tl + col, v0);
+      tc_ld16(tl + col + 16, v1);
       tc_wait_ld();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar(Pl::kDE + (k & 1)));
+      if (j == NB - 1) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(Pl::kDE + (k & 1)));
+      }
       float e[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) e[q] = __uint_as_float(v[q]) + __uint_as_float(v[16 + q]);
+      float2* outj = out + j * out_stride;
       if (FWD) {
         const int u = 128 * mt + t;
-        if (u < d.U) {
-          float2* dst = out + (size_t)u * d.Ns + o * d.GS;
+        if (u < d.U && j < nscene) {
+          float2* dst = outj + (size_t)u * d.Ns + o * d.GS;
 #pragma unroll
           for (int q = 0; q < 8; ++q)
             if (q < d.GS) dst[q] = make_float2(e[q], e[8 + q]);
@@ -448,13 +476,14 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
 #pragma unroll
         for (int q = 0; q < 16; ++q) f[q] = __shfl_xor_sync(0xffffffffu, e[q], 1);
         const int z = 32 * (2 * mt + (t >> 6)) + ((t & 63) >> 1);
-        if ((t & 1) == 0 && z < d.Nz) {
+        if ((t & 1) == 0 && z < d.Nz && j < nscene) {
           const int s0 = o * d.GS;  // the orbit's slots lie in one tile of 64
-          float2* dst = out + (((size_t)(s0 >> 6) * d.anzb + (z >> 5)) * 32 + (z & 31)) * 64 + (s0 & 63);
+          float2* dst = outj + (((size_t)(s0 >> 6) * d.anzb + (z >> 5)) * 32 + (z & 31)) * 64 + (s0 & 63);
 #pragma unroll
           for (int q = 0; q < 8; ++q)
             if (q < d.GS) dst[q] = make_float2(e[q] + f[8 + q], e[8 + q] - f[q]);
         }
+      }
       }
       return true;
     };
@@ -473,7 +502,9 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
         ok = false;
         break;
       }
-      const float* sp = (const float*)(hsm + Pl::kOffS + xs * kHSTile);
+#pragma unroll 1
+      for (int jn = 0; jn < NB; ++jn) {
+      const float* sp = (const float*)(hsm + Pl::kOffS + xs * Pl::kSSlot + jn * (FWD ? 2048 : 4096));
       uint32_t w[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
@@ -490,11 +521,13 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
         if (!slot_ok) v0 = v1 = 0.f;
         w[j] = bf16_pair_part(v0, v1, lo);
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar(Pl::kXE + xs));  // spectra slot read
-      unsigned char* brow = hsm + Pl::kOffB + sl * kHBTile + n * 128;
+      // rows 32 jn .. of the B slot (a multiple of 8, so the swizzle phase is n & 7)
+      unsigned char* brow = hsm + Pl::kOffB + sl * Pl::kBSlot + (32 * jn + n) * 128;
       *(uint4*)(brow + (((2 * cq) ^ (n & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
       *(uint4*)(brow + (((2 * cq + 1) ^ (n & 7)) << 4)) = make_uint4(w[4], w[5], w[6], w[7]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(Pl::kXE + xs));  // spectra slot read
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(Pl::kBF + sl));
@@ -522,18 +555,55 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
   }
 }
 
-template <bool FWD, int NP>
-int launch_h(const PlaneDims& d, const CUtensorMap& tab, const CUtensorMap& spec, float2* out, int* err,
-             cudaStream_t st) {
-  SFS_TRY(ensure_smem_attr(contract_h<FWD, NP>, HPlan<NP>::kSmem));
+template <bool FWD, int NP, int NB>
+int launch_h(const PlaneDims& d, const CUtensorMap& tab, const CUtensorMap& spec, float2* out,
+             long long out_stride, int nscene, int* err, cudaStream_t st) {
+  using Pl = HPlan<NP, NB>;
+  SFS_TRY(ensure_smem_attr(contract_h<FWD, NP, NB>, Pl::kSmem));
   const int No = d.Ns / d.GS;
   const int nmt = FWD ? (d.U + 127) / 128 : (d.nkb + 1) / 2;
   const int nch = FWD ? d.nkb : (d.U + 63) / 64;
   const int nunits = No * nmt;
-  const int G = std::min(d.G, nunits);
+  // d.G = two CTAs per SM
+  const int G = std::min(Pl::kCtasPerSm == 2 ? d.G : d.G / 2, nunits);
   if (G <= 0) return SFS_OK;
-  return launch_pdl(contract_h<FWD, NP>, dim3(G), dim3(kHThreads), (size_t)HPlan<NP>::kSmem, st, tab, spec,
-                    out, d, nmt, nch, nunits, err);
+  return launch_pdl(contract_h<FWD, NP, NB>, dim3(G), dim3(kHThreads), (size_t)Pl::kSmem, st, tab, spec,
+                    out, out_stride, nscene, d, nmt, nch, nunits, err);
+}
+
+// Scene group size of a batched call: one table tile serves up to 4 scenes.
+int group_of(int batch) { return batch >= 3 ? 4 : batch; }
+
+// One contraction launch per group of scenes: spectra of the group from
+// `spec_base` (scene stride spec_stride elements, `rows` rows), outputs from
+// `out` (scene stride out_stride).
+template <bool FWD>
+int launch_groups(const PlaneDims& d, const CUtensorMap& tab, const CUtensorMap* cached, const float2* base,
+                  long long spec_stride, int rows, int box_rows, float2* out, long long out_stride,
+                  int* err, cudaStream_t st) {
+  const int B = std::max(1, d.batch), NB = group_of(B);
+  for (int g0 = 0; g0 < B; g0 += NB) {
+    CUtensorMap local;
+    const CUtensorMap* spec = cached;
+    if (!spec || B > 1) {
+      SFS_TRY(encode_spec(&local, base + g0 * spec_stride, rows, d.Ns, box_rows, B - g0, NB));
+      spec = &local;
+    }
+    float2* o = out + g0 * out_stride;
+    const int n = std::min(NB, B - g0);
+    int rc;
+    if (d.nparts == 2) {
+      rc = NB == 1 ? launch_h<FWD, 2, 1>(d, tab, *spec, o, out_stride, n, err, st)
+         : NB == 2 ? launch_h<FWD, 2, 2>(d, tab, *spec, o, out_stride, n, err, st)
+                   : launch_h<FWD, 2, 4>(d, tab, *spec, o, out_stride, n, err, st);
+    } else {
+      rc = NB == 1 ? launch_h<FWD, 1, 1>(d, tab, *spec, o, out_stride, n, err, st)
+         : NB == 2 ? launch_h<FWD, 1, 2>(d, tab, *spec, o, out_stride, n, err, st)
+                   : launch_h<FWD, 1, 4>(d, tab, *spec, o, out_stride, n, err, st);
+    }
+    SFS_TRY(rc);
+  }
+  return SFS_OK;
 }
 
 int check_maps(const PlaneDims& d) {
@@ -570,35 +640,29 @@ int tc16_setup(sfs_operator* op) {
 
 int launch_contract_fwd_h(const PlaneDims& d, const float2* Xh, float2* Yp, int* err, cudaStream_t st) {
   SFS_TRY(check_maps(d));
-  CUtensorMap local;
-  const CUtensorMap* spec = &d.tmaps->xh;
-  if (Xh != d.tmaps->xh_ptr) {  // spectra elsewhere than the operator's workspace
-    SFS_TRY(encode_spec(&local, Xh, d.Nz, d.Ns, 32));
-    spec = &local;
-  }
-  return d.nparts == 2 ? launch_h<true, 2>(d, d.tmaps->tab_f, *spec, Yp, err, st)
-                       : launch_h<true, 1>(d, d.tmaps->tab_f, *spec, Yp, err, st);
+  const CUtensorMap* cached = (Xh == d.tmaps->xh_ptr && d.batch <= 1) ? &d.tmaps->xh : nullptr;
+  return launch_groups<true>(d, d.tmaps->tab_f, cached, Xh, d.bs_xh, d.Nz, 32, Yp, d.bs_yh, err, st);
 }
 
 int launch_contract_adj_h(const PlaneDims& d, const float2* Rh, float2* Gs, int* err, cudaStream_t st) {
   SFS_TRY(check_maps(d));
-  CUtensorMap local;
-  const CUtensorMap* spec = &d.tmaps->rh;
-  if (Rh != d.tmaps->rh_ptr) {  // e.g. the static scratch of sfs_apply_AH_noalloc
-    SFS_TRY(encode_spec(&local, Rh, d.Up, d.Ns, 64));
-    spec = &local;
-  }
-  return d.nparts == 2 ? launch_h<false, 2>(d, d.tmaps->tab_a, *spec, Gs, err, st)
-                       : launch_h<false, 1>(d, d.tmaps->tab_a, *spec, Gs, err, st);
+  // spectra elsewhere than the operator's workspace (e.g. the static scratch
+  // of sfs_apply_AH_noalloc, or a batched workspace) get a map of their own
+  const CUtensorMap* cached = (Rh == d.tmaps->rh_ptr && d.batch <= 1) ? &d.tmaps->rh : nullptr;
+  return launch_groups<false>(d, d.tmaps->tab_a, cached, Rh, d.bs_rh, d.Up, 64, Gs, d.bs_gh, err, st);
+}
+
+template <int NP, int NB>
+int prepare_one() {
+  SFS_TRY(ensure_smem_attr(contract_h<true, NP, NB>, HPlan<NP, NB>::kSmem));
+  return ensure_smem_attr(contract_h<false, NP, NB>, HPlan<NP, NB>::kSmem);
 }
 
 int prepare_tc16_kernels(const PlaneDims& d) {
-  if (d.nparts == 2) {
-    SFS_TRY(ensure_smem_attr(contract_h<true, 2>, HPlan<2>::kSmem));
-    return ensure_smem_attr(contract_h<false, 2>, HPlan<2>::kSmem);
-  }
-  SFS_TRY(ensure_smem_attr(contract_h<true, 1>, HPlan<1>::kSmem));
-  return ensure_smem_attr(contract_h<false, 1>, HPlan<1>::kSmem);
+  const int NB = group_of(std::max(1, d.batch));
+  if (d.nparts == 2)
+    return NB == 1 ? prepare_one<2, 1>() : NB == 2 ? prepare_one<2, 2>() : prepare_one<2, 4>();
+  return NB == 1 ? prepare_one<1, 1>() : NB == 2 ? prepare_one<1, 2>() : prepare_one<1, 4>();
 }
 
 }  // namespace sfs

@@ -40,6 +40,8 @@ SFS_PREC_BF16X2 = 3
 PRECISION_NAMES = {"fp32": SFS_PREC_FP32, "tf32x3": SFS_PREC_TF32X3, "bf16": SFS_PREC_BF16,
                    "bf16x2": SFS_PREC_BF16X2}
 
+SFS_MAX_BATCH = 256
+
 SFS_FISTA_WARM_START = 1
 SFS_FISTA_TIME_KERNELS = 2
 
@@ -52,7 +54,7 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_select_freqs", "sfs_operator_from_indices", "sfs_operator_from_indices_prec",
            "sfs_destroy_operator",
            "sfs_operator_info", "sfs_apply_A", "sfs_apply_AH", "sfs_apply_AH_noalloc",
-           "sfs_max_abs_AH",
+           "sfs_max_abs_AH", "sfs_apply_A_batched", "sfs_apply_AH_batched", "sfs_fista_batched",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
            "sfs_set_wait_timeout_ns",
            "sfs_inject_wait_timeout", "sfs_check_status", "sfs_last_error", "sfs_version")
@@ -116,6 +118,9 @@ def lib():
         "sfs_apply_AH": [vp, vp, vp, vp],
         "sfs_apply_AH_noalloc": [vp, vp, vp, vp],
         "sfs_max_abs_AH": [vp, vp, P(dbl), vp],
+        "sfs_apply_A_batched": [vp, i32, vp, vp, vp],
+        "sfs_apply_AH_batched": [vp, i32, vp, vp, vp],
+        "sfs_fista_batched": [vp, i32, vp, dbl, dbl, i32, vp, vp],
         "sfs_lipschitz": [vp, i32, dbl, u64, dbl, P(dbl), vp],
         "sfs_fista": [vp, vp, dbl, dbl, i32, vp, u32, P(dbl), vp],
         "sfs_kernel_times": [vp, P(dbl), P(dbl), P(ctypes.c_int32)],
@@ -360,6 +365,32 @@ class Operator:
         x = self._new(self.shape_x) if out is None else out
         sfs_apply_AH(self.handle, _dev_ptr(y, self.S * self.M, "y"), _dev_ptr(x, self.V, "x"),
                      _stream_ptr(stream, y.device))
+        return x
+
+    # ---- batched scenes sharing this operator (leading dimension = scene) ----
+    def apply_A_batched(self, x, out=None, stream=None):
+        B = int(x.shape[0])
+        y = self._new((B,) + self.shape_y) if out is None else out
+        _check(lib().sfs_apply_A_batched(self.handle, B, _dev_ptr(x, B * self.V, "x"),
+                                         _dev_ptr(y, B * self.S * self.M, "y"),
+                                         _stream_ptr(stream, x.device)))
+        return y
+
+    def apply_AH_batched(self, y, out=None, stream=None):
+        B = int(y.shape[0])
+        x = self._new((B,) + self.shape_x) if out is None else out
+        _check(lib().sfs_apply_AH_batched(self.handle, B, _dev_ptr(y, B * self.S * self.M, "y"),
+                                          _dev_ptr(x, B * self.V, "x"),
+                                          _stream_ptr(stream, y.device)))
+        return x
+
+    def fista_batched(self, y, lam, L, iters, x=None, stream=None):
+        """Scenes y[b] (same operator); lam < 0: lambda_b = -lam ||A^H y_b||_inf."""
+        B = int(y.shape[0])
+        x = self._new((B,) + self.shape_x) if x is None else x
+        _check(lib().sfs_fista_batched(self.handle, B, _dev_ptr(y, B * self.S * self.M, "y"),
+                                       float(lam), float(L), int(iters),
+                                       _dev_ptr(x, B * self.V, "x"), _stream_ptr(stream, y.device)))
         return x
 
     def max_abs_AH(self, y, stream=None) -> float:

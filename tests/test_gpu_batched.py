@@ -1,0 +1,144 @@
+"""Batched scenes sharing one operator (sfs_apply_A_batched,
+sfs_apply_AH_batched, sfs_fista_batched) against the single-scene calls and
+the FP64 oracle.
+
+A batched call runs the same arithmetic on every scene as the single-scene
+call: per-scene results agree with it to FP32 rounding (<= 1e-6 relative),
+and with the oracle at the precision's own tolerance (FP32 1e-5, BF16 2^-8,
+BF16X2 4 * 2^-16; see test_gpu_precision.py for their derivation).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests._common import crandn, ensure_built, geom_params, oracle_geometry, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "bf16": 2.0 ** -8, "bf16x2": 4 * 2.0 ** -16}
+
+
+@pytest.fixture(scope="module")
+def sfs():
+    ensure_built()
+    import torch
+    from paper_2012_04534_gb300 import sfs as mod
+    torch.cuda.init()
+    return mod
+
+
+def to_dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex64)).cuda()
+
+
+def to_host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.complex128)
+
+
+# (Nx, Ny, Nz, Nt, M, batch): area and line scans, ragged depths and bin
+# unions, batches that are not multiples of the 16-bit kernels' group of 4
+CASES = [
+    (12, 10, 20, 128, 12, 3),
+    (16, 16, 33, 256, 10, 5),
+    (32, 1, 64, 256, 32, 4),
+    (8, 8, 70, 512, 40, 2),
+    (5, 3, 1, 128, 1, 7),
+]
+
+
+@pytest.mark.parametrize("mode", list(TOL))
+@pytest.mark.parametrize("case", CASES)
+def test_batched_apply_equals_single_and_oracle(sfs, mode, case):
+    Nx, Ny, Nz, Nt, M, B = case
+    params = geom_params(Nx=Nx, Ny=Ny, Nz=Nz, dz=0.15e-3, Nt=Nt)
+    go = oracle_geometry(params)
+    idx = O.select_indices(go, O.SEL_RANDOM, M, True, 17)
+    g = sfs.Geometry(**params)
+    op = sfs.Operator.from_indices(g, idx, precision=sfs.PRECISION_NAMES[mode])
+    A = O.dense_A(go, idx)
+    rng = np.random.default_rng(23)
+    x = crandn(rng, B, Nz, Ny, Nx)
+    y = crandn(rng, B, g.S, M)
+    yb = to_host(op.apply_A_batched(to_dev(x)))
+    xb = to_host(op.apply_AH_batched(to_dev(y)))
+    for b in range(B):
+        ys = to_host(op.apply_A(to_dev(x[b])))
+        xs = to_host(op.apply_AH(to_dev(y[b])))
+        assert rel_err(yb[b], ys) <= 1e-6
+        assert rel_err(xb[b], xs) <= 1e-6
+        assert rel_err(yb[b], A @ x[b].ravel()) <= TOL[mode]
+        assert rel_err(xb[b], A.conj().T @ y[b].ravel()) <= TOL[mode]
+
+
+@pytest.mark.parametrize("mode", list(TOL))
+def test_batched_fista_equals_single_scene_solves(sfs, mode):
+    """Six scenes of the 32 x 32 x 128 workload geometry (U = 81) with their
+    own scatterers and noise, lambda by the mu rule per scene: the batched
+    solve returns every scene's single-scene iterate."""
+    w = synth.WORKLOADS["vol32"]
+    params = synth.geometry_params("vol32")
+    go = oracle_geometry(params)
+    idx = O.select_indices(go, O.SEL_RANDOM, w["M"], True, 1001)
+    g = sfs.Geometry(**params)
+    op = sfs.Operator.from_indices(g, idx, precision=sfs.PRECISION_NAMES[mode])
+    B = 6
+    ys = []
+    for b in range(B):
+        xt = synth.scene(op.shape_x, w["n_scatter"], w["amp"], seed=50 + b)
+        y0 = to_host(op.apply_A(to_dev(xt)))
+        sig = synth.noise_scale(float(np.vdot(y0, y0).real), y0.size, w["snr_db"])
+        ys.append(y0 + sig * synth.unit_noise(y0.shape, seed=70 + b))
+    y = np.stack(ys)
+    L, _ = op.lipschitz(max_iter=300, rtol=1e-6, seed=2, safety=1e-3)
+    xb = to_host(op.fista_batched(to_dev(y), -w["mu"], L, 40))
+    for b in range(B):
+        xs = to_host(op.fista(to_dev(y[b]), -w["mu"], L, 40))
+        assert np.abs(xs).max() > 0
+        assert rel_err(xb[b], xs) <= 1e-5
+
+
+def test_batched_fp32_fista_matches_oracle(sfs):
+    """Three scenes of a 10 x 10 x 16 geometry, 100 iterations, identical L and
+    lambda on both sides: each batched iterate within 1e-4 of the FP64 FISTA."""
+    params = geom_params(Nx=10, Ny=10, Nz=16, dz=0.15e-3, Nt=256)
+    go = oracle_geometry(params)
+    idx = O.select_indices(go, O.SEL_RANDOM, 12, True, 5)
+    g = sfs.Geometry(**params)
+    op = sfs.Operator.from_indices(g, idx)
+    ref = O.LateralFFTOperator(go, idx)
+    L, _ = O.power_iteration(ref.apply_A, ref.apply_AH, op.shape_x, 1, max_iter=400, rtol=1e-10)
+    L *= 1.001
+    ys, refs = [], []
+    for b in range(3):
+        xt = synth.scene(op.shape_x, 4, "uniform", seed=90 + b)
+        y0 = ref.apply_A(xt)
+        sig = synth.noise_scale(float(np.vdot(y0, y0).real), y0.size, 20.0)
+        yb = (y0 + sig * synth.unit_noise(y0.shape, seed=95 + b)).astype(np.complex64).astype(complex)
+        ys.append(yb)
+    lam = O.lambda_from_mu(ref.apply_AH, ys[0], 0.05)   # one lambda for every scene
+    for yb in ys:
+        refs.append(O.fista(ref.apply_A, ref.apply_AH, yb, lam, L, 100))
+    xb = to_host(op.fista_batched(to_dev(np.stack(ys)), lam, L, 100))
+    for b in range(3):
+        assert rel_err(xb[b], refs[b]) <= 1e-4
+
+
+def test_batched_invalid_arguments(sfs):
+    import ctypes
+    import torch
+    g = sfs.Geometry(**geom_params(Nx=4, Ny=4, Nz=4, dz=0.15e-3, Nt=64))
+    op = sfs.Operator.select(g, O.SEL_RANDOM, 3, True, 0)
+    x = torch.zeros((2,) + op.shape_x, dtype=torch.complex64, device="cuda")
+    y = torch.zeros((2,) + op.shape_y, dtype=torch.complex64, device="cuda")
+    L = sfs.lib()
+    for B in (0, -1, sfs.SFS_MAX_BATCH + 1):
+        assert L.sfs_apply_A_batched(op.handle, B, ctypes.c_void_p(x.data_ptr()),
+                                     ctypes.c_void_p(y.data_ptr()), None) == sfs.SFS_ERR_INVALID_ARG
+    assert L.sfs_fista_batched(op.handle, 2, ctypes.c_void_p(y.data_ptr()), 0.1, -1.0, 5,
+                               ctypes.c_void_p(x.data_ptr()), None) == sfs.SFS_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        op.apply_A_batched(x[:, :, :, :2].contiguous())
