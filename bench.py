@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-study", action="store_true",
                     help="skip the BF16 / BF16X2 vs FP32 time-to-same-NMSE study")
+    ap.add_argument("--batch-scenes", type=int, default=16,
+                    help="scenes of the batched-serving measurement (0 skips it)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -123,6 +125,50 @@ def precision_study(sfs, torch, geom, op, args, w, iters, y, L, x_true, flush, s
         else:
             rec.update({"iters_to_target": None, "ms_to_target": None, "speedup_vs_fp32": None})
         out["modes"][mode] = rec
+    return out
+
+
+def batched_study(sfs, torch, geom, op, args, w, iters, L, flush, stream, seed):
+    """Serving pattern of a fixed acquisition setup: args.batch_scenes scenes
+    (own scatterers and noise, same geometry and kept bins) solved by one
+    sfs_fista_batched call, lambda by the mu rule per scene, the same L and
+    iterations as the single-scene line.  Per precision: aggregate
+    scene-iterations/s and the solve latency (every scene of a batch
+    finishes with the batch) over 5 timed solves, L2 flushed before each."""
+    B = args.batch_scenes
+    ys = []
+    for b in range(B):
+        xt = torch.from_numpy(make_scene(w, seed + 100 + b).astype(np.complex64)).cuda()
+        y0 = op.apply_A(xt).cpu().numpy().astype(np.complex128)
+        sig = synth.noise_scale(float(np.vdot(y0, y0).real), y0.size, w["snr_db"])
+        ys.append((y0 + sig * synth.unit_noise(y0.shape, seed=seed + 300 + b)).astype(np.complex64))
+    y = torch.from_numpy(np.stack(ys)).cuda()
+    out = {"scenes": B, "iters": iters, "unit": "scene-iterations/s",
+           "timing": "device time of one batched solve (lambda rule + iterations), 5 solves, "
+                     "L2 flushed before each; latency = solve time (all scenes finish together)",
+           "modes": {}}
+    for mode in ("fp32", "bf16x2", "bf16"):
+        o = op if args.precision == mode else sfs.Operator.from_indices(
+            geom, op.idx, precision=sfs.PRECISION_NAMES[mode])
+        x = torch.empty((B,) + o.shape_x, dtype=torch.complex64, device="cuda")
+        o.fista_batched(y, -w["mu"], L, iters, x=x)  # workspace and graph capture
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(5):
+            flush.fill_(2)
+            a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            o.fista_batched(y, -w["mu"], L, iters, x=x)
+            b2.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b2))
+        ts.sort()
+        out["modes"][mode] = {"value": B * iters / (statistics.mean(ts) / 1e3),
+                              "latency_ms_p50": statistics.median(ts),
+                              "latency_ms_p99": ts[-1],
+                              # two plane launches; contractions per group of 4 scenes
+                              # (16-bit) or per scene (FP32), forward and adjoint
+                              "launches_per_iter": 2 + 2 * (B if mode == "fp32" else -(-B // 4))}
     return out
 
 
@@ -466,6 +512,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_precision_study:
         study = precision_study(sfs, torch, geom, op, args, w, iters, y, L, x_true, flush, stream)
 
+    # ---- batched serving: scenes sharing the operator in one solve ----
+    batched = None
+    if rank == 0 and world == 1 and args.batch_scenes > 0:
+        batched = batched_study(sfs, torch, geom, op, args, w, iters, L, flush, stream, seed)
+
     # ---- CPU baseline: the FP64 oracle, bounded sample, rank 0 only ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -503,6 +554,8 @@ def main():
             line["cpu_baseline"] = cpu
         if study is not None:
             line["precision_study"] = study
+        if batched is not None:
+            line["batched"] = batched
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
