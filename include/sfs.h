@@ -250,6 +250,52 @@ int sfs_fista_batched(sfs_operator* op, int batch, const void* y_dev, double lam
                       double L, int iters, void* x_out_dev, void* stream);
 
 /*
+ * Learned unrolled ISTA (not in the paper, which reconstructs with
+ * ISTA/FISTA, Sec. IV-A; the learned extension the workloads ask for).
+ * Layer l keeps Algorithm 1's gradient step and complex soft threshold with
+ * a learned step eta_l and threshold theta_l, followed by a residual 3-D
+ * convolutional proximal block (2 -> 8 -> 2 channels, 3x3x3, zero padding,
+ * ReLU; FP16 weights, FP32 accumulation):
+ *   z_l = x_l - (eta_l / L) A^H (A x_l - y/sigma),  s_l = tau_{theta_l}(z_l),
+ *   x_{l+1} = s_l + W2_l * relu(W1_l * [Re s_l, Im s_l] + b1_l) + b2_l,
+ * x_0 = 0, output sigma x_L with sigma = ||A^H y||_inf / L per scene, L the
+ * operator's Lipschitz constant (sfs_lipschitz), given at creation: the
+ * normalised data have ||A^H y_n||_inf = L, so eta ~ 1, theta ~ mu and the
+ * layer variables are O(1) whatever the data's scale.
+ * Parameters: float [layers][876] = eta, theta, W1 [8][2][3][3][3], b1 [8],
+ * W2 [2][8][3][3][3], b2 [2] per layer (row-major).  Batches of scenes share
+ * the operator (layouts as in the batched calls).
+ *   create:   network on `op` for up to max_batch scenes (allocates the
+ *             parameters, Adam moments and the activations of every layer).
+ *   set/get:  parameters from / to host memory (synchronous; set resets
+ *             the Adam moments); load_params_dev: from device memory.
+ *   forward:  x_dev [batch][V] <- network(y_dev [batch][S][M]); keeps every
+ *             layer's activations for backward.
+ *   backward: grad_params_dev (float [layers * 876], overwritten) <-
+ *             gradient of a real loss given grad_x_dev = dLoss/dRe x +
+ *             i dLoss/dIm x of the last forward (same batch).
+ *   nmse:     *loss_host = mean_b ||x_b - t_b||^2 / ||t_b||^2 and, if
+ *             grad_x_dev is not NULL, its gradient (synchronises).
+ *   adam:     one Adam step (bias-corrected; `step` counts from 1).
+ * Errors: SFS_ERR_INVALID_ARG, SFS_ERR_OOM, SFS_ERR_CUDA.
+ */
+typedef struct sfs_lista sfs_lista;  /* opaque, library owned */
+int sfs_lista_create(sfs_operator* op, int layers, int max_batch, double L, sfs_lista** out);
+int sfs_lista_destroy(sfs_lista* net);
+int sfs_lista_info(const sfs_lista* net, int32_t* layers, int32_t* nparams);
+int sfs_lista_set_params(sfs_lista* net, const float* params_host);
+int sfs_lista_get_params(const sfs_lista* net, float* params_host);
+/* parameters from device memory, enqueued on `stream` (Adam moments kept) */
+int sfs_lista_load_params_dev(sfs_lista* net, const void* params_dev, void* stream);
+int sfs_lista_forward(sfs_lista* net, int batch, const void* y_dev, void* x_dev, void* stream);
+int sfs_lista_backward(sfs_lista* net, int batch, const void* grad_x_dev, void* grad_params_dev,
+                       void* stream);
+int sfs_lista_nmse(sfs_lista* net, int batch, const void* x_dev, const void* xtrue_dev,
+                   void* grad_x_dev, double* loss_host, void* stream);
+int sfs_lista_adam(sfs_lista* net, const void* grad_params_dev, float lr, float beta1,
+                   float beta2, float eps, int step, void* stream);
+
+/*
  * ||A^H y||_inf (used by the regularisation rule lambda = mu ||beta(y)||_inf
  * of Sec. VII).  Synchronises `stream`; writes the value to *out_host.
  */

@@ -12,21 +12,23 @@ complex soft threshold with its own learned step eta_l and threshold
 theta_l, and adds a residual 3-D convolutional proximal block:
 
     g_l     = A^H (A x_l - y_n)                    gradient of 1/2||A x - y_n||^2
-    z_l     = x_l - eta_l g_l
+    z_l     = x_l - (eta_l / L) g_l
     s_l     = tau_{theta_l}(z_l)                    complex soft threshold
     h_l     = W1_l * [Re s_l, Im s_l] + b1_l        8 channels, 3x3x3
     x_{l+1} = s_l + (W2_l * relu(h_l) + b2_l)       2 channels read as re, im
 
-with x_0 = 0, y_n = y / sigma, sigma = ||A^H y||_inf (so thresholds are in
-units of the data's own scale), output x = sigma x_L.  "*" is the 3-D
+with x_0 = 0, y_n = y / sigma, sigma = ||A^H y||_inf / L (L the operator's
+Lipschitz constant, so that ||A^H y_n||_inf = L and the layer variables are
+O(1) whatever the data's scale), output x = sigma x_L.  "*" is the 3-D
 cross-correlation with zero padding: (W * u)[o](z, y, x) =
 sum_{i, dz, dy, dx} W[o][i][dz][dy][dx] u[i](z + dz - 1, y + dy - 1, x + dx - 1).
 
 Parameters of layer l, flat in this order (876 numbers):
-eta, theta, W1 (8, 2, 3, 3, 3), b1 (8), W2 (2, 8, 3, 3, 3), b2 (2).
+eta, theta, W1 (8, 2, 3, 3, 3), b1 (8), W2 (2, 8, 3, 3, 3), b2 (2).  Both
+eta (step in units of 1/L) and theta are O(1), like the other parameters.
 
-Parity status (tests/test_oracle_pins.py): conv3d is pinned by
-scipy.ndimage.correlate; the forward with zero convolutions and eta = 1/L,
+Parity status (tests/test_lista_oracle_pins.py): conv3d is pinned by
+scipy.ndimage.correlate; the forward with zero convolutions and eta = 1,
 theta = lambda/(sigma L) is pinned by L single-iteration warm-started
 FISTA steps of sfs_oracle.fista (which are ISTA steps); the analytic
 backward is pinned by central finite differences of the loss.
@@ -119,24 +121,24 @@ def soft(z, theta):
     return np.where(mag > theta, z * (1.0 - theta / np.where(mag > 0, mag, 1.0)), 0.0)
 
 
-def forward(apply_A: Callable, apply_AH: Callable, y, params, layers: int):
+def forward(apply_A: Callable, apply_AH: Callable, y, params, layers: int, L: float):
     """Network output x and the cache of every layer's inputs for backward."""
     P = split_params(params, layers)
     y = np.asarray(y, dtype=np.complex128)
-    sigma = float(np.abs(apply_AH(y)).max())
+    sigma = float(np.abs(apply_AH(y)).max()) / L
     yn = y / sigma
     x = np.zeros_like(apply_AH(yn))
     cache = []
     for q in P:
         g = apply_AH(apply_A(x) - yn)
-        z = x - q["eta"] * g
+        z = x - (q["eta"] / L) * g
         s = soft(z, q["theta"])
         sc = np.stack([s.real, s.imag])
         h = conv3d(sc, q["W1"], q["b1"])
         r = conv3d(np.maximum(h, 0.0), q["W2"], q["b2"])
         cache.append(dict(x=x, g=g, z=z, s=s, h=h))
         x = s + (r[0] + 1j * r[1])
-    return sigma * x, dict(layers=cache, sigma=sigma)
+    return sigma * x, dict(layers=cache, sigma=sigma, L=L)
 
 
 def backward(apply_A: Callable, apply_AH: Callable, params, layers: int, cache, grad_x):
@@ -166,9 +168,10 @@ def backward(apply_A: Callable, apply_AH: Callable, params, layers: int, cache, 
         ug = (np.conj(u) * gs).real
         gz = np.where(act, (1.0 - q["theta"] / rs) * gs + (q["theta"] / rs) * u * ug, 0.0)
         dtheta = -float(np.where(act, ug, 0.0).sum())
-        # gradient step z = x - eta A^H (A x - y_n)
-        deta = -float((np.conj(c["g"]) * gz).real.sum())
-        gx = gz - q["eta"] * apply_AH(apply_A(gz))
+        # gradient step z = x - (eta / L) A^H (A x - y_n)
+        L = cache["L"]
+        deta = -float((np.conj(c["g"]) * gz).real.sum()) / L
+        gx = gz - (q["eta"] / L) * apply_AH(apply_A(gz))
         grads[l] = np.concatenate([[deta, dtheta], dW1.ravel(), db1, dW2.ravel(), db2])
     return np.concatenate(grads)
 
@@ -183,11 +186,13 @@ def nmse_loss(x, x_true):
 
 
 def init_params(layers: int, L: float, mu: float, rng, w_scale: float = 0.02):
-    """eta_l = 1/L, theta_l = mu/L (lambda = mu ||A^H y||_inf in units of
-    sigma), small random convolution weights, zero biases."""
+    """eta_l = 1 (step 1/L), theta_l = mu (lambda = mu ||A^H y_n||_inf = mu L,
+    so lambda / L = mu in the normalised units), small random convolution
+    weights, zero biases.  (L is kept in the signature for symmetry with
+    forward; the initial values do not depend on it.)"""
     p = []
     for _ in range(layers):
         W1 = w_scale * rng.standard_normal(C_HID * 2 * 27)
         W2 = w_scale * rng.standard_normal(2 * C_HID * 27)
-        p.append(np.concatenate([[1.0 / L, mu / L], W1, np.zeros(C_HID), W2, np.zeros(2)]))
+        p.append(np.concatenate([[1.0, mu], W1, np.zeros(C_HID), W2, np.zeros(2)]))
     return np.concatenate(p)

@@ -478,6 +478,40 @@ int fista_graph(sfs_operator* op, int iters, bool with_obj, cudaGraphExec_t* out
   return SFS_OK;
 }
 
+}  // namespace
+
+// ---- batched building blocks shared with the learned network (sfs_lista.cu) ----
+int batch_workspace(sfs_operator* op, int batch) { return ensure_batch(op, batch); }
+
+int batched_normal_residual(sfs_operator* op, int batch, const float2* x, const float2* yplane,
+                            float2* g, cudaStream_t st) {
+  SFS_TRY(ensure_batch(op, batch));
+  const PlaneDims d = batch_dims(op, batch);
+  const sfs::BatchWorkspace& w = op->bws;
+  SFS_TRY(launch_fwd_planes(d, x, w.Xh, st));
+  SFS_TRY(launch_contract_fwd(d, op->table, w.Xh, w.Yh, op->ws.err, st));
+  SFS_TRY(launch_inv_resid_fwd(d, w.Yh, op->posmap, yplane, w.Rh, nullptr, st));
+  SFS_TRY(launch_contract_adj(d, op->table, w.Rh, w.Gh, op->ws.err, st));
+  return launch_inv_store(d, w.Gh, op->ws.segslot, g, nullptr, nullptr, st);
+}
+
+int batched_maxabs_AH(sfs_operator* op, int batch, const float2* y, float* scal, cudaStream_t st) {
+  SFS_TRY(ensure_batch(op, batch));
+  const PlaneDims d = batch_dims(op, batch);
+  const sfs::BatchWorkspace& w = op->bws;
+  SFS_TRY(launch_scatter_fwd(d, y, op->posmap, w.Rh, st));
+  SFS_TRY(launch_contract_adj(d, op->table, w.Rh, w.Gh, op->ws.err, st));
+  return launch_inv_store(d, w.Gh, op->ws.segslot, nullptr, nullptr, (unsigned int*)(scal + kLamMax), st);
+}
+
+int batched_scatter_y(sfs_operator* op, int batch, const float2* y, float2* yplane, cudaStream_t st) {
+  return launch_scatter_y_planes(batch_dims(op, batch), y, op->posmap, yplane, st);
+}
+
+int operator_device(const sfs_operator* op) { return op->geo.d.device; }
+
+namespace {
+
 // Reads (and clears) the device timeout flag; call only where the stream is
 // synchronised anyway.
 int check_err_flag(sfs_operator* op, cudaStream_t st) {

@@ -261,6 +261,18 @@ int launch_contract_adj_h(const PlaneDims& d, const float2* Rh, float2* Gs, int*
                           cudaStream_t st);
 int prepare_tc16_kernels(const PlaneDims& d);
 
+// Batched building blocks (sfs_api.cu) used by the learned network
+// (sfs_lista.cu), on the operator's batched workspace:
+//   g = A^H (A x - y) for `batch` scenes, y given by bin plane ([batch][U][S];
+//   zeros give A^H A x);  scal[b * kNumFloatScalars + kLamMax] = max |A^H y_b|
+//   (as float bits, the slots zeroed by the caller);  y -> yplane.
+int batch_workspace(sfs_operator* op, int batch);
+int batched_normal_residual(sfs_operator* op, int batch, const float2* x, const float2* yplane,
+                            float2* g, cudaStream_t st);
+int batched_maxabs_AH(sfs_operator* op, int batch, const float2* y, float* scal, cudaStream_t st);
+int batched_scatter_y(sfs_operator* op, int batch, const float2* y, float2* yplane, cudaStream_t st);
+int operator_device(const sfs_operator* op);
+
 // Small helpers.
 int launch_set_thresholds(float* scal, double* red, double lambda, double L,
                           int use_mu, double mu, int* err, cudaStream_t st);

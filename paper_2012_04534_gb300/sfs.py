@@ -55,6 +55,9 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_destroy_operator",
            "sfs_operator_info", "sfs_apply_A", "sfs_apply_AH", "sfs_apply_AH_noalloc",
            "sfs_max_abs_AH", "sfs_apply_A_batched", "sfs_apply_AH_batched", "sfs_fista_batched",
+           "sfs_lista_create", "sfs_lista_destroy", "sfs_lista_info", "sfs_lista_set_params",
+           "sfs_lista_get_params", "sfs_lista_load_params_dev", "sfs_lista_forward",
+           "sfs_lista_backward", "sfs_lista_nmse", "sfs_lista_adam",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
            "sfs_set_wait_timeout_ns",
            "sfs_inject_wait_timeout", "sfs_check_status", "sfs_last_error", "sfs_version")

@@ -40,8 +40,8 @@ def test_conv3d_transpose_and_weight_grad_are_adjoints():
 
 
 def test_zero_prox_network_is_ista():
-    """W = b = 0, eta_l = 1/L, theta_l = lambda/(sigma L): the network is L
-    ISTA steps, i.e. L warm-started single-iteration FISTA steps."""
+    """W = b = 0, eta_l = 1 (step 1/L), theta_l = lambda/(sigma L): the network is
+    `layers` ISTA steps, i.e. warm-started single-iteration FISTA steps."""
     g = small_geom()
     idx = O.select_indices(g, O.SEL_RANDOM, 4, True, 3)
     A = O.dense_A(g, idx)
@@ -51,13 +51,13 @@ def test_zero_prox_network_is_ista():
     y = rng.standard_normal((g.S, 4)) + 1j * rng.standard_normal((g.S, 4))
     L = float(np.linalg.svd(A, compute_uv=False)[0] ** 2) * 1.01
     lam = 0.1 * float(np.abs(fAH(y)).max())
-    sigma = float(np.abs(fAH(y)).max())
+    sigma = float(np.abs(fAH(y)).max()) / L
     layers = 5
     p = np.zeros(layers * LO.PER_LAYER)
     for l in range(layers):
-        p[l * LO.PER_LAYER] = 1.0 / L
+        p[l * LO.PER_LAYER] = 1.0
         p[l * LO.PER_LAYER + 1] = lam / (sigma * L)
-    x_net, _ = LO.forward(fA, fAH, y, p, layers)
+    x_net, _ = LO.forward(fA, fAH, y, p, layers, L)
     x = np.zeros((g.Nz, g.Ny, g.Nx), complex)
     for _ in range(layers):
         x = O.fista(fA, fAH, y, lam, L, 1, x0=x)
@@ -77,15 +77,15 @@ def test_backward_matches_central_differences():
     L = float(np.linalg.svd(A, compute_uv=False)[0] ** 2) * 1.01
     layers = 2
     p = LO.init_params(layers, L, 0.05, rng, w_scale=0.1)
-    p[1::LO.PER_LAYER][:layers] = 0.02 / L
+    p[1::LO.PER_LAYER][:layers] = 0.02
     # positive first-layer biases: some ReLUs on, some off
     p[LO.PER_LAYER - 2 - 2 * LO.C_HID * 27 - LO.C_HID:LO.PER_LAYER - 2 - 2 * LO.C_HID * 27] = 0.05
 
     def loss(q):
-        x, _ = LO.forward(fA, fAH, y, q, layers)
+        x, _ = LO.forward(fA, fAH, y, q, layers, L)
         return LO.nmse_loss(x, x_true)[0]
 
-    x, cache = LO.forward(fA, fAH, y, p, layers)
+    x, cache = LO.forward(fA, fAH, y, p, layers, L)
     _, gx = LO.nmse_loss(x, x_true)
     grad = LO.backward(fA, fAH, p, layers, cache, gx)
     # eta, theta of both layers, and a sample of weights and biases
