@@ -53,6 +53,9 @@ def parse():
                     help="skip the BF16 / BF16X2 vs FP32 time-to-same-NMSE study")
     ap.add_argument("--batch-scenes", type=int, default=16,
                     help="scenes of the batched-serving measurement (0 skips it)")
+    ap.add_argument("--learned-steps", type=int, default=400,
+                    help="training steps of the learned unrolled ISTA measurement on the vol32 "
+                         "workload (0 skips it)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -170,6 +173,88 @@ def batched_study(sfs, torch, geom, op, args, w, iters, L, flush, stream, seed):
                               # (16-bit) or per scene (FP32), forward and adjoint
                               "launches_per_iter": 2 + 2 * (B if mode == "fp32" else -(-B // 4))}
     return out
+
+
+def learned_study(sfs, torch, op, args, w, L, stream, seed):
+    """Train the 16-layer unrolled ISTA (library kernels: forward, backward,
+    Adam) for args.learned_steps steps of 8 fresh scenes of the LEARNED
+    recipe, then on 32 held-out scenes compare its NMSE and time with
+    batched FISTA (same operator, lambda by the mu rule) at 4 .. 300
+    iterations: the first count of the ladder that reaches the network's
+    NMSE, and its time."""
+    from paper_2012_04534_gb300 import lista
+    layers, B = synth.LEARNED["layers"], 8
+    net = lista.LISTA(op, layers, B, L)
+    rng = np.random.default_rng(seed + 4242)
+    p = []
+    for _ in range(layers):
+        p.append(np.concatenate([[1.0, w["mu"]], 0.02 * rng.standard_normal(432), np.zeros(8),
+                                 0.02 * rng.standard_normal(432), np.zeros(2)]))
+    net.set_params(np.concatenate(p).astype(np.float32))
+
+    def batch(base):
+        xs, snrs = zip(*[synth.learned_draw(op.shape_x, base + b) for b in range(B)])
+        xt = torch.from_numpy(np.stack(xs).astype(np.complex64)).cuda()
+        y0 = op.apply_A_batched(xt).cpu().numpy().astype(np.complex128)
+        ys = []
+        for b in range(B):
+            sig = synth.noise_scale(float(np.vdot(y0[b], y0[b]).real), y0[b].size, snrs[b])
+            ys.append(y0[b] + sig * synth.unit_noise(y0[b].shape, seed=base + b + 99991))
+        return torch.from_numpy(np.stack(ys).astype(np.complex64)).cuda(), xt
+
+    steps = args.learned_steps
+    t0 = time.perf_counter()
+    for step in range(1, steps + 1):
+        yb, xb = batch(seed * 1000003 + step * B)
+        x = net.forward(yb)
+        _, gx = net.nmse(x, xb)
+        g = net.backward(gx)
+        lr = 3e-3 * (0.5 * (1 + math.cos(math.pi * (step - 1) / steps)))
+        net.adam(g, max(lr, 2e-5), step)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    evals = [batch(10 ** 9 + 97 * k) for k in range(4)]
+
+    def timed(f):
+        """Device time per evaluation batch of f(y) (after a warm pass, which
+        also captures FISTA's graphs) and f's outputs."""
+        for y, _ in evals:
+            f(y)
+        torch.cuda.synchronize()
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        outs = [f(y) for y, _ in evals]
+        b2.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b2) / len(evals), outs
+
+    def mean_nmse(xs):
+        v = []
+        for (_, xt), x in zip(evals, xs):
+            num = ((x - xt).abs() ** 2).sum(dim=(1, 2, 3))
+            den = (xt.abs() ** 2).sum(dim=(1, 2, 3))
+            v += (num / den).tolist()
+        return float(10 * np.log10(np.mean(v)))
+
+    ms_lista, xs = timed(lambda y: net.forward(y))
+    nmse_lista = mean_nmse(xs)
+    ladder = []
+    reach = None
+    for K in (4, 8, 16, 32, 64, 128, 160, 192, 224, 256, 300):
+        ms_k, xk = timed(lambda y, K=K: op.fista_batched(y, -w["mu"], L, K))
+        nm = mean_nmse(xk)
+        ladder.append({"iters": K, "nmse_db": nm, "ms_per_batch": ms_k})
+        if reach is None and nm <= nmse_lista:
+            reach = (K, ms_k)
+    return {"layers": layers, "batch": B, "train_steps": steps, "train_scenes": steps * B,
+            "train_s": t_train, "precision": args.precision,
+            "scenes": "1-20 scatterers, U(0.5,1) magnitudes, uniform phase, 10-30 dB SNR "
+                      "(training scenes drawn fresh every step; 32 held-out scenes)",
+            "nmse_db": nmse_lista, "ms_per_batch": ms_lista,
+            "fista": ladder,
+            "fista_iters_to_same_nmse": None if reach is None else reach[0],
+            "fista_ms_to_same_nmse": None if reach is None else reach[1],
+            "speedup_vs_fista": None if reach is None else reach[1] / ms_lista}
 
 
 def workload_desc(name, w, strategy, iters):
@@ -517,6 +602,11 @@ def main():
     if rank == 0 and world == 1 and args.batch_scenes > 0:
         batched = batched_study(sfs, torch, geom, op, args, w, iters, L, flush, stream, seed)
 
+    # ---- learned unrolled ISTA vs FISTA, time to the same NMSE ----
+    learned = None
+    if rank == 0 and world == 1 and args.learned_steps > 0 and args.workload == synth.LEARNED["workload"]:
+        learned = learned_study(sfs, torch, op, args, w, L, stream, seed)
+
     # ---- CPU baseline: the FP64 oracle, bounded sample, rank 0 only ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -556,6 +646,8 @@ def main():
             line["precision_study"] = study
         if batched is not None:
             line["batched"] = batched
+        if learned is not None:
+            line["learned"] = learned
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

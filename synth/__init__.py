@@ -42,6 +42,19 @@ WORKLOADS = {
 GEOM_KEYS = ("Nx", "Ny", "dx", "dy", "Nz", "z0", "dz", "c", "fs", "Nt", "fc",
              "frac_bw", "theta")
 
+# Learned unrolled ISTA: the vol32 geometry with M = 64 random bins, 16
+# layers; training and evaluation scenes with 1-20 scatterers of U(0.5, 1)
+# magnitude and uniform phase, SNR uniform in 10-30 dB.
+LEARNED = dict(workload="vol32", layers=16, n_scatter=(1, 20), snr_db=(10.0, 30.0), amp="uniform")
+
+
+def learned_draw(shape, seed):
+    """One training / evaluation scene of the LEARNED recipe: (x, snr_db)."""
+    rng = np.random.default_rng(seed + 7777)
+    n = int(rng.integers(LEARNED["n_scatter"][0], LEARNED["n_scatter"][1] + 1))
+    snr = float(rng.uniform(*LEARNED["snr_db"]))
+    return scene(shape, n, LEARNED["amp"], seed=seed), snr
+
 
 def geometry_params(name_or_dict):
     """Geometry fields of a workload (a dict usable by both sides)."""
