@@ -33,7 +33,7 @@ import numpy as np  # noqa: E402
 
 import synth  # noqa: E402
 
-STRATEGY_NAMES = {"random": 0, "contiguous": 1, "equispaced": 2}
+STRATEGY_NAMES = {"random": 0, "contiguous": 1, "equispaced": 2, "maximal": 3, "energy": 4}
 
 
 def parse():

@@ -47,7 +47,15 @@ typedef enum sfs_status {
 typedef enum sfs_strategy {
   SFS_SEL_RANDOM = 0,      /* uniform M-subset of the candidate band (Phi_rnd)  */
   SFS_SEL_CONTIGUOUS = 1,  /* M adjacent bins centred on round(fc Nt / fs)      */
-  SFS_SEL_EQUISPACED = 2   /* k_lo + floor((2i+1)|C|/(2M)), i = 0..M-1          */
+  SFS_SEL_EQUISPACED = 2,  /* k_lo + floor((2i+1)|C|/(2M)), i = 0..M-1          */
+  SFS_SEL_MAXIMAL = 3,     /* Phi_max: the M bins of largest |H(f_k)| (ties to
+                              the lower bin), shared by all positions          */
+  SFS_SEL_ENERGY = 4       /* Phi_nrg (shared) or Phi_nrg,f (per_position):
+                              M bins drawn without replacement with
+                              probability ~ |H(f_k)| among those left; integer
+                              weights floor(2^24 |H(f_k)| / max|H|) and draw
+                              r = floor(u W / 2^64) from the SplitMix64 stream
+                              of the position                                  */
 } sfs_strategy;
 
 /*

@@ -53,6 +53,8 @@ import numpy as np
 SEL_RANDOM = 0
 SEL_CONTIGUOUS = 1
 SEL_EQUISPACED = 2
+SEL_MAXIMAL = 3
+SEL_ENERGY = 4
 
 BAND_LADDER_DB = (6.0, 10.0, 20.0, 40.0)
 
@@ -224,6 +226,52 @@ def random_subset(n_cand: int, M: int, stream: SplitMix64):
     return sorted(perm[:M])
 
 
+def pulse_weights(g: Geometry):
+    """Relative pulse magnitudes e_k = |H(f_k)| / max |H| =
+    exp(-(pi (f_k - fc) / alpha)^2) of the bins k = 0..Nt/2 (the analytic
+    pulse has no energy at negative frequencies), and the integer weights
+    floor(2^24 e_k) of the energy-based draw."""
+    e = []
+    for k in range(g.Nt // 2 + 1):
+        a = math.pi * (k * g.fs / g.Nt - g.fc) / g.alpha
+        e.append(math.exp(-a * a))
+    return e, [int(math.floor(v * 16777216.0)) for v in e]
+
+
+def maximal_set(g: Geometry, M: int):
+    """J_M of Sec. III-A (Phi_max): the M bins with the largest |hat h_n|,
+    ties to the lower bin, ascending."""
+    e, _ = pulse_weights(g)
+    if M > len(e):
+        raise ValueError("M exceeds the Nt/2 + 1 bins")
+    return sorted(sorted(range(len(e)), key=lambda k: (-e[k], k))[:M])
+
+
+def energy_subset(weights, M: int, stream: "SplitMix64"):
+    """Random energy-based draw of Sec. III-A (Phi_nrg): M bins drawn one by
+    one with probability proportional to the pulse energy q_i = |hat h_i| /
+    ||hat h||_1 among the bins not yet drawn (drawn bins get weight 0 and the
+    rest is renormalised).  Reading: integer weights floor(2^24 |H| / max|H|)
+    and, per draw, r = floor(u W / 2^64) for the next 64-bit u and the
+    remaining total W; the bin whose cumulative weight first exceeds r is
+    drawn.  Returned ascending."""
+    w = list(weights)
+    if sum(1 for v in w if v > 0) < M:
+        raise ValueError("fewer than M bins carry pulse energy")
+    out = []
+    for _ in range(M):
+        W = sum(w)
+        r = (stream.next() * W) >> 64
+        c = 0
+        for k, v in enumerate(w):
+            c += v
+            if c > r:
+                out.append(k)
+                w[k] = 0
+                break
+    return sorted(out)
+
+
 def select_indices(g: Geometry, strategy: int, M: int, per_position: bool,
                    seed: int):
     """Selected bin indices idx[S][M] (int32, ascending per position).
@@ -236,11 +284,27 @@ def select_indices(g: Geometry, strategy: int, M: int, per_position: bool,
     * EQUISPACED: idx_i = k_lo + floor((2i+1)|C| / (2M)).
     The last two are not in the paper; they are the workloads' comparison
     strategies, shared by all positions.
+    * MAXIMAL: Phi_max (Sec. III-A), the M bins of largest pulse magnitude,
+      shared by all positions.
+    * ENERGY: Phi_nrg, or Phi_nrg,f when per_position (Sec. III-A, Table I),
+      drawn by energy_subset from the same per-position streams as RANDOM.
+    MAXIMAL and ENERGY draw from all bins 0..Nt/2, not from the band C.
     """
-    k_lo, k_hi, _ = candidate_band(g, M)
-    n_cand = k_hi - k_lo + 1
     S = g.S
     idx = np.empty((S, M), dtype=np.int32)
+    if strategy == SEL_MAXIMAL:
+        idx[:] = maximal_set(g, M)
+        return idx
+    if strategy == SEL_ENERGY:
+        _, w = pulse_weights(g)
+        rows = S if per_position else 1
+        for s in range(rows):
+            idx[s] = energy_subset(w, M, SplitMix64(seed ^ ((s * _GOLDEN) & _MASK64)))
+        if not per_position:
+            idx[:] = idx[0]
+        return idx
+    k_lo, k_hi, _ = candidate_band(g, M)
+    n_cand = k_hi - k_lo + 1
     if strategy == SEL_RANDOM:
         rows = S if per_position else 1
         for s in range(rows):

@@ -117,6 +117,20 @@ int candidate_band(const sfs_geometry* g, int M, int* k_lo, int* k_hi, double* d
   return SFS_ERR_BAND_TOO_NARROW;
 }
 
+// Relative pulse magnitudes e_k = |H(f_k)| / max |H| = exp(-(pi (f_k - fc) /
+// alpha)^2) of the bins k = 0..Nt/2 and the integer weights floor(2^24 e_k)
+// of the energy-based draw (Sec. III-A, q_i = |hat h_i| / ||hat h||_1).
+void pulse_weights(const sfs_geometry* g, std::vector<double>& e, std::vector<int64_t>& w) {
+  const int nb = g->d.Nt / 2 + 1;
+  e.resize(nb);
+  w.resize(nb);
+  for (int k = 0; k < nb; ++k) {
+    const double a = M_PI * ((double)k * g->d.fs / g->d.Nt - g->d.fc) / g->alpha;
+    e[k] = exp(-a * a);
+    w[k] = (int64_t)floor(e[k] * 16777216.0);
+  }
+}
+
 int select_host(const sfs_geometry* g, int strategy, int M, int per_position, uint64_t seed,
                 int32_t* idx, int* k_lo_out, int* k_hi_out, double* db_out) {
   if (M <= 0) {
@@ -125,9 +139,64 @@ int select_host(const sfs_geometry* g, int strategy, int M, int per_position, ui
   }
   int k_lo, k_hi;
   double db;
+  const int S = g->d.Nx * g->d.Ny;
+  if (strategy == SFS_SEL_MAXIMAL || strategy == SFS_SEL_ENERGY) {
+    // Phi_max and Phi_nrg(,f) of Sec. III-A draw from all bins 0..Nt/2
+    std::vector<double> e;
+    std::vector<int64_t> w;
+    pulse_weights(g, e, w);
+    const int nb = (int)e.size();
+    int nonzero = 0;
+    for (int64_t v : w) nonzero += v > 0;
+    if (M > (strategy == SFS_SEL_MAXIMAL ? nb : nonzero)) {
+      set_error("M = %d exceeds the %d bins that carry pulse energy", M,
+                strategy == SFS_SEL_MAXIMAL ? nb : nonzero);
+      return SFS_ERR_BAND_TOO_NARROW;
+    }
+    const int rows = (strategy == SFS_SEL_ENERGY && per_position) ? S : 1;
+    for (int s = 0; s < rows; ++s) {
+      std::vector<int> pick;
+      if (strategy == SFS_SEL_MAXIMAL) {
+        std::vector<int> order(nb);
+        for (int k = 0; k < nb; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return e[a] > e[b]; });
+        pick.assign(order.begin(), order.begin() + M);
+      } else {
+        std::vector<int64_t> ww = w;
+        SplitMix64 rng{seed ^ ((uint64_t)s * 0x9E3779B97F4A7C15ull)};
+        for (int n = 0; n < M; ++n) {
+          uint64_t W = 0;
+          for (int64_t v : ww) W += (uint64_t)v;
+          const uint64_t r = (uint64_t)(((unsigned __int128)rng.next() * W) >> 64);
+          uint64_t c = 0;
+          for (int k = 0; k < nb; ++k) {
+            c += (uint64_t)ww[k];
+            if (c > r) {
+              pick.push_back(k);
+              ww[k] = 0;
+              break;
+            }
+          }
+        }
+      }
+      std::sort(pick.begin(), pick.end());
+      for (int m = 0; m < M; ++m) idx[(size_t)s * M + m] = pick[m];
+    }
+    for (int s = rows; s < S; ++s) memcpy(idx + (size_t)s * M, idx, sizeof(int32_t) * M);
+    // the band is reported when it exists; otherwise the span of the sets
+    if (candidate_band(g, M, &k_lo, &k_hi, &db) != SFS_OK) {
+      clear_error();
+      k_lo = *std::min_element(idx, idx + (size_t)S * M);
+      k_hi = *std::max_element(idx, idx + (size_t)S * M);
+      db = NAN;
+    }
+    if (k_lo_out) *k_lo_out = k_lo;
+    if (k_hi_out) *k_hi_out = k_hi;
+    if (db_out) *db_out = db;
+    return SFS_OK;
+  }
   SFS_TRY(candidate_band(g, M, &k_lo, &k_hi, &db));
   const int n = k_hi - k_lo + 1;
-  const int S = g->d.Nx * g->d.Ny;
   switch (strategy) {
     case SFS_SEL_RANDOM: {
       std::vector<int> perm(n);

@@ -32,6 +32,8 @@ SFS_ERR_NON_FINITE = -7
 SFS_SEL_RANDOM = 0
 SFS_SEL_CONTIGUOUS = 1
 SFS_SEL_EQUISPACED = 2
+SFS_SEL_MAXIMAL = 3
+SFS_SEL_ENERGY = 4
 
 SFS_PREC_FP32 = 0
 SFS_PREC_TF32X3 = 1

@@ -67,6 +67,21 @@ def test_host_selection_bit_exact_with_oracle(sfs, name, strategy):
         assert band == (k_lo, k_hi)
 
 
+@pytest.mark.parametrize("name", ["line2d", "vol32", "vol64"])
+@pytest.mark.parametrize("strategy", [O.SEL_MAXIMAL, O.SEL_ENERGY])
+def test_host_knowledge_based_selection_bit_exact_with_oracle(sfs, name, strategy):
+    """Phi_max and Phi_nrg(,f) (Sec. III-A): the host sets equal the oracle's
+    bit for bit, shared and per position, for several seeds and M."""
+    params = synth.geometry_params(name)
+    g = sfs.Geometry(**params)
+    go = O.Geometry(**params)
+    for M in (1, 7, synth.WORKLOADS[name]["M"]):
+        for per in (True, False):
+            for seed in (0, 99, 2**63 + 11):
+                idx, _ = g.select_indices(strategy, M, per, seed=seed)
+                assert np.array_equal(idx, O.select_indices(go, strategy, M, per, seed=seed))
+
+
 def test_host_selection_many_seeds_and_sizes(sfs):
     for (Nx, Ny, Nt, M) in [(5, 3, 128, 7), (1, 1, 64, 1), (9, 1, 256, 20), (4, 4, 512, 40)]:
         p = geom_params(Nx=Nx, Ny=Ny, Nz=3, dz=1e-4, Nt=Nt)

@@ -81,7 +81,8 @@ def test_apply_A_and_AH_match_dense_oracle(sfs, case):
     assert np.abs(xa - ref_x).max() <= 1e-4 * np.abs(ref_x).max()
 
 
-@pytest.mark.parametrize("strategy", [O.SEL_RANDOM, O.SEL_CONTIGUOUS, O.SEL_EQUISPACED])
+@pytest.mark.parametrize("strategy", [O.SEL_RANDOM, O.SEL_CONTIGUOUS, O.SEL_EQUISPACED,
+                                      O.SEL_MAXIMAL, O.SEL_ENERGY])
 @pytest.mark.parametrize("per_position", [True, False])
 def test_strategies_select_and_apply(sfs, strategy, per_position):
     params = geom_params(Nx=9, Ny=6, Nz=11, dz=0.15e-3, Nt=256)

@@ -114,6 +114,50 @@ def test_contiguous_is_centred_on_peak_and_equispaced_spread():
     assert np.array_equal(cells, np.arange(M))
 
 
+def test_maximal_set_holds_the_largest_pulse_magnitudes():
+    """Phi_max (Sec. III-A): the M bins with the largest |H(f_k)| of the
+    pinned pulse spectrum (ties to the lower bin), shared by all positions."""
+    g = small_geom(Nx=4, Ny=3, Nt=512)
+    k = np.arange(g.Nt // 2 + 1)
+    mag = np.abs(O.pulse_spectrum(g.bin_freq(k), g.fc, g.alpha))
+    for M in (1, 2, 9, 40):
+        idx = O.select_indices(g, O.SEL_MAXIMAL, M, True, 3)
+        assert np.all(idx == idx[0])
+        ref = np.sort(np.lexsort((k, -mag))[:M])
+        assert np.array_equal(idx[0], ref)
+        # a contiguous run around the peak bin fc Nt / fs = 64
+        assert np.all(np.diff(idx[0]) == 1) and idx[0][0] <= 64 <= idx[0][-1]
+
+
+def test_energy_draw_follows_the_pulse_energy():
+    """Phi_nrg (Sec. III-A): a single draw picks bin k with probability
+    q_k = |H(f_k)| / sum |H| (chi-square over 20000 streams, p > 1e-4);
+    larger draws are distinct, ascending, reproducible per seed and vary per
+    position (Phi_nrg,f)."""
+    from scipy.stats import chi2
+    g = small_geom(Nx=5, Ny=4, Nt=64)
+    e, w = O.pulse_weights(g)
+    k = np.arange(g.Nt // 2 + 1)
+    q = np.abs(O.pulse_spectrum(g.bin_freq(k), g.fc, g.alpha))
+    q = q / q.sum()
+    T = 20000
+    counts = np.zeros(len(k))
+    for t in range(T):
+        counts[O.energy_subset(w, 1, O.SplitMix64(t * 7919 + 1))[0]] += 1
+    expect = T * q
+    keep = expect >= 5
+    stat = float((((counts - expect) ** 2) / expect)[keep].sum()) + float(
+        ((counts[~keep].sum() - expect[~keep].sum()) ** 2) / max(expect[~keep].sum(), 1e-9))
+    assert chi2.sf(stat, keep.sum()) > 1e-4
+    a = O.select_indices(g, O.SEL_ENERGY, 6, True, 11)
+    assert np.all(np.diff(a, axis=1) > 0)
+    assert np.array_equal(a, O.select_indices(g, O.SEL_ENERGY, 6, True, 11))
+    assert len({tuple(r) for r in a}) > g.S // 2
+    b = O.select_indices(g, O.SEL_ENERGY, 6, False, 11)
+    assert np.all(b == b[0])
+    assert all(w[i] > 0 for i in a.ravel())
+
+
 def test_random_selection_reproducible_and_position_dependent():
     g = small_geom(Nx=8, Ny=8, Nt=256)
     a = O.select_indices(g, O.SEL_RANDOM, 8, True, 7)
