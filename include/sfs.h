@@ -322,6 +322,18 @@ int sfs_max_abs_AH(sfs_operator* op, const void* y_dev, double* out_host,
 int sfs_lipschitz(sfs_operator* op, int max_iter, double rtol, uint64_t seed,
                   double safety, double* L_out, void* stream);
 
+/*
+ * Frobenius norm and the sigma_max estimate of Sec. IV-C (host only, FP64,
+ * no device work).  Every entry of A has magnitude fs g(s, v) |H(f_k)|
+ * (Eq. (4)), so *fro2_out = ||A||_F^2 exactly:
+ * fs^2 sum_s sum_v g(s, v)^2 sum_m |H(f_{idx[s][m]})|^2.
+ * *sigma_hat_out (may be NULL) = ||A||_F / N^(1/4), N = min(S M, V): the
+ * geometric mean of the bounds ||A||_F / sqrt(N) <= sigma_max <= ||A||_F
+ * (Eq. (sigma_hat)).  The estimate is not guaranteed to bound sigma_max from
+ * above; sfs_lipschitz is the safe choice for FISTA's step.
+ */
+int sfs_frobenius(const sfs_operator* op, double* fro2_out, double* sigma_hat_out);
+
 /* Flags of sfs_fista */
 #define SFS_FISTA_WARM_START 1u   /* x_inout_dev holds x_0 on entry (else 0)  */
 #define SFS_FISTA_TIME_KERNELS 2u /* time the two contraction kernels          */

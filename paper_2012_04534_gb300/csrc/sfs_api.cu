@@ -1039,6 +1039,61 @@ int sfs_apply_AH(sfs_operator* op, const void* y_dev, void* x_dev, void* stream)
                     (cudaStream_t)stream);
 }
 
+int sfs_frobenius(const sfs_operator* op, double* fro2_out, double* sigma_hat_out) {
+  clear_error();
+  if (!op || !fro2_out) {
+    set_error("null argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  // |A[(s,m), v]| = fs g(s, v) |H(f_k)|, k = idx[s][m] (Eq. (4)), so
+  // ||A||_F^2 = fs^2 sum_s G(s) sum_m |H(f_{idx[s][m]})|^2 with
+  // G(s) = sum_v g(s, v)^2.  g depends on the lateral offset and the depth
+  // only; G(s) comes from 2-D prefix sums of g^2 over the offsets.
+  const sfs_geometry_desc& d = op->geo.d;
+  const int Nx = d.Nx, Ny = d.Ny, Nz = d.Nz;
+  std::vector<double> G((size_t)Nx * Ny, (double)Nx * Ny * Nz);
+  if (d.theta > 0) {
+    const int WX = 2 * Nx - 1, WY = 2 * Ny - 1;
+    std::fill(G.begin(), G.end(), 0.0);
+    std::vector<double> P((size_t)(WY + 1) * (WX + 1));
+    for (int iz = 0; iz < Nz; ++iz) {
+      const double z = d.z0 + iz * d.dz, w = z * tan(d.theta);
+      // P[j][i] = sum of g^2 over offsets (dy, dx) with dy < j - (Ny-1), dx < i - (Nx-1)
+      std::fill(P.begin(), P.end(), 0.0);
+      for (int j = 0; j < WY; ++j)
+        for (int i = 0; i < WX; ++i) {
+          const double rx = (i - (Nx - 1)) * d.dx, ry = (j - (Ny - 1)) * d.dy;
+          const double gv = exp(-(rx * rx + ry * ry) / (w * w));
+          P[(size_t)(j + 1) * (WX + 1) + i + 1] = gv * gv + P[(size_t)j * (WX + 1) + i + 1] +
+                                                  P[(size_t)(j + 1) * (WX + 1) + i] - P[(size_t)j * (WX + 1) + i];
+        }
+      for (int sy = 0; sy < Ny; ++sy)
+        for (int sx = 0; sx < Nx; ++sx) {
+          // voxel offsets v - s: dx in [-sx, Nx-1-sx], dy in [-sy, Ny-1-sy]
+          const int i0 = Nx - 1 - sx, i1 = i0 + Nx, j0 = Ny - 1 - sy, j1 = j0 + Ny;
+          G[(size_t)sy * Nx + sx] += P[(size_t)j1 * (WX + 1) + i1] - P[(size_t)j0 * (WX + 1) + i1] -
+                                     P[(size_t)j1 * (WX + 1) + i0] + P[(size_t)j0 * (WX + 1) + i0];
+        }
+    }
+  }
+  double fro2 = 0.0;
+  for (int s = 0; s < op->S; ++s) {
+    double h2 = 0.0;
+    for (int m = 0; m < op->M; ++m) {
+      const double h = pulse_mag((double)op->idx[(size_t)s * op->M + m] * d.fs / d.Nt, d.fc, op->geo.alpha);
+      h2 += h * h;
+    }
+    fro2 += G[s] * h2;
+  }
+  fro2 *= d.fs * d.fs;
+  *fro2_out = fro2;
+  // Eq. (sigma_hat) of Sec. IV-C: the geometric mean of the bounds
+  // ||A||_F / sqrt(N) <= sigma_max <= ||A||_F, N = min(S M, V) (rank bound)
+  const double N = std::min((double)op->S * op->M, (double)op->V);
+  if (sigma_hat_out) *sigma_hat_out = sqrt(fro2) / pow(N, 0.25);
+  return SFS_OK;
+}
+
 int sfs_max_abs_AH(sfs_operator* op, const void* y_dev, double* out_host, void* stream) {
   clear_error();
   if (!op || !y_dev || !out_host || !aligned16(y_dev)) {

@@ -59,7 +59,7 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_max_abs_AH", "sfs_apply_A_batched", "sfs_apply_AH_batched", "sfs_fista_batched",
            "sfs_lista_create", "sfs_lista_destroy", "sfs_lista_info", "sfs_lista_set_params",
            "sfs_lista_get_params", "sfs_lista_load_params_dev", "sfs_lista_forward",
-           "sfs_lista_backward", "sfs_lista_nmse", "sfs_lista_adam",
+           "sfs_lista_backward", "sfs_lista_nmse", "sfs_lista_adam", "sfs_frobenius",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
            "sfs_set_wait_timeout_ns",
            "sfs_inject_wait_timeout", "sfs_check_status", "sfs_last_error", "sfs_version")
@@ -123,6 +123,7 @@ def lib():
         "sfs_apply_AH": [vp, vp, vp, vp],
         "sfs_apply_AH_noalloc": [vp, vp, vp, vp],
         "sfs_max_abs_AH": [vp, vp, P(dbl), vp],
+        "sfs_frobenius": [vp, P(dbl), P(dbl)],
         "sfs_apply_A_batched": [vp, i32, vp, vp, vp],
         "sfs_apply_AH_batched": [vp, i32, vp, vp, vp],
         "sfs_fista_batched": [vp, i32, vp, dbl, dbl, i32, vp, vp],
@@ -397,6 +398,12 @@ class Operator:
                                        float(lam), float(L), int(iters),
                                        _dev_ptr(x, B * self.V, "x"), _stream_ptr(stream, y.device)))
         return x
+
+    def frobenius(self):
+        """(||A||_F^2, sigma_hat) of Sec. IV-C (host computation)."""
+        f, sh = ctypes.c_double(), ctypes.c_double()
+        _check(lib().sfs_frobenius(self.handle, ctypes.byref(f), ctypes.byref(sh)))
+        return f.value, sh.value
 
     def max_abs_AH(self, y, stream=None) -> float:
         return sfs_max_abs_AH(self.handle, _dev_ptr(y, self.S * self.M, "y"),

@@ -287,3 +287,19 @@ def test_invalid_arguments_on_gpu(sfs):
     bad = np.array([[5, 5, 6]] * 16, dtype=np.int32)
     with pytest.raises(sfs.SfsError):
         sfs.Operator.from_indices(g, bad)
+
+
+@pytest.mark.parametrize("theta_deg", [0.0, 25.0])
+def test_frobenius_norm_and_sigma_estimate(sfs, theta_deg):
+    """||A||_F^2 of Sec. IV-C from the closed-form magnitudes equals the dense
+    oracle's (1e-12), and the estimate ||A||_F / N^(1/4) lies between the
+    bounds ||A||_F / sqrt(N) <= sigma_max <= ||A||_F."""
+    params = geom_params(Nx=7, Ny=5, Nz=9, dz=0.2e-3, Nt=128, theta=math.radians(theta_deg))
+    g, op, go, idx = make_pair(sfs, params, M=6, seed=31)
+    A = O.dense_A(go, idx)
+    fro2, sigma_hat = op.frobenius()
+    assert fro2 == pytest.approx(float(np.linalg.norm(A) ** 2), rel=1e-12)
+    smax = float(np.linalg.svd(A, compute_uv=False)[0])
+    N = min(A.shape)
+    assert math.sqrt(fro2) / math.sqrt(N) <= smax * (1 + 1e-12) <= math.sqrt(fro2) * (1 + 1e-12)
+    assert sigma_hat == pytest.approx(math.sqrt(fro2) / N ** 0.25, rel=1e-12)
