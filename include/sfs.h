@@ -258,6 +258,24 @@ int sfs_fista_batched(sfs_operator* op, int batch, const void* y_dev, double lam
                       double L, int iters, void* x_out_dev, void* stream);
 
 /*
+ * Serving-style solve of scenes of different geometries: ngroups groups,
+ * group g = `batch[g]` scenes of operator ops[g] (distinct operators on one
+ * device), measurements y_dev[g] ([batch][S_g][M_g]), Lipschitz constant
+ * L[g], results x_out_dev[g] ([batch][V_g]).  The iteration loops of all
+ * groups run as one CUDA graph launch, one forked stream per group, so small
+ * groups share the GPU; lambda as in sfs_fista_batched (lambda < 0: mu rule
+ * per scene).  The graph is captured on the first call for a set of
+ * (operators, batch sizes, iterations) and replayed afterwards (a process-
+ * wide cache of 16 graphs, oldest evicted first).  1 <= ngroups <=
+ * SFS_MAX_GROUPS.  Errors: SFS_ERR_INVALID_ARG (also for an operator used
+ * by two groups), SFS_ERR_OOM, SFS_ERR_CUDA.
+ */
+#define SFS_MAX_GROUPS 64
+int sfs_fista_grouped(int ngroups, sfs_operator* const* ops, const int32_t* batch,
+                      const void* const* y_dev, const double* L, double lambda, int iters,
+                      void* const* x_out_dev, void* stream);
+
+/*
  * Learned unrolled ISTA (not in the paper, which reconstructs with
  * ISTA/FISTA, Sec. IV-A; the learned extension the workloads ask for).
  * Layer l keeps Algorithm 1's gradient step and complex soft threshold with

@@ -12,6 +12,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -482,6 +484,7 @@ int ensure_batch(sfs_operator* op, int batch) {
     return rc;
   }
   w.cap = batch;
+  ++op->bws_gen;
   return SFS_OK;
 }
 
@@ -580,6 +583,91 @@ int batched_scatter_y(sfs_operator* op, int batch, const float2* y, float2* ypla
 int operator_device(const sfs_operator* op) { return op->geo.d.device; }
 
 namespace {
+
+// One executable graph that runs the batched FISTA loops of several
+// operators concurrently (one forked stream per group, joined at the end).
+// Cached process-wide by (operator ids, workspace generations, batches,
+// iterations), at most kGroupedCache graphs, oldest evicted first.
+constexpr size_t kGroupedCache = 16;
+struct GroupedEntry {
+  std::vector<uint64_t> key;
+  cudaGraphExec_t exec;
+  int device;
+};
+std::mutex g_grouped_mu;
+std::vector<GroupedEntry> g_grouped;
+std::vector<cudaStream_t> g_fork_streams;
+std::vector<cudaEvent_t> g_fork_events;
+cudaStream_t g_grouped_capture = nullptr;
+
+int grouped_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch, int iters,
+                  cudaGraphExec_t* out) {
+  std::vector<uint64_t> key = {(uint64_t)iters, (uint64_t)ngroups};
+  for (int g = 0; g < ngroups; ++g) {
+    key.push_back(ops[g]->uid);
+    key.push_back(ops[g]->bws_gen);
+    key.push_back((uint64_t)batch[g]);
+  }
+  int dev = 0;
+  SFS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_grouped_mu);
+  for (auto& e : g_grouped)
+    if (e.key == key && e.device == dev) {
+      *out = e.exec;
+      return SFS_OK;
+    }
+  if (!g_grouped_capture) SFS_CUDA(cudaStreamCreateWithFlags(&g_grouped_capture, cudaStreamNonBlocking));
+  while ((int)g_fork_streams.size() < ngroups) {
+    cudaStream_t s2;
+    SFS_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    g_fork_streams.push_back(s2);
+  }
+  while ((int)g_fork_events.size() < ngroups + 1) {
+    cudaEvent_t e2;
+    SFS_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+    g_fork_events.push_back(e2);
+  }
+  for (int g = 0; g < ngroups; ++g) SFS_TRY(prepare_kernels(batch_dims(ops[g], batch[g])));
+  cudaStream_t cs = g_grouped_capture;
+  SFS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  int rc = SFS_OK;
+  cudaError_t e = cudaEventRecord(g_fork_events[ngroups], cs);
+  if (e != cudaSuccess) rc = cuda_fail(e, "fork event", __FILE__, __LINE__);
+  for (int g = 0; g < ngroups && rc == SFS_OK; ++g) {
+    cudaStream_t sg = g_fork_streams[g];
+    e = cudaStreamWaitEvent(sg, g_fork_events[ngroups], 0);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "fork wait", __FILE__, __LINE__);
+      break;
+    }
+    const sfs::BatchWorkspace& w = ops[g]->bws;
+    const FistaBufs b = {w.ybuf, w.yplane, w.Xh, w.Yh, w.Rh, w.Gh, w.xk, w.gam, w.scal};
+    rc = enqueue_fista_loop(ops[g], batch_dims(ops[g], batch[g]), b, iters, nullptr, false, sg);
+    if (rc == SFS_OK) {
+      e = cudaEventRecord(g_fork_events[g], sg);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, g_fork_events[g], 0);
+      if (e != cudaSuccess) rc = cuda_fail(e, "join", __FILE__, __LINE__);
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cs, &graph);
+  if (rc != SFS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+  if (g_grouped.size() >= kGroupedCache) {
+    cudaGraphExecDestroy(g_grouped.front().exec);
+    g_grouped.erase(g_grouped.begin());
+  }
+  g_grouped.push_back({key, exec, dev});
+  *out = exec;
+  return SFS_OK;
+}
 
 // Reads (and clears) the device timeout flag; call only where the stream is
 // synchronised anyway.
@@ -727,6 +815,10 @@ static int build_operator(sfs_geometry* g, int M, const int32_t* idx_host, int p
     return SFS_ERR_OOM;
   }
   op->geo = *g;
+  {
+    static std::atomic<uint64_t> next_uid{1};
+    op->uid = next_uid++;
+  }
   op->prec = prec;
   op->tc = prec == SFS_PREC_FP32 ? 0 : (prec == SFS_PREC_TF32X3 ? 1 : 2);
   op->nparts = prec == SFS_PREC_BF16X2 ? 2 : 1;
@@ -1390,6 +1482,63 @@ int sfs_fista_batched(sfs_operator* op, int batch, const void* y_dev, double lam
     SFS_CUDA(cudaGraphLaunch(exec, st));
   }
   SFS_CUDA(cudaMemcpyAsync(x_out_dev, w.xk, B * d.bs_x * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+  return SFS_OK;
+}
+
+int sfs_fista_grouped(int ngroups, sfs_operator* const* ops, const int32_t* batch,
+                      const void* const* y_dev, const double* L, double lambda, int iters,
+                      void* const* x_out_dev, void* stream) {
+  clear_error();
+  if (ngroups < 1 || ngroups > SFS_MAX_GROUPS || !ops || !batch || !y_dev || !L || !x_out_dev ||
+      iters < 0 || !isfinite(lambda)) {
+    set_error("invalid argument (1..%d groups)", SFS_MAX_GROUPS);
+    return SFS_ERR_INVALID_ARG;
+  }
+  for (int g = 0; g < ngroups; ++g) {
+    if (!ops[g] || batch[g] < 1 || batch[g] > SFS_MAX_BATCH || !(L[g] > 0) || !y_dev[g] || !x_out_dev[g] ||
+        !aligned16(y_dev[g]) || !aligned16(x_out_dev[g]) || ops[g]->geo.d.device != ops[0]->geo.d.device) {
+      set_error("invalid group %d (operator, batch 1..%d, L > 0, aligned buffers, one device)", g,
+                SFS_MAX_BATCH);
+      return SFS_ERR_INVALID_ARG;
+    }
+    for (int h = 0; h < g; ++h)
+      if (ops[h] == ops[g]) {
+        set_error("groups %d and %d share an operator (its batched workspace)", h, g);
+        return SFS_ERR_INVALID_ARG;
+      }
+  }
+  DeviceScope scope(ops[0]->geo.d.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  // per group: workspace, measurements, zero state, thresholds (mu rule per scene)
+  for (int g = 0; g < ngroups; ++g) SFS_TRY(ensure_batch(ops[g], batch[g]));
+  for (int g = 0; g < ngroups; ++g) {
+    sfs_operator* op = ops[g];
+    const PlaneDims d = batch_dims(op, batch[g]);
+    const sfs::BatchWorkspace& w = op->bws;
+    const size_t B = (size_t)batch[g];
+    SFS_CUDA(cudaMemcpyAsync(w.ybuf, y_dev[g], B * d.bs_y * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    SFS_CUDA(cudaMemsetAsync(w.xk, 0, B * d.bs_x * sizeof(float2), st));
+    SFS_CUDA(cudaMemsetAsync(w.gam, 0, B * d.bs_x * sizeof(float2), st));
+    SFS_CUDA(cudaMemsetAsync(w.scal, 0, B * kNumFloatScalars * sizeof(float), st));
+    const int use_mu = lambda < 0;
+    if (use_mu) {
+      SFS_TRY(launch_scatter_fwd(d, w.ybuf, op->posmap, w.Rh, st));
+      SFS_TRY(launch_contract_adj(d, op->table, w.Rh, w.Gh, op->ws.err, st));
+      SFS_TRY(launch_inv_store(d, w.Gh, op->ws.segslot, nullptr, nullptr, (unsigned int*)(w.scal + kLamMax), st));
+    }
+    SFS_TRY(launch_set_thresholds_batched(w.scal, batch[g], use_mu ? 0.0 : lambda, L[g], use_mu,
+                                          use_mu ? -lambda : 0.0, op->ws.err, st));
+  }
+  if (iters > 0) {
+    cudaGraphExec_t exec = nullptr;
+    SFS_TRY(grouped_graph(ngroups, ops, batch, iters, &exec));
+    SFS_CUDA(cudaGraphLaunch(exec, st));
+  }
+  for (int g = 0; g < ngroups; ++g) {
+    const PlaneDims d = batch_dims(ops[g], batch[g]);
+    SFS_CUDA(cudaMemcpyAsync(x_out_dev[g], ops[g]->bws.xk, (size_t)batch[g] * d.bs_x * sizeof(float2),
+                             cudaMemcpyDeviceToDevice, st));
+  }
   return SFS_OK;
 }
 

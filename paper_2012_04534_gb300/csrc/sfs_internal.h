@@ -149,6 +149,8 @@ struct sfs_operator {
   cudaStream_t capture_stream = nullptr;
   // batched FISTA: workspace and captured loops keyed by (iterations, scenes)
   sfs::BatchWorkspace bws;
+  uint64_t uid = 0;      // process-unique operator id (keys of grouped graphs)
+  uint64_t bws_gen = 0;  // bumped whenever the batched workspace is reallocated
   struct BatchGraphEntry {
     int iters;
     int batch;

@@ -43,6 +43,7 @@ PRECISION_NAMES = {"fp32": SFS_PREC_FP32, "tf32x3": SFS_PREC_TF32X3, "bf16": SFS
                    "bf16x2": SFS_PREC_BF16X2}
 
 SFS_MAX_BATCH = 256
+SFS_MAX_GROUPS = 64
 
 SFS_FISTA_WARM_START = 1
 SFS_FISTA_TIME_KERNELS = 2
@@ -60,6 +61,7 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_lista_create", "sfs_lista_destroy", "sfs_lista_info", "sfs_lista_set_params",
            "sfs_lista_get_params", "sfs_lista_load_params_dev", "sfs_lista_forward",
            "sfs_lista_backward", "sfs_lista_nmse", "sfs_lista_adam", "sfs_frobenius",
+           "sfs_fista_grouped",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
            "sfs_set_wait_timeout_ns",
            "sfs_inject_wait_timeout", "sfs_check_status", "sfs_last_error", "sfs_version")
@@ -124,6 +126,7 @@ def lib():
         "sfs_apply_AH_noalloc": [vp, vp, vp, vp],
         "sfs_max_abs_AH": [vp, vp, P(dbl), vp],
         "sfs_frobenius": [vp, P(dbl), P(dbl)],
+        "sfs_fista_grouped": [i32, P(vp), P(ctypes.c_int32), P(vp), P(dbl), dbl, i32, P(vp), vp],
         "sfs_apply_A_batched": [vp, i32, vp, vp, vp],
         "sfs_apply_AH_batched": [vp, i32, vp, vp, vp],
         "sfs_fista_batched": [vp, i32, vp, dbl, dbl, i32, vp, vp],
@@ -298,6 +301,26 @@ def sfs_version() -> str:
 
 
 # --------------------------------------------------------------- wrappers ---
+
+def fista_grouped(ops, ys, Ls, lam, iters, xs=None, stream=None):
+    """sfs_fista_grouped: ops[g] solves the scenes ys[g] ([batch, S, M]
+    complex64 CUDA tensors) with Lipschitz constant Ls[g]; returns the list
+    of [batch, Nz, Ny, Nx] results."""
+    import torch
+    n = len(ops)
+    if xs is None:
+        xs = [torch.empty((int(y.shape[0]),) + op.shape_x, dtype=torch.complex64, device=y.device)
+              for op, y in zip(ops, ys)]
+    VP = ctypes.c_void_p * n
+    oph = VP(*[op.handle for op in ops])
+    b = (ctypes.c_int32 * n)(*[int(y.shape[0]) for y in ys])
+    yp = VP(*[_dev_ptr(y, int(y.shape[0]) * op.S * op.M, "y") for op, y in zip(ops, ys)])
+    xp = VP(*[_dev_ptr(x, int(x.shape[0]) * op.V, "x") for op, x in zip(ops, xs)])
+    Lv = (ctypes.c_double * n)(*[float(v) for v in Ls])
+    _check(lib().sfs_fista_grouped(n, oph, b, yp, Lv, float(lam), int(iters), xp,
+                                   _stream_ptr(stream, ys[0].device)))
+    return xs
+
 
 class Geometry:
     """Scan / voxel grid and pulse (sfs_geometry_desc)."""

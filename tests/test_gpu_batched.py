@@ -142,3 +142,35 @@ def test_batched_invalid_arguments(sfs):
                                ctypes.c_void_p(x.data_ptr()), None) == sfs.SFS_ERR_INVALID_ARG
     with pytest.raises(ValueError):
         op.apply_A_batched(x[:, :, :, :2].contiguous())
+
+
+def test_grouped_solve_equals_per_operator_batched_solves(sfs):
+    """Three geometries (a line scan and two area scans, FP32 and BF16
+    contractions) solved by one sfs_fista_grouped call: every scene equals the
+    operator's own batched solve; a second call replays the cached graph."""
+    import torch
+    specs = [(dict(Nx=24, Ny=1, Nz=40, Nt=256), 12, 2, "fp32"),
+             (dict(Nx=10, Ny=8, Nz=20, Nt=128), 10, 3, "bf16"),
+             (dict(Nx=12, Ny=12, Nz=33, Nt=256), 16, 1, "fp32")]
+    ops, ys, Ls = [], [], []
+    rng = np.random.default_rng(41)
+    for k, (geo, M, B, mode) in enumerate(specs):
+        params = geom_params(dz=0.15e-3, **geo)
+        go = oracle_geometry(params)
+        idx = O.select_indices(go, O.SEL_RANDOM, M, True, 60 + k)
+        g = sfs.Geometry(**params)
+        op = sfs.Operator.from_indices(g, idx, precision=sfs.PRECISION_NAMES[mode])
+        op._geom = g
+        L, _ = op.lipschitz(max_iter=200, rtol=1e-6, seed=1, safety=1e-3)
+        ops.append(op)
+        Ls.append(L)
+        ys.append(to_dev(crandn(rng, B, op.S, M)))
+    xs = sfs.fista_grouped(ops, ys, Ls, -0.05, 25)
+    for op, y, L, x in zip(ops, ys, Ls, xs):
+        ref = to_host(op.fista_batched(y, -0.05, L, 25))
+        assert rel_err(to_host(x), ref) <= 1e-6
+    xs2 = sfs.fista_grouped(ops, ys, Ls, -0.05, 25)
+    for a, b in zip(xs, xs2):
+        assert torch.equal(a, b)
+    with pytest.raises(sfs.SfsError):
+        sfs.fista_grouped([ops[0], ops[0]], [ys[0], ys[0]], [Ls[0], Ls[0]], -0.05, 5)
