@@ -53,6 +53,8 @@ def parse():
                     help="skip the BF16 / BF16X2 vs FP32 time-to-same-NMSE study")
     ap.add_argument("--batch-scenes", type=int, default=16,
                     help="scenes of the batched-serving measurement (0 skips it)")
+    ap.add_argument("--serving-scenes", type=int, default=256,
+                    help="scenes of the mixed-geometry serving measurement (0 skips it)")
     ap.add_argument("--learned-steps", type=int, default=400,
                     help="training steps of the learned unrolled ISTA measurement on the vol32 "
                          "workload (0 skips it)")
@@ -173,6 +175,60 @@ def batched_study(sfs, torch, geom, op, args, w, iters, L, flush, stream, seed):
                               # (16-bit) or per scene (FP32), forward and adjoint
                               "launches_per_iter": 2 + 2 * (B if mode == "fp32" else -(-B // 4))}
     return out
+
+
+def serving_study(sfs, torch, args, flush, stream, seed):
+    """args.serving_scenes scenes of the SERVING mix (36 geometry classes),
+    one BF16 operator per class present (L by 60 power iterations), all
+    solved by one sfs_fista_grouped call of 200 iterations (lambda by the mu
+    rule per scene).  Reports aggregate scene-iterations/s over 3 timed
+    solves (L2 flushed first) and the solve latency, which every scene
+    shares; setup (tables, L) is timed apart."""
+    sv = synth.SERVING
+    classes = synth.serving_classes()
+    draw = synth.serving_draw(args.serving_scenes, seed + 555)
+    t0 = time.perf_counter()
+    ops, ys, Ls, counts = [], [], [], []
+    for c in sorted(set(draw.tolist())):
+        n = int((draw == c).sum())
+        g = sfs.Geometry(**dict(synth.serving_params(classes[c]), device=torch.cuda.current_device()))
+        op = sfs.Operator.select(g, sfs.SFS_SEL_RANDOM, classes[c][2], True, seed + c,
+                                 precision=sfs.SFS_PREC_BF16)
+        op._geom = g
+        L, _ = op.lipschitz(max_iter=60, rtol=1e-4, seed=seed, safety=1e-2)
+        xt = torch.from_numpy(np.stack([synth.scene(op.shape_x, sv["n_scatter"], "uniform", seed=seed + 1000 * c + b)
+                                        for b in range(n)]).astype(np.complex64)).cuda()
+        y0 = op.apply_A_batched(xt).cpu().numpy().astype(np.complex128)
+        yb = []
+        for b in range(n):
+            sig = synth.noise_scale(float(np.vdot(y0[b], y0[b]).real), y0[b].size, sv["snr_db"])
+            yb.append(y0[b] + sig * synth.unit_noise(y0[b].shape, seed=seed + 2000 * c + b))
+        ops.append(op)
+        Ls.append(L)
+        counts.append(n)
+        ys.append(torch.from_numpy(np.stack(yb).astype(np.complex64)).cuda())
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    iters = sv["iters"]
+    xs = sfs.fista_grouped(ops, ys, Ls, -0.05, iters)  # workspaces and graph capture
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(3):
+        flush.fill_(3)
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sfs.fista_grouped(ops, ys, Ls, -0.05, iters, xs=xs)
+        b2.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b2))
+    ts.sort()
+    total = sum(counts)
+    return {"scenes": total, "classes": len(ops), "iters": iters, "precision": "bf16",
+            "unit": "scene-iterations/s", "value": total * iters / (statistics.mean(ts) / 1e3),
+            "latency_ms_p50": statistics.median(ts), "latency_ms_p99": ts[-1],
+            "latency_note": "one graph launch solves every scene; each scene's latency is the launch's",
+            "setup_s": t_setup,
+            "mix": "grids {16,32,48,64}^2, depths {64,128,256}, M {32,64,128}, 10 scatterers, 20 dB"}
 
 
 def learned_study(sfs, torch, op, args, w, L, stream, seed):
@@ -602,6 +658,11 @@ def main():
     if rank == 0 and world == 1 and args.batch_scenes > 0:
         batched = batched_study(sfs, torch, geom, op, args, w, iters, L, flush, stream, seed)
 
+    # ---- serving mix: scenes of many geometries in one grouped graph launch ----
+    serving = None
+    if rank == 0 and world == 1 and args.serving_scenes > 0:
+        serving = serving_study(sfs, torch, args, flush, stream, seed)
+
     # ---- learned unrolled ISTA vs FISTA, time to the same NMSE ----
     learned = None
     if rank == 0 and world == 1 and args.learned_steps > 0 and args.workload == synth.LEARNED["workload"]:
@@ -648,6 +709,8 @@ def main():
             line["batched"] = batched
         if learned is not None:
             line["learned"] = learned
+        if serving is not None:
+            line["serving"] = serving
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

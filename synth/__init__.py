@@ -48,6 +48,39 @@ GEOM_KEYS = ("Nx", "Ny", "dx", "dy", "Nz", "z0", "dz", "c", "fs", "Nt", "fc",
 LEARNED = dict(workload="vol32", layers=16, n_scatter=(1, 20), snr_db=(10.0, 30.0), amp="uniform")
 
 
+# Serving mix: scenes of independent geometries, each drawn uniformly from
+# scan grids {16, 32, 48, 64}^2, depths {64, 128, 256} and M {32, 64, 128}
+# (0.5 mm pitch, 0.15 mm depth pitch from 10 mm); Nt is the larger of the
+# record length that the line2d / vol32 / vol64 workloads pair with M
+# (256 for 32 bins, 512 for 64, 1024 for 128) and the one they pair with the
+# depth count (256 for 64 depths, 512 for 128, 1024 for 256).  Scenes: 10
+# scatterers, U(0.5, 1) magnitudes and uniform phase, 20 dB SNR.
+SERVING = dict(grids=(16, 32, 48, 64), depths=(64, 128, 256), Ms=(32, 64, 128), n_scatter=10,
+               snr_db=20.0, iters=200)
+
+
+def serving_classes():
+    """All (grid, depth, M, Nt) classes of the serving mix."""
+    out = []
+    for n in SERVING["grids"]:
+        for nz in SERVING["depths"]:
+            for M in SERVING["Ms"]:
+                nt = max({32: 256, 64: 512, 128: 1024}[M], {64: 256, 128: 512, 256: 1024}[nz])
+                out.append((n, nz, M, nt))
+    return out
+
+
+def serving_params(cls):
+    n, nz, M, nt = cls
+    return dict(BASE, Nx=n, Ny=n, Nz=nz, dz=0.15e-3, Nt=nt)
+
+
+def serving_draw(count, seed):
+    """Class index of each of `count` scenes (uniform over the classes)."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, len(serving_classes()), count)
+
+
 def learned_draw(shape, seed):
     """One training / evaluation scene of the LEARNED recipe: (x, snr_db)."""
     rng = np.random.default_rng(seed + 7777)
