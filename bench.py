@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--workload", default="vol32", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--strategy", default="random", choices=sorted(STRATEGY_NAMES))
     ap.add_argument("--precision", default="fp32",
-                    choices=["fp32", "tf32x3", "bf16", "bf16x2"],
+                    choices=["fp32", "tf32x3", "bf16", "bf16x2", "fp16", "fp16x2"],
                     help="arithmetic of the depth contractions (sfs_precision)")
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
@@ -67,11 +67,16 @@ def parse():
 DTYPE_OF = {"fp32": "c64 (f32)",
             "tf32x3": "c64 (f32 state; contractions tf32 hi/lo x3 on tensor cores, f32 accumulate)",
             "bf16": "c64 (f32 state; contractions bf16 table x bf16 hi/lo spectra, f32 accumulate)",
-            "bf16x2": "c64 (f32 state; contractions bf16 hi/lo table x bf16 hi/lo spectra, f32 accumulate)"}
+            "bf16x2": "c64 (f32 state; contractions bf16 hi/lo table x bf16 hi/lo spectra, f32 accumulate)",
+            "fp16": "c64 (f32 state; contractions fp16 table x fp16 hi/lo spectra, power-of-2 scaled, "
+                    "f32 accumulate)",
+            "fp16x2": "c64 (f32 state; contractions fp16 hi/lo table x fp16 hi/lo spectra, power-of-2 scaled, "
+                      "f32 accumulate)"}
+REDUCED = ("bf16", "bf16x2", "fp16", "fp16x2")
 
 
 def precision_study(sfs, torch, geom, op, args, w, iters, y, L, x_true, flush, stream):
-    """FISTA with the FP32 contractions against the BF16 and BF16X2 ones on the
+    """FISTA with the FP32 contractions against the 16-bit ones on the
     same scene, measurements, lambda rule and L: per mode the device time of
     one solve (L2 flushed first), the NMSE against the true scene, and the
     iterations and time a reduced-precision solve needs to reach the FP32
@@ -80,7 +85,7 @@ def precision_study(sfs, torch, geom, op, args, w, iters, y, L, x_true, flush, s
     (which itself matches the FP64 oracle to about 1e-6 in the tests)."""
     xt = torch.from_numpy(x_true.astype(np.complex64)).cuda()
     ops = {}
-    for mode in ("fp32", "bf16", "bf16x2"):
+    for mode in ("fp32",) + REDUCED:
         ops[mode] = op if args.precision == mode else sfs.Operator.from_indices(
             geom, op.idx, precision=sfs.PRECISION_NAMES[mode])
 
@@ -110,7 +115,7 @@ def precision_study(sfs, torch, geom, op, args, w, iters, y, L, x_true, flush, s
            "timing": "device time of one solve (lambda rule + iterations), best of 3, L2 flushed first",
            "modes": {"fp32": {"ms_per_solve": t32, "nmse_db": target,
                               "table_bytes": ops["fp32"].info["table_bytes"]}}}
-    for mode in ("bf16", "bf16x2"):
+    for mode in REDUCED:
         o = ops[mode]
         axm = o.apply_A(xt).cpu().numpy().astype(np.complex128)
         tk, xk = solve(o, iters)
@@ -152,7 +157,7 @@ def batched_study(sfs, torch, geom, op, args, w, iters, L, flush, stream, seed):
            "timing": "device time of one batched solve (lambda rule + iterations), 5 solves, "
                      "L2 flushed before each; latency = solve time (all scenes finish together)",
            "modes": {}}
-    for mode in ("fp32", "bf16x2", "bf16"):
+    for mode in ("fp32",) + REDUCED:
         o = op if args.precision == mode else sfs.Operator.from_indices(
             geom, op.idx, precision=sfs.PRECISION_NAMES[mode])
         x = torch.empty((B,) + o.shape_x, dtype=torch.complex64, device="cuda")

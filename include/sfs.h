@@ -96,12 +96,27 @@ typedef struct sfs_geometry_desc {
  *                    BF16 hi + lo; relative error of A x about u.
  *   SFS_PREC_BF16X2  tensor cores (kind::f16): table stored as BF16 hi + lo
  *                    (u about 2^-16, the bytes of FP32), spectra hi + lo.
+ *   SFS_PREC_FP16    tensor cores (kind::f16, FP16 operands): table rounded
+ *                    to FP16 (u = 2^-11, the bytes of BF16), spectra split
+ *                    into FP16 hi + lo.  FP16 spans only 2^-24 .. 65504, so
+ *                    both operands are scaled by powers of two, which are
+ *                    exact and undone in the FP32 epilogue: the table by
+ *                    2^kT with kT fixed at build from a bound on its
+ *                    magnitude, each scene's spectra by 2^ks with ks taken
+ *                    from the largest |Re| or |Im| of that scene's spectra
+ *                    (the kernels that write the spectra record the maximum
+ *                    per plane).  The result does not depend on the scale
+ *                    of the input, from about 2^-100 to 2^100.
+ *   SFS_PREC_FP16X2  as SFS_PREC_FP16 with the table stored as FP16 hi + lo
+ *                    (u about 2^-22, the bytes of FP32).
  */
 typedef enum sfs_precision {
   SFS_PREC_FP32 = 0,
   SFS_PREC_TF32X3 = 1,
   SFS_PREC_BF16 = 2,
-  SFS_PREC_BF16X2 = 3
+  SFS_PREC_BF16X2 = 3,
+  SFS_PREC_FP16 = 4,
+  SFS_PREC_FP16X2 = 5
 } sfs_precision;
 
 typedef struct sfs_geometry sfs_geometry;  /* opaque, library owned */

@@ -263,6 +263,8 @@ void free_batch(sfs_operator* op) {
   cudaFree(w.yplane);
   cudaFree(w.ybuf);
   cudaFree(w.scal);
+  cudaFree(w.pmx);
+  cudaFree(w.pmr);
   w = sfs::BatchWorkspace();
 }
 
@@ -286,6 +288,8 @@ void free_operator(sfs_operator* op) {
   cudaFree(op->ws.scal);
   cudaFree(op->ws.red);
   cudaFree(op->ws.obj);
+  cudaFree(op->ws.pmx);
+  cudaFree(op->ws.pmr);
   for (cudaEvent_t e : op->ev) cudaEventDestroy(e);
   for (auto& ge : op->graphs) cudaGraphExecDestroy(ge.exec);
   if (op->capture_stream) cudaStreamDestroy(op->capture_stream);
@@ -317,6 +321,13 @@ PlaneDims operator_dims(const sfs_operator* op) {
   d.prec = op->prec;
   d.nkb = op->nkb;
   d.nparts = op->nparts;
+  d.f16 = op->f16;
+  d.tscale = ldexpf(1.0f, op->tscale_exp);
+  d.tinv = ldexpf(1.0f, -op->tscale_exp);
+  d.pm_x = op->f16 ? op->ws.pmx : nullptr;
+  d.pm_r = op->f16 ? op->ws.pmr : nullptr;
+  d.bs_pmx = op->geo.d.Nz;
+  d.bs_pmr = op->Up;
   d.tmaps = op->tmaps;
   d.adj_seg = op->adj_seg;
   d.azb = op->azb;
@@ -452,6 +463,8 @@ int enqueue_fista_iterations(sfs_operator* op, int iters, double* obj, bool timi
 PlaneDims batch_dims(const sfs_operator* op, int batch) {
   PlaneDims d = dims_of(op);
   d.batch = batch;
+  d.pm_x = op->f16 ? op->bws.pmx : nullptr;
+  d.pm_r = op->f16 ? op->bws.pmr : nullptr;
   return d;
 }
 
@@ -473,6 +486,8 @@ int ensure_batch(sfs_operator* op, int batch) {
   if (rc == SFS_OK) rc = dev_alloc(&w.yplane, B * d.bs_yplane);
   if (rc == SFS_OK) rc = dev_alloc(&w.ybuf, B * d.bs_y);
   if (rc == SFS_OK) rc = dev_alloc(&w.scal, B * kNumFloatScalars);
+  if (rc == SFS_OK && op->f16) rc = dev_alloc(&w.pmx, B * d.bs_pmx);
+  if (rc == SFS_OK && op->f16) rc = dev_alloc(&w.pmr, B * d.bs_pmr);
   if (rc == SFS_OK) {
     // spectra rows of the padding bins U..Up-1 are read by the contractions
     // and never written
@@ -821,7 +836,8 @@ static int build_operator(sfs_geometry* g, int M, const int32_t* idx_host, int p
   }
   op->prec = prec;
   op->tc = prec == SFS_PREC_FP32 ? 0 : (prec == SFS_PREC_TF32X3 ? 1 : 2);
-  op->nparts = prec == SFS_PREC_BF16X2 ? 2 : 1;
+  op->nparts = (prec == SFS_PREC_BF16X2 || prec == SFS_PREC_FP16X2) ? 2 : 1;
+  op->f16 = (prec == SFS_PREC_FP16 || prec == SFS_PREC_FP16X2) ? 1 : 0;
   op->M = M;
   op->S = S;
   op->V = S * d.Nz;
@@ -912,6 +928,26 @@ static int build_operator(sfs_geometry* g, int M, const int32_t* idx_host, int p
   for (int u = 0; u < op->U; ++u)
     amp[u] = (float)(d.fs * pulse_mag((double)op->bins[u] * d.fs / d.Nt, d.fc, g->alpha) /
                      ((double)g->Px * g->Py));
+  if (op->f16) {
+    // FP16 table: every entry of FFT2(h_{k,z}) / (Px Py) is at most the sum
+    // of the plane's tap magnitudes, amp[u] * sum over (+-dx, +-dy) of g; the
+    // stored table is scaled by 2^kT so that this bound lies in [2^13, 2^14)
+    // (FP16 holds up to 65504), kT clamped to +-126.
+    double gsum = 0.0;
+    for (int iz = 0; iz < d.Nz; ++iz) {
+      double acc = 0.0;
+      for (int ay = 0; ay < d.Ny; ++ay)
+        for (int ax = 0; ax < d.Nx; ++ax)
+          acc += (ax ? 2.0 : 1.0) * (ay ? 2.0 : 1.0) * gdir[((size_t)iz * d.Ny + ay) * d.Nx + ax];
+      gsum = std::max(gsum, acc);
+    }
+    double amax = 0.0;
+    for (int u = 0; u < op->U; ++u) amax = std::max(amax, (double)fabsf(amp[u]));
+    const double bound = amax * gsum;
+    op->tscale_exp = bound > 0.0 && isfinite(bound)
+                         ? std::min(126, std::max(-126, 13 - (int)floor(log2(bound))))
+                         : 0;
+  }
   std::vector<int32_t> posmap((size_t)op->U * S, -1);
   for (int s = 0; s < S; ++s)
     for (int m = 0; m < M; ++m) posmap[(size_t)u_of[op->idx[(size_t)s * M + m]] * S + s] = m;
@@ -991,6 +1027,8 @@ static int build_operator(sfs_geometry* g, int M, const int32_t* idx_host, int p
   if ((rc = dev_alloc(&op->ws.vbuf, (size_t)S * M)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.scal, kNumFloatScalars)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.red, kNumRed)) != SFS_OK) return fail(rc);
+  if (op->f16 && (rc = dev_alloc(&op->ws.pmx, (size_t)d.Nz)) != SFS_OK) return fail(rc);
+  if (op->f16 && (rc = dev_alloc(&op->ws.pmr, (size_t)op->Up)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&d_tof, nt)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&d_gdir, nt)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&d_amp, (size_t)op->U)) != SFS_OK) return fail(rc);
@@ -1046,7 +1084,7 @@ int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
 int sfs_operator_from_indices_prec(sfs_geometry* g, int M, const int32_t* idx_host,
                                    int precision, sfs_operator** out) {
   clear_error();
-  if (precision < SFS_PREC_FP32 || precision > SFS_PREC_BF16X2) {
+  if (precision < SFS_PREC_FP32 || precision > SFS_PREC_FP16X2) {
     set_error("unknown precision %d", precision);
     return SFS_ERR_INVALID_ARG;
   }

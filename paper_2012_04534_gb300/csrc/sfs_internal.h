@@ -67,6 +67,8 @@ struct BatchWorkspace {
   float2* yplane = nullptr;  // [cap][U][S]
   float2* ybuf = nullptr;    // [cap][S][M] measurements copy
   float* scal = nullptr;     // [cap][kNumFloatScalars]
+  float* pmx = nullptr;      // [cap][Nz] FP16 modes: max |Re|, |Im| of each X^ plane
+  float* pmr = nullptr;      // [cap][Up] FP16 modes: the same of each R^ plane
 };
 
 struct Workspace {
@@ -84,6 +86,8 @@ struct Workspace {
   float2* vbuf = nullptr;   // [S][M] scratch (power iteration)
   float* scal = nullptr;    // kNumFloatScalars floats
   double* red = nullptr;    // kNumRed doubles
+  float* pmx = nullptr;     // [Nz] FP16 modes: max |Re|, |Im| of each X^ plane
+  float* pmr = nullptr;     // [Up] FP16 modes: the same of each R^ plane
   double* obj = nullptr;    // [2 * obj_cap] objective monitor sums
   int obj_cap = 0;
 };
@@ -115,6 +119,8 @@ struct sfs_operator {
   int nzc = 0;                 // depth blocks of 16 in the tf32 tensor-core table
   int nkb = 0;                 // depth blocks of 32 in the 16-bit table
   int nparts = 1;              // 16-bit table parts: 1 (value) or 2 (hi, lo)
+  int f16 = 0;                 // 16-bit table and spectra operands in FP16 (else BF16)
+  int tscale_exp = 0;          // FP16 modes: the table is stored times 2^tscale_exp
   sfs::TcMaps* tmaps = nullptr;  // tensor maps of the 16-bit contractions
   int nzb = 1;                 // depth blocks of <= 128 in the contractions
   int G = 1;                   // persistent CTAs of the contractions
@@ -176,6 +182,17 @@ struct PlaneDims {
   int prec;    // sfs_precision
   int nkb;     // depth blocks of 32 of the 16-bit table
   int nparts;  // parts of the 16-bit table (1 or 2)
+  int f16;     // 16-bit operands are FP16 (scaled by powers of two), else BF16
+  float tscale;  // FP16 modes: scale 2^kT of the stored table (1 otherwise)
+  float tinv;    // 2^-kT
+  // FP16 modes: per-plane maxima of max(|Re|, |Im|) of the spectra, written by
+  // the kernels that store X^ (pm_x, [batch][Nz]) and R^ (pm_r, [batch][Up]);
+  // null otherwise.  The 16-bit contractions scale each scene's spectra by
+  // the power of two that brings its largest value just below 2^14.
+  float* pm_x;
+  float* pm_r;
+  long long bs_pmx;  // per-scene strides of pm_x (Nz) and pm_r (Up)
+  long long bs_pmr;
   TcMaps* tmaps;  // host pointer: tensor maps of the 16-bit contractions
   int adj_seg;  // adjoint by segment-aligned CTAs (dense result) instead of partial sums
   int azb;      // depth rows per adjoint segment (32 segment-aligned, 128 otherwise)

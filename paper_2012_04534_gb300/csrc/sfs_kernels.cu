@@ -15,6 +15,7 @@
 // The two contractions stream T and dominate the run time; everything else
 // works on single planes held in shared memory.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -75,6 +76,24 @@ __device__ __forceinline__ void block_max_bits(float v, unsigned int* out) {
   }
 }
 
+// Block maximum of non-negative v, stored by thread 0 (fmaxf: a NaN input is
+// ignored here; it still reaches the output through the values themselves).
+template <int NT>
+__device__ __forceinline__ void block_max_store(float v, float* out) {
+  __shared__ float part[NT / 32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) part[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < NT / 32 ? part[lane] : 0.0f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if (lane == 0) *out = v;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Generator table: T[kt][u][z][ki] = FFT2(h_{bins[u], z}) / (Px Py)
 // ---------------------------------------------------------------------------
@@ -129,20 +148,28 @@ build_table_kernel(PlaneDims d, const float2* __restrict__ tof,
   // The 16-bit tensor-core contractions (sfs_tc16.cu) use rows of 64 values
   // T16[part][o][z/32][u][2 (z%32) + {0: re, 1: im}]: part 0 holds the BF16
   // rounding of the FP32 value v, part 1 (two-part tables) the BF16 rounding
-  // of v - part 0.
+  // of v - part 0.  FP16 tables round v 2^kT (d.tscale) the same way.
   if (d.tc == 2) {
     const int No = d.Ns / d.GS;
-    __nv_bfloat162* t16 = (__nv_bfloat162*)table;
     for (int o = threadIdx.x; o < No; o += F::NT) {
       const int rep = d.orbit_rep[o];
-      const float2 v = rep >= 0 ? buf[F::kidx(rep)] : make_float2(0.f, 0.f);
-      const __nv_bfloat162 hi = __floats2bfloat162_rn(v.x, v.y);
+      float2 v = rep >= 0 ? buf[F::kidx(rep)] : make_float2(0.f, 0.f);
       const size_t row = ((size_t)o * d.nkb + (z >> 5)) * d.U + u;
-      t16[row * 32 + (z & 31)] = hi;
-      if (d.nparts == 2) {
-        const float2 r = make_float2(v.x - __low2float(hi), v.y - __high2float(hi));
-        const size_t row1 = (((size_t)No + o) * d.nkb + (z >> 5)) * d.U + u;
-        t16[row1 * 32 + (z & 31)] = __floats2bfloat162_rn(r.x, r.y);
+      const size_t row1 = (((size_t)No + o) * d.nkb + (z >> 5)) * d.U + u;
+      if (d.f16) {
+        v = make_float2(v.x * d.tscale, v.y * d.tscale);
+        __half2* t16 = (__half2*)table;
+        const __half2 hi = __floats2half2_rn(v.x, v.y);
+        t16[row * 32 + (z & 31)] = hi;
+        if (d.nparts == 2)
+          t16[row1 * 32 + (z & 31)] = __floats2half2_rn(v.x - __low2float(hi), v.y - __high2float(hi));
+      } else {
+        __nv_bfloat162* t16 = (__nv_bfloat162*)table;
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(v.x, v.y);
+        t16[row * 32 + (z & 31)] = hi;
+        if (d.nparts == 2)
+          t16[row1 * 32 + (z & 31)] =
+              __floats2bfloat162_rn(v.x - __low2float(hi), v.y - __high2float(hi));
       }
     }
     return;
@@ -257,11 +284,14 @@ __device__ __forceinline__ void load_spectrum_adj(float2* buf, const float2* __r
   }
 }
 
+// Stores the plane's spectrum in slot order; with pm (FP16 modes) also the
+// plane's largest |Re| or |Im| at *pm (every thread of the CTA must call).
 template <int P, bool TWO_D>
 __device__ __forceinline__ void store_spectrum(const float2* buf, float2* __restrict__ dst,
-                                               const PlaneDims& d) {
+                                               const PlaneDims& d, float* pm = nullptr) {
   using F = PlaneFFT<P, TWO_D>;
   constexpr int LB = load_batch<P, TWO_D>();
+  float mx = 0.0f;
   for (int j0 = threadIdx.x; j0 < d.Ns; j0 += LB * F::NT) {
     int kap[LB];
 #pragma unroll
@@ -272,9 +302,14 @@ __device__ __forceinline__ void store_spectrum(const float2* buf, float2* __rest
 #pragma unroll
     for (int k = 0; k < LB; ++k) {
       const int j = j0 + k * F::NT;
-      if (j < d.Ns) dst[j] = kap[k] >= 0 ? buf[F::kidx(kap[k])] : make_float2(0.f, 0.f);
+      if (j < d.Ns) {
+        const float2 v = kap[k] >= 0 ? buf[F::kidx(kap[k])] : make_float2(0.f, 0.f);
+        dst[j] = v;
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+      }
     }
   }
+  if (pm) block_max_store<F::NT>(mx, pm);
 }
 
 // Zero every slot of the plane outside the Ny x Nx crop window.
@@ -312,7 +347,8 @@ fwd_planes_kernel(PlaneDims d, const float2* __restrict__ x, float2* __restrict_
     buf[F::sidx(e / d.Nx, e % d.Nx)] = xz[e];
   __syncthreads();
   F::forward(buf, tw, d.Nx);
-  store_spectrum<P, TWO_D>(buf, Xh + (size_t)z * d.Ns, d);
+  store_spectrum<P, TWO_D>(buf, Xh + (size_t)z * d.Ns, d,
+                           d.pm_x ? d.pm_x + blockIdx.y * d.bs_pmx + z : nullptr);
 }
 
 // Yh[u] -> y[s, m] = IFFT2(Yh_u)(s) where bins[u] = idx[s, m]
@@ -395,7 +431,8 @@ inv_resid_fwd_kernel(PlaneDims d, const float2* __restrict__ Yh,
   if (red_sumsq) block_add_double<F::NT>(acc, red_sumsq);
   __syncthreads();
   F::forward(buf, tw, d.Nx);
-  store_spectrum<P, TWO_D>(buf, Rh + (size_t)u * d.Ns, d);
+  store_spectrum<P, TWO_D>(buf, Rh + (size_t)u * d.Ns, d,
+                           d.pm_r ? d.pm_r + blockIdx.y * d.bs_pmr + u : nullptr);
 }
 
 // y[s, m] scattered to bin plane u -> Rh[u] = FFT2(pad(.))
@@ -425,7 +462,8 @@ scatter_fwd_kernel(PlaneDims d, const float2* __restrict__ y,
   }
   __syncthreads();
   F::forward(buf, tw, d.Nx);
-  store_spectrum<P, TWO_D>(buf, Rh + (size_t)u * d.Ns, d);
+  store_spectrum<P, TWO_D>(buf, Rh + (size_t)u * d.Ns, d,
+                           d.pm_r ? d.pm_r + blockIdx.y * d.bs_pmr + u : nullptr);
 }
 
 // Gh[z] -> x plane z = crop(IFFT2(Gh_z)); optional sum |x|^2 and max |x|.
@@ -521,7 +559,8 @@ inv_fista_fwd_kernel(PlaneDims d, const float2* __restrict__ Gh,
   zero_outside<P, TWO_D>(buf, d.Ny, d.Nx);
   __syncthreads();
   F::forward(buf, tw, d.Nx);
-  store_spectrum<P, TWO_D>(buf, Xh + (size_t)z * d.Ns, d);
+  store_spectrum<P, TWO_D>(buf, Xh + (size_t)z * d.Ns, d,
+                           d.pm_x ? d.pm_x + blockIdx.y * d.bs_pmx + z : nullptr);
 }
 
 // ---------------------------------------------------------------------------

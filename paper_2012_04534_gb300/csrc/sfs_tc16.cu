@@ -1,5 +1,5 @@
 // Depth contractions on the tensor cores from a 16-bit table (tcgen05
-// kind::f16, BF16 operands, FP32 accumulation in tensor memory).
+// kind::f16, BF16 or FP16 operands, FP32 accumulation in tensor memory).
 //
 // The generator table holds one entry per symmetry orbit of wavenumbers
 // (the lateral kernel depends on dx^2 + dy^2 only, Eq. (3)), so both
@@ -26,6 +26,12 @@
 // hi and lo = the BF16 rounding of (value - hi); both are stacked along N
 // (N = 32) and summed in the epilogue, so the spectra keep about 16
 // significant bits and the table's rounding dominates the error.
+// FP16 operands (11 significant bits, but only 2^-24 .. 65504) are scaled by
+// powers of two: the table by 2^kT at build, each scene's spectra by 2^ks
+// from the largest |Re| or |Im| of its spectra (the per-plane maxima that
+// the kernels storing the spectra leave in pm), so that the largest value
+// lies in [2^13, 2^14).  The epilogue multiplies by 2^-ks and 2^-kT, which
+// is exact; BF16 operands are not scaled.
 //
 // Per CTA (192 threads, two CTAs per SM, 64 TMEM columns):
 //   warp 4     issues the TMA copies of a chunk's table tile(s) into a stage
@@ -50,6 +56,7 @@
 // MMAs, and warp 0 frees the tensor memory before the CTA exits.
 #include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched at run time)
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -104,14 +111,15 @@ int encoder(EncodeTiledFn* out) {
 
 // 16-bit table [parts * No][nkb][U][64], 128-byte swizzle, box 64 x rows;
 // rows past U and blocks past nkb read as zero.
-int encode_table(CUtensorMap* m, const void* table, int U, int nkb, int planes, int rows) {
+int encode_table(CUtensorMap* m, const void* table, int U, int nkb, int planes, int rows, bool f16) {
   EncodeTiledFn enc;
   SFS_TRY(encoder(&enc));
   const cuuint64_t dims[4] = {64, (cuuint64_t)U, (cuuint64_t)nkb, (cuuint64_t)planes};
   const cuuint64_t strides[3] = {128, (cuuint64_t)U * 128, (cuuint64_t)nkb * U * 128};
   const cuuint32_t box[4] = {64, (cuuint32_t)rows, 1, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(table), dims, strides,
+  const CUresult r = enc(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+                         const_cast<void*>(table), dims, strides,
                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -179,10 +187,10 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t addr, uint32_t lbo, uint
   return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
          ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
-// Instruction descriptor of kind::f16: D f32, A and B bf16, B K-major,
-// A K-major (forward) or MN-major (adjoint).
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn_major) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) |
+// Instruction descriptor of kind::f16: D f32, A and B both bf16 (f16 =
+// false) or both f16, B K-major, A K-major (forward) or MN-major (adjoint).
+__host__ __device__ constexpr uint32_t idesc_16(int M, int N, bool a_mn_major, bool f16) {
+  return (1u << 4) | (f16 ? 0u : (1u << 7) | (1u << 10)) | ((a_mn_major ? 1u : 0u) << 15) |
          ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 // D[tmem] (+)= A[smem] * B[smem]^T
@@ -195,13 +203,22 @@ __device__ __forceinline__ void mma_bf16_ss(uint32_t d, uint64_t adesc, uint64_t
       : "memory");
 }
 
-// Two values as a BF16 pair (low half first): their BF16 roundings (lo =
-// false) or the BF16 roundings of what those leave (lo = true).
-__device__ __forceinline__ uint32_t bf16_pair_part(float v0, float v1, bool lo) {
+// Two values as a 16-bit pair (low half first): their roundings (lo =
+// false) or the roundings of what those leave (lo = true), in FP16 (f16) or
+// BF16.
+__device__ __forceinline__ uint32_t pair16_part(float v0, float v1, bool lo, bool f16) {
+  if (f16) {
+    __half2 h = __floats2half2_rn(v0, v1);
+    if (lo) h = __floats2half2_rn(v0 - __low2float(h), v1 - __high2float(h));
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
   __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
   if (lo) h = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
   return *reinterpret_cast<uint32_t*>(&h);
 }
+
+// 2^k for -126 <= k <= 127, exactly
+__device__ __forceinline__ float pow2f(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }
 
 // ---------------------------------------------------------------------------
 // Shared-memory plan of one CTA
@@ -242,8 +259,10 @@ struct HPlan {
                        kBE = kBF + kSBB, kDF = kBE + kSBB, kDE = kDF + 2, kDR = kDE + 2, kNV = kDR + 1,
                        kNumBars = kNV + 1;
   static constexpr int kOffBar = kOffS + kSS * kSSlot;
+  // TMEM address (0), abort flag (4), FP16 scales 2^ks of the group's scenes
+  // (16 + 4 j) and their inverses (32 + 4 j), per-warp maxima (48 + 16 w + 4 j)
   static constexpr int kOffSlot = kOffBar + kNumBars * 8;
-  static constexpr int kSmem = kOffSlot + 16 + 1024;  // + alignment of the base to 1 KB
+  static constexpr int kSmem = kOffSlot + 128 + 1024;  // + alignment of the base to 1 KB
   static_assert(kSmem <= (NB == 1 ? 115 * 1024 : 227 * 1024), "shared memory plan");
 };
 
@@ -253,7 +272,7 @@ template <bool FWD, int NP, int NB>
 __global__ void __launch_bounds__(kHThreads, HPlan<NP, NB>::kCtasPerSm)
 contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUtensorMap spec,
            float2* __restrict__ out, long long out_stride, int nscene, PlaneDims d, int nmt, int nch,
-           int nunits, int* __restrict__ err) {
+           int nunits, const float* __restrict__ pm, int* __restrict__ err) {
   using Pl = HPlan<NP, NB>;
   constexpr uint32_t kHCols = Pl::kCols;
   constexpr int ST = Pl::kST, SS = Pl::kSS, SBB = Pl::kSBB, LEAD = Pl::kLead;
@@ -381,7 +400,7 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
       mbar_wait_bounded(bar(Pl::kTF + i % ST), (i / ST) & 1, kDrainNs);
   } else if (warp == kHMmaWarp) {
     // ---- MMA issuer (whole warp, one elected lane issues) ----
-    constexpr uint32_t idesc = idesc_bf16(128, 32 * NB, !FWD);
+    const uint32_t idesc = d.f16 ? idesc_16(128, 32 * NB, !FWD, true) : idesc_16(128, 32 * NB, !FWD, false);
     bool ok = true;
     int k = 0, c = 0;
     for (int i = 0; i < items; ++i) {
@@ -436,6 +455,37 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
     const bool lo = n >= 16;
     const int nc = n & 15, sl8 = nc & 7;
     const bool slot_ok = sl8 < d.GS;
+    const bool f16 = d.f16 != 0;
+    float* scl = (float*)(hsm + Pl::kOffSlot + 16);   // [NB] 2^ks
+    float* iscl = (float*)(hsm + Pl::kOffSlot + 32);  // [NB] 2^-ks
+    if (f16) {
+      // scale of scene j of the group from the per-plane maxima of its spectra
+      float* wmax = (float*)(hsm + Pl::kOffSlot + 48);
+      const int pm_n = FWD ? d.Nz : d.U;
+      const long long pm_stride = FWD ? d.bs_pmx : d.bs_pmr;
+      pdl_wait();  // the maxima come from the previous kernel
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        float m = 0.0f;
+        if (pm && j < nscene)
+          for (int i = t; i < pm_n; i += 128) m = fmaxf(m, pm[j * pm_stride + i]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if (lane == 0) wmax[4 * warp + j] = m;
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (t < NB) {
+        const float m = fmaxf(fmaxf(wmax[t], wmax[4 + t]), fmaxf(wmax[8 + t], wmax[12 + t]));
+        int ks = 0;
+        if (m > 0.0f && m <= 3.4e38f) {  // zero, infinite or NaN maxima keep scale 1
+          const int e = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;  // floor(log2 m), -127 if subnormal
+          ks = min(126, max(-126, 13 - e));
+        }
+        scl[t] = pow2f(ks);
+        iscl[t] = pow2f(-ks);
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
     // accumulator of local unit k to the output; false if the wait for its
     // MMAs failed
     auto epilogue = [&](int k) -> bool {
@@ -461,6 +511,11 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
       float e[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) e[q] = __uint_as_float(v[q]) + __uint_as_float(v[16 + q]);
+      if (f16) {  // undo 2^ks and 2^kT (two exact multiplies)
+        const float is = iscl[j];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) e[q] = (e[q] * is) * d.tinv;
+      }
       float2* outj = out + j * out_stride;
       if (FWD) {
         const int u = 128 * mt + t;
@@ -505,6 +560,7 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
 #pragma unroll 1
       for (int jn = 0; jn < NB; ++jn) {
       const float* sp = (const float*)(hsm + Pl::kOffS + xs * Pl::kSSlot + jn * (FWD ? 2048 : 4096));
+      const float sc = f16 ? scl[jn] : 1.0f;
       uint32_t w[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
@@ -519,7 +575,7 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
           v1 = sp[(ub + 1) * 16 + 2 * sl8 + comp];
         }
         if (!slot_ok) v0 = v1 = 0.f;
-        w[j] = bf16_pair_part(v0, v1, lo);
+        w[j] = pair16_part(v0 * sc, v1 * sc, lo, f16);
       }
       // rows 32 jn .. of the B slot (a multiple of 8, so the swizzle phase is n & 7)
       unsigned char* brow = hsm + Pl::kOffB + sl * Pl::kBSlot + (32 * jn + n) * 128;
@@ -557,7 +613,7 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
 
 template <bool FWD, int NP, int NB>
 int launch_h(const PlaneDims& d, const CUtensorMap& tab, const CUtensorMap& spec, float2* out,
-             long long out_stride, int nscene, int* err, cudaStream_t st) {
+             long long out_stride, int nscene, const float* pm, int* err, cudaStream_t st) {
   using Pl = HPlan<NP, NB>;
   SFS_TRY(ensure_smem_attr(contract_h<FWD, NP, NB>, Pl::kSmem));
   const int No = d.Ns / d.GS;
@@ -568,7 +624,7 @@ int launch_h(const PlaneDims& d, const CUtensorMap& tab, const CUtensorMap& spec
   const int G = std::min(Pl::kCtasPerSm == 2 ? d.G : d.G / 2, nunits);
   if (G <= 0) return SFS_OK;
   return launch_pdl(contract_h<FWD, NP, NB>, dim3(G), dim3(kHThreads), (size_t)Pl::kSmem, st, tab, spec,
-                    out, out_stride, nscene, d, nmt, nch, nunits, err);
+                    out, out_stride, nscene, d, nmt, nch, nunits, pm, err);
 }
 
 // Scene group size of a batched call: one table tile serves up to 4 scenes.
@@ -591,15 +647,18 @@ int launch_groups(const PlaneDims& d, const CUtensorMap& tab, const CUtensorMap*
     }
     float2* o = out + g0 * out_stride;
     const int n = std::min(NB, B - g0);
+    // per-plane spectra maxima of the group's first scene (FP16 modes)
+    const float* pm0 = FWD ? d.pm_x : d.pm_r;
+    const float* pm = pm0 ? pm0 + g0 * (FWD ? d.bs_pmx : d.bs_pmr) : nullptr;
     int rc;
     if (d.nparts == 2) {
-      rc = NB == 1 ? launch_h<FWD, 2, 1>(d, tab, *spec, o, out_stride, n, err, st)
-         : NB == 2 ? launch_h<FWD, 2, 2>(d, tab, *spec, o, out_stride, n, err, st)
-                   : launch_h<FWD, 2, 4>(d, tab, *spec, o, out_stride, n, err, st);
+      rc = NB == 1 ? launch_h<FWD, 2, 1>(d, tab, *spec, o, out_stride, n, pm, err, st)
+         : NB == 2 ? launch_h<FWD, 2, 2>(d, tab, *spec, o, out_stride, n, pm, err, st)
+                   : launch_h<FWD, 2, 4>(d, tab, *spec, o, out_stride, n, pm, err, st);
     } else {
-      rc = NB == 1 ? launch_h<FWD, 1, 1>(d, tab, *spec, o, out_stride, n, err, st)
-         : NB == 2 ? launch_h<FWD, 1, 2>(d, tab, *spec, o, out_stride, n, err, st)
-                   : launch_h<FWD, 1, 4>(d, tab, *spec, o, out_stride, n, err, st);
+      rc = NB == 1 ? launch_h<FWD, 1, 1>(d, tab, *spec, o, out_stride, n, pm, err, st)
+         : NB == 2 ? launch_h<FWD, 1, 2>(d, tab, *spec, o, out_stride, n, pm, err, st)
+                   : launch_h<FWD, 1, 4>(d, tab, *spec, o, out_stride, n, pm, err, st);
     }
     SFS_TRY(rc);
   }
@@ -623,8 +682,8 @@ int tc16_setup(sfs_operator* op) {
     return SFS_ERR_OOM;
   }
   const int planes = op->nparts * (op->Ns / op->GS);
-  int rc = encode_table(&m->tab_f, op->table, op->U, op->nkb, planes, 128);
-  if (rc == SFS_OK) rc = encode_table(&m->tab_a, op->table, op->U, op->nkb, planes, 64);
+  int rc = encode_table(&m->tab_f, op->table, op->U, op->nkb, planes, 128, op->f16 != 0);
+  if (rc == SFS_OK) rc = encode_table(&m->tab_a, op->table, op->U, op->nkb, planes, 64, op->f16 != 0);
   if (rc == SFS_OK) rc = encode_spec(&m->xh, op->ws.Xh, op->geo.d.Nz, op->Ns, 32);
   if (rc == SFS_OK) rc = encode_spec(&m->rh, op->ws.Rh, op->Up, op->Ns, 64);
   if (rc != SFS_OK) {

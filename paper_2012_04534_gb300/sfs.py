@@ -39,8 +39,10 @@ SFS_PREC_FP32 = 0
 SFS_PREC_TF32X3 = 1
 SFS_PREC_BF16 = 2
 SFS_PREC_BF16X2 = 3
+SFS_PREC_FP16 = 4
+SFS_PREC_FP16X2 = 5
 PRECISION_NAMES = {"fp32": SFS_PREC_FP32, "tf32x3": SFS_PREC_TF32X3, "bf16": SFS_PREC_BF16,
-                   "bf16x2": SFS_PREC_BF16X2}
+                   "bf16x2": SFS_PREC_BF16X2, "fp16": SFS_PREC_FP16, "fp16x2": SFS_PREC_FP16X2}
 
 SFS_MAX_BATCH = 256
 SFS_MAX_GROUPS = 64

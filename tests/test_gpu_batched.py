@@ -5,7 +5,8 @@ the FP64 oracle.
 A batched call runs the same arithmetic on every scene as the single-scene
 call: per-scene results agree with it to FP32 rounding (<= 1e-6 relative),
 and with the oracle at the precision's own tolerance (FP32 1e-5, BF16 2^-8,
-BF16X2 4 * 2^-16; see test_gpu_precision.py for their derivation).
+BF16X2 4 * 2^-16, FP16 2^-11, FP16X2 1e-5; see test_gpu_precision.py for
+their derivation).
 """
 import numpy as np
 import pytest
@@ -16,7 +17,7 @@ from tests._common import crandn, ensure_built, geom_params, oracle_geometry, re
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "bf16": 2.0 ** -8, "bf16x2": 4 * 2.0 ** -16}
+TOL = {"fp32": 1e-5, "bf16": 2.0 ** -8, "bf16x2": 4 * 2.0 ** -16, "fp16": 2.0 ** -11, "fp16x2": 1e-5}
 
 
 @pytest.fixture(scope="module")

@@ -30,7 +30,7 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex64)).cuda()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "bf16", "bf16x2"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "bf16", "bf16x2", "fp16"])
 def test_forced_wait_timeout_is_reported_and_recoverable(sfs, precision):
     """Every contraction kernel family: CUDA cores, tf32 tensor cores, and the
     TMA-fed 16-bit tensor-core kernels (one and two table parts)."""

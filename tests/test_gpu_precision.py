@@ -13,6 +13,10 @@ oracle at a tolerance derived from the arithmetic of its stored table:
     (element-wise).
   * BF16X2: table stored as BF16 hi + lo (remainder rounded again), relative
     error <= 2^-16 per component, spectra alike; the bar is 4 * 2^-16 in norm.
+  * FP16: as BF16 with u = 2^-11 (11 significant bits).  Both operands are
+    scaled by powers of two into FP16's range, which is exact, so the bars
+    are u and 8u whatever the scale of the input; FP16X2 (table hi + lo,
+    about 2^-22) is held to the FP32 bars.
 """
 import numpy as np
 import pytest
@@ -24,10 +28,13 @@ from tests._common import crandn, ensure_built, geom_params, oracle_geometry, re
 pytestmark = pytest.mark.gpu
 
 U_BF16 = 2.0 ** -8
+U_FP16 = 2.0 ** -11
 TOL = {
     "tf32x3": (1e-5, 1e-4),
     "bf16": (U_BF16, 8 * U_BF16),
     "bf16x2": (4 * 2.0 ** -16, 4e-4),
+    "fp16": (U_FP16, 8 * U_FP16),
+    "fp16x2": (1e-5, 1e-4),
 }
 MODES = list(TOL)
 
@@ -143,7 +150,7 @@ def test_tf32x3_fista_200_iterations_matches_oracle(sfs, case):
     assert rel_err(x_gpu, x_ref) <= 1e-4
 
 
-@pytest.mark.parametrize("mode", ["bf16", "bf16x2"])
+@pytest.mark.parametrize("mode", ["bf16", "bf16x2", "fp16", "fp16x2"])
 def test_reduced_precision_fista_reaches_fp32_nmse(sfs, mode):
     """FISTA with a reduced-precision operator on a noisy 16 x 16 x 40 scene:
     after the same 150 iterations its NMSE against the true scene is within
@@ -184,11 +191,13 @@ def test_bf16_operator_info_and_table_bytes(sfs):
     idx = O.select_indices(go, O.SEL_RANDOM, 16, True, 3)
     g = sfs.Geometry(**params)
     info = {m: sfs.Operator.from_indices(g, idx, precision=sfs.PRECISION_NAMES[m]).info
-            for m in ("fp32", "bf16", "bf16x2")}
+            for m in ("fp32", "bf16", "bf16x2", "fp16", "fp16x2")}
     # 16-bit table: No orbits x ceil(Nz / 32) blocks x U rows x 128 B per part
     No = info["bf16"]["Nslot"] // info["bf16"]["GS"]
     assert info["bf16"]["table_bytes"] == No * 2 * info["bf16"]["U"] * 128
     assert info["bf16x2"]["table_bytes"] == 2 * info["bf16"]["table_bytes"]
+    assert info["fp16"]["table_bytes"] == info["bf16"]["table_bytes"]
+    assert info["fp16x2"]["table_bytes"] == info["bf16x2"]["table_bytes"]
     with pytest.raises(sfs.SfsError):
         sfs.Operator.from_indices(g, idx, precision=17)
 
@@ -206,3 +215,51 @@ def test_bf16_noalloc_adjoint_equals_adjoint(sfs):
     sfs.sfs_apply_AH_noalloc(op.handle, y.data_ptr(), xb.data_ptr(),
                              torch.cuda.current_stream().cuda_stream)
     assert np.array_equal(a, to_host(xb))
+
+
+@pytest.mark.parametrize("mode", ["fp16", "fp16x2", "bf16"])
+def test_16bit_results_scale_with_the_input(sfs, mode):
+    """The spectra scale is a power of two taken from the data, so scaling the
+    input by 2^k scales A x and A^H y by exactly 2^k (bit for bit) while FP16
+    alone spans only 2^-24 .. 2^16; inputs near 1e-25 and 1e25 stay within
+    the mode's tolerance of the oracle.  (Scales stay where no FP32 value of
+    the chain over- or underflows, so that the FP32 FFTs scale exactly too.)"""
+    params = geom_params(Nx=12, Ny=10, Nz=36, dz=0.15e-3, Nt=256)
+    g, op, go, idx = make_pair(sfs, params, mode, M=12, seed=13)
+    A = O.dense_A(go, idx)
+    rng = np.random.default_rng(14)
+    x = crandn(rng, g.Nz, g.Ny, g.Nx)
+    y = crandn(rng, g.S, 12)
+    ya = to_host(op.apply_A(to_dev(x)))
+    xa = to_host(op.apply_AH(to_dev(y)))
+    for k in (-60, -30, 30, 60):
+        c = 2.0 ** k
+        assert np.array_equal(to_host(op.apply_A(to_dev(x * c))), ya * c)
+        assert np.array_equal(to_host(op.apply_AH(to_dev(y * c))), xa * c)
+    tol, _ = TOL[mode]
+    for c in (1e-25, 1e25):
+        yc = to_host(op.apply_A(to_dev(x * c)))
+        xc = to_host(op.apply_AH(to_dev(y * c)))
+        assert rel_err(yc, A @ (x * c).ravel()) <= tol
+        assert rel_err(xc, A.conj().T @ (y * c).ravel()) <= tol
+
+
+@pytest.mark.parametrize("mode", ["fp16", "fp16x2"])
+def test_fp16_batched_scenes_take_their_own_scale(sfs, mode):
+    """Five scenes 10^-12 .. 10^12 apart in one batched call (one contraction
+    launch serves four of them): each scene within the tolerance of the
+    oracle, which a scale shared by the group would break for all but the
+    largest scene."""
+    params = geom_params(Nx=10, Ny=8, Nz=40, dz=0.15e-3, Nt=256)
+    g, op, go, idx = make_pair(sfs, params, mode, M=10, seed=15)
+    A = O.dense_A(go, idx)
+    rng = np.random.default_rng(16)
+    scales = np.array([1e-12, 1e-6, 1.0, 1e6, 1e12])
+    x = crandn(rng, 5, g.Nz, g.Ny, g.Nx) * scales[:, None, None, None]
+    y = crandn(rng, 5, g.S, 10) * scales[:, None, None]
+    yb = to_host(op.apply_A_batched(to_dev(x)))
+    xb = to_host(op.apply_AH_batched(to_dev(y)))
+    tol, _ = TOL[mode]
+    for b in range(5):
+        assert rel_err(yb[b], A @ x[b].ravel()) <= tol
+        assert rel_err(xb[b], A.conj().T @ y[b].ravel()) <= tol
