@@ -26,6 +26,8 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
   dense_A / A_rows    pinned: DFT of the brute-force time-domain echo
                       simulation (time_domain_ascan), closed form below a
                       single scatterer, lateral shift invariance
+  A_cols              pinned: DFT of the simulated echo of one unit
+                      scatterer per column, equal to dense_A's columns
   multilevel_toeplitz pinned: the worked 2-level example printed in Sec. IV-B
   LateralFFTOperator  pinned: equal to dense_A / dense_A^H to 1e-12
   power_iteration     pinned: numpy SVD on tiny grids, Frobenius bounds
@@ -350,6 +352,28 @@ def A_rows(g: Geometry, idx, rows):
     ys = ys[s][:, None]
     tau = time_of_flight(xs, ys, xv[None], yv[None], zv[None], g.c)
     gd = directivity(xs, ys, xv[None], yv[None], zv[None], g.theta)
+    amp = g.fs * pulse_spectrum(f, g.fc, g.alpha) * gd
+    return amp * np.exp(-2j * np.pi * f * (tau - g.t0))
+
+
+def A_cols(g: Geometry, idx, voxels):
+    """Columns of the same dense A (Eq. (4) at the kept bins, Sigma = I):
+    A[:, v] for the flat voxel indices ``voxels`` (v = (z Ny + y) Nx + x),
+    shape (S*M, len(voxels)).  With these, (A^H y)[v] = sum_r conj(A[r, v])
+    y[r] is computable voxel by voxel on grids whose dense A does not fit."""
+    voxels = np.asarray(voxels, dtype=np.int64)
+    M = idx.shape[1]
+    rows = np.arange(idx.size)
+    s, m = np.divmod(rows, M)
+    k = idx[s, m].astype(np.float64)
+    f = g.bin_freq(k)[:, None]
+    xs, ys = g.scan_xy()
+    xv, yv, zv = g.voxel_xyz()
+    xs = xs[s][:, None]
+    ys = ys[s][:, None]
+    xv, yv, zv = xv[voxels][None], yv[voxels][None], zv[voxels][None]
+    tau = time_of_flight(xs, ys, xv, yv, zv, g.c)
+    gd = directivity(xs, ys, xv, yv, zv, g.theta)
     amp = g.fs * pulse_spectrum(f, g.fc, g.alpha) * gd
     return amp * np.exp(-2j * np.pi * f * (tau - g.t0))
 

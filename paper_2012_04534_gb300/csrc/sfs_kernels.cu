@@ -205,9 +205,12 @@ __device__ __forceinline__ void zero_plane(float2* buf) {
 // several L2 round trips overlap instead of queueing one after another.
 constexpr int kLoadBatch = 12;
 // 64 x 64 planes (4544 slots on a 32 x 32 scan) run two CTAs per SM at <= 64
-// registers a thread: 9 slots per thread still cover 4608 slots in one round
+// registers a thread: 9 slots per thread still cover 4608 slots in one round.
+// 128 x 128 planes run 1024 threads (again <= 64 registers): 6 slots a round.
 template <int P, bool TWO_D>
-__host__ __device__ constexpr int load_batch() { return PlaneFFT<P, TWO_D>::LANES64 ? 9 : kLoadBatch; }
+__host__ __device__ constexpr int load_batch() {
+  return PlaneFFT<P, TWO_D>::LANES64 ? 9 : (PlaneFFT<P, TWO_D>::NT >= 1024 ? 6 : kLoadBatch);
+}
 
 // Spectrum of bin plane u from the forward contraction: the sum of its nzb
 // depth-block partials Yp[zb][u][slot] (plane stride Up * Ns).

@@ -197,6 +197,8 @@ def _fista_case(sfs, params, M, n_scatter, iters, mu=0.05, snr_db=20.0, seed=1):
 @pytest.mark.parametrize("case", [
     ("line2d", dict(), 32, 3, 200),
     ("small3d", dict(Nx=12, Ny=12, Nz=24, dz=0.15e-3, Nt=256), 16, 5, 200),
+    # 128 x 128 lateral FFT planes (2 * 40 - 1 > 64), a non-square scan
+    ("p128", dict(Nx=40, Ny=36, Nz=10, dz=0.15e-3, Nt=256), 10, 4, 200),
 ])
 def test_fista_200_iterations_matches_oracle(sfs, case):
     name, over, M, ns, iters = case
@@ -303,3 +305,67 @@ def test_frobenius_norm_and_sigma_estimate(sfs, theta_deg):
     N = min(A.shape)
     assert math.sqrt(fro2) / math.sqrt(N) <= smax * (1 + 1e-12) <= math.sqrt(fro2) * (1 + 1e-12)
     assert sigma_hat == pytest.approx(math.sqrt(fro2) / N ** 0.25, rel=1e-12)
+
+
+# tolerances of the modes against the FP64 oracle (derived in
+# test_gpu_precision.py): relative 2-norm, and element-wise against the
+# largest entry
+P128_TOL = {"fp32": (TOL_OP, 10 * TOL_OP), "bf16": (2.0 ** -8, 8 * 2.0 ** -8),
+            "fp16": (2.0 ** -11, 8 * 2.0 ** -11)}
+
+
+@pytest.mark.parametrize("mode", list(P128_TOL))
+def test_128_point_planes_match_oracle(sfs, mode):
+    """A 48 x 40 scan pads its planes to 128 x 128 (the 1024-thread plane
+    kernels): single and batched (3 scenes in one 16-bit group) A and A^H
+    against the FP64 lateral-FFT oracle."""
+    params = geom_params(Nx=48, Ny=40, Nz=14, dz=0.15e-3, Nt=256)
+    go = oracle_geometry(params)
+    idx = O.select_indices(go, O.SEL_RANDOM, 12, True, 31)
+    g = sfs.Geometry(**params)
+    op = sfs.Operator.from_indices(g, idx, precision=sfs.PRECISION_NAMES[mode])
+    assert op.info["Px"] == 128 and op.info["Py"] == 128
+    ref = O.LateralFFTOperator(go, idx)
+    rng = np.random.default_rng(32)
+    x = crandn(rng, 3, g.Nz, g.Ny, g.Nx)
+    y = crandn(rng, 3, g.S, 12)
+    tol, tol_el = P128_TOL[mode]
+    yb = to_host(op.apply_A_batched(to_dev(x)))
+    xb = to_host(op.apply_AH_batched(to_dev(y)))
+    for b in range(3):
+        ry, rx = ref.apply_A(x[b]), ref.apply_AH(y[b])
+        assert rel_err(yb[b], ry) <= tol
+        assert rel_err(xb[b], rx) <= tol
+        assert np.abs(yb[b] - ry).max() <= tol_el * np.abs(ry).max()
+        assert np.abs(xb[b] - rx).max() <= tol_el * np.abs(rx).max()
+    assert rel_err(to_host(op.apply_A(to_dev(x[0]))), yb[0]) <= 1e-6
+    assert rel_err(to_host(op.apply_AH(to_dev(y[0]))), xb[0]) <= 1e-6
+
+
+@pytest.mark.parametrize("mode", list(P128_TOL))
+def test_vol64_full_size_sampled_outputs(sfs, mode):
+    """The 64 x 64 x 256 workload (Nt = 1024, M = 128, 128 x 128 planes) at
+    full size: 24 sampled entries of A x against rows of the dense
+    definition, 16 sampled voxels of A^H y against its columns."""
+    w = synth.WORKLOADS["vol64"]
+    params = synth.geometry_params("vol64")
+    go = oracle_geometry(params)
+    idx = O.select_indices(go, O.SEL_RANDOM, w["M"], True, 1002)
+    g = sfs.Geometry(**params)
+    op = sfs.Operator.from_indices(g, idx, precision=sfs.PRECISION_NAMES[mode])
+    rng = np.random.default_rng(33)
+    x = synth.scene((g.Nz, g.Ny, g.Nx), None, "uniform", seed=5, p_bernoulli=1e-4)
+    x = x + 0.01 * crandn(rng, g.Nz, g.Ny, g.Nx)
+    y = crandn(rng, g.S, w["M"])
+    ya = to_host(op.apply_A(to_dev(x))).ravel()
+    xa = to_host(op.apply_AH(to_dev(y))).ravel()
+    tol, tol_el = P128_TOL[mode]
+    rows = rng.choice(g.S * w["M"], 24, replace=False)
+    ref_y = np.concatenate([O.A_rows(go, idx, rows[i:i + 6]) @ x.ravel() for i in range(0, 24, 6)])
+    vox = rng.choice(g.V, 16, replace=False)
+    ref_x = O.A_cols(go, idx, vox).conj().T @ y.ravel()
+    assert np.abs(ya[rows] - ref_y).max() <= tol_el * np.abs(ya).max()
+    assert np.abs(xa[vox] - ref_x).max() <= tol_el * np.abs(xa).max()
+    if mode == "fp32":
+        assert rel_err(ya[rows], ref_y) <= tol
+        assert rel_err(xa[vox], ref_x) <= tol

@@ -227,6 +227,24 @@ def test_dense_A_with_directivity_equals_time_domain_echo():
         assert np.linalg.norm(y[s * 12:(s + 1) * 12] - ref) <= 1e-10 * np.linalg.norm(ref)
 
 
+def test_A_cols_equal_time_domain_echo_of_one_scatterer():
+    """Column v of A is the kept-bin DFT of the simulated echo of a unit
+    scatterer at voxel v, at every position (directivity on); the columns
+    also equal the dense A's (a swapped voxel index or axis breaks both)."""
+    g = small_geom(Nx=4, Ny=3, Nz=6, Nt=128, theta=math.radians(25))
+    idx = O.select_indices(g, O.SEL_RANDOM, 7, True, 8)
+    xv, yv, zv = g.voxel_xyz()
+    vox = np.array([0, 5, 17, 40, g.V - 1])
+    C = O.A_cols(g, idx, vox)
+    assert C.shape == (g.S * 7, vox.size)
+    for j, v in enumerate(vox):
+        for s in range(g.S):
+            b = O.time_domain_ascan(g, s, xv[[v]], yv[[v]], zv[[v]], np.ones(1))
+            ref = O.dft_bins(b, idx[s])
+            assert np.linalg.norm(C[s * 7:(s + 1) * 7, j] - ref) <= 1e-10 * np.linalg.norm(ref)
+    np.testing.assert_allclose(C, O.dense_A(g, idx)[:, vox], rtol=0, atol=1e-12 * np.abs(C).max())
+
+
 def test_single_scatterer_below_position_closed_form():
     """A scatterer at depth z straight below the transducer: the echo is the
     pulse delayed by 2z/c, so bin k holds fs H(f_k) e^{-j 2 pi f_k (2z/c - t0)}."""
