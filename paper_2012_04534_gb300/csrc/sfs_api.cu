@@ -278,6 +278,7 @@ void free_operator(sfs_operator* op) {
   cudaFree(op->ws.Gh);
   cudaFree(op->ws.segslot);
   cudaFree(op->slot_kappa);
+  cudaFree(op->quad);
   cudaFree(op->orbit_rep);
   cudaFree(op->ws.err);
   cudaFree(op->ws.xk);
@@ -337,6 +338,7 @@ PlaneDims operator_dims(const sfs_operator* op) {
   d.inject = op->inject;
   d.slot_kappa = op->slot_kappa;
   d.orbit_rep = op->orbit_rep;
+  d.quad = op->quad;
   d.batch = 1;
   d.bs_x = op->V;
   d.bs_xh = (long long)op->geo.d.Nz * op->Ns;
@@ -899,6 +901,28 @@ static int build_operator(sfs_geometry* g, int M, const int32_t* idx_host, int p
       for (size_t m = 0; m < members[o].size(); ++m) slot_kappa[(size_t)o * op->GS + m] = members[o][m];
     }
   }
+  // 128 x 128 planes move their spectra quadrant by quadrant (the output
+  // parities (ky & 1, kx & 1) of the 128-point transforms): offsets of the
+  // four quadrants and the padding slots, then entries (slot << 12) |
+  // (kx / 2 * 64 + ky / 2), slots ascending within each group.
+  std::vector<int32_t> quad;
+  if (two_d && g->Px == 128) {
+    std::vector<int32_t> groups[5];
+    for (int j = 0; j < op->Ns; ++j) {
+      const int kap = slot_kappa[j];
+      if (kap < 0) {
+        groups[4].push_back(j << 12);
+        continue;
+      }
+      const int kx = kap / g->Py, ky = kap % g->Py;
+      groups[2 * (ky & 1) + (kx & 1)].push_back((j << 12) | ((kx >> 1) * 64 + (ky >> 1)));
+    }
+    quad.assign(8, 0);
+    for (int q = 0; q < 5; ++q) {
+      quad[q + 1] = quad[q] + (int32_t)groups[q].size();
+      quad.insert(quad.end(), groups[q].begin(), groups[q].end());
+    }
+  }
 
   // host FP64 geometry tables: (tau - t0) fs / Nt split into (hi, lo) floats,
   // directivity, per-bin amplitude fs H(f_k) / (Px Py)
@@ -1014,6 +1038,7 @@ static int build_operator(sfs_geometry* g, int M, const int32_t* idx_host, int p
   if ((rc = dev_alloc(&op->ws.Xh, Ns * d.Nz)) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->slot_kappa, slot_kappa.size())) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->orbit_rep, orbit_rep.size())) != SFS_OK) return fail(rc);
+  if (!quad.empty() && (rc = dev_alloc(&op->quad, quad.size())) != SFS_OK) return fail(rc);
   if ((rc = dev_alloc(&op->ws.Gh, (size_t)op->nslots * op->azb * kKappaTile)) != SFS_OK)
     return fail(rc);
   if ((rc = dev_alloc(&op->ws.segslot, segslot.size())) != SFS_OK) return fail(rc);
@@ -1049,6 +1074,8 @@ static int build_operator(sfs_geometry* g, int M, const int32_t* idx_host, int p
     e = cudaMemcpy(op->slot_kappa, slot_kappa.data(), slot_kappa.size() * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(op->orbit_rep, orbit_rep.data(), orbit_rep.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !quad.empty())
+    e = cudaMemcpy(op->quad, quad.data(), quad.size() * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(op->ws.segslot, segslot.data(), segslot.size() * sizeof(int2),
                    cudaMemcpyHostToDevice);

@@ -211,24 +211,122 @@ __device__ __forceinline__ void fft64_lanes(float2 v[8], const float2* tw, int l
 // Plane transforms.  TWO_D: P x P plane, row stride P + 1 (P + 4 for P = 64,
 // which the lane-group engine reads and writes without bank conflicts).
 // Otherwise a line of P points (Py = 1).
+//
+// QUAD (P = 128, TWO_D, ALLOW_QUAD): the planes the operator transforms at
+// run time have their spatial support inside 64 x 64 (Ny, Nx <= 64; the
+// padding to 128 only keeps the circular convolution linear).  For such a
+// plane the 128-point DFT splits by output parity into 64-point DFTs of
+// pre-twiddled inputs (W = e^{-2 pi j / 128}):
+//   S[2 ky' + py][2 kx' + px] = FFT64x64( s[y][x] W^(py y + px x) )[ky'][kx']
+// and the inverse, cropped to 64 x 64, is the sum over the four quadrants
+// q = (py, px) of W^-(py y + px x) IFFT64x64(S_q)[y][x].  So a 128 x 128
+// transform is four 64 x 64 lane-group transforms through one 64 x 68 buffer
+// (36 KB with twiddles: two CTAs per SM instead of one), with the spatial
+// plane held in registers between quadrants.  The spectrum is then never
+// whole in shared memory: loads and stores go quadrant by quadrant
+// (sfs_kernels.cu).  The generator table, whose planes fill 127 x 127, is
+// built with the full 128 x 128 engine (ALLOW_QUAD = false).
 // ---------------------------------------------------------------------------
-template <int P, bool TWO_D>
+template <int P, bool TWO_D, bool ALLOW_QUAD = true>
 struct PlaneFFT {
   // 64 x 64 planes use the lane-group engine (512 threads = 64 columns x 8);
-  // 128 x 128 planes (one CTA per SM: the plane takes 129 KB) run 1024
-  // threads, which halves a plane's time against 512 on vol64
+  // full 128 x 128 planes (one CTA per SM: the plane takes 129 KB) run 1024
+  // threads, quadrant planes 512
+  static constexpr bool QUAD = ALLOW_QUAD && TWO_D && P == 128;
   static constexpr bool LANES64 = TWO_D && P == 64;
-  static constexpr int LD = TWO_D ? (LANES64 ? P + 4 : P + 1) : P;
-  static constexpr int NT = TWO_D ? (P >= 128 ? 1024 : (P >= 64 ? 512 : 256)) : (P >= 512 ? 256 : (P >= 128 ? 128 : 64));
-  static constexpr int ELEMS = TWO_D ? P * LD : P;   // float2 slots of the plane
-  static constexpr int SMEM = (ELEMS + P) * 8;       // plane + twiddles
+  static constexpr int LD = QUAD ? 68 : (TWO_D ? (LANES64 ? P + 4 : P + 1) : P);
+  static constexpr int NT = QUAD ? 512
+                                 : (TWO_D ? (P >= 128 ? 1024 : (P >= 64 ? 512 : 256))
+                                          : (P >= 512 ? 256 : (P >= 128 ? 128 : 64)));
+  static constexpr int ELEMS = QUAD ? 64 * LD : (TWO_D ? P * LD : P);  // float2 slots of the plane
+  static constexpr int NTW = QUAD ? P + 64 : P;                         // twiddles (W_P, then W_64)
+  static constexpr int SMEM = (ELEMS + NTW) * 8;                        // plane + twiddles
   // resident CTAs per SM the plane kernels are compiled for: two 64 x 64
-  // planes per SM (at most 64 registers a thread) so that batched calls,
-  // which launch many planes per scene, keep two planes in flight per SM
-  static constexpr int MINB = LANES64 ? 2 : 1;
+  // (or quadrant) planes per SM (at most 64 registers a thread) so that
+  // batched calls, which launch many planes per scene, keep two planes in
+  // flight per SM
+  static constexpr int MINB = (LANES64 || QUAD) ? 2 : 1;
 
-  // spatial element (iy, ix) of the plane
+  // spatial element (iy, ix) of the plane (QUAD: iy, ix < 64)
   __device__ static __forceinline__ int sidx(int iy, int ix) { return TWO_D ? iy * LD + ix : ix; }
+  // QUAD: buffer position of local wavenumber (kx', ky') of a quadrant
+  __device__ static __forceinline__ int qidx(int local) { return (local >> 6) * LD + (local & 63); }
+
+  // QUAD forward: the spatial plane in buf (natural layout, zero outside the
+  // support) -> for q = 0..3 (py = q >> 1, px = q & 1) the quadrant's
+  // spectrum S_q[kx'][ky'] at buf[qidx(kx' 64 + ky')], then store(q).  buf
+  // is overwritten; store(q) must only read it.
+  template <typename Store>
+  __device__ static __forceinline__ void forward_quads(float2* buf, const float2* tw, Store&& store) {
+    static_assert(QUAD, "quadrant engine");
+    const float2* tw64 = tw + P;
+    const int lane = threadIdx.x & 31, l = lane >> 2;
+    const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
+    float2 s[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s[j] = buf[(l + 8 * j) * LD + c];  // (y = l + 8 j, x = c)
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      const int py = q >> 1, px = q & 1;
+      float2 v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = q ? cmul(s[j], tw[py * (l + 8 * j) + px * c]) : s[j];
+      __syncthreads();  // the spatial reads, or the previous quadrant's store, are done
+      // along y for column x = c; written transposed: row x, column ky'
+      fft64_lanes<false>(v, tw64, l);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) buf[c * LD + l + 8 * k] = v[k];
+      __syncthreads();
+      // along x for column ky' = c: kx' = l + 8 k at row kx' (own column only)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
+      fft64_lanes<false>(v, tw64, l);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) buf[(l + 8 * k) * LD + c] = v[k];
+      __syncthreads();
+      store(q);
+    }
+  }
+
+  // QUAD inverse: for q = 0..3, load(q) fills buf[qidx(kx' 64 + ky')] with
+  // S_q (every local position); the cropped 64 x 64 result is left in buf in
+  // the natural layout.
+  template <typename Load>
+  __device__ static __forceinline__ void inverse_quads(float2* buf, const float2* tw, Load&& load) {
+    static_assert(QUAD, "quadrant engine");
+    const float2* tw64 = tw + P;
+    const int lane = threadIdx.x & 31, l = lane >> 2;
+    const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
+    float2 acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      const int py = q >> 1, px = q & 1;
+      __syncthreads();  // earlier readers of buf are done
+      load(q);
+      __syncthreads();
+      float2 v[8];
+      // along kx' for column ky' = c; written transposed: row ky', column x
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
+      __syncthreads();
+      fft64_lanes<true>(v, tw64, l);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) buf[c * LD + l + 8 * k] = v[k];
+      __syncthreads();
+      // along ky' for column x = c: y = l + 8 k
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
+      fft64_lanes<true>(v, tw64, l);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] = q ? cadd(acc[k], cmulc(tw[py * (l + 8 * k) + px * c], v[k])) : v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) buf[(l + 8 * k) * LD + c] = acc[k];
+    __syncthreads();
+  }
   // wavenumber kappa (transposed order, kappa = kx*P + ky) of the plane
   __device__ static __forceinline__ int kidx(int kappa) {
     return TWO_D ? (kappa / P) * LD + (kappa % P) : kappa;

@@ -139,6 +139,7 @@ struct sfs_operator {
                                // (sfs_kernels.cu / sfs_tc.cu)
   int32_t* slot_kappa = nullptr;  // [Ns]
   int32_t* orbit_rep = nullptr;   // [Ns/GS]
+  int32_t* quad = nullptr;        // 128 x 128 planes: [8 + Ns] slots grouped by quadrant
   int32_t* posmap = nullptr;   // [U][S]: m with idx[s][m] == bins[u], else -1
   sfs::Workspace ws;
   // kernel timing (SFS_FISTA_TIME_KERNELS)
@@ -215,6 +216,7 @@ struct PlaneDims {
   int bs_red;           // reduction slots (doubles) per scene
   const int32_t* slot_kappa;  // [Ns] wavenumber of each slot, -1 for padding
   const int32_t* orbit_rep;   // [Ns / GS] representative wavenumber, -1 for padding
+  const int32_t* quad;        // 128 x 128 planes: slots by quadrant (sfs_kernels.cu), else null
 };
 
 // Resident contraction CTAs per SM (8 warps each); the persistent grid is

@@ -104,11 +104,11 @@ __device__ __forceinline__ void block_max_store(float v, float* out) {
 // added, so the reduced phase keeps ~1e-7 turn accuracy where a plain
 // float product of ~100 turns would lose ~1e-5.
 template <int P, bool TWO_D>
-__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT, PlaneFFT<P, TWO_D>::MINB)
+__global__ void __launch_bounds__(PlaneFFT<P, TWO_D, false>::NT, PlaneFFT<P, TWO_D, false>::MINB)
 build_table_kernel(PlaneDims d, const float2* __restrict__ tof,
                    const float* __restrict__ gdir, const float* __restrict__ amp,
                    const int32_t* __restrict__ bins, float2* __restrict__ table) {
-  using F = PlaneFFT<P, TWO_D>;
+  using F = PlaneFFT<P, TWO_D, false>;  // generator planes fill (2 Ny - 1) x (2 Nx - 1)
   extern __shared__ float2 smem[];
   float2* buf = smem;
   float2* tw = smem + F::ELEMS;
@@ -194,6 +194,118 @@ template <int P, bool TWO_D>
 __device__ __forceinline__ void zero_plane(float2* buf) {
   using F = PlaneFFT<P, TWO_D>;
   for (int e = threadIdx.x; e < F::ELEMS; e += F::NT) buf[e] = make_float2(0.f, 0.f);
+}
+
+// Twiddles of the plane engine (QUAD: W_128, then W_64 for the quadrants).
+template <int P, bool TWO_D>
+__device__ __forceinline__ void plane_twiddles(float2* tw) {
+  using F = PlaneFFT<P, TWO_D>;
+  make_twiddles<P, F::NT>(tw);
+  if constexpr (F::QUAD) make_twiddles<64, F::NT>(tw + P);
+}
+
+// QUAD planes: the spectrum moves quadrant by quadrant.  d.quad[0..5] are
+// offsets into the entries d.quad + 8: quadrant q = 2 (ky & 1) + (kx & 1)
+// owns entries quad[q] .. quad[q + 1], the padding slots quad[4] .. quad[5];
+// an entry is (slot << 12) | (kx / 2 * 64 + ky / 2), the quadrant-local
+// wavenumber.  Every slot appears once; each quadrant covers its 64 x 64
+// local wavenumbers once.  Global loads are issued kQuadBatch deep.
+constexpr int kQuadBatch = 8;
+constexpr int kQuadBatchAdj = 4;  // its segment lookups hold more registers
+
+template <int P, bool TWO_D>
+__device__ __forceinline__ void load_quadrant_fwd(float2* buf, const float2* __restrict__ Yp, int u,
+                                                  const PlaneDims& d, int q) {
+  using F = PlaneFFT<P, TWO_D>;
+  const int32_t* ql = d.quad + 8;
+  const float2* src = Yp + (size_t)u * d.Ns;
+  const size_t stride = (size_t)d.Up * d.Ns;
+  const int i1 = __ldg(d.quad + q + 1);
+  for (int i0 = __ldg(d.quad + q) + threadIdx.x; i0 < i1; i0 += kQuadBatch * F::NT) {
+    int ent[kQuadBatch];
+    float2 v[kQuadBatch];
+#pragma unroll
+    for (int k = 0; k < kQuadBatch; ++k) {
+      const int i = i0 + k * F::NT;
+      ent[k] = i < i1 ? __ldg(ql + i) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kQuadBatch; ++k) v[k] = ent[k] >= 0 ? src[ent[k] >> 12] : make_float2(0.f, 0.f);
+    for (int zb = 1; zb < d.nzb; ++zb)
+#pragma unroll
+      for (int k = 0; k < kQuadBatch; ++k)
+        if (ent[k] >= 0) v[k] = cadd(v[k], src[zb * stride + (ent[k] >> 12)]);
+#pragma unroll
+    for (int k = 0; k < kQuadBatch; ++k)
+      if (ent[k] >= 0) buf[F::qidx(ent[k] & 4095)] = v[k];
+  }
+}
+
+template <int P, bool TWO_D>
+__device__ __forceinline__ void load_quadrant_adj(float2* buf, const float2* __restrict__ Gs,
+                                                  const int2* __restrict__ segslot, int z,
+                                                  const PlaneDims& d, int q) {
+  using F = PlaneFFT<P, TWO_D>;
+  const int32_t* ql = d.quad + 8;
+  const int zb = z / d.azb, zr = z % d.azb;
+  const size_t slot_stride = (size_t)d.azb * 64;
+  const int i1 = __ldg(d.quad + q + 1);
+  for (int i0 = __ldg(d.quad + q) + threadIdx.x; i0 < i1; i0 += kQuadBatchAdj * F::NT) {
+    int ent[kQuadBatchAdj];
+    int2 sc[kQuadBatchAdj];
+#pragma unroll
+    for (int k = 0; k < kQuadBatchAdj; ++k) {
+      const int i = i0 + k * F::NT;
+      ent[k] = i < i1 ? __ldg(ql + i) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kQuadBatchAdj; ++k) {
+      const int j = ent[k] >> 12;
+      const int seg = (j >> 6) * d.anzb + zb;
+      sc[k] = ent[k] < 0 ? make_int2(0, 0) : (d.adj_seg ? make_int2(seg, 1) : __ldg(segslot + seg));
+    }
+    float2 v[kQuadBatchAdj];
+#pragma unroll
+    for (int k = 0; k < kQuadBatchAdj; ++k)
+      v[k] = sc[k].y > 0 ? Gs[(size_t)sc[k].x * slot_stride + (size_t)zr * 64 + ((ent[k] >> 12) & 63)]
+                         : make_float2(0.f, 0.f);
+    int more = 0;
+#pragma unroll
+    for (int k = 0; k < kQuadBatchAdj; ++k) more = max(more, sc[k].y);
+    for (int c = 1; c < more; ++c)
+#pragma unroll
+      for (int k = 0; k < kQuadBatchAdj; ++k)
+        if (c < sc[k].y)
+          v[k] = cadd(v[k], Gs[(size_t)(sc[k].x + c) * slot_stride + (size_t)zr * 64 + ((ent[k] >> 12) & 63)]);
+#pragma unroll
+    for (int k = 0; k < kQuadBatchAdj; ++k)
+      if (ent[k] >= 0) buf[F::qidx(ent[k] & 4095)] = v[k];
+  }
+}
+
+// Quadrant q of the spectrum in buf to its slots of dst; mx takes the
+// largest |Re| or |Im| stored.  With q = 4, zero to the padding slots.
+template <int P, bool TWO_D>
+__device__ __forceinline__ void store_quadrant(const float2* buf, float2* __restrict__ dst,
+                                               const PlaneDims& d, int q, float& mx) {
+  using F = PlaneFFT<P, TWO_D>;
+  const int32_t* ql = d.quad + 8;
+  const int i1 = __ldg(d.quad + q + 1);
+  for (int i0 = __ldg(d.quad + q) + threadIdx.x; i0 < i1; i0 += kQuadBatch * F::NT) {
+    int ent[kQuadBatch];
+#pragma unroll
+    for (int k = 0; k < kQuadBatch; ++k) {
+      const int i = i0 + k * F::NT;
+      ent[k] = i < i1 ? __ldg(ql + i) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kQuadBatch; ++k)
+      if (ent[k] >= 0) {
+        const float2 v = q < 4 ? buf[F::qidx(ent[k] & 4095)] : make_float2(0.f, 0.f);
+        dst[ent[k] >> 12] = v;
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+      }
+  }
 }
 
 // Lateral spectra travel between kernels in slot order: slot j holds
@@ -315,14 +427,63 @@ __device__ __forceinline__ void store_spectrum(const float2* buf, float2* __rest
   if (pm) block_max_store<F::NT>(mx, pm);
 }
 
-// Zero every slot of the plane outside the Ny x Nx crop window.
+// Zero every slot of the plane outside the Ny x Nx crop window (QUAD: of the
+// 64 x 64 plane it holds).
 template <int P, bool TWO_D>
 __device__ __forceinline__ void zero_outside(float2* buf, int Ny, int Nx) {
   using F = PlaneFFT<P, TWO_D>;
-  constexpr int PY = TWO_D ? P : 1;
-  for (int e = threadIdx.x; e < P * PY; e += F::NT) {
-    const int py = e / P, px = e % P;
+  constexpr int PX = F::QUAD ? 64 : P;
+  constexpr int PY = F::QUAD ? 64 : (TWO_D ? P : 1);
+  for (int e = threadIdx.x; e < PX * PY; e += F::NT) {
+    const int py = e / PX, px = e % PX;
     if (py >= Ny || px >= Nx) buf[F::sidx(py, px)] = make_float2(0.f, 0.f);
+  }
+}
+
+// Forward transform of the spatial plane in buf (zero outside the support)
+// and the store of its spectrum to dst in slot order; with pm (FP16 modes)
+// also the plane's largest |Re| or |Im| at *pm.  Every thread must call.
+template <int P, bool TWO_D>
+__device__ __forceinline__ void forward_store(float2* buf, const float2* tw, float2* __restrict__ dst,
+                                              const PlaneDims& d, float* pm) {
+  using F = PlaneFFT<P, TWO_D>;
+  if constexpr (F::QUAD) {
+    float mx = 0.0f;
+    F::forward_quads(buf, tw, [&](int q) { store_quadrant<P, TWO_D>(buf, dst, d, q, mx); });
+    store_quadrant<P, TWO_D>(buf, dst, d, 4, mx);
+    if (pm) block_max_store<F::NT>(mx, pm);
+  } else {
+    F::forward(buf, tw, d.Nx);
+    store_spectrum<P, TWO_D>(buf, dst, d, pm);
+  }
+}
+
+// Spectrum of bin plane u from the forward contraction (Yp) into buf and its
+// inverse transform: the natural-layout spatial plane in buf.
+template <int P, bool TWO_D>
+__device__ __forceinline__ void load_inverse_fwd(float2* buf, const float2* tw, const float2* __restrict__ Yp,
+                                                 int u, const PlaneDims& d) {
+  using F = PlaneFFT<P, TWO_D>;
+  if constexpr (F::QUAD) {
+    F::inverse_quads(buf, tw, [&](int q) { load_quadrant_fwd<P, TWO_D>(buf, Yp, u, d, q); });
+  } else {
+    load_spectrum_fwd<P, TWO_D>(buf, Yp, u, d);
+    __syncthreads();
+    F::inverse(buf, tw, d.Nx);
+  }
+}
+
+// The same for voxel plane z from the adjoint contraction (Gs).
+template <int P, bool TWO_D>
+__device__ __forceinline__ void load_inverse_adj(float2* buf, const float2* tw, const float2* __restrict__ Gs,
+                                                 const int2* __restrict__ segslot, int z, const PlaneDims& d) {
+  using F = PlaneFFT<P, TWO_D>;
+  if constexpr (F::QUAD) {
+    F::inverse_quads(buf, tw, [&](int q) { load_quadrant_adj<P, TWO_D>(buf, Gs, segslot, z, d, q); });
+  } else {
+    load_spectrum_adj<P, TWO_D>(buf, Gs, segslot, z, d);
+    __syncthreads();
+    F::inverse(buf, tw, d.Nx);
   }
 }
 
@@ -340,7 +501,7 @@ fwd_planes_kernel(PlaneDims d, const float2* __restrict__ x, float2* __restrict_
   float2* buf = smem;
   float2* tw = smem + F::ELEMS;
   const int z = blockIdx.x;
-  make_twiddles<P, F::NT>(tw);
+  plane_twiddles<P, TWO_D>(tw);
   pdl_wait();
   pdl_trigger();
   zero_plane<P, TWO_D>(buf);
@@ -349,9 +510,8 @@ fwd_planes_kernel(PlaneDims d, const float2* __restrict__ x, float2* __restrict_
   for (int e = threadIdx.x; e < d.Ny * d.Nx; e += F::NT)
     buf[F::sidx(e / d.Nx, e % d.Nx)] = xz[e];
   __syncthreads();
-  F::forward(buf, tw, d.Nx);
-  store_spectrum<P, TWO_D>(buf, Xh + (size_t)z * d.Ns, d,
-                           d.pm_x ? d.pm_x + blockIdx.y * d.bs_pmx + z : nullptr);
+  forward_store<P, TWO_D>(buf, tw, Xh + (size_t)z * d.Ns, d,
+                          d.pm_x ? d.pm_x + blockIdx.y * d.bs_pmx + z : nullptr);
 }
 
 // Yh[u] -> y[s, m] = IFFT2(Yh_u)(s) where bins[u] = idx[s, m]
@@ -371,12 +531,10 @@ inv_gather_kernel(PlaneDims d, const float2* __restrict__ Yh,
   float2* buf = smem;
   float2* tw = smem + F::ELEMS;
   const int u = blockIdx.x;
-  make_twiddles<P, F::NT>(tw);
+  plane_twiddles<P, TWO_D>(tw);
   pdl_wait();
   pdl_trigger();
-  load_spectrum_fwd<P, TWO_D>(buf, Yh, u, d);
-  __syncthreads();
-  F::inverse(buf, tw, d.Nx);
+  load_inverse_fwd<P, TWO_D>(buf, tw, Yh, u, d);
   double acc = 0.0;
   const int32_t* pm = posmap + (size_t)u * d.S;
   for (int s = threadIdx.x; s < d.S; s += F::NT) {
@@ -410,12 +568,10 @@ inv_resid_fwd_kernel(PlaneDims d, const float2* __restrict__ Yh,
   float2* buf = smem;
   float2* tw = smem + F::ELEMS;
   const int u = blockIdx.x;
-  make_twiddles<P, F::NT>(tw);
+  plane_twiddles<P, TWO_D>(tw);
   pdl_wait();
   pdl_trigger();
-  load_spectrum_fwd<P, TWO_D>(buf, Yh, u, d);
-  __syncthreads();
-  F::inverse(buf, tw, d.Nx);
+  load_inverse_fwd<P, TWO_D>(buf, tw, Yh, u, d);
   double acc = 0.0;
   const int32_t* pm = posmap + (size_t)u * d.S;
   const float2* yu = yplane + (size_t)u * d.S;
@@ -433,9 +589,8 @@ inv_resid_fwd_kernel(PlaneDims d, const float2* __restrict__ Yh,
   zero_outside<P, TWO_D>(buf, d.Ny, d.Nx);
   if (red_sumsq) block_add_double<F::NT>(acc, red_sumsq);
   __syncthreads();
-  F::forward(buf, tw, d.Nx);
-  store_spectrum<P, TWO_D>(buf, Rh + (size_t)u * d.Ns, d,
-                           d.pm_r ? d.pm_r + blockIdx.y * d.bs_pmr + u : nullptr);
+  forward_store<P, TWO_D>(buf, tw, Rh + (size_t)u * d.Ns, d,
+                          d.pm_r ? d.pm_r + blockIdx.y * d.bs_pmr + u : nullptr);
 }
 
 // y[s, m] scattered to bin plane u -> Rh[u] = FFT2(pad(.))
@@ -453,7 +608,7 @@ scatter_fwd_kernel(PlaneDims d, const float2* __restrict__ y,
   float2* buf = smem;
   float2* tw = smem + F::ELEMS;
   const int u = blockIdx.x;
-  make_twiddles<P, F::NT>(tw);
+  plane_twiddles<P, TWO_D>(tw);
   pdl_wait();
   pdl_trigger();
   zero_plane<P, TWO_D>(buf);
@@ -464,9 +619,8 @@ scatter_fwd_kernel(PlaneDims d, const float2* __restrict__ y,
     if (m >= 0) buf[F::sidx(s / d.Nx, s % d.Nx)] = y[(size_t)s * d.M + m];
   }
   __syncthreads();
-  F::forward(buf, tw, d.Nx);
-  store_spectrum<P, TWO_D>(buf, Rh + (size_t)u * d.Ns, d,
-                           d.pm_r ? d.pm_r + blockIdx.y * d.bs_pmr + u : nullptr);
+  forward_store<P, TWO_D>(buf, tw, Rh + (size_t)u * d.Ns, d,
+                          d.pm_r ? d.pm_r + blockIdx.y * d.bs_pmr + u : nullptr);
 }
 
 // Gh[z] -> x plane z = crop(IFFT2(Gh_z)); optional sum |x|^2 and max |x|.
@@ -487,12 +641,10 @@ inv_store_kernel(PlaneDims d, const float2* __restrict__ Gh, const int2* __restr
   float2* buf = smem;
   float2* tw = smem + F::ELEMS;
   const int z = blockIdx.x;
-  make_twiddles<P, F::NT>(tw);
+  plane_twiddles<P, TWO_D>(tw);
   pdl_wait();
   pdl_trigger();
-  load_spectrum_adj<P, TWO_D>(buf, Gh, segslot, z, d);
-  __syncthreads();
-  F::inverse(buf, tw, d.Nx);
+  load_inverse_adj<P, TWO_D>(buf, tw, Gh, segslot, z, d);
   double acc = 0.0;
   float mx = 0.f;
   float2* xz = x ? x + (size_t)z * d.Ny * d.Nx : nullptr;
@@ -532,12 +684,10 @@ inv_fista_fwd_kernel(PlaneDims d, const float2* __restrict__ Gh,
   float2* buf = smem;
   float2* tw = smem + F::ELEMS;
   const int z = blockIdx.x;
-  make_twiddles<P, F::NT>(tw);
+  plane_twiddles<P, TWO_D>(tw);
   pdl_wait();
   pdl_trigger();
-  load_spectrum_adj<P, TWO_D>(buf, Gh, segslot, z, d);
-  __syncthreads();
-  F::inverse(buf, tw, d.Nx);
+  load_inverse_adj<P, TWO_D>(buf, tw, Gh, segslot, z, d);
   const float thr = scal[kThr];
   const float invL = scal[kInvL];
   double l1 = 0.0;
@@ -561,9 +711,8 @@ inv_fista_fwd_kernel(PlaneDims d, const float2* __restrict__ Gh,
   if (!do_fwd) return;
   zero_outside<P, TWO_D>(buf, d.Ny, d.Nx);
   __syncthreads();
-  F::forward(buf, tw, d.Nx);
-  store_spectrum<P, TWO_D>(buf, Xh + (size_t)z * d.Ns, d,
-                           d.pm_x ? d.pm_x + blockIdx.y * d.bs_pmx + z : nullptr);
+  forward_store<P, TWO_D>(buf, tw, Xh + (size_t)z * d.Ns, d,
+                          d.pm_x ? d.pm_x + blockIdx.y * d.bs_pmx + z : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1149,9 +1298,10 @@ __global__ void scale_rnorm_kernel(float2* v, int n, const double* sumsq) {
 // Dispatch on the plane size
 // ---------------------------------------------------------------------------
 // nplanes planes of each of `batch` scenes (gridDim.y; blockIdx.y = scene)
-template <int P, bool TWO_D, typename K, typename... Args>
+// QUAD = false: launch shape of the full-plane engine (the table build).
+template <int P, bool TWO_D, bool QUAD = true, typename K, typename... Args>
 int launch_plane(K kernel, int nplanes, int d_batch, cudaStream_t st, Args... args) {
-  using F = PlaneFFT<P, TWO_D>;
+  using F = PlaneFFT<P, TWO_D, QUAD>;
   if (nplanes <= 0) return SFS_OK;
   SFS_TRY(ensure_smem_attr(kernel, F::SMEM));
   return launch_pdl(kernel, dim3(nplanes, std::max(1, d_batch)), dim3(F::NT), F::SMEM, st, args...);
@@ -1222,8 +1372,8 @@ int launch_build_table(const PlaneDims& d, const float2* tof, const float* gdir,
                        const float* amp, const int32_t* bins, float2* table,
                        cudaStream_t st) {
   return dispatch_plane(d, [&]<int P, bool TD>() {
-    return launch_plane<P, TD>(build_table_kernel<P, TD>, d.U * d.Nz, 1, st, d, tof, gdir,
-                               amp, bins, table);
+    return launch_plane<P, TD, false>(build_table_kernel<P, TD>, d.U * d.Nz, 1, st, d, tof, gdir,
+                                      amp, bins, table);
   });
 }
 
@@ -1383,7 +1533,7 @@ int launch_contract_adj(const PlaneDims& d, const float2* table, const float2* R
 int prepare_kernels(const PlaneDims& d) {
   SFS_TRY(dispatch_plane(d, [&]<int P, bool TD>() -> int {
     constexpr int sm = PlaneFFT<P, TD>::SMEM;
-    SFS_TRY(ensure_smem_attr(build_table_kernel<P, TD>, sm));
+    SFS_TRY(ensure_smem_attr(build_table_kernel<P, TD>, PlaneFFT<P, TD, false>::SMEM));
     SFS_TRY(ensure_smem_attr(fwd_planes_kernel<P, TD>, sm));
     SFS_TRY(ensure_smem_attr(inv_gather_kernel<P, TD>, sm));
     SFS_TRY(ensure_smem_attr(inv_resid_fwd_kernel<P, TD>, sm));
