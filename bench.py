@@ -53,6 +53,8 @@ def parse():
                     help="skip the BF16 / BF16X2 vs FP32 time-to-same-NMSE study")
     ap.add_argument("--batch-scenes", type=int, default=16,
                     help="scenes of the batched-serving measurement (0 skips it)")
+    ap.add_argument("--crb-trials", type=int, default=50,
+                    help="trials per random strategy of the Cramer-Rao study (0 skips it)")
     ap.add_argument("--serving-scenes", type=int, default=256,
                     help="scenes of the mixed-geometry serving measurement (0 skips it)")
     ap.add_argument("--learned-steps", type=int, default=400,
@@ -179,6 +181,45 @@ def batched_study(sfs, torch, geom, op, args, w, iters, L, flush, stream, seed):
                               # two plane launches; contractions per group of 4 scenes
                               # (16-bit) or per scene (FP32), forward and adjoint
                               "launches_per_iter": 2 + 2 * (B if mode == "fp32" else -(-B // 4))}
+    return out
+
+
+def crb_study(sfs, torch, args, seed):
+    """Sec. VI's bound on locating one scatterer, per sampling strategy and
+    kept bins per position n_f, relative to keeping every bin 0 .. Nt/2:
+    C / C_full per coordinate (mean, min and max over args.crb_trials draws
+    for the random strategies).  All index sets of a (strategy, n_f) pair go
+    to one sfs_crb call; `gpu_s` is the wall time of those calls (FP64 sums
+    on the GPU, host inversion, transfers included)."""
+    cfg = synth.CRB
+    g = sfs.Geometry(**dict(cfg["params"], device=torch.cuda.current_device()))
+    kmax = cfg["params"]["Nt"] // 2
+    full = np.tile(np.arange(kmax + 1, dtype=np.int32), (g.S, 1))
+    c_full, _ = g.crb(full, cfg["pos"], 1.0, 0.0, 1.0)
+    strategies = {"rnd": (sfs.SFS_SEL_RANDOM, False, True), "rnd_f": (sfs.SFS_SEL_RANDOM, True, True),
+                  "max": (sfs.SFS_SEL_MAXIMAL, False, False), "nrg": (sfs.SFS_SEL_ENERGY, False, True),
+                  "nrg_f": (sfs.SFS_SEL_ENERGY, True, True), "contiguous": (sfs.SFS_SEL_CONTIGUOUS, False, False),
+                  "equispaced": (sfs.SFS_SEL_EQUISPACED, False, False)}
+    out = {"setup": "50 x 50 scan, 0.5 mm, c 5920 m/s, fs 20 MHz, fc 3.2 MHz, 65 % bandwidth, theta 30 deg, "
+                    "Nt 512, scatterer 33.3 mm below the centre",
+           "n_f": list(cfg["n_f"]), "crb_full_m2": [float(v) for v in c_full[0]],
+           "ratio": "C / C_full per coordinate (x, y, z)", "strategies": {}}
+    t_gpu, n_sets = 0.0, 0
+    for name, (st, per_pos, randomised) in strategies.items():
+        rec = {"mean": [], "min": [], "max": []}
+        for nf in cfg["n_f"]:
+            T = args.crb_trials if randomised else 1
+            sets = np.stack([g.select_indices(st, nf, per_pos, seed + 7919 * t)[0] for t in range(T)])
+            t0 = time.perf_counter()
+            c, _ = g.crb(sets, cfg["pos"], 1.0, 0.0, 1.0)
+            t_gpu += time.perf_counter() - t0
+            n_sets += T
+            r = c / c_full[0]
+            rec["mean"].append([float(v) for v in r.mean(axis=0)])
+            rec["min"].append([float(v) for v in r.min(axis=0)])
+            rec["max"].append([float(v) for v in r.max(axis=0)])
+        out["strategies"][name] = rec
+    out.update({"index_sets": n_sets, "gpu_s": t_gpu})
     return out
 
 
@@ -663,6 +704,11 @@ def main():
     if rank == 0 and world == 1 and args.batch_scenes > 0:
         batched = batched_study(sfs, torch, geom, op, args, w, iters, L, flush, stream, seed)
 
+    # ---- Cramer-Rao bound of one scatterer per strategy and n_f ----
+    crb = None
+    if rank == 0 and world == 1 and args.crb_trials > 0:
+        crb = crb_study(sfs, torch, args, seed)
+
     # ---- serving mix: scenes of many geometries in one grouped graph launch ----
     serving = None
     if rank == 0 and world == 1 and args.serving_scenes > 0:
@@ -716,6 +762,8 @@ def main():
             line["learned"] = learned
         if serving is not None:
             line["serving"] = serving
+        if crb is not None:
+            line["crb"] = crb
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

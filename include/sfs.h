@@ -367,6 +367,35 @@ int sfs_lipschitz(sfs_operator* op, int max_iter, double rtol, uint64_t seed,
  */
 int sfs_frobenius(const sfs_operator* op, double* fro2_out, double* sigma_hat_out);
 
+/*
+ * Cramer-Rao bound on the location of one scatterer (Sec. VI, Eq. "fim" and
+ * the block inverse after it), for T index sets at once (e.g. the trials of
+ * a random strategy, or several strategies).  The scatterer sits at the
+ * continuous position pos = {x1, y1, z1} [m] (z1 > 0 the depth below the
+ * scan plane) with amplitude amp > 0 and phase `phase`; the data are its
+ * kept-bin coefficients (Eq. (4), Sigma = I) in white circular Gaussian
+ * noise of variance sigma2 > 0.  J = (2 / sigma2) Re{D^H D} over u = (x1, y1,
+ * z1, a, phi), D = d b / d u^T, with d tau / dp = (2 / c) (p - p_s) / R and,
+ * for theta > 0, the derivatives of g = exp(-r^2 / (z1 tan theta)^2).
+ * param_mask selects the location coordinates estimated (bit 0 x1, bit 1 y1,
+ * bit 2 z1; a line scan cannot see y1, a single A-scan neither x1 nor y1);
+ * a and phi are always nuisance parameters.
+ *   idx_host      int32 [T][S][M], each row strictly ascending in 0..Nt/2
+ *   crb_out_host  double [T][3]: diag of the location block of J^-1 [m^2],
+ *                 NaN for coordinates outside the mask
+ *   fim_out_host  double [T][25] or NULL: J row-major over (x1, y1, z1, a,
+ *                 phi), zero rows and columns outside the mask
+ * The sums over the S*M rows run on the geometry's device in FP64 (one
+ * thread per row, per-CTA partial sums added on the host in a fixed order,
+ * so results are reproducible); J is inverted on the host in FP64.  The
+ * information does not depend on the phase.  Synchronises the device.
+ * Errors: SFS_ERR_INVALID_ARG (sizes, rows, amp, sigma2, z1, mask, or a
+ * singular J), SFS_ERR_CUDA, SFS_ERR_OOM.
+ */
+int sfs_crb(const sfs_geometry* g, int T, int M, const int32_t* idx_host, const double* pos,
+            double amp, double phase, double sigma2, int param_mask, double* crb_out_host,
+            double* fim_out_host);
+
 /* Flags of sfs_fista */
 #define SFS_FISTA_WARM_START 1u   /* x_inout_dev holds x_0 on entry (else 0)  */
 #define SFS_FISTA_TIME_KERNELS 2u /* time the two contraction kernels          */

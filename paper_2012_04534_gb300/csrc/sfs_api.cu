@@ -71,12 +71,6 @@ double pulse_alpha(double fc, double frac_bw) {
   return M_PI * (0.5 * frac_bw * fc) / sqrt(log(2.0));
 }
 
-// |H(f)| of h(t) = exp(-alpha^2 t^2 + j 2 pi fc t): (sqrt(pi)/alpha) exp(-(pi (f - fc)/alpha)^2)
-double pulse_mag(double f, double fc, double alpha) {
-  const double a = M_PI * (f - fc) / alpha;
-  return sqrt(M_PI) / alpha * exp(-a * a);
-}
-
 // SplitMix64 (Steele, Lea, Flood 2014): Weyl increment plus the 64-bit mixer.
 struct SplitMix64 {
   uint64_t s;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <string>
@@ -30,6 +31,13 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
     int rc_ = (call);                 \
     if (rc_ != SFS_OK) return rc_;    \
   } while (0)
+
+// |H(f)| of the pulse h(t) = exp(-alpha^2 t^2 + j 2 pi fc t) (Sec. VI):
+// (sqrt(pi) / alpha) exp(-(pi (f - fc) / alpha)^2).
+inline double pulse_mag(double f, double fc, double alpha) {
+  const double a = M_PI * (f - fc) / alpha;
+  return sqrt(M_PI) / alpha * exp(-a * a);
+}
 
 // Largest lateral FFT side held in one CTA's shared memory (a 128 x 129
 // padded c64 plane is 132 KB).

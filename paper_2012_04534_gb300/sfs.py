@@ -63,7 +63,7 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_lista_create", "sfs_lista_destroy", "sfs_lista_info", "sfs_lista_set_params",
            "sfs_lista_get_params", "sfs_lista_load_params_dev", "sfs_lista_forward",
            "sfs_lista_backward", "sfs_lista_nmse", "sfs_lista_adam", "sfs_frobenius",
-           "sfs_fista_grouped",
+           "sfs_fista_grouped", "sfs_crb",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
            "sfs_set_wait_timeout_ns",
            "sfs_inject_wait_timeout", "sfs_check_status", "sfs_last_error", "sfs_version")
@@ -129,6 +129,7 @@ def lib():
         "sfs_max_abs_AH": [vp, vp, P(dbl), vp],
         "sfs_frobenius": [vp, P(dbl), P(dbl)],
         "sfs_fista_grouped": [i32, P(vp), P(ctypes.c_int32), P(vp), P(dbl), dbl, i32, P(vp), vp],
+        "sfs_crb": [vp, i32, i32, P(ctypes.c_int32), P(dbl), dbl, dbl, dbl, i32, P(dbl), P(dbl)],
         "sfs_apply_A_batched": [vp, i32, vp, vp, vp],
         "sfs_apply_AH_batched": [vp, i32, vp, vp, vp],
         "sfs_fista_batched": [vp, i32, vp, dbl, dbl, i32, vp, vp],
@@ -338,6 +339,24 @@ class Geometry:
 
     def select_indices(self, strategy, M, per_position=True, seed=0):
         return sfs_select_indices(self.handle, strategy, M, per_position, seed, self.S)
+
+    def crb(self, idx, pos, amp=1.0, phase=0.0, sigma2=1.0, mask=7):
+        """sfs_crb: idx int32 [T][S][M] (or [S][M]); returns (crb [T][3] in
+        m^2, NaN outside mask; fim [T][5][5])."""
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        if idx.ndim == 2:
+            idx = idx[None]
+        T, S, M = idx.shape
+        if S != self.S:
+            raise ValueError("index sets must have S = %d rows" % self.S)
+        c = np.empty((T, 3), dtype=np.float64)
+        J = np.empty((T, 5, 5), dtype=np.float64)
+        p = (ctypes.c_double * 3)(*[float(v) for v in pos])
+        _check(lib().sfs_crb(self.handle, T, M, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), p,
+                             float(amp), float(phase), float(sigma2), int(mask),
+                             c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             J.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return c, J
 
     def __del__(self):
         h = getattr(self, "handle", None)

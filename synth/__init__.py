@@ -59,6 +59,16 @@ SERVING = dict(grids=(16, 32, 48, 64), depths=(64, 128, 256), Ms=(32, 64, 128), 
                snr_db=20.0, iters=200)
 
 
+# Cramer-Rao study: the simulation setup of Sec. VII-A's parameter table
+# (50 x 50 scan at 0.5 mm, c = 5920 m/s, fs = 20 MHz, fc = 3.2 MHz, 30 deg
+# directivity; its pulse-width entry is garbled, 65 % fractional bandwidth
+# is the reading), Nt = 512, one scatterer 33.3 mm below the scan centre as
+# in Sec. VI; n_f kept bins per position.
+CRB = dict(params=dict(Nx=50, Ny=50, dx=0.5e-3, dy=0.5e-3, Nz=50, z0=29.6e-3, dz=0.15e-3, c=5920.0,
+                       fs=20e6, Nt=512, fc=3.2e6, frac_bw=0.65, theta=math.radians(30.0)),
+           pos=(12.25e-3, 12.25e-3, 33.3e-3), n_f=(1, 2, 4, 8, 16, 32), trials=50)
+
+
 def serving_classes():
     """All (grid, depth, M, Nt) classes of the serving mix."""
     out = []
