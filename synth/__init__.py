@@ -146,6 +146,13 @@ def scene(shape, n_scatter=None, amp="uniform", seed=0, p_bernoulli=None,
     return x.reshape(shape)
 
 
+def rademacher(shape, seed=0):
+    """Independent uniform draws from {-1, +1} (int8): the mixing sequences
+    xi of Sec. III-A's random sampling."""
+    rng = np.random.default_rng(seed)
+    return (2 * rng.integers(0, 2, size=shape) - 1).astype(np.int8)
+
+
 def unit_noise(shape, seed=0):
     """Circular complex Gaussian noise with E|n|^2 = 1, complex128."""
     rng = np.random.default_rng(seed)
