@@ -396,6 +396,42 @@ int sfs_crb(const sfs_geometry* g, int T, int M, const int32_t* idx_host, const 
             double amp, double phase, double sigma2, int param_mask, double* crb_out_host,
             double* fim_out_host);
 
+/*
+ * Rademacher mixing, Phi_s = S_s F Sigma_s with Sigma_s = Diag{xi_s}, xi_s in
+ * {-1, 1}^Nt (Sec. II-B, Eq. "compressed_model"; Sec. III-A's random
+ * sampling).  Sigma_s acts on the time samples of A-scan s, so each kept
+ * coefficient mixes every bin of that A-scan.  The A-scan is taken
+ * band-limited to the candidate band C of the selection:
+ *   y_s[m] = (1/Nt) sum_{u in C} Xi_s[(k_m - k_u) mod Nt] (A_band x)_s[u],
+ * Xi_s = DFT(xi_s), where A_band is an ordinary operator keeping every bin
+ * of C at every position (idx rows all equal to C).  A_mix = Mix o A_band,
+ * A_mix^H = A_band^H o Mix^H, Mix generated per position from Xi_s.
+ *   band      operator with identical index rows (its union = C); not owned,
+ *             must outlive the mixing object; calls on the two must not
+ *             overlap (they share the band operator's workspace)
+ *   idx_host  int32 [S][M] kept bins, rows strictly ascending in 0..Nt/2
+ *   xi_host   int8 [S][Nt], entries +1 or -1 (the random draws are inputs)
+ * Xi_s is computed on the device in FP64 and stored as c64 (S Nt values).
+ * Errors: SFS_ERR_INVALID_ARG (band rows differ, bad rows or signs, Nt >
+ * 8192), SFS_ERR_CUDA, SFS_ERR_OOM.
+ */
+typedef struct sfs_mixing sfs_mixing;  /* opaque, library owned */
+int sfs_mixing_create(sfs_operator* band, int M, const int32_t* idx_host, const int8_t* xi_host,
+                      sfs_mixing** out);
+int sfs_mixing_destroy(sfs_mixing* mx);
+/* y = A_mix x: x c64 [Nz][Ny][Nx], y c64 [S][M] (device, 16-byte aligned). */
+int sfs_apply_A_mixed(sfs_mixing* mx, const void* x_dev, void* y_dev, void* stream);
+/* x = A_mix^H y. */
+int sfs_apply_AH_mixed(sfs_mixing* mx, const void* y_dev, void* x_dev, void* stream);
+/* L >= ||A_mix||^2 by power iteration (as sfs_lipschitz; syncs each step). */
+int sfs_lipschitz_mixed(sfs_mixing* mx, int max_iter, double rtol, uint64_t seed, double safety,
+                        double* L_out, void* stream);
+/* FISTA (Algorithm 1) on A_mix from x_0 = 0, lambda < 0 meaning the mu rule
+ * lambda = -lambda ||A_mix^H y||_inf; six kernels per iteration, replayed as
+ * one CUDA graph per iteration count. */
+int sfs_fista_mixed(sfs_mixing* mx, const void* y_dev, double lambda, double L, int iters,
+                    void* x_dev, void* stream);
+
 /* Flags of sfs_fista */
 #define SFS_FISTA_WARM_START 1u   /* x_inout_dev holds x_0 on entry (else 0)  */
 #define SFS_FISTA_TIME_KERNELS 2u /* time the two contraction kernels          */

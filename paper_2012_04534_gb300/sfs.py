@@ -63,7 +63,8 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_lista_create", "sfs_lista_destroy", "sfs_lista_info", "sfs_lista_set_params",
            "sfs_lista_get_params", "sfs_lista_load_params_dev", "sfs_lista_forward",
            "sfs_lista_backward", "sfs_lista_nmse", "sfs_lista_adam", "sfs_frobenius",
-           "sfs_fista_grouped", "sfs_crb",
+           "sfs_fista_grouped", "sfs_crb", "sfs_mixing_create", "sfs_mixing_destroy",
+           "sfs_apply_A_mixed", "sfs_apply_AH_mixed", "sfs_lipschitz_mixed", "sfs_fista_mixed",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
            "sfs_set_wait_timeout_ns",
            "sfs_inject_wait_timeout", "sfs_check_status", "sfs_last_error", "sfs_version")
@@ -130,6 +131,12 @@ def lib():
         "sfs_frobenius": [vp, P(dbl), P(dbl)],
         "sfs_fista_grouped": [i32, P(vp), P(ctypes.c_int32), P(vp), P(dbl), dbl, i32, P(vp), vp],
         "sfs_crb": [vp, i32, i32, P(ctypes.c_int32), P(dbl), dbl, dbl, dbl, i32, P(dbl), P(dbl)],
+        "sfs_mixing_create": [vp, i32, P(ctypes.c_int32), P(ctypes.c_int8), P(vp)],
+        "sfs_mixing_destroy": [vp],
+        "sfs_apply_A_mixed": [vp, vp, vp, vp],
+        "sfs_apply_AH_mixed": [vp, vp, vp, vp],
+        "sfs_lipschitz_mixed": [vp, i32, dbl, u64, dbl, P(dbl), vp],
+        "sfs_fista_mixed": [vp, vp, dbl, dbl, i32, vp, vp],
         "sfs_apply_A_batched": [vp, i32, vp, vp, vp],
         "sfs_apply_AH_batched": [vp, i32, vp, vp, vp],
         "sfs_fista_batched": [vp, i32, vp, dbl, dbl, i32, vp, vp],
@@ -495,3 +502,59 @@ class Operator:
 
     def __del__(self):
         self.close()
+
+
+class Mixing:
+    """A_mix = Mix o A_band (sfs_mixing): Rademacher mixing of each A-scan
+    before the DFT and selection.  band: Operator keeping every bin of its
+    band at every position; idx: int32 [S][M] kept bins; xi: int8 [S][Nt]."""
+
+    def __init__(self, band: "Operator", idx, xi):
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        xi = np.ascontiguousarray(xi, dtype=np.int8)
+        S, M = idx.shape
+        if S != band.S or xi.shape != (band.S, band.geom.Nt):
+            raise ValueError("idx must be [S][M] and xi [S][Nt]")
+        self.band = band
+        self.S, self.M, self.V = S, M, band.V
+        self.shape_x = band.shape_x
+        self.shape_y = (S, M)
+        h = ctypes.c_void_p()
+        _check(lib().sfs_mixing_create(band.handle, M, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       xi.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), ctypes.byref(h)))
+        self.handle = h
+
+    def _new(self, shape):
+        import torch
+        return torch.empty(shape, dtype=torch.complex64, device="cuda:%d" % self.band.device)
+
+    def apply_A(self, x, out=None, stream=None):
+        y = self._new(self.shape_y) if out is None else out
+        _check(lib().sfs_apply_A_mixed(self.handle, _dev_ptr(x, self.V, "x"), _dev_ptr(y, self.S * self.M, "y"),
+                                       _stream_ptr(stream, x.device)))
+        return y
+
+    def apply_AH(self, y, out=None, stream=None):
+        x = self._new(self.shape_x) if out is None else out
+        _check(lib().sfs_apply_AH_mixed(self.handle, _dev_ptr(y, self.S * self.M, "y"), _dev_ptr(x, self.V, "x"),
+                                        _stream_ptr(stream, y.device)))
+        return x
+
+    def lipschitz(self, max_iter=300, rtol=1e-6, seed=0, safety=1e-3, stream=None):
+        out = ctypes.c_double()
+        rc = _check(lib().sfs_lipschitz_mixed(self.handle, max_iter, rtol, seed, safety, ctypes.byref(out),
+                                              _stream_ptr(stream, None)), allow=(SFS_ERR_NOT_CONVERGED,))
+        return out.value, rc == SFS_OK
+
+    def fista(self, y, lam, L, iters, x=None, stream=None):
+        """lam >= 0: lambda; lam < 0: lambda = -lam * ||A_mix^H y||_inf."""
+        x = self._new(self.shape_x) if x is None else x
+        _check(lib().sfs_fista_mixed(self.handle, _dev_ptr(y, self.S * self.M, "y"), float(lam), float(L),
+                                     int(iters), _dev_ptr(x, self.V, "x"), _stream_ptr(stream, y.device)))
+        return x
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.sfs_mixing_destroy(h)
+            self.handle = None
