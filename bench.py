@@ -53,6 +53,8 @@ def parse():
                     help="skip the BF16 / BF16X2 vs FP32 time-to-same-NMSE study")
     ap.add_argument("--batch-scenes", type=int, default=16,
                     help="scenes of the batched-serving measurement (0 skips it)")
+    ap.add_argument("--no-mixing", dest="mixing", action="store_false",
+                    help="skip the Rademacher-mixing measurement")
     ap.add_argument("--crb-trials", type=int, default=50,
                     help="trials per random strategy of the Cramer-Rao study (0 skips it)")
     ap.add_argument("--serving-scenes", type=int, default=256,
@@ -184,6 +186,45 @@ def batched_study(sfs, torch, geom, op, args, w, iters, L, flush, stream, seed):
     return out
 
 
+def mixing_study(sfs, torch, geom, op, args, w, iters, x_true, flush, stream, seed):
+    """The workload measured through Rademacher-mixed A-scans (Phi_rnd,m,f:
+    own xi_s and own random bins per position): band operator (every bin of
+    the candidate band at every position) plus the mixing object; FISTA with
+    the same iterations and mu rule, L by power iteration on A_mix.  Reports
+    the device time of a solve (L2 flushed first, best of 3), FISTA it/s and
+    the NMSE against the true scene, beside the unmixed solve's NMSE."""
+    Nt = w["Nt"]
+    band_lo, band_hi = geom.select_indices(sfs.SFS_SEL_RANDOM, w["M"], True, seed)[1]
+    band = np.arange(band_lo, band_hi + 1, dtype=np.int32)
+    bop = sfs.Operator.from_indices(geom, np.tile(band, (geom.S, 1)))
+    xi = synth.rademacher((geom.S, Nt), seed=seed + 4242)
+    mx = sfs.Mixing(bop, op.idx, xi)
+    xt = torch.from_numpy(x_true.astype(np.complex64)).cuda()
+    y0 = mx.apply_A(xt).cpu().numpy().astype(np.complex128)
+    sig = synth.noise_scale(float(np.vdot(y0, y0).real), y0.size, w["snr_db"])
+    y = torch.from_numpy((y0 + sig * synth.unit_noise(y0.shape, seed=seed + 4343)).astype(np.complex64)).cuda()
+    L, _ = mx.lipschitz(max_iter=300, rtol=1e-6, seed=seed, safety=1e-3)
+    x = torch.empty(op.shape_x, dtype=torch.complex64, device="cuda")
+    mx.fista(y, -w["mu"], L, iters, x=x)  # graph capture
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(3):
+        flush.fill_(4)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mx.fista(y, -w["mu"], L, iters, x=x)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b)
+        best = t if best is None else min(best, t)
+    xh = x.cpu().numpy().astype(np.complex128)
+    nmse = float(10 * np.log10(np.linalg.norm(xh - x_true) ** 2 / np.linalg.norm(x_true) ** 2))
+    return {"strategy": "Phi_rnd,m,f (xi_s and bins drawn per position)", "band_bins": int(band.size),
+            "M": int(w["M"]), "iters": iters, "ms_per_solve": best, "fista_it_per_s": iters / (best / 1e3),
+            "nmse_db": nmse, "L": L, "launches_per_iter": 6,
+            "timing": "device time of one solve (lambda rule + iterations), best of 3, L2 flushed first"}
+
+
 def crb_study(sfs, torch, args, seed):
     """Sec. VI's bound on locating one scatterer, per sampling strategy and
     kept bins per position n_f, relative to keeping every bin 0 .. Nt/2:
@@ -255,6 +296,13 @@ def serving_study(sfs, torch, args, flush, stream, seed):
         ys.append(torch.from_numpy(np.stack(yb).astype(np.complex64)).cuda())
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
+    # tile of each class's batched contractions, by the library's autotuner
+    t1 = time.perf_counter()
+    tiles = {}
+    for op_c, n in zip(ops, counts):
+        nb, _ = op_c.autotune(n, reps=3)
+        tiles[str(nb)] = tiles.get(str(nb), 0) + 1
+    t_tune = time.perf_counter() - t1
     iters = sv["iters"]
     xs = sfs.fista_grouped(ops, ys, Ls, -0.05, iters)  # workspaces and graph capture
     torch.cuda.synchronize()
@@ -273,7 +321,7 @@ def serving_study(sfs, torch, args, flush, stream, seed):
             "unit": "scene-iterations/s", "value": total * iters / (statistics.mean(ts) / 1e3),
             "latency_ms_p50": statistics.median(ts), "latency_ms_p99": ts[-1],
             "latency_note": "one graph launch solves every scene; each scene's latency is the launch's",
-            "setup_s": t_setup,
+            "setup_s": t_setup, "autotune_s": t_tune, "tiles_chosen": tiles,
             "mix": "grids {16,32,48,64}^2, depths {64,128,256}, M {32,64,128}, 10 scatterers, 20 dB"}
 
 
@@ -704,6 +752,11 @@ def main():
     if rank == 0 and world == 1 and args.batch_scenes > 0:
         batched = batched_study(sfs, torch, geom, op, args, w, iters, L, flush, stream, seed)
 
+    # ---- Rademacher mixing (Phi_rnd,m) on the same workload ----
+    mixing = None
+    if rank == 0 and world == 1 and args.mixing:
+        mixing = mixing_study(sfs, torch, geom, op, args, w, iters, x_true, flush, stream, seed)
+
     # ---- Cramer-Rao bound of one scatterer per strategy and n_f ----
     crb = None
     if rank == 0 and world == 1 and args.crb_trials > 0:
@@ -764,6 +817,8 @@ def main():
             line["serving"] = serving
         if crb is not None:
             line["crb"] = crb
+        if mixing is not None:
+            line["mixing"] = mixing
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -432,6 +432,25 @@ int sfs_lipschitz_mixed(sfs_mixing* mx, int max_iter, double rtol, uint64_t seed
 int sfs_fista_mixed(sfs_mixing* mx, const void* y_dev, double lambda, double L, int iters,
                     void* x_dev, void* stream);
 
+/*
+ * Tile tuning of the batched 16-bit contractions (BF16 / BF16X2 / FP16 /
+ * FP16X2 operators).  A batched call groups its scenes so that one table
+ * tile serves NB scenes (NB = 1, 2 or 4: an MMA N of 32 NB columns, 64 NB
+ * TMEM columns); by default NB = 4 from three scenes on.
+ * sfs_autotune_batch times `reps` forward + adjoint contraction pairs of
+ * `batch` scenes for each NB up to the batch (CUDA events on a private
+ * stream, after one warm-up pair, on zero spectra), keeps the fastest for
+ * this (operator, batch) and returns it in *nb_out (0 for FP32 / TF32X3
+ * operators, which have nothing to tune); ms_out (may be NULL) receives the
+ * milliseconds per pair for NB = 1, 2, 4 (NaN where not tried).
+ * sfs_set_batch_tile fixes NB (0 restores the default rule).  Results do not
+ * depend on NB: each scene's products and sums are the same.  Both drop the
+ * loops captured for that batch size.  Synchronises the device.
+ * Errors: SFS_ERR_INVALID_ARG, SFS_ERR_CUDA, SFS_ERR_TIMEOUT.
+ */
+int sfs_autotune_batch(sfs_operator* op, int batch, int reps, int32_t* nb_out, double* ms_out);
+int sfs_set_batch_tile(sfs_operator* op, int batch, int nb);
+
 /* Flags of sfs_fista */
 #define SFS_FISTA_WARM_START 1u   /* x_inout_dev holds x_0 on entry (else 0)  */
 #define SFS_FISTA_TIME_KERNELS 2u /* time the two contraction kernels          */

@@ -334,6 +334,7 @@ PlaneDims operator_dims(const sfs_operator* op) {
   d.orbit_rep = op->orbit_rep;
   d.quad = op->quad;
   d.batch = 1;
+  d.nb = 0;
   d.bs_x = op->V;
   d.bs_xh = (long long)op->geo.d.Nz * op->Ns;
   d.bs_yh = (long long)op->nzb * op->Up * op->Ns;
@@ -459,6 +460,8 @@ int enqueue_fista_iterations(sfs_operator* op, int iters, double* obj, bool timi
 PlaneDims batch_dims(const sfs_operator* op, int batch) {
   PlaneDims d = dims_of(op);
   d.batch = batch;
+  for (const auto& bt : op->batch_tile)
+    if (bt.first == batch) d.nb = bt.second;
   d.pm_x = op->f16 ? op->bws.pmx : nullptr;
   d.pm_r = op->f16 ? op->bws.pmr : nullptr;
   return d;
@@ -1611,6 +1614,99 @@ int sfs_kernel_times(sfs_operator* op, double* fwd_ms, double* adj_ms, int32_t* 
   SFS_TRY(sfs_stage_times(op, ms4, n_out_host));
   *fwd_ms = ms4[0];
   *adj_ms = ms4[2];
+  return SFS_OK;
+}
+
+
+// Scenes per table tile of a batched 16-bit contraction (0: the default
+// rule).  Loops captured for this batch size are dropped, and grouped loops
+// see a new workspace generation.
+static void set_batch_tile(sfs_operator* op, int batch, int nb) {
+  for (auto it = op->batch_tile.begin(); it != op->batch_tile.end();)
+    it = it->first == batch ? op->batch_tile.erase(it) : it + 1;
+  if (nb) op->batch_tile.push_back({batch, nb});
+  for (auto it = op->bgraphs.begin(); it != op->bgraphs.end();) {
+    if (it->batch == batch) {
+      cudaGraphExecDestroy(it->exec);
+      it = op->bgraphs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  ++op->bws_gen;
+}
+
+int sfs_set_batch_tile(sfs_operator* op, int batch, int nb) {
+  clear_error();
+  if (!op || batch < 1 || batch > SFS_MAX_BATCH || (nb != 0 && nb != 1 && nb != 2 && nb != 4)) {
+    set_error("invalid argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(op->geo.d.device);
+  set_batch_tile(op, batch, nb);
+  return SFS_OK;
+}
+
+int sfs_autotune_batch(sfs_operator* op, int batch, int reps, int32_t* nb_out, double* ms_out) {
+  clear_error();
+  if (!op || batch < 1 || batch > SFS_MAX_BATCH || reps < 1 || !nb_out) {
+    set_error("invalid argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  if (ms_out) ms_out[0] = ms_out[1] = ms_out[2] = NAN;
+  *nb_out = 0;
+  if (op->tc != 2) return SFS_OK;  // only the 16-bit contractions share table tiles
+  DeviceScope scope(op->geo.d.device);
+  SFS_TRY(ensure_batch(op, batch));
+  const sfs::BatchWorkspace& w = op->bws;
+  PlaneDims d = batch_dims(op, batch);
+  // defined inputs (zero spectra; zero maxima give scale 1 in FP16 modes)
+  SFS_CUDA(cudaMemset(w.Xh, 0, (size_t)batch * d.bs_xh * sizeof(float2)));
+  SFS_CUDA(cudaMemset(w.Rh, 0, (size_t)batch * d.bs_rh * sizeof(float2)));
+  if (w.pmx) SFS_CUDA(cudaMemset(w.pmx, 0, (size_t)batch * d.bs_pmx * sizeof(float)));
+  if (w.pmr) SFS_CUDA(cudaMemset(w.pmr, 0, (size_t)batch * d.bs_pmr * sizeof(float)));
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SFS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  int rc = SFS_OK;
+  double best_ms = 0.0;
+  int best = 0;
+  const int cand[3] = {1, 2, 4};
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    rc = cuda_fail(cudaGetLastError(), "cudaEventCreate", __FILE__, __LINE__);
+  }
+  for (int c = 0; c < 3 && rc == SFS_OK; ++c) {
+    if (cand[c] > 1 && cand[c] / 2 >= batch) break;  // a tile wider than the batch needs
+    d.nb = cand[c];
+    if ((rc = prepare_kernels(d)) != SFS_OK) break;
+    for (int r = -1; r < reps && rc == SFS_OK; ++r) {  // r = -1: warm-up
+      if (r == 0) cudaEventRecord(e0, st);
+      rc = launch_contract_fwd(d, op->table, w.Xh, w.Yh, op->ws.err, st);
+      if (rc == SFS_OK) rc = launch_contract_adj(d, op->table, w.Rh, w.Gh, op->ws.err, st);
+    }
+    if (rc != SFS_OK) break;
+    cudaEventRecord(e1, st);
+    const cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "tuning run", __FILE__, __LINE__);
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double per = (double)ms / reps;
+    if (ms_out) ms_out[c] = per;
+    if (!best || per < best_ms) {
+      best = cand[c];
+      best_ms = per;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  SFS_TRY(rc);
+  SFS_TRY(check_err_flag(op, nullptr));
+  set_batch_tile(op, batch, best);
+  *nb_out = best;
   return SFS_OK;
 }
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/sfs.h"
@@ -165,7 +166,8 @@ struct sfs_operator {
   // batched FISTA: workspace and captured loops keyed by (iterations, scenes)
   sfs::BatchWorkspace bws;
   uint64_t uid = 0;      // process-unique operator id (keys of grouped graphs)
-  uint64_t bws_gen = 0;  // bumped whenever the batched workspace is reallocated
+  uint64_t bws_gen = 0;  // bumped whenever the batched workspace is reallocated (or retuned)
+  std::vector<std::pair<int, int>> batch_tile;  // (batch, scenes per table tile) chosen by tuning
   struct BatchGraphEntry {
     int iters;
     int batch;
@@ -213,6 +215,7 @@ struct PlaneDims {
   // plane kernels, blockIdx.y = scene), and the per-scene strides (elements)
   // of the batched buffers; batch = 1 for single-scene calls.
   int batch;
+  int nb;               // 16-bit contractions: scenes per table tile (1, 2, 4), 0 = default rule
   long long bs_x;       // x, x_k, gamma: V
   long long bs_xh;      // X^: Nz * Ns
   long long bs_yh;      // forward contraction output: nzb * Up * Ns

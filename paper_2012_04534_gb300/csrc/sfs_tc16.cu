@@ -627,8 +627,13 @@ int launch_h(const PlaneDims& d, const CUtensorMap& tab, const CUtensorMap& spec
                     out, out_stride, nscene, d, nmt, nch, nunits, pm, err);
 }
 
-// Scene group size of a batched call: one table tile serves up to 4 scenes.
-int group_of(int batch) { return batch >= 3 ? 4 : batch; }
+// Scene group size of a batched call: one table tile serves up to 4 scenes
+// (default: 4 from three scenes on), unless tuning fixed it (d.nb).
+int group_of(const PlaneDims& d) {
+  const int batch = std::max(1, d.batch);
+  if (d.nb == 1 || d.nb == 2 || d.nb == 4) return d.nb;
+  return batch >= 3 ? 4 : batch;
+}
 
 // One contraction launch per group of scenes: spectra of the group from
 // `spec_base` (scene stride spec_stride elements, `rows` rows), outputs from
@@ -637,7 +642,7 @@ template <bool FWD>
 int launch_groups(const PlaneDims& d, const CUtensorMap& tab, const CUtensorMap* cached, const float2* base,
                   long long spec_stride, int rows, int box_rows, float2* out, long long out_stride,
                   int* err, cudaStream_t st) {
-  const int B = std::max(1, d.batch), NB = group_of(B);
+  const int B = std::max(1, d.batch), NB = group_of(d);
   for (int g0 = 0; g0 < B; g0 += NB) {
     CUtensorMap local;
     const CUtensorMap* spec = cached;
@@ -718,7 +723,7 @@ int prepare_one() {
 }
 
 int prepare_tc16_kernels(const PlaneDims& d) {
-  const int NB = group_of(std::max(1, d.batch));
+  const int NB = group_of(d);
   if (d.nparts == 2)
     return NB == 1 ? prepare_one<2, 1>() : NB == 2 ? prepare_one<2, 2>() : prepare_one<2, 4>();
   return NB == 1 ? prepare_one<1, 1>() : NB == 2 ? prepare_one<1, 2>() : prepare_one<1, 4>();

@@ -65,6 +65,7 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_lista_backward", "sfs_lista_nmse", "sfs_lista_adam", "sfs_frobenius",
            "sfs_fista_grouped", "sfs_crb", "sfs_mixing_create", "sfs_mixing_destroy",
            "sfs_apply_A_mixed", "sfs_apply_AH_mixed", "sfs_lipschitz_mixed", "sfs_fista_mixed",
+           "sfs_autotune_batch", "sfs_set_batch_tile",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
            "sfs_set_wait_timeout_ns",
            "sfs_inject_wait_timeout", "sfs_check_status", "sfs_last_error", "sfs_version")
@@ -133,6 +134,8 @@ def lib():
         "sfs_crb": [vp, i32, i32, P(ctypes.c_int32), P(dbl), dbl, dbl, dbl, i32, P(dbl), P(dbl)],
         "sfs_mixing_create": [vp, i32, P(ctypes.c_int32), P(ctypes.c_int8), P(vp)],
         "sfs_mixing_destroy": [vp],
+        "sfs_autotune_batch": [vp, i32, i32, P(ctypes.c_int32), P(dbl)],
+        "sfs_set_batch_tile": [vp, i32, i32],
         "sfs_apply_A_mixed": [vp, vp, vp, vp],
         "sfs_apply_AH_mixed": [vp, vp, vp, vp],
         "sfs_lipschitz_mixed": [vp, i32, dbl, u64, dbl, P(dbl), vp],
@@ -449,6 +452,17 @@ class Operator:
                                        float(lam), float(L), int(iters),
                                        _dev_ptr(x, B * self.V, "x"), _stream_ptr(stream, y.device)))
         return x
+
+    def autotune(self, batch, reps=5):
+        """sfs_autotune_batch: (chosen scenes per table tile, ms per forward +
+        adjoint pair for 1, 2, 4)."""
+        nb = ctypes.c_int32()
+        ms = (ctypes.c_double * 3)()
+        _check(lib().sfs_autotune_batch(self.handle, int(batch), int(reps), ctypes.byref(nb), ms))
+        return nb.value, [ms[0], ms[1], ms[2]]
+
+    def set_batch_tile(self, batch, nb):
+        _check(lib().sfs_set_batch_tile(self.handle, int(batch), int(nb)))
 
     def frobenius(self):
         """(||A||_F^2, sigma_hat) of Sec. IV-C (host computation)."""

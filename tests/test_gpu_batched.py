@@ -175,3 +175,33 @@ def test_grouped_solve_equals_per_operator_batched_solves(sfs):
         assert torch.equal(a, b)
     with pytest.raises(sfs.SfsError):
         sfs.fista_grouped([ops[0], ops[0]], [ys[0], ys[0]], [Ls[0], Ls[0]], -0.05, 5)
+
+
+@pytest.mark.parametrize("mode", ["bf16", "fp16"])
+def test_batch_tile_choice_keeps_results_and_autotune_picks_one(sfs, mode):
+    """Five scenes with one table tile serving 1, 2 or 4 of them: each
+    scene's products and sums are the same, so A, A^H and FISTA agree bit for
+    bit; sfs_autotune_batch picks one of the tiles it timed."""
+    params = geom_params(Nx=12, Ny=10, Nz=40, dz=0.15e-3, Nt=256)
+    go = oracle_geometry(params)
+    idx = O.select_indices(go, O.SEL_RANDOM, 10, True, 71)
+    g = sfs.Geometry(**params)
+    op = sfs.Operator.from_indices(g, idx, precision=sfs.PRECISION_NAMES[mode])
+    B = 5
+    rng = np.random.default_rng(72)
+    x = to_dev(crandn(rng, B, g.Nz, g.Ny, g.Nx))
+    y = to_dev(crandn(rng, B, g.S, 10))
+    outs = []
+    for nb in (1, 2, 4):
+        op.set_batch_tile(B, nb)
+        outs.append((to_host(op.apply_A_batched(x)), to_host(op.apply_AH_batched(y)),
+                     to_host(op.fista_batched(y, -0.05, 1.0e9, 20))))
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
+    nb, ms = op.autotune(B, reps=3)
+    assert nb in (1, 2, 4)
+    assert all(np.isfinite(ms)) and ms[[1, 2, 4].index(nb)] == min(ms)
+    assert np.array_equal(to_host(op.fista_batched(y, -0.05, 1.0e9, 20)), outs[0][2])
+    op32 = sfs.Operator.from_indices(g, idx)
+    assert op32.autotune(B)[0] == 0
