@@ -31,6 +31,9 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
   multilevel_toeplitz pinned: the worked 2-level example printed in Sec. IV-B
   LateralFFTOperator  pinned: equal to dense_A / dense_A^H to 1e-12
   power_iteration     pinned: numpy SVD on tiny grids, Frobenius bounds
+  fista_backtracking  pinned: with L0 >= ||A||^2 it never backtracks and equals
+                      fista, L_k <= eta ||A||^2 and nondecreasing, the
+                      Beck-Teboulle rate bound with eta ||A||^2
   fista               pinned: lambda >= ||A^H y||_inf gives 0, KKT
                       certificate of the LASSO optimum, Beck-Teboulle rate
                       bound, exact support recovery of isolated scatterers
@@ -568,6 +571,44 @@ def fista(apply_A: Callable, apply_AH: Callable, y, lam: float, L: float,
         if history is not None:
             r = apply_A(x) - y
             history.append(0.5 * np.vdot(r, r).real + lam * np.abs(x).sum())
+    return x_prev
+
+
+def fista_backtracking(apply_A: Callable, apply_AH: Callable, y, lam: float, L0: float,
+                       eta: float, iters: int, L_history: Optional[list] = None):
+    """FISTA with backtracking (Sec. IV-C, "Backtracking": a lower bound
+    sigma_low^2 = L0 and a factor eta > 1 instead of sigma_max; the method of
+    the cited Beck-Teboulle paper).  With f(x) = 1/2 ||A x - y||^2, F = f +
+    lam ||x||_1 and p_L(g) = tau_{lam/L}(g - grad f(g) / L), step k takes the
+    smallest i >= 0 such that L' = eta^i L_{k-1} satisfies
+        F(p_L'(gamma_k)) <= Q_L'(p_L'(gamma_k), gamma_k),
+        Q_L(x, g) = f(g) + Re<x - g, grad f(g)> + L/2 ||x - g||^2 + lam ||x||_1,
+    then L_k = L', x_k = p_{L_k}(gamma_k) and the momentum of Algorithm 1.
+    Returns x_K; ``L_history`` (if a list) receives L_k per iteration."""
+    y = np.asarray(y, dtype=np.complex128)
+    x_prev = np.zeros_like(np.asarray(apply_AH(y), dtype=np.complex128))
+    gamma = x_prev.copy()
+    beta = fista_momentum(iters)
+    L = float(L0)
+
+    def f(v):
+        r = apply_A(v) - y
+        return 0.5 * float(np.vdot(r, r).real)
+
+    for k in range(iters):
+        grad = apply_AH(apply_A(gamma) - y)
+        fg = f(gamma)
+        while True:
+            x = soft_threshold(gamma - grad / L, lam / L)
+            d = x - gamma
+            q = fg + float(np.vdot(d, grad).real) + 0.5 * L * float(np.vdot(d, d).real)
+            if f(x) <= q:     # the l1 terms of F and Q are equal and cancel
+                break
+            L *= eta
+        gamma = x + beta[k] * (x - x_prev)
+        x_prev = x
+        if L_history is not None:
+            L_history.append(L)
     return x_prev
 
 

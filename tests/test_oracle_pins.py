@@ -426,3 +426,38 @@ def test_soft_threshold_special_cases():
     np.testing.assert_allclose(out, [0, (3 + 4j) * 0.8, 0, -1.0], atol=1e-15)
     beta = O.fista_momentum(4)
     assert beta[0] == 0.0 and np.all(np.diff(beta) > 0)
+
+
+# -------------------------------------------------- FISTA with backtracking ---
+
+def test_backtracking_without_backtracks_is_fista():
+    """L0 at or above ||A||^2: f is L0-smooth, so every first trial is
+    accepted and the iterates are FISTA's with L = L0, bit for bit."""
+    g, op, x_true, y, L = _small_problem(seed=6)
+    lam = 0.05 * float(np.abs(op.apply_AH(y)).max())
+    hist = []
+    xb = O.fista_backtracking(op.apply_A, op.apply_AH, y, lam, L * 1.5, 2.0, 40, L_history=hist)
+    xf = O.fista(op.apply_A, op.apply_AH, y, lam, L * 1.5, 40)
+    assert hist == [L * 1.5] * 40
+    assert np.array_equal(xb, xf)
+
+
+def test_backtracking_step_bounds_and_rate():
+    """From a crude lower bound: L_k never falls, never exceeds eta ||A||^2,
+    and F(x_k) - F* <= 2 eta ||A||^2 ||x*||^2 / (k+1)^2 (Beck-Teboulle's
+    bound for the backtracking variant)."""
+    g, op, x_true, y, L = _small_problem(seed=7)
+    lam = 0.05 * float(np.abs(op.apply_AH(y)).max())
+    eta = 1.7
+    hist = []
+    O.fista_backtracking(op.apply_A, op.apply_AH, y, lam, L / 500.0, eta, 80, L_history=hist)
+    assert hist[0] > L / 500.0                     # it did backtrack
+    assert all(b >= a for a, b in zip(hist, hist[1:]))
+    assert max(hist) <= eta * L * (1 + 1e-9)
+    x_star = O.fista(op.apply_A, op.apply_AH, y, lam, L * 1.001, 8000)
+    F_star = O.lasso_objective(op.apply_A, y, lam, x_star)
+    r0 = float(np.vdot(x_star, x_star).real)
+    for k in (10, 40, 80):
+        xk = O.fista_backtracking(op.apply_A, op.apply_AH, y, lam, L / 500.0, eta, k)
+        Fk = O.lasso_objective(op.apply_A, y, lam, xk)
+        assert Fk - F_star <= 2 * eta * L * r0 / (k + 1) ** 2 + 1e-9 * abs(F_star)
