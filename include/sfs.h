@@ -451,6 +451,21 @@ int sfs_fista_mixed(sfs_mixing* mx, const void* y_dev, double lambda, double L, 
 int sfs_autotune_batch(sfs_operator* op, int batch, int reps, int32_t* nb_out, double* ms_out);
 int sfs_set_batch_tile(sfs_operator* op, int batch, int nb);
 
+/*
+ * FISTA with backtracking (Sec. IV-C, "Backtracking"): instead of L >=
+ * sigma_max^2, a lower bound L0 (sigma_low^2) and a factor eta > 1.  Step k
+ * takes the smallest L' = eta^i L_{k-1} with F(p_L') <= Q_L'(p_L', gamma_k)
+ * (the cited Beck-Teboulle rule), evaluated in its exact equivalent form
+ * for the quadratic data term, ||A d||^2 <= L' ||d||^2 with d = p_L' -
+ * gamma_k.  Each trial costs one forward apply and one host read (the
+ * loop is host-driven, not graph-replayed).  x_0 = 0; lambda < 0 means the
+ * mu rule; L_hist_host (may be NULL) receives L_k per iteration.
+ * Errors: SFS_ERR_INVALID_ARG, SFS_ERR_NOT_CONVERGED (no step within 200
+ * trials), SFS_ERR_NON_FINITE, SFS_ERR_TIMEOUT, SFS_ERR_CUDA.
+ */
+int sfs_fista_backtracking(sfs_operator* op, const void* y_dev, double lambda, double L0, double eta,
+                           int iters, void* x_dev, double* L_hist_host, void* stream);
+
 /* Flags of sfs_fista */
 #define SFS_FISTA_WARM_START 1u   /* x_inout_dev holds x_0 on entry (else 0)  */
 #define SFS_FISTA_TIME_KERNELS 2u /* time the two contraction kernels          */

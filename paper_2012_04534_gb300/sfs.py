@@ -65,7 +65,7 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_lista_backward", "sfs_lista_nmse", "sfs_lista_adam", "sfs_frobenius",
            "sfs_fista_grouped", "sfs_crb", "sfs_mixing_create", "sfs_mixing_destroy",
            "sfs_apply_A_mixed", "sfs_apply_AH_mixed", "sfs_lipschitz_mixed", "sfs_fista_mixed",
-           "sfs_autotune_batch", "sfs_set_batch_tile",
+           "sfs_autotune_batch", "sfs_set_batch_tile", "sfs_fista_backtracking",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
            "sfs_set_wait_timeout_ns",
            "sfs_inject_wait_timeout", "sfs_check_status", "sfs_last_error", "sfs_version")
@@ -136,6 +136,7 @@ def lib():
         "sfs_mixing_destroy": [vp],
         "sfs_autotune_batch": [vp, i32, i32, P(ctypes.c_int32), P(dbl)],
         "sfs_set_batch_tile": [vp, i32, i32],
+        "sfs_fista_backtracking": [vp, vp, dbl, dbl, dbl, i32, vp, P(dbl), vp],
         "sfs_apply_A_mixed": [vp, vp, vp, vp],
         "sfs_apply_AH_mixed": [vp, vp, vp, vp],
         "sfs_lipschitz_mixed": [vp, i32, dbl, u64, dbl, P(dbl), vp],
@@ -490,6 +491,16 @@ class Operator:
         sfs_fista(self.handle, _dev_ptr(y, self.S * self.M, "y"), float(lam), float(L), iters,
                   _dev_ptr(x, self.V, "x"), flags, hist, _stream_ptr(stream, y.device))
         return (x, hist) if obj_hist else x
+
+    def fista_backtracking(self, y, lam, L0, eta, iters, x=None, stream=None):
+        """sfs_fista_backtracking: (x, L_k per iteration)."""
+        x = self._new(self.shape_x) if x is None else x
+        hist = np.zeros(max(iters, 1))
+        _check(lib().sfs_fista_backtracking(self.handle, _dev_ptr(y, self.S * self.M, "y"), float(lam),
+                                            float(L0), float(eta), int(iters), _dev_ptr(x, self.V, "x"),
+                                            hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            _stream_ptr(stream, y.device)))
+        return x, hist[:iters]
 
     def kernel_times(self):
         return sfs_kernel_times(self.handle)
