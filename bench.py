@@ -556,15 +556,20 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# Sources that define the contraction kernels or their launch shapes (the
+# FP32, TF32X3 and 16-bit contractions, the plane data they read, their
+# shared headers); a traffic record taken on other versions of these is stale.
+CONTRACTION_SOURCES = ("sfs_kernels.cu", "sfs_tc.cu", "sfs_tc16.cu", "sfs_internal.h", "sfs_launch.h",
+                       "sfs_async.cuh", "sfs_tcgen05.cuh", "sfs_fft.cuh")
+
+
 def kernel_source_hash():
-    """Hash of every kernel source file: a traffic record taken on other
-    sources is stale."""
+    """Hash of the contraction kernels' source files."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2012_04534_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in CONTRACTION_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
