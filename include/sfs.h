@@ -141,7 +141,7 @@ typedef struct sfs_operator_info_t {
 
 /*
  * Geometry.  Validates the descriptor (positive sizes, Nx, Ny <= 64 for a
- * 3-D scan, Nx <= 2048 for a line scan, Nt >= 2, positive pitches, c, fs,
+ * 3-D scan, Nx <= 512 for a line scan, Nt >= 2, positive pitches, c, fs,
  * fc, frac_bw) and stores a copy.  Frees with sfs_destroy_geometry.
  * Errors: SFS_ERR_INVALID_ARG.
  */
