@@ -369,3 +369,32 @@ def test_vol64_full_size_sampled_outputs(sfs, mode):
     if mode == "fp32":
         assert rel_err(ya[rows], ref_y) <= tol
         assert rel_err(xa[vox], ref_x) <= tol
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp16"])
+def test_128_point_batched_fista(sfs, mode):
+    """FISTA on 128 x 128 planes (one 4-CTA cluster per plane in the
+    residual and update kernels), three scenes in one batched call: each
+    equals its single-scene solve, and the FP64 FISTA within 1e-4 (FP32) or
+    4e-3 (FP16 contractions, u = 2^-11 per apply)."""
+    params = geom_params(Nx=40, Ny=36, Nz=10, dz=0.15e-3, Nt=256)
+    go = oracle_geometry(params)
+    idx = O.select_indices(go, O.SEL_RANDOM, 10, True, 41)
+    g = sfs.Geometry(**params)
+    op = sfs.Operator.from_indices(g, idx, precision=sfs.PRECISION_NAMES[mode])
+    ref = O.LateralFFTOperator(go, idx)
+    L, _ = O.power_iteration(ref.apply_A, ref.apply_AH, op.shape_x, 1, max_iter=400, rtol=1e-10)
+    L *= 1.001
+    ys = []
+    for b in range(3):
+        xt = synth.scene(op.shape_x, 4, "uniform", seed=42 + b)
+        y0 = ref.apply_A(xt)
+        sig = synth.noise_scale(float(np.vdot(y0, y0).real), y0.size, 20.0)
+        ys.append((y0 + sig * synth.unit_noise(y0.shape, seed=45 + b)).astype(np.complex64).astype(complex))
+    lam = O.lambda_from_mu(ref.apply_AH, ys[0], 0.05)
+    xb = to_host(op.fista_batched(to_dev(np.stack(ys)), lam, L, 60))
+    for b in range(3):
+        xs = to_host(op.fista(to_dev(ys[b]), lam, L, 60))
+        x_ref = O.fista(ref.apply_A, ref.apply_AH, ys[b], lam, L, 60)
+        assert rel_err(xb[b], xs) <= 1e-6
+        assert rel_err(xb[b], x_ref) <= (1e-4 if mode == "fp32" else 4e-3)
