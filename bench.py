@@ -53,6 +53,8 @@ def parse():
                     help="skip the BF16 / BF16X2 vs FP32 time-to-same-NMSE study")
     ap.add_argument("--batch-scenes", type=int, default=16,
                     help="scenes of the batched-serving measurement (0 skips it)")
+    ap.add_argument("--no-sweep", dest="sweep", action="store_false",
+                    help="skip the run-time sweep of one apply over Nz = Nt and Nx = Ny")
     ap.add_argument("--no-mixing", dest="mixing", action="store_false",
                     help="skip the Rademacher-mixing measurement")
     ap.add_argument("--crb-trials", type=int, default=50,
@@ -183,6 +185,51 @@ def batched_study(sfs, torch, geom, op, args, w, iters, L, flush, stream, seed):
                               # two plane launches; contractions per group of 4 scenes
                               # (16-bit) or per scene (FP32), forward and adjoint
                               "launches_per_iter": 2 + 2 * (B if mode == "fp32" else -(-B // 4))}
+    return out
+
+
+def runtime_sweep(sfs, torch, flush, stream, seed):
+    """Device time of one A and one A^H apply (FP32, best of 5 after one
+    warm-up, L2 flushed before each) over Sec. V's run-time shapes: Nz = Nt
+    at a 64 x 64 scan, and Nx = Ny at Nz = 5 (recipe synth.SWEEP)."""
+    sw = synth.SWEEP
+
+    def one(Nx, Nz, Nt):
+        params = dict(synth.BASE, Nx=Nx, Ny=Nx, Nz=Nz, dz=0.15e-3, Nt=Nt, device=torch.cuda.current_device())
+        g = sfs.Geometry(**params)
+        M = max(1, Nt // 16)
+        while True:
+            try:
+                op = sfs.Operator.select(g, sfs.SFS_SEL_RANDOM, M, True, seed)
+                break
+            except sfs.SfsError:
+                if M == 1:
+                    raise
+                M = max(1, M // 2)
+        xt = torch.from_numpy(synth.scene(op.shape_x, 10, "uniform", seed=seed).astype(np.complex64)).cuda()
+        y = op.apply_A(xt)
+        xo = op.apply_AH(y)
+        torch.cuda.synchronize()
+        ts = {"A": [], "AH": []}
+        for _ in range(5):
+            for key in ("A", "AH"):
+                flush.fill_(5)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                if key == "A":
+                    op.apply_A(xt, out=y)
+                else:
+                    op.apply_AH(y, out=xo)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ts[key].append(a.elapsed_time(b) * 1e3)
+        return {"Nx": Nx, "Nz": Nz, "Nt": Nt, "M": M, "U": op.info["U"], "A_us": min(ts["A"]),
+                "AH_us": min(ts["AH"])}
+
+    out = {"unit": "us per apply (FP32, L2 flushed, best of 5)",
+           "note": "the figure's 100 x 100 scan exceeds the 64 x 64 the lateral FFT engine holds; 64 x 64 stands in",
+           "nz_eq_nt": [one(sw["nxy_at_nz"], n, n) for n in sw["nz_nt"]],
+           "nx_eq_ny": [one(n, sw["nz"], sw["nt_for_nxy"]) for n in sw["nxy"]]}
     return out
 
 
@@ -757,6 +804,11 @@ def main():
     if rank == 0 and world == 1 and args.batch_scenes > 0:
         batched = batched_study(sfs, torch, geom, op, args, w, iters, L, flush, stream, seed)
 
+    # ---- run time of one apply over the shapes of the paper's run-time figure ----
+    sweep = None
+    if rank == 0 and world == 1 and args.sweep:
+        sweep = runtime_sweep(sfs, torch, flush, stream, seed)
+
     # ---- Rademacher mixing (Phi_rnd,m) on the same workload ----
     mixing = None
     if rank == 0 and world == 1 and args.mixing:
@@ -824,6 +876,8 @@ def main():
             line["crb"] = crb
         if mixing is not None:
             line["mixing"] = mixing
+        if sweep is not None:
+            line["runtime_sweep"] = sweep
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -69,6 +69,15 @@ CRB = dict(params=dict(Nx=50, Ny=50, dx=0.5e-3, dy=0.5e-3, Nz=50, z0=29.6e-3, dz
            pos=(12.25e-3, 12.25e-3, 33.3e-3), n_f=(1, 2, 4, 8, 16, 32), trials=50)
 
 
+# Run-time sweep of one forward apply (the shapes of Sec. V's run-time
+# figure): Nz = Nt over a ladder at the widest area scan the lateral FFT
+# engine holds (64 x 64; the figure uses 100 x 100), and Nx = Ny over a
+# ladder at Nz = 5 (Nt = 256).  M = max(1, Nt / 16) random bins per position
+# (fewer where the band is narrower), one scene of 10 scatterers.
+SWEEP = dict(nz_nt=(16, 32, 64, 128, 256, 512), nxy_at_nz=64, nxy=(8, 16, 24, 32, 40, 48, 56, 64), nz=5,
+             nt_for_nxy=256)
+
+
 def serving_classes():
     """All (grid, depth, M, Nt) classes of the serving mix."""
     out = []
