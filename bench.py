@@ -61,7 +61,9 @@ def parse():
                     help="trials per random strategy of the Cramer-Rao study (0 skips it)")
     ap.add_argument("--serving-scenes", type=int, default=256,
                     help="scenes of the mixed-geometry serving measurement (0 skips it)")
-    ap.add_argument("--learned-steps", type=int, default=400,
+    ap.add_argument("--learned-eval", type=int, default=1000,
+                    help="held-out scenes of the learned-ISTA evaluation")
+    ap.add_argument("--learned-steps", type=int, default=1250,
                     help="training steps of the learned unrolled ISTA measurement on the vol32 "
                          "workload (0 skips it)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -375,10 +377,10 @@ def serving_study(sfs, torch, args, flush, stream, seed):
 def learned_study(sfs, torch, op, args, w, L, stream, seed):
     """Train the 16-layer unrolled ISTA (library kernels: forward, backward,
     Adam) for args.learned_steps steps of 8 fresh scenes of the LEARNED
-    recipe, then on 32 held-out scenes compare its NMSE and time with
-    batched FISTA (same operator, lambda by the mu rule) at 4 .. 300
-    iterations: the first count of the ladder that reaches the network's
-    NMSE, and its time."""
+    recipe (1250 steps: 10^4 scenes), then on args.learned_eval held-out
+    scenes compare its NMSE and time with batched FISTA (same operator,
+    lambda by the mu rule) at 4 .. 300 iterations: the first count of the
+    ladder that reaches the network's NMSE, and its time."""
     from paper_2012_04534_gb300 import lista
     layers, B = synth.LEARNED["layers"], 8
     net = lista.LISTA(op, layers, B, L)
@@ -410,13 +412,12 @@ def learned_study(sfs, torch, op, args, w, L, stream, seed):
         net.adam(g, max(lr, 2e-5), step)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    evals = [batch(10 ** 9 + 97 * k) for k in range(4)]
+    evals = [batch(10 ** 9 + 97 * k) for k in range(max(1, args.learned_eval // B))]
 
     def timed(f):
-        """Device time per evaluation batch of f(y) (after a warm pass, which
-        also captures FISTA's graphs) and f's outputs."""
-        for y, _ in evals:
-            f(y)
+        """Device time per evaluation batch of f(y) (after a warm call on the
+        first batch, which also captures FISTA's graphs) and f's outputs."""
+        f(evals[0][0])
         torch.cuda.synchronize()
         a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -446,7 +447,7 @@ def learned_study(sfs, torch, op, args, w, L, stream, seed):
     return {"layers": layers, "batch": B, "train_steps": steps, "train_scenes": steps * B,
             "train_s": t_train, "precision": args.precision,
             "scenes": "1-20 scatterers, U(0.5,1) magnitudes, uniform phase, 10-30 dB SNR "
-                      "(training scenes drawn fresh every step; 32 held-out scenes)",
+                      "(training scenes drawn fresh every step; %d held-out scenes)" % (len(evals) * B),
             "nmse_db": nmse_lista, "ms_per_batch": ms_lista,
             "fista": ladder,
             "fista_iters_to_same_nmse": None if reach is None else reach[0],
