@@ -355,7 +355,7 @@ def serving_study(sfs, torch, args, flush, stream, seed):
     iters = sv["iters"]
     xs = sfs.fista_grouped(ops, ys, Ls, -0.05, iters)  # workspaces and graph capture
     torch.cuda.synchronize()
-    ts = []
+    ts, lat = [], []
     for _ in range(3):
         flush.fill_(3)
         a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -364,12 +364,18 @@ def serving_study(sfs, torch, args, flush, stream, seed):
         b2.record(stream)
         torch.cuda.synchronize()
         ts.append(a.elapsed_time(b2))
+        # each scene's latency: the completion of its class's loop in the graph
+        for t_g, n in zip(sfs.grouped_times(len(ops)), counts):
+            lat += [t_g] * n
     ts.sort()
+    lat.sort()
     total = sum(counts)
     return {"scenes": total, "classes": len(ops), "iters": iters, "precision": "bf16",
             "unit": "scene-iterations/s", "value": total * iters / (statistics.mean(ts) / 1e3),
-            "latency_ms_p50": statistics.median(ts), "latency_ms_p99": ts[-1],
-            "latency_note": "one graph launch solves every scene; each scene's latency is the launch's",
+            "solve_ms": statistics.mean(ts),
+            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+            "latency_note": "per scene: from the start of the grouped call to the end of its class's loop "
+                            "(event-record node in the graph), over 3 solves",
             "setup_s": t_setup, "autotune_s": t_tune, "tiles_chosen": tiles,
             "mix": "grids {16,32,48,64}^2, depths {64,128,256}, M {32,64,128}, 10 scatterers, 20 dB"}
 

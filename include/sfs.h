@@ -291,6 +291,16 @@ int sfs_fista_grouped(int ngroups, sfs_operator* const* ops, const int32_t* batc
                       void* const* x_out_dev, void* stream);
 
 /*
+ * Completion times of the latest sfs_fista_grouped call of the process
+ * (ngroups must match it): ms_out_host[g] = milliseconds from the start of
+ * that call on its stream (before the per-group setup) to the end of group
+ * g's iteration loop (an event-record node in the graph), i.e. the latency
+ * of every scene of group g.  Waits for those events.
+ * Errors: SFS_ERR_INVALID_ARG (no such call), SFS_ERR_CUDA.
+ */
+int sfs_grouped_times(int ngroups, float* ms_out_host);
+
+/*
  * Learned unrolled ISTA (not in the paper, which reconstructs with
  * ISTA/FISTA, Sec. IV-A; the learned extension the workloads ask for).
  * Layer l keeps Algorithm 1's gradient step and complex soft threshold with

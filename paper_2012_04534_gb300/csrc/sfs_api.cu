@@ -613,6 +613,11 @@ std::vector<GroupedEntry> g_grouped;
 std::vector<cudaStream_t> g_fork_streams;
 std::vector<cudaEvent_t> g_fork_events;
 cudaStream_t g_grouped_capture = nullptr;
+// completion of each group's loop (event-record nodes of the graphs) and the
+// start of the latest grouped call, for sfs_grouped_times
+std::vector<cudaEvent_t> g_done_events;
+cudaEvent_t g_grouped_start = nullptr;
+int g_grouped_last_n = 0;
 
 int grouped_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch, int iters,
                   cudaGraphExec_t* out) {
@@ -641,6 +646,11 @@ int grouped_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch, i
     SFS_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
     g_fork_events.push_back(e2);
   }
+  while ((int)g_done_events.size() < ngroups) {
+    cudaEvent_t e3;
+    SFS_CUDA(cudaEventCreate(&e3));
+    g_done_events.push_back(e3);
+  }
   for (int g = 0; g < ngroups; ++g) SFS_TRY(prepare_kernels(batch_dims(ops[g], batch[g])));
   cudaStream_t cs = g_grouped_capture;
   SFS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -658,7 +668,8 @@ int grouped_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch, i
     const FistaBufs b = {w.ybuf, w.yplane, w.Xh, w.Yh, w.Rh, w.Gh, w.xk, w.gam, w.scal};
     rc = enqueue_fista_loop(ops[g], batch_dims(ops[g], batch[g]), b, iters, nullptr, false, sg);
     if (rc == SFS_OK) {
-      e = cudaEventRecord(g_fork_events[g], sg);
+      e = cudaEventRecordWithFlags(g_done_events[g], sg, cudaEventRecordExternal);
+      if (e == cudaSuccess) e = cudaEventRecord(g_fork_events[g], sg);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, g_fork_events[g], 0);
       if (e != cudaSuccess) rc = cuda_fail(e, "join", __FILE__, __LINE__);
     }
@@ -1573,6 +1584,12 @@ int sfs_fista_grouped(int ngroups, sfs_operator* const* ops, const int32_t* batc
   cudaStream_t st = (cudaStream_t)stream;
   // per group: workspace, measurements, zero state, thresholds (mu rule per scene)
   for (int g = 0; g < ngroups; ++g) SFS_TRY(ensure_batch(ops[g], batch[g]));
+  {
+    std::lock_guard<std::mutex> lock(g_grouped_mu);
+    if (!g_grouped_start) SFS_CUDA(cudaEventCreate(&g_grouped_start));
+    SFS_CUDA(cudaEventRecord(g_grouped_start, st));
+    g_grouped_last_n = iters > 0 ? ngroups : 0;
+  }
   for (int g = 0; g < ngroups; ++g) {
     sfs_operator* op = ops[g];
     const PlaneDims d = batch_dims(op, batch[g]);
@@ -1600,6 +1617,20 @@ int sfs_fista_grouped(int ngroups, sfs_operator* const* ops, const int32_t* batc
     const PlaneDims d = batch_dims(ops[g], batch[g]);
     SFS_CUDA(cudaMemcpyAsync(x_out_dev[g], ops[g]->bws.xk, (size_t)batch[g] * d.bs_x * sizeof(float2),
                              cudaMemcpyDeviceToDevice, st));
+  }
+  return SFS_OK;
+}
+
+int sfs_grouped_times(int ngroups, float* ms_out_host) {
+  clear_error();
+  std::lock_guard<std::mutex> lock(g_grouped_mu);
+  if (!ms_out_host || ngroups < 1 || ngroups != g_grouped_last_n || !g_grouped_start) {
+    set_error("no grouped solve of %d groups to report", ngroups);
+    return SFS_ERR_INVALID_ARG;
+  }
+  for (int g = 0; g < ngroups; ++g) {
+    SFS_CUDA(cudaEventSynchronize(g_done_events[g]));
+    SFS_CUDA(cudaEventElapsedTime(&ms_out_host[g], g_grouped_start, g_done_events[g]));
   }
   return SFS_OK;
 }

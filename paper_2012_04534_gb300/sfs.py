@@ -65,7 +65,7 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_lista_backward", "sfs_lista_nmse", "sfs_lista_adam", "sfs_frobenius",
            "sfs_fista_grouped", "sfs_crb", "sfs_mixing_create", "sfs_mixing_destroy",
            "sfs_apply_A_mixed", "sfs_apply_AH_mixed", "sfs_lipschitz_mixed", "sfs_fista_mixed",
-           "sfs_autotune_batch", "sfs_set_batch_tile", "sfs_fista_backtracking",
+           "sfs_autotune_batch", "sfs_set_batch_tile", "sfs_fista_backtracking", "sfs_grouped_times",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
            "sfs_set_wait_timeout_ns",
            "sfs_inject_wait_timeout", "sfs_check_status", "sfs_last_error", "sfs_version")
@@ -137,6 +137,7 @@ def lib():
         "sfs_autotune_batch": [vp, i32, i32, P(ctypes.c_int32), P(dbl)],
         "sfs_set_batch_tile": [vp, i32, i32],
         "sfs_fista_backtracking": [vp, vp, dbl, dbl, dbl, i32, vp, P(dbl), vp],
+        "sfs_grouped_times": [i32, P(ctypes.c_float)],
         "sfs_apply_A_mixed": [vp, vp, vp, vp],
         "sfs_apply_AH_mixed": [vp, vp, vp, vp],
         "sfs_lipschitz_mixed": [vp, i32, dbl, u64, dbl, P(dbl), vp],
@@ -334,6 +335,13 @@ def fista_grouped(ops, ys, Ls, lam, iters, xs=None, stream=None):
     _check(lib().sfs_fista_grouped(n, oph, b, yp, Lv, float(lam), int(iters), xp,
                                    _stream_ptr(stream, ys[0].device)))
     return xs
+
+
+def grouped_times(n):
+    """sfs_grouped_times: per-group completion (ms) of the latest grouped solve."""
+    out = (ctypes.c_float * n)()
+    _check(lib().sfs_grouped_times(int(n), out))
+    return [float(v) for v in out]
 
 
 class Geometry:

@@ -205,3 +205,35 @@ def test_batch_tile_choice_keeps_results_and_autotune_picks_one(sfs, mode):
     assert np.array_equal(to_host(op.fista_batched(y, -0.05, 1.0e9, 20)), outs[0][2])
     op32 = sfs.Operator.from_indices(g, idx)
     assert op32.autotune(B)[0] == 0
+
+
+def test_grouped_completion_times(sfs):
+    """sfs_grouped_times after a grouped solve: one time per group, each
+    positive and within the whole call's event-timed span; the small group
+    finishes no later than the solve."""
+    import torch
+    specs = [(dict(Nx=8, Ny=1, Nz=16, Nt=128), 6, 2), (dict(Nx=16, Ny=16, Nz=40, Nt=256), 16, 3)]
+    ops, ys, Ls = [], [], []
+    rng = np.random.default_rng(81)
+    for k, (geo, M, B) in enumerate(specs):
+        params = geom_params(dz=0.15e-3, **geo)
+        go = oracle_geometry(params)
+        idx = O.select_indices(go, O.SEL_RANDOM, M, True, 80 + k)
+        g = sfs.Geometry(**params)
+        op = sfs.Operator.from_indices(g, idx)
+        op._geom = g
+        ops.append(op)
+        Ls.append(op.lipschitz(max_iter=100, rtol=1e-5, seed=1, safety=1e-2)[0])
+        ys.append(to_dev(crandn(rng, B, op.S, M)))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sfs.fista_grouped(ops, ys, Ls, -0.05, 30)   # capture
+    torch.cuda.synchronize()
+    a.record()
+    sfs.fista_grouped(ops, ys, Ls, -0.05, 30)
+    b.record()
+    torch.cuda.synchronize()
+    total = a.elapsed_time(b)
+    t = sfs.grouped_times(2)
+    assert len(t) == 2 and all(0 < v <= total * 1.01 + 0.05 for v in t)
+    with pytest.raises(sfs.SfsError):
+        sfs.grouped_times(3)
