@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "sfs_internal.h"
+#include "sfs_launch.h"
 
 namespace sfs {
 
@@ -652,6 +653,25 @@ int grouped_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch, i
     g_done_events.push_back(e3);
   }
   for (int g = 0; g < ngroups; ++g) SFS_TRY(prepare_kernels(batch_dims(ops[g], batch[g])));
+  // kernel priorities: the cheaper a group's iteration (scenes x bins x slots
+  // x depths), the higher, so that small groups finish early instead of
+  // with the large ones
+  std::vector<int> prio(ngroups, 0);
+  {
+    int least = 0, greatest = 0;
+    SFS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    std::vector<int> order(ngroups);
+    for (int g = 0; g < ngroups; ++g) order[g] = g;
+    auto cost = [&](int g) {
+      return (double)batch[g] * ops[g]->U * ops[g]->Ns * ops[g]->geo.d.Nz;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) < cost(b); });
+    const int levels = least - greatest + 1;
+    for (int r = 0; r < ngroups; ++r) {
+      const int level = ngroups > 1 ? (r * levels) / ngroups : 0;  // 0 = cheapest
+      prio[order[r]] = greatest + level;
+    }
+  }
   cudaStream_t cs = g_grouped_capture;
   SFS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   int rc = SFS_OK;
@@ -666,7 +686,9 @@ int grouped_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch, i
     }
     const sfs::BatchWorkspace& w = ops[g]->bws;
     const FistaBufs b = {w.ybuf, w.yplane, w.Xh, w.Yh, w.Rh, w.Gh, w.xk, w.gam, w.scal};
+    launch_priority() = prio[g];
     rc = enqueue_fista_loop(ops[g], batch_dims(ops[g], batch[g]), b, iters, nullptr, false, sg);
+    launch_priority() = 0;
     if (rc == SFS_OK) {
       e = cudaEventRecordWithFlags(g_done_events[g], sg, cudaEventRecordExternal);
       if (e == cudaSuccess) e = cudaEventRecord(g_fork_events[g], sg);
@@ -682,7 +704,7 @@ int grouped_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch, i
   }
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
   cudaGraphExec_t exec = nullptr;
-  e = cudaGraphInstantiate(&exec, graph, 0);
+  e = cudaGraphInstantiateWithFlags(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
   if (g_grouped.size() >= kGroupedCache) {

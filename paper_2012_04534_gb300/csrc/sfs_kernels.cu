@@ -1352,6 +1352,11 @@ int ensure_smem_attr_ptr(const void* kernel, int need) {
   return SFS_OK;
 }
 
+int& launch_priority() {
+  static thread_local int prio = 0;
+  return prio;
+}
+
 bool pdl_enabled() {
   static const bool on = [] {
     const char* v = getenv("SFS_PDL");

@@ -27,20 +27,31 @@ int ensure_smem_attr(K kernel, int need) {
 // but are launched in plain stream order by default.
 bool pdl_enabled();
 
+// Priority given to the kernels this thread launches through launch_pdl (0:
+// none, the stream's own); set while grouped loops are captured, whose
+// graphs run with per-node priorities.
+int& launch_priority();
+
 // Launch with programmatic stream serialisation (see pdl_wait).
 template <typename... KArgs, typename... Args>
 int launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                Args&&... args) {
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+  unsigned n = 1;
+  if (launch_priority() != 0) {
+    attr[1].id = cudaLaunchAttributePriority;
+    attr[1].val.priority = launch_priority();
+    n = 2;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = n;
   SFS_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
   return SFS_OK;
 }
