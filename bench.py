@@ -578,6 +578,30 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(ms, world):
+    """The slowest rank's time: an all-reduce MAX over the process group (on
+    the GPU with NCCL, on the CPU with gloo); ms itself for one rank."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps, iters, ms):
+    """Whole-job FISTA iterations/s: every rank runs steps x iters (its own
+    scene, weak scaling) within the slowest rank's time ms."""
+    return world * steps * iters / (ms / 1e3)
+
+
+def rank_seed(rank):
+    """Seed of a rank's scene, noise, selection and power iteration."""
+    return 1001 + 17 * rank
+
+
 def run_reference(args, rank, world):
     """--impl reference: the FP64 CPU oracle, as it stands, on rank 0."""
     if rank != 0:
@@ -664,7 +688,7 @@ def main():
     torch.cuda.set_device(dev)
     w = synth.WORKLOADS[args.workload]
     iters = args.iters or w["iters"]
-    seed = 1001 + 17 * rank
+    seed = rank_seed(rank)
     params = dict(synth.geometry_params(args.workload), device=dev)
 
     # ---- setup (outside the timed region) ----
@@ -729,12 +753,8 @@ def main():
     torch.cuda.nvtx.range_pop()
     barrier()
     clk = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps * iters / (ms / 1e3)
+    ms = max_over_ranks(ms, world)
+    value = job_rate(world, args.steps, iters, ms)
     launches_per_step = 4 * iters + 5 if iters > 0 else 4
 
     # ---- end to end through the public API with pinned host buffers ----
@@ -751,11 +771,8 @@ def main():
     torch.cuda.synchronize()
     ms_e2e = timed_steps(e2e_step)
     barrier()
-    if world > 1:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e = world * args.steps * iters / (ms_e2e / 1e3)
+    ms_e2e = max_over_ranks(ms_e2e, world)
+    e2e = job_rate(world, args.steps, iters, ms_e2e)
 
     # ---- roofline of the dominant kernels (events around each launch) ----
     for i in range(args.steps):
