@@ -202,11 +202,13 @@ def test_bf16_operator_info_and_table_bytes(sfs):
         sfs.Operator.from_indices(g, idx, precision=17)
 
 
-def test_bf16_noalloc_adjoint_equals_adjoint(sfs):
-    """sfs_apply_AH_noalloc on a BF16 operator (spectra in the static scratch,
-    so the adjoint reads them through a tensor map encoded for that array)."""
+@pytest.mark.parametrize("mode", ["bf16", "fp16"])
+def test_16bit_noalloc_adjoint_equals_adjoint(sfs, mode):
+    """sfs_apply_AH_noalloc on a 16-bit operator (spectra in the static
+    scratch, so the adjoint reads them through a tensor map encoded for that
+    array; FP16 also takes its spectra scale from the operator's maxima)."""
     params = geom_params(Nx=12, Ny=10, Nz=36, dz=0.15e-3, Nt=256)
-    g, op, go, idx = make_pair(sfs, params, "bf16", M=12, seed=5)
+    g, op, go, idx = make_pair(sfs, params, mode, M=12, seed=5)
     import torch
     rng = np.random.default_rng(6)
     y = to_dev(crandn(rng, g.S, 12))
