@@ -55,6 +55,8 @@ def parse():
                     help="scenes of the batched-serving measurement (0 skips it)")
     ap.add_argument("--no-sweep", dest="sweep", action="store_false",
                     help="skip the run-time sweep of one apply over Nz = Nt and Nx = Ny")
+    ap.add_argument("--no-backtracking", dest="backtracking", action="store_false",
+                    help="skip the backtracking-FISTA measurement")
     ap.add_argument("--no-mixing", dest="mixing", action="store_false",
                     help="skip the Rademacher-mixing measurement")
     ap.add_argument("--crb-trials", type=int, default=50,
@@ -188,6 +190,38 @@ def batched_study(sfs, torch, geom, op, args, w, iters, L, flush, stream, seed):
                               # (16-bit) or per scene (FP32), forward and adjoint
                               "launches_per_iter": 2 + 2 * (B if mode == "fp32" else -(-B // 4))}
     return out
+
+
+def backtracking_study(sfs, torch, op, w, iters, y, L, x_true, flush, stream):
+    """sfs_fista_backtracking on the workload's scene (same iterations and mu
+    rule) from the Frobenius lower bound L0 = ||A||_F^2 / N <= sigma_max^2,
+    eta = 2: wall time of one solve (host-driven: one read per trial, L2
+    flushed first, best of 2), the accepted L against the power-iteration
+    L, and the NMSE beside the graph-replayed FISTA's with that L."""
+    fro2, _ = op.frobenius()
+    N = min(op.S * op.M, op.V)
+    L0 = fro2 / N
+    x = torch.empty(op.shape_x, dtype=torch.complex64, device="cuda")
+    best, hist = None, None
+    for _ in range(2):
+        flush.fill_(6)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, hist = op.fista_backtracking(y, -w["mu"], L0, 2.0, iters, x=x)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        best = t if best is None else min(best, t)
+
+    def nmse_db(v):
+        v = v.cpu().numpy().astype(np.complex128)
+        return float(10 * np.log10(np.linalg.norm(v - x_true) ** 2 / np.linalg.norm(x_true) ** 2))
+
+    xf = op.fista(y, -w["mu"], L, iters)
+    return {"L0": L0, "eta": 2.0, "iters": iters, "ms_per_solve": best * 1e3,
+            "fista_it_per_s": iters / best, "L_final": float(hist[-1]), "L_power_iteration": L,
+            "backtracks": int(round(math.log(hist[-1] / L0, 2.0))), "nmse_db": nmse_db(x),
+            "fista_nmse_db": nmse_db(xf),
+            "timing": "wall time of one host-driven solve (one host read per trial), best of 2"}
 
 
 def runtime_sweep(sfs, torch, flush, stream, seed):
@@ -833,6 +867,11 @@ def main():
     if rank == 0 and world == 1 and args.sweep:
         sweep = runtime_sweep(sfs, torch, flush, stream, seed)
 
+    # ---- FISTA with backtracking on the same scene ----
+    backtracking = None
+    if rank == 0 and world == 1 and args.backtracking:
+        backtracking = backtracking_study(sfs, torch, op, w, iters, y, L, x_true, flush, stream)
+
     # ---- Rademacher mixing (Phi_rnd,m) on the same workload ----
     mixing = None
     if rank == 0 and world == 1 and args.mixing:
@@ -902,6 +941,8 @@ def main():
             line["mixing"] = mixing
         if sweep is not None:
             line["runtime_sweep"] = sweep
+        if backtracking is not None:
+            line["backtracking"] = backtracking
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
