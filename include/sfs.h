@@ -278,8 +278,10 @@ int sfs_fista_batched(sfs_operator* op, int batch, const void* y_dev, double lam
  * device), measurements y_dev[g] ([batch][S_g][M_g]), Lipschitz constant
  * L[g], results x_out_dev[g] ([batch][V_g]).  The iteration loops of all
  * groups run as one CUDA graph launch, one forked stream per group, so small
- * groups share the GPU; lambda as in sfs_fista_batched (lambda < 0: mu rule
- * per scene).  The graph is captured on the first call for a set of
+ * groups share the GPU.  The graph runs with per-node priorities: a group's
+ * kernels get a higher priority the less work its iteration does (scenes x
+ * bins x slots x depths), so that small groups finish first.  lambda as in
+ * sfs_fista_batched (lambda < 0: mu rule per scene).  The graph is captured on the first call for a set of
  * (operators, batch sizes, iterations) and replayed afterwards (a process-
  * wide cache of 16 graphs, oldest evicted first).  1 <= ngroups <=
  * SFS_MAX_GROUPS.  Errors: SFS_ERR_INVALID_ARG (also for an operator used
