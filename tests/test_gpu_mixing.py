@@ -115,3 +115,27 @@ def test_mixing_invalid_arguments(sfs):
     bad[0, 0] = 0
     with pytest.raises(sfs.SfsError):
         sfs.Mixing(bop, idx, bad)
+
+
+@pytest.mark.parametrize("mode,tol", [("bf16", 2.0 ** -8), ("fp16", 2.0 ** -11)])
+def test_mixing_over_a_16bit_band_operator(sfs, mode, tol):
+    """The band operator on the tensor cores (16-bit table, FP16 with its
+    per-scene scales): A_mix and A_mix^H within the mode's bar of the FP64
+    mixing oracle."""
+    params = geom_params(Nx=12, Ny=10, Nz=24, dz=0.15e-3, Nt=256)
+    go = oracle_geometry(params)
+    lo, hi, _ = O.candidate_band(go, 8)
+    band = np.arange(lo, hi + 1)
+    idx = O.select_indices(go, O.SEL_RANDOM, 8, True, 12)
+    xi = synth.rademacher((go.S, go.Nt), seed=13)
+    g = sfs.Geometry(**params)
+    bop = sfs.Operator.from_indices(g, np.tile(band.astype(np.int32), (go.S, 1)),
+                                    precision=sfs.PRECISION_NAMES[mode])
+    bop._geom = g
+    mx = sfs.Mixing(bop, idx, xi)
+    ref = X.MixedOperator(go, band, idx, xi)
+    rng = np.random.default_rng(14)
+    x = crandn(rng, go.Nz, go.Ny, go.Nx)
+    y = crandn(rng, go.S, 8)
+    assert rel_err(to_host(mx.apply_A(to_dev(x))), ref.apply_A(x)) <= tol
+    assert rel_err(to_host(mx.apply_AH(to_dev(y))), ref.apply_AH(y)) <= tol
