@@ -1,5 +1,7 @@
 """Pins of the Rademacher-mixing oracle (oracle/mixing_oracle.py; Phi_s =
 S_s F Sigma_s, Sec. II-B and III-A)."""
+import math
+
 import numpy as np
 
 import oracle as O
@@ -38,8 +40,7 @@ def test_no_mixing_is_plain_selection():
     """xi = 1: Xi = Nt delta, so the mixed operator is the unmixed one."""
     g = geom()
     idx = O.select_indices(g, O.SEL_RANDOM, 5, True, 2)
-    band = band_of(g, 5)
-    op = X.MixedOperator(g, band, idx, np.ones((g.S, g.Nt)))
+    op = X.MixedOperator(g, idx, np.ones((g.S, g.Nt)))
     ref = O.LateralFFTOperator(g, idx)
     rng = np.random.default_rng(3)
     x = crandn(rng, g.Nz, g.Ny, g.Nx)
@@ -52,10 +53,9 @@ def test_no_mixing_is_plain_selection():
 def test_mixed_operator_equals_dense_and_is_adjoint():
     g = geom()
     idx = O.select_indices(g, O.SEL_RANDOM, 6, True, 4)
-    band = band_of(g, 6)
     xi = synth.rademacher((g.S, g.Nt), seed=5)
-    op = X.MixedOperator(g, band, idx, xi)
-    A = X.dense_A_mixed(g, band, idx, xi)
+    op = X.MixedOperator(g, idx, xi)
+    A = X.dense_A_mixed(g, idx, xi)
     rng = np.random.default_rng(6)
     x = crandn(rng, g.Nz, g.Ny, g.Nx)
     y = crandn(rng, g.S, 6)
@@ -76,3 +76,79 @@ def test_full_mixing_is_unitary():
         allk = np.arange(Nt)
         Mx = X.mixing_matrix(xi, allk, allk, Nt)
         np.testing.assert_allclose(Mx.conj().T @ Mx, np.eye(Nt), atol=1e-12)
+
+
+def scatterer_scene(g, n, seed):
+    """n distinct voxels with complex amplitudes: (x, voxel coordinates, amps)."""
+    rng = np.random.default_rng(seed)
+    vox = rng.choice(g.V, n, replace=False)
+    amps = rng.uniform(0.5, 1.0, n) * np.exp(2j * np.pi * rng.uniform(size=n))
+    x = np.zeros(g.V, dtype=np.complex128)
+    x[vox] = amps
+    xv, yv, zv = g.voxel_xyz()
+    return x.reshape(g.Nz, g.Ny, g.Nx), xv[vox], yv[vox], zv[vox], amps
+
+
+def literal_chain(g, idx, xi, xv, yv, zv, amps):
+    """Eq. (2) echoes sampled on the receive window (periodic fold), times
+    xi_s, direct DFT, kept bins: y_s = S_s F Sigma_s b_s term by term."""
+    out = np.empty(idx.shape, dtype=np.complex128)
+    for s in range(g.S):
+        b = O.time_domain_ascan(g, s, xv, yv, zv, amps)
+        out[s] = O.dft_bins(xi[s] * b, idx[s])
+    return out
+
+
+def test_mixed_operator_is_the_time_domain_chain():
+    """The paper's chain on brute-force A-scans: every bin of the A-scan
+    enters each kept coefficient, the bins above Nt/2 as negative
+    frequencies.  Agreement to 1e-10 pins the full-spectrum sum (a dropped
+    bin range, a wrong sign of the negative frequencies or a transposed
+    mixing index would each fail it)."""
+    for Nt, M, seed in ((128, 6, 1), (256, 8, 2)):
+        g = geom(Nx=5, Ny=4, Nz=6, Nt=Nt)
+        idx = O.select_indices(g, O.SEL_RANDOM, M, True, seed)
+        xi = synth.rademacher((g.S, g.Nt), seed=seed + 10)
+        x, xv, yv, zv, amps = scatterer_scene(g, 4, seed + 20)
+        ref = literal_chain(g, idx, xi, xv, yv, zv, amps)
+        got = X.MixedOperator(g, idx, xi).apply_A(x)
+        assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_band_limited_spectrum_is_not_the_model():
+    """Mixing only the candidate band's bins (the 20 dB rung of the
+    selection) is a different operator: off by more than 1 % on the same
+    chain, so the pin above separates the two."""
+    g = geom(Nx=5, Ny=4, Nz=6, Nt=128)
+    idx = O.select_indices(g, O.SEL_RANDOM, 6, True, 1)
+    xi = synth.rademacher((g.S, g.Nt), seed=11)
+    x, xv, yv, zv, amps = scatterer_scene(g, 4, 21)
+    ref = literal_chain(g, idx, xi, xv, yv, zv, amps)
+    cut = X.MixedOperator(g, idx, xi, band=band_of(g, 6)).apply_A(x)
+    assert np.linalg.norm(cut - ref) > 1e-2 * np.linalg.norm(ref)
+
+
+def test_spectrum_truncated_at_140_dB_is_within_1e6():
+    """Bins whose pulse magnitude |H(f_k)| lies more than 140 dB below the
+    peak carry a fraction erfc(sqrt(2 ln 1e7)) ~ 1e-15 of the pulse energy
+    (Gaussian spectrum of Sec. VI), so dropping them changes A_mix and
+    A_mix^H by far less than 1e-6 relative.  Checked on the full-spectrum
+    operator with random data for two record lengths."""
+    for Nt, M in ((128, 6), (256, 8)):
+        g = geom(Nx=5, Ny=4, Nz=6, Nt=Nt)
+        k = X.full_band(Nt)
+        mag = O.pulse_spectrum(g.bin_freq(k), g.fc, g.alpha)
+        band = k[mag >= 1e-7 * mag.max()]
+        assert band.size < Nt and np.all(np.diff(band) == 1)     # one run of bins
+        assert math.erfc(math.sqrt(2 * math.log(1e7))) < 1e-14
+        idx = O.select_indices(g, O.SEL_RANDOM, M, True, 3)
+        xi = synth.rademacher((g.S, g.Nt), seed=Nt)
+        full = X.MixedOperator(g, idx, xi)
+        cut = X.MixedOperator(g, idx, xi, band=band)
+        rng = np.random.default_rng(Nt)
+        x = crandn(rng, g.Nz, g.Ny, g.Nx)
+        y = crandn(rng, g.S, M)
+        yf = full.apply_A(x)
+        assert np.linalg.norm(cut.apply_A(x) - yf) <= 1e-6 * np.linalg.norm(yf)
+        xf = full.apply_AH(y)
+        assert np.linalg.norm(cut.apply_AH(y) - xf) <= 1e-6 * np.linalg.norm(xf)
