@@ -39,9 +39,10 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
                       bound, exact support recovery of isolated scatterers
   select_indices      pinned: invariants (distinct, sorted, inside the band,
                       count M), closed-form contiguous / equispaced sets,
-                      chi-square uniformity of the random draw.  The exact
-                      SplitMix64 stream is pinned only by its published
-                      definition (no printed test vector is used).
+                      chi-square uniformity of the random draw
+  SplitMix64          pinned: the published first five outputs from state
+                      1234567 (tests/golden/splitmix64_seed1234567.txt) and
+                      the increment floor(2^64 / phi) in exact integers
 """
 from __future__ import annotations
 

@@ -112,3 +112,41 @@ def test_null_handles_rejected(sfs):
     assert L.sfs_fista(None, None, 0.0, 1.0, 1, None, 0, None, None) == sfs.SFS_ERR_INVALID_ARG
     assert L.sfs_operator_from_indices(None, 1, None, None) == sfs.SFS_ERR_INVALID_ARG
     assert L.sfs_destroy_operator(None) == sfs.SFS_OK
+
+
+@pytest.mark.parametrize("name", ["line2d", "vol32", "vol64"])
+def test_mixing_band_is_the_140_dB_run_of_the_pulse(sfs, name):
+    """sfs_mixing_band (host only) equals the run of signed bins -Nt/2 < k <=
+    Nt/2 whose oracle pulse magnitude |H(k fs/Nt)| is within 140 dB of the
+    peak, and it reaches into the negative frequencies."""
+    from oracle import mixing_oracle as X
+    params = synth.geometry_params(name)
+    g = sfs.Geometry(**params)
+    go = O.Geometry(**params)
+    k = X.full_band(go.Nt)
+    mag = O.pulse_spectrum(go.bin_freq(k), go.fc, go.alpha)
+    ref = k[mag >= 10 ** (-140.0 / 20) * mag.max()]
+    got = sfs.Mixing.band_bins(g)
+    assert np.array_equal(got, ref)
+    assert got[0] < 0 < got[-1] <= go.Nt // 2
+
+
+def test_host_random_draw_uses_the_published_splitmix64_stream(sfs):
+    """The C++ host selection keys position 0's stream with the seed itself,
+    so a shared RANDOM set with seed 1234567 consumes the published outputs
+    (tests/golden/splitmix64_seed1234567.txt): partial Fisher-Yates over the
+    candidate band with j = i + floor(hi32(u_i) (|C| - i) / 2^32)."""
+    path = os.path.join(ROOT, "tests", "golden", "splitmix64_seed1234567.txt")
+    gold = [int(l) for l in open(path) if l.strip() and not l.startswith("#")]
+    params = synth.geometry_params("vol32")
+    g = sfs.Geometry(**params)
+    M = len(gold)
+    idx, (lo, hi) = g.select_indices(sfs.SFS_SEL_RANDOM, M, False, 1234567)
+    n = hi - lo + 1
+    perm = list(range(n))
+    for i, u in enumerate(gold):
+        j = i + (((u >> 32) * (n - i)) >> 32)
+        perm[i], perm[j] = perm[j], perm[i]
+    expect = np.array(sorted(lo + v for v in perm[:M]), dtype=np.int32)
+    assert np.array_equal(idx[0], expect)
+    assert all(np.array_equal(r, expect) for r in idx)

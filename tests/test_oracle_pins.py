@@ -461,3 +461,19 @@ def test_backtracking_step_bounds_and_rate():
         xk = O.fista_backtracking(op.apply_A, op.apply_AH, y, lam, L / 500.0, eta, k)
         Fk = O.lasso_objective(op.apply_A, y, lam, xk)
         assert Fk - F_star <= 2 * eta * L * r0 / (k + 1) ** 2 + 1e-9 * abs(F_star)
+
+
+def _golden_splitmix():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "splitmix64_seed1234567.txt")
+    return [int(l) for l in open(path) if l.strip() and not l.startswith("#")]
+
+
+def test_splitmix64_matches_published_outputs():
+    """The oracle's generator reproduces the published first outputs from
+    state 1234567, and its increment is the odd integer floor(2^64 / phi)
+    (the golden-ratio gamma of SplitMix64), computed here in exact integers."""
+    gold = _golden_splitmix()
+    s = O.SplitMix64(1234567)
+    assert [s.next() for _ in gold] == gold
+    gamma = (math.isqrt(5 << 128) - (1 << 64)) // 2       # floor(2^64 (sqrt(5) - 1) / 2)
+    assert gamma == O.sfs_oracle._GOLDEN and gamma % 2 == 1
