@@ -271,17 +271,16 @@ def runtime_sweep(sfs, torch, flush, stream, seed):
 
 def mixing_study(sfs, torch, geom, op, args, w, iters, x_true, flush, stream, seed):
     """The workload measured through Rademacher-mixed A-scans (Phi_rnd,m,f:
-    own xi_s and own random bins per position): band operator (every bin of
-    the candidate band at every position) plus the mixing object; FISTA with
+    own xi_s and own random bins per position): band operator (the signed
+    bins within 140 dB of the pulse peak, sfs_mixing_band, at every
+    position) plus the mixing object; FISTA with
     the same iterations and mu rule, L by power iteration on A_mix.  Reports
     the device time of a solve (L2 flushed first, best of 3), FISTA it/s and
     the NMSE against the true scene, beside the unmixed solve's NMSE."""
     Nt = w["Nt"]
-    band_lo, band_hi = geom.select_indices(sfs.SFS_SEL_RANDOM, w["M"], True, seed)[1]
-    band = np.arange(band_lo, band_hi + 1, dtype=np.int32)
-    bop = sfs.Operator.from_indices(geom, np.tile(band, (geom.S, 1)))
     xi = synth.rademacher((geom.S, Nt), seed=seed + 4242)
-    mx = sfs.Mixing(bop, op.idx, xi)
+    mx = sfs.Mixing.create(geom, op.idx, xi)
+    band = mx.band.idx[0]
     xt = torch.from_numpy(x_true.astype(np.complex64)).cuda()
     y0 = mx.apply_A(xt).cpu().numpy().astype(np.complex128)
     sig = synth.noise_scale(float(np.vdot(y0, y0).real), y0.size, w["snr_db"])
@@ -303,6 +302,7 @@ def mixing_study(sfs, torch, geom, op, args, w, iters, x_true, flush, stream, se
     xh = x.cpu().numpy().astype(np.complex128)
     nmse = float(10 * np.log10(np.linalg.norm(xh - x_true) ** 2 / np.linalg.norm(x_true) ** 2))
     return {"strategy": "Phi_rnd,m,f (xi_s and bins drawn per position)", "band_bins": int(band.size),
+            "band_signed": [int(band[0]), int(band[-1])],
             "M": int(w["M"]), "iters": iters, "ms_per_solve": best, "fista_it_per_s": iters / (best / 1e3),
             "nmse_db": nmse, "L": L, "launches_per_iter": 6,
             "timing": "device time of one solve (lambda rule + iterations), best of 3, L2 flushed first"}

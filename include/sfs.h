@@ -177,7 +177,10 @@ int sfs_select_freqs(sfs_geometry* g, int strategy, int M, int per_position,
 /*
  * Operator from given index sets (e.g. sets shared with another
  * implementation).  idx_host: int32 [S][M], each row strictly ascending,
- * bins in 0..Nt/2.  Builds on the device the lateral-FFT table of the
+ * signed DFT bins -Nt/2 < k <= Nt/2 (the strategies keep 0..Nt/2; a
+ * negative k is DFT bin k + Nt, the negative frequency k fs / Nt of the
+ * A-scan's periodic spectrum, which the mixing model needs; M <= Nt).
+ * Builds on the device the lateral-FFT table of the
  * generating elements of the block 2-level Toeplitz H (Theorem 2, Sec. IV-B)
  * evaluated at the union U of the kept bins with the frequency-domain model
  * of Eq. (4):  h_{k,z}[d] = fs H(f_k) g exp(-j 2 pi f_k (tau(d, z) - t0)).
@@ -411,23 +414,34 @@ int sfs_crb(const sfs_geometry* g, int T, int M, const int32_t* idx_host, const 
 /*
  * Rademacher mixing, Phi_s = S_s F Sigma_s with Sigma_s = Diag{xi_s}, xi_s in
  * {-1, 1}^Nt (Sec. II-B, Eq. "compressed_model"; Sec. III-A's random
- * sampling).  Sigma_s acts on the time samples of A-scan s, so each kept
- * coefficient mixes every bin of that A-scan.  The A-scan is taken
- * band-limited to the candidate band C of the selection:
- *   y_s[m] = (1/Nt) sum_{u in C} Xi_s[(k_m - k_u) mod Nt] (A_band x)_s[u],
- * Xi_s = DFT(xi_s), where A_band is an ordinary operator keeping every bin
- * of C at every position (idx rows all equal to C).  A_mix = Mix o A_band,
+ * sampling).  Sigma_s acts on the Nt time samples of A-scan s, so each kept
+ * coefficient mixes every DFT bin of that A-scan, the bins above Nt/2 being
+ * its negative frequencies (signed bins k - Nt):
+ *   y_s[m] = (1/Nt) sum_k Xi_s[(k_m - k) mod Nt] (A_band x)_s[k],
+ * Xi_s = DFT(xi_s), where A_band is an ordinary operator on signed bins
+ * keeping the same bins at every position.  The sum runs over the bins of
+ * A_band; it must hold at least the run sfs_mixing_band returns, the bins
+ * whose pulse magnitude |H(f_k)| is within SFS_MIX_BAND_DB = 140 dB of the
+ * peak: the Gaussian pulse spectrum (Sec. VI) puts a fraction
+ * erfc(sqrt(2 ln 1e7)) ~ 1e-15 of its energy outside, so the truncation
+ * changes A_mix by less than 1e-7 relative.  A_mix = Mix o A_band,
  * A_mix^H = A_band^H o Mix^H, Mix generated per position from Xi_s.
- *   band      operator with identical index rows (its union = C); not owned,
- *             must outlive the mixing object; calls on the two must not
- *             overlap (they share the band operator's workspace)
+ *   band      operator with identical index rows covering the run of
+ *             sfs_mixing_band; not owned, must outlive the mixing object;
+ *             calls on the two must not overlap (they share the band
+ *             operator's workspace)
  *   idx_host  int32 [S][M] kept bins, rows strictly ascending in 0..Nt/2
  *   xi_host   int8 [S][Nt], entries +1 or -1 (the random draws are inputs)
  * Xi_s is computed on the device in FP64 and stored as c64 (S Nt values).
- * Errors: SFS_ERR_INVALID_ARG (band rows differ, bad rows or signs, Nt >
- * 8192), SFS_ERR_CUDA, SFS_ERR_OOM.
+ * Errors: SFS_ERR_INVALID_ARG (band rows differ or miss a bin of the run,
+ * bad rows or signs, Nt > 8192), SFS_ERR_CUDA, SFS_ERR_OOM.
+ * sfs_mixing_band: the signed bins k_lo..k_hi (inclusive, -Nt/2 < k <=
+ * Nt/2) with |H(k fs / Nt)| >= 10^(-SFS_MIX_BAND_DB / 20) max |H| (host only,
+ * FP64).  Errors: SFS_ERR_INVALID_ARG (null pointer).
  */
+#define SFS_MIX_BAND_DB 140.0
 typedef struct sfs_mixing sfs_mixing;  /* opaque, library owned */
+int sfs_mixing_band(const sfs_geometry* g, int32_t* k_lo, int32_t* k_hi);
 int sfs_mixing_create(sfs_operator* band, int M, const int32_t* idx_host, const int8_t* xi_host,
                       sfs_mixing** out);
 int sfs_mixing_destroy(sfs_mixing* mx);

@@ -843,16 +843,19 @@ static int build_operator(sfs_geometry* g, int M, const int32_t* idx_host, int p
   *out = nullptr;
   const sfs_geometry_desc& d = g->d;
   const int S = d.Nx * d.Ny;
-  const int kmax = d.Nt / 2;
-  if (M <= 0 || M > kmax + 1) {
-    set_error("M = %d out of range 1..%d", M, kmax + 1);
+  // signed DFT bins -Nt/2 < k <= Nt/2: bin k + Nt of the A-scan for k < 0
+  // (the negative frequencies of its periodic spectrum)
+  const int kmax = d.Nt / 2, kmin = -((d.Nt - 1) / 2);
+  const int nbins = kmax - kmin + 1;
+  if (M <= 0 || M > nbins) {
+    set_error("M = %d out of range 1..%d", M, nbins);
     return SFS_ERR_INVALID_ARG;
   }
   for (int s = 0; s < S; ++s)
     for (int m = 0; m < M; ++m) {
       const int k = idx_host[(size_t)s * M + m];
-      if (k < 0 || k > kmax || (m > 0 && k <= idx_host[(size_t)s * M + m - 1])) {
-        set_error("index row %d is not strictly ascending inside 0..%d", s, kmax);
+      if (k < kmin || k > kmax || (m > 0 && k <= idx_host[(size_t)s * M + m - 1])) {
+        set_error("index row %d is not strictly ascending inside %d..%d", s, kmin, kmax);
         return SFS_ERR_INVALID_ARG;
       }
     }
@@ -875,12 +878,12 @@ static int build_operator(sfs_geometry* g, int M, const int32_t* idx_host, int p
   op->V = S * d.Nz;
   op->Nk = g->Px * g->Py;
   op->idx.assign(idx_host, idx_host + (size_t)S * M);
-  std::vector<char> used(kmax + 1, 0);
-  for (int32_t k : op->idx) used[k] = 1;
-  std::vector<int> u_of(kmax + 1, -1);
-  for (int k = 0; k <= kmax; ++k)
-    if (used[k]) {
-      u_of[k] = (int)op->bins.size();
+  std::vector<char> used(nbins, 0);
+  for (int32_t k : op->idx) used[k - kmin] = 1;
+  std::vector<int> u_of(nbins, -1);  // union position of bin k at k - kmin
+  for (int k = kmin; k <= kmax; ++k)
+    if (used[k - kmin]) {
+      u_of[k - kmin] = (int)op->bins.size();
       op->bins.push_back(k);
     }
   op->U = (int)op->bins.size();
@@ -1004,7 +1007,7 @@ static int build_operator(sfs_geometry* g, int M, const int32_t* idx_host, int p
   }
   std::vector<int32_t> posmap((size_t)op->U * S, -1);
   for (int s = 0; s < S; ++s)
-    for (int m = 0; m < M; ++m) posmap[(size_t)u_of[op->idx[(size_t)s * M + m]] * S + s] = m;
+    for (int m = 0; m < M; ++m) posmap[(size_t)u_of[op->idx[(size_t)s * M + m] - kmin] * S + s] = m;
 
   DeviceScope scope(d.device);
   if (!scope.ok()) {

@@ -3,13 +3,20 @@
 // Sec. III-A's random sampling).
 //
 // Sigma_s acts on the time samples of A-scan s, so every kept coefficient
-// mixes all bins of that A-scan.  With the A-scan band-limited to the
-// selection's candidate band C, and Xi_s = DFT(xi_s),
-//   y_s[m] = (1/Nt) sum_{u in C} Xi_s[(k_m - k_u) mod Nt] B_s[k_u],
-// where B = A_band x is the data of a band operator that keeps every bin of
-// C at every position (an ordinary sfs_operator).  So
+// mixes all Nt bins of that A-scan's spectrum B_s (the bins above Nt/2 are
+// the negative frequencies of the periodic spectrum, signed bins k - Nt).
+// With Xi_s = DFT(xi_s), the product xi_s . b_s has the spectrum
+// (1/Nt) Xi_s (*) B_s, so
+//   y_s[m] = (1/Nt) sum_k Xi_s[(k_m - k) mod Nt] B_s[k].
+// B_s[k] = fs H(f_k) (...) carries the Gaussian pulse spectrum (Sec. VI), so
+// the bins more than SFS_MIX_BAND_DB = 140 dB below its peak hold a fraction
+// erfc(sqrt(2 ln 1e7)) ~ 1e-15 of its energy; the sum runs over the others
+// (sfs_mixing_band, one run of signed bins), a truncation below 1e-7
+// relative.  B = A_band x is the data of a band operator that keeps every
+// bin of that run at every position (an ordinary sfs_operator on signed
+// bins).  So
 //   A_mix = Mix o A_band,   A_mix^H = A_band^H o Mix^H,
-// with Mix one M x |C| matrix per position, generated on the fly from the
+// with Mix one M x |band| matrix per position, generated on the fly from the
 // position's Xi_s (Nt complex numbers) instead of stored.  The kernels here
 // are the per-position mixing steps; the band operator's plane and
 // contraction kernels do the rest.  FISTA (Algorithm 1) with mixing runs
@@ -284,12 +291,43 @@ struct Device {
 
 bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Signed bins -Nt/2 < k <= Nt/2 with |H(f_k)| >= 10^(-SFS_MIX_BAND_DB / 20)
+// max |H|, f_k = k fs / Nt: one run, since |H| falls off monotonically on
+// both sides of fc.
+void mixing_band(const sfs_geometry* g, int* lo, int* hi) {
+  const int kmax = g->d.Nt / 2, kmin = -((g->d.Nt - 1) / 2);
+  double peak = 0.0;
+  for (int k = kmin; k <= kmax; ++k)
+    peak = std::max(peak, pulse_mag((double)k * g->d.fs / g->d.Nt, g->d.fc, g->alpha));
+  const double thr = peak * pow(10.0, -SFS_MIX_BAND_DB / 20.0);
+  *lo = kmax;
+  *hi = kmin;
+  for (int k = kmin; k <= kmax; ++k)
+    if (pulse_mag((double)k * g->d.fs / g->d.Nt, g->d.fc, g->alpha) >= thr) {
+      *lo = std::min(*lo, k);
+      *hi = std::max(*hi, k);
+    }
+}
+
 }  // namespace
 }  // namespace sfs
 
 using namespace sfs;
 
 extern "C" {
+
+int sfs_mixing_band(const sfs_geometry* g, int32_t* k_lo, int32_t* k_hi) {
+  clear_error();
+  if (!g || !k_lo || !k_hi) {
+    set_error("null argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  int lo = 0, hi = 0;
+  mixing_band(g, &lo, &hi);
+  *k_lo = lo;
+  *k_hi = hi;
+  return SFS_OK;
+}
 
 int sfs_mixing_create(sfs_operator* band, int M, const int32_t* idx_host, const int8_t* xi_host,
                       sfs_mixing** out) {
@@ -310,6 +348,15 @@ int sfs_mixing_create(sfs_operator* band, int M, const int32_t* idx_host, const 
         set_error("the band operator must keep every bin of its band at every position");
         return SFS_ERR_INVALID_ARG;
       }
+  {
+    int lo = 0, hi = 0;
+    mixing_band(&band->geo, &lo, &hi);
+    const auto first = std::lower_bound(band->bins.begin(), band->bins.end(), lo);
+    if (first == band->bins.end() || band->bins.end() - first < hi - lo + 1 || first[hi - lo] != hi) {
+      set_error("the band operator must keep every signed bin %d..%d (sfs_mixing_band)", lo, hi);
+      return SFS_ERR_INVALID_ARG;
+    }
+  }
   if (M < 1 || M > kmax + 1 || Nt > 8192) {
     set_error("M = %d out of range 1..%d (Nt <= 8192)", M, kmax + 1);
     return SFS_ERR_INVALID_ARG;

@@ -63,7 +63,7 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_lista_create", "sfs_lista_destroy", "sfs_lista_info", "sfs_lista_set_params",
            "sfs_lista_get_params", "sfs_lista_load_params_dev", "sfs_lista_forward",
            "sfs_lista_backward", "sfs_lista_nmse", "sfs_lista_adam", "sfs_frobenius",
-           "sfs_fista_grouped", "sfs_crb", "sfs_mixing_create", "sfs_mixing_destroy",
+           "sfs_fista_grouped", "sfs_crb", "sfs_mixing_band", "sfs_mixing_create", "sfs_mixing_destroy",
            "sfs_apply_A_mixed", "sfs_apply_AH_mixed", "sfs_lipschitz_mixed", "sfs_fista_mixed",
            "sfs_autotune_batch", "sfs_set_batch_tile", "sfs_fista_backtracking", "sfs_grouped_times",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
@@ -132,6 +132,7 @@ def lib():
         "sfs_frobenius": [vp, P(dbl), P(dbl)],
         "sfs_fista_grouped": [i32, P(vp), P(ctypes.c_int32), P(vp), P(dbl), dbl, i32, P(vp), vp],
         "sfs_crb": [vp, i32, i32, P(ctypes.c_int32), P(dbl), dbl, dbl, dbl, i32, P(dbl), P(dbl)],
+        "sfs_mixing_band": [vp, P(ctypes.c_int32), P(ctypes.c_int32)],
         "sfs_mixing_create": [vp, i32, P(ctypes.c_int32), P(ctypes.c_int8), P(vp)],
         "sfs_mixing_destroy": [vp],
         "sfs_autotune_batch": [vp, i32, i32, P(ctypes.c_int32), P(dbl)],
@@ -539,8 +540,24 @@ class Operator:
 
 class Mixing:
     """A_mix = Mix o A_band (sfs_mixing): Rademacher mixing of each A-scan
-    before the DFT and selection.  band: Operator keeping every bin of its
-    band at every position; idx: int32 [S][M] kept bins; xi: int8 [S][Nt]."""
+    before the DFT and selection.  band: Operator keeping the same signed
+    bins at every position, at least the run ``Mixing.band_bins(geom)``;
+    idx: int32 [S][M] kept bins; xi: int8 [S][Nt]."""
+
+    @staticmethod
+    def band_bins(geom: "Geometry"):
+        """Signed bins (int32, ascending) within SFS_MIX_BAND_DB of the pulse
+        peak: the spectrum a band operator for mixing must cover."""
+        lo, hi = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().sfs_mixing_band(geom.handle, ctypes.byref(lo), ctypes.byref(hi)))
+        return np.arange(lo.value, hi.value + 1, dtype=np.int32)
+
+    @classmethod
+    def create(cls, geom: "Geometry", idx, xi, precision=None):
+        """Band operator on ``band_bins(geom)`` (in `precision`) plus the
+        mixing object on it; the mixing object keeps the band operator."""
+        band = Operator.from_indices(geom, np.tile(cls.band_bins(geom), (geom.S, 1)), precision=precision)
+        return cls(band, idx, xi)
 
     def __init__(self, band: "Operator", idx, xi):
         idx = np.ascontiguousarray(idx, dtype=np.int32)

@@ -1,6 +1,8 @@
 """Rademacher mixing (sfs_mixing_*, Phi_s = S_s F Sigma_s) on the GPU against
-the FP64 mixing oracle: A_mix, A_mix^H and FISTA at the FP32 bars of the
-plain operator (1e-5 for the applies, 1e-4 for 100 FISTA iterations)."""
+the FP64 mixing oracle, which mixes every one of the Nt bins of each A-scan:
+A_mix, A_mix^H and FISTA at the FP32 bars of the plain operator (1e-5 for
+the applies, 1e-4 for 100 FISTA iterations).  The library sums over the
+bins within 140 dB of the pulse peak (sfs_mixing_band)."""
 import numpy as np
 import pytest
 
@@ -32,19 +34,16 @@ def to_host(t):
     return t.cpu().numpy().astype(np.complex128)
 
 
-def build(sfs, params, M, seed, xi=None):
+def build(sfs, params, M, seed, xi=None, precision=None):
     go = oracle_geometry(params)
-    lo, hi, _ = O.candidate_band(go, M)
-    band = np.arange(lo, hi + 1)
     idx = O.select_indices(go, O.SEL_RANDOM, M, True, seed)
     if xi is None:
         xi = synth.rademacher((go.S, go.Nt), seed=seed + 1)
     g = sfs.Geometry(**params)
-    bop = sfs.Operator.from_indices(g, np.tile(band.astype(np.int32), (go.S, 1)))
-    bop._geom = g
-    mx = sfs.Mixing(bop, idx, xi)
-    ref = X.MixedOperator(go, band, idx, xi)
-    return mx, ref, go, idx, band, xi
+    mx = sfs.Mixing.create(g, idx, xi, precision=precision)
+    mx.band._geom = g
+    ref = X.MixedOperator(go, idx, xi)
+    return mx, ref, go, idx, mx.band.idx[0], xi
 
 
 @pytest.mark.parametrize("case", [
@@ -109,12 +108,25 @@ def test_mixing_invalid_arguments(sfs):
     plain = sfs.Operator.from_indices(g, idx)   # rows differ: not a band operator
     with pytest.raises(sfs.SfsError):
         sfs.Mixing(plain, idx, synth.rademacher((go.S, go.Nt), seed=2))
-    lo, hi, _ = O.candidate_band(go, 4)
-    bop = sfs.Operator.from_indices(g, np.tile(np.arange(lo, hi + 1, dtype=np.int32), (go.S, 1)))
+    band = sfs.Mixing.band_bins(g)
+    bop = sfs.Operator.from_indices(g, np.tile(band, (go.S, 1)))
     bad = synth.rademacher((go.S, go.Nt), seed=3)
     bad[0, 0] = 0
     with pytest.raises(sfs.SfsError):
         sfs.Mixing(bop, idx, bad)
+    # a band operator that misses bins of the 140 dB run (here the
+    # selection's candidate band only) is rejected
+    lo, hi, _ = O.candidate_band(go, 4)
+    narrow = sfs.Operator.from_indices(g, np.tile(np.arange(lo, hi + 1, dtype=np.int32), (go.S, 1)))
+    with pytest.raises(sfs.SfsError) as ei:
+        sfs.Mixing(narrow, idx, synth.rademacher((go.S, go.Nt), seed=4))
+    assert ei.value.status == sfs.SFS_ERR_INVALID_ARG
+    # a wider band (every signed bin) is accepted and gives the same A_mix
+    wide = sfs.Operator.from_indices(g, np.tile(X.full_band(go.Nt).astype(np.int32), (go.S, 1)))
+    xi = synth.rademacher((go.S, go.Nt), seed=5)
+    m1, m2 = sfs.Mixing(bop, idx, xi), sfs.Mixing(wide, idx, xi)
+    x = to_dev(crandn(np.random.default_rng(6), go.Nz, go.Ny, go.Nx))
+    assert rel_err(to_host(m1.apply_A(x)), to_host(m2.apply_A(x))) <= 1e-6
 
 
 @pytest.mark.parametrize("mode,tol", [("bf16", 2.0 ** -8), ("fp16", 2.0 ** -11)])
@@ -123,17 +135,7 @@ def test_mixing_over_a_16bit_band_operator(sfs, mode, tol):
     per-scene scales): A_mix and A_mix^H within the mode's bar of the FP64
     mixing oracle."""
     params = geom_params(Nx=12, Ny=10, Nz=24, dz=0.15e-3, Nt=256)
-    go = oracle_geometry(params)
-    lo, hi, _ = O.candidate_band(go, 8)
-    band = np.arange(lo, hi + 1)
-    idx = O.select_indices(go, O.SEL_RANDOM, 8, True, 12)
-    xi = synth.rademacher((go.S, go.Nt), seed=13)
-    g = sfs.Geometry(**params)
-    bop = sfs.Operator.from_indices(g, np.tile(band.astype(np.int32), (go.S, 1)),
-                                    precision=sfs.PRECISION_NAMES[mode])
-    bop._geom = g
-    mx = sfs.Mixing(bop, idx, xi)
-    ref = X.MixedOperator(go, band, idx, xi)
+    mx, ref, go, idx, band, xi = build(sfs, params, 8, 12, precision=sfs.PRECISION_NAMES[mode])
     rng = np.random.default_rng(14)
     x = crandn(rng, go.Nz, go.Ny, go.Nx)
     y = crandn(rng, go.S, 8)
