@@ -472,22 +472,71 @@ class LateralFFTOperator:
     Eq. (4) evaluated only at the kept bins; ``lateral_generator`` builds
     those.  The adjoint is the composition beta = beta_H o beta_Phi of
     Sec. IV-B.  Pinned against ``dense_A``.
+
+    ``workers`` > 1 runs independent pieces on that many threads: the
+    generator planes of different bins, the FFTs of different planes, and the
+    depth sums of different lateral wavenumbers.  Every output element is
+    computed by the same operations as with one worker, so the results are
+    identical; only the wall time changes.
     """
 
-    def __init__(self, g: Geometry, idx):
+    def __init__(self, g: Geometry, idx, workers: int = 1):
         self.g = g
         self.idx = np.asarray(idx, dtype=np.int32)
         self.M = self.idx.shape[1]
         self.bins = np.unique(self.idx)                    # union U, ascending
         self.Lx, self.Ly = 2 * g.Nx - 1, 2 * g.Ny - 1
+        self.workers = max(1, int(workers))
+        self._pool = None
         # Hhat[u, z] = FFT2 of the generator for bin U[u], depth z
         self.Hhat = np.empty((self.bins.size, g.Nz, self.Ly, self.Lx),
                              dtype=np.complex128)
-        for u, k in enumerate(self.bins):
-            for iz in range(g.Nz):
-                self.Hhat[u, iz] = np.fft.fft2(lateral_generator(g, int(k), iz))
+
+        def build(us):
+            for u in us:
+                k = int(self.bins[u])
+                for iz in range(g.Nz):
+                    self.Hhat[u, iz] = np.fft.fft2(lateral_generator(g, k, iz))
+        self._chunks(self.bins.size, build)
         # for each kept (s, m): which union entry
         self.u_of = np.searchsorted(self.bins, self.idx)  # [S][M]
+
+    def _chunks(self, n, fn):
+        """fn(range) over a split of range(n): inline for one worker, else on
+        the operator's thread pool (numpy releases the GIL in these calls)."""
+        if self.workers == 1 or n < 2:
+            fn(range(n))
+            return
+        if self._pool is None:
+            from concurrent.futures import ThreadPoolExecutor
+            self._pool = ThreadPoolExecutor(self.workers)
+        parts = [range(int(c[0]), int(c[-1]) + 1)
+                 for c in np.array_split(np.arange(n), min(n, 4 * self.workers)) if c.size]
+        list(self._pool.map(fn, parts))
+
+    def _fft2(self, planes, inverse=False):
+        out = np.empty(planes.shape, dtype=np.complex128)
+        f = np.fft.ifft2 if inverse else np.fft.fft2
+
+        def run(r):
+            out[r.start:r.stop] = f(planes[r.start:r.stop])
+        self._chunks(planes.shape[0], run)
+        return out
+
+    def _depth_sum(self, spec, adjoint):
+        """Forward: sum_z Hhat[u, z] spec[z]; adjoint: sum_u conj(Hhat[u, z])
+        spec[u]; both per lateral wavenumber (a, b)."""
+        U, Nz = self.Hhat.shape[:2]
+        out = np.empty(((Nz if adjoint else U), self.Ly, self.Lx), dtype=np.complex128)
+
+        def run(r):
+            a = slice(r.start, r.stop)
+            if adjoint:
+                out[:, a] = np.einsum("uzab,uab->zab", np.conj(self.Hhat[:, :, a]), spec[:, a])
+            else:
+                out[:, a] = np.einsum("uzab,zab->uab", self.Hhat[:, :, a], spec[:, a])
+        self._chunks(self.Ly, run)
+        return out
 
     def _pad(self, planes):
         out = np.zeros(planes.shape[:-2] + (self.Ly, self.Lx), dtype=np.complex128)
@@ -498,9 +547,9 @@ class LateralFFTOperator:
         """y = A x.  x: [Nz][Ny][Nx] (or flat V) -> y: [S][M]."""
         g = self.g
         x = np.asarray(x, dtype=np.complex128).reshape(g.Nz, g.Ny, g.Nx)
-        xh = np.fft.fft2(self._pad(x))                               # [Nz][Ly][Lx]
-        yh = np.einsum("uzab,zab->uab", self.Hhat, xh)               # sum over depth
-        yk = np.fft.ifft2(yh)[:, :g.Ny, :g.Nx].reshape(self.bins.size, g.S)
+        xh = self._fft2(self._pad(x))                                # [Nz][Ly][Lx]
+        yh = self._depth_sum(xh, adjoint=False)                      # sum over depth
+        yk = self._fft2(yh, inverse=True)[:, :g.Ny, :g.Nx].reshape(self.bins.size, g.S)
         s = np.arange(g.S)[:, None]
         return yk[self.u_of, s]                                      # select
 
@@ -511,11 +560,11 @@ class LateralFFTOperator:
         r = np.zeros((self.bins.size, g.S), dtype=np.complex128)
         s = np.broadcast_to(np.arange(g.S)[:, None], y.shape)
         np.add.at(r, (self.u_of, s), y)                              # beta_Phi
-        rh = np.fft.fft2(self._pad(r.reshape(-1, g.Ny, g.Nx)))       # [U][Ly][Lx]
+        rh = self._fft2(self._pad(r.reshape(-1, g.Ny, g.Nx)))        # [U][Ly][Lx]
         # adjoint of crop(ifft2(Hhat * fft2(pad(.)))): crop(ifft2(conj(Hhat) *
         # fft2(pad(.)))) since ifft2 = fft2^H / (Lx Ly)
-        xh = np.einsum("uzab,uab->zab", np.conj(self.Hhat), rh)
-        return np.fft.ifft2(xh)[:, :g.Ny, :g.Nx]
+        xh = self._depth_sum(rh, adjoint=True)
+        return self._fft2(xh, inverse=True)[:, :g.Ny, :g.Nx]
 
 
 # --------------------------------------------------------------------------
@@ -531,20 +580,22 @@ def soft_threshold(z, alpha: float):
     return z * scale
 
 
-def fista_momentum(iters: int):
-    """Momentum coefficients beta_k = (t_k - 1)/t_{k+1}, t_1 = 1,
-    t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2 (Algorithm 1), for k = 1..iters."""
-    t = 1.0
+def fista_momentum(iters: int, t1: float = 1.0):
+    """Momentum coefficients beta_k = (t_k - 1)/t_{k+1},
+    t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2 (Algorithm 1), for k = 1..iters from
+    t_1 (1 for a fresh start).  Returns (beta, t_{iters+1})."""
+    t = float(t1)
     out = np.empty(iters)
     for k in range(iters):
         t_next = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * t * t))
         out[k] = (t - 1.0) / t_next
         t = t_next
-    return out
+    return out, t
 
 
 def fista(apply_A: Callable, apply_AH: Callable, y, lam: float, L: float,
-          iters: int, x0=None, history: Optional[list] = None):
+          iters: int, x0=None, history: Optional[list] = None, resume=None,
+          return_state: bool = False):
     """FISTA (Algorithm 1) for min 1/2 ||A x - y||^2 + lam ||x||_1.
 
     Readings of Algorithm 1: the printed step gamma - 2 s beta(phi(gamma) - y)
@@ -556,14 +607,23 @@ def fista(apply_A: Callable, apply_AH: Callable, y, lam: float, L: float,
       x_k      = tau_{lam/L}(gamma_k - A^H(A gamma_k - y)/L)
       gamma_k+1 = x_k + beta_k (x_k - x_{k-1})
     Returns x_K.  ``history`` (if a list) receives F(x_k) per iteration.
+    The iteration's whole state after K steps is (gamma_{K+1}, x_K,
+    t_{K+1}): with return_state the call returns (x_K, state), and
+    ``resume=state`` continues from it in place of x0.
     """
     y = np.asarray(y, dtype=np.complex128)
-    if x0 is None:
-        x_prev = np.zeros_like(np.asarray(apply_AH(y), dtype=np.complex128))
+    if resume is not None:
+        gamma0, x_prev, t1 = resume
+        gamma = np.array(gamma0, dtype=np.complex128)
+        x_prev = np.array(x_prev, dtype=np.complex128)
     else:
-        x_prev = np.array(x0, dtype=np.complex128)
-    gamma = x_prev.copy()
-    beta = fista_momentum(iters)
+        if x0 is None:
+            x_prev = np.zeros_like(np.asarray(apply_AH(y), dtype=np.complex128))
+        else:
+            x_prev = np.array(x0, dtype=np.complex128)
+        gamma = x_prev.copy()
+        t1 = 1.0
+    beta, t_end = fista_momentum(iters, t1)
     for k in range(iters):
         grad = apply_AH(apply_A(gamma) - y)
         x = soft_threshold(gamma - grad / L, lam / L)
@@ -572,6 +632,8 @@ def fista(apply_A: Callable, apply_AH: Callable, y, lam: float, L: float,
         if history is not None:
             r = apply_A(x) - y
             history.append(0.5 * np.vdot(r, r).real + lam * np.abs(x).sum())
+    if return_state:
+        return x_prev, (gamma, x_prev, t_end)
     return x_prev
 
 
@@ -589,7 +651,7 @@ def fista_backtracking(apply_A: Callable, apply_AH: Callable, y, lam: float, L0:
     y = np.asarray(y, dtype=np.complex128)
     x_prev = np.zeros_like(np.asarray(apply_AH(y), dtype=np.complex128))
     gamma = x_prev.copy()
-    beta = fista_momentum(iters)
+    beta, _ = fista_momentum(iters)
     L = float(L0)
 
     def f(v):

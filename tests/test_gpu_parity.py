@@ -222,7 +222,7 @@ def test_fista_mu_rule_warm_start_and_monitor(sfs):
     assert rel_err(x_w, r_w) <= TOL_FISTA
     # objective monitor: 1/2||A gamma_k - y||^2 + lam ||x_k||_1
     _, hist = op.fista(to_dev(y), lam, L, 10, obj_hist=True)
-    beta = O.fista_momentum(10)
+    beta, _ = O.fista_momentum(10)
     gam = np.zeros(op.shape_x, complex)
     xp = gam.copy()
     for k in range(10):
@@ -238,20 +238,53 @@ def test_fista_mu_rule_warm_start_and_monitor(sfs):
     assert np.all(to_host(op.fista(to_dev(y), big, L, 20)) == 0)
 
 
-def test_fista_vol32_full_size_30_iterations(sfs):
-    w = synth.WORKLOADS["vol32"]
-    params = synth.geometry_params("vol32")
-    g, op, go, idx = make_pair(sfs, params, M=w["M"], seed=1001)
+@pytest.mark.parametrize("case", [
+    ("fp32", dict(Nx=10, Ny=10, Nz=16, dz=0.15e-3, Nt=256), 12),
+    ("fp16", dict(Nx=10, Ny=10, Nz=16, dz=0.15e-3, Nt=256), 12),
+    ("fp32", dict(Nx=40, Ny=36, Nz=10, dz=0.15e-3, Nt=256), 10),   # 128 x 128 planes
+])
+def test_fista_resumed_from_state_is_bit_exact(sfs, case):
+    """Algorithm 1's state (gamma_{k+1}, x_k, t_{k+1}) through the ABI: 30
+    iterations, then 30 resumed from the state buffer, equal 60 iterations in
+    one call bit for bit, and the FP64 oracle's 60 within the FISTA bar; a
+    restart from x_30 (momentum back at t = 1) differs."""
+    import torch
+    mode, over, M = case
+    params = geom_params(**over)
+    g = sfs.Geometry(**params)
+    go = oracle_geometry(params)
+    idx = O.select_indices(go, O.SEL_RANDOM, M, True, 9)
+    op = sfs.Operator.from_indices(g, idx, precision=sfs.PRECISION_NAMES[mode])
     ref = O.LateralFFTOperator(go, idx)
-    x_true = synth.scene((g.Nz, g.Ny, g.Nx), w["n_scatter"], w["amp"], seed=1001)
+    x_true = synth.scene(op.shape_x, 4, "uniform", seed=10)
     y0 = ref.apply_A(x_true)
-    sig = synth.noise_scale(float(np.vdot(y0, y0).real), y0.size, w["snr_db"])
-    y = (y0 + sig * synth.unit_noise(y0.shape, seed=5)).astype(np.complex64).astype(complex)
-    L, _ = op.lipschitz(max_iter=300, rtol=1e-6, seed=2, safety=1e-3)
-    lam = O.lambda_from_mu(ref.apply_AH, y, w["mu"])
-    x_ref = O.fista(ref.apply_A, ref.apply_AH, y, lam, L, 30)
-    x_gpu = to_host(op.fista(to_dev(y), lam, L, 30))
-    assert rel_err(x_gpu, x_ref) <= TOL_FISTA
+    sig = synth.noise_scale(float(np.vdot(y0, y0).real), y0.size, 20.0)
+    y = (y0 + sig * synth.unit_noise(y0.shape, seed=11)).astype(np.complex64).astype(complex)
+    L, _ = O.power_iteration(ref.apply_A, ref.apply_AH, op.shape_x, 1, max_iter=400, rtol=1e-10)
+    L *= 1.001
+    lam = O.lambda_from_mu(ref.apply_AH, y, 0.05)
+    yd = to_dev(y)
+    x60 = to_host(op.fista(yd, lam, L, 60))
+    state = op.new_fista_state()
+    x30 = op.fista(yd, lam, L, 30, state=state)
+    torch.cuda.synchronize()
+    st = state.cpu().numpy()
+    assert np.array_equal(st[op.V:2 * op.V].reshape(op.shape_x), x30.cpu().numpy())
+    t31, k = st[2 * op.V:].view(np.float64)[0], st[2 * op.V:].view(np.int64)[1]
+    _, t_ref = O.fista_momentum(30)
+    assert k == 30 and t31 == pytest.approx(t_ref, rel=1e-15)
+    x_res = to_host(op.fista(yd, lam, L, 30, state=state, resume=True))
+    assert np.array_equal(x_res, x60)
+    assert state.cpu().numpy()[2 * op.V:].view(np.int64)[1] == 60
+    x_ref = O.fista(ref.apply_A, ref.apply_AH, y, lam, L, 60)
+    assert rel_err(x_res, x_ref) <= (TOL_FISTA if mode == "fp32" else 4e-3)
+    x_warm = to_host(op.fista(yd, lam, L, 30, x=x30.clone(), warm_start=True))
+    assert rel_err(x_warm, x60) > 1e-6
+    # RESUME needs a state buffer and excludes WARM_START
+    with pytest.raises(sfs.SfsError):
+        op.fista(yd, lam, L, 5, resume=True)
+    with pytest.raises(sfs.SfsError):
+        op.fista(yd, lam, L, 5, state=state, resume=True, warm_start=True)
 
 
 def test_deterministic_and_stream_ordered(sfs):
@@ -346,7 +379,8 @@ def test_128_point_planes_match_oracle(sfs, mode):
 def test_vol64_full_size_sampled_outputs(sfs, mode):
     """The 64 x 64 x 256 workload (Nt = 1024, M = 128, 128 x 128 planes) at
     full size: 24 sampled entries of A x against rows of the dense
-    definition, 16 sampled voxels of A^H y against its columns."""
+    definition (Eq. (4)), 16 sampled voxels of A^H y against its columns,
+    within the mode's norm-wise bar."""
     w = synth.WORKLOADS["vol64"]
     params = synth.geometry_params("vol64")
     go = oracle_geometry(params)
@@ -364,11 +398,11 @@ def test_vol64_full_size_sampled_outputs(sfs, mode):
     ref_y = np.concatenate([O.A_rows(go, idx, rows[i:i + 6]) @ x.ravel() for i in range(0, 24, 6)])
     vox = rng.choice(g.V, 16, replace=False)
     ref_x = O.A_cols(go, idx, vox).conj().T @ y.ravel()
-    assert np.abs(ya[rows] - ref_y).max() <= tol_el * np.abs(ya).max()
-    assert np.abs(xa[vox] - ref_x).max() <= tol_el * np.abs(xa).max()
-    if mode == "fp32":
-        assert rel_err(ya[rows], ref_y) <= tol
-        assert rel_err(xa[vox], ref_x) <= tol
+    # norm-wise on the sampled entries against the dense definition (the
+    # element-wise bound, normalised by the oracle's largest entry, is in
+    # test_gpu_fullsize.py with the whole applies)
+    assert rel_err(ya[rows], ref_y) <= tol
+    assert rel_err(xa[vox], ref_x) <= tol
 
 
 @pytest.mark.parametrize("mode", ["fp32", "fp16"])

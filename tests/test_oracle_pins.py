@@ -424,7 +424,7 @@ def test_soft_threshold_special_cases():
     z = np.array([0, 3 + 4j, 0.5j, -2.0])
     out = O.soft_threshold(z, 1.0)
     np.testing.assert_allclose(out, [0, (3 + 4j) * 0.8, 0, -1.0], atol=1e-15)
-    beta = O.fista_momentum(4)
+    beta, _ = O.fista_momentum(4)
     assert beta[0] == 0.0 and np.all(np.diff(beta) > 0)
 
 
@@ -477,3 +477,25 @@ def test_splitmix64_matches_published_outputs():
     assert [s.next() for _ in gold] == gold
     gamma = (math.isqrt(5 << 128) - (1 << 64)) // 2       # floor(2^64 (sqrt(5) - 1) / 2)
     assert gamma == O.sfs_oracle._GOLDEN and gamma % 2 == 1
+
+
+def test_fista_resumed_from_its_state_equals_one_run():
+    """The iteration state (gamma_{K+1}, x_K, t_{K+1}) carries Algorithm 1
+    across calls: 17 + 13 resumed iterations equal 30 in one run exactly,
+    and restarting the momentum at t = 1 instead (a warm start from x_K)
+    does not."""
+    g = O.Geometry(Nx=4, Ny=4, dx=0.5e-3, dy=0.5e-3, Nz=6, z0=10e-3, dz=0.15e-3, c=5900.0,
+                   fs=40e6, Nt=64, fc=5e6, frac_bw=0.7, theta=0.0)
+    idx = O.select_indices(g, O.SEL_RANDOM, 6, True, 3)
+    op = O.LateralFFTOperator(g, idx)
+    x_true = synth.scene((g.Nz, g.Ny, g.Nx), 3, "uniform", seed=4)
+    y = op.apply_A(x_true)
+    L = O.power_iteration(op.apply_A, op.apply_AH, x_true.shape, 1, max_iter=400, rtol=1e-12)[0] * 1.001
+    lam = 0.05 * np.abs(op.apply_AH(y)).max()
+    x30 = O.fista(op.apply_A, op.apply_AH, y, lam, L, 30)
+    x17, st = O.fista(op.apply_A, op.apply_AH, y, lam, L, 17, return_state=True)
+    assert st[2] > 1.0 and np.array_equal(st[1], x17)
+    x_res = O.fista(op.apply_A, op.apply_AH, y, lam, L, 13, resume=st)
+    assert np.array_equal(x_res, x30)
+    x_warm = O.fista(op.apply_A, op.apply_AH, y, lam, L, 13, x0=x17)
+    assert np.linalg.norm(x_warm - x30) > 1e-6 * np.linalg.norm(x30)
