@@ -7,7 +7,7 @@ The operator (generator table) and its Lipschitz constant are built once per
 geometry before the timed region, as the paper reuses sigma_max across
 reconstructions; their setup times are reported separately.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload vol32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload vol64]
   python bench.py --impl reference ...   # the FP64 CPU oracle, same workload
 
 Multi-GPU (torchrun): independent replicas, one scene per rank (weak
@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="vol32", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default="vol64", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--strategy", default="random", choices=sorted(STRATEGY_NAMES))
     ap.add_argument("--precision", default="fp32",
                     choices=["fp32", "tf32x3", "bf16", "bf16x2", "fp16", "fp16x2"],
@@ -51,8 +51,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-study", action="store_true",
                     help="skip the BF16 / BF16X2 vs FP32 time-to-same-NMSE study")
-    ap.add_argument("--batch-scenes", type=int, default=16,
-                    help="scenes of the batched-serving measurement (0 skips it)")
+    ap.add_argument("--batch-scenes", type=int, default=None,
+                    help="scenes of the batched-serving measurement (0 skips it; default 16, "
+                         "4 on the 64 x 64 x 256 workload)")
+    ap.add_argument("--no-strategies", dest="strategies", action="store_false",
+                    help="skip the random / contiguous / equispaced comparison on the 32 x 32 workload")
     ap.add_argument("--no-sweep", dest="sweep", action="store_false",
                     help="skip the run-time sweep of one apply over Nz = Nt and Nx = Ny")
     ap.add_argument("--no-backtracking", dest="backtracking", action="store_false",
@@ -68,6 +71,8 @@ def parse():
     ap.add_argument("--learned-steps", type=int, default=1250,
                     help="training steps of the learned unrolled ISTA measurement on the vol32 "
                          "workload (0 skips it)")
+    ap.add_argument("--oracle-workers", type=int, default=0,
+                    help="threads of the all-core FP64 oracle timing (0: every host core)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -85,14 +90,16 @@ DTYPE_OF = {"fp32": "c64 (f32)",
 REDUCED = ("bf16", "bf16x2", "fp16", "fp16x2")
 
 
-def precision_study(sfs, torch, geom, op, args, w, iters, y, L, x_true, flush, stream):
+def precision_study(sfs, torch, geom, op, args, w, iters, y, L, x_true, flush, stream, oracle=None):
     """FISTA with the FP32 contractions against the 16-bit ones on the
     same scene, measurements, lambda rule and L: per mode the device time of
     one solve (L2 flushed first), the NMSE against the true scene, and the
     iterations and time a reduced-precision solve needs to reach the FP32
     solve's NMSE (first of K, 1.1 K, 1.25 K, 1.5 K, 2 K iterations within
     0.01 dB).  Errors are stated against the FP32 result of the same call
-    (which itself matches the FP64 oracle to about 1e-6 in the tests)."""
+    and, when the FP64 oracle of the workload is given, against it: A x of
+    the true scene, and the iterate after `oracle_iters` FISTA iterations
+    (20, with the oracle's own lambda and the same L on both sides)."""
     xt = torch.from_numpy(x_true.astype(np.complex64)).cuda()
     ops = {}
     for mode in ("fp32",) + REDUCED:
@@ -118,20 +125,46 @@ def precision_study(sfs, torch, geom, op, args, w, iters, y, L, x_true, flush, s
     def nmse_db(x):
         return float(10 * np.log10(np.linalg.norm(x - x_true) ** 2 / np.linalg.norm(x_true) ** 2))
 
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    ref = None
+    if oracle is not None:
+        O, oop, _, _ = oracle
+        yh = y.cpu().numpy().astype(np.complex128)
+        lam64 = O.lambda_from_mu(oop.apply_AH, yh, w["mu"])
+        k64 = 20
+        ax64 = oop.apply_A(x_true)
+        x64 = O.fista(oop.apply_A, oop.apply_AH, yh, lam64, L, k64)
+        ref = {"ax": ax64, "x": x64, "lam": lam64, "iters": k64}
+
+    def vs_fp64(o):
+        if ref is None:
+            return {}
+        axm = o.apply_A(xt).cpu().numpy().astype(np.complex128)
+        xk = o.fista(y, ref["lam"], L, ref["iters"]).cpu().numpy().astype(np.complex128)
+        return {"rel_err_Ax_vs_fp64": rel(axm, ref["ax"]),
+                "rel_err_x%d_vs_fp64" % ref["iters"]: rel(xk, ref["x"]),
+                "nmse_db_x%d" % ref["iters"]: nmse_db(xk)}
+
     ax32 = ops["fp32"].apply_A(xt).cpu().numpy().astype(np.complex128)
     t32, x32 = solve(ops["fp32"], iters)
     target = nmse_db(x32)
     out = {"reference": "fp32", "iters": iters, "target_nmse_db": target,
            "timing": "device time of one solve (lambda rule + iterations), best of 3, L2 flushed first",
-           "modes": {"fp32": {"ms_per_solve": t32, "nmse_db": target,
-                              "table_bytes": ops["fp32"].info["table_bytes"]}}}
+           "modes": {"fp32": dict({"ms_per_solve": t32, "nmse_db": target,
+                                   "table_bytes": ops["fp32"].info["table_bytes"]}, **vs_fp64(ops["fp32"]))}}
+    if ref is not None:
+        out["fp64_oracle"] = {"iters": ref["iters"], "nmse_db_x%d" % ref["iters"]: nmse_db(ref["x"]),
+                              "note": "FP64 lateral-FFT oracle (Algorithm 2) on the host: A x of the true "
+                                      "scene and FISTA with its own lambda (mu rule) and the same L"}
     for mode in REDUCED:
         o = ops[mode]
         axm = o.apply_A(xt).cpu().numpy().astype(np.complex128)
         tk, xk = solve(o, iters)
         rec = {"ms_per_solve": tk, "nmse_db": nmse_db(xk), "table_bytes": o.info["table_bytes"],
-               "rel_err_Ax_vs_fp32": float(np.linalg.norm(axm - ax32) / np.linalg.norm(ax32)),
-               "rel_err_x_vs_fp32": float(np.linalg.norm(xk - x32) / np.linalg.norm(x32))}
+               "rel_err_Ax_vs_fp32": rel(axm, ax32), "rel_err_x_vs_fp32": rel(xk, x32)}
+        rec.update(vs_fp64(o))
         reach = None
         for f in (1.0, 1.1, 1.25, 1.5, 2.0):
             k = int(math.ceil(f * iters))
@@ -145,6 +178,43 @@ def precision_study(sfs, torch, geom, op, args, w, iters, y, L, x_true, flush, s
         else:
             rec.update({"iters_to_target": None, "ms_to_target": None, "speedup_vs_fp32": None})
         out["modes"][mode] = rec
+    return out
+
+
+def strategy_study(sfs, torch, args, flush, stream, seed):
+    """The 32 x 32 x 128 workload's strategy comparison: random (per
+    position), contiguous and equispaced bins, each set computed by the
+    library's host selection and by the FP64 oracle's and compared bit for
+    bit; per strategy FISTA it/s (device time of one solve, best of 3, L2
+    flushed), the NMSE after the workload's iterations, the union U and
+    the table bytes."""
+    import oracle as O
+    name = "vol32"
+    out = {"workload": name, "strategies": {}}
+    for strat in ("random", "contiguous", "equispaced"):
+        ws = workload_setup(sfs, torch, name, strat, seed)
+        w, op, y, L, x_true = ws["w"], ws["op"], ws["y"], ws["L"], ws["x_true"]
+        go = O.Geometry(**synth.geometry_params(name))
+        idx = O.select_indices(go, STRATEGY_NAMES[strat], w["M"], True, seed)
+        x = torch.empty(op.shape_x, dtype=torch.complex64, device="cuda")
+        op.fista(y, -w["mu"], L, w["iters"], x=x)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(3):
+            flush.fill_(7)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            op.fista(y, -w["mu"], L, w["iters"], x=x)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b)
+            best = t if best is None else min(best, t)
+        xh = x.cpu().numpy().astype(np.complex128)
+        out["strategies"][strat] = {
+            "identical_index_sets_cpu_gpu": bool(np.array_equal(op.idx, idx)),
+            "U": op.info["U"], "table_bytes": op.info["table_bytes"], "iters": w["iters"],
+            "ms_per_solve": best, "fista_it_per_s": w["iters"] / (best / 1e3),
+            "nmse_db": float(10 * np.log10(np.linalg.norm(xh - x_true) ** 2 / np.linalg.norm(x_true) ** 2))}
     return out
 
 
@@ -269,15 +339,18 @@ def runtime_sweep(sfs, torch, flush, stream, seed):
     return out
 
 
-def mixing_study(sfs, torch, geom, op, args, w, iters, x_true, flush, stream, seed):
-    """The workload measured through Rademacher-mixed A-scans (Phi_rnd,m,f:
-    own xi_s and own random bins per position): band operator (the signed
-    bins within 140 dB of the pulse peak, sfs_mixing_band, at every
-    position) plus the mixing object; FISTA with
-    the same iterations and mu rule, L by power iteration on A_mix.  Reports
-    the device time of a solve (L2 flushed first, best of 3), FISTA it/s and
+def mixing_study(sfs, torch, args, flush, stream, seed):
+    """The 32 x 32 x 128 workload measured through Rademacher-mixed A-scans
+    (Phi_rnd,m,f: own xi_s and own random bins per position): band operator
+    (the signed bins within 140 dB of the pulse peak, sfs_mixing_band, at
+    every position) plus the mixing object; FISTA with the workload's
+    iterations and mu rule, L by power iteration on A_mix.  Reports the
+    device time of a solve (L2 flushed first, best of 3), FISTA it/s and
     the NMSE against the true scene, beside the unmixed solve's NMSE."""
-    Nt = w["Nt"]
+    name = "vol32"
+    ws = workload_setup(sfs, torch, name, "random", seed)
+    w, geom, op, x_true = ws["w"], ws["geom"], ws["op"], ws["x_true"]
+    iters, Nt = w["iters"], w["Nt"]
     xi = synth.rademacher((geom.S, Nt), seed=seed + 4242)
     mx = sfs.Mixing.create(geom, op.idx, xi)
     band = mx.band.idx[0]
@@ -301,10 +374,12 @@ def mixing_study(sfs, torch, geom, op, args, w, iters, x_true, flush, stream, se
         best = t if best is None else min(best, t)
     xh = x.cpu().numpy().astype(np.complex128)
     nmse = float(10 * np.log10(np.linalg.norm(xh - x_true) ** 2 / np.linalg.norm(x_true) ** 2))
-    return {"strategy": "Phi_rnd,m,f (xi_s and bins drawn per position)", "band_bins": int(band.size),
-            "band_signed": [int(band[0]), int(band[-1])],
+    xu = op.fista(ws["y"], -w["mu"], ws["L"], iters).cpu().numpy().astype(np.complex128)
+    nmse_u = float(10 * np.log10(np.linalg.norm(xu - x_true) ** 2 / np.linalg.norm(x_true) ** 2))
+    return {"workload": name, "strategy": "Phi_rnd,m,f (xi_s and bins drawn per position)",
+            "band_bins": int(band.size), "band_signed": [int(band[0]), int(band[-1])],
             "M": int(w["M"]), "iters": iters, "ms_per_solve": best, "fista_it_per_s": iters / (best / 1e3),
-            "nmse_db": nmse, "L": L, "launches_per_iter": 6,
+            "nmse_db": nmse, "unmixed_nmse_db": nmse_u, "L": L, "launches_per_iter": 6,
             "timing": "device time of one solve (lambda rule + iterations), best of 3, L2 flushed first"}
 
 
@@ -414,7 +489,7 @@ def serving_study(sfs, torch, args, flush, stream, seed):
             "mix": "grids {16,32,48,64}^2, depths {64,128,256}, M {32,64,128}, 10 scatterers, 20 dB"}
 
 
-def learned_study(sfs, torch, op, args, w, L, stream, seed):
+def learned_study(sfs, torch, args, stream, seed):
     """Train the 16-layer unrolled ISTA (library kernels: forward, backward,
     Adam) for args.learned_steps steps of 8 fresh scenes of the LEARNED
     recipe (1250 steps: 10^4 scenes), then on args.learned_eval held-out
@@ -422,6 +497,9 @@ def learned_study(sfs, torch, op, args, w, L, stream, seed):
     lambda by the mu rule) at 4 .. 300 iterations: the first count of the
     ladder that reaches the network's NMSE, and its time."""
     from paper_2012_04534_gb300 import lista
+    ws = workload_setup(sfs, torch, synth.LEARNED["workload"], "random", seed, args.precision
+                        if args.precision in ("fp32", "bf16", "fp16") else "fp32")
+    op, w, L = ws["op"], ws["w"], ws["L"]
     layers, B = synth.LEARNED["layers"], 8
     net = lista.LISTA(op, layers, B, L)
     rng = np.random.default_rng(seed + 4242)
@@ -484,15 +562,39 @@ def learned_study(sfs, torch, op, args, w, L, stream, seed):
         ladder.append({"iters": K, "nmse_db": nm, "ms_per_batch": ms_k})
         if reach is None and nm <= nmse_lista:
             reach = (K, ms_k)
+    # the target: plain FP32 FISTA's NMSE after the workload's iterations
+    target = ladder[-1]["nmse_db"]
+    fista_to_target = next(r for r in ladder if r["nmse_db"] <= target + 0.01)
+
+    def net_then_fista(y, K):
+        x0 = net.forward(y)
+        return op.fista_batched(y, -w["mu"], L, K, x=x0, warm_start=True) if K > 0 else x0
+
+    warm = []
+    warm_reach = None
+    for K in (0, 8, 16, 32, 48, 64, 96, 128, 160, 192, 224, 256, 300):
+        ms_k, xk = timed(lambda y, K=K: net_then_fista(y, K))
+        nm = mean_nmse(xk)
+        warm.append({"fista_iters": K, "nmse_db": nm, "ms_per_batch": ms_k})
+        if nm <= target + 0.01:
+            warm_reach = (K, ms_k)
+            break
     return {"layers": layers, "batch": B, "train_steps": steps, "train_scenes": steps * B,
-            "train_s": t_train, "precision": args.precision,
+            "train_s": t_train, "precision": op.info["precision"],
             "scenes": "1-20 scatterers, U(0.5,1) magnitudes, uniform phase, 10-30 dB SNR "
                       "(training scenes drawn fresh every step; %d held-out scenes)" % (len(evals) * B),
             "nmse_db": nmse_lista, "ms_per_batch": ms_lista,
             "fista": ladder,
             "fista_iters_to_same_nmse": None if reach is None else reach[0],
             "fista_ms_to_same_nmse": None if reach is None else reach[1],
-            "speedup_vs_fista": None if reach is None else reach[1] / ms_lista}
+            "speedup_vs_fista": None if reach is None else reach[1] / ms_lista,
+            "target": {"what": "mean NMSE of plain FP32 FISTA after %d iterations (within 0.01 dB)"
+                               % ladder[-1]["iters"], "nmse_db": target},
+            "fista_to_target": {"iters": fista_to_target["iters"], "ms_per_batch": fista_to_target["ms_per_batch"]},
+            "network_plus_fista": warm,
+            "network_plus_fista_to_target": None if warm_reach is None else
+            {"fista_iters": warm_reach[0], "ms_per_batch": warm_reach[1],
+             "speedup_vs_fista": fista_to_target["ms_per_batch"] / warm_reach[1]}}
 
 
 def workload_desc(name, w, strategy, iters):
@@ -564,13 +666,40 @@ class ClockSampler:
 
 # ------------------------------------------------------------- CPU oracle ---
 
-def oracle_setup(name, w, strategy, seed):
+def host_cores():
+    return os.cpu_count() or 1
+
+
+def mem_available_gb():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    return 0.0
+
+
+def oracle_table_gb(name, w, strategy, seed):
+    """Host memory of the FP64 oracle's generator table for a workload."""
+    import oracle as O
+    params = synth.geometry_params(name)
+    go = O.Geometry(**params)
+    idx = O.select_indices(go, STRATEGY_NAMES[strategy], w["M"], True, seed)
+    U = np.unique(idx).size
+    return U * w["Nz"] * (2 * w["Nx"] - 1) * (2 * w["Ny"] - 1) * 16 / 2 ** 30
+
+
+def oracle_setup(name, w, strategy, seed, workers=1):
+    """The FP64 lateral-FFT oracle of a workload (Algorithm 2) and its noisy
+    measurements of the workload's scene: (O, operator, y, table build s)."""
     import oracle as O
     params = synth.geometry_params(name)
     go = O.Geometry(**params)
     idx = O.select_indices(go, STRATEGY_NAMES[strategy], w["M"], True, seed)
     t0 = time.perf_counter()
-    op = O.LateralFFTOperator(go, idx)
+    op = O.LateralFFTOperator(go, idx, workers=workers)
     t_table = time.perf_counter() - t0
     x_true = make_scene(w, seed)
     y0 = op.apply_A(x_true)
@@ -579,13 +708,16 @@ def oracle_setup(name, w, strategy, seed):
     return O, op, y, t_table
 
 
-def time_oracle_iterations(O, op, y, mu, seconds):
-    """FISTA iterations of the FP64 oracle for about `seconds`; returns
-    (iterations/s, iterations done, threads actually used)."""
+def time_oracle_iterations(O, op, y, mu, seconds, workers=None):
+    """FISTA iterations of the FP64 oracle for about `seconds` on `workers`
+    threads (the operator's own count if None); returns (iterations/s,
+    iterations done, threads actually used: CPU time / wall time)."""
+    if workers is not None:
+        op.workers = workers
     lam = O.lambda_from_mu(op.apply_AH, y, mu)
     L = 1.0e9  # step size does not change the work per iteration
     # one iteration first to size the sample
-    c0, t0 = time.process_time(), time.perf_counter()
+    t0 = time.perf_counter()
     O.fista(op.apply_A, op.apply_AH, y, lam, L, 1)
     one = time.perf_counter() - t0
     n = max(1, int(seconds / max(one, 1e-6)))
@@ -594,6 +726,15 @@ def time_oracle_iterations(O, op, y, mu, seconds):
     wall = time.perf_counter() - t0
     cpu = time.process_time() - c0
     return n / wall, n, max(1, round(cpu / wall))
+
+
+def cpu_baseline_both(O, op, y, mu, seconds, cores):
+    """The oracle as it stands, single-thread and on `cores` threads, each
+    for about `seconds`: (all-core record, single-thread record)."""
+    v1, n1, c1 = time_oracle_iterations(O, op, y, mu, seconds, workers=1)
+    vn, nn, cn = time_oracle_iterations(O, op, y, mu, seconds, workers=cores)
+    return (dict(value=vn, iters=nn, cores=cn, workers=cores),
+            dict(value=v1, iters=n1, cores=c1, workers=1))
 
 
 def make_scene(w, seed):
@@ -637,12 +778,19 @@ def rank_seed(rank):
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the FP64 CPU oracle, as it stands, on rank 0."""
+    """--impl reference: the FP64 CPU oracle, as it stands, on rank 0, on
+    every host core (its threads split independent planes and wavenumbers)."""
     if rank != 0:
         return
     w = synth.WORKLOADS[args.workload]
     iters = args.iters or w["iters"]
-    O, op, y, _ = oracle_setup(args.workload, w, args.strategy, seed=1001)
+    cores = args.oracle_workers or host_cores()
+    need = oracle_table_gb(args.workload, w, args.strategy, 1001)
+    if mem_available_gb() < 2.5 * need + 4:
+        print(json.dumps({"impl": "reference", "unavailable": "the FP64 oracle's %.1f GB table does not fit "
+                          "the host memory available (%.1f GB)" % (need, mem_available_gb())}), flush=True)
+        return
+    O, op, y, _ = oracle_setup(args.workload, w, args.strategy, seed=1001, workers=cores)
     per_step = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         time_oracle_iterations(O, op, y, w["mu"], per_step)
@@ -661,7 +809,7 @@ def run_reference(args, rank, world):
         "config": {"workload": workload_desc(args.workload, w, args.strategy, iters)},
         "cpu_baseline": {"value": value, "unit": "it/s", "cores": threads, "kind": "oracle",
                          "sample": "%d FISTA iterations of the FP64 lateral-FFT oracle over "
-                                   "%d steps" % (n_tot, args.steps)},
+                                   "%d steps, %d threads" % (n_tot, args.steps, cores)},
         "e2e": {"value": value, "unit": "it/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -701,6 +849,40 @@ def measured_traffic(workload, strategy, precision):
     return ent
 
 
+def workload_setup(sfs, torch, name, strategy, seed, precision="fp32", lip_iters=500):
+    """Operator, scene, noisy measurements (host and device) and L of a
+    workload on the current device; setup times are returned apart."""
+    w = synth.WORKLOADS[name]
+    params = dict(synth.geometry_params(name), device=torch.cuda.current_device())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    geom = sfs.Geometry(**params)
+    op = sfs.Operator.select(geom, STRATEGY_NAMES[strategy], w["M"], True, seed,
+                             precision=sfs.PRECISION_NAMES[precision])
+    op._geom = geom
+    torch.cuda.synchronize()
+    t_table = time.perf_counter() - t0
+    x_true = make_scene(w, seed)
+    xt = torch.from_numpy(x_true.astype(np.complex64)).cuda()
+    y0 = op.apply_A(xt)
+    torch.cuda.synchronize()
+    y0h = y0.cpu().numpy().astype(np.complex128)
+    sig = synth.noise_scale(float(np.vdot(y0h, y0h).real), y0h.size, w["snr_db"])
+    y_host = (y0h + sig * synth.unit_noise(y0h.shape, seed=seed + 1)).astype(np.complex64)
+    y = torch.from_numpy(y_host).cuda()
+    t0 = time.perf_counter()
+    L, _ = op.lipschitz(max_iter=lip_iters, rtol=1e-6, seed=seed, safety=1e-3)
+    t_lip = time.perf_counter() - t0
+    return dict(w=w, geom=geom, op=op, x_true=x_true, y=y, y_host=y_host, L=L,
+                t_table=t_table, t_lip=t_lip)
+
+
+def device_caps(torch, dev):
+    """(SM count, L2 bytes) of the device, read from the driver."""
+    p = torch.cuda.get_device_properties(dev)
+    return int(p.multi_processor_count), int(getattr(p, "L2_cache_size", 0) or 0)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -723,36 +905,28 @@ def main():
     w = synth.WORKLOADS[args.workload]
     iters = args.iters or w["iters"]
     seed = rank_seed(rank)
-    params = dict(synth.geometry_params(args.workload), device=dev)
+    n_sm, l2_bytes = device_caps(torch, dev)
 
     # ---- setup (outside the timed region) ----
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    geom = sfs.Geometry(**params)
-    op = sfs.Operator.select(geom, STRATEGY_NAMES[args.strategy], w["M"], True, seed,
-                             precision=sfs.PRECISION_NAMES[args.precision])
-    torch.cuda.synchronize()
-    t_table = time.perf_counter() - t0
+    ws = workload_setup(sfs, torch, args.workload, args.strategy, seed, args.precision)
+    geom, op, x_true, y, y_host, L = ws["geom"], ws["op"], ws["x_true"], ws["y"], ws["y_host"], ws["L"]
+    t_table, t_lip = ws["t_table"], ws["t_lip"]
     info = op.info
-    x_true = make_scene(w, seed)
-    xt = torch.from_numpy(x_true.astype(np.complex64)).cuda()
-    y0 = op.apply_A(xt)
-    torch.cuda.synchronize()
-    y0h = y0.cpu().numpy().astype(np.complex128)
-    sig = synth.noise_scale(float(np.vdot(y0h, y0h).real), y0h.size, w["snr_db"])
-    y_host = (y0h + sig * synth.unit_noise(y0h.shape, seed=seed + 1)).astype(np.complex64)
-    y = torch.from_numpy(y_host).cuda()
-    t0 = time.perf_counter()
-    L, _ = op.lipschitz(max_iter=500, rtol=1e-6, seed=seed, safety=1e-3)
-    t_lip = time.perf_counter() - t0
     x = torch.empty(op.shape_x, dtype=torch.complex64, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step():
+        # the iteration graph with event nodes around the kernels of <= 32
+        # sampled iterations: the per-kernel times of the roofline come from
+        # this same timed loop
+        op.fista(y, -w["mu"], L, iters, x=x, time_kernels=True)
+
+    def step_plain():
         op.fista(y, -w["mu"], L, iters, x=x)
 
     for _ in range(args.warmup):
         step()
+        step_plain()
     torch.cuda.synchronize()
 
     def barrier():
@@ -760,12 +934,16 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    # L2 flush between timed steps: write a buffer larger than the 129 MB L2
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    # L2 flush between timed steps: write a buffer larger than the L2
+    flush = torch.empty(max(256 << 20, 2 * l2_bytes), dtype=torch.uint8, device="cuda")
 
-    def timed_steps(fn):
+    stage_acc = {"sum": np.zeros(4), "n": 0}
+
+    def timed_steps(fn, stages=False):
         """Per-step CUDA events on the library's stream; the L2 flush runs
-        between steps, outside the events.  Returns the summed step time [ms]."""
+        between steps, outside the events.  Returns the summed step time [ms].
+        With stages, the sampled per-kernel times of every step are added up
+        (read after each step's end event, outside the timed span)."""
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
         for i in range(args.steps):
@@ -773,6 +951,11 @@ def main():
             evs[i][0].record(stream)
             fn()
             evs[i][1].record(stream)
+            if stages:
+                evs[i][1].synchronize()
+                ms4, n = op.stage_times()
+                stage_acc["sum"] += np.asarray(ms4) * n
+                stage_acc["n"] += n
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in evs)
 
@@ -783,13 +966,19 @@ def main():
     clocks.start()
     time.sleep(0.3)  # let the sampler start before the timed work
     torch.cuda.nvtx.range_push("timed")
-    ms = timed_steps(step)
+    ms = timed_steps(step, stages=True)
     torch.cuda.nvtx.range_pop()
     barrier()
     clk = clocks.stop()
     ms = max_over_ranks(ms, world)
     value = job_rate(world, args.steps, iters, ms)
     launches_per_step = 4 * iters + 5 if iters > 0 else 4
+    stage_ms = (stage_acc["sum"] / max(1, stage_acc["n"])).tolist()
+
+    # the same steps on the graph without event nodes, for comparison
+    barrier()
+    torch.cuda.synchronize()
+    ms_plain = max_over_ranks(timed_steps(step_plain), world)
 
     # ---- end to end through the public API with pinned host buffers ----
     y_pin = torch.from_numpy(y_host).pin_memory()
@@ -808,98 +997,129 @@ def main():
     ms_e2e = max_over_ranks(ms_e2e, world)
     e2e = job_rate(world, args.steps, iters, ms_e2e)
 
-    # ---- roofline of the dominant kernels (events around each launch) ----
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)
-        op.fista(y, -w["mu"], L, iters, x=x, time_kernels=True)
-    fwd_ms, adj_ms, n_launch = op.kernel_times()
-    stage_ms, _ = op.stage_times()
+    # ---- roofline of the dominant kernels, from the timed loop's event nodes ----
+    fwd_ms, adj_ms = stage_ms[0], stage_ms[2]
     Nk, U, Nz, Ns = info["Nkappa"], info["U"], info["Nz"], info["Nslot"]
     # algorithmic bytes per launch: the folded table plus the spectra read and
     # written; algorithmic flops: one complex multiply-add (8 flops) per
-    # (slot, bin, depth)
+    # (wavenumber, bin, depth)
     alg_bytes = info["table_bytes"] + 8 * Ns * (Nz + U)
-    alg_flops = 8.0 * Ns * U * Nz
+    alg_flops = 8.0 * Nk * U * Nz
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(peaks_path) as fh:
             pk = json.load(fh)
         peak = float(pk["hbm_gbs"])
         sm_max = float(pk.get("sm_max_mhz", 2070.0))
+        tc_peak = float(pk["bf16_tflops"])
         peak_src = "measured"
     except (OSError, ValueError, KeyError):
-        peak, sm_max, peak_src = 6800.0, 2070.0, "fallback"
-    # FP32 FMA issue peak: 152 SMs x 128 lanes x 2 flops x max SM clock
-    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+        peak, sm_max, tc_peak, peak_src = 6800.0, 2070.0, 1900.0, "fallback"
+    # FP32 FMA issue peak: SMs x 128 lanes x 2 flops x max SM clock
+    alu_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
     avg_ms = 0.5 * (fwd_ms + adj_ms)
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
     achieved_tf = alg_flops / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else 0.0
     traffic = measured_traffic(args.workload, args.strategy, args.precision)
     hbm_frac, alu_frac = achieved / peak, achieved_tf / alu_peak
-    if hbm_frac >= alu_frac or args.precision != "fp32":
+    in_l2 = l2_bytes > 0 and alg_bytes <= l2_bytes
+    if not in_l2:
+        # the table streams from HBM on every launch
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": hbm_frac, "peak_source": peak_src}
-    else:
+                "frac": hbm_frac, "peak_source": peak_src + " (HBM copy bandwidth)"}
+    elif args.precision in ("fp32",):
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": alu_frac,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz" % sm_max}
+                "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flops x %.0f MHz" % (n_sm, sm_max)}
+    else:
+        roof = {"bound": "tensor", "achieved": achieved_tf, "peak": tc_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / tc_peak, "peak_source": peak_src + " (cuBLAS BF16 burst)"}
     roof.update({"traffic": None if traffic is None else traffic["bytes_per_launch"],
                  "kernel": "depth contraction (forward and adjoint, averaged)",
+                 "table_location": "L2-resident" if in_l2 else "HBM (table larger than the %.0f MB L2)"
+                                   % (l2_bytes / 1e6),
                  "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": alg_flops,
                  "hbm_frac": hbm_frac, "alu_frac": alu_frac,
-                 "fwd_ms": fwd_ms, "adj_ms": adj_ms, "launches_timed": 2 * n_launch,
+                 "fwd_ms": fwd_ms, "adj_ms": adj_ms, "iterations_timed": stage_acc["n"],
+                 "timing": "event-record nodes around the kernels of <= 32 sampled iterations of each "
+                           "timed step's graph; stages sum to the time of those iterations",
                  "iteration_stages_ms": {"contract_fwd": stage_ms[0], "resid_planes": stage_ms[1],
-                                         "contract_adj": stage_ms[2], "update_planes": stage_ms[3]}})
+                                         "contract_adj": stage_ms[2], "update_planes": stage_ms[3]},
+                 "iteration_ms": ms / args.steps / max(1, iters)})
 
-    # ---- precision study: reduced-precision contractions vs FP32, time to
-    # the FP32 solve's NMSE (rank 0 at N = 1 only) ----
+    ran_here = rank == 0 and world == 1
+    # ---- FP64 oracle of the workload (CPU baseline and precision study) ----
+    oracle = None
+    cores = args.oracle_workers or host_cores()
+    if ran_here and not (args.no_cpu_baseline and args.no_precision_study):
+        need = oracle_table_gb(args.workload, w, args.strategy, seed)
+        if mem_available_gb() >= 2.5 * need + 4:
+            oracle = oracle_setup(args.workload, w, args.strategy, seed, workers=cores)
+
+    # ---- precision study: reduced-precision contractions vs FP32 and the
+    # FP64 oracle, time to the FP32 solve's NMSE ----
     study = None
-    if rank == 0 and world == 1 and not args.no_precision_study:
-        study = precision_study(sfs, torch, geom, op, args, w, iters, y, L, x_true, flush, stream)
+    if ran_here and not args.no_precision_study:
+        study = precision_study(sfs, torch, geom, op, args, w, iters, y, L, x_true, flush, stream,
+                                oracle=oracle)
 
     # ---- batched serving: scenes sharing the operator in one solve ----
     batched = None
-    if rank == 0 and world == 1 and args.batch_scenes > 0:
+    nbatch = args.batch_scenes if args.batch_scenes is not None else (4 if args.workload == "vol64" else 16)
+    if ran_here and nbatch > 0:
+        args.batch_scenes = nbatch
         batched = batched_study(sfs, torch, geom, op, args, w, iters, L, flush, stream, seed)
+
+    # ---- random / contiguous / equispaced on the 32 x 32 workload ----
+    strategies = None
+    if ran_here and args.strategies:
+        strategies = strategy_study(sfs, torch, args, flush, stream, seed)
 
     # ---- run time of one apply over the shapes of the paper's run-time figure ----
     sweep = None
-    if rank == 0 and world == 1 and args.sweep:
+    if ran_here and args.sweep:
         sweep = runtime_sweep(sfs, torch, flush, stream, seed)
 
     # ---- FISTA with backtracking on the same scene ----
     backtracking = None
-    if rank == 0 and world == 1 and args.backtracking:
+    if ran_here and args.backtracking:
         backtracking = backtracking_study(sfs, torch, op, w, iters, y, L, x_true, flush, stream)
 
-    # ---- Rademacher mixing (Phi_rnd,m) on the same workload ----
+    # ---- Rademacher mixing (Phi_rnd,m) on the 32 x 32 workload ----
     mixing = None
-    if rank == 0 and world == 1 and args.mixing:
-        mixing = mixing_study(sfs, torch, geom, op, args, w, iters, x_true, flush, stream, seed)
+    if ran_here and args.mixing:
+        mixing = mixing_study(sfs, torch, args, flush, stream, seed)
 
     # ---- Cramer-Rao bound of one scatterer per strategy and n_f ----
     crb = None
-    if rank == 0 and world == 1 and args.crb_trials > 0:
+    if ran_here and args.crb_trials > 0:
         crb = crb_study(sfs, torch, args, seed)
 
     # ---- serving mix: scenes of many geometries in one grouped graph launch ----
     serving = None
-    if rank == 0 and world == 1 and args.serving_scenes > 0:
+    if ran_here and args.serving_scenes > 0:
         serving = serving_study(sfs, torch, args, flush, stream, seed)
 
     # ---- learned unrolled ISTA vs FISTA, time to the same NMSE ----
     learned = None
-    if rank == 0 and world == 1 and args.learned_steps > 0 and args.workload == synth.LEARNED["workload"]:
-        learned = learned_study(sfs, torch, op, args, w, L, stream, seed)
+    if ran_here and args.learned_steps > 0:
+        learned = learned_study(sfs, torch, args, stream, seed)
 
     # ---- CPU baseline: the FP64 oracle, bounded sample, rank 0 only ----
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        O, oop, oy, t_otab = oracle_setup(args.workload, w, args.strategy, seed)
-        v, n, threads = time_oracle_iterations(O, oop, oy, w["mu"], args.cpu_seconds)
-        cpu = {"value": v, "unit": "it/s", "cores": threads, "kind": "oracle",
-               "sample": "%d FISTA iterations of the FP64 lateral-FFT oracle on the same "
-                         "workload (table build %.1f s excluded)" % (n, t_otab)}
+    if ran_here and not args.no_cpu_baseline:
+        if oracle is None:
+            cpu = {"value": None, "unit": "it/s", "cores": 0, "kind": "oracle",
+                   "sample": "not run: the FP64 oracle's table does not fit the host memory available"}
+        else:
+            O, oop, oy, t_otab = oracle
+            allc, one = cpu_baseline_both(O, oop, oy, w["mu"], args.cpu_seconds, cores)
+            cpu = {"value": allc["value"], "unit": "it/s", "cores": allc["cores"], "kind": "oracle",
+                   "sample": "%d FISTA iterations of the FP64 lateral-FFT oracle on the same workload, "
+                             "%d threads (table build %.1f s excluded)" % (allc["iters"], cores, t_otab),
+                   "single_thread": {"value": one["value"], "unit": "it/s", "cores": one["cores"],
+                                     "sample": "%d FISTA iterations, 1 thread" % one["iters"]},
+                   "host_cores": host_cores()}
 
     if rank == 0:
         line = {
@@ -911,12 +1131,14 @@ def main():
                 "workload": workload_desc(args.workload, w, args.strategy, iters),
                 "precision": args.precision,
                 "parallelism": "replicas" if world > 1 else "single GPU",
-                "l2": "L2 flushed before every timed step (256 MB buffer write outside the "
-                      "per-step events); generator table %.0f MB" % (info["table_bytes"] / 1e6),
+                "l2": "L2 flushed before every timed step (%d MB buffer write outside the "
+                      "per-step events); generator table %.0f MB, L2 %.0f MB"
+                      % (flush.numel() >> 20, info["table_bytes"] / 1e6, l2_bytes / 1e6),
                 "U": U, "Nkappa": Nk, "Nslot": Ns, "orbit_slots": info["GS"], "Nz": Nz,
-                "P": [info["Px"], info["Py"]],
+                "P": [info["Px"], info["Py"]], "sms": n_sm,
                 "setup_s": {"table_build": round(t_table, 4), "lipschitz": round(t_lip, 4)},
                 "L": L,
+                "value_graph_without_event_nodes": job_rate(world, args.steps, iters, ms_plain),
             },
             "e2e": {"value": e2e, "unit": "it/s",
                     "h2d_bytes_per_step": int(y_host.nbytes),
@@ -927,22 +1149,11 @@ def main():
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
-        if study is not None:
-            line["precision_study"] = study
-        if batched is not None:
-            line["batched"] = batched
-        if learned is not None:
-            line["learned"] = learned
-        if serving is not None:
-            line["serving"] = serving
-        if crb is not None:
-            line["crb"] = crb
-        if mixing is not None:
-            line["mixing"] = mixing
-        if sweep is not None:
-            line["runtime_sweep"] = sweep
-        if backtracking is not None:
-            line["backtracking"] = backtracking
+        for key, val in (("precision_study", study), ("batched", batched), ("strategies", strategies),
+                         ("learned", learned), ("serving", serving), ("crb", crb), ("mixing", mixing),
+                         ("runtime_sweep", sweep), ("backtracking", backtracking)):
+            if val is not None:
+                line[key] = val
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -264,16 +264,24 @@ int sfs_apply_AH_noalloc(sfs_operator* op, const void* y_dev, void* x_dev, void*
  * sfs_fista_batched: Algorithm 1 on every scene with the same L and
  * iteration count; lambda >= 0 is used for every scene, lambda < 0 means
  * lambda_b = -lambda ||A^H y_b||_inf per scene (the mu rule of Sec. VII);
- * x_out_dev receives x_iters of every scene (no warm start, no monitor).
+ * x_inout_dev receives x_iters of every scene; with flags =
+ * SFS_FISTA_WARM_START it holds every scene's x_0 = gamma_1 on entry
+ * (t_1 = 1), else x_0 = 0 (no other flag is accepted; no monitor).
  * Errors: SFS_ERR_INVALID_ARG, SFS_ERR_OOM, SFS_ERR_CUDA.
  */
+/* Flags of sfs_fista */
+#define SFS_FISTA_WARM_START 1u   /* x_inout_dev holds x_0 on entry (else 0)  */
+#define SFS_FISTA_TIME_KERNELS 2u /* event nodes around every kernel of the
+                                     replayed loop (sfs_stage_times)          */
+#define SFS_FISTA_RESUME 4u       /* continue from state_dev (gamma, x, t)     */
+
 #define SFS_MAX_BATCH 256
 int sfs_apply_A_batched(sfs_operator* op, int batch, const void* x_dev, void* y_dev,
                         void* stream);
 int sfs_apply_AH_batched(sfs_operator* op, int batch, const void* y_dev, void* x_dev,
                          void* stream);
 int sfs_fista_batched(sfs_operator* op, int batch, const void* y_dev, double lambda,
-                      double L, int iters, void* x_out_dev, void* stream);
+                      double L, int iters, void* x_inout_dev, uint32_t flags, void* stream);
 
 /*
  * Serving-style solve of scenes of different geometries: ngroups groups,
@@ -492,42 +500,62 @@ int sfs_set_batch_tile(sfs_operator* op, int batch, int nb);
 int sfs_fista_backtracking(sfs_operator* op, const void* y_dev, double lambda, double L0, double eta,
                            int iters, void* x_dev, double* L_hist_host, void* stream);
 
-/* Flags of sfs_fista */
-#define SFS_FISTA_WARM_START 1u   /* x_inout_dev holds x_0 on entry (else 0)  */
-#define SFS_FISTA_TIME_KERNELS 2u /* time the two contraction kernels          */
+
+/* Bytes of the FISTA state of an operator with V voxels (see sfs_fista). */
+#define SFS_FISTA_STATE_BYTES(V) (16u * (uint64_t)(V) + 16u)
 
 /*
  * FISTA (Algorithm 1, Sec. IV-A) for min 1/2||A x - y||^2 + lambda ||x||_1:
  *   x_k = tau_{lambda/L}(gamma_k - A^H(A gamma_k - y)/L),
+ *   t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2,
  *   gamma_{k+1} = x_k + ((t_k - 1)/t_{k+1})(x_k - x_{k-1}),  t_1 = 1,
  * with tau the complex soft threshold max(|z| - a, 0) z/|z|.
  * y_dev: c64 [S][M] (read).  lambda >= 0 is used as given; lambda < 0 means
  * lambda = -lambda * ||A^H y||_inf (the mu rule of Sec. VII, computed on the
  * device).  L: Lipschitz constant (> 0), e.g. from sfs_lipschitz.
- * x_inout_dev: c64 [Nz][Ny][Nx]; receives x_iters.  obj_hist_host (may be
- * NULL): double [iters], entry k-1 = 1/2||A gamma_k - y||^2 + lambda||x_k||_1
- * (a monitor evaluated with the residual at gamma_k); when given, the call
- * synchronises `stream`.  Errors: SFS_ERR_INVALID_ARG, SFS_ERR_CUDA.
+ * x_inout_dev: c64 [Nz][Ny][Nx]; receives x_K after the call's `iters`
+ * iterations (with SFS_FISTA_WARM_START it also holds x_0 = gamma_1 on entry).
+ * state_dev (may be NULL): SFS_FISTA_STATE_BYTES(V) bytes of device memory
+ * holding the iteration state, so that a solve can be checkpointed and
+ * continued: c64 gamma_{K+1} [V], c64 x_K [V] (the previous iterate of the
+ * next step), double t_{K+1}, int64 total iterations.  When given, the call
+ * writes the state reached at its end.  With SFS_FISTA_RESUME the call starts
+ * from that state instead of x_0 (x_inout_dev is then output only), so n1
+ * iterations followed by a resumed n2 give the same result, bit for bit, as
+ * n1 + n2 iterations in one call with the same lambda and L (the momentum
+ * coefficients are computed on the device in FP64 from the stored t).
+ * obj_hist_host (may be NULL): double [iters], entry k-1 =
+ * 1/2||A gamma_k - y||^2 + lambda||x_k||_1 (a monitor evaluated with the
+ * residual at gamma_k); when given, the call synchronises `stream`.
+ * SFS_FISTA_TIME_KERNELS records an event before and after every kernel of
+ * ceil(iters / 32)-spaced iterations (at most 32, spread over the solve) as
+ * event-record nodes of the replayed iteration graph, read by
+ * sfs_stage_times; the other iterations run without them.
+ * Errors: SFS_ERR_INVALID_ARG (also RESUME without state_dev, or RESUME
+ * with WARM_START), SFS_ERR_CUDA.
  */
 int sfs_fista(sfs_operator* op, const void* y_dev, double lambda, double L,
-              int iters, void* x_inout_dev, uint32_t flags,
+              int iters, void* x_inout_dev, void* state_dev, uint32_t flags,
               double* obj_hist_host, void* stream);
 
 /*
  * Average device time per launch [ms] of the forward and adjoint depth
  * contraction kernels during the last sfs_fista call made with
- * SFS_FISTA_TIME_KERNELS (CUDA events around each launch).  Synchronises the
- * operator's device.  n_out_host receives the number of launches averaged.
+ * SFS_FISTA_TIME_KERNELS (the event nodes of its replayed graph, over the
+ * sampled iterations).  Synchronises the operator's device.  n_out_host
+ * receives the number of iterations averaged.
  */
 int sfs_kernel_times(sfs_operator* op, double* fwd_ms, double* adj_ms,
                      int32_t* n_out_host);
 
 /*
- * Average device time per iteration [ms] of each of the four stages of the
- * last sfs_fista call made with SFS_FISTA_TIME_KERNELS: ms4_host[0] forward
- * contraction, [1] residual planes (inverse FFT, residual, forward FFT),
- * [2] adjoint contraction, [3] update planes (inverse FFT, FISTA step,
- * forward FFT).  Synchronises the operator's device.
+ * Average device time per iteration [ms] of each of the four kernels of
+ * the last sfs_fista call made with SFS_FISTA_TIME_KERNELS, from the event
+ * nodes between consecutive kernels of its sampled iterations (so the four
+ * sum to the time of those iterations): ms4_host[0] forward contraction, [1]
+ * residual planes (inverse FFT, residual, forward FFT), [2] adjoint
+ * contraction, [3] update planes (inverse FFT, FISTA step, forward FFT).
+ * Synchronises the operator's device.
  */
 int sfs_stage_times(sfs_operator* op, double* ms4_host, int32_t* n_out_host);
 

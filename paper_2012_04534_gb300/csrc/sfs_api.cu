@@ -284,6 +284,8 @@ void free_operator(sfs_operator* op) {
   cudaFree(op->ws.scal);
   cudaFree(op->ws.red);
   cudaFree(op->ws.obj);
+  cudaFree(op->ws.beta);
+  cudaFree(op->ws.tnext);
   cudaFree(op->ws.pmx);
   cudaFree(op->ws.pmr);
   for (cudaEvent_t e : op->ev) cudaEventDestroy(e);
@@ -403,6 +405,22 @@ int ensure_obj(sfs_operator* op, int iters) {
   return SFS_OK;
 }
 
+// Device momentum table for `iters` iterations (grown on demand; loops
+// captured on the old table are dropped) and the t_{k+1} slot.
+int ensure_beta(sfs_operator* op, int iters) {
+  if (!op->ws.tnext) SFS_TRY(dev_alloc(&op->ws.tnext, 2));
+  if (op->ws.beta_cap >= iters) return SFS_OK;
+  for (auto& ge : op->graphs) cudaGraphExecDestroy(ge.exec);
+  op->graphs.clear();
+  cudaFree(op->ws.beta);
+  op->ws.beta = nullptr;
+  op->ws.beta_cap = 0;
+  const int cap = std::max(iters, 64);
+  SFS_TRY(dev_alloc(&op->ws.beta, (size_t)cap));
+  op->ws.beta_cap = cap;
+  return SFS_OK;
+}
+
 int ensure_events(sfs_operator* op, int n) {
   while ((int)op->ev.size() < n) {
     cudaEvent_t e;
@@ -415,8 +433,15 @@ int ensure_events(sfs_operator* op, int n) {
 // The FISTA iteration loop (Algorithm 1): X^ of gamma_1, then per iteration
 // forward contraction, residual planes (with the adjoint scatter and FFT),
 // adjoint contraction, and the update planes that also transform
-// gamma_{k+1}.  beta_k = (t_k - 1)/t_{k+1} is fixed by k, so the loop can be
-// captured once and replayed.
+// gamma_{k+1}.  beta_k = (t_k - 1)/t_{k+1} is read from the device table
+// beta_dev (single-scene calls, which may resume from a stored t) or fixed
+// by k from t_1 = 1 (batched calls), so the loop can be captured once and
+// replayed.  With `timing`, events are recorded before and after each
+// kernel of every timing_stride(iters)-th iteration (op->ev[5 i + j] for
+// the i-th such iteration, at most kTimedIters of them); inside a stream
+// capture they become event-record nodes of the graph, so the per-kernel
+// times come from the replayed loop itself, and the other iterations run
+// without the few microseconds each event node adds.
 // Buffers of one FISTA loop: the operator's workspace (one scene) or the
 // batched workspace (d.batch scenes).
 struct FistaBufs {
@@ -424,8 +449,12 @@ struct FistaBufs {
   float* scal;
 };
 
+constexpr int kTimedIters = 32;
+int timing_stride(int iters) { return std::max(1, (iters + kTimedIters - 1) / kTimedIters); }
+int timed_iters(int iters) { return iters > 0 ? (iters - 1) / timing_stride(iters) + 1 : 0; }
+
 int enqueue_fista_loop(sfs_operator* op, const PlaneDims& d, const FistaBufs& b, int iters,
-                       double* obj, bool timing, cudaStream_t st) {
+                       double* obj, bool timing, cudaStream_t st, const float* beta_dev = nullptr) {
   std::vector<float> beta(iters);
   double t = 1.0;
   for (int k = 0; k < iters; ++k) {
@@ -433,19 +462,29 @@ int enqueue_fista_loop(sfs_operator* op, const PlaneDims& d, const FistaBufs& b,
     beta[k] = (float)((t - 1.0) / tn);
     t = tn;
   }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (timing) SFS_CUDA(cudaStreamIsCapturing(st, &cap));
+  const unsigned evflags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+  const int stride = timing_stride(iters);
+  auto mark = [&](int k, int j) -> int {
+    if (timing && k % stride == 0)
+      SFS_CUDA(cudaEventRecordWithFlags(op->ev[5 * (k / stride) + j], st, evflags));
+    return SFS_OK;
+  };
   SFS_TRY(launch_scatter_y_planes(d, b.ybuf, op->posmap, b.yplane, st));
   SFS_TRY(launch_fwd_planes(d, b.gam, b.Xh, st));
   for (int k = 0; k < iters; ++k) {
-    if (timing) SFS_CUDA(cudaEventRecord(op->ev[5 * k + 0], st));
+    SFS_TRY(mark(k, 0));
     SFS_TRY(launch_contract_fwd(d, op->table, b.Xh, b.Yh, op->ws.err, st));
-    if (timing) SFS_CUDA(cudaEventRecord(op->ev[5 * k + 1], st));
+    SFS_TRY(mark(k, 1));
     SFS_TRY(launch_inv_resid_fwd(d, b.Yh, op->posmap, b.yplane, b.Rh, obj ? obj + 2 * k : nullptr, st));
-    if (timing) SFS_CUDA(cudaEventRecord(op->ev[5 * k + 2], st));
+    SFS_TRY(mark(k, 2));
     SFS_TRY(launch_contract_adj(d, op->table, b.Rh, b.Gh, op->ws.err, st));
-    if (timing) SFS_CUDA(cudaEventRecord(op->ev[5 * k + 3], st));
+    SFS_TRY(mark(k, 3));
     SFS_TRY(launch_inv_fista_fwd(d, b.Gh, op->ws.segslot, b.xk, b.gam, b.scal, beta[k], k + 1 < iters,
-                                 b.Xh, obj ? obj + 2 * k + 1 : nullptr, st));
-    if (timing) SFS_CUDA(cudaEventRecord(op->ev[5 * k + 4], st));
+                                 b.Xh, obj ? obj + 2 * k + 1 : nullptr, st,
+                                 beta_dev ? beta_dev + k : nullptr));
+    SFS_TRY(mark(k, 4));
   }
   return SFS_OK;
 }
@@ -454,7 +493,7 @@ int enqueue_fista_iterations(sfs_operator* op, int iters, double* obj, bool timi
                              cudaStream_t st) {
   const FistaBufs b = {op->ws.ybuf, op->ws.yplane, op->ws.Xh, op->ws.Yh, op->ws.Rh,
                        op->ws.Gh,   op->ws.xk,     op->ws.gam, op->ws.scal};
-  return enqueue_fista_loop(op, dims_of(op), b, iters, obj, timing, st);
+  return enqueue_fista_loop(op, dims_of(op), b, iters, obj, timing, st, op->ws.beta);
 }
 
 // Dimensions of a batched call on `batch` scenes.
@@ -534,12 +573,13 @@ int fista_graph_batched(sfs_operator* op, int iters, int batch, cudaGraphExec_t*
   return SFS_OK;
 }
 
-// Executable graph of the iteration loop for (iters, monitor), captured on
-// the operator's own stream the first time it is needed.  All pointers it
-// bakes in are operator-owned, so it stays valid for the operator's life.
-int fista_graph(sfs_operator* op, int iters, bool with_obj, cudaGraphExec_t* out) {
+// Executable graph of the iteration loop for (iters, monitor, timed),
+// captured on the operator's own stream the first time it is needed.  All
+// pointers and events it bakes in are operator-owned, so it stays valid for
+// the operator's life (or until the momentum or monitor buffer grows).
+int fista_graph(sfs_operator* op, int iters, bool with_obj, bool timed, cudaGraphExec_t* out) {
   for (auto& ge : op->graphs)
-    if (ge.iters == iters && ge.with_obj == with_obj) {
+    if (ge.iters == iters && ge.with_obj == with_obj && ge.timed == timed) {
       *out = ge.exec;
       return SFS_OK;
     }
@@ -548,7 +588,7 @@ int fista_graph(sfs_operator* op, int iters, bool with_obj, cudaGraphExec_t* out
   SFS_TRY(prepare_kernels(dims_of(op)));  // function attributes are set outside the capture
   cudaStream_t cs = op->capture_stream;
   SFS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  int rc = enqueue_fista_iterations(op, iters, with_obj ? op->ws.obj : nullptr, false, cs);
+  int rc = enqueue_fista_iterations(op, iters, with_obj ? op->ws.obj : nullptr, timed, cs);
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(cs, &graph);
   if (rc != SFS_OK) {
@@ -560,7 +600,7 @@ int fista_graph(sfs_operator* op, int iters, bool with_obj, cudaGraphExec_t* out
   const cudaError_t e2 = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaGraphInstantiate", __FILE__, __LINE__);
-  op->graphs.push_back({iters, with_obj, exec});
+  op->graphs.push_back({iters, with_obj, timed, exec});
   *out = exec;
   return SFS_OK;
 }
@@ -1387,26 +1427,42 @@ int sfs_lipschitz(sfs_operator* op, int max_iter, double rtol, uint64_t seed, do
 }
 
 int sfs_fista(sfs_operator* op, const void* y_dev, double lambda, double L, int iters,
-              void* x_inout_dev, uint32_t flags, double* obj_hist_host, void* stream) {
+              void* x_inout_dev, void* state_dev, uint32_t flags, double* obj_hist_host,
+              void* stream) {
   clear_error();
+  const bool resume = (flags & SFS_FISTA_RESUME) != 0;
   if (!op || !y_dev || !x_inout_dev || iters < 0 || !(L > 0) || !isfinite(lambda) ||
-      !aligned16(y_dev) || !aligned16(x_inout_dev)) {
+      !aligned16(y_dev) || !aligned16(x_inout_dev) || (state_dev && !aligned16(state_dev)) ||
+      (resume && !state_dev) || (resume && (flags & SFS_FISTA_WARM_START))) {
     set_error("invalid argument");
     return SFS_ERR_INVALID_ARG;
   }
   DeviceScope scope(op->geo.d.device);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t vbytes = (size_t)op->V * sizeof(float2);
+  // state layout: gamma_{k+1} [V], x_k [V] (c64), t_{k+1} (double), k (int64)
+  float2* st_gam = state_dev ? (float2*)state_dev : nullptr;
+  float2* st_x = state_dev ? st_gam + op->V : nullptr;
+  double* st_t = state_dev ? (double*)(st_x + op->V) : nullptr;
+  long long* st_k = state_dev ? (long long*)(st_t + 1) : nullptr;
   float2* y = op->ws.ybuf;
   SFS_CUDA(cudaMemcpyAsync(y, y_dev, (size_t)op->S * op->M * sizeof(float2),
                            cudaMemcpyDeviceToDevice, st));
-  if (flags & SFS_FISTA_WARM_START) {
+  if (resume) {
+    SFS_CUDA(cudaMemcpyAsync(op->ws.gam, st_gam, vbytes, cudaMemcpyDeviceToDevice, st));
+    SFS_CUDA(cudaMemcpyAsync(op->ws.xk, st_x, vbytes, cudaMemcpyDeviceToDevice, st));
+  } else if (flags & SFS_FISTA_WARM_START) {
     SFS_CUDA(cudaMemcpyAsync(op->ws.xk, x_inout_dev, vbytes, cudaMemcpyDeviceToDevice, st));
     SFS_CUDA(cudaMemcpyAsync(op->ws.gam, x_inout_dev, vbytes, cudaMemcpyDeviceToDevice, st));
   } else {
     SFS_CUDA(cudaMemsetAsync(op->ws.xk, 0, vbytes, st));
     SFS_CUDA(cudaMemsetAsync(op->ws.gam, 0, vbytes, st));
   }
+  if (state_dev && !resume) SFS_CUDA(cudaMemsetAsync(st_k, 0, sizeof(long long), st));
+  // momentum table of this call, continuing the stored t_k when resuming
+  SFS_TRY(ensure_beta(op, std::max(iters, 1)));
+  SFS_TRY(launch_fista_betas(resume ? st_t : nullptr, iters, op->ws.beta,
+                             state_dev ? st_t : op->ws.tnext, state_dev ? st_k : nullptr, st));
   // thresholds: lambda/L and 1/L, with the mu rule evaluated on the device
   const int use_mu = lambda < 0;
   if (use_mu) {
@@ -1424,21 +1480,20 @@ int sfs_fista(sfs_operator* op, const void* y_dev, double lambda, double L, int 
   }
   const bool timing = (flags & SFS_FISTA_TIME_KERNELS) != 0;
   if (timing) {
-    SFS_TRY(ensure_events(op, 5 * iters));
+    SFS_TRY(ensure_events(op, 5 * timed_iters(iters)));
     op->ev_used = 0;
   }
   if (iters > 0) {
-    if (timing) {
-      // direct launches with events around the two contractions
-      SFS_TRY(enqueue_fista_iterations(op, iters, obj, true, st));
-    } else {
-      cudaGraphExec_t exec = nullptr;
-      SFS_TRY(fista_graph(op, iters, obj != nullptr, &exec));
-      SFS_CUDA(cudaGraphLaunch(exec, st));
-    }
+    cudaGraphExec_t exec = nullptr;
+    SFS_TRY(fista_graph(op, iters, obj != nullptr, timing, &exec));
+    SFS_CUDA(cudaGraphLaunch(exec, st));
   }
-  if (timing) op->ev_used = iters;
+  if (timing) op->ev_used = timed_iters(iters);
   SFS_CUDA(cudaMemcpyAsync(x_inout_dev, op->ws.xk, vbytes, cudaMemcpyDeviceToDevice, st));
+  if (state_dev) {
+    SFS_CUDA(cudaMemcpyAsync(st_gam, op->ws.gam, vbytes, cudaMemcpyDeviceToDevice, st));
+    SFS_CUDA(cudaMemcpyAsync(st_x, op->ws.xk, vbytes, cudaMemcpyDeviceToDevice, st));
+  }
   if (obj) {
     std::vector<double> h(2 * (size_t)iters);
     double lam = 0.0;
@@ -1548,10 +1603,11 @@ int sfs_apply_AH_batched(sfs_operator* op, int batch, const void* y_dev, void* x
 }
 
 int sfs_fista_batched(sfs_operator* op, int batch, const void* y_dev, double lambda, double L,
-                      int iters, void* x_out_dev, void* stream) {
+                      int iters, void* x_out_dev, uint32_t flags, void* stream) {
   clear_error();
   if (!op || batch < 1 || batch > SFS_MAX_BATCH || !y_dev || !x_out_dev || iters < 0 || !(L > 0) ||
-      !isfinite(lambda) || !aligned16(y_dev) || !aligned16(x_out_dev)) {
+      !isfinite(lambda) || !aligned16(y_dev) || !aligned16(x_out_dev) ||
+      (flags & ~(uint32_t)SFS_FISTA_WARM_START)) {
     set_error("invalid argument");
     return SFS_ERR_INVALID_ARG;
   }
@@ -1562,8 +1618,13 @@ int sfs_fista_batched(sfs_operator* op, int batch, const void* y_dev, double lam
   cudaStream_t st = (cudaStream_t)stream;
   const size_t B = (size_t)batch;
   SFS_CUDA(cudaMemcpyAsync(w.ybuf, y_dev, B * d.bs_y * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-  SFS_CUDA(cudaMemsetAsync(w.xk, 0, B * d.bs_x * sizeof(float2), st));
-  SFS_CUDA(cudaMemsetAsync(w.gam, 0, B * d.bs_x * sizeof(float2), st));
+  if (flags & SFS_FISTA_WARM_START) {
+    SFS_CUDA(cudaMemcpyAsync(w.xk, x_out_dev, B * d.bs_x * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    SFS_CUDA(cudaMemcpyAsync(w.gam, x_out_dev, B * d.bs_x * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+  } else {
+    SFS_CUDA(cudaMemsetAsync(w.xk, 0, B * d.bs_x * sizeof(float2), st));
+    SFS_CUDA(cudaMemsetAsync(w.gam, 0, B * d.bs_x * sizeof(float2), st));
+  }
   const int use_mu = lambda < 0;
   SFS_CUDA(cudaMemsetAsync(w.scal, 0, B * kNumFloatScalars * sizeof(float), st));
   if (use_mu) {  // max |A^H y_b| of every scene, on the device

@@ -99,6 +99,9 @@ struct Workspace {
   float* pmr = nullptr;     // [Up] FP16 modes: the same of each R^ plane
   double* obj = nullptr;    // [2 * obj_cap] objective monitor sums
   int obj_cap = 0;
+  float* beta = nullptr;    // [beta_cap] momentum coefficients of the current FISTA call
+  int beta_cap = 0;
+  double* tnext = nullptr;  // t_{k+1} after the current FISTA call (no state buffer given)
 };
 
 }  // namespace sfs
@@ -155,10 +158,12 @@ struct sfs_operator {
   std::vector<cudaEvent_t> ev;
   int ev_used = 0;
   // FISTA iteration loops captured as CUDA graphs, keyed by (iterations,
-  // objective monitor on/off); replayed on the caller's stream
+  // objective monitor on/off, event nodes around each kernel on/off);
+  // replayed on the caller's stream
   struct GraphEntry {
     int iters;
     bool with_obj;
+    bool timed;
     cudaGraphExec_t exec;
   };
   std::vector<GraphEntry> graphs;
@@ -264,9 +269,15 @@ int launch_scatter_fwd(const PlaneDims& d, const float2* y, const int32_t* posma
 int launch_inv_store(const PlaneDims& d, const float2* Gh, const int2* segslot,
                      float2* x, double* red_sumsq, unsigned int* maxabs_bits,
                      cudaStream_t st);
+// beta_dev (optional): device pointer to this iteration's beta, else `beta`.
 int launch_inv_fista_fwd(const PlaneDims& d, const float2* Gh, const int2* segslot,
                          float2* xk, float2* gam, const float* scal, float beta,
-                         int do_fwd, float2* Xh, double* red_l1, cudaStream_t st);
+                         int do_fwd, float2* Xh, double* red_l1, cudaStream_t st,
+                         const float* beta_dev = nullptr);
+// Momentum table beta[0..iters) of Algorithm 1 from t_1 = *t_in (1 if null),
+// t_{iters+1} to *t_out, iters added to *cnt (if not null); one thread.
+int launch_fista_betas(const double* t_in, int iters, float* beta, double* t_out, long long* cnt,
+                       cudaStream_t st);
 
 // Depth contractions over the generator table.  Yp: [nzb][U][Nk] depth-block
 // partials; Gs: [slots][128][64] adjoint partials (see segment_slots).  err:

@@ -664,12 +664,15 @@ inv_store_kernel(PlaneDims d, const float2* __restrict__ Gh, const int2* __restr
 // Gh[z] (spectrum of A^H(A gamma - y)) -> FISTA step on plane z (Algorithm 1):
 //   x_k = tau_{lambda/L}(gamma_k - grad/L), gamma_{k+1} = x_k + beta_k (x_k - x_{k-1})
 // then, unless this is the last iteration, Xh[z] = FFT2(pad(gamma_{k+1})).
+// beta_k is *beta_dev when given (a table written on the device by
+// fista_betas_kernel), else beta_arg.
 template <int P, bool TWO_D>
 __global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT, PlaneFFT<P, TWO_D>::MINB)
 inv_fista_fwd_kernel(PlaneDims d, const float2* __restrict__ Gh,
                      const int2* __restrict__ segslot, float2* __restrict__ xk,
-                     float2* __restrict__ gam, const float* __restrict__ scal, float beta,
-                     int do_fwd, float2* __restrict__ Xh, double* __restrict__ red_l1) {
+                     float2* __restrict__ gam, const float* __restrict__ scal, float beta_arg,
+                     const float* __restrict__ beta_dev, int do_fwd, float2* __restrict__ Xh,
+                     double* __restrict__ red_l1) {
   using F = PlaneFFT<P, TWO_D>;
   {  // scene blockIdx.y of a batched launch
     const long long b = blockIdx.y;
@@ -690,6 +693,7 @@ inv_fista_fwd_kernel(PlaneDims d, const float2* __restrict__ Gh,
   load_inverse_adj<P, TWO_D>(buf, tw, Gh, segslot, z, d);
   const float thr = scal[kThr];
   const float invL = scal[kInvL];
+  const float beta = beta_dev ? *beta_dev : beta_arg;
   double l1 = 0.0;
   const size_t off = (size_t)z * d.Ny * d.Nx;
   for (int e = threadIdx.x; e < d.Ny * d.Nx; e += F::NT) {
@@ -1422,11 +1426,37 @@ int launch_inv_store(const PlaneDims& d, const float2* Gh, const int2* segslot, 
 
 int launch_inv_fista_fwd(const PlaneDims& d, const float2* Gh, const int2* segslot, float2* xk,
                          float2* gam, const float* scal, float beta, int do_fwd, float2* Xh,
-                         double* red_l1, cudaStream_t st) {
+                         double* red_l1, cudaStream_t st, const float* beta_dev) {
   return dispatch_plane(d, [&]<int P, bool TD>() {
     return launch_plane<P, TD>(inv_fista_fwd_kernel<P, TD>, d.Nz, d.batch, st, d, Gh, segslot, xk, gam,
-                               scal, beta, do_fwd, Xh, red_l1);
+                               scal, beta, beta_dev, do_fwd, Xh, red_l1);
   });
+}
+
+// Momentum coefficients of Algorithm 1 in FP64, one thread:
+// beta_k = (t_k - 1) / t_{k+1}, t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2 for
+// k = 1..iters from t_1 = *t_in (1 when t_in is null); writes t_{iters+1} to
+// *t_out and, when cnt is given, adds iters to it.  Every FISTA call of an
+// operator runs this same code, so a call resumed from a stored t continues
+// the sequence of an uninterrupted call bit for bit.
+__global__ void fista_betas_kernel(const double* t_in, int iters, float* __restrict__ beta,
+                                   double* t_out, long long* cnt) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t = t_in ? *t_in : 1.0;
+  for (int k = 0; k < iters; ++k) {
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    beta[k] = (float)((t - 1.0) / tn);
+    t = tn;
+  }
+  *t_out = t;
+  if (cnt) *cnt += iters;
+}
+
+int launch_fista_betas(const double* t_in, int iters, float* beta, double* t_out, long long* cnt,
+                       cudaStream_t st) {
+  fista_betas_kernel<<<1, 1, 0, st>>>(t_in, iters, beta, t_out, cnt);
+  SFS_CUDA(cudaGetLastError());
+  return SFS_OK;
 }
 
 int contract_units(const PlaneDims& d) {

@@ -49,6 +49,7 @@ SFS_MAX_GROUPS = 64
 
 SFS_FISTA_WARM_START = 1
 SFS_FISTA_TIME_KERNELS = 2
+SFS_FISTA_RESUME = 4
 
 STATUS_NAMES = {0: "SFS_OK", -1: "SFS_ERR_INVALID_ARG", -2: "SFS_ERR_BAND_TOO_NARROW",
                 -3: "SFS_ERR_CUDA", -4: "SFS_ERR_OOM", -5: "SFS_ERR_TIMEOUT",
@@ -145,9 +146,9 @@ def lib():
         "sfs_fista_mixed": [vp, vp, dbl, dbl, i32, vp, vp],
         "sfs_apply_A_batched": [vp, i32, vp, vp, vp],
         "sfs_apply_AH_batched": [vp, i32, vp, vp, vp],
-        "sfs_fista_batched": [vp, i32, vp, dbl, dbl, i32, vp, vp],
+        "sfs_fista_batched": [vp, i32, vp, dbl, dbl, i32, vp, u32, vp],
         "sfs_lipschitz": [vp, i32, dbl, u64, dbl, P(dbl), vp],
-        "sfs_fista": [vp, vp, dbl, dbl, i32, vp, u32, P(dbl), vp],
+        "sfs_fista": [vp, vp, dbl, dbl, i32, vp, vp, u32, P(dbl), vp],
         "sfs_kernel_times": [vp, P(dbl), P(dbl), P(ctypes.c_int32)],
         "sfs_set_wait_timeout_ns": [vp, u64],
         "sfs_stage_times": [vp, P(dbl), P(ctypes.c_int32)],
@@ -278,11 +279,12 @@ def sfs_lipschitz(op, max_iter, rtol, seed, safety, stream_ptr):
     return out.value, rc == SFS_OK
 
 
-def sfs_fista(op, y_dev_ptr, lam, L, iters, x_dev_ptr, flags, obj_hist, stream_ptr):
+def sfs_fista(op, y_dev_ptr, lam, L, iters, x_dev_ptr, state_dev_ptr, flags, obj_hist, stream_ptr):
     ptr = None
     if obj_hist is not None:
         ptr = obj_hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-    _check(lib().sfs_fista(op, y_dev_ptr, lam, L, iters, x_dev_ptr, flags, ptr, stream_ptr))
+    _check(lib().sfs_fista(op, y_dev_ptr, lam, L, iters, x_dev_ptr, state_dev_ptr, flags, ptr,
+                           stream_ptr))
 
 
 def sfs_kernel_times(op):
@@ -454,13 +456,19 @@ class Operator:
                                           _stream_ptr(stream, y.device)))
         return x
 
-    def fista_batched(self, y, lam, L, iters, x=None, stream=None):
-        """Scenes y[b] (same operator); lam < 0: lambda_b = -lam ||A^H y_b||_inf."""
+    def fista_batched(self, y, lam, L, iters, x=None, warm_start=False, stream=None):
+        """Scenes y[b] (same operator); lam < 0: lambda_b = -lam ||A^H y_b||_inf.
+        warm_start: x holds every scene's x_0 on entry."""
         B = int(y.shape[0])
-        x = self._new((B,) + self.shape_x) if x is None else x
+        if x is None:
+            if warm_start:
+                raise ValueError("warm_start needs x")
+            x = self._new((B,) + self.shape_x)
         _check(lib().sfs_fista_batched(self.handle, B, _dev_ptr(y, B * self.S * self.M, "y"),
                                        float(lam), float(L), int(iters),
-                                       _dev_ptr(x, B * self.V, "x"), _stream_ptr(stream, y.device)))
+                                       _dev_ptr(x, B * self.V, "x"),
+                                       SFS_FISTA_WARM_START if warm_start else 0,
+                                       _stream_ptr(stream, y.device)))
         return x
 
     def autotune(self, batch, reps=5):
@@ -489,16 +497,25 @@ class Operator:
         return sfs_lipschitz(self.handle, max_iter, rtol, seed, safety,
                              _stream_ptr(stream, torch.device("cuda", self.device)))
 
+    def new_fista_state(self):
+        """Device buffer for sfs_fista's state (gamma, x, t, count):
+        complex64 [2 V + 2], i.e. SFS_FISTA_STATE_BYTES(V) bytes."""
+        return self._new((2 * self.V + 2,))
+
     def fista(self, y, lam, L, iters, x=None, warm_start=False, obj_hist=False,
-              time_kernels=False, stream=None):
-        """lam >= 0: lambda; lam < 0: lambda = -lam * ||A^H y||_inf."""
+              time_kernels=False, state=None, resume=False, stream=None):
+        """lam >= 0: lambda; lam < 0: lambda = -lam * ||A^H y||_inf.
+        state: buffer from new_fista_state() that receives the iteration
+        state at the end; resume=True continues from it."""
         if x is None:
             x = self._new(self.shape_x)
         flags = (SFS_FISTA_WARM_START if warm_start else 0) | \
-                (SFS_FISTA_TIME_KERNELS if time_kernels else 0)
+                (SFS_FISTA_TIME_KERNELS if time_kernels else 0) | \
+                (SFS_FISTA_RESUME if resume else 0)
         hist = np.zeros(iters) if obj_hist else None
+        sp = None if state is None else _dev_ptr(state, 2 * self.V + 2, "state")
         sfs_fista(self.handle, _dev_ptr(y, self.S * self.M, "y"), float(lam), float(L), iters,
-                  _dev_ptr(x, self.V, "x"), flags, hist, _stream_ptr(stream, y.device))
+                  _dev_ptr(x, self.V, "x"), sp, flags, hist, _stream_ptr(stream, y.device))
         return (x, hist) if obj_hist else x
 
     def fista_backtracking(self, y, lam, L0, eta, iters, x=None, stream=None):

@@ -109,7 +109,7 @@ def test_null_handles_rejected(sfs):
     L = sfs.lib()
     assert L.sfs_apply_A(None, None, None, None) == sfs.SFS_ERR_INVALID_ARG
     assert "null" in L.sfs_last_error().decode()
-    assert L.sfs_fista(None, None, 0.0, 1.0, 1, None, 0, None, None) == sfs.SFS_ERR_INVALID_ARG
+    assert L.sfs_fista(None, None, 0.0, 1.0, 1, None, None, 0, None, None) == sfs.SFS_ERR_INVALID_ARG
     assert L.sfs_operator_from_indices(None, 1, None, None) == sfs.SFS_ERR_INVALID_ARG
     assert L.sfs_destroy_operator(None) == sfs.SFS_OK
 

@@ -126,6 +126,14 @@ def test_batched_fp32_fista_matches_oracle(sfs):
     xb = to_host(op.fista_batched(to_dev(np.stack(ys)), lam, L, 100))
     for b in range(3):
         assert rel_err(xb[b], refs[b]) <= 1e-4
+    # warm start: every scene from its own x_0 (the oracle's 30th iterate),
+    # 30 more iterations with the momentum restarted at t = 1
+    x0 = [O.fista(ref.apply_A, ref.apply_AH, yb, lam, L, 30) for yb in ys]
+    xw = to_host(op.fista_batched(to_dev(np.stack(ys)), lam, L, 30, x=to_dev(np.stack(x0)),
+                                  warm_start=True))
+    for b in range(3):
+        rw = O.fista(ref.apply_A, ref.apply_AH, ys[b], lam, L, 30, x0=x0[b])
+        assert rel_err(xw[b], rw) <= 1e-4
 
 
 def test_batched_invalid_arguments(sfs):
@@ -140,7 +148,11 @@ def test_batched_invalid_arguments(sfs):
         assert L.sfs_apply_A_batched(op.handle, B, ctypes.c_void_p(x.data_ptr()),
                                      ctypes.c_void_p(y.data_ptr()), None) == sfs.SFS_ERR_INVALID_ARG
     assert L.sfs_fista_batched(op.handle, 2, ctypes.c_void_p(y.data_ptr()), 0.1, -1.0, 5,
-                               ctypes.c_void_p(x.data_ptr()), None) == sfs.SFS_ERR_INVALID_ARG
+                               ctypes.c_void_p(x.data_ptr()), 0, None) == sfs.SFS_ERR_INVALID_ARG
+    # only SFS_FISTA_WARM_START is a batched flag
+    assert L.sfs_fista_batched(op.handle, 2, ctypes.c_void_p(y.data_ptr()), 0.1, 1.0, 5,
+                               ctypes.c_void_p(x.data_ptr()), sfs.SFS_FISTA_RESUME,
+                               None) == sfs.SFS_ERR_INVALID_ARG
     with pytest.raises(ValueError):
         op.apply_A_batched(x[:, :, :, :2].contiguous())
 
