@@ -137,6 +137,9 @@ typedef struct sfs_operator_info_t {
   int32_t Nslot;        /* wavenumber slots (orbit-major, padded to 64)        */
   int32_t GS;           /* slots per symmetry orbit (2, 4 or 8)               */
   int32_t precision;    /* sfs_precision of the depth contractions            */
+  int32_t nshards, shard;  /* bin shard of sfs_operator_shard (1, 0 otherwise)  */
+  int32_t shard_first;  /* position of this operator's first bin in the union  */
+  int32_t U_all;        /* bins in the union of all shards                    */
 } sfs_operator_info_t;
 
 /*
@@ -239,8 +242,12 @@ int sfs_apply_AH(sfs_operator* op, const void* y_dev, void* x_dev, void* stream)
  * call's contents, so calls whose device work overlaps in time (on other
  * streams, or with other operators of the same device) race and give wrong
  * results; order them on one stream.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  An operator whose scratch,
+ * the array's device address (cudaGetSymbolAddress) with that device current
+ * and keeps it for the life of the process; make that first call before any
+ * stream capture.  A device reset (cudaDeviceReset, or any teardown of the
+ * device's primary context) invalidates the kept address together with every
+ * operator of that device: do not call this entry point again on that
+ * device in the same process after one.  An operator whose scratch,
  * 8 * (U * Nslot + slots * 8192) bytes, exceeds the maximum is rejected with
  * SFS_ERR_INVALID_ARG and a message naming both sizes.
  */
@@ -586,6 +593,49 @@ int sfs_inject_wait_timeout(sfs_operator* op, int enable);
  * the last check.
  */
 int sfs_check_status(sfs_operator* op, void* stream);
+
+/*
+ * Multi-GPU split by bins (one process per GPU).  The union U of the kept
+ * bins is cut into nshards contiguous runs; run j holds union positions
+ * [floor(j U / n), floor((j + 1) U / n)) (sfs_shard_run, host only).  The
+ * runs partition the rows of A = Phi H (Eq. (10)/(11): a row is one kept
+ * coefficient (s, m)), so with A_j the rows of run j,
+ *   A x = the rows of every A_j x,   A^H y = sum_j A_j^H y,
+ *   A^H (A x - y) = sum_j A_j^H (A_j x - y):
+ * each rank builds the generator table (Theorem 2) of its own bins only and
+ * forms its partial gradient without any exchange; one all-reduce (sum) of
+ * the V voxel values per FISTA iteration joins them, and the elementwise
+ * update of Algorithm 1 is replicated (sfs_prox_momentum).
+ *   sfs_operator_shard: operator of run `shard` (as
+ *     sfs_operator_from_indices_prec otherwise).  Its measurement layout
+ *     stays the full [S][M]: sfs_apply_A writes only the entries of its
+ *     bins (the others are left as they were), sfs_apply_AH and
+ *     sfs_normal_residual read only those.  Errors: SFS_ERR_INVALID_ARG
+ *     (also for a run with no bin, nshards > U).
+ *   sfs_normal_residual: g = A_j^H (A_j x - y) (y c64 [S][M], x and g c64
+ *     [Nz][Ny][Nx]); on an unsharded operator the full gradient of
+ *     1/2||A x - y||^2.  Enqueued on `stream`.
+ *   sfs_prox_momentum: for i < n (c64 elements), w = gamma - grad / L,
+ *     x_i <- tau_{lambda/L}(w) (complex soft threshold), gamma_i <- x_i +
+ *     beta (x_i - x_prev_i) with x holding x_prev on entry: one iteration's
+ *     update of Algorithm 1 (beta = (t_k - 1)/t_{k+1}), in the arithmetic of
+ *     sfs_fista's fused update.  lambda >= 0, L > 0.  Enqueued on `stream`.
+ *   sfs_vec_sumsq / sfs_vec_max_abs: sum |v_i|^2 (FP64) and max |v_i| of a
+ *     c64 device vector (reduction slots of `op`; synchronise `stream`).
+ *   sfs_vec_scale: v *= a.  sfs_vec_randn: complex Gaussian entries from a
+ *     counter-based hash of (seed, i), the start vector of sfs_lipschitz.
+ */
+int sfs_shard_run(int U, int nshards, int shard, int32_t* first, int32_t* count);
+int sfs_operator_shard(sfs_geometry* g, int M, const int32_t* idx_host, int nshards, int shard,
+                       int precision, sfs_operator** op);
+int sfs_normal_residual(sfs_operator* op, const void* x_dev, const void* y_dev, void* g_dev,
+                        void* stream);
+int sfs_prox_momentum(int n, void* x_dev, void* gamma_dev, const void* grad_dev, double lambda,
+                      double L, double beta, void* stream);
+int sfs_vec_sumsq(sfs_operator* op, const void* v_dev, int n, double* out_host, void* stream);
+int sfs_vec_max_abs(sfs_operator* op, const void* v_dev, int n, double* out_host, void* stream);
+int sfs_vec_scale(void* v_dev, int n, double a, void* stream);
+int sfs_vec_randn(void* v_dev, int n, uint64_t seed, void* stream);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char* sfs_last_error(void);

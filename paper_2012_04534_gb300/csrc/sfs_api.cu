@@ -798,6 +798,14 @@ std::vector<int2> segment_slots(int nseg, int U, int G) {
 }  // namespace
 }  // namespace sfs
 
+namespace sfs {
+void shard_run(int U, int nshards, int shard, int* first, int* count) {
+  const long long a = (long long)U * shard / nshards, b = (long long)U * (shard + 1) / nshards;
+  *first = (int)a;
+  *count = (int)(b - a);
+}
+}  // namespace sfs
+
 using namespace sfs;
 
 extern "C" {
@@ -875,7 +883,7 @@ int sfs_select_indices(const sfs_geometry* g, int strategy, int M, int per_posit
 }
 
 static int build_operator(sfs_geometry* g, int M, const int32_t* idx_host, int prec,
-                          sfs_operator** out) {
+                          sfs_operator** out, int nshards = 1, int shard = 0) {
   if (!g || !idx_host || !out) {
     set_error("null argument");
     return SFS_ERR_INVALID_ARG;
@@ -920,12 +928,26 @@ static int build_operator(sfs_geometry* g, int M, const int32_t* idx_host, int p
   op->idx.assign(idx_host, idx_host + (size_t)S * M);
   std::vector<char> used(nbins, 0);
   for (int32_t k : op->idx) used[k - kmin] = 1;
-  std::vector<int> u_of(nbins, -1);  // union position of bin k at k - kmin
+  std::vector<int32_t> all_bins;
   for (int k = kmin; k <= kmax; ++k)
-    if (used[k - kmin]) {
-      u_of[k - kmin] = (int)op->bins.size();
-      op->bins.push_back(k);
-    }
+    if (used[k - kmin]) all_bins.push_back(k);
+  // the operator's run of the union (all of it unless sharded)
+  int first = 0, count = (int)all_bins.size();
+  shard_run((int)all_bins.size(), nshards, shard, &first, &count);
+  if (count < 1) {
+    set_error("shard %d of %d holds no bin (the union has %d)", shard, nshards, (int)all_bins.size());
+    delete op;
+    return SFS_ERR_INVALID_ARG;
+  }
+  op->nshards = nshards;
+  op->shard = shard;
+  op->shard_first = first;
+  op->U_all = (int)all_bins.size();
+  std::vector<int> u_of(nbins, -1);  // position of bin k in this operator's bins, at k - kmin
+  for (int j = 0; j < count; ++j) {
+    u_of[all_bins[first + j] - kmin] = j;
+    op->bins.push_back(all_bins[first + j]);
+  }
   op->U = (int)op->bins.size();
   // band the strategies would use (reported only)
   if (candidate_band(g, M, &op->k_lo, &op->k_hi, &op->band_db) != SFS_OK) {
@@ -1047,7 +1069,10 @@ static int build_operator(sfs_geometry* g, int M, const int32_t* idx_host, int p
   }
   std::vector<int32_t> posmap((size_t)op->U * S, -1);
   for (int s = 0; s < S; ++s)
-    for (int m = 0; m < M; ++m) posmap[(size_t)u_of[op->idx[(size_t)s * M + m] - kmin] * S + s] = m;
+    for (int m = 0; m < M; ++m) {
+      const int u = u_of[op->idx[(size_t)s * M + m] - kmin];
+      if (u >= 0) posmap[(size_t)u * S + s] = m;  // rows of other shards stay unmapped
+    }
 
   DeviceScope scope(d.device);
   if (!scope.ok()) {
@@ -1171,6 +1196,29 @@ static int build_operator(sfs_geometry* g, int M, const int32_t* idx_host, int p
   return SFS_OK;
 }
 
+}  // extern "C"
+
+namespace sfs {
+int build_operator_shard(sfs_geometry* g, int M, const int32_t* idx_host, int prec, int nshards,
+                         int shard, sfs_operator** out) {
+  return build_operator(g, M, idx_host, prec, out, nshards, shard);
+}
+
+int normal_residual(sfs_operator* op, const float2* x, const float2* y, float2* g, cudaStream_t st) {
+  const PlaneDims d = dims_of(op);
+  SFS_TRY(launch_scatter_y_planes(d, y, op->posmap, op->ws.yplane, st));
+  SFS_TRY(launch_fwd_planes(d, x, op->ws.Xh, st));
+  SFS_TRY(launch_contract_fwd(d, op->table, op->ws.Xh, op->ws.Yh, op->ws.err, st));
+  SFS_TRY(launch_inv_resid_fwd(d, op->ws.Yh, op->posmap, op->ws.yplane, op->ws.Rh, nullptr, st));
+  SFS_TRY(launch_contract_adj(d, op->table, op->ws.Rh, op->ws.Gh, op->ws.err, st));
+  return launch_inv_store(d, op->ws.Gh, op->ws.segslot, g, nullptr, nullptr, st);
+}
+
+int check_err_flag_op(sfs_operator* op, cudaStream_t st) { return check_err_flag(op, st); }
+}  // namespace sfs
+
+extern "C" {
+
 int sfs_operator_from_indices(sfs_geometry* g, int M, const int32_t* idx_host,
                               sfs_operator** out) {
   clear_error();
@@ -1245,6 +1293,10 @@ int sfs_operator_info(const sfs_operator* op, sfs_operator_info_t* info) {
   info->Nslot = op->Ns;
   info->GS = op->GS;
   info->precision = op->prec;
+  info->nshards = op->nshards;
+  info->shard = op->shard;
+  info->shard_first = op->shard_first;
+  info->U_all = op->U_all;
   return SFS_OK;
 }
 
@@ -1310,7 +1362,9 @@ int sfs_frobenius(const sfs_operator* op, double* fro2_out, double* sigma_hat_ou
   for (int s = 0; s < op->S; ++s) {
     double h2 = 0.0;
     for (int m = 0; m < op->M; ++m) {
-      const double h = pulse_mag((double)op->idx[(size_t)s * op->M + m] * d.fs / d.Nt, d.fc, op->geo.alpha);
+      const int k = op->idx[(size_t)s * op->M + m];
+      if (k < op->bins.front() || k > op->bins.back()) continue;  // another shard's row
+      const double h = pulse_mag((double)k * d.fs / d.Nt, d.fc, op->geo.alpha);
       h2 += h * h;
     }
     fro2 += G[s] * h2;

@@ -132,6 +132,19 @@ extern "C" int sfs_fista_backtracking(sfs_operator* op, const void* y_dev, doubl
   SFS_CUDA(cudaMemsetAsync(op->ws.xk, 0, (size_t)V * sizeof(float2), st));
   SFS_CUDA(cudaMemsetAsync(op->ws.gam, 0, (size_t)V * sizeof(float2), st));
   SFS_TRY(launch_scatter_y_planes(d, ybuf, op->posmap, op->ws.yplane, st));
+  // An early exit first reads (and clears) the operator's device error flag:
+  // a bounded wait that ran out in a contraction can surface as a
+  // non-finite sum, and is then reported as the timeout it was.
+  auto early_exit = [&](int rc) -> int {
+    int hf = 0;
+    if (cudaMemcpyAsync(&hf, op->ws.err, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+        cudaStreamSynchronize(st) == cudaSuccess && hf) {
+      cudaMemset(op->ws.err, 0, sizeof(int));
+      set_error("a bounded wait in a contraction kernel timed out");
+      return SFS_ERR_TIMEOUT;
+    }
+    return rc;
+  };
   double lam = lambda;
   if (lambda < 0) {  // mu rule: lambda = -lambda ||A^H y||_inf
     unsigned int* bits = (unsigned int*)(op->ws.scal + kLamMax);
@@ -146,7 +159,7 @@ extern "C" int sfs_fista_backtracking(sfs_operator* op, const void* y_dev, doubl
     memcpy(&mx, &hb, sizeof(mx));
     if (!isfinite(mx)) {
       set_error("non-finite value reached the lambda rule");
-      return SFS_ERR_NON_FINITE;
+      return early_exit(SFS_ERR_NON_FINITE);
     }
     lam = -lambda * (double)mx;
   }
@@ -162,7 +175,7 @@ extern "C" int sfs_fista_backtracking(sfs_operator* op, const void* y_dev, doubl
     for (int trial = 0;; ++trial) {
       if (trial > 200 || !isfinite(L)) {
         set_error("backtracking found no step (L = %g)", L);
-        return SFS_ERR_NOT_CONVERGED;
+        return early_exit(SFS_ERR_NOT_CONVERGED);
       }
       bt_prox_kernel<<<gridv, kBtThreads, 0, st>>>(V, op->ws.gam, g, (float)(1.0 / L), (float)(lam / L), p, dv,
                                                    part);
@@ -177,7 +190,7 @@ extern "C" int sfs_fista_backtracking(sfs_operator* op, const void* y_dev, doubl
       SFS_CUDA(cudaStreamSynchronize(st));
       if (!isfinite(h[0]) || !isfinite(h[1])) {
         set_error("non-finite step in backtracking");
-        return SFS_ERR_NON_FINITE;
+        return early_exit(SFS_ERR_NON_FINITE);
       }
       if (h[1] <= L * h[0]) break;  // ||A d||^2 <= L ||d||^2 (d = 0 passes)
       L *= eta;

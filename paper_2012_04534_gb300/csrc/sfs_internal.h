@@ -142,6 +142,10 @@ struct sfs_operator {
   int inject = 0;                                // see PlaneDims::inject
   int k_lo = 0, k_hi = 0;
   double band_db = 0.0;
+  // bin shard (sfs_operator_shard): this operator holds the run
+  // [shard_first, shard_first + U) of the union of all kept bins, split
+  // into nshards runs; its rows are the measurements of those bins
+  int nshards = 1, shard = 0, shard_first = 0, U_all = 0;
   std::vector<int32_t> idx;    // [S][M]
   std::vector<int32_t> bins;   // [U] union of kept bins, ascending
   // device data
@@ -245,6 +249,18 @@ int contract_units(const PlaneDims& d);
 
 // Kernel-side dimensions and tables of an operator (sfs_api.cu).
 PlaneDims operator_dims(const sfs_operator* op);
+
+// Operator build (sfs_api.cu): the union of the kept bins of idx_host is
+// split into nshards contiguous runs of floor-balanced length (run j holds
+// positions [j U / n, (j + 1) U / n) of the ascending union); the operator
+// keeps run `shard` (nshards = 1: every bin).
+int build_operator_shard(sfs_geometry* g, int M, const int32_t* idx_host, int prec, int nshards,
+                         int shard, sfs_operator** out);
+// First union position and length of run `shard` of U bins in nshards.
+void shard_run(int U, int nshards, int shard, int* first, int* count);
+// g = A^H (A x - y) on the operator's own rows (single scene, its workspace).
+int normal_residual(sfs_operator* op, const float2* x, const float2* y, float2* g, cudaStream_t st);
+int check_err_flag_op(sfs_operator* op, cudaStream_t st);
 
 // Table of generators (Theorem 2 / Eq. (4)); tof: float2 [Nz][Ny][Nx]
 // (hi, lo) of (tau - t0) fs / Nt in turns per unit bin; gdir: float

@@ -77,6 +77,10 @@ struct TcMaps {
   CUtensorMap rh;     // R^ c64 [Up][Ns] as floats, box 16 x 64
   const void* xh_ptr = nullptr;
   const void* rh_ptr = nullptr;
+  // map of single-scene residual spectra at one other address (the static
+  // scratch of sfs_apply_AH_noalloc), encoded on first use and kept
+  CUtensorMap rh_alt;
+  const void* rh_alt_ptr = nullptr;
 };
 
 void free_tc_maps(TcMaps* m) { delete m; }
@@ -710,9 +714,22 @@ int launch_contract_fwd_h(const PlaneDims& d, const float2* Xh, float2* Yp, int*
 
 int launch_contract_adj_h(const PlaneDims& d, const float2* Rh, float2* Gs, int* err, cudaStream_t st) {
   SFS_TRY(check_maps(d));
-  // spectra elsewhere than the operator's workspace (e.g. the static scratch
-  // of sfs_apply_AH_noalloc, or a batched workspace) get a map of their own
-  const CUtensorMap* cached = (Rh == d.tmaps->rh_ptr && d.batch <= 1) ? &d.tmaps->rh : nullptr;
+  // spectra elsewhere than the operator's workspace get a map of their own:
+  // a batched workspace per launch, one other single-scene address (the
+  // static scratch of sfs_apply_AH_noalloc) once, then from the cache
+  const CUtensorMap* cached = nullptr;
+  if (d.batch <= 1) {
+    if (Rh == d.tmaps->rh_ptr) {
+      cached = &d.tmaps->rh;
+    } else {
+      if (Rh != d.tmaps->rh_alt_ptr) {
+        d.tmaps->rh_alt_ptr = nullptr;
+        SFS_TRY(encode_spec(&d.tmaps->rh_alt, Rh, d.Up, d.Ns, 64));
+        d.tmaps->rh_alt_ptr = Rh;
+      }
+      cached = &d.tmaps->rh_alt;
+    }
+  }
   return launch_groups<false>(d, d.tmaps->tab_a, cached, Rh, d.bs_rh, d.Up, 64, Gs, d.bs_gh, err, st);
 }
 

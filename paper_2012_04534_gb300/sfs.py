@@ -68,7 +68,8 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_apply_A_mixed", "sfs_apply_AH_mixed", "sfs_lipschitz_mixed", "sfs_fista_mixed",
            "sfs_autotune_batch", "sfs_set_batch_tile", "sfs_fista_backtracking", "sfs_grouped_times",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
-           "sfs_set_wait_timeout_ns",
+           "sfs_set_wait_timeout_ns", "sfs_shard_run", "sfs_operator_shard", "sfs_normal_residual",
+           "sfs_prox_momentum", "sfs_vec_sumsq", "sfs_vec_max_abs", "sfs_vec_scale", "sfs_vec_randn",
            "sfs_inject_wait_timeout", "sfs_check_status", "sfs_last_error", "sfs_version")
 
 
@@ -96,7 +97,9 @@ class OperatorInfo(ctypes.Structure):
                 ("band_db", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("t0", ctypes.c_double), ("table_bytes", ctypes.c_int64),
                 ("launches_per_iter", ctypes.c_int32), ("Nslot", ctypes.c_int32),
-                ("GS", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("GS", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("nshards", ctypes.c_int32), ("shard", ctypes.c_int32),
+                ("shard_first", ctypes.c_int32), ("U_all", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -154,6 +157,14 @@ def lib():
         "sfs_stage_times": [vp, P(dbl), P(ctypes.c_int32)],
         "sfs_check_status": [vp, vp],
         "sfs_inject_wait_timeout": [vp, i32],
+        "sfs_shard_run": [i32, i32, i32, P(ctypes.c_int32), P(ctypes.c_int32)],
+        "sfs_operator_shard": [vp, i32, P(ctypes.c_int32), i32, i32, i32, P(vp)],
+        "sfs_normal_residual": [vp, vp, vp, vp, vp],
+        "sfs_prox_momentum": [i32, vp, vp, vp, dbl, dbl, dbl, vp],
+        "sfs_vec_sumsq": [vp, vp, i32, P(dbl), vp],
+        "sfs_vec_max_abs": [vp, vp, i32, P(dbl), vp],
+        "sfs_vec_scale": [vp, i32, dbl, vp],
+        "sfs_vec_randn": [vp, i32, u64, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -285,6 +296,31 @@ def sfs_fista(op, y_dev_ptr, lam, L, iters, x_dev_ptr, state_dev_ptr, flags, obj
         ptr = obj_hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     _check(lib().sfs_fista(op, y_dev_ptr, lam, L, iters, x_dev_ptr, state_dev_ptr, flags, ptr,
                            stream_ptr))
+
+
+def shard_run(U: int, nshards: int, shard: int):
+    """sfs_shard_run: (first union position, count) of run `shard`."""
+    f, c = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().sfs_shard_run(int(U), int(nshards), int(shard), ctypes.byref(f), ctypes.byref(c)))
+    return f.value, c.value
+
+
+def prox_momentum(x, gamma, grad, lam, L, beta, stream=None):
+    """sfs_prox_momentum: x <- tau_{lam/L}(gamma - grad/L), gamma <- x + beta (x - x_prev)."""
+    n = int(x.numel())
+    _check(lib().sfs_prox_momentum(n, _dev_ptr(x, n, "x"), _dev_ptr(gamma, n, "gamma"),
+                                   _dev_ptr(grad, n, "grad"), float(lam), float(L), float(beta),
+                                   _stream_ptr(stream, x.device)))
+
+
+def vec_scale(v, a, stream=None):
+    _check(lib().sfs_vec_scale(_dev_ptr(v, v.numel(), "v"), int(v.numel()), float(a),
+                               _stream_ptr(stream, v.device)))
+
+
+def vec_randn(v, seed, stream=None):
+    _check(lib().sfs_vec_randn(_dev_ptr(v, v.numel(), "v"), int(v.numel()), int(seed),
+                               _stream_ptr(stream, v.device)))
 
 
 def sfs_kernel_times(op):
@@ -422,6 +458,39 @@ class Operator:
         op = cls(geom, h)
         op.idx = np.ascontiguousarray(idx, dtype=np.int32)
         return op
+
+    @classmethod
+    def shard(cls, geom: Geometry, idx, nshards: int, shard: int, precision: int = SFS_PREC_FP32):
+        """sfs_operator_shard: the rows of run `shard` of the bin union cut in
+        `nshards` (measurement layout stays [S][M])."""
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(lib().sfs_operator_shard(geom.handle, idx.shape[1],
+                                        idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                        int(nshards), int(shard), int(precision), ctypes.byref(h)))
+        op = cls(geom, h)
+        op.idx = idx
+        return op
+
+    def normal_residual(self, x, y, out=None, stream=None):
+        """sfs_normal_residual: A^H (A x - y) over this operator's rows."""
+        g = self._new(self.shape_x) if out is None else out
+        _check(lib().sfs_normal_residual(self.handle, _dev_ptr(x, self.V, "x"),
+                                         _dev_ptr(y, self.S * self.M, "y"), _dev_ptr(g, self.V, "g"),
+                                         _stream_ptr(stream, x.device)))
+        return g
+
+    def vec_sumsq(self, v, stream=None):
+        out = ctypes.c_double()
+        _check(lib().sfs_vec_sumsq(self.handle, _dev_ptr(v, v.numel(), "v"), int(v.numel()),
+                                   ctypes.byref(out), _stream_ptr(stream, v.device)))
+        return out.value
+
+    def vec_max_abs(self, v, stream=None):
+        out = ctypes.c_double()
+        _check(lib().sfs_vec_max_abs(self.handle, _dev_ptr(v, v.numel(), "v"), int(v.numel()),
+                                     ctypes.byref(out), _stream_ptr(stream, v.device)))
+        return out.value
 
     def _new(self, shape):
         import torch
