@@ -916,7 +916,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step():
-        # the iteration graph with event nodes around the kernels of <= 32
+        # the iteration graph with event nodes around the kernels of <= 8
         # sampled iterations: the per-kernel times of the roofline come from
         # this same timed loop
         op.fista(y, -w["mu"], L, iters, x=x, time_kernels=True)
@@ -1041,7 +1041,7 @@ def main():
                  "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": alg_flops,
                  "hbm_frac": hbm_frac, "alu_frac": alu_frac,
                  "fwd_ms": fwd_ms, "adj_ms": adj_ms, "iterations_timed": stage_acc["n"],
-                 "timing": "event-record nodes around the kernels of <= 32 sampled iterations of each "
+                 "timing": "event-record nodes around the kernels of <= 8 sampled iterations of each "
                            "timed step's graph; stages sum to the time of those iterations",
                  "iteration_stages_ms": {"contract_fwd": stage_ms[0], "resid_planes": stage_ms[1],
                                          "contract_adj": stage_ms[2], "update_planes": stage_ms[3]},

@@ -535,7 +535,7 @@ int sfs_fista_backtracking(sfs_operator* op, const void* y_dev, double lambda, d
  * 1/2||A gamma_k - y||^2 + lambda||x_k||_1 (a monitor evaluated with the
  * residual at gamma_k); when given, the call synchronises `stream`.
  * SFS_FISTA_TIME_KERNELS records an event before and after every kernel of
- * ceil(iters / 32)-spaced iterations (at most 32, spread over the solve) as
+ * ceil(iters / 8)-spaced iterations (at most 8, spread over the solve) as
  * event-record nodes of the replayed iteration graph, read by
  * sfs_stage_times; the other iterations run without them.
  * Errors: SFS_ERR_INVALID_ARG (also RESUME without state_dev, or RESUME

@@ -58,6 +58,31 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
+// L2 policy for data read once per launch and larger than the L2 (the
+// generator table of the large workloads): evict first, so that the
+// spectra the kernels re-read stay resident.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// bulk_g2s with an L2 cache policy.
+__device__ __forceinline__ void bulk_g2s_hint(uint32_t dst, const void* src, uint32_t bytes,
+                                              uint32_t bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, "
+      "[%3], %4;" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(policy)
+      : "memory");
+}
+// The table copy of the contractions: with `stream` set, evict-first.
+__device__ __forceinline__ void bulk_g2s_table(uint32_t dst, const void* src, uint32_t bytes,
+                                               uint32_t bar, bool stream, uint64_t policy) {
+  if (stream)
+    bulk_g2s_hint(dst, src, bytes, bar, policy);
+  else
+    bulk_g2s(dst, src, bytes, bar);
+}
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(

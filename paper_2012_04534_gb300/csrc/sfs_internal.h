@@ -101,6 +101,7 @@ struct Workspace {
   int obj_cap = 0;
   float* beta = nullptr;    // [beta_cap] momentum coefficients of the current FISTA call
   int beta_cap = 0;
+  int beta_fresh = 0;       // beta[0..beta_fresh) holds the sequence from t_1 = 1
   double* tnext = nullptr;  // t_{k+1} after the current FISTA call (no state buffer given)
 };
 
@@ -139,6 +140,7 @@ struct sfs_operator {
   int nslots = 0;              // adjoint partial-sum slots
   int adj_seg = 0, azb = 128, anzb = 1, Ga = 0;  // adjoint layout (see PlaneDims)
   uint64_t wait_ns = 2000000000ull;              // bounded-wait limit (2 s)
+  int stream_table = 0;                          // see PlaneDims::stream_table
   int inject = 0;                                // see PlaneDims::inject
   int k_lo = 0, k_hi = 0;
   double band_db = 0.0;
@@ -218,6 +220,7 @@ struct PlaneDims {
   int azb;      // depth rows per adjoint segment (32 segment-aligned, 128 otherwise)
   int anzb;     // adjoint depth blocks per slot tile
   int Ga;       // CTAs of the segment-aligned adjoint (= its segment count)
+  int stream_table;  // the table exceeds half the L2: its copies are evict-first
   uint64_t wait_ns;  // limit of each bounded mbarrier wait in the contractions
   int inject;        // failure-handling tests: first wait of each warp never completes
   // Scenes sharing this operator processed by one launch (gridDim.y of the

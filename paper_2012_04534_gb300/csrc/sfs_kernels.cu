@@ -860,7 +860,7 @@ template <int GS>
 __global__ void __launch_bounds__(kContractThreads, kContractCtasPerSm)
 contract_fwd_stream(const float4* __restrict__ T4, const float4* __restrict__ Xh,
                     float4* __restrict__ Yp, int Nz, int Up, int Ns, int nzb, int nunits,
-                    int* __restrict__ err, uint64_t wait_ns, int inject) {
+                    int* __restrict__ err, uint64_t wait_ns, int inject, int stream_table) {
   constexpr int E = kKappaTile / GS;
   constexpr int UP = GS / 2;
   constexpr int STAGE = UP * kZPairs * E;  // float4 per stage (32 KB)
@@ -894,9 +894,11 @@ contract_fwd_stream(const float4* __restrict__ T4, const float4* __restrict__ Xh
     const float4* src = T4 + ((size_t)(ip.st * Up + ip.ug * UP) * Nzp + ip.zb * kZPairs) * E;
     fence_proxy_async();
     mbar_expect_tx(bar, bytes * UP);
+    const uint64_t pol = stream_table ? l2_evict_first_policy() : 0ull;
 #pragma unroll
     for (int q = 0; q < UP; ++q)
-      bulk_g2s(smem_addr(stage + q * kZPairs * E), src + (size_t)q * Nzp * E, bytes, bar);
+      bulk_g2s_table(smem_addr(stage + q * kZPairs * E), src + (size_t)q * Nzp * E, bytes, bar,
+                     stream_table != 0, pol);
     ip.next(NUG, nzb);
   };
   if (threadIdx.x == 0)
@@ -985,7 +987,7 @@ contract_fwd_stream(const float4* __restrict__ T4, const float4* __restrict__ Xh
 template <int GS>
 __device__ __forceinline__ void issue_adj_unit(const float4* __restrict__ T4, const UnitPos& p,
                                                int Up, int Nzp, int w, float4* slot,
-                                               uint32_t bar) {
+                                               uint32_t bar, int stream_table) {
   constexpr int E = kKappaTile / GS;
   constexpr int UP = GS / 2;
   const int p0 = p.zb * kZPairs + w * kPairsPerWarp;
@@ -995,9 +997,11 @@ __device__ __forceinline__ void issue_adj_unit(const float4* __restrict__ T4, co
   mbar_expect_tx(bar, bytes * UP);
   if (bytes) {
     const float4* src = T4 + ((size_t)(p.st * Up + p.ug * UP) * Nzp + p0) * E;
+    const uint64_t pol = stream_table ? l2_evict_first_policy() : 0ull;
 #pragma unroll
     for (int q = 0; q < UP; ++q)
-      bulk_g2s(smem_addr(slot + q * kPairsPerWarp * E), src + (size_t)q * Nzp * E, bytes, bar);
+      bulk_g2s_table(smem_addr(slot + q * kPairsPerWarp * E), src + (size_t)q * Nzp * E, bytes, bar,
+                     stream_table != 0, pol);
   }
 }
 
@@ -1011,7 +1015,7 @@ template <int GS>
 __global__ void __launch_bounds__(kContractThreads, kContractCtasPerSm)
 contract_adj_stream(const float4* __restrict__ T4, const float4* __restrict__ Rh,
                     float4* __restrict__ Gs, int Nz, int Up, int Ns, int nzb, int nunits,
-                    int* __restrict__ err, uint64_t wait_ns, int inject) {
+                    int* __restrict__ err, uint64_t wait_ns, int inject, int stream_table) {
   constexpr int E = kKappaTile / GS;
   constexpr int UP = GS / 2;
   constexpr int SLOT = UP * kPairsPerWarp * E;  // float4 per slot (4 KB)
@@ -1040,7 +1044,7 @@ contract_adj_stream(const float4* __restrict__ T4, const float4* __restrict__ Rh
   for (; next_issue < kSlots - 1 && next_issue < n; ++next_issue, ip.next(NUG, nzb))
     if (lane == 0)
       issue_adj_unit<GS>(T4, ip, Up, Nzp, w, my + (next_issue % kSlots) * SLOT,
-                         bar0 + 8u * (next_issue % kSlots));
+                         bar0 + 8u * (next_issue % kSlots), stream_table);
   pdl_wait();  // Rh comes from the predecessor; the table copies above do not
   pdl_trigger();
   // Rh rows of the next unit prefetched into registers
@@ -1065,7 +1069,7 @@ contract_adj_stream(const float4* __restrict__ T4, const float4* __restrict__ Rh
     if (next_issue < n) {
       if (lane == 0)
         issue_adj_unit<GS>(T4, ip, Up, Nzp, w, my + (next_issue % kSlots) * SLOT,
-                           bar0 + 8u * (next_issue % kSlots));
+                           bar0 + 8u * (next_issue % kSlots), stream_table);
       ++next_issue;
       ip.next(NUG, nzb);
     }
@@ -1486,7 +1490,7 @@ int launch_fwd_gs(const PlaneDims& d, const float2* table, const float2* Xh, flo
   const int G = std::min(d.G, n);
   return launch_pdl(contract_fwd_stream<GS>, dim3(G), dim3(kContractThreads), smem, st,
                     (const float4*)table, (const float4*)Xh, (float4*)Yp, d.Nz, d.Up, d.Ns, d.nzb, n,
-                    err, d.wait_ns, d.inject);
+                    err, d.wait_ns, d.inject, d.stream_table);
 }
 template <int GS>
 int launch_adj_gs(const PlaneDims& d, const float2* table, const float2* Rh, float2* Gs,
@@ -1497,7 +1501,7 @@ int launch_adj_gs(const PlaneDims& d, const float2* table, const float2* Rh, flo
   const int G = std::min(d.G, n);
   return launch_pdl(contract_adj_stream<GS>, dim3(G), dim3(kContractThreads), smem, st,
                     (const float4*)table, (const float4*)Rh, (float4*)Gs, d.Nz, d.Up, d.Ns, d.nzb, n, err, d.wait_ns,
-                    d.inject);
+                    d.inject, d.stream_table);
 }
 }  // namespace
 

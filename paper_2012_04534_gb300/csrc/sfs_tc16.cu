@@ -166,6 +166,22 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
       "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
       : "memory");
 }
+// The same with an L2 cache policy (evict-first for a table larger than L2).
+__device__ __forceinline__ void tma_load_4d_hint(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                                 int c3, uint32_t bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6], %7;" ::"r"(dst),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_table(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                               int c3, uint32_t bar, bool stream, uint64_t policy) {
+  if (stream)
+    tma_load_4d_hint(dst, map, c0, c1, c2, c3, bar, policy);
+  else
+    tma_load_4d(dst, map, c0, c1, c2, c3, bar);
+}
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
                                             uint32_t bar) {
   asm volatile(
@@ -380,15 +396,19 @@ contract_h(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUte
       item(i, o, mt, c);
       if (elect_one()) {
         const uint32_t dst = sbase + (uint32_t)(s * Pl::kTStage), fb = bar(Pl::kTF + s);
+        const bool stream = d.stream_table != 0;
+        const uint64_t pol = stream ? l2_evict_first_policy() : 0ull;
         mbar_expect_tx(fb, NP * kHATile);
         if (FWD) {  // bins 128 mt .., depth block c
 #pragma unroll
-          for (int p = 0; p < NP; ++p) tma_load_4d(dst + p * kHATile, &tab, 0, 128 * mt, c, p * No + o, fb);
+          for (int p = 0; p < NP; ++p)
+            tma_load_table(dst + p * kHATile, &tab, 0, 128 * mt, c, p * No + o, fb, stream, pol);
         } else {  // bins 64 c .., depth blocks 2 mt and 2 mt + 1
 #pragma unroll
           for (int p = 0; p < NP; ++p) {
-            tma_load_4d(dst + p * kHATile, &tab, 0, 64 * c, 2 * mt, p * No + o, fb);
-            tma_load_4d(dst + p * kHATile + 8192, &tab, 0, 64 * c, 2 * mt + 1, p * No + o, fb);
+            tma_load_table(dst + p * kHATile, &tab, 0, 64 * c, 2 * mt, p * No + o, fb, stream, pol);
+            tma_load_table(dst + p * kHATile + 8192, &tab, 0, 64 * c, 2 * mt + 1, p * No + o, fb, stream,
+                           pol);
           }
         }
       }

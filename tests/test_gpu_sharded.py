@@ -80,8 +80,9 @@ def test_sharded_operator_and_fista(sfs, case):
     assert rel_err(to_host(full.normal_residual(xd, yd)), ref.apply_AH(ref.apply_A(x) - y)) <= tol
     if mode != "fp32":
         return
-    L_ref, _ = O.power_iteration(ref.apply_A, ref.apply_AH, full.shape_x, 1, max_iter=600, rtol=1e-12)
-    L_sh, ok = solver.lipschitz(max_iter=600, rtol=1e-9, seed=3, safety=0.0)
+    L_ref, _ = O.power_iteration(ref.apply_A, ref.apply_AH, full.shape_x, 1, max_iter=3000, rtol=1e-12)
+    # FP32 vectors: the estimate's relative change settles near 1e-7, so stop at 1e-6
+    L_sh, ok = solver.lipschitz(max_iter=3000, rtol=1e-6, seed=3, safety=0.0)
     assert ok and abs(L_sh - L_ref) <= 1e-4 * L_ref
     L = L_ref * 1.001
     x_true = synth.scene(full.shape_x, 4, "uniform", seed=23)
