@@ -972,7 +972,10 @@ def main():
     clk = clocks.stop()
     ms = max_over_ranks(ms, world)
     value = job_rate(world, args.steps, iters, ms)
-    launches_per_step = 4 * iters + 5 if iters > 0 else 4
+    # per step: the lambda rule (scatter_fwd, adjoint contraction, inv_store),
+    # set_thresholds, scatter_y_planes and the first fwd_planes, then four
+    # kernels per iteration (the momentum table of a fresh start is reused)
+    launches_per_step = 4 * iters + 6 if iters > 0 else 4
     stage_ms = (stage_acc["sum"] / max(1, stage_acc["n"])).tolist()
 
     # the same steps on the graph without event nodes, for comparison
