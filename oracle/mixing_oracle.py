@@ -67,16 +67,17 @@ def mix_time_domain(B_band, xi, kept, band, Nt: int):
 class MixedOperator:
     """A_mix = Mix o A_band: A_band evaluates every bin of `band` (default:
     all Nt bins of the A-scan, ``full_band``) at every position with the
-    lateral-FFT oracle of Sec. IV-B, and Mix applies each position's mixing
-    matrix.  idx: [S][M] kept bins, xi: [S][Nt] of +-1."""
+    lateral-FFT oracle of Sec. IV-B (``workers`` threads, identical results),
+    and Mix applies each position's mixing matrix.  idx: [S][M] kept bins,
+    xi: [S][Nt] of +-1."""
 
-    def __init__(self, g: Geometry, idx, xi, band=None):
+    def __init__(self, g: Geometry, idx, xi, band=None, workers: int = 1):
         self.g = g
         self.band = full_band(g.Nt) if band is None else np.asarray(band, dtype=np.int64)
         self.idx = np.asarray(idx, dtype=np.int64)
         self.xi = np.asarray(xi, dtype=np.float64)
         S = g.S
-        self.A_band = LateralFFTOperator(g, np.tile(self.band.astype(np.int32), (S, 1)))
+        self.A_band = LateralFFTOperator(g, np.tile(self.band.astype(np.int32), (S, 1)), workers=workers)
         self.Mix = np.stack([mixing_matrix(self.xi[s], self.idx[s], self.band, g.Nt) for s in range(S)])
 
     def apply_A(self, x):

@@ -5,6 +5,10 @@ depend on the thread count).
   * 32 x 32 scan, 32 x 32 x 128 voxels (Nt 512, M 64 random bins per
     position): FISTA after 200 and after 300 iterations within 1e-4, same
     L and lambda on both sides.
+  * the same 32 x 32 workload measured through Rademacher mixing (every
+    position its own xi_s and bins): A_mix and A_mix^H within 1e-5 of the
+    oracle that mixes all 512 bins of each A-scan, and 30 mixed FISTA
+    iterations within 1e-4.
   * 64 x 64 scan, 64 x 64 x 256 voxels (Nt 1024, M 128, 128 x 128 lateral
     planes, 723 MB folded table): one whole A x and A^H y in FP32 (1e-5 in
     norm, 1e-4 of the oracle's largest entry element-wise), BF16 and FP16
@@ -134,3 +138,28 @@ def test_vol64_fista_20_iterations(sfs, vol64):
     x_ref = O.fista(ref.apply_A, ref.apply_AH, y, lam, L, 20)
     assert np.abs(x_ref).max() > 0
     assert rel_err(to_host(op.fista(to_dev(y), lam, L, 20)), x_ref) <= TOL_FISTA
+
+
+def test_vol32_mixing_full_size(sfs):
+    from oracle import mixing_oracle as X
+    w = synth.WORKLOADS["vol32"]
+    params = synth.geometry_params("vol32")
+    go = oracle_geometry(params)
+    g = sfs.Geometry(**params)
+    idx = O.select_indices(go, O.SEL_RANDOM, w["M"], True, 1001)
+    xi = synth.rademacher((go.S, go.Nt), seed=1001 + 4242)
+    mx = sfs.Mixing.create(g, idx, xi)
+    mx.band._geom = g
+    ref = X.MixedOperator(go, idx, xi, workers=WORKERS)
+    rng = np.random.default_rng(41)
+    x = crandn(rng, go.Nz, go.Ny, go.Nx)
+    y = crandn(rng, go.S, w["M"])
+    assert rel_err(to_host(mx.apply_A(to_dev(x))), ref.apply_A(x)) <= TOL_OP
+    assert rel_err(to_host(mx.apply_AH(to_dev(y))), ref.apply_AH(y)) <= TOL_OP
+    x_true = synth.scene((go.Nz, go.Ny, go.Nx), w["n_scatter"], w["amp"], seed=1001)
+    ym = noisy_measurements(ref, x_true, w["snr_db"], 7)
+    L, _ = mx.lipschitz(max_iter=300, rtol=1e-6, seed=3, safety=1e-3)
+    lam = O.lambda_from_mu(ref.apply_AH, ym, w["mu"])
+    x_ref = O.fista(ref.apply_A, ref.apply_AH, ym, lam, L, 30)
+    assert np.abs(x_ref).max() > 0
+    assert rel_err(to_host(mx.fista(to_dev(ym), lam, L, 30)), x_ref) <= TOL_FISTA
