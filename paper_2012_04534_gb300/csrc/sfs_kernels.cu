@@ -542,7 +542,9 @@ inv_gather_kernel(PlaneDims d, const float2* __restrict__ Yh,
     if (m >= 0) {
       const float2 v = buf[F::sidx(s / d.Nx, s % d.Nx)];
       y[(size_t)s * d.M + m] = v;
-      acc += (double)v.x * v.x + (double)v.y * v.y;
+      // FP64 sums only when asked for: the FP64 pipe runs at a small
+      // fraction of the FP32 rate, and the iteration loop asks for none
+      if (red_sumsq) acc += (double)v.x * v.x + (double)v.y * v.y;
     }
   }
   if (red_sumsq) block_add_double<F::NT>(acc, red_sumsq);
@@ -582,7 +584,7 @@ inv_resid_fwd_kernel(PlaneDims d, const float2* __restrict__ Yh,
     float2 r = make_float2(0.f, 0.f);
     if (m >= 0) {
       r = csub(buf[e], yv);
-      acc += (double)r.x * r.x + (double)r.y * r.y;
+      if (red_sumsq) acc += (double)r.x * r.x + (double)r.y * r.y;
     }
     buf[e] = r;
   }
@@ -651,8 +653,8 @@ inv_store_kernel(PlaneDims d, const float2* __restrict__ Gh, const int2* __restr
   for (int e = threadIdx.x; e < d.Ny * d.Nx; e += F::NT) {
     const float2 v = buf[F::sidx(e / d.Nx, e % d.Nx)];
     if (xz) xz[e] = v;
-    acc += (double)v.x * v.x + (double)v.y * v.y;
-    mx = nanmax(mx, hypotf(v.x, v.y));
+    if (red_sumsq) acc += (double)v.x * v.x + (double)v.y * v.y;
+    if (maxabs_bits) mx = nanmax(mx, hypotf(v.x, v.y));
   }
   if (red_sumsq) block_add_double<F::NT>(acc, red_sumsq);
   if (maxabs_bits) {
@@ -708,7 +710,7 @@ inv_fista_fwd_kernel(PlaneDims d, const float2* __restrict__ Gh,
     const float2 gn = make_float2(fmaf(beta, xn.x - xp.x, xn.x), fmaf(beta, xn.y - xp.y, xn.y));
     xk[off + e] = xn;
     gam[off + e] = gn;
-    l1 += (double)(mag > thr ? mag - thr : 0.0f);
+    if (red_l1) l1 += (double)(mag > thr ? mag - thr : 0.0f);
     buf[b] = gn;
   }
   if (red_l1) block_add_double<F::NT>(l1, red_l1);
