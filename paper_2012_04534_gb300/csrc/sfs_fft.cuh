@@ -240,7 +240,9 @@ struct PlaneFFT {
                                           : (P >= 512 ? 256 : (P >= 128 ? 128 : 64)));
   static constexpr int ELEMS = QUAD ? 64 * LD : (TWO_D ? P * LD : P);  // float2 slots of the plane
   static constexpr int NTW = QUAD ? P + 64 : P;                         // twiddles (W_P, then W_64)
-  static constexpr int SMEM = (ELEMS + NTW) * 8;                        // plane + twiddles
+  // plane + twiddles; QUAD planes also hold a second 64 x 68 buffer after
+  // the twiddles (aux), for the half-transformed quadrants
+  static constexpr int SMEM = (ELEMS + NTW + (QUAD ? ELEMS : 0)) * 8;
   // resident CTAs per SM the plane kernels are compiled for: two 64 x 64
   // (or quadrant) planes per SM (at most 64 registers a thread) so that
   // batched calls, which launch many planes per scene, keep two planes in
@@ -255,78 +257,158 @@ struct PlaneFFT {
   // QUAD forward: the spatial plane in buf (natural layout, zero outside the
   // support) -> for q = 0..3 (py = q >> 1, px = q & 1) the quadrant's
   // spectrum S_q[kx'][ky'] at buf[qidx(kx' 64 + ky')], then store(q).  buf
-  // is overwritten; store(q) must only read it.
+  // and the aux buffer (tw + NTW) are overwritten; store(q) must only read
+  // buf.  The pre-twiddle W^(py y + px x) splits into W^(py y), applied
+  // before the transform along y, and W^(px x), which commutes with it and
+  // is applied before the transform along x; so the two quadrants of one py
+  // share their pass along y: 6 lane-group passes per plane instead of 8.
   template <typename Store>
   __device__ static __forceinline__ void forward_quads(float2* buf, const float2* tw, Store&& store) {
     static_assert(QUAD, "quadrant engine");
     const float2* tw64 = tw + P;
+    float2* aux = const_cast<float2*>(tw) + NTW;
     const int lane = threadIdx.x & 31, l = lane >> 2;
     const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
     float2 s[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) s[j] = buf[(l + 8 * j) * LD + c];  // (y = l + 8 j, x = c)
 #pragma unroll 1
-    for (int q = 0; q < 4; ++q) {
-      const int py = q >> 1, px = q & 1;
+    for (int py = 0; py < 2; ++py) {
       float2 v[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = q ? cmul(s[j], tw[py * (l + 8 * j) + px * c]) : s[j];
-      __syncthreads();  // the spatial reads, or the previous quadrant's store, are done
-      // along y for column x = c; written transposed: row x, column ky'
+      for (int j = 0; j < 8; ++j) v[j] = py ? cmul(s[j], tw[l + 8 * j]) : s[j];
+      // along y for column x = c; written transposed to aux: row x, column ky'
       fft64_lanes<false>(v, tw64, l);
+      // (the previous py's reads of aux came before the barriers of its last store)
 #pragma unroll
-      for (int k = 0; k < 8; ++k) buf[c * LD + l + 8 * k] = v[k];
+      for (int k = 0; k < 8; ++k) aux[c * LD + l + 8 * k] = v[k];
       __syncthreads();
-      // along x for column ky' = c: kx' = l + 8 k at row kx' (own column only)
+#pragma unroll 1
+      for (int px = 0; px < 2; ++px) {
+        // along x for column ky' = c (rows x = l + 8 j): kx' = l + 8 k at row kx'
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
-      fft64_lanes<false>(v, tw64, l);
+        for (int j = 0; j < 8; ++j) {
+          const float2 t = aux[(l + 8 * j) * LD + c];
+          v[j] = px ? cmul(t, tw[l + 8 * j]) : t;
+        }
+        fft64_lanes<false>(v, tw64, l);
+        __syncthreads();  // the spatial reads, or the previous quadrant's store, are done
 #pragma unroll
-      for (int k = 0; k < 8; ++k) buf[(l + 8 * k) * LD + c] = v[k];
-      __syncthreads();
-      store(q);
+        for (int k = 0; k < 8; ++k) buf[(l + 8 * k) * LD + c] = v[k];
+        __syncthreads();
+        store(2 * py + px);
+      }
     }
   }
 
   // QUAD inverse: for q = 0..3, load(q) fills buf[qidx(kx' 64 + ky')] with
   // S_q (every local position); the cropped 64 x 64 result is left in buf in
-  // the natural layout.
+  // the natural layout (aux is overwritten).  The post-twiddle
+  // W^-(py y + px x) splits as in forward_quads: the two quadrants of one py
+  // are transformed along kx', twiddled by W^-(px x) and added in aux, and
+  // share one pass along ky' (6 lane-group passes per plane instead of 8).
   template <typename Load>
   __device__ static __forceinline__ void inverse_quads(float2* buf, const float2* tw, Load&& load) {
     static_assert(QUAD, "quadrant engine");
     const float2* tw64 = tw + P;
+    float2* aux = const_cast<float2*>(tw) + NTW;
     const int lane = threadIdx.x & 31, l = lane >> 2;
     const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
     float2 acc[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.f, 0.f);
 #pragma unroll 1
-    for (int q = 0; q < 4; ++q) {
-      const int py = q >> 1, px = q & 1;
-      __syncthreads();  // earlier readers of buf are done
-      load(q);
-      __syncthreads();
+    for (int py = 0; py < 2; ++py) {
       float2 v[8];
-      // along kx' for column ky' = c; written transposed: row ky', column x
+#pragma unroll 1
+      for (int px = 0; px < 2; ++px) {
+        __syncthreads();  // earlier readers of buf (and, for px = 0, of aux) are done
+        load(2 * py + px);
+        __syncthreads();
+        // along kx' for column ky' = c: x = l + 8 k, added transposed into aux
+        // (row ky' = c, column x: slots this thread alone writes)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
-      __syncthreads();
-      fft64_lanes<true>(v, tw64, l);
+        for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
+        fft64_lanes<true>(v, tw64, l);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) buf[c * LD + l + 8 * k] = v[k];
-      __syncthreads();
+        for (int k = 0; k < 8; ++k) {
+          float2* a = aux + c * LD + l + 8 * k;
+          *a = px ? cadd(*a, cmulc(tw[l + 8 * k], v[k])) : v[k];
+        }
+      }
+      __syncthreads();  // aux holds both quadrants of this py
       // along ky' for column x = c: y = l + 8 k
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
+      for (int j = 0; j < 8; ++j) v[j] = aux[(l + 8 * j) * LD + c];
       fft64_lanes<true>(v, tw64, l);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) acc[k] = q ? cadd(acc[k], cmulc(tw[py * (l + 8 * k) + px * c], v[k])) : v[k];
+      for (int k = 0; k < 8; ++k) acc[k] = py ? cadd(acc[k], cmulc(tw[l + 8 * k], v[k])) : v[k];
     }
-    __syncthreads();
+    // the last reads of buf came before the barrier above
 #pragma unroll
     for (int k = 0; k < 8; ++k) buf[(l + 8 * k) * LD + c] = acc[k];
     __syncthreads();
   }
+  // QUAD, one quadrant q (the cluster kernels, one CTA per quadrant):
+  // load(q) fills buf[qidx(kx' 64 + ky')] with S_q; on return this thread's
+  //   acc[k] = W^-(py y + px x) IFFT64x64(S_q)[y = l + 8 k][x = c],
+  // its share of the cropped inverse.  The thread group of column c last
+  // touched buf at rows l + 8 k of column c, so acc may be written back there
+  // without a barrier.
+  template <typename Load>
+  __device__ static __forceinline__ void inverse_quad(float2* buf, const float2* tw, int q, float2 acc[8],
+                                                      Load&& load) {
+    static_assert(QUAD, "quadrant engine");
+    const float2* tw64 = tw + P;
+    const int lane = threadIdx.x & 31, l = lane >> 2;
+    const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
+    const int py = q >> 1, px = q & 1;
+    load(q);
+    __syncthreads();
+    float2 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
+    __syncthreads();
+    fft64_lanes<true>(v, tw64, l);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) buf[c * LD + l + 8 * k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
+    fft64_lanes<true>(v, tw64, l);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = q ? cmulc(tw[py * (l + 8 * k) + px * c], v[k]) : v[k];
+  }
+
+  // QUAD, one quadrant q: s[j] = spatial value (y = l + 8 j, x = c), zero
+  // outside the support -> S_q at buf[qidx(kx' 64 + ky')].  No thread of the
+  // CTA may still read buf when this is called.
+  __device__ static __forceinline__ void forward_quad(float2* buf, const float2* tw, int q, const float2 s[8]) {
+    static_assert(QUAD, "quadrant engine");
+    const float2* tw64 = tw + P;
+    const int lane = threadIdx.x & 31, l = lane >> 2;
+    const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
+    const int py = q >> 1, px = q & 1;
+    float2 v[8];
+    // the twiddle in two factors, as forward_quads applies it, so that both
+    // produce the same spectra bit for bit
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = py ? cmul(s[j], tw[l + 8 * j]) : s[j];
+    fft64_lanes<false>(v, tw64, l);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) buf[c * LD + l + 8 * k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float2 t = buf[(l + 8 * j) * LD + c];
+      v[j] = px ? cmul(t, tw[l + 8 * j]) : t;
+    }
+    fft64_lanes<false>(v, tw64, l);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) buf[(l + 8 * k) * LD + c] = v[k];
+    __syncthreads();
+  }
+
   // wavenumber kappa (transposed order, kappa = kx*P + ky) of the plane
   __device__ static __forceinline__ int kidx(int kappa) {
     return TWO_D ? (kappa / P) * LD + (kappa % P) : kappa;

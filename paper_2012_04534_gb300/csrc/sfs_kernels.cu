@@ -722,6 +722,236 @@ inv_fista_fwd_kernel(PlaneDims d, const float2* __restrict__ Gh,
 }
 
 // ---------------------------------------------------------------------------
+// Cluster plane kernels (QUAD planes, P = 128): one cluster of four CTAs per
+// plane instead of one CTA.  CTA rank q = 2 py + px of the cluster owns
+// quadrant q of the spectrum and rows 16 q .. 16 q + 15 of the 64 x 64
+// spatial plane:
+//   1. inverse of quadrant q, twiddled: CTA q's share of the cropped inverse
+//      (PlaneFFT::inverse_quad), left in its own plane buffer;
+//   2. cluster barrier; each CTA adds the four shares of its 16 rows, reading
+//      the other CTAs' buffers through distributed shared memory, and applies
+//      the row-local step (residual, or FISTA update);
+//   3. cluster barrier; each CTA reads the 64 rows of the new spatial plane
+//      from the four CTAs' row buffers and runs the forward transform of its
+//      own quadrant (PlaneFFT::forward_quad), then stores its slots.
+// The forward transform is the one-CTA engine's arithmetic bit for bit (a
+// FISTA call resumed from its state, whose first spectra come from
+// fwd_planes_kernel, continues an uninterrupted call exactly).  The inverse
+// adds the four twiddled quadrant shares in the order 0 + 1 + 2 + 3, where
+// the one-CTA engine adds the two quadrants of each py before its pass along
+// ky': the two agree to FP32 rounding.  A CTA leaves only after the
+// last cluster barrier, so no CTA reads the shared memory of one that has
+// exited.  Every CTA of a cluster passes the same barriers (the branches
+// around them depend on kernel arguments only).
+// ---------------------------------------------------------------------------
+constexpr int kQuadCl = 4;                 // CTAs per plane (one per quadrant)
+constexpr int kQuadRows = 64 / kQuadCl;    // spatial rows per CTA
+
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ int cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return (int)r;
+}
+// generic address of the same shared-memory location in CTA `rank` of the cluster
+template <typename T>
+__device__ __forceinline__ T* cluster_map(T* p, int rank) {
+  uint64_t out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"((uint64_t)p), "r"(rank));
+  return reinterpret_cast<T*>(out);
+}
+
+// Shared memory of a cluster plane CTA: plane buffer, twiddles, the 16 x 64
+// row buffer, and the per-CTA maxima of the FP16 modes.
+template <int P, bool TWO_D>
+__host__ __device__ constexpr int quad_cl_smem() {
+  return (PlaneFFT<P, TWO_D>::ELEMS + PlaneFFT<P, TWO_D>::NTW + kQuadRows * 64) * 8 + 8 * 4;
+}
+
+// After step 1: the four shares of row y, column x, added in quadrant order.
+template <int LD>
+__device__ __forceinline__ float2 sum_shares(float2* const sh[kQuadCl], int y, int x) {
+  const int o = y * LD + x;
+  float2 g = sh[0][o];
+#pragma unroll
+  for (int r = 1; r < kQuadCl; ++r) g = cadd(g, sh[r][o]);
+  return g;
+}
+
+// Step 3 of the cluster kernels: the spatial column of this thread from the
+// row buffers of the cluster, the forward transform of quadrant q and the
+// store of its slots (rank 0 also zeroes the padding slots); with pm, the
+// plane's largest |Re| or |Im| at *pm.
+template <int P, bool TWO_D>
+__device__ __forceinline__ void quad_cl_forward_store(float2* buf, const float2* tw, float2* xg, float* mxs,
+                                                      int q, float2* __restrict__ dst, const PlaneDims& d,
+                                                      float* pm) {
+  using F = PlaneFFT<P, TWO_D>;
+  const int lane = threadIdx.x & 31, l = lane >> 2;
+  const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
+  float2 s[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int y = l + 8 * j;
+    s[j] = cluster_map(xg, y / kQuadRows)[(y % kQuadRows) * 64 + c];
+  }
+  cluster_arrive();  // this CTA's reads of the row buffers are done
+  F::forward_quad(buf, tw, q, s);
+  float mx = 0.0f;
+  store_quadrant<P, TWO_D>(buf, dst, d, q, mx);
+  if (q == 0) store_quadrant<P, TWO_D>(buf, dst, d, 4, mx);
+  cluster_wait();
+  if (pm) {  // the cluster's maximum, gathered in rank 0's shared memory
+    block_max_store<F::NT>(mx, mxs + 4);
+    if (threadIdx.x == 0) *cluster_map(mxs + q, 0) = mxs[4];
+    cluster_arrive();
+    cluster_wait();
+    if (q == 0 && threadIdx.x == 0) *pm = fmaxf(fmaxf(mxs[0], mxs[1]), fmaxf(mxs[2], mxs[3]));
+  }
+}
+
+// inv_resid_fwd_kernel on a cluster of four CTAs per bin plane.
+template <int P, bool TWO_D>
+__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT, 2)
+inv_resid_fwd_cl_kernel(PlaneDims d, const float2* __restrict__ Yh, const int32_t* __restrict__ posmap,
+                        const float2* __restrict__ yplane, float2* __restrict__ Rh,
+                        double* __restrict__ red_sumsq) {
+  using F = PlaneFFT<P, TWO_D>;
+  static_assert(F::QUAD, "cluster plane kernels run quadrant planes");
+  {  // scene blockIdx.y of a batched launch
+    const long long b = blockIdx.y;
+    Yh += b * d.bs_yh;
+    yplane += b * d.bs_yplane;
+    Rh += b * d.bs_rh;
+    if (red_sumsq) red_sumsq += b * d.bs_red;
+  }
+  extern __shared__ float2 smem[];
+  float2* buf = smem;
+  float2* tw = smem + F::ELEMS;
+  float2* xg = tw + F::NTW;
+  float* mxs = reinterpret_cast<float*>(xg + kQuadRows * 64);
+  const int q = cluster_rank();
+  const int u = blockIdx.x / kQuadCl;
+  const int lane = threadIdx.x & 31, l = lane >> 2;
+  const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
+  plane_twiddles<P, TWO_D>(tw);
+  pdl_wait();
+  pdl_trigger();
+  float2 acc[8];
+  F::inverse_quad(buf, tw, q, acc, [&](int qq) { load_quadrant_fwd<P, TWO_D>(buf, Yh, u, d, qq); });
+#pragma unroll
+  for (int k = 0; k < 8; ++k) buf[(l + 8 * k) * F::LD + c] = acc[k];
+  cluster_arrive();
+  cluster_wait();  // every share is in its CTA's buffer
+  float2* sh[kQuadCl];
+#pragma unroll
+  for (int r = 0; r < kQuadCl; ++r) sh[r] = cluster_map(buf, r);
+  const int32_t* pmap = posmap + (size_t)u * d.S;
+  const float2* yu = yplane + (size_t)u * d.S;
+  double accs = 0.0;
+#pragma unroll
+  for (int i = 0; i < kQuadRows * 64 / F::NT; ++i) {
+    const int e = threadIdx.x + i * F::NT;
+    const int y = q * kQuadRows + (e >> 6), x = e & 63;
+    const float2 g = sum_shares<F::LD>(sh, y, x);
+    float2 r = make_float2(0.f, 0.f);
+    if (y < d.Ny && x < d.Nx) {
+      const int s = y * d.Nx + x;
+      const int m = pmap[s];
+      if (m >= 0) {
+        r = csub(g, yu[s]);
+        if (red_sumsq) accs += (double)r.x * r.x + (double)r.y * r.y;
+      }
+    }
+    xg[e] = r;
+  }
+  if (red_sumsq) block_add_double<F::NT>(accs, red_sumsq);
+  cluster_arrive();
+  cluster_wait();  // the row buffers are complete; the shares have been read
+  quad_cl_forward_store<P, TWO_D>(buf, tw, xg, mxs, q, Rh + (size_t)u * d.Ns, d,
+                                  d.pm_r ? d.pm_r + blockIdx.y * d.bs_pmr + u : nullptr);
+}
+
+// inv_fista_fwd_kernel on a cluster of four CTAs per depth plane.
+template <int P, bool TWO_D>
+__global__ void __launch_bounds__(PlaneFFT<P, TWO_D>::NT, 2)
+inv_fista_fwd_cl_kernel(PlaneDims d, const float2* __restrict__ Gh, const int2* __restrict__ segslot,
+                        float2* __restrict__ xk, float2* __restrict__ gam, const float* __restrict__ scal,
+                        float beta_arg, const float* __restrict__ beta_dev, int do_fwd,
+                        float2* __restrict__ Xh, double* __restrict__ red_l1) {
+  using F = PlaneFFT<P, TWO_D>;
+  static_assert(F::QUAD, "cluster plane kernels run quadrant planes");
+  {  // scene blockIdx.y of a batched launch
+    const long long b = blockIdx.y;
+    Gh += b * d.bs_gh;
+    xk += b * d.bs_x;
+    gam += b * d.bs_x;
+    scal += b * d.bs_scal;
+    Xh += b * d.bs_xh;
+    if (red_l1) red_l1 += b * d.bs_red;
+  }
+  extern __shared__ float2 smem[];
+  float2* buf = smem;
+  float2* tw = smem + F::ELEMS;
+  float2* xg = tw + F::NTW;
+  float* mxs = reinterpret_cast<float*>(xg + kQuadRows * 64);
+  const int q = cluster_rank();
+  const int z = blockIdx.x / kQuadCl;
+  const int lane = threadIdx.x & 31, l = lane >> 2;
+  const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
+  plane_twiddles<P, TWO_D>(tw);
+  pdl_wait();
+  pdl_trigger();
+  float2 acc[8];
+  F::inverse_quad(buf, tw, q, acc,
+                  [&](int qq) { load_quadrant_adj<P, TWO_D>(buf, Gh, segslot, z, d, qq); });
+#pragma unroll
+  for (int k = 0; k < 8; ++k) buf[(l + 8 * k) * F::LD + c] = acc[k];
+  cluster_arrive();
+  cluster_wait();  // every share is in its CTA's buffer
+  float2* sh[kQuadCl];
+#pragma unroll
+  for (int r = 0; r < kQuadCl; ++r) sh[r] = cluster_map(buf, r);
+  const float thr = scal[kThr];
+  const float invL = scal[kInvL];
+  const float beta = beta_dev ? *beta_dev : beta_arg;
+  const size_t off = (size_t)z * d.Ny * d.Nx;
+  double l1 = 0.0;
+#pragma unroll
+  for (int i = 0; i < kQuadRows * 64 / F::NT; ++i) {
+    const int e = threadIdx.x + i * F::NT;
+    const int y = q * kQuadRows + (e >> 6), x = e & 63;
+    const float2 g = sum_shares<F::LD>(sh, y, x);
+    float2 gn = make_float2(0.f, 0.f);
+    if (y < d.Ny && x < d.Nx) {
+      const size_t v = off + (size_t)y * d.Nx + x;
+      const float2 gm = gam[v];
+      const float2 xp = xk[v];
+      const float2 w = make_float2(fmaf(-g.x, invL, gm.x), fmaf(-g.y, invL, gm.y));
+      const float mag = hypotf(w.x, w.y);
+      const float sc = mag > thr ? 1.0f - thr / mag : 0.0f;
+      const float2 xn = make_float2(w.x * sc, w.y * sc);
+      gn = make_float2(fmaf(beta, xn.x - xp.x, xn.x), fmaf(beta, xn.y - xp.y, xn.y));
+      xk[v] = xn;
+      gam[v] = gn;
+      if (red_l1) l1 += (double)(mag > thr ? mag - thr : 0.0f);
+    }
+    xg[e] = gn;
+  }
+  if (red_l1) block_add_double<F::NT>(l1, red_l1);
+  cluster_arrive();
+  cluster_wait();  // the row buffers are complete; the shares have been read
+  if (!do_fwd) return;  // kernel argument: the whole cluster leaves here
+  quad_cl_forward_store<P, TWO_D>(buf, tw, xg, mxs, q, Xh + (size_t)z * d.Ns, d,
+                                  d.pm_x ? d.pm_x + blockIdx.y * d.bs_pmx + z : nullptr);
+}
+
+// ---------------------------------------------------------------------------
 // Depth contractions (the blockwise products of Sec. IV-B restricted to the
 // kept bins).
 //
@@ -1317,6 +1547,35 @@ int launch_plane(K kernel, int nplanes, int d_batch, cudaStream_t st, Args... ar
   return launch_pdl(kernel, dim3(nplanes, std::max(1, d_batch)), dim3(F::NT), F::SMEM, st, args...);
 }
 
+// The cluster version of a plane kernel: kQuadCl CTAs per plane.
+template <int P, bool TWO_D, typename K, typename... Args>
+int launch_plane_cl(K kernel, int nplanes, int d_batch, cudaStream_t st, Args... args) {
+  using F = PlaneFFT<P, TWO_D>;
+  if (nplanes <= 0) return SFS_OK;
+  constexpr int smem = quad_cl_smem<P, TWO_D>();
+  SFS_TRY(ensure_smem_attr(kernel, smem));
+  return launch_pdl_cluster(kernel, kQuadCl, dim3(nplanes * kQuadCl, std::max(1, d_batch)), dim3(F::NT),
+                            smem, st, args...);
+}
+
+// Whether n quadrant planes (planes x scenes of one launch) run as clusters.
+// One-CTA planes (two per SM) take about three times as long as a cluster's
+// CTA (one quadrant each); the cluster form pays off while its 4 n CTAs fill
+// at most three waves of two per SM, i.e. 2 n <= 3 SMs.  Measured on GB300,
+// vol64 (152 SMs): 163 bin planes 57.5 -> 53.3 us as clusters, 256 depth
+// planes 60.3 -> 73.1 us (four waves), so those stay one CTA per plane.
+bool plane_clusters(long long n) {
+  static int sms[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  if (sms[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return false;
+    sms[dev] = v;
+  }
+  return 2 * n <= 3LL * sms[dev];
+}
+
 // Calls fn.template operator()<P, TWO_D>() for the plane shape of d.
 template <typename Fn>
 int dispatch_plane(const PlaneDims& d, Fn&& fn) {
@@ -1410,6 +1669,11 @@ int launch_inv_resid_fwd(const PlaneDims& d, const float2* Yh, const int32_t* po
                          const float2* yplane, float2* Rh, double* red_sumsq,
                          cudaStream_t st) {
   return dispatch_plane(d, [&]<int P, bool TD>() {
+    if constexpr (PlaneFFT<P, TD>::QUAD) {
+      if (plane_clusters((long long)d.U * std::max(1, d.batch)))
+        return launch_plane_cl<P, TD>(inv_resid_fwd_cl_kernel<P, TD>, d.U, d.batch, st, d, Yh, posmap,
+                                      yplane, Rh, red_sumsq);
+    }
     return launch_plane<P, TD>(inv_resid_fwd_kernel<P, TD>, d.U, d.batch, st, d, Yh, posmap, yplane,
                                Rh, red_sumsq);
   });
@@ -1434,6 +1698,11 @@ int launch_inv_fista_fwd(const PlaneDims& d, const float2* Gh, const int2* segsl
                          float2* gam, const float* scal, float beta, int do_fwd, float2* Xh,
                          double* red_l1, cudaStream_t st, const float* beta_dev) {
   return dispatch_plane(d, [&]<int P, bool TD>() {
+    if constexpr (PlaneFFT<P, TD>::QUAD) {
+      if (plane_clusters((long long)d.Nz * std::max(1, d.batch)))
+        return launch_plane_cl<P, TD>(inv_fista_fwd_cl_kernel<P, TD>, d.Nz, d.batch, st, d, Gh, segslot,
+                                      xk, gam, scal, beta, beta_dev, do_fwd, Xh, red_l1);
+    }
     return launch_plane<P, TD>(inv_fista_fwd_kernel<P, TD>, d.Nz, d.batch, st, d, Gh, segslot, xk, gam,
                                scal, beta, beta_dev, do_fwd, Xh, red_l1);
   });

@@ -249,3 +249,47 @@ def test_grouped_completion_times(sfs):
     assert len(t) == 2 and all(0 < v <= total * 1.01 + 0.05 for v in t)
     with pytest.raises(sfs.SfsError):
         sfs.grouped_times(3)
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp16"])
+def test_quadrant_planes_as_clusters_and_one_cta_agree(sfs, mode):
+    """128 x 128 planes run as one cluster of four CTAs per plane while the
+    launch holds few planes (2 n <= 3 SMs), one CTA per plane otherwise.  A
+    batch large enough for the one-CTA kernels and single-scene solves (the
+    cluster kernels) must give the same FISTA iterates to FP32 rounding
+    (FP32: also the oracle's); FP16 also exercises the per-plane maxima gathered across the
+    cluster."""
+    import torch
+    params = geom_params(Nx=40, Ny=36, Nz=10, dz=0.15e-3, Nt=256)
+    go = oracle_geometry(params)
+    g = sfs.Geometry(**params)
+    idx = O.select_indices(go, O.SEL_RANDOM, 10, True, 61)
+    op = sfs.Operator.from_indices(g, idx, precision=sfs.PRECISION_NAMES[mode])
+    assert op.info["Px"] == 128
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    U = op.info["U"]
+    B = (3 * sms) // (2 * min(U, g.Nz)) + 1          # past the cluster rule for both plane kernels
+    assert 2 * B * g.Nz > 3 * sms and 2 * B * U > 3 * sms
+    ref = O.LateralFFTOperator(go, idx)
+    ys = []
+    for b in range(B):
+        x_true = synth.scene(op.shape_x, 3, "uniform", seed=300 + b)
+        y0 = ref.apply_A(x_true) if b < 2 else None
+        if y0 is None:
+            ys.append(crandn(np.random.default_rng(400 + b), g.S, op.M) * 0.1)
+            continue
+        sig = synth.noise_scale(float(np.vdot(y0, y0).real), y0.size, 20.0)
+        ys.append((y0 + sig * synth.unit_noise(y0.shape, seed=500 + b)).astype(np.complex64).astype(complex))
+    Y = np.stack(ys)
+    L, _ = op.lipschitz(max_iter=300, rtol=1e-6, seed=2, safety=1e-3)
+    xb = to_host(op.fista_batched(to_dev(Y), -0.05, L, 60))
+    for b in (0, 1, B - 1):
+        xs = to_host(op.fista(to_dev(Y[b]), -0.05, L, 60))
+        # the one-CTA engine applies the quadrant twiddles as two factors, the
+        # cluster CTAs as one: FP32 roundings apart, carried through 60 steps
+        assert rel_err(xb[b], xs) <= 1e-5
+    if mode == "fp32":
+        lam = O.lambda_from_mu(ref.apply_AH, Y[0], 0.05)
+        x_ref = O.fista(ref.apply_A, ref.apply_AH, Y[0], lam, L, 60)
+        assert np.abs(x_ref).max() > 0
+        assert rel_err(xb[0], x_ref) <= 1e-4
