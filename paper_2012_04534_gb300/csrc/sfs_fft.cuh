@@ -231,12 +231,13 @@ template <int P, bool TWO_D, bool ALLOW_QUAD = true>
 struct PlaneFFT {
   // 64 x 64 planes use the lane-group engine (512 threads = 64 columns x 8);
   // full 128 x 128 planes (one CTA per SM: the plane takes 129 KB) run 1024
-  // threads, quadrant planes 512
+  // threads, quadrant planes 512, and 32 x 32 planes 512 as well, so that
+  // every plane the operator transforms at run time takes a 512-thread CTA
   static constexpr bool QUAD = ALLOW_QUAD && TWO_D && P == 128;
   static constexpr bool LANES64 = TWO_D && P == 64;
   static constexpr int LD = QUAD ? 68 : (TWO_D ? (LANES64 ? P + 4 : P + 1) : P);
   static constexpr int NT = QUAD ? 512
-                                 : (TWO_D ? (P >= 128 ? 1024 : (P >= 64 ? 512 : 256))
+                                 : (TWO_D ? (P >= 128 ? 1024 : 512)
                                           : (P >= 512 ? 256 : (P >= 128 ? 128 : 64)));
   static constexpr int ELEMS = QUAD ? 64 * LD : (TWO_D ? P * LD : P);  // float2 slots of the plane
   static constexpr int NTW = QUAD ? P + 64 : P;                         // twiddles (W_P, then W_64)
