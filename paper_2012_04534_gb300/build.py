@@ -19,7 +19,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["sfs_kernels.cu", "sfs_tc.cu", "sfs_tc16.cu", "sfs_api.cu", "sfs_noalloc.cu", "sfs_lista.cu",
            "sfs_crb.cu", "sfs_mix.cu",
-           "sfs_backtrack.cu", "sfs_shard.cu"]
+           "sfs_backtrack.cu", "sfs_shard.cu", "sfs_persist.cu"]
 HEADERS = ["sfs_internal.h", "sfs_fft.cuh", "sfs_planes.cuh", "sfs_tc16_dev.cuh", "sfs_async.cuh", "sfs_launch.h", "sfs_tcgen05.cuh"]
 
 

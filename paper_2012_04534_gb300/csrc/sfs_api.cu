@@ -650,6 +650,7 @@ struct GroupedEntry {
   std::vector<uint64_t> key;
   cudaGraphExec_t exec;
   int device;
+  PersistPlan* plan;  // persistent solves: the kernel's plan (owned), else null
 };
 std::mutex g_grouped_mu;
 std::vector<GroupedEntry> g_grouped;
@@ -661,6 +662,16 @@ cudaStream_t g_grouped_capture = nullptr;
 std::vector<cudaEvent_t> g_done_events;
 cudaEvent_t g_grouped_start = nullptr;
 int g_grouped_last_n = 0;
+
+// Adds an entry to the cache (g_grouped_mu held), evicting the oldest.
+void cache_grouped(const GroupedEntry& ent) {
+  if (g_grouped.size() >= kGroupedCache) {
+    cudaGraphExecDestroy(g_grouped.front().exec);
+    persist_free(g_grouped.front().plan);
+    g_grouped.erase(g_grouped.begin());
+  }
+  g_grouped.push_back(ent);
+}
 
 int grouped_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch, int iters,
                   cudaGraphExec_t* out) {
@@ -749,11 +760,65 @@ int grouped_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch, i
   e = cudaGraphInstantiateWithFlags(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
-  if (g_grouped.size() >= kGroupedCache) {
-    cudaGraphExecDestroy(g_grouped.front().exec);
-    g_grouped.erase(g_grouped.begin());
+  cache_grouped({key, exec, dev, nullptr});
+  *out = exec;
+  return SFS_OK;
+}
+
+// The persistent solve's graph: per group the measurements by plane and X^ of
+// gamma_1 (plain launches), then the one cooperative kernel of all
+// iterations.  Cached with the grouped graphs (its key starts with a tag).
+int persistent_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch, int iters,
+                     cudaGraphExec_t* out) {
+  std::vector<uint64_t> key = {(uint64_t)iters, (uint64_t)ngroups | (1ull << 40)};
+  for (int g = 0; g < ngroups; ++g) {
+    key.push_back(ops[g]->uid);
+    key.push_back(ops[g]->bws_gen);
+    key.push_back((uint64_t)batch[g]);
   }
-  g_grouped.push_back({key, exec, dev});
+  int dev = 0;
+  SFS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_grouped_mu);
+  for (auto& e : g_grouped)
+    if (e.key == key && e.device == dev) {
+      *out = e.exec;
+      return SFS_OK;
+    }
+  if (!g_grouped_capture) SFS_CUDA(cudaStreamCreateWithFlags(&g_grouped_capture, cudaStreamNonBlocking));
+  std::vector<PlaneDims> dims(ngroups);
+  for (int g = 0; g < ngroups; ++g) {
+    dims[g] = batch_dims(ops[g], batch[g]);
+    SFS_TRY(prepare_kernels(dims[g]));
+  }
+  PersistPlan* plan = nullptr;
+  SFS_TRY(persist_build(ngroups, ops, dims.data(), iters, &plan));
+  cudaStream_t cs = g_grouped_capture;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    persist_free(plan);
+    return cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+  }
+  int rc = SFS_OK;
+  for (int g = 0; g < ngroups && rc == SFS_OK; ++g) {
+    const sfs::BatchWorkspace& w = ops[g]->bws;
+    rc = launch_scatter_y_planes(dims[g], w.ybuf, ops[g]->posmap, w.yplane, cs);
+    if (rc == SFS_OK) rc = launch_fwd_planes(dims[g], w.gam, w.Xh, cs);
+  }
+  if (rc == SFS_OK) rc = persist_launch(plan, cs);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cs, &graph);
+  if (rc == SFS_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+  cudaGraphExec_t exec = nullptr;
+  if (rc == SFS_OK) {
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (rc != SFS_OK) {
+    persist_free(plan);
+    return rc;
+  }
+  cache_grouped({key, exec, dev, plan});
   *out = exec;
   return SFS_OK;
 }
@@ -1712,10 +1777,13 @@ int sfs_fista_batched(sfs_operator* op, int batch, const void* y_dev, double lam
   return SFS_OK;
 }
 
-int sfs_fista_grouped(int ngroups, sfs_operator* const* ops, const int32_t* batch,
-                      const void* const* y_dev, const double* L, double lambda, int iters,
-                      void* const* x_out_dev, void* stream) {
-  clear_error();
+namespace {
+
+// Checks the groups of a grouped or persistent solve and prepares each
+// group's workspace: measurements, zero state, thresholds (mu rule per
+// scene).
+int grouped_setup(int ngroups, sfs_operator* const* ops, const int32_t* batch, const void* const* y_dev,
+                  const double* L, double lambda, int iters, void* const* x_out_dev, cudaStream_t st) {
   if (ngroups < 1 || ngroups > SFS_MAX_GROUPS || !ops || !batch || !y_dev || !L || !x_out_dev ||
       iters < 0 || !isfinite(lambda)) {
     set_error("invalid argument (1..%d groups)", SFS_MAX_GROUPS);
@@ -1734,15 +1802,12 @@ int sfs_fista_grouped(int ngroups, sfs_operator* const* ops, const int32_t* batc
         return SFS_ERR_INVALID_ARG;
       }
   }
-  DeviceScope scope(ops[0]->geo.d.device);
-  cudaStream_t st = (cudaStream_t)stream;
-  // per group: workspace, measurements, zero state, thresholds (mu rule per scene)
   for (int g = 0; g < ngroups; ++g) SFS_TRY(ensure_batch(ops[g], batch[g]));
   {
     std::lock_guard<std::mutex> lock(g_grouped_mu);
     if (!g_grouped_start) SFS_CUDA(cudaEventCreate(&g_grouped_start));
     SFS_CUDA(cudaEventRecord(g_grouped_start, st));
-    g_grouped_last_n = iters > 0 ? ngroups : 0;
+    g_grouped_last_n = 0;
   }
   for (int g = 0; g < ngroups; ++g) {
     sfs_operator* op = ops[g];
@@ -1762,17 +1827,68 @@ int sfs_fista_grouped(int ngroups, sfs_operator* const* ops, const int32_t* batc
     SFS_TRY(launch_set_thresholds_batched(w.scal, batch[g], use_mu ? 0.0 : lambda, L[g], use_mu,
                                           use_mu ? -lambda : 0.0, op->ws.err, st));
   }
-  if (iters > 0) {
-    cudaGraphExec_t exec = nullptr;
-    SFS_TRY(grouped_graph(ngroups, ops, batch, iters, &exec));
-    SFS_CUDA(cudaGraphLaunch(exec, st));
-  }
+  return SFS_OK;
+}
+
+int grouped_results(int ngroups, sfs_operator* const* ops, const int32_t* batch, void* const* x_out_dev,
+                    cudaStream_t st) {
   for (int g = 0; g < ngroups; ++g) {
     const PlaneDims d = batch_dims(ops[g], batch[g]);
     SFS_CUDA(cudaMemcpyAsync(x_out_dev[g], ops[g]->bws.xk, (size_t)batch[g] * d.bs_x * sizeof(float2),
                              cudaMemcpyDeviceToDevice, st));
   }
   return SFS_OK;
+}
+
+}  // namespace
+
+int sfs_fista_grouped(int ngroups, sfs_operator* const* ops, const int32_t* batch,
+                      const void* const* y_dev, const double* L, double lambda, int iters,
+                      void* const* x_out_dev, void* stream) {
+  clear_error();
+  if (ngroups < 1 || !ops || !ops[0]) {
+    set_error("invalid argument (1..%d groups)", SFS_MAX_GROUPS);
+    return SFS_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(ops[0]->geo.d.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  SFS_TRY(grouped_setup(ngroups, ops, batch, y_dev, L, lambda, iters, x_out_dev, st));
+  if (iters > 0) {
+    cudaGraphExec_t exec = nullptr;
+    SFS_TRY(grouped_graph(ngroups, ops, batch, iters, &exec));
+    SFS_CUDA(cudaGraphLaunch(exec, st));
+    std::lock_guard<std::mutex> lock(g_grouped_mu);
+    g_grouped_last_n = ngroups;
+  }
+  return grouped_results(ngroups, ops, batch, x_out_dev, st);
+}
+
+int sfs_fista_persistent(int ngroups, sfs_operator* const* ops, const int32_t* batch,
+                         const void* const* y_dev, const double* L, double lambda, int iters,
+                         void* const* x_out_dev, void* stream) {
+  clear_error();
+  if (ngroups < 1 || ngroups > SFS_MAX_GROUPS || !ops) {
+    set_error("invalid argument (1..%d groups)", SFS_MAX_GROUPS);
+    return SFS_ERR_INVALID_ARG;
+  }
+  for (int g = 0; g < ngroups; ++g) {
+    const sfs_operator* op = ops[g];
+    if (!op || op->tc != 2 || op->nparts != 1 || op->geo.Py == 1 ||
+        (op->geo.Px != 32 && op->geo.Px != 64 && op->geo.Px != 128)) {
+      set_error("group %d: the persistent solve runs area-scan operators with a one-part 16-bit table "
+                "(SFS_PREC_BF16 or SFS_PREC_FP16)", g);
+      return SFS_ERR_INVALID_ARG;
+    }
+  }
+  DeviceScope scope(ops[0]->geo.d.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  SFS_TRY(grouped_setup(ngroups, ops, batch, y_dev, L, lambda, iters, x_out_dev, st));
+  if (iters > 0) {
+    cudaGraphExec_t exec = nullptr;
+    SFS_TRY(persistent_graph(ngroups, ops, batch, iters, &exec));
+    SFS_CUDA(cudaGraphLaunch(exec, st));
+  }
+  return grouped_results(ngroups, ops, batch, x_out_dev, st);
 }
 
 int sfs_grouped_times(int ngroups, float* ms_out_host) {

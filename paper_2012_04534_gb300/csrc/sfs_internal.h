@@ -1,6 +1,7 @@
 // Internal declarations of libsfs: operator state and the kernel launchers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -322,6 +323,29 @@ int launch_contract_fwd_h(const PlaneDims& d, const float2* Xh, float2* Yp, int*
 int launch_contract_adj_h(const PlaneDims& d, const float2* Rh, float2* Gs, int* err,
                           cudaStream_t st);
 int prepare_tc16_kernels(const PlaneDims& d);
+// Work units of one 16-bit contraction launch (forward: (orbit, tile of 128
+// bins), nch chunks of 32 depths; adjoint: (orbit, pair of 32-depth blocks),
+// nch chunks of 64 bins), the scenes a table tile serves, the table's tensor
+// maps and the map of a batch's spectra (scene tiles of box_scenes).
+void tc16_units(const PlaneDims& d, bool fwd, int* nmt, int* nch, int* nunits);
+int tc16_group_of(const PlaneDims& d);
+int tc16_table_maps(const sfs_operator* op, CUtensorMap* tab_f, CUtensorMap* tab_a);
+int tc16_encode_spec(CUtensorMap* m, const void* base, int rows, int Ns, int box_rows, int scenes,
+                     int box_scenes);
+
+// ---- the persistent FISTA loop over groups of scenes (sfs_persist.cu) ----
+// persist_build prepares the device plan of `iters` iterations of Algorithm 1
+// for the groups (ops[g], dims[g] = the batched dimensions of its scenes) on
+// the operators' batched workspaces: 16-bit single-part 2-D operators only.
+// persist_launch zeroes the grid barrier and launches the cooperative kernel
+// (capturable); the measurements by plane, the thresholds and X^ of gamma_1
+// must be in the workspaces first.
+struct PersistPlan;
+int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, int iters,
+                  PersistPlan** out);
+int persist_launch(const PersistPlan* pp, cudaStream_t st);
+void persist_free(PersistPlan* pp);
+void persist_shape(const PersistPlan* pp, int* grid, int* smem);
 
 // Batched building blocks (sfs_api.cu) used by the learned network
 // (sfs_lista.cu), on the operator's batched workspace:

@@ -1,0 +1,446 @@
+// The FISTA iteration loop of many scene groups (serving: scenes of different
+// scan grids, depths and bin counts) as one persistent kernel.
+//
+// Algorithm 1 for every scene of every group, iteration k:
+//   1. forward contraction of every group's spectra X^ of gamma_k (16-bit
+//      tensor-core table, Sec. IV-B / Algorithm 2);
+//   2. residual planes: inverse lateral FFT, A gamma_k - y at the kept
+//      positions, forward FFT of the residual;
+//   3. adjoint contraction of the residual spectra;
+//   4. update planes: inverse FFT of the gradient, soft threshold, momentum,
+//      forward FFT of gamma_{k+1}.
+// One cooperative launch of one 512-thread CTA per SM runs all iterations.
+// Each step's work of all groups is one list: contraction units (orbit, tile)
+// of every (group, scene tile), cut into equal contiguous shares per CTA, and
+// planes of every (group, scene), taken round robin.  The CTAs meet at a grid
+// barrier after each step (a global arrival counter, waited on with a time
+// limit: a CTA that gives up sets the error flag and the kernel ends).  The
+// contraction and plane steps are the code of the standalone kernels
+// (sfs_tc16_dev.cuh, sfs_planes.cuh), so a persistent solve computes what the
+// grouped one computes, up to the plane engine variant (the cluster plane
+// kernels of sfs_kernels.cu add the inverse quadrant shares in another
+// order).
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sfs_async.cuh"
+#include "sfs_internal.h"
+#include "sfs_launch.h"
+#include "sfs_planes.cuh"
+#include "sfs_tc16_dev.cuh"
+
+namespace sfs {
+namespace {
+
+constexpr int kPThreads = 512;  // the plane engines' CTA; warps 0-6 run the contraction roles
+
+// One group as the kernel reads it (device memory).
+struct PGroup {
+  PlaneDims d;  // batched dimensions: d.batch scenes, per-scene strides
+  float2 *Xh, *Yh, *Rh, *Gh, *xk, *gam;
+  const float2* yplane;
+  const float* scal;
+  const int32_t* posmap;
+  const int2* segslot;
+  int* err;
+  int NB;                       // scenes per table tile
+  int nmt_f, nch_f, nmt_a, nch_a;
+  int map0;                     // maps[map0], maps[map0 + 1]: table (fwd, adj); then per scene tile
+                                // j maps[map0 + 2 + 2 j] (X^), maps[map0 + 3 + 2 j] (R^)
+};
+
+struct PPlan {
+  int ngroups, njobs, iters;
+  const CUtensorMap* maps;
+  const int2* job;              // contraction job: {group, scene tile}
+  const long long* cum_f;       // [njobs + 1] cumulative forward units
+  const long long* cum_a;       // [njobs + 1] cumulative adjoint units
+  const long long* cum_r;       // [ngroups + 1] cumulative residual planes (scenes x bins)
+  const long long* cum_u;       // [ngroups + 1] cumulative update planes (scenes x depths)
+  const float* beta;            // [iters] momentum coefficients from t_1 = 1
+  unsigned int* arrivals;       // grid barrier counter, zero at launch
+  int* err;                     // set when a grid barrier wait gives up
+  uint64_t wait_ns;
+};
+
+// The kernel's parameter: the plan and the groups, read through the
+// constant cache (a __grid_constant__ parameter of at most 32 KB).
+struct PParams {
+  PPlan p;
+  PGroup groups[SFS_MAX_GROUPS];
+};
+static_assert(sizeof(PParams) <= 32000, "kernel parameter size");
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier number `epoch` (1, 2, ...): every CTA's writes before it are
+// visible to every CTA after it, to plain loads and to bulk / tensor copies,
+// and the shared memory a step leaves may be rewritten by the next step's
+// copies.  False (for the whole CTA) when the wait gave up.
+__device__ bool grid_sync(const PPlan& p, unsigned int epoch) {
+  __shared__ int ok;
+  fence_proxy_async_all();  // this step's accesses, either proxy, before the arrival
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(p.arrivals, 1u);
+    const unsigned int target = epoch * gridDim.x;
+    int good = 1;
+    if (ld_acquire(p.arrivals) < target) {
+      const uint64_t t0 = global_ns();
+      while (ld_acquire(p.arrivals) < target) {
+        if (global_ns() - t0 > p.wait_ns) {
+          atomicExch(p.err, 1);
+          good = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  fence_proxy_async_all();  // the next step's copies and MMAs after it
+  return ok != 0;
+}
+
+// Step 1 or 3: this CTA's share of the units of every contraction job.
+template <bool FWD>
+__device__ __forceinline__ void contract_step(const PParams& prm, unsigned char* smem) {
+  const PPlan& p = prm.p;
+  const long long* cum = FWD ? p.cum_f : p.cum_a;
+  const long long T = cum[p.njobs];
+  const long long u0 = T * blockIdx.x / gridDim.x, u1 = T * (blockIdx.x + 1) / gridDim.x;
+  for (int j = 0; j < p.njobs; ++j) {
+    const long long a = max(u0, cum[j]), e = min(u1, cum[j + 1]);
+    if (e <= a) continue;
+    const int2 jb = p.job[j];
+    const PGroup& g = prm.groups[jb.x];
+    const int s0 = jb.y * g.NB;
+    const int nscene = min(g.NB, g.d.batch - s0);
+    const CUtensorMap* tab = p.maps + g.map0 + (FWD ? 0 : 1);
+    const CUtensorMap* spec = p.maps + g.map0 + 2 + 2 * jb.y + (FWD ? 0 : 1);
+    float2* out = FWD ? g.Yh + s0 * g.d.bs_yh : g.Gh + s0 * g.d.bs_gh;
+    const long long ostride = FWD ? g.d.bs_yh : g.d.bs_gh;
+    const float* pm0 = FWD ? g.d.pm_x : g.d.pm_r;
+    const float* pm = pm0 ? pm0 + s0 * (FWD ? g.d.bs_pmx : g.d.bs_pmr) : nullptr;
+    const int nmt = FWD ? g.nmt_f : g.nmt_a, nch = FWD ? g.nch_f : g.nch_a;
+    const int first = (int)(a - cum[j]), nu = (int)(e - a);
+    if (g.NB == 1)
+      contract_h_run<FWD, 1, 1>(tab, spec, out, ostride, nscene, g.d, nmt, nch, first, nu, pm, g.err, smem,
+                                true);
+    else if (g.NB == 2)
+      contract_h_run<FWD, 1, 2>(tab, spec, out, ostride, nscene, g.d, nmt, nch, first, nu, pm, g.err, smem,
+                                true);
+    else
+      contract_h_run<FWD, 1, 4>(tab, spec, out, ostride, nscene, g.d, nmt, nch, first, nu, pm, g.err, smem,
+                                true);
+  }
+}
+
+// The group of plane task t (cum: cumulative plane counts per group).
+__device__ __forceinline__ int group_of_task(const long long* cum, int ngroups, long long t) {
+  int g = 0;
+  while (g + 1 < ngroups && cum[g + 1] <= t) ++g;
+  return g;
+}
+
+// The group's dimensions copied to shared memory for one plane task: the
+// plane steps then read them with shared-memory loads instead of holding
+// constant-bank copies in registers.  Called by every thread.
+__device__ __forceinline__ const PlaneDims& stage_dims(const PlaneDims& d) {
+  __shared__ __align__(16) PlaneDims sd;
+  static_assert(sizeof(PlaneDims) % 4 == 0, "word copy");
+  __syncthreads();  // earlier readers of sd are done
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&d);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&sd);
+  for (int i = threadIdx.x; i < (int)(sizeof(PlaneDims) / 4); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  return sd;
+}
+
+// The plane steps as separate functions, so that each keeps the register
+// allocation of its standalone kernel instead of sharing one with the rest
+// of the persistent kernel.
+template <int P>
+__device__ __noinline__ void resid_plane_call(const PlaneDims& d, int u, long long b, float2* smem,
+                                              const PGroup& g) {
+  resid_plane_step<P, true>(d, u, b, smem, g.Yh, g.posmap, g.yplane, g.Rh, nullptr);
+}
+template <int P>
+__device__ __noinline__ void update_plane_call(const PlaneDims& d, int z, long long b, float2* smem,
+                                               const PGroup& g, float beta, int do_fwd) {
+  update_plane_step<P, true>(d, z, b, smem, g.Gh, g.segslot, g.xk, g.gam, g.scal, beta, nullptr, do_fwd, g.Xh,
+                             nullptr);
+}
+
+// Step 2: residual planes of every (group, scene, bin), round robin.
+__device__ __forceinline__ void resid_step(const PParams& prm, float2* smem) {
+  const PPlan& p = prm.p;
+  const long long T = p.cum_r[p.ngroups];
+  for (long long t = blockIdx.x; t < T; t += gridDim.x) {
+    const int gi = group_of_task(p.cum_r, p.ngroups, t);
+    const PGroup& g = prm.groups[gi];
+    const PlaneDims& sd = stage_dims(g.d);
+    const long long r = t - p.cum_r[gi];
+    const long long b = r / sd.U;
+    const int u = (int)(r - b * sd.U);
+    if (sd.Px == 128)
+      resid_plane_call<128>(sd, u, b, smem, g);
+    else if (sd.Px == 64)
+      resid_plane_call<64>(sd, u, b, smem, g);
+    else
+      resid_plane_call<32>(sd, u, b, smem, g);
+    __syncthreads();  // the next plane reuses the shared memory
+  }
+}
+
+// Step 4: update planes of every (group, scene, depth), round robin.
+__device__ __forceinline__ void update_step(const PParams& prm, int k, float2* smem) {
+  const PPlan& p = prm.p;
+  const long long T = p.cum_u[p.ngroups];
+  const float beta = p.beta[k];
+  const int do_fwd = k + 1 < p.iters;
+  for (long long t = blockIdx.x; t < T; t += gridDim.x) {
+    const int gi = group_of_task(p.cum_u, p.ngroups, t);
+    const PGroup& g = prm.groups[gi];
+    const PlaneDims& sd = stage_dims(g.d);
+    const long long r = t - p.cum_u[gi];
+    const long long b = r / sd.Nz;
+    const int z = (int)(r - b * sd.Nz);
+    if (sd.Px == 128)
+      update_plane_call<128>(sd, z, b, smem, g, beta, do_fwd);
+    else if (sd.Px == 64)
+      update_plane_call<64>(sd, z, b, smem, g, beta, do_fwd);
+    else
+      update_plane_call<32>(sd, z, b, smem, g, beta, do_fwd);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kPThreads, 1) fista_persistent_kernel(const __grid_constant__ PParams prm) {
+  extern __shared__ __align__(1024) unsigned char psm[];
+  const PPlan& p = prm.p;
+  unsigned int epoch = 0;
+  for (int k = 0; k < p.iters; ++k) {
+    contract_step<true>(prm, psm);
+    if (!grid_sync(p, ++epoch)) return;
+    resid_step(prm, reinterpret_cast<float2*>(psm));
+    if (!grid_sync(p, ++epoch)) return;
+    contract_step<false>(prm, psm);
+    if (!grid_sync(p, ++epoch)) return;
+    update_step(prm, k, reinterpret_cast<float2*>(psm));
+    if (k + 1 < p.iters && !grid_sync(p, ++epoch)) return;
+  }
+}
+
+}  // namespace
+
+// Plan of one persistent solve: the kernel parameter (plan and groups) on
+// the host, and one device allocation holding the tensor maps, the job and
+// task tables, the momentum coefficients and the barrier counter.
+struct PersistPlan {
+  PParams prm;
+  void* blob = nullptr;
+  int grid = 0;
+  int smem = 0;
+};
+
+namespace {
+
+size_t align_up(size_t off, size_t a) { return (off + a - 1) / a * a; }
+
+int plan_smem(int NB, int P) {
+  const int c = NB == 1 ? HPlan<1, 1>::kSmem : NB == 2 ? HPlan<1, 2>::kSmem : HPlan<1, 4>::kSmem;
+  const int pl = P == 128 ? PlaneFFT<128, true>::SMEM : P == 64 ? PlaneFFT<64, true>::SMEM
+                                                                : PlaneFFT<32, true>::SMEM;
+  return std::max(c, pl);
+}
+
+}  // namespace
+
+int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, int iters,
+                  PersistPlan** out) {
+  *out = nullptr;
+  if (ngroups < 1 || ngroups > SFS_MAX_GROUPS) {
+    set_error("1..%d groups", SFS_MAX_GROUPS);
+    return SFS_ERR_INVALID_ARG;
+  }
+  PersistPlan* pp = new (std::nothrow) PersistPlan;
+  if (!pp) {
+    set_error("host allocation failed");
+    return SFS_ERR_OOM;
+  }
+  memset(&pp->prm, 0, sizeof(pp->prm));
+  std::vector<CUtensorMap> maps;
+  std::vector<int2> jobs;
+  std::vector<long long> cum_f(1, 0), cum_a(1, 0), cum_r(1, 0), cum_u(1, 0);
+  int smem = 0;
+  int rc = SFS_OK;
+  for (int gi = 0; gi < ngroups && rc == SFS_OK; ++gi) {
+    const sfs_operator* op = ops[gi];
+    const PlaneDims& d = dims[gi];
+    PGroup& g = pp->prm.groups[gi];
+    g.d = d;
+    const sfs::BatchWorkspace& w = op->bws;
+    g.Xh = w.Xh;
+    g.Yh = w.Yh;
+    g.Rh = w.Rh;
+    g.Gh = w.Gh;
+    g.xk = w.xk;
+    g.gam = w.gam;
+    g.yplane = w.yplane;
+    g.scal = w.scal;
+    g.posmap = op->posmap;
+    g.segslot = op->ws.segslot;
+    g.err = op->ws.err;
+    g.NB = tc16_group_of(d);
+    int nunits_f = 0, nunits_a = 0;
+    tc16_units(d, true, &g.nmt_f, &g.nch_f, &nunits_f);
+    tc16_units(d, false, &g.nmt_a, &g.nch_a, &nunits_a);
+    g.map0 = (int)maps.size();
+    maps.resize(maps.size() + 2);
+    rc = tc16_table_maps(op, &maps[g.map0], &maps[g.map0 + 1]);
+    const int B = std::max(1, d.batch);
+    for (int s0 = 0, j = 0; s0 < B && rc == SFS_OK; s0 += g.NB, ++j) {
+      CUtensorMap mx, mr;
+      rc = tc16_encode_spec(&mx, w.Xh + s0 * d.bs_xh, d.Nz, d.Ns, 32, B - s0, g.NB);
+      if (rc == SFS_OK) rc = tc16_encode_spec(&mr, w.Rh + s0 * d.bs_rh, d.Up, d.Ns, 64, B - s0, g.NB);
+      maps.push_back(mx);
+      maps.push_back(mr);
+      jobs.push_back(make_int2(gi, j));
+      cum_f.push_back(cum_f.back() + nunits_f);
+      cum_a.push_back(cum_a.back() + nunits_a);
+    }
+    cum_r.push_back(cum_r.back() + (long long)B * d.U);
+    cum_u.push_back(cum_u.back() + (long long)B * d.Nz);
+    smem = std::max(smem, plan_smem(g.NB, d.Px));
+  }
+  if (rc != SFS_OK) {
+    persist_free(pp);
+    return rc;
+  }
+  std::vector<float> beta(std::max(iters, 1));
+  {
+    double t = 1.0;
+    for (int k = 0; k < iters; ++k) {
+      const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+      beta[k] = (float)((t - 1.0) / tn);
+      t = tn;
+    }
+  }
+  // layout of the device allocation (tensor maps first: 64-byte alignment)
+  size_t off = 0;
+  const size_t o_maps = off;
+  off = align_up(off + sizeof(CUtensorMap) * maps.size(), 64);
+  const size_t o_jobs = off;
+  off = align_up(off + sizeof(int2) * jobs.size(), 64);
+  const size_t o_cf = off;
+  off += sizeof(long long) * cum_f.size();
+  const size_t o_ca = off;
+  off += sizeof(long long) * cum_a.size();
+  const size_t o_cr = off;
+  off += sizeof(long long) * cum_r.size();
+  const size_t o_cu = off;
+  off = align_up(off + sizeof(long long) * cum_u.size(), 64);
+  const size_t o_beta = off;
+  off = align_up(off + sizeof(float) * beta.size(), 64);
+  const size_t o_arr = off;
+  off += 64;
+  std::vector<unsigned char> host(off, 0);
+  cudaError_t e = cudaMalloc(&pp->blob, off);
+  if (e != cudaSuccess) {
+    pp->blob = nullptr;
+    persist_free(pp);
+    return cuda_fail(e, "persistent plan", __FILE__, __LINE__);
+  }
+  unsigned char* base = (unsigned char*)pp->blob;
+  PPlan& hp = pp->prm.p;
+  hp.ngroups = ngroups;
+  hp.njobs = (int)jobs.size();
+  hp.iters = iters;
+  hp.maps = (const CUtensorMap*)(base + o_maps);
+  hp.job = (const int2*)(base + o_jobs);
+  hp.cum_f = (const long long*)(base + o_cf);
+  hp.cum_a = (const long long*)(base + o_ca);
+  hp.cum_r = (const long long*)(base + o_cr);
+  hp.cum_u = (const long long*)(base + o_cu);
+  hp.beta = (const float*)(base + o_beta);
+  hp.arrivals = (unsigned int*)(base + o_arr);
+  hp.err = ops[0]->ws.err;
+  hp.wait_ns = ops[0]->wait_ns;
+  memcpy(host.data() + o_maps, maps.data(), sizeof(CUtensorMap) * maps.size());
+  memcpy(host.data() + o_jobs, jobs.data(), sizeof(int2) * jobs.size());
+  memcpy(host.data() + o_cf, cum_f.data(), sizeof(long long) * cum_f.size());
+  memcpy(host.data() + o_ca, cum_a.data(), sizeof(long long) * cum_a.size());
+  memcpy(host.data() + o_cr, cum_r.data(), sizeof(long long) * cum_r.size());
+  memcpy(host.data() + o_cu, cum_u.data(), sizeof(long long) * cum_u.size());
+  memcpy(host.data() + o_beta, beta.data(), sizeof(float) * beta.size());
+  e = cudaMemcpy(pp->blob, host.data(), off, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    persist_free(pp);
+    return cuda_fail(e, "persistent plan copy", __FILE__, __LINE__);
+  }
+  pp->smem = smem;
+  rc = ensure_smem_attr(fista_persistent_kernel, smem);
+  int dev = 0, sms = 0, occ = 0;
+  if (rc == SFS_OK) {
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fista_persistent_kernel, kPThreads, smem);
+    if (e != cudaSuccess) rc = cuda_fail(e, "persistent kernel occupancy", __FILE__, __LINE__);
+  }
+  if (rc == SFS_OK && occ < 1) {
+    set_error("the persistent kernel does not fit an SM (%d bytes of shared memory)", smem);
+    rc = SFS_ERR_INVALID_ARG;
+  }
+  if (rc != SFS_OK) {
+    persist_free(pp);
+    return rc;
+  }
+  pp->grid = sms * std::min(occ, 2);
+  *out = pp;
+  return SFS_OK;
+}
+
+int persist_launch(const PersistPlan* pp, cudaStream_t st) {
+  SFS_CUDA(cudaMemsetAsync(pp->prm.p.arrivals, 0, sizeof(unsigned int), st));
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(pp->grid);
+  cfg.blockDim = dim3(kPThreads);
+  cfg.dynamicSmemBytes = (size_t)pp->smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  SFS_CUDA(cudaLaunchKernelEx(&cfg, fista_persistent_kernel, pp->prm));
+  return SFS_OK;
+}
+
+void persist_free(PersistPlan* pp) {
+  if (!pp) return;
+  if (pp->blob) cudaFree(pp->blob);
+  delete pp;
+}
+
+void persist_shape(const PersistPlan* pp, int* grid, int* smem) {
+  *grid = pp->grid;
+  *smem = pp->smem;
+}
+
+}  // namespace sfs

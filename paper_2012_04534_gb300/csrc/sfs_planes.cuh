@@ -210,7 +210,10 @@ constexpr int kLoadBatch = 12;
 // 128 x 128 planes run 1024 threads (again <= 64 registers): 6 slots a round.
 template <int P, bool TWO_D>
 __host__ __device__ constexpr int load_batch() {
-  return PlaneFFT<P, TWO_D>::LANES64 ? 9 : (PlaneFFT<P, TWO_D>::NT >= 1024 ? 6 : kLoadBatch);
+  return PlaneFFT<P, TWO_D>::LANES64 ? 9
+         : PlaneFFT<P, TWO_D>::NT >= 1024 ? 6
+         : (TWO_D && P == 32) ? 4  // 32 x 32 planes: at most 2 slots a thread (about 1,100 slots)
+                              : kLoadBatch;
 }
 
 // Spectrum of bin plane u from the forward contraction: the sum of its nzb

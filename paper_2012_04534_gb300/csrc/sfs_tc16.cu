@@ -175,10 +175,8 @@ int launch_h(const PlaneDims& d, const CUtensorMap& tab, const CUtensorMap& spec
              long long out_stride, int nscene, const float* pm, int* err, cudaStream_t st) {
   using Pl = HPlan<NP, NB>;
   SFS_TRY(ensure_smem_attr(contract_h<FWD, NP, NB>, Pl::kSmem));
-  const int No = d.Ns / d.GS;
-  const int nmt = FWD ? (d.U + 127) / 128 : (d.nkb + 1) / 2;
-  const int nch = FWD ? d.nkb : (d.U + 63) / 64;
-  const int nunits = No * nmt;
+  int nmt = 0, nch = 0, nunits = 0;
+  tc16_units(d, FWD, &nmt, &nch, &nunits);
   // d.G = two CTAs per SM
   const int G = std::min(Pl::kCtasPerSm == 2 ? d.G : d.G / 2, nunits);
   if (G <= 0) return SFS_OK;
@@ -238,6 +236,30 @@ int check_maps(const PlaneDims& d) {
 }
 
 }  // namespace
+
+void tc16_units(const PlaneDims& d, bool fwd, int* nmt, int* nch, int* nunits) {
+  const int No = d.Ns / d.GS;
+  *nmt = fwd ? (d.U + 127) / 128 : (d.nkb + 1) / 2;
+  *nch = fwd ? d.nkb : (d.U + 63) / 64;
+  *nunits = No * *nmt;
+}
+
+int tc16_group_of(const PlaneDims& d) { return group_of(d); }
+
+int tc16_table_maps(const sfs_operator* op, CUtensorMap* tab_f, CUtensorMap* tab_a) {
+  if (!op->tmaps) {
+    set_error("16-bit contraction without tensor maps");
+    return SFS_ERR_INVALID_ARG;
+  }
+  *tab_f = op->tmaps->tab_f;
+  *tab_a = op->tmaps->tab_a;
+  return SFS_OK;
+}
+
+int tc16_encode_spec(CUtensorMap* m, const void* base, int rows, int Ns, int box_rows, int scenes,
+                     int box_scenes) {
+  return encode_spec(m, base, rows, Ns, box_rows, scenes, box_scenes);
+}
 
 int tc16_setup(sfs_operator* op) {
   TcMaps* m = new (std::nothrow) TcMaps;

@@ -154,14 +154,16 @@ struct HPlan {
 // mt), nch chunks each) by the calling CTA, whose dynamic shared memory
 // starts at hsm_raw.  Warps 0-6 take the roles above; further warps of a
 // larger CTA only pass the CTA barriers at the start and the end.  The
-// mbarriers are invalidated and the tensor memory freed before it returns,
-// so a CTA may run it again on other units.
+// tensor memory is freed before it returns.  With `reuse` (a CTA that runs
+// it again on other units) the roles also wait for the MMAs' last releases
+// of the table stages and B slots, so that no arrival is still on its way,
+// and the mbarriers are invalidated before the shared memory is used again.
 template <bool FWD, int NP, int NB>
 __device__ __forceinline__ void contract_h_run(const CUtensorMap* tab, const CUtensorMap* spec,
                                                float2* __restrict__ out, long long out_stride, int nscene,
                                                const PlaneDims& d, int nmt, int nch, int first, int nu,
                                                const float* __restrict__ pm, int* __restrict__ err,
-                                               unsigned char* hsm_raw) {
+                                               unsigned char* hsm_raw, bool reuse = false) {
   using Pl = HPlan<NP, NB>;
   constexpr uint32_t kHCols = Pl::kCols;
   constexpr int ST = Pl::kST, SS = Pl::kSS, SBB = Pl::kSBB, LEAD = Pl::kLead;
@@ -208,7 +210,9 @@ __device__ __forceinline__ void contract_h_run(const CUtensorMap* tab, const CUt
   }
   if (warp == 0) {
     tc_alloc(smem_addr(tslot), kHCols);
-    tc_relinquish();
+    // a CTA that allocates again later keeps its permit (allocating after
+    // relinquishing it is illegal)
+    if (!reuse) tc_relinquish();
   }
   tc_fence_before();
   __syncthreads();
@@ -288,6 +292,11 @@ __device__ __forceinline__ void contract_h_run(const CUtensorMap* tab, const CUt
     // copies in flight: the latest use of each stage
     for (int i = max(0, issued - ST); i < issued; ++i)
       mbar_wait_bounded(bar(Pl::kTF + i % ST), (i / ST) & 1, kDrainNs);
+    // and the MMAs' release of those stages (their commits), so that nothing
+    // arrives on a barrier after the barriers are invalidated
+    if (reuse && ok)
+      for (int i = max(0, issued - ST); i < issued; ++i)
+        mbar_wait_bounded(bar(Pl::kTE + i % ST), (i / ST) & 1, kDrainNs);
   } else if (warp == kHMmaWarp) {
     // ---- MMA issuer (whole warp, one elected lane issues) ----
     const uint32_t idesc = d.f16 ? idesc_16(128, 32 * NB, !FWD, true) : idesc_16(128, 32 * NB, !FWD, false);
@@ -491,6 +500,10 @@ __device__ __forceinline__ void contract_h_run(const CUtensorMap* tab, const CUt
       *abort_flag = 1;
       atomicExch(err, 1);
     }
+    // the MMAs' release of the last B slots (their commits), as above
+    if (reuse && ok)
+      for (int i = max(0, items - SBB); i < items; ++i)
+        mbar_wait_bounded(bar(Pl::kBE + i % SBB), (i / SBB) & 1, kDrainNs);
   }
   pdl_trigger();
   tc_fence_before();
@@ -499,9 +512,12 @@ __device__ __forceinline__ void contract_h_run(const CUtensorMap* tab, const CUt
     tc_fence_after();
     tc_dealloc(tmem, kHCols);
   }
-  if (threadIdx.x == 0)  // every copy and MMA has completed: nothing arrives any more
-    for (int k = 0; k < Pl::kNumBars; ++k) mbar_inval(bar(k));
-  __syncthreads();
+  if (reuse) {
+    if (threadIdx.x == 0)  // every copy, MMA and release has completed: nothing arrives any more
+      for (int k = 0; k < Pl::kNumBars; ++k) mbar_inval(bar(k));
+    fence_proxy_async_all();  // whatever uses this shared memory next, through either proxy
+    __syncthreads();
+  }
 }
 
 }  // namespace

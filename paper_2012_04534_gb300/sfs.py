@@ -64,7 +64,7 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_lista_create", "sfs_lista_destroy", "sfs_lista_info", "sfs_lista_set_params",
            "sfs_lista_get_params", "sfs_lista_load_params_dev", "sfs_lista_forward",
            "sfs_lista_backward", "sfs_lista_nmse", "sfs_lista_adam", "sfs_frobenius",
-           "sfs_fista_grouped", "sfs_crb", "sfs_mixing_band", "sfs_mixing_create", "sfs_mixing_destroy",
+           "sfs_fista_grouped", "sfs_fista_persistent", "sfs_crb", "sfs_mixing_band", "sfs_mixing_create", "sfs_mixing_destroy",
            "sfs_apply_A_mixed", "sfs_apply_AH_mixed", "sfs_lipschitz_mixed", "sfs_fista_mixed",
            "sfs_autotune_batch", "sfs_set_batch_tile", "sfs_fista_backtracking", "sfs_grouped_times",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
@@ -135,6 +135,7 @@ def lib():
         "sfs_max_abs_AH": [vp, vp, P(dbl), vp],
         "sfs_frobenius": [vp, P(dbl), P(dbl)],
         "sfs_fista_grouped": [i32, P(vp), P(ctypes.c_int32), P(vp), P(dbl), dbl, i32, P(vp), vp],
+        "sfs_fista_persistent": [i32, P(vp), P(ctypes.c_int32), P(vp), P(dbl), dbl, i32, P(vp), vp],
         "sfs_crb": [vp, i32, i32, P(ctypes.c_int32), P(dbl), dbl, dbl, dbl, i32, P(dbl), P(dbl)],
         "sfs_mixing_band": [vp, P(ctypes.c_int32), P(ctypes.c_int32)],
         "sfs_mixing_create": [vp, i32, P(ctypes.c_int32), P(ctypes.c_int8), P(vp)],
@@ -356,10 +357,11 @@ def sfs_version() -> str:
 
 # --------------------------------------------------------------- wrappers ---
 
-def fista_grouped(ops, ys, Ls, lam, iters, xs=None, stream=None):
+def fista_grouped(ops, ys, Ls, lam, iters, xs=None, stream=None, persistent=False):
     """sfs_fista_grouped: ops[g] solves the scenes ys[g] ([batch, S, M]
     complex64 CUDA tensors) with Lipschitz constant Ls[g]; returns the list
-    of [batch, Nz, Ny, Nx] results."""
+    of [batch, Nz, Ny, Nx] results.  persistent: sfs_fista_persistent (the
+    loop of all groups in one persistent kernel)."""
     import torch
     n = len(ops)
     if xs is None:
@@ -371,9 +373,15 @@ def fista_grouped(ops, ys, Ls, lam, iters, xs=None, stream=None):
     yp = VP(*[_dev_ptr(y, int(y.shape[0]) * op.S * op.M, "y") for op, y in zip(ops, ys)])
     xp = VP(*[_dev_ptr(x, int(x.shape[0]) * op.V, "x") for op, x in zip(ops, xs)])
     Lv = (ctypes.c_double * n)(*[float(v) for v in Ls])
-    _check(lib().sfs_fista_grouped(n, oph, b, yp, Lv, float(lam), int(iters), xp,
-                                   _stream_ptr(stream, ys[0].device)))
+    fn = lib().sfs_fista_persistent if persistent else lib().sfs_fista_grouped
+    _check(fn(n, oph, b, yp, Lv, float(lam), int(iters), xp, _stream_ptr(stream, ys[0].device)))
     return xs
+
+
+def fista_persistent(ops, ys, Ls, lam, iters, xs=None, stream=None):
+    """sfs_fista_persistent: fista_grouped with the iteration loop of every
+    group in one persistent kernel."""
+    return fista_grouped(ops, ys, Ls, lam, iters, xs=xs, stream=stream, persistent=True)
 
 
 def grouped_times(n):
