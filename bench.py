@@ -479,13 +479,39 @@ def serving_study(sfs, torch, args, flush, stream, seed):
     ts.sort()
     lat.sort()
     total = sum(counts)
+    # the same solve with the loops of all classes in one persistent kernel
+    xg = [x.clone() for x in xs]
+    t2 = time.perf_counter()
+    policy, probe_ms = sfs.autotune_persistent(ops, ys, Ls, -0.05, probe_iters=10, reps=2)
+    t_ptune = time.perf_counter() - t2
+    xp = sfs.fista_persistent(ops, ys, Ls, -0.05, iters, nb_policy=policy)  # graph capture
+    torch.cuda.synchronize()
+    tp = []
+    for _ in range(3):
+        flush.fill_(3)
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sfs.fista_persistent(ops, ys, Ls, -0.05, iters, xs=xp, nb_policy=policy)
+        b2.record(stream)
+        torch.cuda.synchronize()
+        tp.append(a.elapsed_time(b2))
+    agree = max(float(torch.linalg.vector_norm(p_ - g_) / torch.linalg.vector_norm(g_))
+                for pg, gg in zip(xp, xg) for p_, g_ in zip(pg, gg) if float(torch.linalg.vector_norm(g_)) > 0)
+    persistent = {"value": total * iters / (statistics.mean(tp) / 1e3), "solve_ms": statistics.mean(tp),
+                  "latency_ms_p50": statistics.mean(tp), "latency_ms_p99": statistics.mean(tp),
+                  "max_rel_diff_vs_grouped": agree, "tile_policy": policy,
+                  "probe_ms_policies_0_1_2_4": probe_ms, "tile_tuning_s": t_ptune,
+                  "note": "sfs_fista_persistent: one cooperative kernel runs all iterations of every class "
+                          "(a grid barrier between the 4 steps of an iteration); every scene ends with the "
+                          "solve. Before it, as in the grouped solve, the lambda rule per class and, in the "
+                          "captured graph, 2 setup kernels per class"}
     return {"scenes": total, "classes": len(ops), "iters": iters, "precision": "bf16",
             "unit": "scene-iterations/s", "value": total * iters / (statistics.mean(ts) / 1e3),
             "solve_ms": statistics.mean(ts),
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
             "latency_note": "per scene: from the start of the grouped call to the end of its class's loop "
                             "(event-record node in the graph), over 3 solves",
-            "setup_s": t_setup, "autotune_s": t_tune, "tiles_chosen": tiles,
+            "setup_s": t_setup, "autotune_s": t_tune, "tiles_chosen": tiles, "persistent": persistent,
             "mix": "grids {16,32,48,64}^2, depths {64,128,256}, M {32,64,128}, 10 scatterers, 20 dB"}
 
 

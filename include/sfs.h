@@ -313,28 +313,46 @@ int sfs_fista_grouped(int ngroups, sfs_operator* const* ops, const int32_t* batc
 /*
  * The same solve (arguments, results and errors as sfs_fista_grouped) with
  * the iteration loop of all groups in ONE persistent kernel: a cooperative
- * launch of 512-thread CTAs (as many as fit, one or two per SM) that runs
- * every iteration of Algorithm 1 for every scene.  Per iteration it takes
- * four steps over the work of all groups at once: the forward contractions
- * (every group's (orbit, bin tile) units of every scene tile, cut into equal
- * contiguous shares per CTA), the residual planes (every group's scenes x
- * bins, round robin), the adjoint contractions and the update planes
- * (scenes x depths); the CTAs meet at a grid barrier between steps.  The
- * barrier waits are bounded (the operators' wait limit, 2 s by default); a
- * CTA that gives up sets the first operator's error flag (sfs_check_status
- * then reports SFS_ERR_TIMEOUT) and the kernel ends.  The contraction of a
- * group uses its scenes-per-tile choice (sfs_autotune_batch /
- * sfs_set_batch_tile).  The per-group setup (measurements by plane, X^ of
- * gamma_1) and the persistent kernel are captured as one graph on the first
- * call for a set of (operators, batch sizes, iterations) and replayed
- * afterwards (shared cache with sfs_fista_grouped).  Every scene finishes
- * with the solve.  Operators: area scans (lateral FFT planes 32, 64 or 128)
- * with a one-part 16-bit table (SFS_PREC_BF16 or SFS_PREC_FP16); others give
- * SFS_ERR_INVALID_ARG.
+ * launch of one 512-thread CTA per SM that runs every iteration of
+ * Algorithm 1 for every scene.  Per iteration it takes four steps over the
+ * work of all groups at once: the forward contractions (every group's table
+ * chunks of every scene tile, cut into equal contiguous shares per CTA, a
+ * unit of chunks going to the CTA that holds its first chunk), the residual
+ * planes (every group's scenes x bins, handed out one at a time from a
+ * counter, groups with the largest planes first), the adjoint contractions
+ * and the update planes (scenes x depths, likewise); the CTAs meet at a grid
+ * barrier between steps.  The barrier waits are bounded (the operators' wait
+ * limit, 2 s by default); a CTA that gives up sets the first operator's
+ * error flag (sfs_check_status then reports SFS_ERR_TIMEOUT) and the kernel
+ * ends.  nb_policy sets the scenes per table tile of the contractions: 0
+ * takes each group's own choice (sfs_autotune_batch / sfs_set_batch_tile),
+ * 1, 2 or 4 that many for every group (fewer where the batch is smaller);
+ * other values give SFS_ERR_INVALID_ARG.  The per-group setup (measurements
+ * by plane, X^ of gamma_1) and the persistent kernel are captured as one
+ * graph on the first call for a set of (operators, batch sizes, iterations,
+ * policy) and replayed afterwards (shared cache with sfs_fista_grouped).
+ * Every scene finishes with the solve.  Operators: area scans (lateral FFT
+ * planes 32, 64 or 128) with a one-part 16-bit table (SFS_PREC_BF16 or
+ * SFS_PREC_FP16); others give SFS_ERR_INVALID_ARG.
  */
 int sfs_fista_persistent(int ngroups, sfs_operator* const* ops, const int32_t* batch,
                          const void* const* y_dev, const double* L, double lambda, int iters,
-                         void* const* x_out_dev, void* stream);
+                         void* const* x_out_dev, int nb_policy, void* stream);
+
+/*
+ * Tuner of the persistent solve's contraction tiles: times `reps` persistent
+ * solves of probe_iters iterations (after one that captures the graph) for
+ * each tile policy 0, 1, 2, 4 of sfs_fista_persistent on the given groups
+ * (its arguments; x_out_dev receives the last probe's results), writes the
+ * fastest policy to *policy_out and the ms per probe solve of each to
+ * ms_out[0..3] (in that order) if ms_out is not null.  Policy 0 uses the
+ * groups' own choices, so tune those first (sfs_autotune_batch).  Errors
+ * as sfs_fista_persistent.
+ */
+int sfs_autotune_persistent(int ngroups, sfs_operator* const* ops, const int32_t* batch,
+                            const void* const* y_dev, const double* L, double lambda, int probe_iters,
+                            int reps, void* const* x_out_dev, int32_t* policy_out, double* ms_out,
+                            void* stream);
 
 /*
  * Completion times of the latest sfs_fista_grouped call of the process

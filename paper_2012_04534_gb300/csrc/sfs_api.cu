@@ -768,9 +768,9 @@ int grouped_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch, i
 // The persistent solve's graph: per group the measurements by plane and X^ of
 // gamma_1 (plain launches), then the one cooperative kernel of all
 // iterations.  Cached with the grouped graphs (its key starts with a tag).
-int persistent_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch, int iters,
+int persistent_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch, int iters, int nb_policy,
                      cudaGraphExec_t* out) {
-  std::vector<uint64_t> key = {(uint64_t)iters, (uint64_t)ngroups | (1ull << 40)};
+  std::vector<uint64_t> key = {(uint64_t)iters, (uint64_t)ngroups | ((uint64_t)(nb_policy + 1) << 40)};
   for (int g = 0; g < ngroups; ++g) {
     key.push_back(ops[g]->uid);
     key.push_back(ops[g]->bws_gen);
@@ -791,7 +791,7 @@ int persistent_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch
     SFS_TRY(prepare_kernels(dims[g]));
   }
   PersistPlan* plan = nullptr;
-  SFS_TRY(persist_build(ngroups, ops, dims.data(), iters, &plan));
+  SFS_TRY(persist_build(ngroups, ops, dims.data(), iters, nb_policy, &plan));
   cudaStream_t cs = g_grouped_capture;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) {
@@ -1865,10 +1865,11 @@ int sfs_fista_grouped(int ngroups, sfs_operator* const* ops, const int32_t* batc
 
 int sfs_fista_persistent(int ngroups, sfs_operator* const* ops, const int32_t* batch,
                          const void* const* y_dev, const double* L, double lambda, int iters,
-                         void* const* x_out_dev, void* stream) {
+                         void* const* x_out_dev, int nb_policy, void* stream) {
   clear_error();
-  if (ngroups < 1 || ngroups > SFS_MAX_GROUPS || !ops) {
-    set_error("invalid argument (1..%d groups)", SFS_MAX_GROUPS);
+  if (ngroups < 1 || ngroups > SFS_MAX_GROUPS || !ops ||
+      (nb_policy != 0 && nb_policy != 1 && nb_policy != 2 && nb_policy != 4)) {
+    set_error("invalid argument (1..%d groups, scenes per table tile 0, 1, 2 or 4)", SFS_MAX_GROUPS);
     return SFS_ERR_INVALID_ARG;
   }
   for (int g = 0; g < ngroups; ++g) {
@@ -1885,10 +1886,64 @@ int sfs_fista_persistent(int ngroups, sfs_operator* const* ops, const int32_t* b
   SFS_TRY(grouped_setup(ngroups, ops, batch, y_dev, L, lambda, iters, x_out_dev, st));
   if (iters > 0) {
     cudaGraphExec_t exec = nullptr;
-    SFS_TRY(persistent_graph(ngroups, ops, batch, iters, &exec));
+    SFS_TRY(persistent_graph(ngroups, ops, batch, iters, nb_policy, &exec));
     SFS_CUDA(cudaGraphLaunch(exec, st));
   }
   return grouped_results(ngroups, ops, batch, x_out_dev, st);
+}
+
+int sfs_autotune_persistent(int ngroups, sfs_operator* const* ops, const int32_t* batch,
+                            const void* const* y_dev, const double* L, double lambda, int probe_iters,
+                            int reps, void* const* x_out_dev, int32_t* policy_out, double* ms_out,
+                            void* stream) {
+  clear_error();
+  if (!policy_out || probe_iters < 1 || reps < 1 || ngroups < 1 || !ops || !ops[0]) {
+    set_error("invalid argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  static const int kPolicies[4] = {0, 1, 2, 4};
+  if (ms_out)
+    for (int i = 0; i < 4; ++i) ms_out[i] = NAN;
+  *policy_out = -1;
+  DeviceScope scope(ops[0]->geo.d.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SFS_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    set_error("cudaEventCreate failed");
+    return SFS_ERR_CUDA;
+  }
+  int rc = SFS_OK;
+  double best = 0.0;
+  for (int i = 0; i < 4 && rc == SFS_OK; ++i) {
+    const int pol = kPolicies[i];
+    // the first solve builds and captures the plan
+    rc = sfs_fista_persistent(ngroups, ops, batch, y_dev, L, lambda, probe_iters, x_out_dev, pol, stream);
+    if (rc != SFS_OK) break;
+    cudaEventRecord(e0, st);
+    for (int k = 0; k < reps && rc == SFS_OK; ++k)
+      rc = sfs_fista_persistent(ngroups, ops, batch, y_dev, L, lambda, probe_iters, x_out_dev, pol, stream);
+    if (rc != SFS_OK) break;
+    cudaEventRecord(e1, st);
+    const cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "tuning run", __FILE__, __LINE__);
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double per = (double)ms / reps;
+    if (ms_out) ms_out[i] = per;
+    if (*policy_out < 0 || per < best) {
+      *policy_out = pol;
+      best = per;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  SFS_TRY(rc);
+  return check_err_flag(ops[0], st);
 }
 
 int sfs_grouped_times(int ngroups, float* ms_out_host) {

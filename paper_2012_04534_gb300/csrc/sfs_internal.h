@@ -341,7 +341,9 @@ int tc16_encode_spec(CUtensorMap* m, const void* base, int rows, int Ns, int box
 // (capturable); the measurements by plane, the thresholds and X^ of gamma_1
 // must be in the workspaces first.
 struct PersistPlan;
-int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, int iters,
+// nb_policy: scenes per table tile of every group, 0 (each group's own
+// choice), 1, 2 or 4 (at most what its batch needs).
+int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, int iters, int nb_policy,
                   PersistPlan** out);
 int persist_launch(const PersistPlan* pp, cudaStream_t st);
 void persist_free(PersistPlan* pp);

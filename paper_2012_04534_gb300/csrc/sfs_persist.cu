@@ -9,17 +9,18 @@
 //   3. adjoint contraction of the residual spectra;
 //   4. update planes: inverse FFT of the gradient, soft threshold, momentum,
 //      forward FFT of gamma_{k+1}.
-// One cooperative launch of one 512-thread CTA per SM runs all iterations.
-// Each step's work of all groups is one list: contraction units (orbit, tile)
-// of every (group, scene tile), cut into equal contiguous shares per CTA, and
-// planes of every (group, scene), taken round robin.  The CTAs meet at a grid
-// barrier after each step (a global arrival counter, waited on with a time
-// limit: a CTA that gives up sets the error flag and the kernel ends).  The
-// contraction and plane steps are the code of the standalone kernels
-// (sfs_tc16_dev.cuh, sfs_planes.cuh), so a persistent solve computes what the
-// grouped one computes, up to the plane engine variant (the cluster plane
-// kernels of sfs_kernels.cu add the inverse quadrant shares in another
-// order).
+// One cooperative launch of one 512-thread CTA per SM runs all iterations.  Each step's work of all groups is one list: the table chunks
+// of every (group, scene tile) contraction, cut into equal contiguous shares
+// per CTA (a unit of chunks, whose accumulator lives in one CTA's tensor
+// memory, goes to the CTA holding its first chunk), and the planes of every
+// (group, scene), handed out one at a time from a counter per step, groups
+// with the largest planes first.  The CTAs meet at a grid barrier after each
+// step (a global arrival counter, waited on with a time limit: a CTA that
+// gives up sets the error flag and the kernel ends).  The contraction and
+// plane steps are the code of the standalone kernels (sfs_tc16_dev.cuh,
+// sfs_planes.cuh), so a persistent solve computes what the grouped one
+// computes, up to the plane engine variant (the cluster plane kernels of
+// sfs_kernels.cu add the inverse quadrant shares in another order).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -60,12 +61,14 @@ struct PPlan {
   int ngroups, njobs, iters;
   const CUtensorMap* maps;
   const int2* job;              // contraction job: {group, scene tile}
-  const long long* cum_f;       // [njobs + 1] cumulative forward units
-  const long long* cum_a;       // [njobs + 1] cumulative adjoint units
-  const long long* cum_r;       // [ngroups + 1] cumulative residual planes (scenes x bins)
-  const long long* cum_u;       // [ngroups + 1] cumulative update planes (scenes x depths)
+  const long long* cum_f;       // [njobs + 1] cumulative forward chunks (units x chunks per unit)
+  const long long* cum_a;       // [njobs + 1] cumulative adjoint chunks
+  const int* porder;            // [ngroups] groups in plane-task order (largest planes first)
+  const long long* cum_r;       // [ngroups + 1] cumulative residual planes (scenes x bins), porder
+  const long long* cum_u;       // [ngroups + 1] cumulative update planes (scenes x depths), porder
   const float* beta;            // [iters] momentum coefficients from t_1 = 1
   unsigned int* arrivals;       // grid barrier counter, zero at launch
+  unsigned int* tasks;          // [2 iters] plane-task counters of the steps, zero at launch
   int* err;                     // set when a grid barrier wait gives up
   uint64_t wait_ns;
 };
@@ -116,17 +119,24 @@ __device__ bool grid_sync(const PPlan& p, unsigned int epoch) {
   return ok != 0;
 }
 
-// Step 1 or 3: this CTA's share of the units of every contraction job.
+// Step 1 or 3: this CTA's share of the chunks of every contraction job (a
+// chunk streams one table tile: the cost unit).  The CTA takes the units
+// whose first chunk lies in its share, so every unit has one owner.
 template <bool FWD>
 __device__ __forceinline__ void contract_step(const PParams& prm, unsigned char* smem) {
   const PPlan& p = prm.p;
   const long long* cum = FWD ? p.cum_f : p.cum_a;
   const long long T = cum[p.njobs];
-  const long long u0 = T * blockIdx.x / gridDim.x, u1 = T * (blockIdx.x + 1) / gridDim.x;
+  const long long c0 = T * blockIdx.x / gridDim.x, c1 = T * (blockIdx.x + 1) / gridDim.x;
   for (int j = 0; j < p.njobs; ++j) {
-    const long long a = max(u0, cum[j]), e = min(u1, cum[j + 1]);
+    if (cum[j + 1] <= c0 || cum[j] >= c1) continue;
+    const int2 jb0 = p.job[j];
+    const int nchj = FWD ? prm.groups[jb0.x].nch_f : prm.groups[jb0.x].nch_a;
+    // units whose first chunk is in [c0, c1): ceil of both ends, relative to the job
+    const long long a = (max(c0, cum[j]) - cum[j] + nchj - 1) / nchj;
+    const long long e = (min(c1, cum[j + 1]) - cum[j] + nchj - 1) / nchj;
     if (e <= a) continue;
-    const int2 jb = p.job[j];
+    const int2 jb = jb0;
     const PGroup& g = prm.groups[jb.x];
     const int s0 = jb.y * g.NB;
     const int nscene = min(g.NB, g.d.batch - s0);
@@ -137,7 +147,7 @@ __device__ __forceinline__ void contract_step(const PParams& prm, unsigned char*
     const float* pm0 = FWD ? g.d.pm_x : g.d.pm_r;
     const float* pm = pm0 ? pm0 + s0 * (FWD ? g.d.bs_pmx : g.d.bs_pmr) : nullptr;
     const int nmt = FWD ? g.nmt_f : g.nmt_a, nch = FWD ? g.nch_f : g.nch_a;
-    const int first = (int)(a - cum[j]), nu = (int)(e - a);
+    const int first = (int)a, nu = (int)(e - a);
     if (g.NB == 1)
       contract_h_run<FWD, 1, 1>(tab, spec, out, ostride, nscene, g.d, nmt, nch, first, nu, pm, g.err, smem,
                                 true);
@@ -150,11 +160,21 @@ __device__ __forceinline__ void contract_step(const PParams& prm, unsigned char*
   }
 }
 
-// The group of plane task t (cum: cumulative plane counts per group).
+// The position (in porder) of the group of plane task t (cum: cumulative
+// plane counts in that order).
 __device__ __forceinline__ int group_of_task(const long long* cum, int ngroups, long long t) {
   int g = 0;
   while (g + 1 < ngroups && cum[g + 1] <= t) ++g;
   return g;
+}
+
+// The next plane task of step counter `ctr` for the whole CTA.
+__device__ __forceinline__ long long next_task(unsigned int* ctr) {
+  __shared__ unsigned int s_task;
+  __syncthreads();  // every thread has read the previous value
+  if (threadIdx.x == 0) s_task = atomicAdd(ctr, 1u);
+  __syncthreads();
+  return (long long)s_task;
 }
 
 // The group's dimensions copied to shared memory for one plane task: the
@@ -186,15 +206,16 @@ __device__ __noinline__ void update_plane_call(const PlaneDims& d, int z, long l
                              nullptr);
 }
 
-// Step 2: residual planes of every (group, scene, bin), round robin.
-__device__ __forceinline__ void resid_step(const PParams& prm, float2* smem) {
+// Step 2: residual planes of every (group, scene, bin); each CTA takes the
+// next task from the step's counter, largest planes first.
+__device__ __forceinline__ void resid_step(const PParams& prm, int k, float2* smem) {
   const PPlan& p = prm.p;
   const long long T = p.cum_r[p.ngroups];
-  for (long long t = blockIdx.x; t < T; t += gridDim.x) {
-    const int gi = group_of_task(p.cum_r, p.ngroups, t);
-    const PGroup& g = prm.groups[gi];
+  for (long long t = next_task(p.tasks + 2 * k); t < T; t = next_task(p.tasks + 2 * k)) {
+    const int pos = group_of_task(p.cum_r, p.ngroups, t);
+    const PGroup& g = prm.groups[p.porder[pos]];
     const PlaneDims& sd = stage_dims(g.d);
-    const long long r = t - p.cum_r[gi];
+    const long long r = t - p.cum_r[pos];
     const long long b = r / sd.U;
     const int u = (int)(r - b * sd.U);
     if (sd.Px == 128)
@@ -207,17 +228,17 @@ __device__ __forceinline__ void resid_step(const PParams& prm, float2* smem) {
   }
 }
 
-// Step 4: update planes of every (group, scene, depth), round robin.
+// Step 4: update planes of every (group, scene, depth), taken likewise.
 __device__ __forceinline__ void update_step(const PParams& prm, int k, float2* smem) {
   const PPlan& p = prm.p;
   const long long T = p.cum_u[p.ngroups];
   const float beta = p.beta[k];
   const int do_fwd = k + 1 < p.iters;
-  for (long long t = blockIdx.x; t < T; t += gridDim.x) {
-    const int gi = group_of_task(p.cum_u, p.ngroups, t);
-    const PGroup& g = prm.groups[gi];
+  for (long long t = next_task(p.tasks + 2 * k + 1); t < T; t = next_task(p.tasks + 2 * k + 1)) {
+    const int pos = group_of_task(p.cum_u, p.ngroups, t);
+    const PGroup& g = prm.groups[p.porder[pos]];
     const PlaneDims& sd = stage_dims(g.d);
-    const long long r = t - p.cum_u[gi];
+    const long long r = t - p.cum_u[pos];
     const long long b = r / sd.Nz;
     const int z = (int)(r - b * sd.Nz);
     if (sd.Px == 128)
@@ -237,7 +258,7 @@ __global__ void __launch_bounds__(kPThreads, 1) fista_persistent_kernel(const __
   for (int k = 0; k < p.iters; ++k) {
     contract_step<true>(prm, psm);
     if (!grid_sync(p, ++epoch)) return;
-    resid_step(prm, reinterpret_cast<float2*>(psm));
+    resid_step(prm, k, reinterpret_cast<float2*>(psm));
     if (!grid_sync(p, ++epoch)) return;
     contract_step<false>(prm, psm);
     if (!grid_sync(p, ++epoch)) return;
@@ -256,6 +277,8 @@ struct PersistPlan {
   void* blob = nullptr;
   int grid = 0;
   int smem = 0;
+  int nb_policy = 0;
+  size_t counters_bytes = 0;  // the barrier and task counters zeroed before each launch
 };
 
 namespace {
@@ -271,11 +294,12 @@ int plan_smem(int NB, int P) {
 
 }  // namespace
 
-int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, int iters,
+int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, int iters, int nb_policy,
                   PersistPlan** out) {
   *out = nullptr;
-  if (ngroups < 1 || ngroups > SFS_MAX_GROUPS) {
-    set_error("1..%d groups", SFS_MAX_GROUPS);
+  if (ngroups < 1 || ngroups > SFS_MAX_GROUPS ||
+      (nb_policy != 0 && nb_policy != 1 && nb_policy != 2 && nb_policy != 4)) {
+    set_error("1..%d groups, scenes per table tile 0 (each group's own), 1, 2 or 4", SFS_MAX_GROUPS);
     return SFS_ERR_INVALID_ARG;
   }
   PersistPlan* pp = new (std::nothrow) PersistPlan;
@@ -306,7 +330,15 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
     g.posmap = op->posmap;
     g.segslot = op->ws.segslot;
     g.err = op->ws.err;
-    g.NB = tc16_group_of(d);
+    // scenes per table tile: the group's own choice, or the policy's (no
+    // wider than the batch needs)
+    if (nb_policy == 0) {
+      g.NB = tc16_group_of(d);
+    } else {
+      const int B = std::max(1, d.batch);
+      g.NB = std::min(nb_policy, B >= 3 ? 4 : B);
+    }
+    g.d.nb = g.NB;
     int nunits_f = 0, nunits_a = 0;
     tc16_units(d, true, &g.nmt_f, &g.nch_f, &nunits_f);
     tc16_units(d, false, &g.nmt_a, &g.nch_a, &nunits_a);
@@ -321,12 +353,21 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
       maps.push_back(mx);
       maps.push_back(mr);
       jobs.push_back(make_int2(gi, j));
-      cum_f.push_back(cum_f.back() + nunits_f);
-      cum_a.push_back(cum_a.back() + nunits_a);
+      cum_f.push_back(cum_f.back() + (long long)nunits_f * g.nch_f);
+      cum_a.push_back(cum_a.back() + (long long)nunits_a * g.nch_a);
     }
-    cum_r.push_back(cum_r.back() + (long long)B * d.U);
-    cum_u.push_back(cum_u.back() + (long long)B * d.Nz);
     smem = std::max(smem, plan_smem(g.NB, d.Px));
+  }
+  // plane tasks: groups with the largest planes first, so that the last
+  // tasks a step hands out are the short ones
+  std::vector<int> porder(ngroups);
+  for (int g = 0; g < ngroups; ++g) porder[g] = g;
+  std::stable_sort(porder.begin(), porder.end(), [&](int a, int b) { return dims[a].Px > dims[b].Px; });
+  for (int i = 0; i < ngroups; ++i) {
+    const PlaneDims& d = dims[porder[i]];
+    const long long B = std::max(1, d.batch);
+    cum_r.push_back(cum_r.back() + B * d.U);
+    cum_u.push_back(cum_u.back() + B * d.Nz);
   }
   if (rc != SFS_OK) {
     persist_free(pp);
@@ -347,6 +388,8 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
   off = align_up(off + sizeof(CUtensorMap) * maps.size(), 64);
   const size_t o_jobs = off;
   off = align_up(off + sizeof(int2) * jobs.size(), 64);
+  const size_t o_po = off;
+  off = align_up(off + sizeof(int) * porder.size(), 64);
   const size_t o_cf = off;
   off += sizeof(long long) * cum_f.size();
   const size_t o_ca = off;
@@ -357,8 +400,9 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
   off = align_up(off + sizeof(long long) * cum_u.size(), 64);
   const size_t o_beta = off;
   off = align_up(off + sizeof(float) * beta.size(), 64);
-  const size_t o_arr = off;
-  off += 64;
+  const size_t o_arr = off;  // arrivals, then 2 iters task counters
+  const size_t counters = sizeof(unsigned int) * (1 + 2 * (size_t)std::max(iters, 1));
+  off += align_up(counters, 64);
   std::vector<unsigned char> host(off, 0);
   cudaError_t e = cudaMalloc(&pp->blob, off);
   if (e != cudaSuccess) {
@@ -373,16 +417,19 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
   hp.iters = iters;
   hp.maps = (const CUtensorMap*)(base + o_maps);
   hp.job = (const int2*)(base + o_jobs);
+  hp.porder = (const int*)(base + o_po);
   hp.cum_f = (const long long*)(base + o_cf);
   hp.cum_a = (const long long*)(base + o_ca);
   hp.cum_r = (const long long*)(base + o_cr);
   hp.cum_u = (const long long*)(base + o_cu);
   hp.beta = (const float*)(base + o_beta);
   hp.arrivals = (unsigned int*)(base + o_arr);
+  hp.tasks = hp.arrivals + 1;
   hp.err = ops[0]->ws.err;
   hp.wait_ns = ops[0]->wait_ns;
   memcpy(host.data() + o_maps, maps.data(), sizeof(CUtensorMap) * maps.size());
   memcpy(host.data() + o_jobs, jobs.data(), sizeof(int2) * jobs.size());
+  memcpy(host.data() + o_po, porder.data(), sizeof(int) * porder.size());
   memcpy(host.data() + o_cf, cum_f.data(), sizeof(long long) * cum_f.size());
   memcpy(host.data() + o_ca, cum_a.data(), sizeof(long long) * cum_a.size());
   memcpy(host.data() + o_cr, cum_r.data(), sizeof(long long) * cum_r.size());
@@ -394,13 +441,15 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
     return cuda_fail(e, "persistent plan copy", __FILE__, __LINE__);
   }
   pp->smem = smem;
-  rc = ensure_smem_attr(fista_persistent_kernel, smem);
+  pp->nb_policy = nb_policy;
+  pp->counters_bytes = counters;
+  const void* kern = (const void*)fista_persistent_kernel;
+  rc = ensure_smem_attr_ptr(kern, smem);
   int dev = 0, sms = 0, occ = 0;
   if (rc == SFS_OK) {
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fista_persistent_kernel, kPThreads, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPThreads, smem);
     if (e != cudaSuccess) rc = cuda_fail(e, "persistent kernel occupancy", __FILE__, __LINE__);
   }
   if (rc == SFS_OK && occ < 1) {
@@ -411,13 +460,13 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
     persist_free(pp);
     return rc;
   }
-  pp->grid = sms * std::min(occ, 2);
+  pp->grid = sms;
   *out = pp;
   return SFS_OK;
 }
 
 int persist_launch(const PersistPlan* pp, cudaStream_t st) {
-  SFS_CUDA(cudaMemsetAsync(pp->prm.p.arrivals, 0, sizeof(unsigned int), st));
+  SFS_CUDA(cudaMemsetAsync(pp->prm.p.arrivals, 0, pp->counters_bytes, st));
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;

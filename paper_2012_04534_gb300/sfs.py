@@ -64,7 +64,7 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_lista_create", "sfs_lista_destroy", "sfs_lista_info", "sfs_lista_set_params",
            "sfs_lista_get_params", "sfs_lista_load_params_dev", "sfs_lista_forward",
            "sfs_lista_backward", "sfs_lista_nmse", "sfs_lista_adam", "sfs_frobenius",
-           "sfs_fista_grouped", "sfs_fista_persistent", "sfs_crb", "sfs_mixing_band", "sfs_mixing_create", "sfs_mixing_destroy",
+           "sfs_fista_grouped", "sfs_fista_persistent", "sfs_autotune_persistent", "sfs_crb", "sfs_mixing_band", "sfs_mixing_create", "sfs_mixing_destroy",
            "sfs_apply_A_mixed", "sfs_apply_AH_mixed", "sfs_lipschitz_mixed", "sfs_fista_mixed",
            "sfs_autotune_batch", "sfs_set_batch_tile", "sfs_fista_backtracking", "sfs_grouped_times",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
@@ -135,7 +135,9 @@ def lib():
         "sfs_max_abs_AH": [vp, vp, P(dbl), vp],
         "sfs_frobenius": [vp, P(dbl), P(dbl)],
         "sfs_fista_grouped": [i32, P(vp), P(ctypes.c_int32), P(vp), P(dbl), dbl, i32, P(vp), vp],
-        "sfs_fista_persistent": [i32, P(vp), P(ctypes.c_int32), P(vp), P(dbl), dbl, i32, P(vp), vp],
+        "sfs_fista_persistent": [i32, P(vp), P(ctypes.c_int32), P(vp), P(dbl), dbl, i32, P(vp), i32, vp],
+        "sfs_autotune_persistent": [i32, P(vp), P(ctypes.c_int32), P(vp), P(dbl), dbl, i32, i32, P(vp),
+                                    P(ctypes.c_int32), P(dbl), vp],
         "sfs_crb": [vp, i32, i32, P(ctypes.c_int32), P(dbl), dbl, dbl, dbl, i32, P(dbl), P(dbl)],
         "sfs_mixing_band": [vp, P(ctypes.c_int32), P(ctypes.c_int32)],
         "sfs_mixing_create": [vp, i32, P(ctypes.c_int32), P(ctypes.c_int8), P(vp)],
@@ -357,11 +359,7 @@ def sfs_version() -> str:
 
 # --------------------------------------------------------------- wrappers ---
 
-def fista_grouped(ops, ys, Ls, lam, iters, xs=None, stream=None, persistent=False):
-    """sfs_fista_grouped: ops[g] solves the scenes ys[g] ([batch, S, M]
-    complex64 CUDA tensors) with Lipschitz constant Ls[g]; returns the list
-    of [batch, Nz, Ny, Nx] results.  persistent: sfs_fista_persistent (the
-    loop of all groups in one persistent kernel)."""
+def _group_args(ops, ys, Ls, xs):
     import torch
     n = len(ops)
     if xs is None:
@@ -373,15 +371,41 @@ def fista_grouped(ops, ys, Ls, lam, iters, xs=None, stream=None, persistent=Fals
     yp = VP(*[_dev_ptr(y, int(y.shape[0]) * op.S * op.M, "y") for op, y in zip(ops, ys)])
     xp = VP(*[_dev_ptr(x, int(x.shape[0]) * op.V, "x") for op, x in zip(ops, xs)])
     Lv = (ctypes.c_double * n)(*[float(v) for v in Ls])
-    fn = lib().sfs_fista_persistent if persistent else lib().sfs_fista_grouped
-    _check(fn(n, oph, b, yp, Lv, float(lam), int(iters), xp, _stream_ptr(stream, ys[0].device)))
+    return n, oph, b, yp, Lv, xp, xs
+
+
+def fista_grouped(ops, ys, Ls, lam, iters, xs=None, stream=None, persistent=False, nb_policy=0):
+    """sfs_fista_grouped: ops[g] solves the scenes ys[g] ([batch, S, M]
+    complex64 CUDA tensors) with Lipschitz constant Ls[g]; returns the list
+    of [batch, Nz, Ny, Nx] results.  persistent: sfs_fista_persistent (the
+    loop of all groups in one persistent kernel, scenes per table tile by
+    nb_policy: 0 each group's own, else 1, 2 or 4)."""
+    n, oph, b, yp, Lv, xp, xs = _group_args(ops, ys, Ls, xs)
+    if persistent:
+        _check(lib().sfs_fista_persistent(n, oph, b, yp, Lv, float(lam), int(iters), xp, int(nb_policy),
+                                          _stream_ptr(stream, ys[0].device)))
+    else:
+        _check(lib().sfs_fista_grouped(n, oph, b, yp, Lv, float(lam), int(iters), xp,
+                                       _stream_ptr(stream, ys[0].device)))
     return xs
 
 
-def fista_persistent(ops, ys, Ls, lam, iters, xs=None, stream=None):
+def fista_persistent(ops, ys, Ls, lam, iters, xs=None, stream=None, nb_policy=0):
     """sfs_fista_persistent: fista_grouped with the iteration loop of every
     group in one persistent kernel."""
-    return fista_grouped(ops, ys, Ls, lam, iters, xs=xs, stream=stream, persistent=True)
+    return fista_grouped(ops, ys, Ls, lam, iters, xs=xs, stream=stream, persistent=True,
+                         nb_policy=nb_policy)
+
+
+def autotune_persistent(ops, ys, Ls, lam, probe_iters=10, reps=3, xs=None, stream=None):
+    """sfs_autotune_persistent: (tile policy chosen, [ms per probe solve for
+    policies 0, 1, 2, 4])."""
+    n, oph, b, yp, Lv, xp, xs = _group_args(ops, ys, Ls, xs)
+    c = ctypes.c_int32()
+    ms = (ctypes.c_double * 4)()
+    _check(lib().sfs_autotune_persistent(n, oph, b, yp, Lv, float(lam), int(probe_iters), int(reps), xp,
+                                         ctypes.byref(c), ms, _stream_ptr(stream, ys[0].device)))
+    return c.value, [ms[i] for i in range(4)]
 
 
 def grouped_times(n):

@@ -86,6 +86,14 @@ def test_persistent_equals_grouped(sfs):
     xp2 = [to_host(x) for x in sfs.fista_persistent(ops, ys, Ls, -0.05, 40)]
     for g in range(len(ops)):
         assert np.array_equal(xp2[g], xp[g])
+    # every group with one scene per table tile: the same results
+    xp1 = [to_host(x) for x in sfs.fista_persistent(ops, ys, Ls, -0.05, 40, nb_policy=1)]
+    for g in range(len(ops)):
+        for b in range(xg[g].shape[0]):
+            assert rel_err(xp1[g][b], xg[g][b]) <= 1e-4, (g, b)
+    # the tile tuner times the four policies and picks the fastest
+    c, ms = sfs.autotune_persistent(ops, ys, Ls, -0.05, probe_iters=4, reps=2)
+    assert c in (0, 1, 2, 4) and all(v > 0 for v in ms) and ms[(0, 1, 2, 4).index(c)] == min(ms)
     for op in ops:
         assert op.check_status() == 0
 
@@ -113,6 +121,8 @@ def test_persistent_one_group_matches_oracle(sfs):
 
 @pytest.mark.parametrize("kind", ["fp32", "bf16x2", "line"])
 def test_persistent_rejects_other_operators(sfs, kind):
+    """FP32, two-part 16-bit and line-scan operators, and a tile policy other
+    than 0, 1, 2 or 4, are refused."""
     if kind == "line":
         params = geom_params(Nx=16, Ny=1, Nz=8, dz=0.15e-3, Nt=128)
         prec = sfs.SFS_PREC_BF16
@@ -125,3 +135,9 @@ def test_persistent_rejects_other_operators(sfs, kind):
     y = to_dev(np.zeros((1, op.S, op.M)))
     with pytest.raises(sfs.SfsError):
         sfs.fista_persistent([op], [y], [1.0], -0.05, 5)
+    if kind == "line":
+        g2 = sfs.Geometry(**geom_params(Nx=8, Ny=8, Nz=8, dz=0.15e-3, Nt=128))
+        op2 = sfs.Operator.from_indices(g2, O.select_indices(oracle_geometry(geom_params(
+            Nx=8, Ny=8, Nz=8, dz=0.15e-3, Nt=128)), O.SEL_RANDOM, 4, True, 5), precision=sfs.SFS_PREC_BF16)
+        with pytest.raises(sfs.SfsError):
+            sfs.fista_persistent([op2], [to_dev(np.zeros((1, op2.S, op2.M)))], [1.0], -0.05, 5, nb_policy=3)
