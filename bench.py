@@ -495,11 +495,13 @@ def serving_study(sfs, torch, args, flush, stream, seed):
         b2.record(stream)
         torch.cuda.synchronize()
         tp.append(a.elapsed_time(b2))
+    step_ms = sfs.persistent_step_times()
     agree = max(float(torch.linalg.vector_norm(p_ - g_) / torch.linalg.vector_norm(g_))
                 for pg, gg in zip(xp, xg) for p_, g_ in zip(pg, gg) if float(torch.linalg.vector_norm(g_)) > 0)
     persistent = {"value": total * iters / (statistics.mean(tp) / 1e3), "solve_ms": statistics.mean(tp),
                   "latency_ms_p50": statistics.mean(tp), "latency_ms_p99": statistics.mean(tp),
                   "max_rel_diff_vs_grouped": agree, "tile_policy": policy,
+                  "step_ms_fwd_resid_adj_update": step_ms,
                   "probe_ms_policies_0_1_2_4": probe_ms, "tile_tuning_s": t_ptune,
                   "note": "sfs_fista_persistent: one cooperative kernel runs all iterations of every class "
                           "(a grid barrier between the 4 steps of an iteration); every scene ends with the "

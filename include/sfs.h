@@ -355,6 +355,17 @@ int sfs_autotune_persistent(int ngroups, sfs_operator* const* ops, const int32_t
                             void* stream);
 
 /*
+ * Time of the four kinds of step of the latest sfs_fista_persistent solve of
+ * the process, summed over its iterations (ms, host array of 4: forward
+ * contractions, residual planes, adjoint contractions, update planes), as
+ * CTA 0 sees them: each from the grid barrier that starts the step to the
+ * one that ends it (the last update step to CTA 0's own end).  Waits for the
+ * device.  Errors: SFS_ERR_INVALID_ARG (no such solve, or its graph was
+ * evicted from the cache), SFS_ERR_CUDA.
+ */
+int sfs_persistent_step_times(double* ms_out_host);
+
+/*
  * Completion times of the latest sfs_fista_grouped call of the process
  * (ngroups must match it): ms_out_host[g] = milliseconds from the start of
  * that call on its stream (before the per-group setup) to the end of group

@@ -662,6 +662,8 @@ cudaStream_t g_grouped_capture = nullptr;
 std::vector<cudaEvent_t> g_done_events;
 cudaEvent_t g_grouped_start = nullptr;
 int g_grouped_last_n = 0;
+// key of the latest persistent solve's cache entry (sfs_persistent_step_times)
+std::vector<uint64_t> g_last_persist_key;
 
 // Adds an entry to the cache (g_grouped_mu held), evicting the oldest.
 void cache_grouped(const GroupedEntry& ent) {
@@ -779,6 +781,8 @@ int persistent_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch
   int dev = 0;
   SFS_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(g_grouped_mu);
+  g_last_persist_key = key;
+  g_last_persist_key.push_back((uint64_t)dev);
   for (auto& e : g_grouped)
     if (e.key == key && e.device == dev) {
       *out = e.exec;
@@ -1944,6 +1948,29 @@ int sfs_autotune_persistent(int ngroups, sfs_operator* const* ops, const int32_t
   cudaEventDestroy(e1);
   SFS_TRY(rc);
   return check_err_flag(ops[0], st);
+}
+
+int sfs_persistent_step_times(double* ms_out_host) {
+  clear_error();
+  if (!ms_out_host) {
+    set_error("invalid argument");
+    return SFS_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_grouped_mu);
+  if (g_last_persist_key.empty()) {
+    set_error("no persistent solve to report");
+    return SFS_ERR_INVALID_ARG;
+  }
+  std::vector<uint64_t> key(g_last_persist_key.begin(), g_last_persist_key.end() - 1);
+  const int dev = (int)g_last_persist_key.back();
+  for (auto& e : g_grouped)
+    if (e.key == key && e.device == dev && e.plan) {
+      DeviceScope scope(dev);
+      SFS_CUDA(cudaDeviceSynchronize());
+      return persist_step_ms(e.plan, ms_out_host);
+    }
+  set_error("the latest persistent solve's plan is no longer cached");
+  return SFS_ERR_INVALID_ARG;
 }
 
 int sfs_grouped_times(int ngroups, float* ms_out_host) {

@@ -348,6 +348,9 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
 int persist_launch(const PersistPlan* pp, cudaStream_t st);
 void persist_free(PersistPlan* pp);
 void persist_shape(const PersistPlan* pp, int* grid, int* smem);
+// Time (ms) of the forward-contraction, residual-plane, adjoint-contraction
+// and update-plane steps summed over the iterations of the plan's latest run.
+int persist_step_ms(const PersistPlan* pp, double* ms4);
 
 // Batched building blocks (sfs_api.cu) used by the learned network
 // (sfs_lista.cu), on the operator's batched workspace:

@@ -69,6 +69,8 @@ struct PPlan {
   const float* beta;            // [iters] momentum coefficients from t_1 = 1
   unsigned int* arrivals;       // grid barrier counter, zero at launch
   unsigned int* tasks;          // [2 iters] plane-task counters of the steps, zero at launch
+  unsigned long long* step_ns;  // [4] time of each kind of step summed over the iterations (CTA 0's
+                                //     view: from one barrier to the next), zero at launch
   int* err;                     // set when a grid barrier wait gives up
   uint64_t wait_ns;
 };
@@ -255,15 +257,28 @@ __global__ void __launch_bounds__(kPThreads, 1) fista_persistent_kernel(const __
   extern __shared__ __align__(1024) unsigned char psm[];
   const PPlan& p = prm.p;
   unsigned int epoch = 0;
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  uint64_t t = timer ? global_ns() : 0;
+  auto mark = [&](int step) {  // CTA 0, after the barrier that ends a step
+    if (timer) {
+      const uint64_t now = global_ns();
+      p.step_ns[step] += now - t;
+      t = now;
+    }
+  };
   for (int k = 0; k < p.iters; ++k) {
     contract_step<true>(prm, psm);
     if (!grid_sync(p, ++epoch)) return;
+    mark(0);
     resid_step(prm, k, reinterpret_cast<float2*>(psm));
     if (!grid_sync(p, ++epoch)) return;
+    mark(1);
     contract_step<false>(prm, psm);
     if (!grid_sync(p, ++epoch)) return;
+    mark(2);
     update_step(prm, k, reinterpret_cast<float2*>(psm));
     if (k + 1 < p.iters && !grid_sync(p, ++epoch)) return;
+    mark(3);  // the last update step: CTA 0's own end
   }
 }
 
@@ -400,8 +415,8 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
   off = align_up(off + sizeof(long long) * cum_u.size(), 64);
   const size_t o_beta = off;
   off = align_up(off + sizeof(float) * beta.size(), 64);
-  const size_t o_arr = off;  // arrivals, then 2 iters task counters
-  const size_t counters = sizeof(unsigned int) * (1 + 2 * (size_t)std::max(iters, 1));
+  const size_t o_arr = off;  // step times, arrivals, then 2 iters task counters
+  const size_t counters = 4 * sizeof(unsigned long long) + sizeof(unsigned int) * (1 + 2 * (size_t)std::max(iters, 1));
   off += align_up(counters, 64);
   std::vector<unsigned char> host(off, 0);
   cudaError_t e = cudaMalloc(&pp->blob, off);
@@ -423,7 +438,8 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
   hp.cum_r = (const long long*)(base + o_cr);
   hp.cum_u = (const long long*)(base + o_cu);
   hp.beta = (const float*)(base + o_beta);
-  hp.arrivals = (unsigned int*)(base + o_arr);
+  hp.step_ns = (unsigned long long*)(base + o_arr);
+  hp.arrivals = (unsigned int*)(hp.step_ns + 4);
   hp.tasks = hp.arrivals + 1;
   hp.err = ops[0]->ws.err;
   hp.wait_ns = ops[0]->wait_ns;
@@ -466,7 +482,7 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
 }
 
 int persist_launch(const PersistPlan* pp, cudaStream_t st) {
-  SFS_CUDA(cudaMemsetAsync(pp->prm.p.arrivals, 0, pp->counters_bytes, st));
+  SFS_CUDA(cudaMemsetAsync(pp->prm.p.step_ns, 0, pp->counters_bytes, st));
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
@@ -490,6 +506,13 @@ void persist_free(PersistPlan* pp) {
 void persist_shape(const PersistPlan* pp, int* grid, int* smem) {
   *grid = pp->grid;
   *smem = pp->smem;
+}
+
+int persist_step_ms(const PersistPlan* pp, double* ms4) {
+  unsigned long long ns[4];
+  SFS_CUDA(cudaMemcpy(ns, pp->prm.p.step_ns, sizeof(ns), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 4; ++i) ms4[i] = (double)ns[i] * 1e-6;
+  return SFS_OK;
 }
 
 }  // namespace sfs

@@ -64,7 +64,7 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_lista_create", "sfs_lista_destroy", "sfs_lista_info", "sfs_lista_set_params",
            "sfs_lista_get_params", "sfs_lista_load_params_dev", "sfs_lista_forward",
            "sfs_lista_backward", "sfs_lista_nmse", "sfs_lista_adam", "sfs_frobenius",
-           "sfs_fista_grouped", "sfs_fista_persistent", "sfs_autotune_persistent", "sfs_crb", "sfs_mixing_band", "sfs_mixing_create", "sfs_mixing_destroy",
+           "sfs_fista_grouped", "sfs_fista_persistent", "sfs_autotune_persistent", "sfs_persistent_step_times", "sfs_crb", "sfs_mixing_band", "sfs_mixing_create", "sfs_mixing_destroy",
            "sfs_apply_A_mixed", "sfs_apply_AH_mixed", "sfs_lipschitz_mixed", "sfs_fista_mixed",
            "sfs_autotune_batch", "sfs_set_batch_tile", "sfs_fista_backtracking", "sfs_grouped_times",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
@@ -138,6 +138,7 @@ def lib():
         "sfs_fista_persistent": [i32, P(vp), P(ctypes.c_int32), P(vp), P(dbl), dbl, i32, P(vp), i32, vp],
         "sfs_autotune_persistent": [i32, P(vp), P(ctypes.c_int32), P(vp), P(dbl), dbl, i32, i32, P(vp),
                                     P(ctypes.c_int32), P(dbl), vp],
+        "sfs_persistent_step_times": [P(dbl)],
         "sfs_crb": [vp, i32, i32, P(ctypes.c_int32), P(dbl), dbl, dbl, dbl, i32, P(dbl), P(dbl)],
         "sfs_mixing_band": [vp, P(ctypes.c_int32), P(ctypes.c_int32)],
         "sfs_mixing_create": [vp, i32, P(ctypes.c_int32), P(ctypes.c_int8), P(vp)],
@@ -395,6 +396,15 @@ def fista_persistent(ops, ys, Ls, lam, iters, xs=None, stream=None, nb_policy=0)
     group in one persistent kernel."""
     return fista_grouped(ops, ys, Ls, lam, iters, xs=xs, stream=stream, persistent=True,
                          nb_policy=nb_policy)
+
+
+def persistent_step_times():
+    """sfs_persistent_step_times: ms of the forward contractions, residual
+    planes, adjoint contractions and update planes of the latest persistent
+    solve, summed over its iterations."""
+    out = (ctypes.c_double * 4)()
+    _check(lib().sfs_persistent_step_times(out))
+    return [out[i] for i in range(4)]
 
 
 def autotune_persistent(ops, ys, Ls, lam, probe_iters=10, reps=3, xs=None, stream=None):
