@@ -847,8 +847,8 @@ def run_reference(args, rank, world):
 # Sources that define the contraction kernels or their launch shapes (the
 # FP32, TF32X3 and 16-bit contractions, the plane data they read, their
 # shared headers); a traffic record taken on other versions of these is stale.
-CONTRACTION_SOURCES = ("sfs_kernels.cu", "sfs_tc.cu", "sfs_tc16.cu", "sfs_internal.h", "sfs_launch.h",
-                       "sfs_async.cuh", "sfs_tcgen05.cuh", "sfs_fft.cuh")
+CONTRACTION_SOURCES = ("sfs_kernels.cu", "sfs_tc.cu", "sfs_tc16.cu", "sfs_tc16_dev.cuh", "sfs_internal.h",
+                       "sfs_launch.h", "sfs_async.cuh", "sfs_tcgen05.cuh", "sfs_fft.cuh", "sfs_planes.cuh")
 
 
 def kernel_source_hash():
