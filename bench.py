@@ -501,7 +501,8 @@ def serving_study(sfs, torch, args, flush, stream, seed):
     persistent = {"value": total * iters / (statistics.mean(tp) / 1e3), "solve_ms": statistics.mean(tp),
                   "latency_ms_p50": statistics.mean(tp), "latency_ms_p99": statistics.mean(tp),
                   "max_rel_diff_vs_grouped": agree, "tile_policy": policy,
-                  "step_ms_fwd_resid_adj_update": step_ms,
+                  "step_ms_fwd_resid_adj_update": step_ms[:4],
+                  "mean_cta_busy_ms_fwd_resid_adj_update": step_ms[4:],
                   "probe_ms_policies_0_1_2_4": probe_ms, "tile_tuning_s": t_ptune,
                   "note": "sfs_fista_persistent: one cooperative kernel runs all iterations of every class "
                           "(a grid barrier between the 4 steps of an iteration); every scene ends with the "

@@ -356,11 +356,12 @@ int sfs_autotune_persistent(int ngroups, sfs_operator* const* ops, const int32_t
 
 /*
  * Time of the four kinds of step of the latest sfs_fista_persistent solve of
- * the process, summed over its iterations (ms, host array of 4: forward
- * contractions, residual planes, adjoint contractions, update planes), as
- * CTA 0 sees them: each from the grid barrier that starts the step to the
- * one that ends it (the last update step to CTA 0's own end).  Waits for the
- * device.  Errors: SFS_ERR_INVALID_ARG (no such solve, or its graph was
+ * the process, summed over its iterations (ms, host array of 8: [0..3] the
+ * forward contractions, residual planes, adjoint contractions and update
+ * planes as CTA 0 sees them, each from the grid barrier that starts the step
+ * to the one that ends it, the last update step to CTA 0's own end; [4..7]
+ * the mean over CTAs of their busy time in the same steps, up to their
+ * arrival at the barrier).  Waits for the device.  Errors: SFS_ERR_INVALID_ARG (no such solve, or its graph was
  * evicted from the cache), SFS_ERR_CUDA.
  */
 int sfs_persistent_step_times(double* ms_out_host);

@@ -349,8 +349,9 @@ int persist_launch(const PersistPlan* pp, cudaStream_t st);
 void persist_free(PersistPlan* pp);
 void persist_shape(const PersistPlan* pp, int* grid, int* smem);
 // Time (ms) of the forward-contraction, residual-plane, adjoint-contraction
-// and update-plane steps summed over the iterations of the plan's latest run.
-int persist_step_ms(const PersistPlan* pp, double* ms4);
+// and update-plane steps summed over the iterations of the plan's latest run
+// (ms8[0..3]), and the mean over CTAs of their busy time in each (ms8[4..7]).
+int persist_step_ms(const PersistPlan* pp, double* ms8);
 
 // Batched building blocks (sfs_api.cu) used by the learned network
 // (sfs_lista.cu), on the operator's batched workspace:

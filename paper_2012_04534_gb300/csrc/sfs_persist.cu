@@ -61,16 +61,19 @@ struct PPlan {
   int ngroups, njobs, iters;
   const CUtensorMap* maps;
   const int2* job;              // contraction job: {group, scene tile}
-  const long long* cum_f;       // [njobs + 1] cumulative forward chunks (units x chunks per unit)
-  const long long* cum_a;       // [njobs + 1] cumulative adjoint chunks
+  const int4* ctask_f;          // forward contraction tasks {job, first unit, units, -}, largest first
+  const int4* ctask_a;          // adjoint contraction tasks
+  int nct_f, nct_a;
   const int* porder;            // [ngroups] groups in plane-task order (largest planes first)
   const long long* cum_r;       // [ngroups + 1] cumulative residual planes (scenes x bins), porder
   const long long* cum_u;       // [ngroups + 1] cumulative update planes (scenes x depths), porder
   const float* beta;            // [iters] momentum coefficients from t_1 = 1
   unsigned int* arrivals;       // grid barrier counter, zero at launch
-  unsigned int* tasks;          // [2 iters] plane-task counters of the steps, zero at launch
+  unsigned int* tasks;          // [4 iters] task counters of the steps, zero at launch
   unsigned long long* step_ns;  // [4] time of each kind of step summed over the iterations (CTA 0's
-                                //     view: from one barrier to the next), zero at launch
+                                //     view: from one barrier to the next), then [4] the CTAs' busy
+                                //     time in each kind of step (before their barrier arrival)
+                                //     summed over CTAs and iterations; zero at launch
   int* err;                     // set when a grid barrier wait gives up
   uint64_t wait_ns;
 };
@@ -121,24 +124,27 @@ __device__ bool grid_sync(const PPlan& p, unsigned int epoch) {
   return ok != 0;
 }
 
-// Step 1 or 3: this CTA's share of the chunks of every contraction job (a
-// chunk streams one table tile: the cost unit).  The CTA takes the units
-// whose first chunk lies in its share, so every unit has one owner.
+// The next task of step counter `ctr` for the whole CTA.
+__device__ __forceinline__ long long next_task(unsigned int* ctr) {
+  __shared__ unsigned int s_task;
+  __syncthreads();  // every thread has read the previous value
+  if (threadIdx.x == 0) s_task = atomicAdd(ctr, 1u);
+  __syncthreads();
+  return (long long)s_task;
+}
+
+// Step 1 or 3: contraction tasks (a run of units of one job, about the same
+// number of table chunks each, largest first) taken one at a time from the
+// step's counter.
 template <bool FWD>
-__device__ __forceinline__ void contract_step(const PParams& prm, unsigned char* smem) {
+__device__ __forceinline__ void contract_step(const PParams& prm, int k, unsigned char* smem) {
   const PPlan& p = prm.p;
-  const long long* cum = FWD ? p.cum_f : p.cum_a;
-  const long long T = cum[p.njobs];
-  const long long c0 = T * blockIdx.x / gridDim.x, c1 = T * (blockIdx.x + 1) / gridDim.x;
-  for (int j = 0; j < p.njobs; ++j) {
-    if (cum[j + 1] <= c0 || cum[j] >= c1) continue;
-    const int2 jb0 = p.job[j];
-    const int nchj = FWD ? prm.groups[jb0.x].nch_f : prm.groups[jb0.x].nch_a;
-    // units whose first chunk is in [c0, c1): ceil of both ends, relative to the job
-    const long long a = (max(c0, cum[j]) - cum[j] + nchj - 1) / nchj;
-    const long long e = (min(c1, cum[j + 1]) - cum[j] + nchj - 1) / nchj;
-    if (e <= a) continue;
-    const int2 jb = jb0;
+  const int4* tasks = FWD ? p.ctask_f : p.ctask_a;
+  const long long T = FWD ? p.nct_f : p.nct_a;
+  unsigned int* ctr = p.tasks + 4 * k + (FWD ? 0 : 2);
+  for (long long t = next_task(ctr); t < T; t = next_task(ctr)) {
+    const int4 tk = tasks[t];
+    const int2 jb = p.job[tk.x];
     const PGroup& g = prm.groups[jb.x];
     const int s0 = jb.y * g.NB;
     const int nscene = min(g.NB, g.d.batch - s0);
@@ -149,15 +155,14 @@ __device__ __forceinline__ void contract_step(const PParams& prm, unsigned char*
     const float* pm0 = FWD ? g.d.pm_x : g.d.pm_r;
     const float* pm = pm0 ? pm0 + s0 * (FWD ? g.d.bs_pmx : g.d.bs_pmr) : nullptr;
     const int nmt = FWD ? g.nmt_f : g.nmt_a, nch = FWD ? g.nch_f : g.nch_a;
-    const int first = (int)a, nu = (int)(e - a);
     if (g.NB == 1)
-      contract_h_run<FWD, 1, 1>(tab, spec, out, ostride, nscene, g.d, nmt, nch, first, nu, pm, g.err, smem,
+      contract_h_run<FWD, 1, 1>(tab, spec, out, ostride, nscene, g.d, nmt, nch, tk.y, tk.z, pm, g.err, smem,
                                 true);
     else if (g.NB == 2)
-      contract_h_run<FWD, 1, 2>(tab, spec, out, ostride, nscene, g.d, nmt, nch, first, nu, pm, g.err, smem,
+      contract_h_run<FWD, 1, 2>(tab, spec, out, ostride, nscene, g.d, nmt, nch, tk.y, tk.z, pm, g.err, smem,
                                 true);
     else
-      contract_h_run<FWD, 1, 4>(tab, spec, out, ostride, nscene, g.d, nmt, nch, first, nu, pm, g.err, smem,
+      contract_h_run<FWD, 1, 4>(tab, spec, out, ostride, nscene, g.d, nmt, nch, tk.y, tk.z, pm, g.err, smem,
                                 true);
   }
 }
@@ -170,14 +175,7 @@ __device__ __forceinline__ int group_of_task(const long long* cum, int ngroups, 
   return g;
 }
 
-// The next plane task of step counter `ctr` for the whole CTA.
-__device__ __forceinline__ long long next_task(unsigned int* ctr) {
-  __shared__ unsigned int s_task;
-  __syncthreads();  // every thread has read the previous value
-  if (threadIdx.x == 0) s_task = atomicAdd(ctr, 1u);
-  __syncthreads();
-  return (long long)s_task;
-}
+
 
 // The group's dimensions copied to shared memory for one plane task: the
 // plane steps then read them with shared-memory loads instead of holding
@@ -213,7 +211,7 @@ __device__ __noinline__ void update_plane_call(const PlaneDims& d, int z, long l
 __device__ __forceinline__ void resid_step(const PParams& prm, int k, float2* smem) {
   const PPlan& p = prm.p;
   const long long T = p.cum_r[p.ngroups];
-  for (long long t = next_task(p.tasks + 2 * k); t < T; t = next_task(p.tasks + 2 * k)) {
+  for (long long t = next_task(p.tasks + 4 * k + 1); t < T; t = next_task(p.tasks + 4 * k + 1)) {
     const int pos = group_of_task(p.cum_r, p.ngroups, t);
     const PGroup& g = prm.groups[p.porder[pos]];
     const PlaneDims& sd = stage_dims(g.d);
@@ -236,7 +234,7 @@ __device__ __forceinline__ void update_step(const PParams& prm, int k, float2* s
   const long long T = p.cum_u[p.ngroups];
   const float beta = p.beta[k];
   const int do_fwd = k + 1 < p.iters;
-  for (long long t = next_task(p.tasks + 2 * k + 1); t < T; t = next_task(p.tasks + 2 * k + 1)) {
+  for (long long t = next_task(p.tasks + 4 * k + 3); t < T; t = next_task(p.tasks + 4 * k + 3)) {
     const int pos = group_of_task(p.cum_u, p.ngroups, t);
     const PGroup& g = prm.groups[p.porder[pos]];
     const PlaneDims& sd = stage_dims(g.d);
@@ -259,27 +257,37 @@ __global__ void __launch_bounds__(kPThreads, 1) fista_persistent_kernel(const __
   unsigned int epoch = 0;
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   uint64_t t = timer ? global_ns() : 0;
-  auto mark = [&](int step) {  // CTA 0, after the barrier that ends a step
+  uint64_t busy[4] = {0, 0, 0, 0}, t_step = threadIdx.x == 0 ? global_ns() : 0;
+  auto done = [&](int step) {  // thread 0 of every CTA, at the end of its share of a step
+    if (threadIdx.x == 0) busy[step] += global_ns() - t_step;
+  };
+  auto mark = [&](int step) {  // after the barrier that ends a step
+    if (threadIdx.x == 0) t_step = global_ns();
     if (timer) {
-      const uint64_t now = global_ns();
-      p.step_ns[step] += now - t;
-      t = now;
+      p.step_ns[step] += t_step - t;
+      t = t_step;
     }
   };
   for (int k = 0; k < p.iters; ++k) {
-    contract_step<true>(prm, psm);
+    contract_step<true>(prm, k, psm);
+    done(0);
     if (!grid_sync(p, ++epoch)) return;
     mark(0);
     resid_step(prm, k, reinterpret_cast<float2*>(psm));
+    done(1);
     if (!grid_sync(p, ++epoch)) return;
     mark(1);
-    contract_step<false>(prm, psm);
+    contract_step<false>(prm, k, psm);
+    done(2);
     if (!grid_sync(p, ++epoch)) return;
     mark(2);
     update_step(prm, k, reinterpret_cast<float2*>(psm));
+    done(3);
     if (k + 1 < p.iters && !grid_sync(p, ++epoch)) return;
     mark(3);  // the last update step: CTA 0's own end
   }
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 4; ++i) atomicAdd(p.step_ns + 4 + i, (unsigned long long)busy[i]);
 }
 
 }  // namespace
@@ -325,7 +333,8 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
   memset(&pp->prm, 0, sizeof(pp->prm));
   std::vector<CUtensorMap> maps;
   std::vector<int2> jobs;
-  std::vector<long long> cum_f(1, 0), cum_a(1, 0), cum_r(1, 0), cum_u(1, 0);
+  std::vector<long long> cum_r(1, 0), cum_u(1, 0);
+  std::vector<int2> units_f, units_a;  // per job: {units, chunks per unit}
   int smem = 0;
   int rc = SFS_OK;
   for (int gi = 0; gi < ngroups && rc == SFS_OK; ++gi) {
@@ -368,8 +377,8 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
       maps.push_back(mx);
       maps.push_back(mr);
       jobs.push_back(make_int2(gi, j));
-      cum_f.push_back(cum_f.back() + (long long)nunits_f * g.nch_f);
-      cum_a.push_back(cum_a.back() + (long long)nunits_a * g.nch_a);
+      units_f.push_back(make_int2(nunits_f, g.nch_f));
+      units_a.push_back(make_int2(nunits_a, g.nch_a));
     }
     smem = std::max(smem, plan_smem(g.NB, d.Px));
   }
@@ -388,6 +397,33 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
     persist_free(pp);
     return rc;
   }
+  // contraction tasks: runs of units of about kTaskChunks table chunks
+  // (about four per CTA and step), largest first
+  int dev = 0, sms = 0, occ = 0;
+  {
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e0 != cudaSuccess) {
+      persist_free(pp);
+      return cuda_fail(e0, "SM count", __FILE__, __LINE__);
+    }
+  }
+  auto make_tasks = [&](const std::vector<int2>& units) {
+    long long total = 0;
+    for (const int2& u : units) total += (long long)u.x * u.y;
+    const long long target = std::max(1LL, (total + 4LL * sms - 1) / (4LL * sms));
+    std::vector<int4> t;
+    for (int j = 0; j < (int)units.size(); ++j) {
+      const int upt = (int)std::max(1LL, (target + units[j].y - 1) / units[j].y);
+      for (int u0 = 0; u0 < units[j].x; u0 += upt)
+        t.push_back(make_int4(j, u0, std::min(upt, units[j].x - u0), 0));
+    }
+    std::stable_sort(t.begin(), t.end(), [&](const int4& a, const int4& b) {
+      return (long long)a.z * units[a.x].y > (long long)b.z * units[b.x].y;
+    });
+    return t;
+  };
+  const std::vector<int4> ctf = make_tasks(units_f), cta = make_tasks(units_a);
   std::vector<float> beta(std::max(iters, 1));
   {
     double t = 1.0;
@@ -405,10 +441,10 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
   off = align_up(off + sizeof(int2) * jobs.size(), 64);
   const size_t o_po = off;
   off = align_up(off + sizeof(int) * porder.size(), 64);
-  const size_t o_cf = off;
-  off += sizeof(long long) * cum_f.size();
-  const size_t o_ca = off;
-  off += sizeof(long long) * cum_a.size();
+  const size_t o_tf = off;
+  off += sizeof(int4) * ctf.size();
+  const size_t o_ta = off;
+  off += sizeof(int4) * cta.size();
   const size_t o_cr = off;
   off += sizeof(long long) * cum_r.size();
   const size_t o_cu = off;
@@ -416,7 +452,7 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
   const size_t o_beta = off;
   off = align_up(off + sizeof(float) * beta.size(), 64);
   const size_t o_arr = off;  // step times, arrivals, then 2 iters task counters
-  const size_t counters = 4 * sizeof(unsigned long long) + sizeof(unsigned int) * (1 + 2 * (size_t)std::max(iters, 1));
+  const size_t counters = 8 * sizeof(unsigned long long) + sizeof(unsigned int) * (1 + 4 * (size_t)std::max(iters, 1));
   off += align_up(counters, 64);
   std::vector<unsigned char> host(off, 0);
   cudaError_t e = cudaMalloc(&pp->blob, off);
@@ -433,21 +469,23 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
   hp.maps = (const CUtensorMap*)(base + o_maps);
   hp.job = (const int2*)(base + o_jobs);
   hp.porder = (const int*)(base + o_po);
-  hp.cum_f = (const long long*)(base + o_cf);
-  hp.cum_a = (const long long*)(base + o_ca);
+  hp.ctask_f = (const int4*)(base + o_tf);
+  hp.ctask_a = (const int4*)(base + o_ta);
+  hp.nct_f = (int)ctf.size();
+  hp.nct_a = (int)cta.size();
   hp.cum_r = (const long long*)(base + o_cr);
   hp.cum_u = (const long long*)(base + o_cu);
   hp.beta = (const float*)(base + o_beta);
   hp.step_ns = (unsigned long long*)(base + o_arr);
-  hp.arrivals = (unsigned int*)(hp.step_ns + 4);
+  hp.arrivals = (unsigned int*)(hp.step_ns + 8);
   hp.tasks = hp.arrivals + 1;
   hp.err = ops[0]->ws.err;
   hp.wait_ns = ops[0]->wait_ns;
   memcpy(host.data() + o_maps, maps.data(), sizeof(CUtensorMap) * maps.size());
   memcpy(host.data() + o_jobs, jobs.data(), sizeof(int2) * jobs.size());
   memcpy(host.data() + o_po, porder.data(), sizeof(int) * porder.size());
-  memcpy(host.data() + o_cf, cum_f.data(), sizeof(long long) * cum_f.size());
-  memcpy(host.data() + o_ca, cum_a.data(), sizeof(long long) * cum_a.size());
+  memcpy(host.data() + o_tf, ctf.data(), sizeof(int4) * ctf.size());
+  memcpy(host.data() + o_ta, cta.data(), sizeof(int4) * cta.size());
   memcpy(host.data() + o_cr, cum_r.data(), sizeof(long long) * cum_r.size());
   memcpy(host.data() + o_cu, cum_u.data(), sizeof(long long) * cum_u.size());
   memcpy(host.data() + o_beta, beta.data(), sizeof(float) * beta.size());
@@ -461,11 +499,8 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
   pp->counters_bytes = counters;
   const void* kern = (const void*)fista_persistent_kernel;
   rc = ensure_smem_attr_ptr(kern, smem);
-  int dev = 0, sms = 0, occ = 0;
   if (rc == SFS_OK) {
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPThreads, smem);
     if (e != cudaSuccess) rc = cuda_fail(e, "persistent kernel occupancy", __FILE__, __LINE__);
   }
   if (rc == SFS_OK && occ < 1) {
@@ -508,10 +543,11 @@ void persist_shape(const PersistPlan* pp, int* grid, int* smem) {
   *smem = pp->smem;
 }
 
-int persist_step_ms(const PersistPlan* pp, double* ms4) {
-  unsigned long long ns[4];
+int persist_step_ms(const PersistPlan* pp, double* ms8) {
+  unsigned long long ns[8];
   SFS_CUDA(cudaMemcpy(ns, pp->prm.p.step_ns, sizeof(ns), cudaMemcpyDeviceToHost));
-  for (int i = 0; i < 4; ++i) ms4[i] = (double)ns[i] * 1e-6;
+  for (int i = 0; i < 4; ++i) ms8[i] = (double)ns[i] * 1e-6;
+  for (int i = 4; i < 8; ++i) ms8[i] = (double)ns[i] * 1e-6 / std::max(1, pp->grid);
   return SFS_OK;
 }
 

@@ -401,10 +401,10 @@ def fista_persistent(ops, ys, Ls, lam, iters, xs=None, stream=None, nb_policy=0)
 def persistent_step_times():
     """sfs_persistent_step_times: ms of the forward contractions, residual
     planes, adjoint contractions and update planes of the latest persistent
-    solve, summed over its iterations."""
-    out = (ctypes.c_double * 4)()
+    solve, summed over its iterations, then the mean CTA busy time in each."""
+    out = (ctypes.c_double * 8)()
     _check(lib().sfs_persistent_step_times(out))
-    return [out[i] for i in range(4)]
+    return [out[i] for i in range(8)]
 
 
 def autotune_persistent(ops, ys, Ls, lam, probe_iters=10, reps=3, xs=None, stream=None):

@@ -87,7 +87,8 @@ def test_persistent_equals_grouped(sfs):
     for g in range(len(ops)):
         assert np.array_equal(xp2[g], xp[g])
     st = sfs.persistent_step_times()
-    assert len(st) == 4 and all(v > 0 for v in st)
+    assert len(st) == 8 and all(v > 0 for v in st)
+    assert all(st[4 + i] <= st[i] * 1.05 + 1e-3 for i in range(3))  # busy within the step
     # every group with one scene per table tile: the same results
     xp1 = [to_host(x) for x in sfs.fista_persistent(ops, ys, Ls, -0.05, 40, nb_policy=1)]
     for g in range(len(ops)):
