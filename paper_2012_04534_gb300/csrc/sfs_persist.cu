@@ -397,8 +397,8 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
     persist_free(pp);
     return rc;
   }
-  // contraction tasks: runs of units of about kTaskChunks table chunks
-  // (about four per CTA and step), largest first
+  // contraction tasks: runs of units of about an eighth of a CTA's share of
+  // the step's table chunks, largest first
   int dev = 0, sms = 0, occ = 0;
   {
     cudaError_t e0 = cudaGetDevice(&dev);
@@ -411,7 +411,7 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
   auto make_tasks = [&](const std::vector<int2>& units) {
     long long total = 0;
     for (const int2& u : units) total += (long long)u.x * u.y;
-    const long long target = std::max(1LL, (total + 4LL * sms - 1) / (4LL * sms));
+    const long long target = std::max(1LL, (total + 8LL * sms - 1) / (8LL * sms));
     std::vector<int4> t;
     for (int j = 0; j < (int)units.size(); ++j) {
       const int upt = (int)std::max(1LL, (target + units[j].y - 1) / units[j].y);
