@@ -315,13 +315,12 @@ int sfs_fista_grouped(int ngroups, sfs_operator* const* ops, const int32_t* batc
  * the iteration loop of all groups in ONE persistent kernel: a cooperative
  * launch of one 512-thread CTA per SM that runs every iteration of
  * Algorithm 1 for every scene.  Per iteration it takes four steps over the
- * work of all groups at once: the forward contractions (every group's table
- * chunks of every scene tile, cut into equal contiguous shares per CTA, a
- * unit of chunks going to the CTA that holds its first chunk), the residual
- * planes (every group's scenes x bins, handed out one at a time from a
- * counter, groups with the largest planes first), the adjoint contractions
- * and the update planes (scenes x depths, likewise); the CTAs meet at a grid
- * barrier between steps.  The barrier waits are bounded (the operators' wait
+ * work of all groups at once: the forward contractions (every group's units
+ * of every scene tile, in runs of about equal table bytes, largest first),
+ * the residual planes (every group's scenes x bins, groups with the largest
+ * planes first), the adjoint contractions and the update planes (scenes x
+ * depths); each step's tasks are handed out one at a time from a counter,
+ * and the CTAs meet at a grid barrier between steps.  The barrier waits are bounded (the operators' wait
  * limit, 2 s by default); a CTA that gives up sets the first operator's
  * error flag (sfs_check_status then reports SFS_ERR_TIMEOUT) and the kernel
  * ends.  nb_policy sets the scenes per table tile of the contractions: 0

@@ -9,18 +9,19 @@
 //   3. adjoint contraction of the residual spectra;
 //   4. update planes: inverse FFT of the gradient, soft threshold, momentum,
 //      forward FFT of gamma_{k+1}.
-// One cooperative launch of one 512-thread CTA per SM runs all iterations.  Each step's work of all groups is one list: the table chunks
-// of every (group, scene tile) contraction, cut into equal contiguous shares
-// per CTA (a unit of chunks, whose accumulator lives in one CTA's tensor
-// memory, goes to the CTA holding its first chunk), and the planes of every
-// (group, scene), handed out one at a time from a counter per step, groups
-// with the largest planes first.  The CTAs meet at a grid barrier after each
-// step (a global arrival counter, waited on with a time limit: a CTA that
-// gives up sets the error flag and the kernel ends).  The contraction and
-// plane steps are the code of the standalone kernels (sfs_tc16_dev.cuh,
-// sfs_planes.cuh), so a persistent solve computes what the grouped one
-// computes, up to the plane engine variant (the cluster plane kernels of
-// sfs_kernels.cu add the inverse quadrant shares in another order).
+// One cooperative launch of one 512-thread CTA per SM runs all iterations.
+// Each step's work of all groups is one list of tasks handed out one at a
+// time from a counter per step: runs of contraction units of every (group,
+// scene tile) job of about equal table bytes (a unit's accumulator lives in
+// one CTA's tensor memory, so a unit is never split), largest first, or the
+// planes of every (group, scene), groups with the largest planes first.  The
+// CTAs meet at a grid barrier after each step (a global arrival counter,
+// waited on with a time limit: a CTA that gives up sets the error flag and
+// the kernel ends).  The contraction and plane steps are the code of the
+// standalone kernels (sfs_tc16_dev.cuh, sfs_planes.cuh), so a persistent
+// solve computes what the grouped one computes, up to the plane engine
+// variant (the cluster plane kernels of sfs_kernels.cu add the inverse
+// quadrant shares in another order).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
