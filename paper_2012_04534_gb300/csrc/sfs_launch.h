@@ -21,10 +21,12 @@ int ensure_smem_attr(K kernel, int need) {
 
 // Programmatic dependent launch is off unless SFS_PDL=1 is set in the
 // environment (read once per process).  Measured on GB300 with the graph-
-// replayed FISTA loop it was 4-5 % slower than plain stream order (vol32
-// 19,955 vs 20,887 iterations/s; vol64 1,593 vs 1,662), so the kernels keep
-// their pdl_wait / pdl_trigger points (no-ops without the launch attribute)
-// but are launched in plain stream order by default.
+// replayed FISTA loop it was 4-5 % slower than plain stream order with the
+// first kernels (vol32 19,955 vs 20,887 iterations/s; vol64 1,593 vs 1,662)
+// and is neutral with the current ones (vol64 FP32 2,408 vs 2,404, BF16
+// 3,674 vs 3,682), so the kernels keep their pdl_wait / pdl_trigger points
+// (no-ops without the launch attribute) but are launched in plain stream
+// order by default.
 bool pdl_enabled();
 
 // Priority given to the kernels this thread launches through launch_pdl (0:

@@ -202,11 +202,12 @@ def test_bf16_operator_info_and_table_bytes(sfs):
         sfs.Operator.from_indices(g, idx, precision=17)
 
 
-@pytest.mark.parametrize("mode", ["bf16", "fp16"])
+@pytest.mark.parametrize("mode", ["bf16", "fp16", "tf32x3"])
 def test_16bit_noalloc_adjoint_equals_adjoint(sfs, mode):
-    """sfs_apply_AH_noalloc on a 16-bit operator (spectra in the static
-    scratch, so the adjoint reads them through a tensor map encoded for that
-    array; FP16 also takes its spectra scale from the operator's maxima)."""
+    """sfs_apply_AH_noalloc on a tensor-core operator: 16-bit (spectra in the
+    static scratch, so the adjoint reads them through a tensor map encoded for
+    that array; FP16 also takes its spectra scale from the operator's maxima)
+    and TF32X3 (its bulk copies read the scratch directly)."""
     params = geom_params(Nx=12, Ny=10, Nz=36, dz=0.15e-3, Nt=256)
     g, op, go, idx = make_pair(sfs, params, mode, M=12, seed=5)
     import torch
