@@ -313,8 +313,8 @@ int sfs_fista_grouped(int ngroups, sfs_operator* const* ops, const int32_t* batc
 /*
  * The same solve (arguments, results and errors as sfs_fista_grouped) with
  * the iteration loop of all groups in ONE persistent kernel: a cooperative
- * launch of one 512-thread CTA per SM that runs every iteration of
- * Algorithm 1 for every scene.  Per iteration it takes four steps over the
+ * launch of one 1024-thread CTA per SM (two plane transforms at a time in
+ * plane steps) that runs every iteration of Algorithm 1 for every scene.  Per iteration it takes four steps over the
  * work of all groups at once: the forward contractions (every group's units
  * of every scene tile, in runs of about equal table bytes, largest first),
  * the residual planes (every group's scenes x bins, groups with the largest

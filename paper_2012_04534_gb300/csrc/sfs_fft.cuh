@@ -79,10 +79,34 @@ __host__ __device__ constexpr int pass_radix(int N, int Ns) {
   return (N / Ns) % 8 == 0 ? 8 : ((N / Ns) % 4 == 0 ? 4 : 2);
 }
 
+// Thread groups of the plane engine.  A plane is transformed by a group of
+// NT threads: the whole CTA of the plane kernels, or one of the equal groups
+// of a larger CTA (the persistent solve runs two 512-thread groups, one plane
+// each).  gtid<NT>() is the thread's index in its group, group_of<NT>() the
+// group, group_sync<NT>() the group's barrier (named barrier 2 or 3;
+// barriers 0 and 1 are left to whole-CTA and other uses).
+template <int NT>
+__device__ __forceinline__ int gtid() {
+  static_assert((NT & (NT - 1)) == 0 && NT >= 32, "group size");
+  return (int)threadIdx.x & (NT - 1);
+}
+template <int NT>
+__device__ __forceinline__ int group_of() {
+  return (int)threadIdx.x / NT;
+}
+template <int NT>
+__device__ __forceinline__ void group_sync() {
+  // immediate barrier numbers, so that a kernel reserves only the barriers it uses
+  if (threadIdx.x < NT)
+    asm volatile("bar.sync 2, %0;" ::"n"(NT) : "memory");
+  else
+    asm volatile("bar.sync 3, %0;" ::"n"(NT) : "memory");
+}
+
 // twiddle table: tw[m] = exp(-2 pi j m / N), m in [0, N)
 template <int N, int NT>
 __device__ __forceinline__ void make_twiddles(float2* tw) {
-  for (int m = threadIdx.x; m < N; m += NT) {
+  for (int m = gtid<NT>(); m < N; m += NT) {
     float s, c;
     sincospif(-2.0f * (float)m / (float)N, &s, &c);
     tw[m] = make_float2(c, s);
@@ -101,7 +125,7 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int count, int es,
   const int total = count * NB;
 #pragma unroll
   for (int i = 0; i < MAXB; ++i) {
-    const int b = threadIdx.x + i * NT;
+    const int b = gtid<NT>() + i * NT;
     if (b < total) {
       const int q = QFAST ? b % count : b / NB;
       const int j = QFAST ? b / count : b % NB;
@@ -110,10 +134,10 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int count, int es,
       for (int r = 0; r < R; ++r) v[i][r] = src[(j + r * NB) * es];
     }
   }
-  __syncthreads();
+  group_sync<NT>();
 #pragma unroll
   for (int i = 0; i < MAXB; ++i) {
-    const int b = threadIdx.x + i * NT;
+    const int b = gtid<NT>() + i * NT;
     if (b < total) {
       const int q = QFAST ? b % count : b / NB;
       const int j = QFAST ? b / count : b % NB;
@@ -134,7 +158,7 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int count, int es,
       for (int r = 0; r < R; ++r) dst[(base + r * Ns) * es] = v[i][r];
     }
   }
-  __syncthreads();
+  group_sync<NT>();
 }
 
 // Full FFT of length N on `count` sequences (all passes).
@@ -156,16 +180,16 @@ __device__ __forceinline__ void transpose_plane(float2* buf) {
   float2 v[PER];
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
-    const int e = threadIdx.x + i * NT;
+    const int e = gtid<NT>() + i * NT;
     if (e < P * P) v[i] = buf[(e / P) * LD + (e % P)];
   }
-  __syncthreads();
+  group_sync<NT>();
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
-    const int e = threadIdx.x + i * NT;
+    const int e = gtid<NT>() + i * NT;
     if (e < P * P) buf[(e % P) * LD + (e / P)] = v[i];
   }
-  __syncthreads();
+  group_sync<NT>();
 }
 
 // ---------------------------------------------------------------------------
@@ -269,7 +293,7 @@ struct PlaneFFT {
     const float2* tw64 = tw + P;
     float2* aux = const_cast<float2*>(tw) + NTW;
     const int lane = threadIdx.x & 31, l = lane >> 2;
-    const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
+    const int c = (gtid<NT>() >> 5) * 4 + (lane & 3);
     float2 s[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) s[j] = buf[(l + 8 * j) * LD + c];  // (y = l + 8 j, x = c)
@@ -283,7 +307,7 @@ struct PlaneFFT {
       // (the previous py's reads of aux came before the barriers of its last store)
 #pragma unroll
       for (int k = 0; k < 8; ++k) aux[c * LD + l + 8 * k] = v[k];
-      __syncthreads();
+      group_sync<NT>();
 #pragma unroll 1
       for (int px = 0; px < 2; ++px) {
         // along x for column ky' = c (rows x = l + 8 j): kx' = l + 8 k at row kx'
@@ -293,10 +317,10 @@ struct PlaneFFT {
           v[j] = px ? cmul(t, tw[l + 8 * j]) : t;
         }
         fft64_lanes<false>(v, tw64, l);
-        __syncthreads();  // the spatial reads, or the previous quadrant's store, are done
+        group_sync<NT>();  // the spatial reads, or the previous quadrant's store, are done
 #pragma unroll
         for (int k = 0; k < 8; ++k) buf[(l + 8 * k) * LD + c] = v[k];
-        __syncthreads();
+        group_sync<NT>();
         store(2 * py + px);
       }
     }
@@ -314,7 +338,7 @@ struct PlaneFFT {
     const float2* tw64 = tw + P;
     float2* aux = const_cast<float2*>(tw) + NTW;
     const int lane = threadIdx.x & 31, l = lane >> 2;
-    const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
+    const int c = (gtid<NT>() >> 5) * 4 + (lane & 3);
     float2 acc[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.f, 0.f);
@@ -323,9 +347,9 @@ struct PlaneFFT {
       float2 v[8];
 #pragma unroll 1
       for (int px = 0; px < 2; ++px) {
-        __syncthreads();  // earlier readers of buf (and, for px = 0, of aux) are done
+        group_sync<NT>();  // earlier readers of buf (and, for px = 0, of aux) are done
         load(2 * py + px);
-        __syncthreads();
+        group_sync<NT>();
         // along kx' for column ky' = c: x = l + 8 k, added transposed into aux
         // (row ky' = c, column x: slots this thread alone writes)
 #pragma unroll
@@ -337,7 +361,7 @@ struct PlaneFFT {
           *a = px ? cadd(*a, cmulc(tw[l + 8 * k], v[k])) : v[k];
         }
       }
-      __syncthreads();  // aux holds both quadrants of this py
+      group_sync<NT>();  // aux holds both quadrants of this py
       // along ky' for column x = c: y = l + 8 k
 #pragma unroll
       for (int j = 0; j < 8; ++j) v[j] = aux[(l + 8 * j) * LD + c];
@@ -348,7 +372,7 @@ struct PlaneFFT {
     // the last reads of buf came before the barrier above
 #pragma unroll
     for (int k = 0; k < 8; ++k) buf[(l + 8 * k) * LD + c] = acc[k];
-    __syncthreads();
+    group_sync<NT>();
   }
   // QUAD, one quadrant q (the cluster kernels, one CTA per quadrant):
   // load(q) fills buf[qidx(kx' 64 + ky')] with S_q; on return this thread's
@@ -362,18 +386,18 @@ struct PlaneFFT {
     static_assert(QUAD, "quadrant engine");
     const float2* tw64 = tw + P;
     const int lane = threadIdx.x & 31, l = lane >> 2;
-    const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
+    const int c = (gtid<NT>() >> 5) * 4 + (lane & 3);
     const int py = q >> 1, px = q & 1;
     load(q);
-    __syncthreads();
+    group_sync<NT>();
     float2 v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
-    __syncthreads();
+    group_sync<NT>();
     fft64_lanes<true>(v, tw64, l);
 #pragma unroll
     for (int k = 0; k < 8; ++k) buf[c * LD + l + 8 * k] = v[k];
-    __syncthreads();
+    group_sync<NT>();
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
     fft64_lanes<true>(v, tw64, l);
@@ -388,7 +412,7 @@ struct PlaneFFT {
     static_assert(QUAD, "quadrant engine");
     const float2* tw64 = tw + P;
     const int lane = threadIdx.x & 31, l = lane >> 2;
-    const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
+    const int c = (gtid<NT>() >> 5) * 4 + (lane & 3);
     const int py = q >> 1, px = q & 1;
     float2 v[8];
     // the twiddle in two factors, as forward_quads applies it, so that both
@@ -398,7 +422,7 @@ struct PlaneFFT {
     fft64_lanes<false>(v, tw64, l);
 #pragma unroll
     for (int k = 0; k < 8; ++k) buf[c * LD + l + 8 * k] = v[k];
-    __syncthreads();
+    group_sync<NT>();
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const float2 t = buf[(l + 8 * j) * LD + c];
@@ -407,7 +431,7 @@ struct PlaneFFT {
     fft64_lanes<false>(v, tw64, l);
 #pragma unroll
     for (int k = 0; k < 8; ++k) buf[(l + 8 * k) * LD + c] = v[k];
-    __syncthreads();
+    group_sync<NT>();
   }
 
   // wavenumber kappa (transposed order, kappa = kx*P + ky) of the plane
@@ -420,24 +444,24 @@ struct PlaneFFT {
   __device__ static __forceinline__ void forward(float2* buf, const float2* tw, int ncols) {
     if constexpr (LANES64) {
       const int lane = threadIdx.x & 31, l = lane >> 2;
-      const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
+      const int c = (gtid<NT>() >> 5) * 4 + (lane & 3);
       float2 v[8];
       // along y for column x = c; written transposed: row x, column ky
 #pragma unroll
       for (int j = 0; j < 8; ++j)
         v[j] = c < ncols ? buf[(l + 8 * j) * LD + c] : make_float2(0.f, 0.f);
-      __syncthreads();
+      group_sync<NT>();
       fft64_lanes<false>(v, tw, l);
 #pragma unroll
       for (int k = 0; k < 8; ++k) buf[c * LD + l + 8 * k] = v[k];
-      __syncthreads();
+      group_sync<NT>();
       // along x for column ky = c: result kx = l + 8 k at row kx (own column only)
 #pragma unroll
       for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
       fft64_lanes<false>(v, tw, l);
 #pragma unroll
       for (int k = 0; k < 8; ++k) buf[(l + 8 * k) * LD + c] = v[k];
-      __syncthreads();
+      group_sync<NT>();
     } else if constexpr (TWO_D) {
       fft_multi<P, false, NT, P, true>(buf, ncols, LD, 1, tw);   // along y
       transpose_plane<P, LD, NT>(buf);
@@ -451,16 +475,16 @@ struct PlaneFFT {
   __device__ static __forceinline__ void inverse(float2* buf, const float2* tw, int ncols) {
     if constexpr (LANES64) {
       const int lane = threadIdx.x & 31, l = lane >> 2;
-      const int c = (threadIdx.x >> 5) * 4 + (lane & 3);
+      const int c = (gtid<NT>() >> 5) * 4 + (lane & 3);
       float2 v[8];
       // along kx for column ky = c; written transposed: row ky, column x
 #pragma unroll
       for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
-      __syncthreads();
+      group_sync<NT>();
       fft64_lanes<true>(v, tw, l);
 #pragma unroll
       for (int k = 0; k < 8; ++k) buf[c * LD + l + 8 * k] = v[k];
-      __syncthreads();
+      group_sync<NT>();
       // along ky for column x = c: result y = l + 8 k at row y (own column only)
 #pragma unroll
       for (int j = 0; j < 8; ++j) v[j] = buf[(l + 8 * j) * LD + c];
@@ -469,7 +493,7 @@ struct PlaneFFT {
 #pragma unroll
         for (int k = 0; k < 8; ++k) buf[(l + 8 * k) * LD + c] = v[k];
       }
-      __syncthreads();
+      group_sync<NT>();
     } else if constexpr (TWO_D) {
       fft_multi<P, true, NT, P, true>(buf, P, LD, 1, tw);        // kx -> x
       transpose_plane<P, LD, NT>(buf);

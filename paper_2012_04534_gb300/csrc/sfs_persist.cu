@@ -9,7 +9,10 @@
 //   3. adjoint contraction of the residual spectra;
 //   4. update planes: inverse FFT of the gradient, soft threshold, momentum,
 //      forward FFT of gamma_{k+1}.
-// One cooperative launch of one 512-thread CTA per SM runs all iterations.
+// One cooperative launch of one 1024-thread CTA per SM runs all iterations:
+// its warps 0-6 run the contraction roles in contraction steps, and in plane
+// steps its two 512-thread groups each transform their own plane (named
+// barriers per group, their own shared memory).
 // Each step's work of all groups is one list of tasks handed out one at a
 // time from a counter per step: runs of contraction units of every (group,
 // scene tile) job of about equal table bytes (a unit's accumulator lives in
@@ -41,7 +44,14 @@
 namespace sfs {
 namespace {
 
-constexpr int kPThreads = 512;  // the plane engines' CTA; warps 0-6 run the contraction roles
+constexpr int kPlaneThreads = 512;                 // one plane group (a plane engine)
+constexpr int kPGroups = 2;                         // plane groups per CTA
+constexpr int kPThreads = kPGroups * kPlaneThreads;  // warps 0-6 run the contraction roles
+// shared memory of one plane group: the largest run-time plane (128 x 128 as
+// quadrants), rounded to 128 bytes
+constexpr int kPlaneSmem = (PlaneFFT<128, true>::SMEM + 127) / 128 * 128;
+static_assert(PlaneFFT<64, true>::SMEM <= kPlaneSmem && PlaneFFT<32, true>::SMEM <= kPlaneSmem,
+              "plane group shared memory");
 
 // One group as the kernel reads it (device memory).
 struct PGroup {
@@ -178,18 +188,30 @@ __device__ __forceinline__ int group_of_task(const long long* cum, int ngroups, 
 
 
 
-// The group's dimensions copied to shared memory for one plane task: the
-// plane steps then read them with shared-memory loads instead of holding
-// constant-bank copies in registers.  Called by every thread.
+// The next plane task of step counter `ctr` for this thread's plane group.
+__device__ __forceinline__ long long next_group_task(unsigned int* ctr) {
+  __shared__ unsigned int s_gtask[kPGroups];
+  const int grp = group_of<kPlaneThreads>();
+  group_sync<kPlaneThreads>();  // the group has read the previous value
+  if (gtid<kPlaneThreads>() == 0) s_gtask[grp] = atomicAdd(ctr, 1u);
+  group_sync<kPlaneThreads>();
+  return (long long)s_gtask[grp];
+}
+
+// The group's dimensions copied to shared memory for one plane task of this
+// thread's plane group: the plane steps then read them with shared-memory
+// loads instead of holding constant-bank copies in registers.  Called by
+// every thread of the plane group.
 __device__ __forceinline__ const PlaneDims& stage_dims(const PlaneDims& d) {
-  __shared__ __align__(16) PlaneDims sd;
+  __shared__ __align__(16) PlaneDims sd[kPGroups];
   static_assert(sizeof(PlaneDims) % 4 == 0, "word copy");
-  __syncthreads();  // earlier readers of sd are done
+  const int grp = group_of<kPlaneThreads>();
+  group_sync<kPlaneThreads>();  // earlier readers of sd[grp] are done
   const uint32_t* src = reinterpret_cast<const uint32_t*>(&d);
-  uint32_t* dst = reinterpret_cast<uint32_t*>(&sd);
-  for (int i = threadIdx.x; i < (int)(sizeof(PlaneDims) / 4); i += blockDim.x) dst[i] = src[i];
-  __syncthreads();
-  return sd;
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&sd[grp]);
+  for (int i = gtid<kPlaneThreads>(); i < (int)(sizeof(PlaneDims) / 4); i += kPlaneThreads) dst[i] = src[i];
+  group_sync<kPlaneThreads>();
+  return sd[grp];
 }
 
 // The plane steps as separate functions, so that each keeps the register
@@ -207,12 +229,14 @@ __device__ __noinline__ void update_plane_call(const PlaneDims& d, int z, long l
                              nullptr);
 }
 
-// Step 2: residual planes of every (group, scene, bin); each CTA takes the
-// next task from the step's counter, largest planes first.
+// Step 2: residual planes of every (group, scene, bin); each plane group of
+// the CTA takes the next task from the step's counter, largest planes first,
+// in its own part of the shared memory (smem: that part).
 __device__ __forceinline__ void resid_step(const PParams& prm, int k, float2* smem) {
   const PPlan& p = prm.p;
   const long long T = p.cum_r[p.ngroups];
-  for (long long t = next_task(p.tasks + 4 * k + 1); t < T; t = next_task(p.tasks + 4 * k + 1)) {
+  unsigned int* ctr = p.tasks + 4 * k + 1;
+  for (long long t = next_group_task(ctr); t < T; t = next_group_task(ctr)) {
     const int pos = group_of_task(p.cum_r, p.ngroups, t);
     const PGroup& g = prm.groups[p.porder[pos]];
     const PlaneDims& sd = stage_dims(g.d);
@@ -225,7 +249,7 @@ __device__ __forceinline__ void resid_step(const PParams& prm, int k, float2* sm
       resid_plane_call<64>(sd, u, b, smem, g);
     else
       resid_plane_call<32>(sd, u, b, smem, g);
-    __syncthreads();  // the next plane reuses the shared memory
+    group_sync<kPlaneThreads>();  // the next plane reuses the shared memory
   }
 }
 
@@ -235,7 +259,8 @@ __device__ __forceinline__ void update_step(const PParams& prm, int k, float2* s
   const long long T = p.cum_u[p.ngroups];
   const float beta = p.beta[k];
   const int do_fwd = k + 1 < p.iters;
-  for (long long t = next_task(p.tasks + 4 * k + 3); t < T; t = next_task(p.tasks + 4 * k + 3)) {
+  unsigned int* ctr = p.tasks + 4 * k + 3;
+  for (long long t = next_group_task(ctr); t < T; t = next_group_task(ctr)) {
     const int pos = group_of_task(p.cum_u, p.ngroups, t);
     const PGroup& g = prm.groups[p.porder[pos]];
     const PlaneDims& sd = stage_dims(g.d);
@@ -248,7 +273,7 @@ __device__ __forceinline__ void update_step(const PParams& prm, int k, float2* s
       update_plane_call<64>(sd, z, b, smem, g, beta, do_fwd);
     else
       update_plane_call<32>(sd, z, b, smem, g, beta, do_fwd);
-    __syncthreads();
+    group_sync<kPlaneThreads>();
   }
 }
 
@@ -274,7 +299,7 @@ __global__ void __launch_bounds__(kPThreads, 1) fista_persistent_kernel(const __
     done(0);
     if (!grid_sync(p, ++epoch)) return;
     mark(0);
-    resid_step(prm, k, reinterpret_cast<float2*>(psm));
+    resid_step(prm, k, reinterpret_cast<float2*>(psm + group_of<kPlaneThreads>() * kPlaneSmem));
     done(1);
     if (!grid_sync(p, ++epoch)) return;
     mark(1);
@@ -282,7 +307,7 @@ __global__ void __launch_bounds__(kPThreads, 1) fista_persistent_kernel(const __
     done(2);
     if (!grid_sync(p, ++epoch)) return;
     mark(2);
-    update_step(prm, k, reinterpret_cast<float2*>(psm));
+    update_step(prm, k, reinterpret_cast<float2*>(psm + group_of<kPlaneThreads>() * kPlaneSmem));
     done(3);
     if (k + 1 < p.iters && !grid_sync(p, ++epoch)) return;
     mark(3);  // the last update step: CTA 0's own end
@@ -309,11 +334,9 @@ namespace {
 
 size_t align_up(size_t off, size_t a) { return (off + a - 1) / a * a; }
 
-int plan_smem(int NB, int P) {
+int plan_smem(int NB) {
   const int c = NB == 1 ? HPlan<1, 1>::kSmem : NB == 2 ? HPlan<1, 2>::kSmem : HPlan<1, 4>::kSmem;
-  const int pl = P == 128 ? PlaneFFT<128, true>::SMEM : P == 64 ? PlaneFFT<64, true>::SMEM
-                                                                : PlaneFFT<32, true>::SMEM;
-  return std::max(c, pl);
+  return std::max(c, kPGroups * kPlaneSmem);
 }
 
 }  // namespace
@@ -381,7 +404,7 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
       units_f.push_back(make_int2(nunits_f, g.nch_f));
       units_a.push_back(make_int2(nunits_a, g.nch_a));
     }
-    smem = std::max(smem, plan_smem(g.NB, d.Px));
+    smem = std::max(smem, plan_smem(g.NB));
   }
   // plane tasks: groups with the largest planes first, so that the last
   // tasks a step hands out are the short ones

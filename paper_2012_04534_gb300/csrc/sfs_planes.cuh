@@ -20,12 +20,13 @@ namespace {
 // ---------------------------------------------------------------------------
 template <int NT>
 __device__ __forceinline__ void block_add_double(double v, double* out) {
-  __shared__ double part[NT / 32];
+  __shared__ double part_g[2][NT / 32];  // per thread group (at most two per CTA)
+  double* part = part_g[group_of<NT>()];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = gtid<NT>() >> 5, lane = threadIdx.x & 31;
   if (lane == 0) part[warp] = v;
-  __syncthreads();
+  group_sync<NT>();
   if (warp == 0) {
     v = lane < NT / 32 ? part[lane] : 0.0;
 #pragma unroll
@@ -42,12 +43,13 @@ __device__ __forceinline__ float nanmax(float a, float b) {
 
 template <int NT>
 __device__ __forceinline__ void block_max_bits(float v, unsigned int* out) {
-  __shared__ float part[NT / 32];
+  __shared__ float part_g[2][NT / 32];
+  float* part = part_g[group_of<NT>()];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, off));
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = gtid<NT>() >> 5, lane = threadIdx.x & 31;
   if (lane == 0) part[warp] = v;
-  __syncthreads();
+  group_sync<NT>();
   if (warp == 0) {
     v = lane < NT / 32 ? part[lane] : 0.0f;
 #pragma unroll
@@ -62,12 +64,13 @@ __device__ __forceinline__ void block_max_bits(float v, unsigned int* out) {
 // ignored here; it still reaches the output through the values themselves).
 template <int NT>
 __device__ __forceinline__ void block_max_store(float v, float* out) {
-  __shared__ float part[NT / 32];
+  __shared__ float part_g[2][NT / 32];
+  float* part = part_g[group_of<NT>()];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = gtid<NT>() >> 5, lane = threadIdx.x & 31;
   if (lane == 0) part[warp] = v;
-  __syncthreads();
+  group_sync<NT>();
   if (warp == 0) {
     v = lane < NT / 32 ? part[lane] : 0.0f;
 #pragma unroll
@@ -82,7 +85,7 @@ __device__ __forceinline__ void block_max_store(float v, float* out) {
 template <int P, bool TWO_D>
 __device__ __forceinline__ void zero_plane(float2* buf) {
   using F = PlaneFFT<P, TWO_D>;
-  for (int e = threadIdx.x; e < F::ELEMS; e += F::NT) buf[e] = make_float2(0.f, 0.f);
+  for (int e = gtid<F::NT>(); e < F::ELEMS; e += F::NT) buf[e] = make_float2(0.f, 0.f);
 }
 
 // Twiddles of the plane engine (QUAD: W_128, then W_64 for the quadrants).
@@ -110,7 +113,7 @@ __device__ __forceinline__ void load_quadrant_fwd(float2* buf, const float2* __r
   const float2* src = Yp + (size_t)u * d.Ns;
   const size_t stride = (size_t)d.Up * d.Ns;
   const int i1 = __ldg(d.quad + q + 1);
-  for (int i0 = __ldg(d.quad + q) + threadIdx.x; i0 < i1; i0 += kQuadBatch * F::NT) {
+  for (int i0 = __ldg(d.quad + q) + gtid<F::NT>(); i0 < i1; i0 += kQuadBatch * F::NT) {
     int ent[kQuadBatch];
     float2 v[kQuadBatch];
 #pragma unroll
@@ -139,7 +142,7 @@ __device__ __forceinline__ void load_quadrant_adj(float2* buf, const float2* __r
   const int zb = z / d.azb, zr = z % d.azb;
   const size_t slot_stride = (size_t)d.azb * 64;
   const int i1 = __ldg(d.quad + q + 1);
-  for (int i0 = __ldg(d.quad + q) + threadIdx.x; i0 < i1; i0 += kQuadBatchAdj * F::NT) {
+  for (int i0 = __ldg(d.quad + q) + gtid<F::NT>(); i0 < i1; i0 += kQuadBatchAdj * F::NT) {
     int ent[kQuadBatchAdj];
     int2 sc[kQuadBatchAdj];
 #pragma unroll
@@ -180,7 +183,7 @@ __device__ __forceinline__ void store_quadrant(const float2* buf, float2* __rest
   using F = PlaneFFT<P, TWO_D>;
   const int32_t* ql = d.quad + 8;
   const int i1 = __ldg(d.quad + q + 1);
-  for (int i0 = __ldg(d.quad + q) + threadIdx.x; i0 < i1; i0 += kQuadBatch * F::NT) {
+  for (int i0 = __ldg(d.quad + q) + gtid<F::NT>(); i0 < i1; i0 += kQuadBatch * F::NT) {
     int ent[kQuadBatch];
 #pragma unroll
     for (int k = 0; k < kQuadBatch; ++k) {
@@ -225,7 +228,7 @@ __device__ __forceinline__ void load_spectrum_fwd(float2* buf, const float2* __r
   constexpr int LB = load_batch<P, TWO_D>();
   const float2* src = Yp + (size_t)u * d.Ns;
   const size_t stride = (size_t)d.Up * d.Ns;
-  for (int j0 = threadIdx.x; j0 < d.Ns; j0 += LB * F::NT) {
+  for (int j0 = gtid<F::NT>(); j0 < d.Ns; j0 += LB * F::NT) {
     int kap[LB];
     float2 v[LB];
 #pragma unroll
@@ -257,7 +260,7 @@ __device__ __forceinline__ void load_spectrum_adj(float2* buf, const float2* __r
   constexpr int LB = load_batch<P, TWO_D>();
   const int zb = z / d.azb, zr = z % d.azb;
   const size_t slot_stride = (size_t)d.azb * 64;
-  for (int j0 = threadIdx.x; j0 < d.Ns; j0 += LB * F::NT) {
+  for (int j0 = gtid<F::NT>(); j0 < d.Ns; j0 += LB * F::NT) {
     int kap[LB];
     int2 sc[LB];
 #pragma unroll
@@ -299,7 +302,7 @@ __device__ __forceinline__ void store_spectrum(const float2* buf, float2* __rest
   using F = PlaneFFT<P, TWO_D>;
   constexpr int LB = load_batch<P, TWO_D>();
   float mx = 0.0f;
-  for (int j0 = threadIdx.x; j0 < d.Ns; j0 += LB * F::NT) {
+  for (int j0 = gtid<F::NT>(); j0 < d.Ns; j0 += LB * F::NT) {
     int kap[LB];
 #pragma unroll
     for (int k = 0; k < LB; ++k) {
@@ -326,7 +329,7 @@ __device__ __forceinline__ void zero_outside(float2* buf, int Ny, int Nx) {
   using F = PlaneFFT<P, TWO_D>;
   constexpr int PX = F::QUAD ? 64 : P;
   constexpr int PY = F::QUAD ? 64 : (TWO_D ? P : 1);
-  for (int e = threadIdx.x; e < PX * PY; e += F::NT) {
+  for (int e = gtid<F::NT>(); e < PX * PY; e += F::NT) {
     const int py = e / PX, px = e % PX;
     if (py >= Ny || px >= Nx) buf[F::sidx(py, px)] = make_float2(0.f, 0.f);
   }
@@ -360,7 +363,7 @@ __device__ __forceinline__ void load_inverse_fwd(float2* buf, const float2* tw, 
     F::inverse_quads(buf, tw, [&](int q) { load_quadrant_fwd<P, TWO_D>(buf, Yp, u, d, q); });
   } else {
     load_spectrum_fwd<P, TWO_D>(buf, Yp, u, d);
-    __syncthreads();
+    group_sync<F::NT>();
     F::inverse(buf, tw, d.Nx);
   }
 }
@@ -374,7 +377,7 @@ __device__ __forceinline__ void load_inverse_adj(float2* buf, const float2* tw, 
     F::inverse_quads(buf, tw, [&](int q) { load_quadrant_adj<P, TWO_D>(buf, Gs, segslot, z, d, q); });
   } else {
     load_spectrum_adj<P, TWO_D>(buf, Gs, segslot, z, d);
-    __syncthreads();
+    group_sync<F::NT>();
     F::inverse(buf, tw, d.Nx);
   }
 }
@@ -404,7 +407,7 @@ __device__ __forceinline__ void resid_plane_step(const PlaneDims& d, int u, long
   double acc = 0.0;
   const int32_t* pm = posmap + (size_t)u * d.S;
   const float2* yu = yplane + (size_t)u * d.S;
-  for (int s = threadIdx.x; s < d.S; s += F::NT) {
+  for (int s = gtid<F::NT>(); s < d.S; s += F::NT) {
     const int m = pm[s];
     const float2 yv = yu[s];
     const int e = F::sidx(s / d.Nx, s % d.Nx);
@@ -417,7 +420,7 @@ __device__ __forceinline__ void resid_plane_step(const PlaneDims& d, int u, long
   }
   zero_outside<P, TWO_D>(buf, d.Ny, d.Nx);
   if (red_sumsq) block_add_double<F::NT>(acc, red_sumsq);
-  __syncthreads();
+  group_sync<F::NT>();
   forward_store<P, TWO_D>(buf, tw, Rh + (size_t)u * d.Ns, d, d.pm_r ? d.pm_r + b * d.bs_pmr + u : nullptr);
 }
 
@@ -453,7 +456,7 @@ __device__ __forceinline__ void update_plane_step(const PlaneDims& d, int z, lon
   const float beta = beta_dev ? *beta_dev : beta_arg;
   double l1 = 0.0;
   const size_t off = (size_t)z * d.Ny * d.Nx;
-  for (int e = threadIdx.x; e < d.Ny * d.Nx; e += F::NT) {
+  for (int e = gtid<F::NT>(); e < d.Ny * d.Nx; e += F::NT) {
     const int bi = F::sidx(e / d.Nx, e % d.Nx);
     const float2 g = buf[bi];
     const float2 gm = gam[off + e];
@@ -471,7 +474,7 @@ __device__ __forceinline__ void update_plane_step(const PlaneDims& d, int z, lon
   if (red_l1) block_add_double<F::NT>(l1, red_l1);
   if (!do_fwd) return;
   zero_outside<P, TWO_D>(buf, d.Ny, d.Nx);
-  __syncthreads();
+  group_sync<F::NT>();
   forward_store<P, TWO_D>(buf, tw, Xh + (size_t)z * d.Ns, d, d.pm_x ? d.pm_x + b * d.bs_pmx + z : nullptr);
 }
 
