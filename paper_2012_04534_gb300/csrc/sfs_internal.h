@@ -347,7 +347,6 @@ int persist_build(int ngroups, sfs_operator* const* ops, const PlaneDims* dims, 
                   PersistPlan** out);
 int persist_launch(const PersistPlan* pp, cudaStream_t st);
 void persist_free(PersistPlan* pp);
-void persist_shape(const PersistPlan* pp, int* grid, int* smem);
 // Time (ms) of the forward-contraction, residual-plane, adjoint-contraction
 // and update-plane steps summed over the iterations of the plan's latest run
 // (ms8[0..3]), and the mean over CTAs of their busy time in each (ms8[4..7]).

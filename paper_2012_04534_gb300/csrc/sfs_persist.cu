@@ -562,11 +562,6 @@ void persist_free(PersistPlan* pp) {
   delete pp;
 }
 
-void persist_shape(const PersistPlan* pp, int* grid, int* smem) {
-  *grid = pp->grid;
-  *smem = pp->smem;
-}
-
 int persist_step_ms(const PersistPlan* pp, double* ms8) {
   unsigned long long ns[8];
   SFS_CUDA(cudaMemcpy(ns, pp->prm.p.step_ns, sizeof(ns), cudaMemcpyDeviceToHost));
