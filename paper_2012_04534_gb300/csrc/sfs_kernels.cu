@@ -607,7 +607,10 @@ struct PairAcc {
 // re_2p+1, im_2p, im_2p+1) one table word; real hr xr - hi xi, imag hr xi +
 // hi xr.  Scalar FMAs: with the spectra of 8 depth pairs held in registers
 // the packed form needs more registers than the 2-CTA budget leaves and
-// measured slower.
+// measured slower.  A packed form that keeps only one bin's sums live (bin
+// by bin, FFMA2 over the two depths of a pair, real part as sum hr xr - sum
+// hi xi, 122-125 registers, no spills) was slower too: vol64 forward 210.8
+// against 160.6 us, vol32 22.5 against 18.4 us.
 __device__ __forceinline__ void fwd_mac(float4& a, const float4 h4, const PairX& x) {
   a.x = fmaf(h4.x, x.ra.x, a.x); a.x = fmaf(-h4.z, x.ia.x, a.x);
   a.x = fmaf(h4.y, x.ra.y, a.x); a.x = fmaf(-h4.w, x.ia.y, a.x);
