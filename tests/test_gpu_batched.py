@@ -136,6 +136,32 @@ def test_batched_fp32_fista_matches_oracle(sfs):
         assert rel_err(xw[b], rw) <= 1e-4
 
 
+@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+def test_largest_batch(sfs, mode):
+    """SFS_MAX_BATCH scenes in one batched call (the 16-bit kernels' last
+    table tile full, 64 tiles of 4): sampled scenes (first, ragged middle,
+    last) equal their single-scene A, A^H and FISTA."""
+    B = sfs.SFS_MAX_BATCH
+    params = geom_params(Nx=8, Ny=6, Nz=12, dz=0.15e-3, Nt=128)
+    go = oracle_geometry(params)
+    idx = O.select_indices(go, O.SEL_RANDOM, 6, True, 31)
+    g = sfs.Geometry(**params)
+    op = sfs.Operator.from_indices(g, idx, precision=sfs.PRECISION_NAMES[mode])
+    rng = np.random.default_rng(32)
+    x = crandn(rng, B, g.Nz, g.Ny, g.Nx)
+    y = crandn(rng, B, g.S, 6)
+    yb = to_host(op.apply_A_batched(to_dev(x)))
+    xb = to_host(op.apply_AH_batched(to_dev(y)))
+    L, _ = op.lipschitz(max_iter=200, rtol=1e-6, seed=1, safety=1e-3)
+    fb = to_host(op.fista_batched(to_dev(y), -0.05, L, 15))
+    for b in (0, 1, 77, 130, B - 2, B - 1):
+        assert rel_err(yb[b], to_host(op.apply_A(to_dev(x[b])))) <= 1e-6
+        assert rel_err(xb[b], to_host(op.apply_AH(to_dev(y[b])))) <= 1e-6
+        fs = to_host(op.fista(to_dev(y[b]), -0.05, L, 15))
+        assert np.abs(fs).max() > 0
+        assert rel_err(fb[b], fs) <= 1e-5
+
+
 def test_batched_invalid_arguments(sfs):
     import ctypes
     import torch

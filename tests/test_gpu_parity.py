@@ -238,6 +238,39 @@ def test_fista_mu_rule_warm_start_and_monitor(sfs):
     assert np.all(to_host(op.fista(to_dev(y), big, L, 20)) == 0)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_fista_recovers_isolated_scatterers_noiseless_on_gpu(sfs, prec):
+    """Noiseless data of isolated scatterers (at least 4 voxels apart) and a
+    small mu: the 4 largest magnitudes of the GPU iterate sit exactly on the
+    true positions (the recovery the oracle is pinned by, here through the
+    C ABI, Algorithm 1 with the mu rule evaluated on the device)."""
+    params = geom_params(Nx=10, Ny=10, Nz=16, dz=0.15e-3, Nt=256)
+    go = oracle_geometry(params)
+    idx = O.select_indices(go, O.SEL_RANDOM, 16, True, 77)
+    g = sfs.Geometry(**params)
+    op = sfs.Operator.from_indices(g, idx, precision=sfs.PRECISION_NAMES[prec])
+    x_true = synth.scene(op.shape_x, 4, "unit", seed=13, min_sep=4)
+    y = O.LateralFFTOperator(go, idx).apply_A(x_true)
+    L, _ = op.lipschitz(max_iter=2000, rtol=1e-9, seed=1, safety=1e-3)
+    x = to_host(op.fista(to_dev(y), -0.02, L, 400))
+    top = np.argsort(np.abs(x).ravel())[-4:]
+    assert set(top.tolist()) == set(np.nonzero(x_true.ravel())[0].tolist())
+
+
+def test_fista_on_zero_data_stays_zero(sfs):
+    """y = 0: the mu rule gives lambda = 0 and the gradient is zero at
+    x = 0, so every iterate is exactly zero (no division by lambda or by a
+    norm of the data anywhere on the path)."""
+    params = geom_params(Nx=12, Ny=10, Nz=20, dz=0.15e-3, Nt=128)
+    g = sfs.Geometry(**params)
+    op = sfs.Operator.select(g, O.SEL_RANDOM, 8, True, 3)
+    y = np.zeros(op.shape_y, complex)
+    for lam in (-0.05, 0.0, 0.1):
+        x = to_host(op.fista(to_dev(y), lam, 1.0, 25))
+        assert np.all(x == 0), lam
+    assert op.max_abs_AH(to_dev(y)) == 0.0
+
+
 @pytest.mark.parametrize("case", [
     ("fp32", dict(Nx=10, Ny=10, Nz=16, dz=0.15e-3, Nt=256), 12),
     ("fp16", dict(Nx=10, Ny=10, Nz=16, dz=0.15e-3, Nt=256), 12),

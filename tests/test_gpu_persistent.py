@@ -101,6 +101,37 @@ def test_persistent_equals_grouped(sfs):
         assert op.check_status() == 0
 
 
+def test_largest_group_count(sfs):
+    """SFS_MAX_GROUPS groups (operators of a few small geometries and depths,
+    one or two scenes each) in one grouped and one persistent solve: every
+    scene agrees between the two and with its operator's own batched solve."""
+    G = sfs.SFS_MAX_GROUPS
+    ops, ys, Ls = [], [], []
+    rng = np.random.default_rng(55)
+    for k in range(G):
+        Nx, Ny = (6, 6) if k % 3 == 0 else (10, 8) if k % 3 == 1 else (20, 18)
+        params = geom_params(Nx=Nx, Ny=Ny, Nz=8 + 4 * (k % 4), dz=0.15e-3, Nt=128)
+        go = oracle_geometry(params)
+        M = 4 + k % 5
+        idx = O.select_indices(go, O.SEL_RANDOM, M, True, 500 + k)
+        g = sfs.Geometry(**params)
+        op = sfs.Operator.from_indices(g, idx, precision=sfs.SFS_PREC_BF16)
+        op._geom = g
+        ops.append(op)
+        Ls.append(op.lipschitz(max_iter=100, rtol=1e-5, seed=1, safety=1e-2)[0])
+        ys.append(to_dev(crandn(rng, 1 + k % 2, op.S, M)))
+    xg = [to_host(x) for x in sfs.fista_grouped(ops, ys, Ls, -0.05, 12)]
+    xp = [to_host(x) for x in sfs.fista_persistent(ops, ys, Ls, -0.05, 12)]
+    for k in (0, 1, 2, 31, G - 1):
+        xb = to_host(ops[k].fista_batched(ys[k], -0.05, Ls[k], 12))
+        assert np.abs(xb).max() > 0
+        assert rel_err(xg[k], xb) <= 1e-5, k
+    for k in range(G):
+        assert rel_err(xp[k], xg[k]) <= 1e-4, k
+    for op in ops:
+        assert op.check_status() == 0
+
+
 def test_persistent_one_group_matches_oracle(sfs):
     geo, M = dict(Nx=24, Ny=20, Nz=12, Nt=256), 10
     params = geom_params(dz=0.15e-3, **geo)
