@@ -479,6 +479,32 @@ def serving_study(sfs, torch, args, flush, stream, seed):
     ts.sort()
     lat.sort()
     total = sum(counts)
+    # the other priority orders of the grouped graph (same kernels, same
+    # results): throughput and latency of 2 solves each
+    orders = {}
+    for name, order in (("largest_first", sfs.SFS_GROUPED_LARGEST_FIRST),
+                        ("no_priority", sfs.SFS_GROUPED_NO_PRIORITY)):
+        sfs.set_grouped_order(order)
+        try:
+            xo = sfs.fista_grouped(ops, ys, Ls, -0.05, iters)  # graph capture for this order
+            torch.cuda.synchronize()
+            to, lo = [], []
+            for _ in range(2):
+                flush.fill_(3)
+                a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sfs.fista_grouped(ops, ys, Ls, -0.05, iters, xs=xo)
+                b2.record(stream)
+                torch.cuda.synchronize()
+                to.append(a.elapsed_time(b2))
+                for t_g, n in zip(sfs.grouped_times(len(ops)), counts):
+                    lo += [t_g] * n
+            same = all(torch.equal(p_, g_) for p_, g_ in zip(xo, xs))
+        finally:
+            sfs.set_grouped_order(sfs.SFS_GROUPED_CHEAPEST_FIRST)
+        orders[name] = {"value": total * iters / (statistics.mean(to) / 1e3), "solve_ms": statistics.mean(to),
+                        "latency_ms_p50": float(np.percentile(lo, 50)),
+                        "latency_ms_p99": float(np.percentile(lo, 99)), "results_identical": same}
     # the same solve with the loops of all classes in one persistent kernel
     xg = [x.clone() for x in xs]
     t2 = time.perf_counter()
@@ -514,7 +540,9 @@ def serving_study(sfs, torch, args, flush, stream, seed):
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
             "latency_note": "per scene: from the start of the grouped call to the end of its class's loop "
                             "(event-record node in the graph), over 3 solves",
-            "setup_s": t_setup, "autotune_s": t_tune, "tiles_chosen": tiles, "persistent": persistent,
+            "setup_s": t_setup, "autotune_s": t_tune, "tiles_chosen": tiles,
+            "priority_order": "cheapest_first (sfs_set_grouped_order default)", "other_orders": orders,
+            "persistent": persistent,
             "mix": "grids {16,32,48,64}^2, depths {64,128,256}, M {32,64,128}, 10 scatterers, 20 dB"}
 
 

@@ -296,9 +296,10 @@ int sfs_fista_batched(sfs_operator* op, int batch, const void* y_dev, double lam
  * device), measurements y_dev[g] ([batch][S_g][M_g]), Lipschitz constant
  * L[g], results x_out_dev[g] ([batch][V_g]).  The iteration loops of all
  * groups run as one CUDA graph launch, one forked stream per group, so small
- * groups share the GPU.  The graph runs with per-node priorities: a group's
- * kernels get a higher priority the less work its iteration does (scenes x
- * bins x slots x depths), so that small groups finish first.  lambda as in
+ * groups share the GPU.  The graph runs with per-node priorities set by
+ * sfs_set_grouped_order (by default a group's kernels get a higher priority
+ * the less work its iteration does, scenes x bins x slots x depths, so that
+ * small groups finish first).  lambda as in
  * sfs_fista_batched (lambda < 0: mu rule per scene).  The graph is captured on the first call for a set of
  * (operators, batch sizes, iterations) and replayed afterwards (a process-
  * wide cache of 16 graphs, oldest evicted first).  1 <= ngroups <=
@@ -309,6 +310,23 @@ int sfs_fista_batched(sfs_operator* op, int batch, const void* y_dev, double lam
 int sfs_fista_grouped(int ngroups, sfs_operator* const* ops, const int32_t* batch,
                       const void* const* y_dev, const double* L, double lambda, int iters,
                       void* const* x_out_dev, void* stream);
+
+/*
+ * Order of the kernel priorities of the graphs sfs_fista_grouped captures
+ * from now on in this process (a graph already cached for another order is
+ * not reused): SFS_GROUPED_CHEAPEST_FIRST (default) ranks the groups by the
+ * work of their iteration, least work highest, which lowers the median
+ * latency; SFS_GROUPED_LARGEST_FIRST ranks them the other way, so that the
+ * longest loops start first (the longest-processing-time rule, which aims at
+ * the shortest makespan); SFS_GROUPED_NO_PRIORITY gives every kernel the
+ * default priority.  The order changes only which ready kernel the GPU
+ * starts first: every group's arithmetic, and so its result, is the same
+ * bit for bit.  Errors: SFS_ERR_INVALID_ARG for another value.
+ */
+#define SFS_GROUPED_CHEAPEST_FIRST 0
+#define SFS_GROUPED_LARGEST_FIRST 1
+#define SFS_GROUPED_NO_PRIORITY 2
+int sfs_set_grouped_order(int order);
 
 /*
  * The same solve (arguments, results and errors as sfs_fista_grouped) with

@@ -664,6 +664,8 @@ cudaEvent_t g_grouped_start = nullptr;
 int g_grouped_last_n = 0;
 // key of the latest persistent solve's cache entry (sfs_persistent_step_times)
 std::vector<uint64_t> g_last_persist_key;
+// priority order of the grouped graphs captured next (sfs_set_grouped_order)
+std::atomic<int> g_grouped_order{SFS_GROUPED_CHEAPEST_FIRST};
 
 // Adds an entry to the cache (g_grouped_mu held), evicting the oldest.
 void cache_grouped(const GroupedEntry& ent) {
@@ -677,7 +679,8 @@ void cache_grouped(const GroupedEntry& ent) {
 
 int grouped_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch, int iters,
                   cudaGraphExec_t* out) {
-  std::vector<uint64_t> key = {(uint64_t)iters, (uint64_t)ngroups};
+  const int order_kind = g_grouped_order.load();
+  std::vector<uint64_t> key = {(uint64_t)iters, (uint64_t)ngroups | ((uint64_t)order_kind << 48)};
   for (int g = 0; g < ngroups; ++g) {
     key.push_back(ops[g]->uid);
     key.push_back(ops[g]->bws_gen);
@@ -708,17 +711,19 @@ int grouped_graph(int ngroups, sfs_operator* const* ops, const int32_t* batch, i
     g_done_events.push_back(e3);
   }
   for (int g = 0; g < ngroups; ++g) SFS_TRY(prepare_kernels(batch_dims(ops[g], batch[g])));
-  // kernel priorities: the cheaper a group's iteration (scenes x bins x slots
-  // x depths), the higher, so that small groups finish early instead of
-  // with the large ones
+  // kernel priorities ranked by the work of a group's iteration (scenes x
+  // bins x slots x depths): by default the cheaper, the higher, so that small
+  // groups finish early instead of with the large ones; or the larger, the
+  // higher (longest loops first); or none
   std::vector<int> prio(ngroups, 0);
-  {
+  if (order_kind != SFS_GROUPED_NO_PRIORITY) {
     int least = 0, greatest = 0;
     SFS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
     std::vector<int> order(ngroups);
     for (int g = 0; g < ngroups; ++g) order[g] = g;
     auto cost = [&](int g) {
-      return (double)batch[g] * ops[g]->U * ops[g]->Ns * ops[g]->geo.d.Nz;
+      const double c = (double)batch[g] * ops[g]->U * ops[g]->Ns * ops[g]->geo.d.Nz;
+      return order_kind == SFS_GROUPED_LARGEST_FIRST ? -c : c;
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) < cost(b); });
     const int levels = least - greatest + 1;
@@ -1845,6 +1850,16 @@ int grouped_results(int ngroups, sfs_operator* const* ops, const int32_t* batch,
 }
 
 }  // namespace
+
+int sfs_set_grouped_order(int order) {
+  if (order != SFS_GROUPED_CHEAPEST_FIRST && order != SFS_GROUPED_LARGEST_FIRST &&
+      order != SFS_GROUPED_NO_PRIORITY) {
+    set_error("grouped order %d (0 cheapest first, 1 largest first, 2 no priority)", order);
+    return SFS_ERR_INVALID_ARG;
+  }
+  g_grouped_order.store(order);
+  return SFS_OK;
+}
 
 int sfs_fista_grouped(int ngroups, sfs_operator* const* ops, const int32_t* batch,
                       const void* const* y_dev, const double* L, double lambda, int iters,

@@ -47,6 +47,10 @@ PRECISION_NAMES = {"fp32": SFS_PREC_FP32, "tf32x3": SFS_PREC_TF32X3, "bf16": SFS
 SFS_MAX_BATCH = 256
 SFS_MAX_GROUPS = 64
 
+SFS_GROUPED_CHEAPEST_FIRST = 0
+SFS_GROUPED_LARGEST_FIRST = 1
+SFS_GROUPED_NO_PRIORITY = 2
+
 SFS_FISTA_WARM_START = 1
 SFS_FISTA_TIME_KERNELS = 2
 SFS_FISTA_RESUME = 4
@@ -67,6 +71,7 @@ EXPORTS = ("sfs_create_geometry", "sfs_destroy_geometry", "sfs_select_indices",
            "sfs_fista_grouped", "sfs_fista_persistent", "sfs_autotune_persistent", "sfs_persistent_step_times", "sfs_crb", "sfs_mixing_band", "sfs_mixing_create", "sfs_mixing_destroy",
            "sfs_apply_A_mixed", "sfs_apply_AH_mixed", "sfs_lipschitz_mixed", "sfs_fista_mixed",
            "sfs_autotune_batch", "sfs_set_batch_tile", "sfs_fista_backtracking", "sfs_grouped_times",
+           "sfs_set_grouped_order",
            "sfs_lipschitz", "sfs_fista", "sfs_kernel_times", "sfs_stage_times",
            "sfs_set_wait_timeout_ns", "sfs_shard_run", "sfs_operator_shard", "sfs_normal_residual",
            "sfs_prox_momentum", "sfs_vec_sumsq", "sfs_vec_max_abs", "sfs_vec_scale", "sfs_vec_randn",
@@ -147,6 +152,7 @@ def lib():
         "sfs_set_batch_tile": [vp, i32, i32],
         "sfs_fista_backtracking": [vp, vp, dbl, dbl, dbl, i32, vp, P(dbl), vp],
         "sfs_grouped_times": [i32, P(ctypes.c_float)],
+        "sfs_set_grouped_order": [i32],
         "sfs_apply_A_mixed": [vp, vp, vp, vp],
         "sfs_apply_AH_mixed": [vp, vp, vp, vp],
         "sfs_lipschitz_mixed": [vp, i32, dbl, u64, dbl, P(dbl), vp],
@@ -416,6 +422,12 @@ def autotune_persistent(ops, ys, Ls, lam, probe_iters=10, reps=3, xs=None, strea
     _check(lib().sfs_autotune_persistent(n, oph, b, yp, Lv, float(lam), int(probe_iters), int(reps), xp,
                                          ctypes.byref(c), ms, _stream_ptr(stream, ys[0].device)))
     return c.value, [ms[i] for i in range(4)]
+
+
+def set_grouped_order(order):
+    """sfs_set_grouped_order: priority order of the grouped graphs captured
+    from now on (SFS_GROUPED_CHEAPEST_FIRST, _LARGEST_FIRST, _NO_PRIORITY)."""
+    _check(lib().sfs_set_grouped_order(int(order)))
 
 
 def grouped_times(n):

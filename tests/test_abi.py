@@ -38,6 +38,17 @@ def test_library_exports_every_declared_symbol(sfs):
     assert "sm_103a" in sfs.sfs_version()
 
 
+def test_grouped_order_setter(sfs):
+    """sfs_set_grouped_order takes the three documented orders and refuses
+    any other value (host logic, no device work)."""
+    for bad in (-1, 3, 100):
+        with pytest.raises(sfs.SfsError) as ei:
+            sfs.set_grouped_order(bad)
+        assert ei.value.status == sfs.SFS_ERR_INVALID_ARG
+    for order in (sfs.SFS_GROUPED_LARGEST_FIRST, sfs.SFS_GROUPED_NO_PRIORITY, sfs.SFS_GROUPED_CHEAPEST_FIRST):
+        sfs.set_grouped_order(order)
+
+
 def test_geometry_validation(sfs):
     ok = geom_params(Nx=8, Ny=8, Nz=4, dz=1e-4, Nt=64)
     g = sfs.Geometry(**ok)

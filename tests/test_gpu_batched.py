@@ -215,6 +215,41 @@ def test_grouped_solve_equals_per_operator_batched_solves(sfs):
         sfs.fista_grouped([ops[0], ops[0]], [ys[0], ys[0]], [Ls[0], Ls[0]], -0.05, 5)
 
 
+def test_grouped_priority_orders_give_identical_results(sfs):
+    """The three priority orders of the grouped graph (cheapest first,
+    largest first, none) schedule the same kernels: every scene's result is
+    the same bit for bit, and each order captures its own graph."""
+    import torch
+    specs = [(dict(Nx=24, Ny=1, Nz=40, Nt=256), 12, 2, "fp32"),
+             (dict(Nx=10, Ny=8, Nz=20, Nt=128), 10, 3, "bf16"),
+             (dict(Nx=20, Ny=18, Nz=33, Nt=256), 16, 2, "bf16")]
+    ops, ys, Ls = [], [], []
+    rng = np.random.default_rng(43)
+    for k, (geo, M, B, mode) in enumerate(specs):
+        params = geom_params(dz=0.15e-3, **geo)
+        go = oracle_geometry(params)
+        idx = O.select_indices(go, O.SEL_RANDOM, M, True, 80 + k)
+        g = sfs.Geometry(**params)
+        op = sfs.Operator.from_indices(g, idx, precision=sfs.PRECISION_NAMES[mode])
+        op._geom = g
+        ops.append(op)
+        Ls.append(op.lipschitz(max_iter=200, rtol=1e-6, seed=1, safety=1e-3)[0])
+        ys.append(to_dev(crandn(rng, B, op.S, M)))
+    outs = []
+    try:
+        for order in (sfs.SFS_GROUPED_CHEAPEST_FIRST, sfs.SFS_GROUPED_LARGEST_FIRST,
+                      sfs.SFS_GROUPED_NO_PRIORITY):
+            sfs.set_grouped_order(order)
+            outs.append([x.clone() for x in sfs.fista_grouped(ops, ys, Ls, -0.05, 20)])
+            assert len(sfs.grouped_times(len(ops))) == len(ops)
+    finally:
+        sfs.set_grouped_order(sfs.SFS_GROUPED_CHEAPEST_FIRST)
+    assert any(float(x.abs().max()) > 0 for x in outs[0])
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("mode", ["bf16", "fp16"])
 def test_batch_tile_choice_keeps_results_and_autotune_picks_one(sfs, mode):
     """Five scenes with one table tile serving 1, 2 or 4 of them: each
