@@ -227,6 +227,25 @@ def test_dense_A_with_directivity_equals_time_domain_echo():
         assert np.linalg.norm(y[s * 12:(s + 1) * 12] - ref) <= 1e-10 * np.linalg.norm(ref)
 
 
+def test_directivity_depends_on_the_angle_only():
+    """Directivity reading of Sec. VI (the printed form is not dimensionless):
+    the characteristic is a function of the angle atan(r / z) between the
+    beam axis and the scatterer alone, equal to 1 straight below the
+    transducer and to 1/e at the beam half-angle theta, at every depth and
+    lateral direction; theta = 0 switches it off.  The echo pins above use
+    the same routine on both sides, so this is its independent pin."""
+    th = math.radians(25.0)
+    for z in (5e-3, 12e-3, 30e-3):
+        assert O.directivity(1e-3, 2e-3, 1e-3, 2e-3, z, th) == 1.0
+        r = z * math.tan(th)
+        for dx, dy in ((r, 0.0), (0.0, -r), (r / math.sqrt(2.0), r / math.sqrt(2.0))):
+            assert O.directivity(1e-3 + dx, 2e-3 + dy, 1e-3, 2e-3, z, th) == pytest.approx(math.exp(-1.0), rel=1e-12)
+        a = O.directivity(0.3 * z, 0.0, 0.0, 0.0, z, th)
+        b = O.directivity(0.6 * z, 0.0, 0.0, 0.0, 2.0 * z, th)
+        assert 0.0 < a < 1.0 and a == pytest.approx(b, rel=1e-12)
+    assert O.directivity(1e-3, 0.0, 0.0, 0.0, 10e-3, 0.0) == 1.0
+
+
 def test_A_cols_equal_time_domain_echo_of_one_scatterer():
     """Column v of A is the kept-bin DFT of the simulated echo of a unit
     scatterer at voxel v, at every position (directivity on); the columns
