@@ -328,3 +328,187 @@ def test_unmutated_oracle_passes_the_same_pins():
                     P.test_random_subset_uniform_chi_square,
                     P.test_splitmix64_matches_published_outputs,
                     P.test_contiguous_is_centred_on_peak_and_equispaced_spread]) == []
+
+
+# ------------------------------------------- Cramér-Rao bound oracle ---
+
+import oracle.crb_oracle as CO  # noqa: E402
+import tests.test_crb_oracle_pins as PC  # noqa: E402
+
+
+def _jacobian(delay=lambda c: 2.0 / c, dlng_z_sign=1.0):
+    """data_jacobian with the delay derivative's factor 2/c replaced by
+    delay(c), or the sign of the directivity's depth derivative
+    flipped: the two ways the paper's printed derivative can be misread."""
+    def jac(g, idx, p, amp, phase, params=CO.PARAMS):
+        idx = np.asarray(idx)
+        M = idx.shape[1]
+        s, m = np.divmod(np.arange(idx.size), M)
+        f = g.bin_freq(idx[s, m])
+        xs, ys = g.scan_xy()
+        xs, ys = xs[s], ys[s]
+        x1, y1, z1 = (float(v) for v in p)
+        b = CO.scatterer_data(g, idx, p, amp, phase)
+        R = np.sqrt((x1 - xs) ** 2 + (y1 - ys) ** 2 + z1 ** 2)
+        k = delay(g.c)
+        dtau = {"x": k * (x1 - xs) / R, "y": k * (y1 - ys) / R, "z": k * z1 / R}
+        if g.theta > 0.0:
+            w2 = (z1 * math.tan(g.theta)) ** 2
+            r2 = (x1 - xs) ** 2 + (y1 - ys) ** 2
+            dlng = {"x": -2.0 * (x1 - xs) / w2, "y": -2.0 * (y1 - ys) / w2,
+                    "z": dlng_z_sign * 2.0 * r2 / (z1 ** 3 * math.tan(g.theta) ** 2)}
+        else:
+            dlng = {"x": 0.0 * R, "y": 0.0 * R, "z": 0.0 * R}
+        cols = []
+        for q in params:
+            if q in "xyz":
+                cols.append(b * (dlng[q] - 2j * np.pi * f * dtau[q]))
+            elif q == "a":
+                cols.append(b / amp)
+            else:
+                cols.append(1j * b)
+        return np.stack(cols, axis=1)
+    return jac
+
+
+def test_unmutated_jacobian_copy_passes():
+    """The copy used for the two mutations below, unmutated, passes the
+    pins, so their failures come from the planted change."""
+    mp = pytest.MonkeyPatch()
+    try:
+        mp.setattr(CO, "data_jacobian", _jacobian())
+        assert failing([PC.test_jacobian_equals_finite_differences_of_the_data,
+                        PC.test_single_ascan_depth_bound_is_the_delay_bound]) == []
+    finally:
+        mp.undo()
+
+
+def test_crb_delay_derivative_with_c_over_2_is_caught(monkeypatch):
+    """d tau / d x with c/2 where 2/c belongs (the printed form)."""
+    monkeypatch.setattr(CO, "data_jacobian", _jacobian(delay=lambda c: 0.5 * c))
+    assert_caught([PC.test_jacobian_equals_finite_differences_of_the_data])
+
+
+def test_crb_directivity_depth_derivative_sign_is_caught(monkeypatch):
+    monkeypatch.setattr(CO, "data_jacobian", _jacobian(dlng_z_sign=-1.0))
+    assert_caught([PC.test_jacobian_equals_finite_differences_of_the_data])
+
+
+def test_fisher_information_without_the_factor_2_is_caught(monkeypatch):
+    orig = CO.fisher_information
+    monkeypatch.setattr(CO, "fisher_information", lambda *a, **kw: 0.5 * orig(*a, **kw))
+    assert_caught([PC.test_single_ascan_depth_bound_is_the_delay_bound])
+
+
+def test_crb_from_the_inverted_diagonal_is_caught(monkeypatch):
+    """1 / J_ii instead of (J^-1)_ii: ignores the coupling of depth and phase."""
+    def wrong(g, idx, p, amp, phase, sigma2, params=CO.PARAMS):
+        J = CO.fisher_information(g, idx, p, amp, phase, sigma2, params)
+        c = np.full(3, np.nan)
+        for i, q in enumerate(params):
+            if q in "xyz":
+                c["xyz".index(q)] = 1.0 / J[i, i]
+        return c, J
+    monkeypatch.setattr(CO, "crb", wrong)
+    assert_caught([PC.test_single_ascan_depth_bound_is_the_delay_bound])
+
+
+# ------------------------------------------------ Rademacher mixing ---
+
+import oracle.mixing_oracle as XO  # noqa: E402
+import tests.test_mixing_oracle_pins as PX  # noqa: E402
+
+
+def test_mixing_matrix_with_transposed_index_is_caught(monkeypatch):
+    """Xi[(k_u - k_m) mod Nt] instead of Xi[(k_m - k_u) mod Nt]."""
+    def wrong(xi, kept, band, Nt):
+        Xi = np.fft.fft(np.asarray(xi, dtype=np.float64))
+        kept = np.asarray(kept, dtype=np.int64)
+        band = np.asarray(band, dtype=np.int64)
+        return Xi[(band[None, :] - kept[:, None]) % Nt] / Nt
+    monkeypatch.setattr(XO, "mixing_matrix", wrong)
+    assert_caught([PX.test_mixing_matrix_is_the_time_domain_definition,
+                   PX.test_mixed_operator_is_the_time_domain_chain])
+
+
+def test_mixing_matrix_without_1_over_Nt_is_caught(monkeypatch):
+    orig = XO.mixing_matrix
+    monkeypatch.setattr(XO, "mixing_matrix", lambda xi, kept, band, Nt: Nt * orig(xi, kept, band, Nt))
+    assert_caught([PX.test_mixing_matrix_is_the_time_domain_definition, PX.test_no_mixing_is_plain_selection])
+
+
+def test_mixing_over_the_nonnegative_half_spectrum_is_caught(monkeypatch):
+    """The band-limited reading: only bins 0 .. Nt/2 of the A-scan enter
+    the mixing, the negative frequencies dropped."""
+    monkeypatch.setattr(XO, "full_band", lambda Nt: np.arange(0, Nt // 2 + 1, dtype=np.int64))
+    assert_caught([PX.test_mixed_operator_is_the_time_domain_chain])
+
+
+def test_mixed_adjoint_without_the_conjugate_is_caught(monkeypatch):
+    def wrong(self, y):
+        rb = np.einsum("smu,sm->su", self.Mix, np.asarray(y, dtype=np.complex128))
+        return self.A_band.apply_AH(rb)
+    monkeypatch.setattr(XO.MixedOperator, "apply_AH", wrong)
+    assert_caught([PX.test_mixed_operator_equals_dense_and_is_adjoint])
+
+
+# ------------------------------------------------- learned ISTA oracle ---
+
+import oracle.lista_oracle as LO  # noqa: E402
+import tests.test_lista_oracle_pins as PL  # noqa: E402
+
+
+def test_conv3d_as_convolution_is_caught(monkeypatch):
+    """The kernel flipped (a true convolution instead of the correlation)."""
+    orig = LO.conv3d
+    monkeypatch.setattr(LO, "conv3d", lambda u, W, b=None: orig(u, W[:, :, ::-1, ::-1, ::-1], b))
+    assert_caught([PL.test_conv3d_equals_scipy_correlate])
+
+
+def test_conv3d_transpose_with_unflipped_shift_is_caught(monkeypatch):
+    """The adjoint convolution reading the same window as the forward."""
+    def wrong(gout, W):
+        cout, nz, ny, nx = gout.shape
+        gp = np.zeros((cout, nz + 2, ny + 2, nx + 2))
+        gp[:, 1:-1, 1:-1, 1:-1] = gout
+        gin = np.zeros((W.shape[1], nz, ny, nx))
+        for dz in range(3):
+            for dy in range(3):
+                for dx in range(3):
+                    sl = gp[:, dz:dz + nz, dy:dy + ny, dx:dx + nx]
+                    gin += np.einsum("oi,ozyx->izyx", W[:, :, dz, dy, dx], sl)
+        return gin
+    monkeypatch.setattr(LO, "conv3d_transpose", wrong)
+    assert_caught([PL.test_conv3d_transpose_and_weight_grad_are_adjoints])
+
+
+def test_lista_soft_threshold_without_the_phase_is_caught(monkeypatch):
+    def wrong(z, theta):
+        mag = np.abs(z)
+        return np.where(mag > theta, mag - theta, 0.0).astype(np.complex128)
+    monkeypatch.setattr(LO, "soft", wrong)
+    assert_caught([PL.test_zero_prox_network_is_ista])
+
+
+def test_lista_backward_without_the_normal_operator_is_caught(monkeypatch):
+    """The gradient passed to the previous layer without the -(eta/L)
+    A^H A term of the gradient step (apply_AH o apply_A treated as zero)."""
+    orig = LO.backward
+
+    def wrong(apply_A, apply_AH, params, layers, cache, grad_x):
+        return orig(apply_A, lambda r: 0.0 * apply_AH(r), params, layers, cache, grad_x)
+    monkeypatch.setattr(LO, "backward", wrong)
+    assert_caught([PL.test_backward_matches_central_differences])
+
+
+def test_unmutated_mixing_crb_and_lista_oracles_pass_the_same_pins():
+    assert failing([PX.test_mixing_matrix_is_the_time_domain_definition,
+                    PX.test_no_mixing_is_plain_selection,
+                    PX.test_mixed_operator_is_the_time_domain_chain,
+                    PX.test_mixed_operator_equals_dense_and_is_adjoint,
+                    PC.test_jacobian_equals_finite_differences_of_the_data,
+                    PC.test_single_ascan_depth_bound_is_the_delay_bound,
+                    PL.test_conv3d_equals_scipy_correlate,
+                    PL.test_conv3d_transpose_and_weight_grad_are_adjoints,
+                    PL.test_zero_prox_network_is_ista,
+                    PL.test_backward_matches_central_differences]) == []
