@@ -613,7 +613,7 @@ def learned_study(sfs, torch, args, stream, seed):
     nmse_lista = mean_nmse(xs)
     ladder = []
     reach = None
-    for K in (4, 8, 16, 32, 64, 128, 160, 192, 224, 256, 300):
+    for K in (4, 8, 16, 32, 64, 128, 160, 192, 224, 256, 272, 288, 300):
         ms_k, xk = timed(lambda y, K=K: op.fista_batched(y, -w["mu"], L, K))
         nm = mean_nmse(xk)
         ladder.append({"iters": K, "nmse_db": nm, "ms_per_batch": ms_k})
@@ -629,7 +629,7 @@ def learned_study(sfs, torch, args, stream, seed):
 
     warm = []
     warm_reach = None
-    for K in (0, 8, 16, 32, 48, 64, 96, 128, 160, 192, 224, 256, 300):
+    for K in (0, 8, 16, 32, 48, 64, 96, 128, 136, 144, 152, 160, 192, 224, 256, 300):
         ms_k, xk = timed(lambda y, K=K: net_then_fista(y, K))
         nm = mean_nmse(xk)
         warm.append({"fista_iters": K, "nmse_db": nm, "ms_per_batch": ms_k})
