@@ -107,6 +107,12 @@ def test_printed_directivity_form_is_caught(monkeypatch):
     assert_caught([P.test_directivity_depends_on_the_angle_only])
 
 
+def test_time_gate_without_the_envelope_margin_is_caught(monkeypatch):
+    """t0 at the earliest echo itself, without the three envelope widths."""
+    plant(monkeypatch, "auto_t0", lambda g: math.floor((2.0 * g.z0 / g.c) * g.fs) / g.fs)
+    assert_caught([(P.test_time_gate_holds_every_echo, "vol32")])
+
+
 # ------------------------------------------ dense operator and the DFT ---
 
 def test_dense_A_without_the_time_gate_is_caught(monkeypatch):
@@ -314,6 +320,7 @@ def test_unmutated_oracle_passes_the_same_pins():
                     P.test_dense_A_equals_dft_of_time_domain_echo,
                     P.test_dense_A_with_directivity_equals_time_domain_echo,
                     P.test_single_scatterer_below_position_closed_form,
+                    (P.test_time_gate_holds_every_echo, "vol32"),
                     P.test_directivity_depends_on_the_angle_only,
                     P.test_lateral_shift_invariance,
                     P.test_multilevel_toeplitz_matches_printed_example,

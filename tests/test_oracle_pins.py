@@ -192,6 +192,23 @@ def test_random_subset_uniform_chi_square():
 
 # ------------------------------------------------------- dense operator ---
 
+@pytest.mark.parametrize("name", ["line2d", "vol32", "vol64"])
+def test_time_gate_holds_every_echo(name):
+    """Time-gate reading (t0 is not given for the workloads): t0 lies on the
+    sample grid, at least three envelope widths 1/alpha before the earliest
+    echo (the closest voxel straight below a transducer) and within one sample
+    of that bound; the window t0 .. t0 + Nt/fs reaches three widths past the
+    latest echo (the deepest voxel at the far corner), so no echo wraps."""
+    g = O.Geometry(**synth.geometry_params(name))
+    n0 = g.t0 * g.fs
+    assert abs(n0 - round(n0)) <= 1e-6
+    first = 2.0 * g.z0 / g.c - 3.0 / g.alpha
+    assert first - 1.0 / g.fs < g.t0 <= first
+    zmax = g.z0 + (g.Nz - 1) * g.dz
+    last = O.time_of_flight(0.0, 0.0, (g.Nx - 1) * g.dx, (g.Ny - 1) * g.dy, zmax, g.c) + 3.0 / g.alpha
+    assert g.t0 + g.Nt / g.fs >= last
+
+
 def test_dense_A_equals_dft_of_time_domain_echo():
     """A x at the kept bins equals the direct DFT of the brute-force simulated
     A-scan of Eq. (2) (periodically folded), for random scatterers."""
