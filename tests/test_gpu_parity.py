@@ -99,6 +99,22 @@ def test_strategies_select_and_apply(sfs, strategy, per_position):
     assert rel_err(to_host(op.apply_A(to_dev(x))), A @ x.ravel()) <= TOL_OP
 
 
+@pytest.mark.parametrize("name", ["line2d", "vol32"])
+def test_host_time_gate_pulse_rate_and_band_equal_the_oracle(sfs, name):
+    """The library's readings of the geometry (t0 on the sample grid, the
+    pulse rate alpha, the candidate band and its rung) are the oracle's."""
+    w = synth.WORKLOADS[name]
+    params = synth.geometry_params(name)
+    go = oracle_geometry(params)
+    op = sfs.Operator.select(sfs.Geometry(**params), O.SEL_CONTIGUOUS, w["M"], False, 0)
+    info = op.info
+    assert round(info["t0"] * go.fs) == round(go.t0 * go.fs)
+    assert abs(info["t0"] * go.fs - round(info["t0"] * go.fs)) <= 1e-6
+    assert info["alpha"] == pytest.approx(go.alpha, rel=1e-13)
+    k_lo, k_hi, b = O.candidate_band(go, w["M"])
+    assert (info["k_lo"], info["k_hi"]) == (k_lo, k_hi) and info["band_db"] == b
+
+
 def test_directivity_geometry(sfs):
     params = geom_params(Nx=10, Ny=8, Nz=12, dz=0.2e-3, Nt=256, theta=math.radians(30))
     g, op, go, idx = make_pair(sfs, params, M=9)
