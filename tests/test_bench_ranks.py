@@ -60,3 +60,31 @@ def test_reference_arm_prints_on_rank_0_only(capsys):
         sys.argv = saved
     assert bench.run_reference(args, rank=1, world=2) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_keeps_the_contract(capsys):
+    """rank 0 of --impl reference times the FP64 oracle on the host (here the
+    small line-scan workload, about a second of work) and prints one JSON line
+    with the contract's keys: the oracle as cpu_baseline, an e2e with no
+    copies, and the same metric and unit as the GPU arm."""
+    import json
+    import bench
+    saved = sys.argv
+    sys.argv = ["bench.py", "--impl", "reference", "--workload", "line2d", "--steps", "2",
+                "--warmup", "1", "--cpu-seconds", "1"]
+    try:
+        args = bench.parse()
+    finally:
+        sys.argv = saved
+    bench.run_reference(args, rank=0, world=1)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and "unavailable" not in d
+    assert d["metric"] == "FISTA iterations/s" and d["unit"] == "it/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 1
+    assert d["ms_per_step"] > 0 and d["dtype"] == "f64" and d["data"] == "synthetic"
+    assert d["config"]["workload"].startswith("line2d")
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
