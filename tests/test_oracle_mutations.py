@@ -310,6 +310,96 @@ def test_contiguous_block_off_centre_is_caught(monkeypatch):
     assert_caught([P.test_contiguous_is_centred_on_peak_and_equispaced_spread])
 
 
+def test_maximal_set_by_smallest_magnitude_is_caught(monkeypatch):
+    """Phi_max sorted the wrong way (the M weakest bins)."""
+    def wrong(g, M):
+        e, _ = SO.pulse_weights(g)
+        return sorted(sorted(range(len(e)), key=lambda k: (e[k], k))[:M])
+    plant(monkeypatch, "maximal_set", wrong)
+    assert_caught([P.test_maximal_set_holds_the_largest_pulse_magnitudes])
+
+
+def test_energy_draw_ignoring_the_weights_is_caught(monkeypatch):
+    """Phi_nrg drawn uniformly among the bins with energy (q_k dropped)."""
+    orig = SO.energy_subset
+    plant(monkeypatch, "energy_subset",
+          lambda weights, M, stream: orig([1 if v > 0 else 0 for v in weights], M, stream))
+    assert_caught([P.test_energy_draw_follows_the_pulse_energy])
+
+
+def test_equispaced_without_the_half_cell_is_caught(monkeypatch):
+    """idx_i = k_lo + floor(i |C| / M): the points at the cells' left edges."""
+    orig = SO.select_indices
+
+    def wrong(g, strategy, M, per_position, seed):
+        if strategy != SO.SEL_EQUISPACED:
+            return orig(g, strategy, M, per_position, seed)
+        k_lo, k_hi, _ = SO.candidate_band(g, M)
+        i = np.arange(M, dtype=np.int64)
+        idx = np.empty((g.S, M), dtype=np.int32)
+        idx[:] = k_lo + (i * (k_hi - k_lo + 1)) // M
+        return idx
+    plant(monkeypatch, "select_indices", wrong)
+    assert_caught([P.test_contiguous_is_centred_on_peak_and_equispaced_spread])
+
+
+def test_fast_operator_gathering_the_neighbouring_bin_is_caught(monkeypatch):
+    """The kept bin of (s, m) looked up one entry too far in the union
+    (a searchsorted off by one), clamped to the union."""
+    orig = SO.LateralFFTOperator.__init__
+
+    def wrong(self, g, idx, workers=1):
+        orig(self, g, idx, workers)
+        self.u_of = np.minimum(self.u_of + 1, self.bins.size - 1)
+    monkeypatch.setattr(SO.LateralFFTOperator, "__init__", wrong)
+    assert_caught([(P.test_lateral_fft_operator_equals_dense, (5, 4, 6), O.SEL_RANDOM)])
+
+
+def test_backtracking_with_the_test_inverted_is_caught(monkeypatch):
+    """The step accepted when F exceeds the quadratic model (>= for <=)."""
+    def wrong(apply_A, apply_AH, y, lam, L0, eta, iters, L_history=None):
+        y = np.asarray(y, dtype=np.complex128)
+        x_prev = np.zeros_like(np.asarray(apply_AH(y), dtype=np.complex128))
+        gamma = x_prev.copy()
+        beta, _ = SO.fista_momentum(iters)
+        L = float(L0)
+
+        def f(v):
+            r = apply_A(v) - y
+            return 0.5 * float(np.vdot(r, r).real)
+        for k in range(iters):
+            grad = apply_AH(apply_A(gamma) - y)
+            fg = f(gamma)
+            for _ in range(60):
+                x = SO.soft_threshold(gamma - grad / L, lam / L)
+                d = x - gamma
+                q = fg + float(np.vdot(d, grad).real) + 0.5 * L * float(np.vdot(d, d).real)
+                if f(x) >= q:
+                    break
+                L *= eta
+            gamma = x + beta[k] * (x - x_prev)
+            x_prev = x
+            if L_history is not None:
+                L_history.append(L)
+        return x_prev
+    plant(monkeypatch, "fista_backtracking", wrong)
+    assert_caught([P.test_backtracking_without_backtracks_is_fista])
+
+
+def test_resume_restarting_the_momentum_is_caught(monkeypatch):
+    """A resumed FISTA run that restarts t at 1 instead of carrying t_{K+1}."""
+    orig = SO.fista
+
+    def wrong(apply_A, apply_AH, y, lam, L, iters, x0=None, history=None, resume=None,
+              return_state=False):
+        if resume is not None:
+            resume = (resume[0], resume[1], 1.0)
+        return orig(apply_A, apply_AH, y, lam, L, iters, x0=x0, history=history, resume=resume,
+                    return_state=return_state)
+    plant(monkeypatch, "fista", wrong)
+    assert_caught([P.test_fista_resumed_from_its_state_equals_one_run])
+
+
 # ---------------------------------------------------------- control ---
 
 def test_unmutated_oracle_passes_the_same_pins():
@@ -334,7 +424,11 @@ def test_unmutated_oracle_passes_the_same_pins():
                     P.test_band_sizes_of_workloads,
                     P.test_random_subset_uniform_chi_square,
                     P.test_splitmix64_matches_published_outputs,
-                    P.test_contiguous_is_centred_on_peak_and_equispaced_spread]) == []
+                    P.test_contiguous_is_centred_on_peak_and_equispaced_spread,
+                    P.test_maximal_set_holds_the_largest_pulse_magnitudes,
+                    P.test_energy_draw_follows_the_pulse_energy,
+                    P.test_backtracking_without_backtracks_is_fista,
+                    P.test_fista_resumed_from_its_state_equals_one_run]) == []
 
 
 # ------------------------------------------- Cramér-Rao bound oracle ---
