@@ -369,6 +369,10 @@ def sfs_version() -> str:
 def _group_args(ops, ys, Ls, xs):
     import torch
     n = len(ops)
+    if len(ys) != n or len(Ls) != n or (xs is not None and len(xs) != n):
+        raise ValueError("one measurement tensor, one L (and one result tensor) per operator: "
+                         "%d operators, %d y, %d L%s" % (n, len(ys), len(Ls),
+                                                        "" if xs is None else ", %d x" % len(xs)))
     if xs is None:
         xs = [torch.empty((int(y.shape[0]),) + op.shape_x, dtype=torch.complex64, device=y.device)
               for op, y in zip(ops, ys)]

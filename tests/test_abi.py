@@ -49,6 +49,18 @@ def test_grouped_order_setter(sfs):
         sfs.set_grouped_order(order)
 
 
+def test_grouped_argument_lists_must_match(sfs):
+    """The grouped and persistent solves take one y, one L (and one x) per
+    operator; lists of other lengths are refused before anything reaches
+    the library."""
+    ops = [object(), object()]
+    for ys, Ls, xs in (([object()], [1.0, 1.0], None), ([object()] * 2, [1.0], None),
+                       ([object()] * 2, [1.0, 1.0], [object()])):
+        for persistent in (False, True):
+            with pytest.raises(ValueError):
+                sfs.fista_grouped(ops, ys, Ls, -0.05, 5, xs=xs, persistent=persistent)
+
+
 def test_geometry_validation(sfs):
     ok = geom_params(Nx=8, Ny=8, Nz=4, dz=1e-4, Nt=64)
     g = sfs.Geometry(**ok)
