@@ -3,7 +3,10 @@ FISTA with complex soft thresholding and the power-iteration Lipschitz bound.
 
 TEST INFRASTRUCTURE ONLY.  This package is the independent checker of the
 CUDA library.  Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
-CPU-baseline / reference legs may import it.  The product library never
+CPU-baseline and reference legs may import it, plus the two checks bench.py
+reports beside its studies, outside every timed region: the index sets of
+the strategy study compared with the oracle's bit for bit, and the precision
+study's errors against FP64.  The product library never
 imports, links or executes anything under ``oracle/``, and nothing here
 imports the product library.  The only code the two sides share is the
 seeded input generator package ``synth`` (scenes, noise), which holds none
