@@ -171,7 +171,9 @@ int sfs_select_indices(const sfs_geometry* g, int strategy, int M,
  * sfs_select_indices does (bit-identical), then builds the operator as
  * sfs_operator_from_indices does.  idx_out_host (int32 [S][M]) and
  * mask_out_host (uint32 [S][ceil((Nt/2+1)/32)], bit k of position s set when
- * bin k is kept) may be NULL.  Synchronises the device.
+ * bin k is kept) may be NULL.  Synchronises the device.  Errors: as
+ * sfs_select_indices and sfs_operator_from_indices (SFS_ERR_INVALID_ARG,
+ * SFS_ERR_BAND_TOO_NARROW, SFS_ERR_OOM, SFS_ERR_CUDA).
  */
 int sfs_select_freqs(sfs_geometry* g, int strategy, int M, int per_position,
                      uint64_t seed, int32_t* idx_out_host,
@@ -217,6 +219,11 @@ int sfs_operator_info(const sfs_operator* op, sfs_operator_info_t* info);
  * Forward projection phi_{Phi H}: y = A x (Sec. IV-A; computed by the fast
  * transform of Sec. IV-B, Algorithm 2, restricted to the kept bins).
  * x_dev: c64 [Nz][Ny][Nx] (read), y_dev: c64 [S][M] (written).
+ * Errors: SFS_ERR_INVALID_ARG (null operator, null or misaligned pointer),
+ * SFS_ERR_CUDA (a launch failed).  A bounded device wait that gives up does
+ * not fail the call (it is asynchronous): it sets the operator's error flag,
+ * which sfs_check_status and the next synchronising call report as
+ * SFS_ERR_TIMEOUT.
  */
 int sfs_apply_A(sfs_operator* op, const void* x_dev, void* y_dev, void* stream);
 
@@ -224,7 +231,7 @@ int sfs_apply_A(sfs_operator* op, const void* x_dev, void* y_dev, void* stream);
  * Backward projection beta_{Phi H}: x = A^H y (Sec. IV-A; the composition
  * beta_H o beta_Phi of Sec. IV-B).  y_dev: c64 [S][M] (read),
  * x_dev: c64 [Nz][Ny][Nx] (written).  With y the measurements this is the
- * one-step "compressed SAFT" image of Remark 1.
+ * one-step "compressed SAFT" image of Remark 1.  Errors: as sfs_apply_A.
  */
 int sfs_apply_AH(sfs_operator* op, const void* y_dev, void* x_dev, void* stream);
 
@@ -442,6 +449,9 @@ int sfs_lista_adam(sfs_lista* net, const void* grad_params_dev, float lr, float 
 /*
  * ||A^H y||_inf (used by the regularisation rule lambda = mu ||beta(y)||_inf
  * of Sec. VII).  Synchronises `stream`; writes the value to *out_host.
+ * Errors: SFS_ERR_INVALID_ARG (null or misaligned argument), SFS_ERR_CUDA,
+ * SFS_ERR_TIMEOUT (a kernel's bounded wait gave up), SFS_ERR_NON_FINITE (NaN
+ * or Inf in A^H y).
  */
 int sfs_max_abs_AH(sfs_operator* op, const void* y_dev, double* out_host,
                    void* stream);
@@ -453,7 +463,9 @@ int sfs_max_abs_AH(sfs_operator* op, const void* y_dev, double* out_host,
  * changes by less than rtol (checked every few iterations) or after
  * max_iter iterations; *L_out = estimate * (1 + safety).  Synchronises
  * `stream`.  Returns SFS_ERR_NOT_CONVERGED (with *L_out set) when max_iter
- * is reached.
+ * is reached.  Other errors: SFS_ERR_INVALID_ARG (null operator or output,
+ * max_iter < 1, negative or NaN rtol or safety), SFS_ERR_NON_FINITE (a NaN or
+ * Inf Rayleigh quotient), SFS_ERR_OOM, SFS_ERR_CUDA, SFS_ERR_TIMEOUT.
  */
 int sfs_lipschitz(sfs_operator* op, int max_iter, double rtol, uint64_t seed,
                   double safety, double* L_out, void* stream);
@@ -466,7 +478,8 @@ int sfs_lipschitz(sfs_operator* op, int max_iter, double rtol, uint64_t seed,
  * *sigma_hat_out (may be NULL) = ||A||_F / N^(1/4), N = min(S M, V): the
  * geometric mean of the bounds ||A||_F / sqrt(N) <= sigma_max <= ||A||_F
  * (Eq. (sigma_hat)).  The estimate is not guaranteed to bound sigma_max from
- * above; sfs_lipschitz is the safe choice for FISTA's step.
+ * above; sfs_lipschitz is the safe choice for FISTA's step.  Errors:
+ * SFS_ERR_INVALID_ARG (null operator or fro2_out).
  */
 int sfs_frobenius(const sfs_operator* op, double* fro2_out, double* sigma_hat_out);
 
@@ -533,7 +546,9 @@ int sfs_mixing_band(const sfs_geometry* g, int32_t* k_lo, int32_t* k_hi);
 int sfs_mixing_create(sfs_operator* band, int M, const int32_t* idx_host, const int8_t* xi_host,
                       sfs_mixing** out);
 int sfs_mixing_destroy(sfs_mixing* mx);
-/* y = A_mix x: x c64 [Nz][Ny][Nx], y c64 [S][M] (device, 16-byte aligned). */
+/* y = A_mix x: x c64 [Nz][Ny][Nx], y c64 [S][M] (device, 16-byte aligned).
+ * Errors of this and the next three calls: as their unmixed counterparts
+ * (sfs_apply_A, sfs_apply_AH, sfs_lipschitz, sfs_fista). */
 int sfs_apply_A_mixed(sfs_mixing* mx, const void* x_dev, void* y_dev, void* stream);
 /* x = A_mix^H y. */
 int sfs_apply_AH_mixed(sfs_mixing* mx, const void* y_dev, void* x_dev, void* stream);
@@ -623,7 +638,9 @@ int sfs_fista(sfs_operator* op, const void* y_dev, double lambda, double L,
  * contraction kernels during the last sfs_fista call made with
  * SFS_FISTA_TIME_KERNELS (the event nodes of its replayed graph, over the
  * sampled iterations).  Synchronises the operator's device.  n_out_host
- * receives the number of iterations averaged.
+ * receives the number of iterations averaged (0, with zero times, when no
+ * such call has run).  Errors: SFS_ERR_INVALID_ARG (null operator or
+ * output), SFS_ERR_CUDA.
  */
 int sfs_kernel_times(sfs_operator* op, double* fwd_ms, double* adj_ms,
                      int32_t* n_out_host);
@@ -635,7 +652,10 @@ int sfs_kernel_times(sfs_operator* op, double* fwd_ms, double* adj_ms,
  * sum to the time of those iterations): ms4_host[0] forward contraction, [1]
  * residual planes (inverse FFT, residual, forward FFT), [2] adjoint
  * contraction, [3] update planes (inverse FFT, FISTA step, forward FFT).
- * Synchronises the operator's device.
+ * Synchronises the operator's device.  n_out_host (may be NULL) receives
+ * the number of iterations averaged (0, with zero times, when no such call
+ * has run).  Errors: SFS_ERR_INVALID_ARG (null operator or ms4_host),
+ * SFS_ERR_CUDA.
  */
 int sfs_stage_times(sfs_operator* op, double* ms4_host, int32_t* n_out_host);
 
